@@ -1,0 +1,339 @@
+"""Throughput of the whole hot path (views -> ORB -> matching) on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--plain-steps P]
+
+Workload (one step = one image pair through match_pair, all stages): a
+1024x768 uint8 synthetic textured pair under extreme tilt (absolute tilt 75
+deg, transition tilt near 85 deg, noise sigma 2), 43 simulated views per image
+(t = sqrt2^k, k <= 5, phi step 72/t), ORB with 8 levels at scale 1.2, 1000
+keypoints per view, FAST threshold 20, rBRIEF-256, brute-force Hamming match of
+the pooled descriptors with ratio 4/5.  Every rank processes its own pairs
+(weak scaling, no collective on the data path).
+
+The JSON line reports image pairs/s (views/s = 86 x pairs/s beside it), with
+inputs resident in HBM; `e2e` is the same metric through the C ABI with the
+images copied from pinned host memory and the accepted pairs copied back inside
+the timed region.  `roofline` is for the dominant kernel (the Hamming matcher,
+integer popc bound); `cpu_baseline` is the CPU oracle timed on a bounded
+sample of the same workload.  `--impl reference` times the CPU oracle as the
+reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H, W, KMAX, LEVELS, NFEAT, THR = 768, 1024, 5, 8, 1000, 20
+WORKLOAD = "asift_pair_1024x768_extreme_tilt_43views_orb8x1000"
+SM_COUNT = 152
+POPC_PER_SM_CLK = 16       # 32-bit population count: 16 results / clock / SM
+POPC_PER_PAIR = 8          # a 256-bit Hamming distance = 8 x popc(32-bit xor)
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _pair(rank: int, i: int):
+    from paper_2503_03479_gb300 import synth
+    return synth.pair_extreme_tilt(seed=2000 + 97 * rank + i)
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                out, _ = self.p.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        if not getattr(self, "lines", None):
+            return None
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+def oracle_sample(rank: int = 0):
+    """Times the CPU oracle on a bounded sample of one pair and scales it to a
+    whole pair: warp + ORB of 6 views (2 per tilt class of each image) scaled by
+    the per-view pixel count to all 86 views, and the brute-force matcher on
+    1500 queries against a full-size train pool scaled to all queries."""
+    import oracle as O
+    p = _pair(rank, 0)
+    pat = O.pattern()
+    t_views, px_done, px_total = 0.0, 0, 0
+    picks = {0: [0, 6, 30], 1: [3, 15, 42]}
+    for im_i, img in enumerate((p.img1, p.img2)):
+        views = O.view_table(H, W, KMAX)
+        px_total += sum(v.Wr * v.Hr for v in views)
+        for vi in picks[im_i]:
+            v = views[vi]
+            t0 = time.perf_counter()
+            vo = O.warp_view(img, v)
+            O.orb_view(vo.u8, vo.mask, LEVELS, NFEAT, THR, pat)
+            t_views += time.perf_counter() - t0
+            px_done += v.Wr * v.Hr
+    from paper_2503_03479_gb300 import synth
+    n_pool = 43 * NFEAT
+    nq = 1500
+    q = synth.random_descriptors(nq, 1)
+    t = synth.random_descriptors(n_pool, 2)
+    t0 = time.perf_counter()
+    O.match(q, t)
+    t_match = (time.perf_counter() - t0) * (n_pool / nq)
+    t_pair = t_views * px_total / px_done + t_match
+    sample = (f"warp+ORB of 6 of 86 views (scaled by canvas pixels), match of {nq} of {n_pool} queries "
+              f"(scaled); single-threaded oracle")
+    return 1.0 / t_pair, t_pair, sample
+
+
+def run_reference(args):
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup if args.warmup < 1 else 0):
+        oracle_sample()
+    times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        v, t_pair, sample = oracle_sample()
+        times.append(t_pair)
+    t = statistics.mean(times)
+    val = 1.0 / t
+    line = {"impl": "reference", "metric": "image pairs/s (warp+ORB+match)", "value": val, "unit": "pairs/s",
+            "n_gpus": world, "steps": len(times), "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+int",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "H": H, "W": W, "views_per_image": 43,
+                                            "levels": LEVELS, "features_per_view": NFEAT},
+            "cpu_baseline": {"value": val, "unit": "pairs/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import torch
+    rank, world, local = _dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2503_03479_gb300 import build as B
+    if rank == 0 or world == 1:
+        B.build()
+    if dist:
+        dist.barrier()
+    from paper_2503_03479_gb300 import asift as A
+
+    ctx = A.Context(n_levels=LEVELS, n_features=NFEAT, fast_threshold=THR)
+    pc = ctx.pair_cfg(kmax=KMAX)
+    n_pairs = 2
+    pairs = [_pair(rank, i) for i in range(n_pairs)]
+    d1 = [torch.from_numpy(p.img1).cuda() for p in pairs]
+    d2 = [torch.from_numpy(p.img2).cuda() for p in pairs]
+    ws = ctx.match_pair_workspace((H, W), (H, W), pc)
+    nv = len(A.view_table(H, W, KMAX))
+    cap = nv * NFEAT
+    out = torch.zeros(cap * A.PAIR_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    n_out = torch.zeros(1, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")     # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        ctx.match_pair(d1[i % n_pairs], d2[i % n_pairs], pc, out, n_out, ws)
+
+    for i in range(args.warmup):
+        step(i)
+        flush.zero_()
+    torch.cuda.synchronize()
+    if ctx.read_status(ws) != 0:
+        raise RuntimeError("device status word set during warm-up")
+
+    # ---- timed region: K steps, L2 flushed between steps (outside the events)
+    ctx.profile(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stage_ms = []
+    l0 = A.launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            step(i)
+            ev[i][1].record(stream)
+            stage_ms.append(ctx.profile_read())
+            flush.zero_()
+        torch.cuda.synchronize()
+    launches = A.launch_count() - l0
+    if dist:
+        dist.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ctx.profile(False)
+    if ctx.read_status(ws) != 0:
+        raise RuntimeError("device status word set during the timed region")
+    t_max = ms
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * args.steps / (t_max / 1e3)
+
+    # ---- dominant kernel: the Hamming matcher, timed live by the stage events
+    st = {k: statistics.mean(s[k] for s in stage_ms) for k in stage_ms[0]}
+    n_acc = int(n_out.item())
+    kp1, dd1, kp2, dd2, _ = ctx.inspect_pair((H, W), (H, W), pc, ws)
+    n1, n2 = len(kp1), len(kp2)
+    peaks = _peaks()
+    clocks = clk.summary()
+    f_clk = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
+    peak_popc = SM_COUNT * POPC_PER_SM_CLK * f_clk / 1e12          # T popc / s
+    achieved = n1 * n2 * POPC_PER_PAIR / (st["match"] / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": "hamming_top2_kernel+merge_kernel", "achieved": achieved,
+                "peak": peak_popc, "unit": "Tpopc/s", "frac": achieved / peak_popc, "traffic": None,
+                "peak_source": f"derived: {SM_COUNT} SMs x {POPC_PER_SM_CLK} popc/clk x {f_clk/1e6:.0f} MHz"}
+
+    # ---- plain per-view form (same kernels, one launch per view and stage)
+    plain = None
+    if args.plain_steps > 0:
+        pcp = ctx.pair_cfg(kmax=KMAX, per_view=True)
+        wsp = ctx.match_pair_workspace((H, W), (H, W), pcp)
+        for i in range(2):
+            ctx.match_pair(d1[0], d2[0], pcp, out, n_out, wsp)
+        torch.cuda.synchronize()
+        evp = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.plain_steps)]
+        for i in range(args.plain_steps):
+            evp[i][0].record(stream)
+            ctx.match_pair(d1[i % n_pairs], d2[i % n_pairs], pcp, out, n_out, wsp)
+            evp[i][1].record(stream)
+            flush.zero_()
+        torch.cuda.synchronize()
+        msp = sum(a.elapsed_time(b) for a, b in evp) / args.plain_steps
+        plain = {"value": 1e3 / msp, "unit": "pairs/s", "ms_per_step": msp}
+
+    # ---- end to end through the C ABI with host buffers
+    h1 = [torch.from_numpy(p.img1).pin_memory() for p in pairs]
+    h2 = [torch.from_numpy(p.img2).pin_memory() for p in pairs]
+    hout = torch.empty(cap * A.PAIR_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    hn = torch.empty(1, dtype=torch.int32).pin_memory()
+    e2e_t = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d1[0].copy_(h1[i % n_pairs], non_blocking=True)
+        d2[0].copy_(h2[i % n_pairs], non_blocking=True)
+        ctx.match_pair(d1[0], d2[0], pc, out, n_out, ws)
+        hn.copy_(n_out, non_blocking=True)
+        hout.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_t.append(time.perf_counter() - t0)
+    e2e = {"value": world / statistics.mean(e2e_t), "unit": "pairs/s",
+           "h2d_bytes_per_step": 2 * H * W, "d2h_bytes_per_step": int(hout.numel() + 4)}
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            v, t_pair, sample = oracle_sample()
+            cpu = {"value": v, "unit": "pairs/s", "cores": 1, "kind": "oracle", "sample": sample}
+        line = {"metric": "image pairs/s (warp+ORB+match)", "value": value, "unit": "pairs/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+int",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "H": H, "W": W, "views_per_image": nv, "levels": LEVELS,
+                           "features_per_view": NFEAT, "fast_threshold": THR, "ratio": "4/5",
+                           "l2": "flushed between steps (256 MB write)", "form": "batched: one launch per stage"},
+                "views_per_s": value * 2 * nv,
+                "stage_ms": st,
+                "keypoints": [n1, n2], "accepted": n_acc,
+                "plain_per_view": plain,
+                "batched_vs_plain": (value / world) / plain["value"] if plain else None,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,265 @@
+/*
+ * asift.h -- C ABI of libasift, a GB300 (sm_103a) implementation of the
+ * data-parallel hot path of "Feature Point Extraction for Extra-Affine Image"
+ * (arXiv 2503.03479): affine view simulation over tilt t and longitude phi
+ * (Sec. III-B, Eq. (2)) with a Gaussian anti-alias along the tilt axis and
+ * Lanczos-3 resampling (Eq. (3)-(4)), ORB on every view (Sec. III-B: FAST-9 +
+ * Harris + NMS on a 1.2 pyramid, intensity-centroid orientation, steered
+ * rBRIEF-256), and brute-force Hamming matching with the nearest /
+ * second-nearest ratio test over all views of two images (Sec. III-B, IV-C).
+ *
+ * Problem statement (Sec. III-A, IV-B): given two 8-bit images of one planar
+ * scene, return matched point pairs (x1, y1) <-> (x2, y2).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named d_* are DEVICE pointers owned by the caller; h_* are host
+ *    pointers owned by the caller.  The library never frees caller memory.
+ *  - Work is enqueued asynchronously on `stream` (a cudaStream_t, NULL = the
+ *    legacy default stream).  Host arrays passed in (view tables) are consumed
+ *    before the call returns.
+ *  - The hot-path calls allocate no device memory: scratch comes from a
+ *    caller-provided workspace whose size is returned by the *_workspace_size
+ *    queries.  Only asift_ctx_create / asift_plan_create allocate.
+ *  - Return value: ASIFT_OK when the work was enqueued; ASIFT_ERR_ARG for a bad
+ *    argument (nothing enqueued); ASIFT_ERR_CUDA for a CUDA launch/copy error.
+ *    Conditions found on the device while the work runs (a candidate buffer
+ *    overflow, a bounded wait that timed out) are written to the int32 status
+ *    word at the start of the workspace; read it with asift_read_status after
+ *    the stream has progressed past the call.
+ *  - No exceptions cross the ABI.  A context is not thread-safe: use one per
+ *    host thread.
+ */
+#ifndef ASIFT_H
+#define ASIFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ASIFT_API __attribute__((visibility("default")))
+#else
+#define ASIFT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ASIFT_OK = 0,
+    ASIFT_ERR_ARG = -1,      /* invalid argument; nothing was enqueued            */
+    ASIFT_ERR_CUDA = -2,     /* CUDA runtime error (launch, copy, no device)      */
+    ASIFT_ERR_CAPACITY = -3, /* device-side buffer overflow (status word)         */
+    ASIFT_ERR_TIMEOUT = -4,  /* a bounded device wait gave up (status word)       */
+    ASIFT_ERR_NOMEM = -5     /* allocation failed in a create call                */
+} asift_status;
+
+#define ASIFT_MAX_GAUSS 48   /* Gaussian taps g_0..g_{K}, K < 48 (t <= 11.3)    */
+#define ASIFT_MAX_LEVELS 12  /* ORB pyramid levels                              */
+
+/*
+ * One simulated view (Eq. (2) with psi = 0, s = 1, no translation).
+ * Geometry, as both this library and any independent check define it:
+ *   canvas pixel (i, j) of the Wr x Hr rotated canvas takes the source point
+ *   p = R(phi)^T ((i, j) - c_r) + c_s, c = (size - 1)/2, in Q32 fixed point:
+ *     px = cq (2i - Wr + 1) + sq (2j - Hr + 1) + (W - 1) 2^31
+ *     py = -sq (2i - Wr + 1) + cq (2j - Hr + 1) + (H - 1) 2^31
+ *   view pixel (x', j) samples canvas row j at X = tq (2x' - Wv + 1) + (Wr - 1) 2^31.
+ */
+typedef struct {
+    int32_t k, j;           /* tilt exponent (t = sqrt2^k), longitude index      */
+    int32_t W, H;           /* source image size                                  */
+    int32_t Wr, Hr;         /* canvas size: ceil(W|cos|+H|sin| - 1e-9), ceil(W|sin|+H|cos| - 1e-9) */
+    int32_t Wv, Hv;         /* view size: ceil(Wr / t), Hr                        */
+    int32_t K;              /* Gaussian half width ceil(4 sigma)                  */
+    int32_t pad0;
+    double t, phi_deg;      /* tilt, longitude (degrees)                          */
+    double sigma;           /* 0.8 sqrt(t^2 - 1) (0 at t = 1)                     */
+    int64_t cq, sq, tq;     /* rint(cos phi 2^31), rint(sin phi 2^31), rint(t 2^31) */
+    float g[ASIFT_MAX_GAUSS]; /* normalised Gaussian taps g_0..g_K (fp32 of fp64) */
+} asift_view_desc;
+
+/* ORB settings (Sec. III-B / IV-C; defaults of the 320x240 configuration). */
+typedef struct {
+    int32_t n_levels;       /* pyramid levels, scale 1.2 (default 4)             */
+    int32_t n_features;     /* keypoints per view (default 500)                  */
+    int32_t fast_threshold; /* FAST-9 threshold (default 20)                     */
+    int32_t cand_per_mpx;   /* candidate capacity per level, per 10^6 px + 4096 (default 60000) */
+} asift_orb_cfg;
+
+/* A keypoint of a view: position in its pyramid level, orientation bin
+ * (angle = 12 * bin degrees), Harris response x 25. */
+typedef struct {
+    int16_t x, y;
+    uint8_t level, bin;
+    uint16_t view;          /* view index within the call                        */
+    int64_t r25;
+} asift_keypoint;
+
+/* Result of matching one query descriptor. */
+typedef struct {
+    int32_t best;           /* index of the nearest train descriptor (-1 if none) */
+    uint16_t d1, d2;        /* nearest / second-nearest Hamming distance (257 = none) */
+} asift_match;
+
+/* An accepted match, back-projected to source-image pixel coordinates. */
+typedef struct {
+    float x1, y1, x2, y2;
+    int32_t q, t;           /* pool indices in image 1 / image 2                 */
+    uint16_t d1, d2;
+} asift_pair_match;
+
+typedef struct asift_ctx asift_ctx;
+
+/* Creates a context on the current CUDA device: generates the seeded rBRIEF-256
+ * sampling pattern (30 steered copies, ORB [23]) and the orientation sector
+ * table on the host and uploads them (allocates ~31 KB).  cfg NULL -> defaults.
+ * Errors: ASIFT_ERR_ARG (bad cfg), ASIFT_ERR_NOMEM, ASIFT_ERR_CUDA. */
+ASIFT_API asift_status asift_ctx_create(asift_ctx **ctx, const asift_orb_cfg *cfg, uint64_t pattern_seed);
+ASIFT_API void asift_ctx_destroy(asift_ctx *ctx);
+ASIFT_API asift_status asift_ctx_orb_cfg(const asift_ctx *ctx, asift_orb_cfg *out);
+/* Copies the steered pattern (int8 [30][256][4] = {px,py,qx,qy}) to h_out. */
+ASIFT_API asift_status asift_ctx_pattern(const asift_ctx *ctx, int8_t *h_out);
+
+/* View table of the sampling rule of Sec. III-B: t = sqrt(2)^k for k = 0..kmax,
+ * phi = j 72/t degrees for all j >= 0 with j 72/t < 180 (one view at t = 1).
+ * Host only.  Writes min(n, cap) descriptors to h_out (may be NULL) and the
+ * total count to *n_views.  Errors: ASIFT_ERR_ARG if H, W < 1 or kmax outside
+ * [0, 7]. */
+ASIFT_API asift_status asift_view_table(int H, int W, int kmax, asift_view_desc *h_out, int cap, int *n_views);
+/* One descriptor for an arbitrary tilt t in [1, 11.4) and longitude phi (deg). */
+ASIFT_API asift_status asift_make_view(int H, int W, double t, double phi_deg, asift_view_desc *h_out);
+
+/* Host-only copies of the tables a context uploads: the seeded steered rBRIEF
+ * pattern (int8 [30][256][4] = {px, py, qx, qy}; SplitMix64 -> Box-Muller
+ * N(0, (31/5)^2) rounded ties-to-even inside the radius-15 disc, p != q;
+ * rotated by 12 b degrees and rounded half away from zero for b < 15, negated
+ * for b >= 15) and the orientation sector boundaries (int64 [30][2], Q30 unit
+ * vectors at 12 b - 6 degrees, negated for b >= 15).  ORB [23] steering with a
+ * 2 pi / 30 angle discretisation.  Errors: ASIFT_ERR_ARG on NULL. */
+ASIFT_API asift_status asift_pattern_table(uint64_t seed, int8_t *h_out);
+ASIFT_API asift_status asift_bin_table(int64_t *h_out);
+
+/* Pyramid sizes of a view: W_l = round-half-up(Wv (5/6)^l), exact integers. */
+ASIFT_API int asift_level_size(int n0, int level);
+
+/* Bytes of the view arena for n views: sum of Wv*Hv (u8 views), same for masks. */
+ASIFT_API int64_t asift_views_bytes(const asift_view_desc *h_views, int n_views);
+
+/*
+ * asift_views -- simulate n_views views of one 8-bit image (Eq. (2)-(4)).
+ * d_img: H x W uint8 with row pitch `pitch` bytes (>= W).  View v is written
+ * at byte offset h_offsets[v] of d_view_u8 and d_mask (Wv*Hv bytes, pitch Wv)
+ * and, if d_view_f32 != NULL, at element offset h_offsets[v] of d_view_f32.
+ *   canvas C = Lanczos-3 rotation (normalised 6x6 weights, clamp-to-edge taps,
+ *              0 outside [-0.5, W-0.5) x [-0.5, H-0.5));
+ *   B = Gaussian (taps g) along canvas rows, clamped;
+ *   v = Lanczos-3 sample of B at X; u8 = clamp(rint(v)) ties-to-even;
+ *   mask = 1 iff canvas columns floor(X) and floor(X)+1 of row j map inside
+ *          [0.5, W-1.5] x [0.5, H-1.5].
+ * Workspace: asift_views_workspace_size(W, H, n_views).
+ */
+ASIFT_API size_t asift_views_workspace_size(int H, int W, int n_views);
+ASIFT_API asift_status asift_views(asift_ctx *ctx, const uint8_t *d_img, int H, int W, int pitch,
+                         const asift_view_desc *h_views, int n_views, const int64_t *h_offsets,
+                         float *d_view_f32, uint8_t *d_view_u8, uint8_t *d_mask,
+                         void *d_workspace, size_t ws_bytes, void *stream);
+
+/*
+ * orb_extract -- ORB on n_views views (ORB [23] as used in Sec. III-B).
+ * Inputs: views as written by asift_views (d_view_u8 / d_mask at h_offsets).
+ * Per view: n_levels pyramid levels (centre-aligned integer bilinear, scale
+ * 1.2), FAST-9 (strict, threshold) inside a 16 px border with the four corners
+ * of the 33x33 box mask-valid, Harris x25 (Sobel 3x3, 7x7 window, k = 1/25),
+ * 3x3 NMS (ties to the raster-first), per-level quota floor(N A_l / sum A)
+ * (remainder to level 0), top by (R25 desc, y, x), orientation bin from the
+ * centroid moments over the radius-15 disc, steered BRIEF on the level smoothed
+ * by [18 34 49 54 49 34 18]/256 per axis.
+ * Outputs (capacity n_views * n_features entries): keypoints and 32-byte
+ * descriptors in canonical order (view, level, selection order) packed from
+ * index 0; d_view_count[v] / d_view_offset[v] give each view's slice (int32).
+ * Workspace: orb_workspace_size.  Candidate overflow -> status word
+ * ASIFT_ERR_CAPACITY (the view's level keeps its first candidates; result then
+ * not defined).
+ */
+ASIFT_API size_t orb_workspace_size(const asift_ctx *ctx, const asift_view_desc *h_views, int n_views);
+ASIFT_API asift_status orb_extract(asift_ctx *ctx, const uint8_t *d_view_u8, const uint8_t *d_mask,
+                         const asift_view_desc *h_views, int n_views, const int64_t *h_offsets,
+                         asift_keypoint *d_kp, uint8_t *d_desc, int32_t *d_view_count,
+                         int32_t *d_view_offset, int32_t *d_total,
+                         void *d_workspace, size_t ws_bytes, void *stream);
+
+/*
+ * hamming_match -- brute-force matcher (Sec. III-B) with the ratio test
+ * (Sec. IV-C).  For each of nq query descriptors (d_q, nq x 32 bytes, bit i in
+ * byte i>>3 at position i&7) over nt train descriptors: best = argmin Hamming
+ * distance (lowest index on ties), d1 = its distance, d2 = min over r != best
+ * (257 if nt < 2).  Accepted iff nt >= 2 and ratio_den * d1 < ratio_num * d2,
+ * exactly in integers (ratio 0.8 = 4/5).  d_out[nq]; d_accept[nq] (uint8, may
+ * be NULL); *d_n_accepted (int32, may be NULL).
+ * nq and nt may come from the device: if d_nq / d_nt are non-NULL they hold
+ * the counts (int32) and nq / nt are only capacities.
+ * Workspace: hamming_workspace_size(nq, nt).
+ */
+ASIFT_API size_t hamming_workspace_size(int nq, int nt);
+ASIFT_API asift_status hamming_match(asift_ctx *ctx, const uint8_t *d_q, int nq, const int32_t *d_nq,
+                           const uint8_t *d_t, int nt, const int32_t *d_nt,
+                           int ratio_num, int ratio_den, asift_match *d_out, uint8_t *d_accept,
+                           int32_t *d_n_accepted, void *d_workspace, size_t ws_bytes, void *stream);
+
+/* View-set configuration of match_pair. */
+typedef struct {
+    int32_t kmax;           /* t = sqrt2^k, k = 0..kmax (default 5)             */
+    int32_t ratio_num, ratio_den; /* ratio test (default 4/5)                   */
+    int32_t per_view;       /* 1 = launch every stage once per view (the plain
+                               per-view form); 0 = one launch per stage over all
+                               views of both images                            */
+} asift_pair_cfg;
+
+/*
+ * match_pair -- the whole hot path for one image pair: the views of both
+ * images (sampling rule of Sec. III-B), ORB on every view, pooling of each
+ * image's keypoints in canonical order, brute-force matching of pool 1 against
+ * pool 2 with the ratio test, and back-projection of the accepted pairs to
+ * source-image coordinates.  d_out receives up to `cap` accepted pairs in
+ * query order; *d_n (int32) their count (may exceed cap: then the status word
+ * is ASIFT_ERR_CAPACITY).  Workspace: match_pair_workspace_size.
+ */
+ASIFT_API size_t match_pair_workspace_size(const asift_ctx *ctx, int H1, int W1, int H2, int W2,
+                                 const asift_pair_cfg *cfg);
+ASIFT_API asift_status match_pair(asift_ctx *ctx, const uint8_t *d_img1, int H1, int W1, int pitch1,
+                        const uint8_t *d_img2, int H2, int W2, int pitch2,
+                        const asift_pair_cfg *cfg, asift_pair_match *d_out, int cap, int32_t *d_n,
+                        void *d_workspace, size_t ws_bytes, void *stream);
+
+/* Debug view into match_pair's workspace after a call: device pointers to the
+ * pooled keypoints / descriptors / per-query matches of each image and the
+ * host view tables used.  Any output pointer may be NULL. */
+ASIFT_API asift_status match_pair_inspect(const asift_ctx *ctx, int H1, int W1, int H2, int W2,
+                                const asift_pair_cfg *cfg, void *d_workspace,
+                                asift_keypoint **d_kp1, uint8_t **d_desc1, int32_t **d_n1,
+                                asift_keypoint **d_kp2, uint8_t **d_desc2, int32_t **d_n2,
+                                asift_match **d_match);
+
+/* Synchronises `stream` and copies the status word at the start of a
+ * workspace to *h_status (ASIFT_OK, ASIFT_ERR_CAPACITY or ASIFT_ERR_TIMEOUT);
+ * clears it when clear != 0. */
+ASIFT_API asift_status asift_read_status(void *d_workspace, int clear, int32_t *h_status, void *stream);
+
+/* Stage timing of match_pair with CUDA events on the call's stream.  Stages:
+ * 0 input upload + conversion, 1 warp, 2 pyramid, 3 FAST/Harris/NMS,
+ * 4 top-N selection, 5 pool offsets + orientation + BRIEF, 6 Hamming match,
+ * 7 accepted-pair output.  Enabling creates the events (no device memory).
+ * asift_profile_read synchronises on the last recorded event and writes the
+ * milliseconds of each stage of the most recent match_pair to h_ms[0..n). */
+#define ASIFT_PROF_STAGES 8
+ASIFT_API asift_status asift_profile_enable(asift_ctx *ctx, int on);
+ASIFT_API asift_status asift_profile_read(asift_ctx *ctx, float *h_ms, int n);
+
+/* Number of kernels this library has launched in the calling process. */
+ASIFT_API int64_t asift_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ASIFT_H */

@@ -1,0 +1,356 @@
+"""Thin ctypes binding of libasift (include/asift.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  PyTorch provides device memory and the current CUDA stream.
+Importing this module loads ``_build/libasift.so``; if it is missing the import
+fails with an error telling how to build it (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libasift.so")
+
+ASIFT_OK, ASIFT_ERR_ARG, ASIFT_ERR_CUDA, ASIFT_ERR_CAPACITY, ASIFT_ERR_TIMEOUT, ASIFT_ERR_NOMEM = 0, -1, -2, -3, -4, -5
+_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_CAPACITY", -4: "ERR_TIMEOUT", -5: "ERR_NOMEM"}
+MAX_GAUSS = 48
+PATTERN_SEED = 250303479
+
+EXPORTED = ["asift_ctx_create", "asift_ctx_destroy", "asift_ctx_orb_cfg", "asift_ctx_pattern", "asift_view_table",
+            "asift_make_view", "asift_level_size", "asift_views_bytes", "asift_views_workspace_size", "asift_views",
+            "orb_workspace_size", "orb_extract", "hamming_workspace_size", "hamming_match",
+            "match_pair_workspace_size", "match_pair", "match_pair_inspect", "asift_read_status",
+            "asift_launch_count", "asift_pattern_table", "asift_bin_table", "asift_profile_enable",
+            "asift_profile_read"]
+PROF_STAGES = ["upload", "warp", "pyramid", "detect", "select", "orient_brief", "match", "pairs"]
+
+
+class AsiftError(RuntimeError):
+    def __init__(self, where: str, code: int):
+        super().__init__(f"{where} failed: {_NAMES.get(code, code)}")
+        self.code = code
+
+
+class ViewDesc(C.Structure):
+    _fields_ = [("k", C.c_int32), ("j", C.c_int32), ("W", C.c_int32), ("H", C.c_int32),
+                ("Wr", C.c_int32), ("Hr", C.c_int32), ("Wv", C.c_int32), ("Hv", C.c_int32),
+                ("K", C.c_int32), ("pad0", C.c_int32),
+                ("t", C.c_double), ("phi_deg", C.c_double), ("sigma", C.c_double),
+                ("cq", C.c_int64), ("sq", C.c_int64), ("tq", C.c_int64),
+                ("g", C.c_float * MAX_GAUSS)]
+
+
+class OrbCfg(C.Structure):
+    _fields_ = [("n_levels", C.c_int32), ("n_features", C.c_int32), ("fast_threshold", C.c_int32),
+                ("cand_per_mpx", C.c_int32)]
+
+
+class PairCfg(C.Structure):
+    _fields_ = [("kmax", C.c_int32), ("ratio_num", C.c_int32), ("ratio_den", C.c_int32), ("per_view", C.c_int32)]
+
+
+KP_DTYPE = np.dtype([("x", np.int16), ("y", np.int16), ("level", np.uint8), ("bin", np.uint8),
+                     ("view", np.uint16), ("r25", np.int64)])
+MATCH_DTYPE = np.dtype([("best", np.int32), ("d1", np.uint16), ("d2", np.uint16)])
+PAIR_DTYPE = np.dtype([("x1", np.float32), ("y1", np.float32), ("x2", np.float32), ("y2", np.float32),
+                       ("q", np.int32), ("t", np.int32), ("d1", np.uint16), ("d2", np.uint16)])
+
+_lib = None
+
+
+def load_library():
+    """Loads libasift.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libasift.so not found at {LIB_PATH}; build it with "
+                          "`python -m paper_2503_03479_gb300.build` (needs nvcc)")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, sz = C.c_void_p, C.c_int, C.c_int64, C.c_size_t
+    P = C.POINTER
+    sig = {
+        "asift_ctx_create": (i32, [P(vp), P(OrbCfg), C.c_uint64]),
+        "asift_ctx_destroy": (None, [vp]),
+        "asift_ctx_orb_cfg": (i32, [vp, P(OrbCfg)]),
+        "asift_ctx_pattern": (i32, [vp, vp]),
+        "asift_view_table": (i32, [i32, i32, i32, vp, i32, P(C.c_int)]),
+        "asift_make_view": (i32, [i32, i32, C.c_double, C.c_double, P(ViewDesc)]),
+        "asift_level_size": (i32, [i32, i32]),
+        "asift_views_bytes": (i64, [vp, i32]),
+        "asift_views_workspace_size": (sz, [i32, i32, i32]),
+        "asift_views": (i32, [vp, vp, i32, i32, i32, vp, i32, vp, vp, vp, vp, vp, sz, vp]),
+        "orb_workspace_size": (sz, [vp, vp, i32]),
+        "orb_extract": (i32, [vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
+        "hamming_workspace_size": (sz, [i32, i32]),
+        "hamming_match": (i32, [vp, vp, i32, vp, vp, i32, vp, i32, i32, vp, vp, vp, vp, sz, vp]),
+        "match_pair_workspace_size": (sz, [vp, i32, i32, i32, i32, P(PairCfg)]),
+        "match_pair": (i32, [vp, vp, i32, i32, i32, vp, i32, i32, i32, P(PairCfg), vp, i32, vp, vp, sz, vp]),
+        "match_pair_inspect": (i32, [vp, i32, i32, i32, i32, P(PairCfg), vp, vp, vp, vp, vp, vp, vp, vp]),
+        "asift_read_status": (i32, [vp, i32, P(C.c_int32), vp]),
+        "asift_launch_count": (i64, []),
+        "asift_pattern_table": (i32, [C.c_uint64, vp]),
+        "asift_bin_table": (i32, [vp]),
+        "asift_profile_enable": (i32, [vp, i32]),
+        "asift_profile_read": (i32, [vp, vp, i32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(where: str, code: int):
+    if code != ASIFT_OK:
+        raise AsiftError(where, code)
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def launch_count() -> int:
+    return int(load_library().asift_launch_count())
+
+
+def level_size(n0: int, l: int) -> int:
+    return int(load_library().asift_level_size(n0, l))
+
+
+def view_table(H: int, W: int, kmax: int) -> list[ViewDesc]:
+    L = load_library()
+    n = C.c_int()
+    _check("asift_view_table", L.asift_view_table(H, W, kmax, None, 0, C.byref(n)))
+    arr = (ViewDesc * n.value)()
+    _check("asift_view_table", L.asift_view_table(H, W, kmax, arr, n.value, C.byref(n)))
+    return list(arr)
+
+
+def pattern_table(seed: int = PATTERN_SEED) -> np.ndarray:
+    out = np.zeros((30, 256, 4), np.int8)
+    _check("asift_pattern_table", load_library().asift_pattern_table(seed, out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def bin_table() -> np.ndarray:
+    out = np.zeros((30, 2), np.int64)
+    _check("asift_bin_table", load_library().asift_bin_table(out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def make_view(H: int, W: int, t: float, phi_deg: float) -> ViewDesc:
+    v = ViewDesc()
+    _check("asift_make_view", load_library().asift_make_view(H, W, float(t), float(phi_deg), C.byref(v)))
+    return v
+
+
+def _view_array(views):
+    arr = (ViewDesc * len(views))()
+    for i, v in enumerate(views):
+        arr[i] = v
+    return arr
+
+
+def view_offsets(views) -> np.ndarray:
+    sizes = np.array([v.Wv * v.Hv for v in views], dtype=np.int64)
+    return np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64), int(sizes.sum())
+
+
+@dataclass
+class ViewsOut:
+    u8: torch.Tensor       # flat arena, view v at offsets[v], Hv x Wv
+    mask: torch.Tensor
+    f32: torch.Tensor | None
+    offsets: np.ndarray
+    views: list
+
+    def view(self, i: int, which: str = "u8") -> torch.Tensor:
+        v = self.views[i]
+        buf = {"u8": self.u8, "mask": self.mask, "f32": self.f32}[which]
+        o = int(self.offsets[i])
+        return buf[o:o + v.Wv * v.Hv].view(v.Hv, v.Wv)
+
+
+@dataclass
+class OrbOut:
+    kp: torch.Tensor        # (cap * 16) bytes of asift_keypoint
+    desc: torch.Tensor      # (cap, 32) uint8
+    view_count: torch.Tensor
+    view_offset: torch.Tensor
+    total: torch.Tensor     # int32 [1]
+
+    def host(self):
+        n = int(self.total.item())
+        kp = self.kp[: n * 16].cpu().numpy().view(KP_DTYPE)
+        return kp, self.desc[:n].cpu().numpy(), self.view_count.cpu().numpy(), self.view_offset.cpu().numpy()
+
+
+class Context:
+    """A libasift context (pattern tables on the device) plus cached workspaces."""
+
+    def __init__(self, n_levels: int = 4, n_features: int = 500, fast_threshold: int = 20,
+                 cand_per_mpx: int = 60000, pattern_seed: int = PATTERN_SEED, device: int | None = None):
+        self.L = load_library()
+        if device is not None:
+            torch.cuda.set_device(device)
+        self.cfg = OrbCfg(n_levels, n_features, fast_threshold, cand_per_mpx)
+        self._ctx = C.c_void_p()
+        _check("asift_ctx_create", self.L.asift_ctx_create(C.byref(self._ctx), C.byref(self.cfg), pattern_seed))
+        self._ws: dict = {}
+
+    def close(self):
+        if self._ctx:
+            self.L.asift_ctx_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- workspace cache (allocation happens here, outside the library)
+    def workspace(self, key, nbytes: int) -> torch.Tensor:
+        w = self._ws.get(key)
+        if w is None or w.numel() < nbytes:
+            w = torch.zeros(max(nbytes, 256), dtype=torch.uint8, device="cuda")
+            self._ws[key] = w
+        return w
+
+    def profile(self, on: bool = True):
+        _check("asift_profile_enable", self.L.asift_profile_enable(self._ctx, int(on)))
+
+    def profile_read(self) -> dict:
+        ms = np.zeros(len(PROF_STAGES), np.float32)
+        _check("asift_profile_read", self.L.asift_profile_read(self._ctx, ms.ctypes.data_as(C.c_void_p), len(ms)))
+        return dict(zip(PROF_STAGES, ms.tolist()))
+
+    def pattern(self) -> np.ndarray:
+        out = np.zeros((30, 256, 4), np.int8)
+        _check("asift_ctx_pattern", self.L.asift_ctx_pattern(self._ctx, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def read_status(self, ws: torch.Tensor, clear: bool = True) -> int:
+        st = C.c_int32()
+        _check("asift_read_status", self.L.asift_read_status(_ptr(ws), int(clear), C.byref(st), _stream()))
+        return st.value
+
+    # -- asift_views
+    def views(self, img: torch.Tensor, views, with_f32: bool = False) -> ViewsOut:
+        assert img.is_cuda and img.dtype == torch.uint8 and img.dim() == 2
+        H, W = img.shape
+        pitch = img.stride(0)
+        offs, total = view_offsets(views)
+        u8 = torch.empty(max(total, 1), dtype=torch.uint8, device=img.device)
+        mask = torch.empty_like(u8)
+        f32 = torch.empty(max(total, 1), dtype=torch.float32, device=img.device) if with_f32 else None
+        nbytes = self.L.asift_views_workspace_size(H, W, len(views))
+        ws = self.workspace("views", nbytes)
+        arr = _view_array(views)
+        _check("asift_views", self.L.asift_views(self._ctx, _ptr(img), H, W, pitch, arr, len(views),
+                                                 offs.ctypes.data_as(C.c_void_p), _ptr(f32), _ptr(u8), _ptr(mask),
+                                                 _ptr(ws), ws.numel(), _stream()))
+        return ViewsOut(u8, mask, f32, offs, list(views))
+
+    # -- orb_extract
+    def orb_extract(self, vo: ViewsOut) -> OrbOut:
+        views = vo.views
+        nv = len(views)
+        cap = nv * self.cfg.n_features
+        arr = _view_array(views)
+        nbytes = self.L.orb_workspace_size(self._ctx, arr, nv)
+        ws = self.workspace("orb", nbytes)
+        dev = vo.u8.device
+        kp = torch.zeros(cap * 16, dtype=torch.uint8, device=dev)
+        desc = torch.zeros((cap, 32), dtype=torch.uint8, device=dev)
+        vc = torch.zeros(nv, dtype=torch.int32, device=dev)
+        vof = torch.zeros(nv, dtype=torch.int32, device=dev)
+        total = torch.zeros(1, dtype=torch.int32, device=dev)
+        _check("orb_extract", self.L.orb_extract(self._ctx, _ptr(vo.u8), _ptr(vo.mask), arr, nv,
+                                                 vo.offsets.ctypes.data_as(C.c_void_p), _ptr(kp), _ptr(desc),
+                                                 _ptr(vc), _ptr(vof), _ptr(total), _ptr(ws), ws.numel(), _stream()))
+        self.last_orb_ws = ws
+        return OrbOut(kp, desc, vc, vof, total)
+
+    # -- hamming_match
+    def hamming_match(self, q: torch.Tensor, t: torch.Tensor, num: int = 4, den: int = 5):
+        """q: (nq, 32) uint8, t: (nt, 32) uint8 on the GPU -> (best, d1, d2, accepted, n_accepted)."""
+        nq, nt = q.shape[0], t.shape[0]
+        dev = q.device
+        out = torch.zeros(max(nq, 1) * 8, dtype=torch.uint8, device=dev)
+        acc = torch.zeros(max(nq, 1), dtype=torch.uint8, device=dev)
+        nacc = torch.zeros(1, dtype=torch.int32, device=dev)
+        ws = self.workspace("hamming", self.L.hamming_workspace_size(nq, nt))
+        _check("hamming_match", self.L.hamming_match(self._ctx, _ptr(q) if nq else None, nq, None,
+                                                     _ptr(t) if nt else None, nt, None, num, den, _ptr(out),
+                                                     _ptr(acc), _ptr(nacc), _ptr(ws), ws.numel(), _stream()))
+        m = out[: nq * 8].cpu().numpy().view(MATCH_DTYPE)
+        return (m["best"].copy(), m["d1"].astype(np.int32), m["d2"].astype(np.int32),
+                acc[:nq].cpu().numpy().astype(bool), int(nacc.item()))
+
+    # -- match_pair
+    def pair_cfg(self, kmax: int = 5, num: int = 4, den: int = 5, per_view: bool = False) -> PairCfg:
+        return PairCfg(kmax, num, den, int(per_view))
+
+    def match_pair_workspace(self, shape1, shape2, pc: PairCfg) -> torch.Tensor:
+        n = self.L.match_pair_workspace_size(self._ctx, shape1[0], shape1[1], shape2[0], shape2[1], C.byref(pc))
+        if n == 0:
+            raise AsiftError("match_pair_workspace_size", ASIFT_ERR_ARG)
+        return self.workspace(("pair", tuple(shape1), tuple(shape2), pc.kmax, pc.per_view), n)
+
+    def match_pair(self, img1: torch.Tensor, img2: torch.Tensor, pc: PairCfg, out: torch.Tensor | None = None,
+                   n_out: torch.Tensor | None = None, ws: torch.Tensor | None = None):
+        """Whole hot path for one pair.  Returns (pairs byte buffer, count tensor, workspace)."""
+        H1, W1 = img1.shape
+        H2, W2 = img2.shape
+        if ws is None:
+            ws = self.match_pair_workspace((H1, W1), (H2, W2), pc)
+        n1 = len(view_table(H1, W1, pc.kmax))
+        cap = n1 * self.cfg.n_features
+        if out is None:
+            out = torch.zeros(max(cap, 1) * PAIR_DTYPE.itemsize, dtype=torch.uint8, device=img1.device)
+        if n_out is None:
+            n_out = torch.zeros(1, dtype=torch.int32, device=img1.device)
+        cap = out.numel() // PAIR_DTYPE.itemsize
+        _check("match_pair", self.L.match_pair(self._ctx, _ptr(img1), H1, W1, img1.stride(0), _ptr(img2), H2, W2,
+                                               img2.stride(0), C.byref(pc), _ptr(out), cap, _ptr(n_out), _ptr(ws),
+                                               ws.numel(), _stream()))
+        return out, n_out, ws
+
+    def pairs_host(self, out: torch.Tensor, n_out: torch.Tensor) -> np.ndarray:
+        n = int(n_out.item())
+        cap = out.numel() // PAIR_DTYPE.itemsize
+        return out[: min(n, cap) * PAIR_DTYPE.itemsize].cpu().numpy().view(PAIR_DTYPE)
+
+    def inspect_pair(self, shape1, shape2, pc: PairCfg, ws: torch.Tensor):
+        """Pooled keypoints / descriptors / matches of the last match_pair on ws (host copies)."""
+        ptrs = [C.c_void_p() for _ in range(7)]
+        _check("match_pair_inspect", self.L.match_pair_inspect(self._ctx, shape1[0], shape1[1], shape2[0], shape2[1],
+                                                               C.byref(pc), _ptr(ws), *[C.byref(p) for p in ptrs]))
+        torch.cuda.synchronize()
+        base = ws.data_ptr()
+
+        def sl(p, nbytes):
+            o = p.value - base
+            return ws[o:o + nbytes].cpu().numpy()
+
+        n1 = int(sl(ptrs[2], 4).view(np.int32)[0])
+        n2 = int(sl(ptrs[5], 4).view(np.int32)[0])
+        kp1 = sl(ptrs[0], n1 * 16).view(KP_DTYPE)
+        d1 = sl(ptrs[1], n1 * 32).reshape(n1, 32)
+        kp2 = sl(ptrs[3], n2 * 16).view(KP_DTYPE)
+        d2 = sl(ptrs[4], n2 * 32).reshape(n2, 32)
+        m = sl(ptrs[6], n1 * 8).view(MATCH_DTYPE)
+        return kp1, d1, kp2, d2, m

@@ -1,0 +1,94 @@
+// common.cuh -- device-side tables and helpers shared by the libasift kernels.
+// Internal to the library (the public ABI is include/asift.h).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "asift.h"
+
+namespace asift {
+
+constexpr int kBorder = 16;       // ORB keypoint border: patch radius 15 + 1
+constexpr int kPatchR2 = 225;     // orientation / BRIEF disc x^2 + y^2 <= 15^2
+constexpr int kBins = 30;         // 12-degree orientation sectors
+constexpr int kPairs = 256;       // rBRIEF-256
+
+// ---------------------------------------------------------------- warp stage
+// One view of one source image, as the warp kernel reads it.
+struct DevView {
+    const float *src;       // source image as fp32, row pitch src_pitch elements
+    int32_t src_pitch, W, H;
+    int32_t Wr, Hr, Wv, Hv, K;
+    int32_t tile_start;     // first linear tile of this view in the launch
+    int32_t ntx;            // tiles along x
+    int32_t pad;
+    long long cq, sq, tq;   // Q31 cos, sin, tilt
+    long long out_off;      // byte offset of the view in the u8 / mask arenas
+    double cosd, sind, t;   // fp64 geometry for back-projection
+    float g[ASIFT_MAX_GAUSS];
+};
+
+constexpr int kWarpTW = 32;   // view columns per warp tile
+constexpr int kWarpTH = 8;    // view rows per warp tile
+constexpr int kWarpThreads = 256;
+
+// ---------------------------------------------------------------- ORB stage
+// One (view, pyramid level) as the ORB kernels read it.
+struct DevLevel {
+    const uint8_t *img;     // level image (pitch W)
+    const uint8_t *mask;    // level mask (pitch W)
+    uint8_t *img_w;         // writable alias (levels >= 1 are produced by the pyramid kernel)
+    uint8_t *mask_w;
+    const uint8_t *prev;    // level l-1 image / mask (levels >= 1)
+    const uint8_t *prev_mask;
+    int32_t W, H, Wp, Hp;   // size, previous level size
+    int32_t view, level;
+    int32_t quota, qoff;    // keypoint quota of the level and its offset within the view's slots
+    int32_t cand_off, cand_cap;   // candidate buffer slice
+    int32_t det_tile_start, det_ntx;   // FAST/Harris/NMS tiles
+    int32_t pyr_tile_start, pyr_ntx;   // pyramid tiles (levels >= 1)
+};
+
+struct Candidate {          // a corner that survived NMS
+    long long r25;
+    int32_t yx;             // (y << 16) | x
+    int32_t pad;
+};
+
+struct SlotKp {             // a selected keypoint before orientation / description
+    long long r25;
+    int32_t yx;             // (y << 16) | x
+    int32_t e;              // level entry (relative to the select launch)
+};
+
+constexpr int kDetTW = 32, kDetTH = 16;   // FAST tile
+constexpr int kPyrTW = 64, kPyrTH = 16;   // pyramid tile (4 px per thread across x)
+
+// ---------------------------------------------------------------- helpers
+__host__ __device__ inline int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// Binary search of the last entry with start <= idx in a monotone array
+// reached through a strided field accessor.
+template <class T, class F>
+__device__ inline int find_owner(const T *tab, int n, int idx, F start_of)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (start_of(tab[mid]) <= idx) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Records the first device-side error in the workspace status word.
+__device__ inline void set_status(int32_t *status, int32_t code)
+{
+    if (status) atomicCAS(status, 0, code);
+}
+
+}  // namespace asift
+
+// Host-side helpers shared by the API translation units.
+namespace asift {
+void note_launch(int n = 1);
+}

@@ -1,0 +1,57 @@
+// kernels.h -- launchers of the libasift kernels (internal).
+#pragma once
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "asift.h"
+
+namespace asift {
+
+struct DevView;
+struct DevLevel;
+struct Candidate;
+struct SlotKp;
+
+// warp.cu
+void warp_strip_widths(const asift_view_desc &v, int *cw, int *bw);
+cudaError_t launch_u8_to_f32(const uint8_t *src, int pitch, int W, int H, float *dst, cudaStream_t s);
+cudaError_t launch_warp(const DevView *d_views, int n_views, int n_tiles, int cw_max, int bw_max, uint8_t *u8,
+                        uint8_t *mask, float *f32, cudaStream_t s);
+
+// orb.cu
+cudaError_t launch_pyramid(const DevLevel *d_lv, int n, int n_tiles, cudaStream_t s);
+cudaError_t launch_detect(const DevLevel *d_lv, int n, int n_tiles, int thr, Candidate *cand, int32_t *count,
+                          cudaStream_t s);
+size_t select_smem_bytes();
+cudaError_t launch_select(const DevLevel *d_lv, int n, const Candidate *cand, const int32_t *count, int n_features,
+                          SlotKp *slots, int32_t *taken, int32_t *status, cudaStream_t s);
+cudaError_t launch_pool_scan(const int32_t *taken, int n_views, int n_levels, const int32_t *group_first_view,
+                             int n_groups, int n_features, int32_t *pool_off, int32_t *view_count,
+                             int32_t *view_off, int32_t *group_total, cudaStream_t s);
+cudaError_t launch_orient_brief(const DevLevel *d_lv, int n_views, int n_levels, int n_features, int v_begin,
+                                int v_end, const SlotKp *slots, const int32_t *taken, const int32_t *pool_off,
+                                const int *pattern, const long long *bins, asift_keypoint *kp, uint4 *desc,
+                                cudaStream_t s);
+
+// match.cu
+void hamming_plan(int nq, int nt, int *n_split, int *chunk);
+size_t hamming_partial_bytes(int nq, int nt);
+cudaError_t launch_hamming(const uint8_t *q, int nq, const int32_t *d_nq, const uint8_t *t, int nt,
+                           const int32_t *d_nt, int num, int den, asift_match *out, uint8_t *accept,
+                           int32_t *n_acc, void *part, cudaStream_t s);
+int pair_blocks(int nq);
+cudaError_t launch_pairs(const uint8_t *accept, const asift_match *m, int nq_cap, const int32_t *d_nq,
+                         int32_t *block_count, const asift_keypoint *kp1, const asift_keypoint *kp2,
+                         const DevView *views, asift_pair_match *out, int cap, int32_t *d_n, int32_t *status,
+                         cudaStream_t s);
+
+// tables.cpp (host; each table generated from its written definition)
+void make_view_desc(int H, int W, double t, double phi_deg, int k, int j, asift_view_desc *v);
+int view_table(int H, int W, int kmax, asift_view_desc *out, int cap);
+int level_size(int n0, int l);
+void make_pattern(uint64_t seed, int8_t pat[30][256][4]);
+void make_bin_table(long long e[30][2]);
+
+}  // namespace asift

@@ -1,0 +1,565 @@
+// orb.cu -- ORB on every simulated view (Sec. III-B; ORB [23]) on sm_103a.
+//
+// Stages, each one launch over all (view, level) entries of a call:
+//   pyramid_kernel      level l from level l-1: centre-aligned integer bilinear
+//                       (Q11 weights, round half up) + AND of the four mask taps
+//   detect_kernel       FAST-9 + Harris x25 + 3x3 NMS on shared-memory tiles;
+//                       survivors appended with a warp-aggregated atomic
+//   select_kernel       per (view, level): exact top-q by (R25 desc, y, x) via
+//                       MSD radix select on a 96-bit key + bitonic sort
+//   pool_scan_kernel    canonical pool offsets (view, level, rank)
+//   orient_brief_kernel one warp per keypoint: 37x37 patch in shared memory,
+//                       integer smoothing, centroid moments -> 30-bin angle,
+//                       steered BRIEF-256 packed with warp ballots
+// All arithmetic is integer, so the results are exactly those of the
+// definitions (and of any independent implementation of them).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace asift {
+
+// ---------------------------------------------------------------- pyramid
+__global__ void __launch_bounds__(256)
+pyramid_kernel(const DevLevel *__restrict__ lv, int n)
+{
+    const int tile = blockIdx.x;
+    const int e = find_owner(lv, n, tile, [](const DevLevel &d) { return d.pyr_tile_start; });
+    const DevLevel &L = lv[e];
+    const int lt = tile - L.pyr_tile_start;
+    const int ty = lt / L.pyr_ntx, tx = lt - ty * L.pyr_ntx;
+    const int Wl = L.W, Hl = L.H, Wp = L.Wp, Hp = L.Hp;
+    for (int p = threadIdx.x; p < kPyrTW * kPyrTH; p += blockDim.x) {
+        const int x = tx * kPyrTW + (p % kPyrTW), y = ty * kPyrTH + p / kPyrTW;
+        if (x >= Wl || y >= Hl) continue;
+        const long long ny = (2LL * y + 1) * Hp - Hl, dy = 2LL * Hl;
+        const int y0 = (int)(ny / dy);
+        const int fy = (int)(((ny - y0 * dy) << 11) / dy);
+        const int y1 = min(y0 + 1, Hp - 1);
+        const long long nx = (2LL * x + 1) * Wp - Wl, dx = 2LL * Wl;
+        const int x0 = (int)(nx / dx);
+        const int fx = (int)(((nx - x0 * dx) << 11) / dx);
+        const int x1 = min(x0 + 1, Wp - 1);
+        const uint8_t *r0 = L.prev + (size_t)y0 * Wp, *r1 = L.prev + (size_t)y1 * Wp;
+        const unsigned a = r0[x0], b = r0[x1], c = r1[x0], d = r1[x1];
+        const unsigned s = (unsigned)(2048 - fx) * (unsigned)(2048 - fy) * a + (unsigned)fx * (unsigned)(2048 - fy) * b +
+                           (unsigned)(2048 - fx) * (unsigned)fy * c + (unsigned)fx * (unsigned)fy * d;
+        L.img_w[(size_t)y * Wl + x] = (uint8_t)((s + (1u << 21)) >> 22);
+        const uint8_t *m0 = L.prev_mask + (size_t)y0 * Wp, *m1 = L.prev_mask + (size_t)y1 * Wp;
+        L.mask_w[(size_t)y * Wl + x] = (uint8_t)(m0[x0] && m0[x1] && m1[x0] && m1[x1]);
+    }
+}
+
+// ---------------------------------------------------------------- detection
+// Bresenham circle of radius 3, from (0,-3) clockwise on screen.
+__constant__ int8_t c_circ[16][2] = {{0, -3}, {1, -3}, {2, -2}, {3, -1}, {3, 0}, {3, 1}, {2, 2}, {1, 3},
+                                     {0, 3}, {-1, 3}, {-2, 2}, {-3, 1}, {-3, 0}, {-3, -1}, {-2, -2}, {-1, -3}};
+
+constexpr int kHalo = 5;                        // FAST (3) + Harris (4) at the ring + 1
+constexpr int kSW = kDetTW + 2 * kHalo;         // 42
+constexpr int kSH = kDetTH + 2 * kHalo;         // 26
+constexpr int kRW = kDetTW + 2, kRH = kDetTH + 2;   // tile + one-pixel ring
+
+// 1 iff 9 cyclically consecutive bits of the 16-bit mask m are set.
+__device__ __forceinline__ bool has_run9(unsigned m)
+{
+    m |= m << 16;
+    unsigned r = m & (m >> 1);     // 2
+    r &= r >> 2;                    // 4
+    r &= r >> 4;                    // 8
+    r &= m >> 8;                    // 9
+    return r != 0u;
+}
+
+__global__ void __launch_bounds__(256)
+detect_kernel(const DevLevel *__restrict__ lv, int n, int thr, Candidate *__restrict__ cand,
+              int32_t *__restrict__ cand_count)
+{
+    __shared__ uint8_t img[kSH][kSW];
+    __shared__ uint8_t isc[kRH][kRW];
+    __shared__ long long R[kRH][kRW];
+    __shared__ int16_t clist[kRH * kRW];
+    __shared__ int ncl;
+
+    const int tile = blockIdx.x;
+    const int e = find_owner(lv, n, tile, [](const DevLevel &d) { return d.det_tile_start; });
+    const DevLevel &L = lv[e];
+    const int lt = tile - L.det_tile_start;
+    const int ty = lt / L.det_ntx, tx = lt - ty * L.det_ntx;
+    const int W = L.W, H = L.H;
+    const int x0 = tx * kDetTW, y0 = ty * kDetTH;
+    // tiles that hold no pixel of the border-limited region, nor a ring pixel of one
+    if (x0 + kDetTW + 1 <= kBorder || y0 + kDetTH + 1 <= kBorder || x0 - 1 >= W - kBorder || y0 - 1 >= H - kBorder)
+        return;
+
+    if (threadIdx.x == 0) ncl = 0;
+    for (int p = threadIdx.x; p < kSH * kSW; p += blockDim.x) {
+        const int r = p / kSW, c = p - r * kSW;
+        const int gx = clampi(x0 - kHalo + c, 0, W - 1), gy = clampi(y0 - kHalo + r, 0, H - 1);
+        img[r][c] = L.img[(size_t)gy * W + gx];
+    }
+    __syncthreads();
+
+    // corner flags on the tile + ring
+    for (int p = threadIdx.x; p < kRH * kRW; p += blockDim.x) {
+        const int r = p / kRW, c = p - r * kRW;
+        const int x = x0 - 1 + c, y = y0 - 1 + r;
+        uint8_t flag = 0;
+        if (x >= kBorder && x < W - kBorder && y >= kBorder && y < H - kBorder) {
+            const int sx = c - 1 + kHalo, sy = r - 1 + kHalo;
+            const int ctr = img[sy][sx];
+            const int hi = ctr + thr, lo = ctr - thr;
+            unsigned bm = 0, dm = 0;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int v = img[sy + c_circ[k][1]][sx + c_circ[k][0]];
+                bm |= (unsigned)(v > hi) << k;
+                dm |= (unsigned)(v < lo) << k;
+            }
+            if (has_run9(bm) || has_run9(dm)) {
+                const uint8_t *M = L.mask;
+                const int b = kBorder;
+                flag = M[(size_t)(y - b) * W + x - b] && M[(size_t)(y - b) * W + x + b] &&
+                       M[(size_t)(y + b) * W + x - b] && M[(size_t)(y + b) * W + x + b];
+            }
+        }
+        isc[r][c] = flag;
+        if (flag) clist[atomicAdd(&ncl, 1)] = (int16_t)p;
+    }
+    __syncthreads();
+
+    // Harris x25 at every corner of the tile + ring (Sobel 3x3, 7x7 window)
+    const int nc = ncl;
+    for (int q = threadIdx.x; q < nc; q += blockDim.x) {
+        const int p = clist[q];
+        const int r = p / kRW, c = p - r * kRW;
+        const int sx = c - 1 + kHalo, sy = r - 1 + kHalo;
+        int a = 0, bb = 0, cc = 0;
+        for (int dy = -3; dy <= 3; ++dy) {
+#pragma unroll
+            for (int dx = -3; dx <= 3; ++dx) {
+                const int X = sx + dx, Y = sy + dy;
+                const int ix = (img[Y - 1][X + 1] + 2 * img[Y][X + 1] + img[Y + 1][X + 1]) -
+                               (img[Y - 1][X - 1] + 2 * img[Y][X - 1] + img[Y + 1][X - 1]);
+                const int iy = (img[Y + 1][X - 1] + 2 * img[Y + 1][X] + img[Y + 1][X + 1]) -
+                               (img[Y - 1][X - 1] + 2 * img[Y - 1][X] + img[Y - 1][X + 1]);
+                a += ix * ix;
+                bb += iy * iy;
+                cc += ix * iy;
+            }
+        }
+        const long long A = a, B = bb, Cc = cc;
+        R[r][c] = 25 * (A * B - Cc * Cc) - (A + B) * (A + B);
+    }
+    __syncthreads();
+
+    // 3x3 NMS on the tile; survivors appended with one atomic per warp
+    const unsigned lane = threadIdx.x & 31u;
+    for (int it = 0; it < (kDetTW * kDetTH + blockDim.x - 1) / blockDim.x; ++it) {
+        const int p = it * blockDim.x + threadIdx.x;
+        bool keep = false;
+        long long rv = 0;
+        int x = 0, y = 0;
+        if (p < kDetTW * kDetTH) {
+            const int r = p / kDetTW + 1, c = p % kDetTW + 1;
+            x = x0 + c - 1;
+            y = y0 + r - 1;
+            if (isc[r][c]) {
+                rv = R[r][c];
+                keep = true;
+#pragma unroll
+                for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        if ((dx | dy) == 0 || !isc[r + dy][c + dx]) continue;
+                        const long long rn = R[r + dy][c + dx];
+                        // the neighbour precedes p in raster order iff dy < 0 or (dy == 0 and dx < 0)
+                        const bool n_first = dy < 0 || (dy == 0 && dx < 0);
+                        if (!(rv > rn || (rv == rn && !n_first))) keep = false;
+                    }
+            }
+        }
+        const unsigned ballot = __ballot_sync(0xffffffffu, keep);
+        if (ballot) {
+            const int leader = __ffs(ballot) - 1;
+            int base = 0;
+            if ((int)lane == leader) base = atomicAdd(&cand_count[e], __popc(ballot));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (keep) {
+                const int slot = base + __popc(ballot & ((1u << lane) - 1u));
+                if (slot < L.cand_cap) {
+                    Candidate cd;
+                    cd.r25 = rv;
+                    cd.yx = (y << 16) | x;
+                    cd.pad = 0;
+                    cand[L.cand_off + slot] = cd;
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- selection
+// Selection key: ascending order = (R25 descending, y ascending, x ascending).
+__device__ __forceinline__ unsigned long long key_hi(long long r)
+{
+    return ~((unsigned long long)r ^ 0x8000000000000000ULL);
+}
+
+constexpr int kSelThreads = 512;
+constexpr int kSelMax = 4096;   // quota per level <= kSelMax
+
+__global__ void __launch_bounds__(kSelThreads)
+select_kernel(const DevLevel *__restrict__ lv, const Candidate *__restrict__ cand,
+              const int32_t *__restrict__ cand_count, int n_features, SlotKp *__restrict__ slots,
+              int32_t *__restrict__ taken, int32_t *__restrict__ status)
+{
+    extern __shared__ unsigned char sm_raw[];
+    unsigned long long *kh = (unsigned long long *)sm_raw;          // [kSelMax]
+    unsigned *kl = (unsigned *)(kh + kSelMax);                      // [kSelMax]
+    __shared__ unsigned hist[256];
+    __shared__ unsigned long long pre_hi, msk_hi;
+    __shared__ unsigned pre_lo, msk_lo;
+    __shared__ int need, done, nsel;
+
+    const int e = blockIdx.x;
+    const DevLevel &L = lv[e];
+    int n = cand_count[e];
+    if (n > L.cand_cap) {
+        if (threadIdx.x == 0) set_status(status, ASIFT_ERR_CAPACITY);
+        n = L.cand_cap;
+    }
+    const int q = L.quota;
+    const int k = min(q, n);
+    if (threadIdx.x == 0) taken[e] = k;
+    if (k == 0) return;
+    const Candidate *C = cand + L.cand_off;
+
+    if (threadIdx.x == 0) {
+        pre_hi = 0; msk_hi = 0; pre_lo = 0; msk_lo = 0;
+        need = k; done = (n <= q); nsel = 0;
+    }
+    __syncthreads();
+    // MSD radix select of the k smallest 96-bit keys (8-bit digits)
+    for (int d = 0; d < 12 && !done; ++d) {
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+        __syncthreads();
+        const unsigned long long ph = pre_hi, mh = msk_hi;
+        const unsigned pl = pre_lo, ml = msk_lo;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const unsigned long long h = key_hi(C[i].r25);
+            const unsigned l = (unsigned)C[i].yx;
+            if ((h & mh) == ph && (l & ml) == pl) {
+                const unsigned dig = d < 8 ? (unsigned)(h >> (56 - 8 * d)) & 255u : (l >> (24 - 8 * (d - 8))) & 255u;
+                atomicAdd(&hist[dig], 1u);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int cum = 0, b = 0;
+            for (b = 0; b < 256; ++b) {
+                if (cum + (int)hist[b] >= need) break;
+                cum += (int)hist[b];
+            }
+            need -= cum;
+            if (d < 8) {
+                pre_hi |= (unsigned long long)b << (56 - 8 * d);
+                msk_hi |= 255ULL << (56 - 8 * d);
+            } else {
+                pre_lo |= (unsigned)b << (24 - 8 * (d - 8));
+                msk_lo |= 255u << (24 - 8 * (d - 8));
+            }
+            if ((int)hist[b] == need) done = 1;   // the whole bucket is selected
+        }
+        __syncthreads();
+    }
+    // threshold: every key <= (prefix with the undecided digits all ones)
+    const unsigned long long th = done ? (pre_hi | ~msk_hi) : pre_hi;
+    const unsigned tl = done ? (pre_lo | ~msk_lo) : pre_lo;
+    const bool all = (n <= q);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const unsigned long long h = key_hi(C[i].r25);
+        const unsigned l = (unsigned)C[i].yx;
+        if (all || h < th || (h == th && l <= tl)) {
+            const int s = atomicAdd(&nsel, 1);
+            if (s < kSelMax) { kh[s] = h; kl[s] = l; }
+        }
+    }
+    __syncthreads();
+    const int m = min(nsel, kSelMax);
+    int P = 1;
+    while (P < m) P <<= 1;
+    for (int i = m + threadIdx.x; i < P; i += blockDim.x) { kh[i] = ~0ULL; kl[i] = ~0u; }
+    __syncthreads();
+    // bitonic sort ascending by (hi, lo)
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < P / 2; i += blockDim.x) {
+                const int lo = 2 * i - (i & (stride - 1));
+                const int hi = lo + stride;
+                const bool up = ((lo & size) == 0);
+                const bool gt = kh[lo] > kh[hi] || (kh[lo] == kh[hi] && kl[lo] > kl[hi]);
+                if (gt == up) {
+                    const unsigned long long th2 = kh[lo]; kh[lo] = kh[hi]; kh[hi] = th2;
+                    const unsigned tl2 = kl[lo]; kl[lo] = kl[hi]; kl[hi] = tl2;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    SlotKp *out = slots + (size_t)L.view * n_features + L.qoff;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        SlotKp s;
+        s.r25 = (long long)(~kh[i] ^ 0x8000000000000000ULL);
+        s.yx = (int32_t)kl[i];
+        s.e = e;
+        out[i] = s;
+    }
+}
+
+// ---------------------------------------------------------------- pool offsets
+// Canonical pool order: view-major, then level, then selection rank.  Views are
+// grouped (one group per image); group g owns views [first[g], first[g+1]) and
+// the pool slice starting at first[g] * n_features.  One CTA per group.
+// Entries of the level table are level-major (index l * n_views + v).
+__global__ void __launch_bounds__(1024)
+pool_scan_kernel(const int32_t *__restrict__ taken, int n_views, int n_levels, const int32_t *__restrict__ first,
+                 int n_features, int32_t *__restrict__ pool_off, int32_t *__restrict__ view_count,
+                 int32_t *__restrict__ view_off, int32_t *__restrict__ group_total)
+{
+    __shared__ int32_t warp_sums[32];
+    __shared__ int32_t carry;
+    const int g = blockIdx.x;
+    const int v0 = first[g], v1 = first[g + 1];
+    const int base0 = v0 * n_features;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int n = (v1 - v0) * n_levels;
+    const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + threadIdx.x;           // canonical index (v - v0) * L + l
+        int v = 0, l = 0, val = 0;
+        if (i < n) {
+            v = v0 + i / n_levels;
+            l = i % n_levels;
+            val = taken[l * n_views + v];
+        }
+        int x = val;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((int)lane >= o) x += y;
+        }
+        if (lane == 31) warp_sums[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int s = (lane < (blockDim.x >> 5)) ? warp_sums[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, s, o);
+                if ((int)lane >= o) s += y;
+            }
+            warp_sums[lane] = s;
+        }
+        __syncthreads();
+        const int excl = carry + x - val + (wid ? warp_sums[wid - 1] : 0);
+        if (i < n) {
+            pool_off[l * n_views + v] = base0 + excl;
+            if (l == 0) view_off[v] = base0 + excl;
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + val;
+        __syncthreads();
+    }
+    for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+        int c = 0;
+        for (int l = 0; l < n_levels; ++l) c += taken[l * n_views + v];
+        view_count[v] = c;
+    }
+    if (threadIdx.x == 0) group_total[g] = carry;
+}
+
+// ---------------------------------------------------------------- orientation + BRIEF
+constexpr int kObWarps = 8;
+constexpr int kPatch = 37;          // raw patch: radius 15 + smoothing radius 3
+constexpr int kSm = 31;             // smoothed patch
+
+__constant__ int c_smooth[7] = {18, 34, 49, 54, 49, 34, 18};
+
+__global__ void __launch_bounds__(kObWarps * 32)
+orient_brief_kernel(const DevLevel *__restrict__ lv, int n_views, int n_levels, int n_features, int v_begin, int v_end,
+                    const SlotKp *__restrict__ slots, const int32_t *__restrict__ taken,
+                    const int32_t *__restrict__ pool_off, const int *__restrict__ pattern /* [30][256] packed int8x4 */,
+                    const long long *__restrict__ bins /* [30][2] Q30 */, asift_keypoint *__restrict__ kp_out,
+                    uint4 *__restrict__ desc_out)
+{
+    __shared__ uint8_t P[kObWarps][kPatch * kPatch];
+    __shared__ uint16_t Hs[kObWarps][kPatch * kSm];
+    __shared__ uint8_t S[kObWarps][kSm * kSm];
+    __shared__ long long eb[kBins][2];
+    for (int i = threadIdx.x; i < kBins * 2; i += blockDim.x) eb[i >> 1][i & 1] = bins[i];
+    __syncthreads();
+
+    const int w = threadIdx.x >> 5;
+    const unsigned lane = threadIdx.x & 31u;
+    const long long slot = (long long)v_begin * n_features + (long long)blockIdx.x * kObWarps + w;
+    if (slot >= (long long)v_end * n_features) return;
+    const int v = (int)(slot / n_features), rnk = (int)(slot - (long long)v * n_features);
+    // find the level whose slot range holds rnk
+    int e = -1, r = 0;
+    for (int l = 0; l < n_levels; ++l) {
+        const int ei = l * n_views + v;
+        const DevLevel &L = lv[ei];
+        if (rnk >= L.qoff && rnk < L.qoff + taken[ei]) { e = ei; r = rnk - L.qoff; break; }
+    }
+    if (e < 0) return;
+    const DevLevel &L = lv[e];
+    const SlotKp s = slots[slot];
+    const int x = s.yx & 0xffff, y = s.yx >> 16;
+    const int W = L.W, H = L.H;
+
+    uint8_t *p = P[w];
+    for (int i = lane; i < kPatch * kPatch; i += 32) {
+        const int rr = i / kPatch, cc = i - rr * kPatch;
+        const int gx = clampi(x - 18 + cc, 0, W - 1), gy = clampi(y - 18 + rr, 0, H - 1);
+        p[i] = L.img[(size_t)gy * W + gx];
+    }
+    __syncwarp();
+    // horizontal smoothing pass (exact sums)
+    uint16_t *h = Hs[w];
+    for (int i = lane; i < kPatch * kSm; i += 32) {
+        const int rr = i / kSm, cc = i - rr * kSm;
+        const uint8_t *row = p + rr * kPatch + cc;   // taps cc..cc+6 = offsets -3..3 around cc+3
+        unsigned a = 0;
+#pragma unroll
+        for (int t = 0; t < 7; ++t) a += (unsigned)c_smooth[t] * row[t];
+        h[i] = (uint16_t)a;
+    }
+    // centroid moments on the raw patch (disc of radius 15)
+    int m10 = 0, m01 = 0;
+    for (int i = lane; i < kSm * kSm; i += 32) {
+        const int dy = i / kSm - 15, dx = i % kSm - 15;
+        if (dx * dx + dy * dy <= kPatchR2) {
+            const int val = p[(dy + 18) * kPatch + dx + 18];
+            m10 += dx * val;
+            m01 += dy * val;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        m10 += __shfl_xor_sync(0xffffffffu, m10, o);
+        m01 += __shfl_xor_sync(0xffffffffu, m01, o);
+    }
+    __syncwarp();
+    // vertical pass, rounded half up
+    uint8_t *sm = S[w];
+    for (int i = lane; i < kSm * kSm; i += 32) {
+        const int rr = i / kSm, cc = i - rr * kSm;
+        unsigned a = 0;
+#pragma unroll
+        for (int t = 0; t < 7; ++t) a += (unsigned)c_smooth[t] * h[(rr + t) * kSm + cc];
+        sm[i] = (uint8_t)((a + 32768u) >> 16);
+    }
+    // orientation sector: on or left of e_b, strictly right of e_{b+1}
+    int bin = 0;
+    if (m10 != 0 || m01 != 0) {
+        bin = -1;
+        if (lane < kBins) {
+            const long long mx = m10, my = m01;
+            const int b2 = (lane + 1) % kBins;
+            const long long c0 = eb[lane][0] * my - eb[lane][1] * mx;
+            const long long c1 = eb[b2][0] * my - eb[b2][1] * mx;
+            if (c0 >= 0 && c1 < 0) bin = (int)lane;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, bin >= 0);
+        bin = bal ? __ffs(bal) - 1 : 0;
+    }
+    __syncwarp();
+    // steered BRIEF: test i = 32 j + lane, word j = ballot
+    const int *pat = pattern + bin * kPairs;
+    unsigned word = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int pk = __ldg(pat + 32 * j + lane);
+        const int px = (int8_t)(pk & 0xff), py = (int8_t)((pk >> 8) & 0xff);
+        const int qx = (int8_t)((pk >> 16) & 0xff), qy = (int8_t)((pk >> 24) & 0xff);
+        const bool bit = sm[(py + 15) * kSm + px + 15] < sm[(qy + 15) * kSm + qx + 15];
+        const unsigned bal = __ballot_sync(0xffffffffu, bit);
+        if ((int)lane == j) word = bal;
+    }
+    const int out = pool_off[e] + r;
+    unsigned *d = reinterpret_cast<unsigned *>(desc_out + 2LL * out);
+    if (lane < 8) d[lane] = word;
+    if (lane == 0) {
+        asift_keypoint k;
+        k.x = (int16_t)x;
+        k.y = (int16_t)y;
+        k.level = (uint8_t)L.level;
+        k.bin = (uint8_t)bin;
+        k.view = (uint16_t)v;
+        k.r25 = s.r25;
+        kp_out[out] = k;
+    }
+}
+
+// ---------------------------------------------------------------- host side
+cudaError_t launch_pyramid(const DevLevel *d_lv, int n, int n_tiles, cudaStream_t s)
+{
+    if (n_tiles <= 0) return cudaSuccess;
+    pyramid_kernel<<<n_tiles, 256, 0, s>>>(d_lv, n);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_detect(const DevLevel *d_lv, int n, int n_tiles, int thr, Candidate *cand, int32_t *count,
+                          cudaStream_t s)
+{
+    if (n_tiles <= 0) return cudaSuccess;
+    detect_kernel<<<n_tiles, 256, 0, s>>>(d_lv, n, thr, cand, count);
+    note_launch();
+    return cudaGetLastError();
+}
+
+size_t select_smem_bytes() { return (size_t)kSelMax * (sizeof(unsigned long long) + sizeof(unsigned)); }
+
+cudaError_t launch_select(const DevLevel *d_lv, int n, const Candidate *cand, const int32_t *count, int n_features,
+                          SlotKp *slots, int32_t *taken, int32_t *status, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    static bool attr_set = false;
+    const size_t smem = select_smem_bytes();
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    select_kernel<<<n, kSelThreads, smem, s>>>(d_lv, cand, count, n_features, slots, taken, status);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pool_scan(const int32_t *taken, int n_views, int n_levels, const int32_t *group_first_view,
+                             int n_groups, int n_features, int32_t *pool_off, int32_t *view_count,
+                             int32_t *view_off, int32_t *group_total, cudaStream_t s)
+{
+    if (n_groups <= 0) return cudaSuccess;
+    pool_scan_kernel<<<n_groups, 1024, 0, s>>>(taken, n_views, n_levels, group_first_view, n_features, pool_off,
+                                               view_count, view_off, group_total);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_orient_brief(const DevLevel *d_lv, int n_views, int n_levels, int n_features, int v_begin,
+                                int v_end, const SlotKp *slots, const int32_t *taken, const int32_t *pool_off,
+                                const int *pattern, const long long *bins, asift_keypoint *kp, uint4 *desc,
+                                cudaStream_t s)
+{
+    const long long nslots = (long long)(v_end - v_begin) * n_features;
+    if (nslots <= 0) return cudaSuccess;
+    const int blocks = (int)((nslots + kObWarps - 1) / kObWarps);
+    orient_brief_kernel<<<blocks, kObWarps * 32, 0, s>>>(d_lv, n_views, n_levels, n_features, v_begin, v_end, slots,
+                                                         taken, pool_off, pattern, bins, kp, desc);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace asift
