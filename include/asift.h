@@ -207,6 +207,34 @@ ASIFT_API asift_status hamming_match(asift_ctx *ctx, const uint8_t *d_q, int nq,
                            int ratio_num, int ratio_den, asift_match *d_out, uint8_t *d_accept,
                            int32_t *d_n_accepted, void *d_workspace, size_t ws_bytes, void *stream);
 
+/*
+ * hamming_match_noalloc -- the same matcher as hamming_match (same results, bit
+ * for bit) for callers that cannot allocate device memory: code handed only its
+ * input and output buffers by a host framework that owns all device memory and
+ * offers no workspace, and latency-bound loops that forbid cudaMalloc/cudaFree
+ * after start-up because those calls can synchronise the device and take
+ * unbounded time.  This paper-independent convenience has no counterpart in
+ * the paper.
+ * It takes no context and no workspace: its scratch (the per-slice partial
+ * nearest / second-nearest keys) is a fixed device array of
+ * ASIFT_NOALLOC_SCRATCH_BYTES that the library declares at file scope, so every
+ * GPU that loads the library holds those bytes until the process exits.
+ * Limits: nq <= ASIFT_NOALLOC_MAX_QUERIES and nt <= 8388607; larger sizes return
+ * ASIFT_ERR_ARG with nothing enqueued.  The first call on a device (the device
+ * current at the call) looks up the array's device address; make that first
+ * call before any stream capture on that device.  Every call uses the same
+ * array and leaves its contents behind (nothing in it needs to start at zero:
+ * each call writes every entry it reads), so calls whose work overlaps on the
+ * GPU (different streams, or different host threads) race and must be
+ * serialised by the caller.  Arguments otherwise as hamming_match.
+ */
+#define ASIFT_NOALLOC_SCRATCH_BYTES (8u << 20)
+#define ASIFT_NOALLOC_MAX_QUERIES (1 << 20)
+ASIFT_API asift_status hamming_match_noalloc(const uint8_t *d_q, int nq, const int32_t *d_nq, const uint8_t *d_t,
+                                             int nt, const int32_t *d_nt, int ratio_num, int ratio_den,
+                                             asift_match *d_out, uint8_t *d_accept, int32_t *d_n_accepted,
+                                             void *stream);
+
 /* View-set configuration of match_pair. */
 typedef struct {
     int32_t kmax;           /* t = sqrt2^k, k = 0..kmax (default 5)             */

@@ -27,7 +27,7 @@ EXPORTED = ["asift_ctx_create", "asift_ctx_destroy", "asift_ctx_orb_cfg", "asift
             "orb_workspace_size", "orb_extract", "hamming_workspace_size", "hamming_match",
             "match_pair_workspace_size", "match_pair", "match_pair_inspect", "asift_read_status",
             "asift_launch_count", "asift_pattern_table", "asift_bin_table", "asift_profile_enable",
-            "asift_profile_read"]
+            "asift_profile_read", "hamming_match_noalloc"]
 PROF_STAGES = ["upload", "warp", "pyramid", "detect", "select", "orient_brief", "match", "pairs"]
 
 
@@ -99,6 +99,7 @@ def load_library():
         "asift_bin_table": (i32, [vp]),
         "asift_profile_enable": (i32, [vp, i32]),
         "asift_profile_read": (i32, [vp, vp, i32]),
+        "hamming_match_noalloc": (i32, [vp, i32, vp, vp, i32, vp, i32, i32, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -195,6 +196,24 @@ class OrbOut:
         n = int(self.total.item())
         kp = self.kp[: n * 16].cpu().numpy().view(KP_DTYPE)
         return kp, self.desc[:n].cpu().numpy(), self.view_count.cpu().numpy(), self.view_offset.cpu().numpy()
+
+
+def hamming_match_noalloc(q: torch.Tensor, t: torch.Tensor, num: int = 4, den: int = 5):
+    """Matcher without a context or workspace (output buffers are the caller's).
+
+    Returns (best, d1, d2, accepted, n_accepted) like Context.hamming_match."""
+    L = load_library()
+    nq, nt = q.shape[0], t.shape[0]
+    dev = q.device
+    out = torch.zeros(max(nq, 1) * 8, dtype=torch.uint8, device=dev)
+    acc = torch.zeros(max(nq, 1), dtype=torch.uint8, device=dev)
+    nacc = torch.zeros(1, dtype=torch.int32, device=dev)
+    _check("hamming_match_noalloc", L.hamming_match_noalloc(_ptr(q) if nq else None, nq, None,
+                                                            _ptr(t) if nt else None, nt, None, num, den,
+                                                            _ptr(out), _ptr(acc), _ptr(nacc), _stream()))
+    m = out[: nq * 8].cpu().numpy().view(MATCH_DTYPE)
+    return (m["best"].copy(), m["d1"].astype(np.int32), m["d2"].astype(np.int32),
+            acc[:nq].cpu().numpy().astype(bool), int(nacc.item()))
 
 
 class Context:
@@ -299,6 +318,11 @@ class Context:
         m = out[: nq * 8].cpu().numpy().view(MATCH_DTYPE)
         return (m["best"].copy(), m["d1"].astype(np.int32), m["d2"].astype(np.int32),
                 acc[:nq].cpu().numpy().astype(bool), int(nacc.item()))
+
+    # -- hamming_match_noalloc (no workspace: the library's fixed scratch array)
+    def hamming_match_noalloc(self, q: torch.Tensor, t: torch.Tensor, num: int = 4, den: int = 5):
+        """As hamming_match, through the allocation-free entry point."""
+        return hamming_match_noalloc(q, t, num, den)
 
     # -- match_pair
     def pair_cfg(self, kmax: int = 5, num: int = 4, den: int = 5, per_view: bool = False) -> PairCfg:

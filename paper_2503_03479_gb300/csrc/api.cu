@@ -599,6 +599,21 @@ asift_status hamming_match(asift_ctx *ctx, const uint8_t *d_q, int nq, const int
     return cuda_status(e);
 }
 
+asift_status hamming_match_noalloc(const uint8_t *d_q, int nq, const int32_t *d_nq, const uint8_t *d_t, int nt,
+                                   const int32_t *d_nt, int ratio_num, int ratio_den, asift_match *d_out,
+                                   uint8_t *d_accept, int32_t *d_n_accepted, void *stream)
+{
+    if (nq < 0 || nt < 0 || nq > ASIFT_NOALLOC_MAX_QUERIES || nt > (1 << 23) - 1 || (nq && (!d_q || !d_out)) ||
+        (nt && !d_t) || ratio_num < 0 || ratio_den < 1 || ratio_num > (1 << 20) || ratio_den > (1 << 20))
+        return ASIFT_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (d_n_accepted) e = cudaMemsetAsync(d_n_accepted, 0, sizeof(int32_t), s);
+    if (nq == 0 || e != cudaSuccess) return cuda_status(e);
+    e = launch_hamming_noalloc(d_q, nq, d_nq, d_t, nt, d_nt, ratio_num, ratio_den, d_out, d_accept, d_n_accepted, s);
+    return cuda_status(e);
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------- match_pair

@@ -41,6 +41,9 @@ size_t hamming_partial_bytes(int nq, int nt);
 cudaError_t launch_hamming(const uint8_t *q, int nq, const int32_t *d_nq, const uint8_t *t, int nt,
                            const int32_t *d_nt, int num, int den, asift_match *out, uint8_t *accept,
                            int32_t *n_acc, void *part, cudaStream_t s);
+cudaError_t launch_hamming_noalloc(const uint8_t *q, int nq, const int32_t *d_nq, const uint8_t *t, int nt,
+                                   const int32_t *d_nt, int num, int den, asift_match *out, uint8_t *accept,
+                                   int32_t *n_acc, cudaStream_t s);
 int pair_blocks(int nq);
 cudaError_t launch_pairs(const uint8_t *accept, const asift_match *m, int nq_cap, const int32_t *d_nq,
                          int32_t *block_count, const asift_keypoint *kp1, const asift_keypoint *kp2,

@@ -8,6 +8,8 @@
 // min/max network gives the lowest index on distance ties and d2 counts equal
 // distances.  The train set is split over gridDim.y slices; merge_kernel takes
 // the two smallest keys over the slices (exact: keys are unique).
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -218,6 +220,68 @@ cudaError_t launch_hamming(const uint8_t *q, int nq, const int32_t *d_nq, const 
     if (nq <= 0) return cudaSuccess;
     int n_split, chunk;
     hamming_plan(nq, nt, &n_split, &chunk);
+    if (nt > 0) {
+        dim3 grid((nq + kMThreads * kMQ - 1) / (kMThreads * kMQ), n_split);
+        hamming_top2_kernel<<<grid, kMThreads, 0, s>>>(reinterpret_cast<const uint4 *>(q), nq, d_nq,
+                                                      reinterpret_cast<const uint4 *>(t), nt, d_nt, chunk,
+                                                      static_cast<uint2 *>(part));
+        note_launch();
+    }
+    merge_kernel<<<(nq + 255) / 256, 256, 0, s>>>(static_cast<const uint2 *>(part), nt > 0 ? n_split : 0, chunk, nq,
+                                                  d_nq, nt, d_nt, num, den, out, accept, n_acc);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- allocation-free matcher
+// The partial keys of hamming_match_noalloc live in this file-scope array
+// (ASIFT_NOALLOC_SCRATCH_BYTES per device that loads the library).  Host code
+// must not pass the symbol itself to a kernel (on the host it names a host-side
+// shadow, not device memory): its device address is looked up once per device
+// with cudaGetSymbolAddress, with that device current, and cached.
+static __device__ __align__(256) uint2 g_noalloc_part[ASIFT_NOALLOC_SCRATCH_BYTES / sizeof(uint2)];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoAllocMaxDevices] = {};
+}  // namespace
+
+static cudaError_t noalloc_scratch(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_part);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return cudaSuccess;
+}
+
+cudaError_t launch_hamming_noalloc(const uint8_t *q, int nq, const int32_t *d_nq, const uint8_t *t, int nt,
+                                   const int32_t *d_nt, int num, int den, asift_match *out, uint8_t *accept,
+                                   int32_t *n_acc, cudaStream_t s)
+{
+    if (nq <= 0) return cudaSuccess;
+    void *part = nullptr;
+    cudaError_t e = noalloc_scratch(&part);
+    if (e != cudaSuccess) return e;
+    const long long cap = (long long)(ASIFT_NOALLOC_SCRATCH_BYTES / sizeof(uint2));
+    int n_split, chunk;
+    hamming_plan(nq, nt, &n_split, &chunk);
+    if ((long long)n_split * nq > cap) {          // fewer, longer train slices
+        const int s_max = (int)std::max(1LL, cap / nq);
+        chunk = (nt + s_max - 1) / s_max;
+        chunk = ((chunk + kMTile - 1) / kMTile) * kMTile;
+        if (chunk <= 0) chunk = kMTile;
+        n_split = std::max(1, (nt + chunk - 1) / chunk);
+    }
     if (nt > 0) {
         dim3 grid((nq + kMThreads * kMQ - 1) / (kMThreads * kMQ), n_split);
         hamming_top2_kernel<<<grid, kMThreads, 0, s>>>(reinterpret_cast<const uint4 *>(q), nq, d_nq,
