@@ -229,7 +229,7 @@ ASIFT_API asift_status hamming_match(asift_ctx *ctx, const uint8_t *d_q, int nq,
  * serialised by the caller.  Arguments otherwise as hamming_match.
  */
 #define ASIFT_NOALLOC_SCRATCH_BYTES (8u << 20)
-#define ASIFT_NOALLOC_MAX_QUERIES (1 << 20)
+#define ASIFT_NOALLOC_MAX_QUERIES 1000000
 ASIFT_API asift_status hamming_match_noalloc(const uint8_t *d_q, int nq, const int32_t *d_nq, const uint8_t *d_t,
                                              int nt, const int32_t *d_nt, int ratio_num, int ratio_den,
                                              asift_match *d_out, uint8_t *d_accept, int32_t *d_n_accepted,

@@ -28,8 +28,8 @@ struct DevView {
     float g[ASIFT_MAX_GAUSS];
 };
 
-constexpr int kWarpTW = 32;   // view columns per warp tile
-constexpr int kWarpTH = 8;    // view rows per warp tile
+constexpr int kWarpTW = 64;   // view columns per warp tile
+constexpr int kWarpTH = 16;   // view rows per warp tile
 constexpr int kWarpThreads = 256;
 
 // ---------------------------------------------------------------- ORB stage
@@ -61,7 +61,7 @@ struct SlotKp {             // a selected keypoint before orientation / descript
     int32_t e;              // level entry (relative to the select launch)
 };
 
-constexpr int kDetTW = 32, kDetTH = 16;   // FAST tile
+constexpr int kDetTW = 64, kDetTH = 16;   // FAST tile
 constexpr int kPyrTW = 64, kPyrTH = 16;   // pyramid tile (4 px per thread across x)
 
 // ---------------------------------------------------------------- helpers

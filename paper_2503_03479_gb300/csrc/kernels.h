@@ -36,7 +36,7 @@ cudaError_t launch_orient_brief(const DevLevel *d_lv, int n_views, int n_levels,
                                 cudaStream_t s);
 
 // match.cu
-void hamming_plan(int nq, int nt, int *n_split, int *chunk);
+int hamming_splits_alloc(int nt_cap);
 size_t hamming_partial_bytes(int nq, int nt);
 cudaError_t launch_hamming(const uint8_t *q, int nq, const int32_t *d_nq, const uint8_t *t, int nt,
                            const int32_t *d_nt, int num, int den, asift_match *out, uint8_t *accept,

@@ -20,76 +20,126 @@ constexpr int kMThreads = 128;
 constexpr int kMTile = 256;
 constexpr unsigned kNoKey = 0xffffffffu;
 
-__device__ __forceinline__ unsigned ham256(const uint4 &a0, const uint4 &a1, const uint4 &b0, const uint4 &b1)
+// Hamming distance of two 256-bit descriptors.  The eight XOR words are summed
+// bit-sliced with carry-save adders (three-input XOR and majority, one LOP3
+// each), leaving four words of weight 1, 2, 4 and 8: four popc instead of
+// eight, the popc pipe being the matcher's bottleneck.
+__device__ __forceinline__ void csa(unsigned a, unsigned b, unsigned c, unsigned &sum, unsigned &carry)
 {
-    return __popc(a0.x ^ b0.x) + __popc(a0.y ^ b0.y) + __popc(a0.z ^ b0.z) + __popc(a0.w ^ b0.w) +
-           __popc(a1.x ^ b1.x) + __popc(a1.y ^ b1.y) + __popc(a1.z ^ b1.z) + __popc(a1.w ^ b1.w);
+    sum = a ^ b ^ c;
+    carry = (a & b) | (c & (a ^ b));
 }
 
-__global__ void __launch_bounds__(kMThreads)
+__device__ __forceinline__ unsigned ham256(const uint4 &a0, const uint4 &a1, const uint4 &b0, const uint4 &b1)
+{
+    const unsigned x0 = a0.x ^ b0.x, x1 = a0.y ^ b0.y, x2 = a0.z ^ b0.z, x3 = a0.w ^ b0.w;
+    const unsigned x4 = a1.x ^ b1.x, x5 = a1.y ^ b1.y, x6 = a1.z ^ b1.z, x7 = a1.w ^ b1.w;
+    unsigned s1, c1, s2, c2, s3, c3, t1, d1;
+    csa(x0, x1, x2, s1, c1);
+    csa(x3, x4, x5, s2, c2);
+    csa(s1, s2, x6, s3, c3);
+    const unsigned ones = s3 ^ x7, c4 = s3 & x7;          // weight 1; c1..c4 weight 2
+    csa(c1, c2, c3, t1, d1);
+    const unsigned twos = t1 ^ c4, d2 = t1 & c4;          // weight 2; d1, d2 weight 4
+    const unsigned fours = d1 ^ d2, eights = d1 & d2;     // weight 4, 8
+    return __popc(ones) + 2 * __popc(twos) + 4 * __popc(fours) + 8 * __popc(eights);
+}
+
+// Split of the work into (query block, train slice) items, decided on the
+// device from the actual counts so that a pool smaller than its capacity
+// still fills the GPU.  Every CTA derives the same plan.
+struct MatchPlan {
+    int n_split, chunk;
+};
+
+__device__ __forceinline__ MatchPlan match_plan(int nq, int nt, int s_alloc, int target_items)
+{
+    MatchPlan p{0, kMTile};
+    if (nq <= 0 || nt <= 0) return p;
+    const int qblocks = (nq + kMThreads * kMQ - 1) / (kMThreads * kMQ);
+    int s = max(1, (target_items + qblocks - 1) / qblocks);
+    s = min(s, (nt + kMTile - 1) / kMTile);
+    s = max(1, min(s, s_alloc));
+    int chunk = (nt + s - 1) / s;
+    chunk = ((chunk + kMTile - 1) / kMTile) * kMTile;
+    p.chunk = chunk;
+    p.n_split = (nt + chunk - 1) / chunk;
+    return p;
+}
+
+// Persistent over the items: item = split * qblocks + query block.  The plan
+// is published in plan_out (two ints) for the merge kernel.
+__global__ void __launch_bounds__(kMThreads, 8)
 hamming_top2_kernel(const uint4 *__restrict__ q, int nq_cap, const int32_t *__restrict__ d_nq,
-                    const uint4 *__restrict__ t, int nt_cap, const int32_t *__restrict__ d_nt, int chunk,
-                    uint2 *__restrict__ part)
+                    const uint4 *__restrict__ t, int nt_cap, const int32_t *__restrict__ d_nt, int s_alloc,
+                    int target_items, int *__restrict__ plan_out, uint2 *__restrict__ part)
 {
     __shared__ uint4 st[2 * kMTile];
     const int nq = d_nq ? min(*d_nq, nq_cap) : nq_cap;
     const int nt = d_nt ? min(*d_nt, nt_cap) : nt_cap;
-    const int qbase = blockIdx.x * (kMThreads * kMQ);
-    if (qbase >= nq) return;
-    const int t0 = blockIdx.y * chunk, t1 = min(nt, t0 + chunk);
-
-    uint4 qa[kMQ], qb[kMQ];
-    unsigned b1[kMQ], b2[kMQ];
-#pragma unroll
-    for (int k = 0; k < kMQ; ++k) {
-        const int qi = qbase + k * kMThreads + threadIdx.x;
-        if (qi < nq) {
-            qa[k] = q[2LL * qi];
-            qb[k] = q[2LL * qi + 1];
-        } else {
-            qa[k] = make_uint4(0, 0, 0, 0);
-            qb[k] = qa[k];
-        }
-        b1[k] = kNoKey;
-        b2[k] = kNoKey;
+    const MatchPlan P = match_plan(nq, nt, s_alloc, target_items);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        plan_out[0] = P.n_split;
+        plan_out[1] = P.chunk;
     }
-    for (int tb = t0; tb < t1; tb += kMTile) {
-        const int nb = min(kMTile, t1 - tb);
-        __syncthreads();
-        for (int i = threadIdx.x; i < 2 * nb; i += blockDim.x) st[i] = t[2LL * tb + i];
-        __syncthreads();
-        for (int j = 0; j < nb; ++j) {
-            const uint4 x0 = st[2 * j], x1 = st[2 * j + 1];
-            const unsigned idx = (unsigned)(tb + j);
+    const int qblocks = (nq + kMThreads * kMQ - 1) / (kMThreads * kMQ);
+    const int items = qblocks * P.n_split;
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        const int split = item / qblocks, qb = item - split * qblocks;
+        const int qbase = qb * (kMThreads * kMQ);
+        const int t0 = split * P.chunk, t1 = min(nt, t0 + P.chunk);
+        uint4 qa[kMQ], qc[kMQ];
+        unsigned b1[kMQ], b2[kMQ];
 #pragma unroll
-            for (int k = 0; k < kMQ; ++k) {
-                const unsigned key = (ham256(qa[k], qb[k], x0, x1) << 23) | idx;
-                b2[k] = min(b2[k], max(b1[k], key));
-                b1[k] = min(b1[k], key);
+        for (int k = 0; k < kMQ; ++k) {
+            const int qi = qbase + k * kMThreads + threadIdx.x;
+            if (qi < nq) {
+                qa[k] = q[2LL * qi];
+                qc[k] = q[2LL * qi + 1];
+            } else {
+                qa[k] = make_uint4(0, 0, 0, 0);
+                qc[k] = qa[k];
+            }
+            b1[k] = kNoKey;
+            b2[k] = kNoKey;
+        }
+        for (int tb = t0; tb < t1; tb += kMTile) {
+            const int nb = min(kMTile, t1 - tb);
+            __syncthreads();
+            for (int i = threadIdx.x; i < 2 * nb; i += blockDim.x) st[i] = t[2LL * tb + i];
+            __syncthreads();
+            for (int j = 0; j < nb; ++j) {
+                const uint4 x0 = st[2 * j], x1 = st[2 * j + 1];
+                const unsigned idx = (unsigned)(tb + j);
+#pragma unroll
+                for (int k = 0; k < kMQ; ++k) {
+                    const unsigned key = (ham256(qa[k], qc[k], x0, x1) << 23) | idx;
+                    b2[k] = min(b2[k], max(b1[k], key));
+                    b1[k] = min(b1[k], key);
+                }
             }
         }
-    }
-    if (t0 >= t1) return;
 #pragma unroll
-    for (int k = 0; k < kMQ; ++k) {
-        const int qi = qbase + k * kMThreads + threadIdx.x;
-        if (qi < nq) part[(size_t)blockIdx.y * nq_cap + qi] = make_uint2(b1[k], b2[k]);
+        for (int k = 0; k < kMQ; ++k) {
+            const int qi = qbase + k * kMThreads + threadIdx.x;
+            if (qi < nq) part[(size_t)split * nq_cap + qi] = make_uint2(b1[k], b2[k]);
+        }
     }
 }
 
 __global__ void __launch_bounds__(256)
-merge_kernel(const uint2 *__restrict__ part, int n_split, int chunk, int nq_cap, const int32_t *__restrict__ d_nq,
-             int nt_cap, const int32_t *__restrict__ d_nt, int num, int den, asift_match *__restrict__ out,
-             uint8_t *__restrict__ accept, int32_t *__restrict__ n_acc)
+merge_kernel(const uint2 *__restrict__ part, const int *__restrict__ plan, int nq_cap,
+             const int32_t *__restrict__ d_nq, int nt_cap, const int32_t *__restrict__ d_nt, int num, int den,
+             asift_match *__restrict__ out, uint8_t *__restrict__ accept, int32_t *__restrict__ n_acc)
 {
     const int nq = d_nq ? min(*d_nq, nq_cap) : nq_cap;
     const int nt = d_nt ? min(*d_nt, nt_cap) : nt_cap;
+    const int n_split = (plan && nt > 0) ? plan[0] : 0;
     const int qi = blockIdx.x * blockDim.x + threadIdx.x;
     bool acc = false;
     if (qi < nq) {
         unsigned b1 = kNoKey, b2 = kNoKey;
         for (int s = 0; s < n_split; ++s) {
-            if (s * chunk >= nt) break;
             const uint2 p = part[(size_t)s * nq_cap + qi];
             b2 = min(b2, max(b1, p.x));
             b1 = min(b1, p.x);
@@ -192,45 +242,43 @@ pair_write_kernel(const uint8_t *__restrict__ accept, const asift_match *__restr
 }
 
 // ---------------------------------------------------------------- host side
-void hamming_plan(int nq, int nt, int *n_split, int *chunk)
-{
-    const int qblocks = std::max(1, (nq + kMThreads * kMQ - 1) / (kMThreads * kMQ));
-    const int target = 152 * 6;                     // CTAs in flight over the 152 SMs
-    int s = std::max(1, (target + qblocks - 1) / qblocks);
-    const int max_s = std::max(1, (nt + kMTile - 1) / kMTile);
-    s = std::min(s, max_s);
-    int c = (nt + s - 1) / s;
-    c = ((c + kMTile - 1) / kMTile) * kMTile;       // whole train tiles per slice
-    if (c <= 0) c = kMTile;
-    *chunk = c;
-    *n_split = std::max(1, (nt + c - 1) / c);
-}
+constexpr int kMatchMaxSplits = 64;
+constexpr int kMatchGrid = 152 * 8;            // persistent CTAs (8 per SM at 64 registers)
+constexpr int kMatchTargetItems = 2 * kMatchGrid;
+constexpr size_t kPlanBytes = 256;             // the published plan precedes the partials
+
+int hamming_splits_alloc(int nt_cap) { return std::max(1, std::min(kMatchMaxSplits, (nt_cap + kMTile - 1) / kMTile)); }
 
 size_t hamming_partial_bytes(int nq, int nt)
 {
-    int s, c;
-    hamming_plan(nq, nt, &s, &c);
-    return sizeof(uint2) * (size_t)s * (size_t)std::max(nq, 1);
+    return kPlanBytes + sizeof(uint2) * (size_t)hamming_splits_alloc(nt) * (size_t)std::max(nq, 1);
+}
+
+static cudaError_t launch_match_kernels(const uint8_t *q, int nq, const int32_t *d_nq, const uint8_t *t, int nt,
+                                        const int32_t *d_nt, int num, int den, asift_match *out, uint8_t *accept,
+                                        int32_t *n_acc, void *region, int s_alloc, cudaStream_t s)
+{
+    if (nq <= 0) return cudaSuccess;
+    int *plan = static_cast<int *>(region);
+    uint2 *part = reinterpret_cast<uint2 *>(static_cast<char *>(region) + kPlanBytes);
+    if (nt > 0) {
+        hamming_top2_kernel<<<kMatchGrid, kMThreads, 0, s>>>(reinterpret_cast<const uint4 *>(q), nq, d_nq,
+                                                            reinterpret_cast<const uint4 *>(t), nt, d_nt, s_alloc,
+                                                            kMatchTargetItems, plan, part);
+        note_launch();
+    }
+    merge_kernel<<<(nq + 255) / 256, 256, 0, s>>>(part, nt > 0 ? plan : nullptr, nq, d_nq, nt, d_nt, num, den, out,
+                                                  accept, n_acc);
+    note_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_hamming(const uint8_t *q, int nq, const int32_t *d_nq, const uint8_t *t, int nt,
                            const int32_t *d_nt, int num, int den, asift_match *out, uint8_t *accept,
                            int32_t *n_acc, void *part, cudaStream_t s)
 {
-    if (nq <= 0) return cudaSuccess;
-    int n_split, chunk;
-    hamming_plan(nq, nt, &n_split, &chunk);
-    if (nt > 0) {
-        dim3 grid((nq + kMThreads * kMQ - 1) / (kMThreads * kMQ), n_split);
-        hamming_top2_kernel<<<grid, kMThreads, 0, s>>>(reinterpret_cast<const uint4 *>(q), nq, d_nq,
-                                                      reinterpret_cast<const uint4 *>(t), nt, d_nt, chunk,
-                                                      static_cast<uint2 *>(part));
-        note_launch();
-    }
-    merge_kernel<<<(nq + 255) / 256, 256, 0, s>>>(static_cast<const uint2 *>(part), nt > 0 ? n_split : 0, chunk, nq,
-                                                  d_nq, nt, d_nt, num, den, out, accept, n_acc);
-    note_launch();
-    return cudaGetLastError();
+    return launch_match_kernels(q, nq, d_nq, t, nt, d_nt, num, den, out, accept, n_acc, part,
+                                hamming_splits_alloc(nt), s);
 }
 
 // ---------------------------------------------------------------- allocation-free matcher
@@ -239,7 +287,7 @@ cudaError_t launch_hamming(const uint8_t *q, int nq, const int32_t *d_nq, const 
 // must not pass the symbol itself to a kernel (on the host it names a host-side
 // shadow, not device memory): its device address is looked up once per device
 // with cudaGetSymbolAddress, with that device current, and cached.
-static __device__ __align__(256) uint2 g_noalloc_part[ASIFT_NOALLOC_SCRATCH_BYTES / sizeof(uint2)];
+static __device__ __align__(256) unsigned char g_noalloc_part[ASIFT_NOALLOC_SCRATCH_BYTES];
 
 namespace {
 constexpr int kNoAllocMaxDevices = 64;
@@ -269,30 +317,13 @@ cudaError_t launch_hamming_noalloc(const uint8_t *q, int nq, const int32_t *d_nq
                                    int32_t *n_acc, cudaStream_t s)
 {
     if (nq <= 0) return cudaSuccess;
-    void *part = nullptr;
-    cudaError_t e = noalloc_scratch(&part);
+    void *region = nullptr;
+    cudaError_t e = noalloc_scratch(&region);
     if (e != cudaSuccess) return e;
-    const long long cap = (long long)(ASIFT_NOALLOC_SCRATCH_BYTES / sizeof(uint2));
-    int n_split, chunk;
-    hamming_plan(nq, nt, &n_split, &chunk);
-    if ((long long)n_split * nq > cap) {          // fewer, longer train slices
-        const int s_max = (int)std::max(1LL, cap / nq);
-        chunk = (nt + s_max - 1) / s_max;
-        chunk = ((chunk + kMTile - 1) / kMTile) * kMTile;
-        if (chunk <= 0) chunk = kMTile;
-        n_split = std::max(1, (nt + chunk - 1) / chunk);
-    }
-    if (nt > 0) {
-        dim3 grid((nq + kMThreads * kMQ - 1) / (kMThreads * kMQ), n_split);
-        hamming_top2_kernel<<<grid, kMThreads, 0, s>>>(reinterpret_cast<const uint4 *>(q), nq, d_nq,
-                                                      reinterpret_cast<const uint4 *>(t), nt, d_nt, chunk,
-                                                      static_cast<uint2 *>(part));
-        note_launch();
-    }
-    merge_kernel<<<(nq + 255) / 256, 256, 0, s>>>(static_cast<const uint2 *>(part), nt > 0 ? n_split : 0, chunk, nq,
-                                                  d_nq, nt, d_nt, num, den, out, accept, n_acc);
-    note_launch();
-    return cudaGetLastError();
+    // as many train slices as the fixed array holds for nq queries (at least one)
+    const long long entries = (long long)((ASIFT_NOALLOC_SCRATCH_BYTES - kPlanBytes) / sizeof(uint2));
+    const int s_alloc = (int)std::max(1LL, std::min<long long>(hamming_splits_alloc(nt), entries / nq));
+    return launch_match_kernels(q, nq, d_nq, t, nt, d_nt, num, den, out, accept, n_acc, region, s_alloc, s);
 }
 
 int pair_blocks(int nq) { return std::max(1, (nq + kPairBlock - 1) / kPairBlock); }

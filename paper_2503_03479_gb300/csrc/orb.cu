@@ -19,45 +19,58 @@
 namespace asift {
 
 // ---------------------------------------------------------------- pyramid
+// Each CTA makes a kPyrTW x kPyrTH tile of level l.  The source columns and
+// weights of the tile's columns and rows are computed once (32-bit integer
+// divisions) and shared; each pixel is then four byte loads and integer FMAs.
 __global__ void __launch_bounds__(256)
 pyramid_kernel(const DevLevel *__restrict__ lv, int n)
 {
+    __shared__ int16_t sx0[kPyrTW], sx1[kPyrTW], sfx[kPyrTW];
+    __shared__ int16_t sy0[kPyrTH], sy1[kPyrTH], sfy[kPyrTH];
     const int tile = blockIdx.x;
     const int e = find_owner(lv, n, tile, [](const DevLevel &d) { return d.pyr_tile_start; });
     const DevLevel &L = lv[e];
     const int lt = tile - L.pyr_tile_start;
     const int ty = lt / L.pyr_ntx, tx = lt - ty * L.pyr_ntx;
     const int Wl = L.W, Hl = L.H, Wp = L.Wp, Hp = L.Hp;
+    const int xb = tx * kPyrTW, yb = ty * kPyrTH;
+    for (int i = threadIdx.x; i < kPyrTW + kPyrTH; i += blockDim.x) {
+        // centre-aligned source position ((2x+1) Wp - Wl) / (2 Wl), Q11 fraction
+        const bool isx = i < kPyrTW;
+        const int o = isx ? xb + i : yb + (i - kPyrTW);
+        const int nl = isx ? Wl : Hl, np = isx ? Wp : Hp;
+        const int num = (2 * o + 1) * np - nl, den = 2 * nl;
+        const int q0 = num / den;
+        const int f = ((num - q0 * den) << 11) / den;
+        const int q1 = min(q0 + 1, np - 1);
+        if (isx) { sx0[i] = (int16_t)q0; sx1[i] = (int16_t)q1; sfx[i] = (int16_t)f; }
+        else { sy0[i - kPyrTW] = (int16_t)q0; sy1[i - kPyrTW] = (int16_t)q1; sfy[i - kPyrTW] = (int16_t)f; }
+    }
+    __syncthreads();
     for (int p = threadIdx.x; p < kPyrTW * kPyrTH; p += blockDim.x) {
-        const int x = tx * kPyrTW + (p % kPyrTW), y = ty * kPyrTH + p / kPyrTW;
+        const int cx = p % kPyrTW, cy = p / kPyrTW;
+        const int x = xb + cx, y = yb + cy;
         if (x >= Wl || y >= Hl) continue;
-        const long long ny = (2LL * y + 1) * Hp - Hl, dy = 2LL * Hl;
-        const int y0 = (int)(ny / dy);
-        const int fy = (int)(((ny - y0 * dy) << 11) / dy);
-        const int y1 = min(y0 + 1, Hp - 1);
-        const long long nx = (2LL * x + 1) * Wp - Wl, dx = 2LL * Wl;
-        const int x0 = (int)(nx / dx);
-        const int fx = (int)(((nx - x0 * dx) << 11) / dx);
-        const int x1 = min(x0 + 1, Wp - 1);
-        const uint8_t *r0 = L.prev + (size_t)y0 * Wp, *r1 = L.prev + (size_t)y1 * Wp;
+        const int x0 = sx0[cx], x1 = sx1[cx], fx = sfx[cx];
+        const int y0 = sy0[cy], y1 = sy1[cy], fy = sfy[cy];
+        const uint8_t *r0 = L.prev + y0 * Wp, *r1 = L.prev + y1 * Wp;
         const unsigned a = r0[x0], b = r0[x1], c = r1[x0], d = r1[x1];
-        const unsigned s = (unsigned)(2048 - fx) * (unsigned)(2048 - fy) * a + (unsigned)fx * (unsigned)(2048 - fy) * b +
-                           (unsigned)(2048 - fx) * (unsigned)fy * c + (unsigned)fx * (unsigned)fy * d;
-        L.img_w[(size_t)y * Wl + x] = (uint8_t)((s + (1u << 21)) >> 22);
-        const uint8_t *m0 = L.prev_mask + (size_t)y0 * Wp, *m1 = L.prev_mask + (size_t)y1 * Wp;
-        L.mask_w[(size_t)y * Wl + x] = (uint8_t)(m0[x0] && m0[x1] && m1[x0] && m1[x1]);
+        const unsigned gx = 2048 - fx, gy = 2048 - fy;
+        const unsigned s = gx * gy * a + (unsigned)fx * gy * b + gx * (unsigned)fy * c + (unsigned)fx * (unsigned)fy * d;
+        L.img_w[y * Wl + x] = (uint8_t)((s + (1u << 21)) >> 22);
+        const uint8_t *m0 = L.prev_mask + y0 * Wp, *m1 = L.prev_mask + y1 * Wp;
+        L.mask_w[y * Wl + x] = (uint8_t)(m0[x0] & m0[x1] & m1[x0] & m1[x1]);
     }
 }
 
 // ---------------------------------------------------------------- detection
-// Bresenham circle of radius 3, from (0,-3) clockwise on screen.
-__constant__ int8_t c_circ[16][2] = {{0, -3}, {1, -3}, {2, -2}, {3, -1}, {3, 0}, {3, 1}, {2, 2}, {1, 3},
-                                     {0, 3}, {-1, 3}, {-2, 2}, {-3, 1}, {-3, 0}, {-3, -1}, {-2, -2}, {-1, -3}};
-
-constexpr int kHalo = 5;                        // FAST (3) + Harris (4) at the ring + 1
-constexpr int kSW = kDetTW + 2 * kHalo;         // 42
-constexpr int kSH = kDetTH + 2 * kHalo;         // 26
+constexpr int kHalo = 5;                        // FAST (3) / Harris (4) at the ring pixels + 1
+constexpr int kSW = kDetTW + 2 * kHalo;         // staged image
+constexpr int kSH = kDetTH + 2 * kHalo;
 constexpr int kRW = kDetTW + 2, kRH = kDetTH + 2;   // tile + one-pixel ring
+constexpr int kGW = kDetTW + 8, kGH = kDetTH + 8;   // Sobel gradients for the ring's 7x7 windows
+constexpr int kDetCols = 64;                    // threads along x; blockDim = kDetCols * kDetRowsPar
+constexpr int kDetRowsPar = 4;
 
 // 1 iff 9 cyclically consecutive bits of the 16-bit mask m are set.
 __device__ __forceinline__ bool has_run9(unsigned m)
@@ -70,13 +83,38 @@ __device__ __forceinline__ bool has_run9(unsigned m)
     return r != 0u;
 }
 
-__global__ void __launch_bounds__(256)
+// FAST-9 at the staged pixel p (row pitch kSW): the Bresenham circle of radius
+// 3 from (0,-3) clockwise, with compile-time offsets.  A 9-arc holds at least
+// 2 of the 4 compass points, so pixels with fewer bright and fewer dark
+// compass points are rejected before the full test.
+__device__ __forceinline__ bool fast9_staged(const uint8_t *p, int thr)
+{
+    const int ctr = p[0];
+    const int hi = ctr + thr, lo = ctr - thr;
+    const int n0 = p[-3 * kSW], n4 = p[3], n8 = p[3 * kSW], n12 = p[-3];
+    const int nb = (n0 > hi) + (n4 > hi) + (n8 > hi) + (n12 > hi);
+    const int nd = (n0 < lo) + (n4 < lo) + (n8 < lo) + (n12 < lo);
+    if (nb < 2 && nd < 2) return false;
+    const int v[16] = {n0, p[-3 * kSW + 1], p[-2 * kSW + 2], p[-kSW + 3], n4, p[kSW + 3], p[2 * kSW + 2],
+                       p[3 * kSW + 1], n8, p[3 * kSW - 1], p[2 * kSW - 2], p[kSW - 3], n12, p[-kSW - 3],
+                       p[-2 * kSW - 2], p[-3 * kSW - 1]};
+    unsigned bm = 0, dm = 0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        bm |= (unsigned)(v[k] > hi) << k;
+        dm |= (unsigned)(v[k] < lo) << k;
+    }
+    return has_run9(bm) || has_run9(dm);
+}
+
+__global__ void __launch_bounds__(kDetCols * kDetRowsPar)
 detect_kernel(const DevLevel *__restrict__ lv, int n, int thr, Candidate *__restrict__ cand,
               int32_t *__restrict__ cand_count)
 {
     __shared__ uint8_t img[kSH][kSW];
     __shared__ uint8_t isc[kRH][kRW];
     __shared__ long long R[kRH][kRW];
+    __shared__ int16_t gx[kGH][kGW], gy[kGH][kGW];
     __shared__ int16_t clist[kRH * kRW];
     __shared__ int ncl;
 
@@ -90,58 +128,65 @@ detect_kernel(const DevLevel *__restrict__ lv, int n, int thr, Candidate *__rest
     // tiles that hold no pixel of the border-limited region, nor a ring pixel of one
     if (x0 + kDetTW + 1 <= kBorder || y0 + kDetTH + 1 <= kBorder || x0 - 1 >= W - kBorder || y0 - 1 >= H - kBorder)
         return;
+    const int tc = threadIdx.x % kDetCols, tr = threadIdx.x / kDetCols;
 
     if (threadIdx.x == 0) ncl = 0;
-    for (int p = threadIdx.x; p < kSH * kSW; p += blockDim.x) {
-        const int r = p / kSW, c = p - r * kSW;
-        const int gx = clampi(x0 - kHalo + c, 0, W - 1), gy = clampi(y0 - kHalo + r, 0, H - 1);
-        img[r][c] = L.img[(size_t)gy * W + gx];
+    const uint8_t *__restrict__ I = L.img;
+    const bool interior = x0 - kHalo >= 0 && y0 - kHalo >= 0 && x0 + kDetTW + kHalo <= W && y0 + kDetTH + kHalo <= H;
+    for (int r = tr; r < kSH; r += kDetRowsPar) {
+        const int gyy = interior ? y0 - kHalo + r : clampi(y0 - kHalo + r, 0, H - 1);
+        const uint8_t *row = I + gyy * W;
+        for (int c = tc; c < kSW; c += kDetCols) {
+            const int gxx = interior ? x0 - kHalo + c : clampi(x0 - kHalo + c, 0, W - 1);
+            img[r][c] = row[gxx];
+        }
     }
     __syncthreads();
 
     // corner flags on the tile + ring
-    for (int p = threadIdx.x; p < kRH * kRW; p += blockDim.x) {
-        const int r = p / kRW, c = p - r * kRW;
-        const int x = x0 - 1 + c, y = y0 - 1 + r;
-        uint8_t flag = 0;
-        if (x >= kBorder && x < W - kBorder && y >= kBorder && y < H - kBorder) {
-            const int sx = c - 1 + kHalo, sy = r - 1 + kHalo;
-            const int ctr = img[sy][sx];
-            const int hi = ctr + thr, lo = ctr - thr;
-            unsigned bm = 0, dm = 0;
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const int v = img[sy + c_circ[k][1]][sx + c_circ[k][0]];
-                bm |= (unsigned)(v > hi) << k;
-                dm |= (unsigned)(v < lo) << k;
-            }
-            if (has_run9(bm) || has_run9(dm)) {
+    const int xlo = kBorder, xhi = W - kBorder, ylo = kBorder, yhi = H - kBorder;
+    for (int r = tr; r < kRH; r += kDetRowsPar) {
+        const int y = y0 - 1 + r;
+        for (int c = tc; c < kRW; c += kDetCols) {
+            const int x = x0 - 1 + c;
+            uint8_t flag = 0;
+            if (x >= xlo && x < xhi && y >= ylo && y < yhi && fast9_staged(&img[r - 1 + kHalo][c - 1 + kHalo], thr)) {
                 const uint8_t *M = L.mask;
                 const int b = kBorder;
-                flag = M[(size_t)(y - b) * W + x - b] && M[(size_t)(y - b) * W + x + b] &&
-                       M[(size_t)(y + b) * W + x - b] && M[(size_t)(y + b) * W + x + b];
+                flag = M[(y - b) * W + x - b] & M[(y - b) * W + x + b] & M[(y + b) * W + x - b] & M[(y + b) * W + x + b];
             }
+            isc[r][c] = flag;
+            if (flag) clist[atomicAdd(&ncl, 1)] = (int16_t)(r * kRW + c);
         }
-        isc[r][c] = flag;
-        if (flag) clist[atomicAdd(&ncl, 1)] = (int16_t)p;
+    }
+    __syncthreads();
+    const int nc = ncl;
+    if (nc == 0) return;
+
+    // Sobel derivatives once per pixel of the ring's windows; gradient (r, c)
+    // is image pixel (x0 - 4 + c, y0 - 4 + r), staged pixel (c + 1, r + 1)
+    for (int r = tr; r < kGH; r += kDetRowsPar) {
+        for (int c = tc; c < kGW; c += kDetCols) {
+            const int X = c + 1, Y = r + 1;
+            gx[r][c] = (int16_t)((img[Y - 1][X + 1] + 2 * img[Y][X + 1] + img[Y + 1][X + 1]) -
+                                 (img[Y - 1][X - 1] + 2 * img[Y][X - 1] + img[Y + 1][X - 1]));
+            gy[r][c] = (int16_t)((img[Y + 1][X - 1] + 2 * img[Y + 1][X] + img[Y + 1][X + 1]) -
+                                 (img[Y - 1][X - 1] + 2 * img[Y - 1][X] + img[Y - 1][X + 1]));
+        }
     }
     __syncthreads();
 
-    // Harris x25 at every corner of the tile + ring (Sobel 3x3, 7x7 window)
-    const int nc = ncl;
+    // Harris x25 at every corner of the tile + ring (7x7 window of the ring
+    // pixel (r, c) = gradient rows r..r+6, columns c..c+6)
     for (int q = threadIdx.x; q < nc; q += blockDim.x) {
         const int p = clist[q];
         const int r = p / kRW, c = p - r * kRW;
-        const int sx = c - 1 + kHalo, sy = r - 1 + kHalo;
         int a = 0, bb = 0, cc = 0;
-        for (int dy = -3; dy <= 3; ++dy) {
 #pragma unroll
-            for (int dx = -3; dx <= 3; ++dx) {
-                const int X = sx + dx, Y = sy + dy;
-                const int ix = (img[Y - 1][X + 1] + 2 * img[Y][X + 1] + img[Y + 1][X + 1]) -
-                               (img[Y - 1][X - 1] + 2 * img[Y][X - 1] + img[Y + 1][X - 1]);
-                const int iy = (img[Y + 1][X - 1] + 2 * img[Y + 1][X] + img[Y + 1][X + 1]) -
-                               (img[Y - 1][X - 1] + 2 * img[Y - 1][X] + img[Y - 1][X + 1]);
+        for (int dy = 0; dy < 7; ++dy) {
+#pragma unroll
+            for (int dx = 0; dx < 7; ++dx) {
+                const int ix = gx[r + dy][c + dx], iy = gy[r + dy][c + dx];
                 a += ix * ix;
                 bb += iy * iy;
                 cc += ix * iy;
@@ -154,29 +199,24 @@ detect_kernel(const DevLevel *__restrict__ lv, int n, int thr, Candidate *__rest
 
     // 3x3 NMS on the tile; survivors appended with one atomic per warp
     const unsigned lane = threadIdx.x & 31u;
-    for (int it = 0; it < (kDetTW * kDetTH + blockDim.x - 1) / blockDim.x; ++it) {
-        const int p = it * blockDim.x + threadIdx.x;
+    for (int rr = tr; rr < kDetTH; rr += kDetRowsPar) {
+        const int r = rr + 1, c = tc + 1;
+        const int x = x0 + tc, y = y0 + rr;
         bool keep = false;
         long long rv = 0;
-        int x = 0, y = 0;
-        if (p < kDetTW * kDetTH) {
-            const int r = p / kDetTW + 1, c = p % kDetTW + 1;
-            x = x0 + c - 1;
-            y = y0 + r - 1;
-            if (isc[r][c]) {
-                rv = R[r][c];
-                keep = true;
+        if (isc[r][c]) {
+            rv = R[r][c];
+            keep = true;
 #pragma unroll
-                for (int dy = -1; dy <= 1; ++dy)
+            for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        if ((dx | dy) == 0 || !isc[r + dy][c + dx]) continue;
-                        const long long rn = R[r + dy][c + dx];
-                        // the neighbour precedes p in raster order iff dy < 0 or (dy == 0 and dx < 0)
-                        const bool n_first = dy < 0 || (dy == 0 && dx < 0);
-                        if (!(rv > rn || (rv == rn && !n_first))) keep = false;
-                    }
-            }
+                for (int dx = -1; dx <= 1; ++dx) {
+                    if ((dx | dy) == 0 || !isc[r + dy][c + dx]) continue;
+                    const long long rn = R[r + dy][c + dx];
+                    // the neighbour precedes p in raster order iff dy < 0 or (dy == 0 and dx < 0)
+                    const bool n_first = dy < 0 || (dy == 0 && dx < 0);
+                    if (!(rv > rn || (rv == rn && !n_first))) keep = false;
+                }
         }
         const unsigned ballot = __ballot_sync(0xffffffffu, keep);
         if (ballot) {
@@ -514,7 +554,7 @@ cudaError_t launch_detect(const DevLevel *d_lv, int n, int n_tiles, int thr, Can
                           cudaStream_t s)
 {
     if (n_tiles <= 0) return cudaSuccess;
-    detect_kernel<<<n_tiles, 256, 0, s>>>(d_lv, n, thr, cand, count);
+    detect_kernel<<<n_tiles, kDetCols * kDetRowsPar, 0, s>>>(d_lv, n, thr, cand, count);
     note_launch();
     return cudaGetLastError();
 }

@@ -40,8 +40,9 @@ def _pair(nq, nt, seed):
 
 def test_noalloc_equals_workspace_matcher_on_two_calls(A):
     ctx = A.Context()
-    # a large call (150k queries in 4 train slices, 600k scratch entries of
-    # the 1M the fixed array holds), then a smaller one
+    # a large call (150k queries: the fixed array holds only 6 train slices of
+    # partial keys for them, fewer than the workspace matcher uses), then a
+    # smaller one
     for nq, nt, seed in ((150_000, 9_000, 11), (3_001, 2_049, 12)):
         q, t = _pair(nq, nt, seed)
         got = A.hamming_match_noalloc(q, t)
@@ -54,6 +55,6 @@ def test_noalloc_equals_workspace_matcher_on_two_calls(A):
 
 def test_noalloc_rejects_sizes_beyond_its_limit(A):
     L = A.load_library()
-    assert L.hamming_match_noalloc(None, (1 << 20) + 1, None, None, 0, None, 4, 5, None, None, None,
+    assert L.hamming_match_noalloc(None, 1_000_001, None, None, 0, None, 4, 5, None, None, None,
                                    None) == A.ASIFT_ERR_ARG
     assert L.hamming_match_noalloc(None, -1, None, None, 0, None, 4, 5, None, None, None, None) == A.ASIFT_ERR_ARG
