@@ -260,6 +260,50 @@ ASIFT_API asift_status match_pair(asift_ctx *ctx, const uint8_t *d_img1, int H1,
                         const asift_pair_cfg *cfg, asift_pair_match *d_out, int cap, int32_t *d_n,
                         void *d_workspace, size_t ws_bytes, void *stream);
 
+/*
+ * Batched form: all views of many image pairs (uneven sizes) in one launch per
+ * stage, captured once in a CUDA graph and replayed.  asift_plan_create
+ * builds the view / level / matching tables of every pair, allocates the
+ * plan's device workspace and output buffers (the only allocation), uploads
+ * the tables, runs the sequence once uncaptured to validate it, and captures
+ * it in a CUDA graph (use_graph != 0).  The image pointers are fixed at
+ * creation: update the images in place between runs.  asift_plan_run replays
+ * the graph (or relaunches the sequence) on `stream`; results are bit-identical
+ * to match_pair on each pair.  Errors: ASIFT_ERR_ARG, ASIFT_ERR_NOMEM,
+ * ASIFT_ERR_CUDA.
+ */
+typedef struct {
+    const uint8_t *d_img1;
+    int32_t H1, W1, pitch1;
+    const uint8_t *d_img2;
+    int32_t H2, W2, pitch2;
+} asift_pair_desc;
+
+/* Launch shapes of the batched stages (0 = one CTA per tile / the default).
+ * A positive grid makes the stage's kernel persistent over its tile list. */
+typedef struct {
+    int32_t warp_grid, pyramid_grid, detect_grid, match_grid, match_target_items;
+} asift_tuning;
+
+typedef struct asift_plan asift_plan;
+ASIFT_API asift_status asift_plan_create(asift_ctx *ctx, const asift_pair_desc *h_pairs, int n_pairs,
+                                         const asift_pair_cfg *cfg, const asift_tuning *tuning, int use_graph,
+                                         asift_plan **out);
+ASIFT_API asift_status asift_plan_run(asift_plan *plan, void *stream);
+/* Device pointers of pair i's accepted matches, their capacity and count. */
+ASIFT_API asift_status asift_plan_pairs(const asift_plan *plan, int i, asift_pair_match **d_pairs, int *cap,
+                                        int32_t **d_n);
+/* The plan's workspace (status word first) and the pooled keypoint counts
+ * (int32 [2 n_pairs]: image 1, image 2 of each pair). */
+ASIFT_API asift_status asift_plan_workspace(const asift_plan *plan, void **d_workspace, int32_t **d_pool_counts);
+ASIFT_API asift_status asift_plan_set_tuning(asift_plan *plan, const asift_tuning *tuning);
+ASIFT_API asift_status asift_plan_get_tuning(const asift_plan *plan, asift_tuning *out);
+/* Autotuner: times candidate launch shapes of each stage (coordinate descent,
+ * `reps` graph replays per candidate, CUDA events on the plan's stream), keeps
+ * the fastest, re-captures the graph and returns the choice in *out. */
+ASIFT_API asift_status asift_plan_autotune(asift_plan *plan, int reps, asift_tuning *out);
+ASIFT_API void asift_plan_destroy(asift_plan *plan);
+
 /* Debug view into match_pair's workspace after a call: device pointers to the
  * pooled keypoints / descriptors / per-query matches of each image and the
  * host view tables used.  Any output pointer may be NULL. */

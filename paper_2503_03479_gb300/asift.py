@@ -27,7 +27,9 @@ EXPORTED = ["asift_ctx_create", "asift_ctx_destroy", "asift_ctx_orb_cfg", "asift
             "orb_workspace_size", "orb_extract", "hamming_workspace_size", "hamming_match",
             "match_pair_workspace_size", "match_pair", "match_pair_inspect", "asift_read_status",
             "asift_launch_count", "asift_pattern_table", "asift_bin_table", "asift_profile_enable",
-            "asift_profile_read", "hamming_match_noalloc"]
+            "asift_profile_read", "hamming_match_noalloc", "asift_plan_create", "asift_plan_run",
+            "asift_plan_pairs", "asift_plan_workspace", "asift_plan_set_tuning", "asift_plan_get_tuning",
+            "asift_plan_autotune", "asift_plan_destroy"]
 PROF_STAGES = ["upload", "warp", "pyramid", "detect", "select", "orient_brief", "match", "pairs"]
 
 
@@ -53,6 +55,19 @@ class OrbCfg(C.Structure):
 
 class PairCfg(C.Structure):
     _fields_ = [("kmax", C.c_int32), ("ratio_num", C.c_int32), ("ratio_den", C.c_int32), ("per_view", C.c_int32)]
+
+
+class PairDesc(C.Structure):
+    _fields_ = [("d_img1", C.c_void_p), ("H1", C.c_int32), ("W1", C.c_int32), ("pitch1", C.c_int32),
+                ("d_img2", C.c_void_p), ("H2", C.c_int32), ("W2", C.c_int32), ("pitch2", C.c_int32)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("warp_grid", C.c_int32), ("pyramid_grid", C.c_int32), ("detect_grid", C.c_int32),
+                ("match_grid", C.c_int32), ("match_target_items", C.c_int32)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
 
 KP_DTYPE = np.dtype([("x", np.int16), ("y", np.int16), ("level", np.uint8), ("bin", np.uint8),
@@ -100,6 +115,14 @@ def load_library():
         "asift_profile_enable": (i32, [vp, i32]),
         "asift_profile_read": (i32, [vp, vp, i32]),
         "hamming_match_noalloc": (i32, [vp, i32, vp, vp, i32, vp, i32, i32, vp, vp, vp, vp]),
+        "asift_plan_create": (i32, [vp, vp, i32, P(PairCfg), P(Tuning), i32, P(vp)]),
+        "asift_plan_run": (i32, [vp, vp]),
+        "asift_plan_pairs": (i32, [vp, i32, P(vp), P(C.c_int), P(vp)]),
+        "asift_plan_workspace": (i32, [vp, P(vp), P(vp)]),
+        "asift_plan_set_tuning": (i32, [vp, P(Tuning)]),
+        "asift_plan_get_tuning": (i32, [vp, P(Tuning)]),
+        "asift_plan_autotune": (i32, [vp, i32, P(Tuning)]),
+        "asift_plan_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -378,3 +401,92 @@ class Context:
         d2 = sl(ptrs[4], n2 * 32).reshape(n2, 32)
         m = sl(ptrs[6], n1 * 8).view(MATCH_DTYPE)
         return kp1, d1, kp2, d2, m
+
+
+class Plan:
+    """Batched form: all views of many pairs, one launch per stage, replayed
+    from a CUDA graph.  The images (uint8 CUDA tensors) are captured by
+    address: update them in place between runs."""
+
+    def __init__(self, ctx: Context, imgs1, imgs2, kmax: int = 5, num: int = 4, den: int = 5,
+                 tuning: dict | None = None, use_graph: bool = True):
+        self.ctx = ctx
+        self.L = ctx.L
+        self.imgs = list(zip(imgs1, imgs2))      # keep the tensors alive
+        arr = (PairDesc * len(self.imgs))()
+        for i, (a, b) in enumerate(self.imgs):
+            assert a.is_cuda and a.dtype == torch.uint8 and b.is_cuda and b.dtype == torch.uint8
+            arr[i] = PairDesc(a.data_ptr(), a.shape[0], a.shape[1], a.stride(0),
+                              b.data_ptr(), b.shape[0], b.shape[1], b.stride(0))
+        pc = PairCfg(kmax, num, den, 0)
+        tn = Tuning(**tuning) if tuning else None
+        self._p = C.c_void_p()
+        torch.cuda.synchronize()
+        _check("asift_plan_create", self.L.asift_plan_create(ctx._ctx, arr, len(self.imgs), C.byref(pc),
+                                                             C.byref(tn) if tn else None, int(use_graph),
+                                                             C.byref(self._p)))
+
+    def close(self):
+        if self._p:
+            self.L.asift_plan_destroy(self._p)
+            self._p = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self):
+        _check("asift_plan_run", self.L.asift_plan_run(self._p, _stream()))
+
+    def tuning(self) -> dict:
+        t = Tuning()
+        _check("asift_plan_get_tuning", self.L.asift_plan_get_tuning(self._p, C.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, tuning: dict):
+        t = Tuning(**tuning)
+        _check("asift_plan_set_tuning", self.L.asift_plan_set_tuning(self._p, C.byref(t)))
+
+    def autotune(self, reps: int = 3) -> dict:
+        t = Tuning()
+        _check("asift_plan_autotune", self.L.asift_plan_autotune(self._p, reps, C.byref(t)))
+        return t.as_dict()
+
+    def workspace(self):
+        ws, cnt = C.c_void_p(), C.c_void_p()
+        _check("asift_plan_workspace", self.L.asift_plan_workspace(self._p, C.byref(ws), C.byref(cnt)))
+        return ws.value, cnt.value
+
+    def status(self) -> int:
+        ws, _ = self.workspace()
+        st = C.c_int32()
+        _check("asift_read_status", self.L.asift_read_status(C.c_void_p(ws), 1, C.byref(st), _stream()))
+        return st.value
+
+    def pool_counts(self) -> np.ndarray:
+        _, cnt = self.workspace()
+        return device_view(cnt, (2 * len(self.imgs),), "<i4").cpu().numpy()
+
+    def pairs(self, i: int) -> np.ndarray:
+        ptr, cap, dn = C.c_void_p(), C.c_int(), C.c_void_p()
+        _check("asift_plan_pairs", self.L.asift_plan_pairs(self._p, i, C.byref(ptr), C.byref(cap), C.byref(dn)))
+        k = min(int(device_view(dn.value, (1,), "<i4").item()), cap.value)
+        if k == 0:
+            return np.zeros(0, PAIR_DTYPE)
+        return device_view(ptr.value, (k * PAIR_DTYPE.itemsize,), "|u1").cpu().numpy().view(PAIR_DTYPE)
+
+
+class _DevPtr:
+    """A raw device pointer exposed through __cuda_array_interface__ so that
+    torch can view the library's own buffers without copying."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+def device_view(ptr: int, shape, typestr: str) -> torch.Tensor:
+    torch.cuda.synchronize()
+    return torch.as_tensor(_DevPtr(ptr, shape, typestr), device="cuda")

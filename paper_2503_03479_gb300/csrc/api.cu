@@ -451,8 +451,9 @@ static void orb_layout(Bump &b, const LevelTables &T, int nv, int n_groups, cons
 // The level table and group boundaries must already be uploaded.
 static cudaError_t run_orb(asift_ctx *ctx, const LevelTables &T, int nv, int n_groups, const OrbBuffers &o,
                            bool per_view, asift_keypoint *kp, uint8_t *desc, int32_t *view_count, int32_t *view_off,
-                           cudaStream_t s)
+                           cudaStream_t s, const asift_tuning *tune = nullptr)
 {
+    const int pyr_grid = tune ? tune->pyramid_grid : 0, det_grid = tune ? tune->detect_grid : 0;
     const asift_orb_cfg &cfg = ctx->cfg;
     const int L = cfg.n_levels, N = cfg.n_features;
     const size_t nl = (size_t)L * nv;
@@ -460,10 +461,10 @@ static cudaError_t run_orb(asift_ctx *ctx, const LevelTables &T, int nv, int n_g
     if (e != cudaSuccess) return e;
     if (!per_view) {
         for (int l = 1; l < L && e == cudaSuccess; ++l)
-            e = launch_pyramid(o.lv + (size_t)l * nv, nv, T.pyr_tiles[l], s);
+            e = launch_pyramid(o.lv + (size_t)l * nv, nv, T.pyr_tiles[l], s, pyr_grid);
         prof_mark(ctx, 3, s);
         if (e == cudaSuccess)
-            e = launch_detect(o.lv, (int)nl, T.det_tiles, cfg.fast_threshold, o.cand, o.cand_count, s);
+            e = launch_detect(o.lv, (int)nl, T.det_tiles, cfg.fast_threshold, o.cand, o.cand_count, s, det_grid);
         prof_mark(ctx, 4, s);
         if (e == cudaSuccess)
             e = launch_select(o.lv, (int)nl, o.cand, o.cand_count, N, o.slots, o.taken, o.status, s);
@@ -616,77 +617,204 @@ asift_status hamming_match_noalloc(const uint8_t *d_q, int nq, const int32_t *d_
 
 }  // extern "C"
 
-// ---------------------------------------------------------------- match_pair
+// ---------------------------------------------------------------- pair pipeline
+// The whole hot path for P image pairs at once: the views of all 2P images in
+// one warp launch, ORB over all of them (one pool slice per image), and P
+// matching problems in one matcher launch.  match_pair is the case P = 1; the
+// plan API captures the same sequence in a CUDA graph.
 namespace asift {
 
-struct PairLayout {
-    int nv1 = 0, nv2 = 0;
-    std::vector<asift_view_desc> views;     // image 1 views then image 2 views
-    std::vector<int64_t> level0_off;        // per view: offset of level 0 in the arena
+struct PairSpec {
+    int H1, W1, H2, W2;
+};
+
+struct Pipeline {
+    int n_pairs = 0;
+    std::vector<int> nv1, nv2;               // views per image
+    std::vector<int> first;                  // view index of each image's first view (2P + 1)
+    std::vector<asift_view_desc> views;      // all views, image by image
+    std::vector<int64_t> level0_off;         // per view: level-0 offset in the arena
     LevelTables T;
+    int nv = 0;
+    // device regions
     int32_t *status = nullptr;
     DevView *dv = nullptr;
     OrbBuffers o{};
-    float *src1 = nullptr, *src2 = nullptr;
+    MatchProblem *probs = nullptr;
+    ImageConv *conv = nullptr;
+    std::vector<float *> src;                // fp32 copy of each image
     int32_t *view_count = nullptr, *view_off = nullptr;
     asift_keypoint *kp = nullptr;
     uint8_t *desc = nullptr;
     asift_match *match = nullptr;
     uint8_t *accept = nullptr;
     int32_t *n_acc = nullptr;
-    void *part = nullptr;
+    std::vector<void *> part;                // matcher partials per problem
     int32_t *block_count = nullptr;
+    // host copies of the device tables (uploaded as one blob from dv)
+    std::vector<DevView> h_dv;
+    std::vector<MatchProblem> h_probs;
+    std::vector<ImageConv> h_conv;
+    int n_tiles = 0, cw_max = 0, bw_max = 0, total_q = 0, total_blk = 0;
+    long long max_px = 0;
+    size_t tab_bytes = 0;                    // bytes from dv to the end of the table region
     size_t bytes = 0;
 };
 
-static bool pair_layout(const asift_ctx *ctx, int H1, int W1, int H2, int W2, const asift_pair_cfg &pc, void *base,
-                        bool per_view, PairLayout &P)
+static bool pipeline_layout(const asift_ctx *ctx, const PairSpec *ps, int P, int kmax, bool per_view, void *base,
+                            Pipeline &L)
 {
     const asift_orb_cfg &cfg = ctx->cfg;
-    int n1 = view_table(H1, W1, pc.kmax, nullptr, 0), n2 = view_table(H2, W2, pc.kmax, nullptr, 0);
-    P.nv1 = n1;
-    P.nv2 = n2;
-    P.views.resize(n1 + n2);
-    view_table(H1, W1, pc.kmax, P.views.data(), n1);
-    view_table(H2, W2, pc.kmax, P.views.data() + n1, n2);
-    const int nv = n1 + n2;
-    if (nv > 65535) return false;
-    // level 0 of every view lives in the same arena as the other levels
+    const int N = cfg.n_features;
+    L.n_pairs = P;
+    L.nv1.assign(P, 0);
+    L.nv2.assign(P, 0);
+    L.first.assign(2 * P + 1, 0);
+    L.views.clear();
+    for (int p = 0; p < P; ++p) {
+        const int a = view_table(ps[p].H1, ps[p].W1, kmax, nullptr, 0);
+        const int b = view_table(ps[p].H2, ps[p].W2, kmax, nullptr, 0);
+        L.nv1[p] = a;
+        L.nv2[p] = b;
+        const size_t o = L.views.size();
+        L.views.resize(o + a + b);
+        view_table(ps[p].H1, ps[p].W1, kmax, L.views.data() + o, a);
+        view_table(ps[p].H2, ps[p].W2, kmax, L.views.data() + o + a, b);
+        L.first[2 * p + 1] = (int)o + a;
+        L.first[2 * p + 2] = (int)o + a + b;
+    }
+    L.nv = (int)L.views.size();
+    if (L.nv > 65535 || L.nv < 1) return false;
+    // the tables uploaded per call are contiguous: dv, probs, conv, lv, group_first
     Bump b(base);
-    P.status = b.take<int32_t>(64);
-    P.dv = b.take<DevView>(nv);
-    build_levels(cfg, P.views.data(), nv, nullptr, nullptr, nullptr, nullptr, per_view, P.T);
-    orb_layout(b, P.T, nv, 2, cfg, P.o);
-    P.o.status = P.status;
-    // pointers of the level table with the real arena base
-    build_levels(cfg, P.views.data(), nv, nullptr, nullptr, P.o.arena_u8, P.o.arena_mask, per_view, P.T);
-    P.level0_off.resize(nv);
-    for (int v = 0; v < nv; ++v)
-        P.level0_off[v] = P.o.arena_u8 ? (int64_t)(P.T.lv[v].img - P.o.arena_u8) : 0;
-    if (!base) {
-        // offsets are needed for the table layout even in the size query
-        long long off = 0;
-        for (int v = 0; v < nv; ++v) {
-            P.level0_off[v] = off;
-            for (int l = 0; l < cfg.n_levels; ++l)
-                off += ((long long)level_size(P.views[v].Wv, l) * level_size(P.views[v].Hv, l) + 15) & ~15LL;
+    L.status = b.take<int32_t>(64);
+    const size_t tab0 = (b.off + 255) & ~(size_t)255;
+    L.dv = b.take<DevView>(L.nv);
+    L.probs = b.take<MatchProblem>(P);
+    L.conv = b.take<ImageConv>(2 * P);
+    build_levels(cfg, L.views.data(), L.nv, nullptr, nullptr, nullptr, nullptr, per_view, L.T);
+    orb_layout(b, L.T, L.nv, 2 * P, cfg, L.o);
+    L.tab_bytes = (size_t)((char *)(L.o.group_first + 2 * P + 1) - (char *)L.dv);
+    if (!base) {                              // sizing pass: the same offsets from a null base
+        Bump c(nullptr);
+        c.take<int32_t>(64);
+        c.take<DevView>(L.nv);
+        c.take<MatchProblem>(P);
+        c.take<ImageConv>(2 * P);
+        c.take<DevLevel>(std::max<size_t>((size_t)cfg.n_levels * L.nv, 1));
+        c.take<int32_t>(2 * P + 1);
+        L.tab_bytes = c.off - tab0;
+    }
+    L.o.status = L.status;
+    build_levels(cfg, L.views.data(), L.nv, nullptr, nullptr, L.o.arena_u8, L.o.arena_mask, per_view, L.T);
+    L.level0_off.assign(L.nv, 0);
+    long long off = 0;
+    for (int v = 0; v < L.nv; ++v) {
+        L.level0_off[v] = off;
+        for (int l = 0; l < cfg.n_levels; ++l)
+            off += ((long long)level_size(L.views[v].Wv, l) * level_size(L.views[v].Hv, l) + 15) & ~15LL;
+    }
+    L.src.assign(2 * P, nullptr);
+    L.max_px = 0;
+    for (int p = 0; p < P; ++p) {
+        L.src[2 * p] = b.take<float>((size_t)ps[p].W1 * ps[p].H1);
+        L.src[2 * p + 1] = b.take<float>((size_t)ps[p].W2 * ps[p].H2);
+        L.max_px = std::max(L.max_px, std::max((long long)ps[p].W1 * ps[p].H1, (long long)ps[p].W2 * ps[p].H2));
+    }
+    L.view_count = b.take<int32_t>(L.nv);
+    L.view_off = b.take<int32_t>(L.nv);
+    const size_t cap = (size_t)L.nv * N;
+    L.kp = b.take<asift_keypoint>(cap);
+    L.desc = b.take<uint8_t>(cap * 32);
+    L.match = b.take<asift_match>(cap);
+    L.accept = b.take<uint8_t>(cap);
+    L.n_acc = b.take<int32_t>(P);
+    L.part.assign(P, nullptr);
+    L.h_probs.assign(P, MatchProblem{});
+    for (int p = 0; p < P; ++p) {
+        const int nq = L.nv1[p] * N, nt = L.nv2[p] * N;
+        L.part[p] = b.take<unsigned char>(hamming_partial_bytes(nq, nt));
+        const size_t q0 = (size_t)L.first[2 * p] * N, t0 = (size_t)L.first[2 * p + 1] * N;
+        MatchProblem &M = L.h_probs[p];
+        match_problem_init(M, L.desc + q0 * 32, nq, L.o.group_total + 2 * p, L.desc + t0 * 32, nt,
+                           L.o.group_total + 2 * p + 1, L.part[p], 0, L.match + q0, L.accept + q0, L.n_acc + p);
+        M.kp1 = L.kp + q0;
+        M.kp2 = L.kp + t0;
+    }
+    match_problems_offsets(L.h_probs.data(), P, &L.total_q, &L.total_blk);
+    L.block_count = b.take<int32_t>(std::max(L.total_blk, 1));
+    L.bytes = b.off + 256;
+    return true;
+}
+
+// Fills the host tables that depend on the image pointers and the outputs,
+// and packs everything that goes to the device into one blob starting at dv.
+static void pipeline_tables(Pipeline &L, const asift_pair_desc *pairs, asift_pair_match *const *outs,
+                            const int *caps, int32_t *const *d_ns, bool per_view, std::vector<unsigned char> &blob)
+{
+    const int P = L.n_pairs;
+    std::vector<const float *> srcs(L.nv);
+    std::vector<int> pitches(L.nv);
+    L.h_conv.assign(2 * P, ImageConv{});
+    for (int p = 0; p < P; ++p) {
+        for (int im = 0; im < 2; ++im) {
+            const int g = 2 * p + im;
+            for (int v = L.first[g]; v < L.first[g + 1]; ++v) {
+                srcs[v] = L.src[g];
+                pitches[v] = im ? pairs[p].W2 : pairs[p].W1;
+            }
+            ImageConv &c = L.h_conv[g];
+            c.src = im ? pairs[p].d_img2 : pairs[p].d_img1;
+            c.dst = L.src[g];
+            c.pitch = im ? pairs[p].pitch2 : pairs[p].pitch1;
+            c.W = im ? pairs[p].W2 : pairs[p].W1;
+            c.H = im ? pairs[p].H2 : pairs[p].H1;
+        }
+        L.h_probs[p].pairs = outs[p];
+        L.h_probs[p].cap = caps[p];
+        L.h_probs[p].d_n = d_ns[p];
+    }
+    build_views(L.views.data(), L.nv, srcs.data(), pitches.data(), L.level0_off.data(), per_view, L.h_dv, &L.n_tiles,
+                &L.cw_max, &L.bw_max);
+    blob.assign(L.tab_bytes, 0);
+    char *b0 = (char *)L.dv;
+    std::memcpy(blob.data(), L.h_dv.data(), sizeof(DevView) * L.nv);
+    std::memcpy(blob.data() + ((char *)L.o.lv - b0), L.T.lv.data(), sizeof(DevLevel) * L.T.lv.size());
+    std::memcpy(blob.data() + ((char *)L.o.group_first - b0), L.first.data(), sizeof(int32_t) * L.first.size());
+    std::memcpy(blob.data() + ((char *)L.probs - b0), L.h_probs.data(), sizeof(MatchProblem) * P);
+    std::memcpy(blob.data() + ((char *)L.conv - b0), L.h_conv.data(), sizeof(ImageConv) * 2 * P);
+}
+
+// The launch sequence (tables already on the device).
+static cudaError_t pipeline_run(asift_ctx *ctx, const Pipeline &L, const asift_pair_cfg &pc, bool per_view,
+                                const asift_tuning *tune, cudaStream_t s)
+{
+    const int P = L.n_pairs;
+    cudaError_t e = launch_convert_images(L.conv, 2 * P, L.max_px, s);
+    prof_mark(ctx, 1, s);
+    if (e == cudaSuccess) {
+        if (!per_view) {
+            e = launch_warp(L.dv, L.nv, L.n_tiles, L.cw_max, L.bw_max, L.o.arena_u8, L.o.arena_mask, nullptr, s,
+                            tune ? tune->warp_grid : 0);
+        } else {
+            for (int v = 0; v < L.nv && e == cudaSuccess; ++v) {
+                const int tiles = L.h_dv[v].ntx * ((L.views[v].Hv + kWarpTH - 1) / kWarpTH);
+                e = launch_warp(L.dv + v, 1, tiles, L.cw_max, L.bw_max, L.o.arena_u8, L.o.arena_mask, nullptr, s);
+            }
         }
     }
-    P.src1 = b.take<float>((size_t)W1 * H1);
-    P.src2 = b.take<float>((size_t)W2 * H2);
-    P.view_count = b.take<int32_t>(nv);
-    P.view_off = b.take<int32_t>(nv);
-    const size_t cap = (size_t)nv * cfg.n_features;
-    P.kp = b.take<asift_keypoint>(cap);
-    P.desc = b.take<uint8_t>(cap * 32);
-    const int nq = n1 * cfg.n_features, nt = n2 * cfg.n_features;
-    P.match = b.take<asift_match>(nq);
-    P.accept = b.take<uint8_t>(nq);
-    P.n_acc = b.take<int32_t>(1);
-    P.part = b.take<unsigned char>(hamming_partial_bytes(nq, nt));
-    P.block_count = b.take<int32_t>(pair_blocks(nq));
-    P.bytes = b.off + 256;
-    return true;
+    prof_mark(ctx, 2, s);
+    if (e == cudaSuccess)
+        e = run_orb(ctx, L.T, L.nv, 2 * P, L.o, per_view, L.kp, L.desc, L.view_count, L.view_off, s, tune);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.n_acc, 0, sizeof(int32_t) * P, s);
+    if (e == cudaSuccess) {
+        MatchTuning mt{tune ? tune->match_grid : 0, tune ? tune->match_target_items : 0};
+        e = launch_match(L.probs, P, L.h_probs[0], L.total_q, true, pc.ratio_num, pc.ratio_den, mt, s);
+    }
+    prof_mark(ctx, 7, s);
+    if (e == cudaSuccess) e = launch_pairs(L.probs, P, L.h_probs[0], L.total_blk, L.block_count, L.dv, L.status, s);
+    prof_mark(ctx, 8, s);
+    return e;
 }
 
 }  // namespace asift
@@ -704,9 +832,10 @@ size_t match_pair_workspace_size(const asift_ctx *ctx, int H1, int W1, int H2, i
     if (!ctx || H1 < 1 || W1 < 1 || H2 < 1 || W2 < 1) return 0;
     const asift_pair_cfg pc = pair_cfg_or_default(cfg);
     if (pc.kmax < 0 || pc.kmax > 7) return 0;
-    PairLayout P;
-    if (!pair_layout(ctx, H1, W1, H2, W2, pc, nullptr, pc.per_view != 0, P)) return 0;
-    return P.bytes;
+    Pipeline L;
+    PairSpec ps{H1, W1, H2, W2};
+    if (!pipeline_layout(ctx, &ps, 1, pc.kmax, pc.per_view != 0, nullptr, L)) return 0;
+    return L.bytes;
 }
 
 asift_status match_pair(asift_ctx *ctx, const uint8_t *d_img1, int H1, int W1, int pitch1, const uint8_t *d_img2,
@@ -719,60 +848,17 @@ asift_status match_pair(asift_ctx *ctx, const uint8_t *d_img1, int H1, int W1, i
         pc.ratio_num < 0 || cap < 0 || (cap && !d_out) || !d_n || !d_workspace)
         return ASIFT_ERR_ARG;
     const bool per_view = pc.per_view != 0;
-    PairLayout P;
-    if (!pair_layout(ctx, H1, W1, H2, W2, pc, d_workspace, per_view, P)) return ASIFT_ERR_ARG;
-    if (ws_bytes < P.bytes) return ASIFT_ERR_ARG;
-    const asift_orb_cfg &oc = ctx->cfg;
-    const int nv = P.nv1 + P.nv2, N = oc.n_features;
-    const int nq = P.nv1 * N, nt = P.nv2 * N;
+    Pipeline L;
+    PairSpec ps{H1, W1, H2, W2};
+    if (!pipeline_layout(ctx, &ps, 1, pc.kmax, per_view, d_workspace, L)) return ASIFT_ERR_ARG;
+    if (ws_bytes < L.bytes) return ASIFT_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-
-    // host tables: views (warp) + levels (ORB) + group boundaries, one upload
-    std::vector<const float *> srcs(nv);
-    std::vector<int> pitches(nv);
-    for (int v = 0; v < nv; ++v) {
-        srcs[v] = v < P.nv1 ? P.src1 : P.src2;
-        pitches[v] = v < P.nv1 ? W1 : W2;
-    }
-    std::vector<DevView> dv;
-    int n_tiles, cwm, bwm;
-    build_views(P.views.data(), nv, srcs.data(), pitches.data(), P.level0_off.data(), per_view, dv, &n_tiles, &cwm,
-                &bwm);
-    const size_t tab_end = (size_t)((char *)P.o.group_first - (char *)P.dv) + 3 * sizeof(int32_t);
-    std::vector<unsigned char> blob(tab_end);
-    std::memcpy(blob.data(), dv.data(), sizeof(DevView) * nv);
-    std::memcpy(blob.data() + ((char *)P.o.lv - (char *)P.dv), P.T.lv.data(), sizeof(DevLevel) * P.T.lv.size());
-    const int32_t gf[3] = {0, P.nv1, nv};
-    std::memcpy(blob.data() + ((char *)P.o.group_first - (char *)P.dv), gf, sizeof(gf));
-
+    asift_pair_desc pd{d_img1, H1, W1, pitch1, d_img2, H2, W2, pitch2};
+    std::vector<unsigned char> blob;
+    pipeline_tables(L, &pd, &d_out, &cap, &d_n, per_view, blob);
     prof_mark(ctx, 0, s);
-    cudaError_t e = upload(ctx, P.dv, blob.data(), blob.size(), s);
-    if (e == cudaSuccess) e = launch_u8_to_f32(d_img1, pitch1, W1, H1, P.src1, s);
-    if (e == cudaSuccess) e = launch_u8_to_f32(d_img2, pitch2, W2, H2, P.src2, s);
-    prof_mark(ctx, 1, s);
-    if (e == cudaSuccess) {
-        if (!per_view) {
-            e = launch_warp(P.dv, nv, n_tiles, cwm, bwm, P.o.arena_u8, P.o.arena_mask, nullptr, s);
-        } else {
-            for (int v = 0; v < nv && e == cudaSuccess; ++v) {
-                const int tiles = dv[v].ntx * ((P.views[v].Hv + kWarpTH - 1) / kWarpTH);
-                e = launch_warp(P.dv + v, 1, tiles, cwm, bwm, P.o.arena_u8, P.o.arena_mask, nullptr, s);
-            }
-        }
-    }
-    prof_mark(ctx, 2, s);
-    if (e == cudaSuccess) e = run_orb(ctx, P.T, nv, 2, P.o, per_view, P.kp, P.desc, P.view_count, P.view_off, s);
-    // pool 1 = views of image 1 (slice 0), pool 2 = views of image 2 (slice nv1 * N)
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(P.n_acc, 0, sizeof(int32_t), s);
-    if (e == cudaSuccess)
-        e = launch_hamming(P.desc, nq, P.o.group_total, P.desc + (size_t)P.nv1 * N * 32, nt, P.o.group_total + 1,
-                           pc.ratio_num, pc.ratio_den, P.match, P.accept, P.n_acc, P.part, s);
-    prof_mark(ctx, 7, s);
-    if (e == cudaSuccess)
-        e = launch_pairs(P.accept, P.match, nq, P.o.group_total, P.block_count, P.kp, P.kp + (size_t)P.nv1 * N, P.dv,
-                         d_out, cap, d_n, P.status, s);
-    prof_mark(ctx, 8, s);
+    cudaError_t e = upload(ctx, L.dv, blob.data(), blob.size(), s);
+    if (e == cudaSuccess) e = pipeline_run(ctx, L, pc, per_view, nullptr, s);
     return cuda_status(e);
 }
 
@@ -782,17 +868,246 @@ asift_status match_pair_inspect(const asift_ctx *ctx, int H1, int W1, int H2, in
 {
     if (!ctx || !d_workspace) return ASIFT_ERR_ARG;
     const asift_pair_cfg pc = pair_cfg_or_default(cfg);
-    PairLayout P;
-    if (!pair_layout(ctx, H1, W1, H2, W2, pc, d_workspace, pc.per_view != 0, P)) return ASIFT_ERR_ARG;
-    const size_t off2 = (size_t)P.nv1 * ctx->cfg.n_features;
-    if (d_kp1) *d_kp1 = P.kp;
-    if (d_desc1) *d_desc1 = P.desc;
-    if (d_n1) *d_n1 = P.o.group_total;
-    if (d_kp2) *d_kp2 = P.kp + off2;
-    if (d_desc2) *d_desc2 = P.desc + off2 * 32;
-    if (d_n2) *d_n2 = P.o.group_total + 1;
-    if (d_match) *d_match = P.match;
+    Pipeline L;
+    PairSpec ps{H1, W1, H2, W2};
+    if (!pipeline_layout(ctx, &ps, 1, pc.kmax, pc.per_view != 0, d_workspace, L)) return ASIFT_ERR_ARG;
+    const size_t off2 = (size_t)L.first[1] * ctx->cfg.n_features;
+    if (d_kp1) *d_kp1 = L.kp;
+    if (d_desc1) *d_desc1 = L.desc;
+    if (d_n1) *d_n1 = L.o.group_total;
+    if (d_kp2) *d_kp2 = L.kp + off2;
+    if (d_desc2) *d_desc2 = L.desc + off2 * 32;
+    if (d_n2) *d_n2 = L.o.group_total + 1;
+    if (d_match) *d_match = L.match;
     return ASIFT_OK;
 }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- batched plan
+struct asift_plan {
+    asift_ctx *ctx = nullptr;
+    asift_pair_cfg pc{};
+    asift_tuning tune{};
+    std::vector<asift_pair_desc> pairs;
+    asift::Pipeline L;
+    void *ws = nullptr;
+    std::vector<asift_pair_match *> outs;
+    std::vector<int> caps;
+    int32_t *d_ns = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool use_graph = true;
+};
+
+static void plan_free(asift_plan *p)
+{
+    if (!p) return;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    for (auto *o : p->outs)
+        if (o) cudaFree(o);
+    if (p->d_ns) cudaFree(p->d_ns);
+    if (p->ws) cudaFree(p->ws);
+    if (p->stream) cudaStreamDestroy(p->stream);
+    delete p;
+}
+
+// Captures the launch sequence of the plan in a CUDA graph on its stream.
+static cudaError_t plan_capture(asift_plan *p)
+{
+    if (p->exec) { cudaGraphExecDestroy(p->exec); p->exec = nullptr; }
+    if (p->graph) { cudaGraphDestroy(p->graph); p->graph = nullptr; }
+    if (!p->use_graph) return cudaSuccess;
+    const bool prof = p->ctx->prof;
+    p->ctx->prof = false;                    // no stage events inside the graph
+    cudaError_t e = cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t r = asift::pipeline_run(p->ctx, p->L, p->pc, false, &p->tune, p->stream);
+        cudaError_t c = cudaStreamEndCapture(p->stream, &p->graph);
+        e = (r != cudaSuccess) ? r : c;
+    }
+    p->ctx->prof = prof;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+    return e;
+}
+
+static cudaError_t plan_launch(asift_plan *p, cudaStream_t s)
+{
+    if (p->use_graph && p->exec) return cudaGraphLaunch(p->exec, s);
+    return asift::pipeline_run(p->ctx, p->L, p->pc, false, &p->tune, s);
+}
+
+extern "C" {
+
+asift_status asift_plan_create(asift_ctx *ctx, const asift_pair_desc *h_pairs, int n_pairs,
+                               const asift_pair_cfg *cfg, const asift_tuning *tuning, int use_graph,
+                               asift_plan **out)
+{
+    if (!ctx || !h_pairs || n_pairs < 1 || n_pairs > asift::match_max_problems() || !out) return ASIFT_ERR_ARG;
+    *out = nullptr;
+    const asift_pair_cfg pc = pair_cfg_or_default(cfg);
+    if (pc.kmax < 0 || pc.kmax > 7 || pc.ratio_den < 1 || pc.ratio_num < 0 || pc.per_view) return ASIFT_ERR_ARG;
+    std::vector<asift::PairSpec> ps(n_pairs);
+    for (int i = 0; i < n_pairs; ++i) {
+        const asift_pair_desc &d = h_pairs[i];
+        if (!d.d_img1 || !d.d_img2 || d.H1 < 1 || d.W1 < 1 || d.H2 < 1 || d.W2 < 1 || d.H1 > 16384 || d.W1 > 16384 ||
+            d.H2 > 16384 || d.W2 > 16384 || d.pitch1 < d.W1 || d.pitch2 < d.W2)
+            return ASIFT_ERR_ARG;
+        ps[i] = asift::PairSpec{d.H1, d.W1, d.H2, d.W2};
+    }
+    asift_plan *p = new (std::nothrow) asift_plan;
+    if (!p) return ASIFT_ERR_NOMEM;
+    p->ctx = ctx;
+    p->pc = pc;
+    if (tuning) p->tune = *tuning;
+    p->use_graph = use_graph != 0;
+    p->pairs.assign(h_pairs, h_pairs + n_pairs);
+    if (!asift::pipeline_layout(ctx, ps.data(), n_pairs, pc.kmax, false, nullptr, p->L)) {
+        plan_free(p);
+        return ASIFT_ERR_ARG;
+    }
+    const size_t bytes = p->L.bytes;
+    if (cudaMalloc(&p->ws, bytes) != cudaSuccess) { plan_free(p); return ASIFT_ERR_NOMEM; }
+    if (cudaMemset(p->ws, 0, 256) != cudaSuccess) { plan_free(p); return ASIFT_ERR_CUDA; }
+    p->L = asift::Pipeline{};
+    asift::pipeline_layout(ctx, ps.data(), n_pairs, pc.kmax, false, p->ws, p->L);
+    p->outs.assign(n_pairs, nullptr);
+    p->caps.assign(n_pairs, 0);
+    if (cudaMalloc(&p->d_ns, sizeof(int32_t) * n_pairs) != cudaSuccess) { plan_free(p); return ASIFT_ERR_NOMEM; }
+    std::vector<int32_t *> ns(n_pairs);
+    for (int i = 0; i < n_pairs; ++i) {
+        p->caps[i] = std::max(1, p->L.nv1[i] * ctx->cfg.n_features);
+        if (cudaMalloc(&p->outs[i], sizeof(asift_pair_match) * p->caps[i]) != cudaSuccess) {
+            plan_free(p);
+            return ASIFT_ERR_NOMEM;
+        }
+        ns[i] = p->d_ns + i;
+    }
+    if (cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        plan_free(p);
+        return ASIFT_ERR_CUDA;
+    }
+    std::vector<unsigned char> blob;
+    asift::pipeline_tables(p->L, p->pairs.data(), p->outs.data(), p->caps.data(), ns.data(), false, blob);
+    cudaError_t e = cudaMemcpyAsync(p->L.dv, blob.data(), blob.size(), cudaMemcpyHostToDevice, p->stream);
+    // one plain run validates the sequence and sets the kernels' attributes before capture
+    if (e == cudaSuccess) e = asift::pipeline_run(ctx, p->L, pc, false, &p->tune, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e == cudaSuccess) e = plan_capture(p);
+    if (e != cudaSuccess) {
+        plan_free(p);
+        return ASIFT_ERR_CUDA;
+    }
+    *out = p;
+    return ASIFT_OK;
+}
+
+asift_status asift_plan_run(asift_plan *plan, void *stream)
+{
+    if (!plan) return ASIFT_ERR_ARG;
+    return cuda_status(plan_launch(plan, static_cast<cudaStream_t>(stream)));
+}
+
+asift_status asift_plan_pairs(const asift_plan *plan, int i, asift_pair_match **d_pairs, int *cap, int32_t **d_n)
+{
+    if (!plan || i < 0 || i >= (int)plan->outs.size()) return ASIFT_ERR_ARG;
+    if (d_pairs) *d_pairs = plan->outs[i];
+    if (cap) *cap = plan->caps[i];
+    if (d_n) *d_n = plan->d_ns + i;
+    return ASIFT_OK;
+}
+
+asift_status asift_plan_workspace(const asift_plan *plan, void **d_workspace, int32_t **d_pool_counts)
+{
+    if (!plan) return ASIFT_ERR_ARG;
+    if (d_workspace) *d_workspace = plan->ws;
+    if (d_pool_counts) *d_pool_counts = plan->L.o.group_total;
+    return ASIFT_OK;
+}
+
+asift_status asift_plan_set_tuning(asift_plan *plan, const asift_tuning *tuning)
+{
+    if (!plan || !tuning) return ASIFT_ERR_ARG;
+    if (tuning->warp_grid < 0 || tuning->pyramid_grid < 0 || tuning->detect_grid < 0 || tuning->match_grid < 0 ||
+        tuning->match_target_items < 0)
+        return ASIFT_ERR_ARG;
+    plan->tune = *tuning;
+    if (cudaStreamSynchronize(plan->stream) != cudaSuccess) return ASIFT_ERR_CUDA;
+    return cuda_status(plan_capture(plan));
+}
+
+asift_status asift_plan_get_tuning(const asift_plan *plan, asift_tuning *out)
+{
+    if (!plan || !out) return ASIFT_ERR_ARG;
+    *out = plan->tune;
+    return ASIFT_OK;
+}
+
+// Milliseconds per replay of the plan's current sequence.
+static cudaError_t plan_time(asift_plan *p, int reps, float *ms)
+{
+    cudaEvent_t a, b;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&b);
+    if (e != cudaSuccess) { cudaEventDestroy(a); return e; }
+    e = plan_launch(p, p->stream);                 // warm
+    if (e == cudaSuccess) e = cudaEventRecord(a, p->stream);
+    for (int i = 0; i < reps && e == cudaSuccess; ++i) e = plan_launch(p, p->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b, p->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+    if (e == cudaSuccess) *ms /= std::max(1, reps);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return e;
+}
+
+asift_status asift_plan_autotune(asift_plan *plan, int reps, asift_tuning *out)
+{
+    if (!plan || reps < 1) return ASIFT_ERR_ARG;
+    int sms = 152;
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    // coordinate descent over one knob at a time, the others at their best
+    struct Knob {
+        int32_t *field;
+        std::vector<int> cands;
+    };
+    asift_tuning &t = plan->tune;
+    std::vector<Knob> knobs = {
+        {&t.warp_grid, {0, 2 * sms, 3 * sms}},
+        {&t.pyramid_grid, {0, 4 * sms, 8 * sms}},
+        {&t.detect_grid, {0, 4 * sms, 8 * sms}},
+        {&t.match_grid, {7 * sms, 4 * sms}},
+        {&t.match_target_items, {0, 4 * 7 * sms, 7 * sms}},
+    };
+    cudaError_t e = cudaSuccess;
+    for (auto &k : knobs) {
+        int best = *k.field;
+        float best_ms = 1e30f;
+        for (int c : k.cands) {
+            *k.field = c;
+            e = plan_capture(plan);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = plan_time(plan, reps, &ms);
+            if (e != cudaSuccess) break;
+            if (ms < best_ms) { best_ms = ms; best = c; }
+        }
+        *k.field = best;
+        if (e != cudaSuccess) break;
+    }
+    if (e == cudaSuccess) e = plan_capture(plan);
+    if (out) *out = plan->tune;
+    return cuda_status(e);
+}
+
+void asift_plan_destroy(asift_plan *plan) { plan_free(plan); }
 
 }  // extern "C"

@@ -32,6 +32,13 @@ constexpr int kWarpTW = 64;   // view columns per warp tile
 constexpr int kWarpTH = 16;   // view rows per warp tile
 constexpr int kWarpThreads = 256;
 
+// A source image to convert to fp32 (the warp reads fp32 sources).
+struct ImageConv {
+    const uint8_t *src;
+    float *dst;
+    int32_t pitch, W, H, pad;
+};
+
 // ---------------------------------------------------------------- ORB stage
 // One (view, pyramid level) as the ORB kernels read it.
 struct DevLevel {
@@ -63,6 +70,33 @@ struct SlotKp {             // a selected keypoint before orientation / descript
 
 constexpr int kDetTW = 64, kDetTH = 16;   // FAST tile
 constexpr int kPyrTW = 64, kPyrTH = 16;   // pyramid tile (4 px per thread across x)
+
+// ---------------------------------------------------------------- matching
+// One brute-force matching problem (query pool vs train pool of one pair),
+// with where its results and, for match_pair, its accepted pairs go.
+struct MatchProblem {
+    const uint4 *q, *t;               // descriptors (2 x uint4 each)
+    const int32_t *d_nq, *d_nt;       // device counts (NULL: the capacities are the counts)
+    int32_t nq_cap, nt_cap;
+    int32_t s_alloc;                  // train slices the partial buffer holds
+    int32_t q_off;                    // first query of this problem in a merged launch
+    int32_t blk_off, n_blk;           // output blocks of the pair writer
+    int32_t cap, pad;                 // accepted-pair capacity
+    int *plan;                        // {n_split, chunk} published by the top-2 kernel
+    uint2 *part;                      // partial keys [s_alloc][nq_cap]
+    asift_match *out;                 // per query
+    uint8_t *accept;
+    int32_t *n_acc;
+    const asift_keypoint *kp1, *kp2;  // pools, for the pair writer
+    asift_pair_match *pairs;
+    int32_t *d_n;
+};
+
+// Launch shapes of the matcher (0 = default).
+struct MatchTuning {
+    int grid;
+    int target_items;
+};
 
 // ---------------------------------------------------------------- helpers
 __host__ __device__ inline int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }

@@ -17,13 +17,15 @@ struct SlotKp;
 // warp.cu
 void warp_strip_widths(const asift_view_desc &v, int *cw, int *bw);
 cudaError_t launch_u8_to_f32(const uint8_t *src, int pitch, int W, int H, float *dst, cudaStream_t s);
+struct ImageConv;
+cudaError_t launch_convert_images(const ImageConv *d_list, int n, long long max_px, cudaStream_t s);
 cudaError_t launch_warp(const DevView *d_views, int n_views, int n_tiles, int cw_max, int bw_max, uint8_t *u8,
-                        uint8_t *mask, float *f32, cudaStream_t s);
+                        uint8_t *mask, float *f32, cudaStream_t s, int grid = 0);
 
 // orb.cu
-cudaError_t launch_pyramid(const DevLevel *d_lv, int n, int n_tiles, cudaStream_t s);
+cudaError_t launch_pyramid(const DevLevel *d_lv, int n, int n_tiles, cudaStream_t s, int grid = 0);
 cudaError_t launch_detect(const DevLevel *d_lv, int n, int n_tiles, int thr, Candidate *cand, int32_t *count,
-                          cudaStream_t s);
+                          cudaStream_t s, int grid = 0);
 size_t select_smem_bytes();
 cudaError_t launch_select(const DevLevel *d_lv, int n, const Candidate *cand, const int32_t *count, int n_features,
                           SlotKp *slots, int32_t *taken, int32_t *status, cudaStream_t s);
@@ -36,19 +38,26 @@ cudaError_t launch_orient_brief(const DevLevel *d_lv, int n_views, int n_levels,
                                 cudaStream_t s);
 
 // match.cu
+struct MatchProblem;
+struct MatchTuning;
 int hamming_splits_alloc(int nt_cap);
 size_t hamming_partial_bytes(int nq, int nt);
+int pair_blocks(int nq);
+int match_max_problems();
+void match_problem_init(MatchProblem &P, const uint8_t *q, int nq, const int32_t *d_nq, const uint8_t *t, int nt,
+                        const int32_t *d_nt, void *region, int s_alloc, asift_match *out, uint8_t *accept,
+                        int32_t *n_acc);
+void match_problems_offsets(MatchProblem *probs, int n, int *total_q, int *total_blk);
+cudaError_t launch_match(const MatchProblem *d_probs, int n_probs, const MatchProblem &single, int total_q,
+                         bool any_train, int num, int den, const MatchTuning &tune, cudaStream_t s);
 cudaError_t launch_hamming(const uint8_t *q, int nq, const int32_t *d_nq, const uint8_t *t, int nt,
                            const int32_t *d_nt, int num, int den, asift_match *out, uint8_t *accept,
                            int32_t *n_acc, void *part, cudaStream_t s);
 cudaError_t launch_hamming_noalloc(const uint8_t *q, int nq, const int32_t *d_nq, const uint8_t *t, int nt,
                                    const int32_t *d_nt, int num, int den, asift_match *out, uint8_t *accept,
                                    int32_t *n_acc, cudaStream_t s);
-int pair_blocks(int nq);
-cudaError_t launch_pairs(const uint8_t *accept, const asift_match *m, int nq_cap, const int32_t *d_nq,
-                         int32_t *block_count, const asift_keypoint *kp1, const asift_keypoint *kp2,
-                         const DevView *views, asift_pair_match *out, int cap, int32_t *d_n, int32_t *status,
-                         cudaStream_t s);
+cudaError_t launch_pairs(const MatchProblem *d_probs, int n_probs, const MatchProblem &single, int total_blk,
+                         int32_t *block_count, const DevView *views, int32_t *status, cudaStream_t s);
 
 // tables.cpp (host; each table generated from its written definition)
 void make_view_desc(int H, int W, double t, double phi_deg, int k, int j, asift_view_desc *v);

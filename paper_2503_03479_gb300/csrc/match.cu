@@ -1,13 +1,15 @@
 // match.cu -- brute-force Hamming matching with the ratio test (Sec. III-B,
 // Sec. IV-C) on sm_103a, and the accepted-pair output of match_pair.
 //
-// hamming_top2_kernel: each thread keeps kMQ query descriptors (2 x uint4 each)
-// in registers; the CTA stages kMTile train descriptors in shared memory and
-// every thread scans them with XOR + popc.  The running nearest and
-// second-nearest are kept as packed keys (distance << 23 | train index), so a
-// min/max network gives the lowest index on distance ties and d2 counts equal
-// distances.  The train set is split over gridDim.y slices; merge_kernel takes
-// the two smallest keys over the slices (exact: keys are unique).
+// One launch serves a list of independent problems (one per image pair):
+// hamming_top2_kernel is persistent over (problem, train slice, query block)
+// items.  Each thread keeps kMQ query descriptors (2 x uint4 each) in
+// registers; the CTA stages kMTile train descriptors in shared memory and every
+// thread scans them.  The running nearest and second-nearest are kept as
+// packed keys (distance << 23 | train index), so a min/max network gives the
+// lowest index on distance ties and d2 counts equal distances.  merge_kernel
+// takes the two smallest keys over a problem's slices (exact: keys are unique).
+// How a problem is sliced is decided on the device from its actual pool sizes.
 #include <mutex>
 
 #include "common.cuh"
@@ -19,11 +21,12 @@ constexpr int kMQ = 4;
 constexpr int kMThreads = 128;
 constexpr int kMTile = 256;
 constexpr unsigned kNoKey = 0xffffffffu;
+constexpr int kMaxMatchProblems = 512;
 
 // Hamming distance of two 256-bit descriptors.  The eight XOR words are summed
 // bit-sliced with carry-save adders (three-input XOR and majority, one LOP3
 // each), leaving four words of weight 1, 2, 4 and 8: four popc instead of
-// eight, the popc pipe being the matcher's bottleneck.
+// eight.
 __device__ __forceinline__ void csa(unsigned a, unsigned b, unsigned c, unsigned &sum, unsigned &carry)
 {
     sum = a ^ b ^ c;
@@ -45,49 +48,79 @@ __device__ __forceinline__ unsigned ham256(const uint4 &a0, const uint4 &a1, con
     return __popc(ones) + 2 * __popc(twos) + 4 * __popc(fours) + 8 * __popc(eights);
 }
 
-// Split of the work into (query block, train slice) items, decided on the
-// device from the actual counts so that a pool smaller than its capacity
-// still fills the GPU.  Every CTA derives the same plan.
-struct MatchPlan {
-    int n_split, chunk;
-};
-
-__device__ __forceinline__ MatchPlan match_plan(int nq, int nt, int s_alloc, int target_items)
+__device__ __forceinline__ const MatchProblem &prob(const MatchProblem *many, const MatchProblem &single, int i)
 {
-    MatchPlan p{0, kMTile};
-    if (nq <= 0 || nt <= 0) return p;
-    const int qblocks = (nq + kMThreads * kMQ - 1) / (kMThreads * kMQ);
-    int s = max(1, (target_items + qblocks - 1) / qblocks);
-    s = min(s, (nt + kMTile - 1) / kMTile);
-    s = max(1, min(s, s_alloc));
-    int chunk = (nt + s - 1) / s;
-    chunk = ((chunk + kMTile - 1) / kMTile) * kMTile;
-    p.chunk = chunk;
-    p.n_split = (nt + chunk - 1) / chunk;
-    return p;
+    return many ? many[i] : single;
 }
 
-// Persistent over the items: item = split * qblocks + query block.  The plan
-// is published in plan_out (two ints) for the merge kernel.
-__global__ void __launch_bounds__(kMThreads, 8)
-hamming_top2_kernel(const uint4 *__restrict__ q, int nq_cap, const int32_t *__restrict__ d_nq,
-                    const uint4 *__restrict__ t, int nt_cap, const int32_t *__restrict__ d_nt, int s_alloc,
-                    int target_items, int *__restrict__ plan_out, uint2 *__restrict__ part)
+__device__ __forceinline__ int count_of(const int32_t *d, int cap) { return d ? min(max(*d, 0), cap) : cap; }
+
+// Slicing of one problem: about `target` items of kMThreads*kMQ queries x
+// chunk trains, chunk a multiple of kMTile, at most s_alloc slices.
+__device__ __forceinline__ void match_plan(int nq, int nt, int s_alloc, int target, int &n_split, int &chunk)
+{
+    n_split = 0;
+    chunk = kMTile;
+    if (nq <= 0 || nt <= 0) return;
+    const int qblocks = (nq + kMThreads * kMQ - 1) / (kMThreads * kMQ);
+    int s = max(1, (target + qblocks - 1) / qblocks);
+    s = min(s, (nt + kMTile - 1) / kMTile);
+    s = max(1, min(s, s_alloc));
+    int c = (nt + s - 1) / s;
+    c = ((c + kMTile - 1) / kMTile) * kMTile;
+    chunk = c;
+    n_split = (nt + c - 1) / c;
+}
+
+__global__ void __launch_bounds__(kMThreads, 7)
+hamming_top2_kernel(const MatchProblem *__restrict__ many, int n_probs, const MatchProblem single, int target_items)
 {
     __shared__ uint4 st[2 * kMTile];
-    const int nq = d_nq ? min(*d_nq, nq_cap) : nq_cap;
-    const int nt = d_nt ? min(*d_nt, nt_cap) : nt_cap;
-    const MatchPlan P = match_plan(nq, nt, s_alloc, target_items);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        plan_out[0] = P.n_split;
-        plan_out[1] = P.chunk;
+    __shared__ int s_items[kMaxMatchProblems + 1];      // item prefix over problems
+    __shared__ int s_chunk[kMaxMatchProblems], s_qblocks[kMaxMatchProblems];
+    const int np = many ? n_probs : 1;
+    if (threadIdx.x == 0) {
+        // the target is shared out in proportion to each problem's pair count
+        double total = 0.0;
+        for (int p = 0; p < np; ++p) {
+            const MatchProblem &P = prob(many, single, p);
+            total += (double)count_of(P.d_nq, P.nq_cap) * (double)count_of(P.d_nt, P.nt_cap);
+        }
+        int acc = 0;
+        for (int p = 0; p < np; ++p) {
+            const MatchProblem &P = prob(many, single, p);
+            const int nq = count_of(P.d_nq, P.nq_cap), nt = count_of(P.d_nt, P.nt_cap);
+            const double w = total > 0 ? (double)nq * (double)nt / total : 0.0;
+            const int tgt = max(1, (int)(target_items * w));
+            int ns, ch;
+            match_plan(nq, nt, P.s_alloc, tgt, ns, ch);
+            s_chunk[p] = ch;
+            s_qblocks[p] = (nq + kMThreads * kMQ - 1) / (kMThreads * kMQ);
+            s_items[p] = acc;
+            acc += ns * s_qblocks[p];
+            if (blockIdx.x == 0) {
+                P.plan[0] = ns;
+                P.plan[1] = ch;
+            }
+        }
+        s_items[np] = acc;
     }
-    const int qblocks = (nq + kMThreads * kMQ - 1) / (kMThreads * kMQ);
-    const int items = qblocks * P.n_split;
+    __syncthreads();
+    const int items = s_items[np];
     for (int item = blockIdx.x; item < items; item += gridDim.x) {
-        const int split = item / qblocks, qb = item - split * qblocks;
+        int p = 0;
+        while (s_items[p + 1] <= item) ++p;
+        const MatchProblem &P = prob(many, single, p);
+        const int nq = count_of(P.d_nq, P.nq_cap), nt = count_of(P.d_nt, P.nt_cap);
+        const int nq_cap = P.nq_cap;
+        uint2 *__restrict__ part = P.part;
+        const int local = item - s_items[p];
+        const int qblocks = s_qblocks[p];
+        const int split = local / qblocks, qb = local - split * qblocks;
         const int qbase = qb * (kMThreads * kMQ);
-        const int t0 = split * P.chunk, t1 = min(nt, t0 + P.chunk);
+        const int t0 = split * s_chunk[p], t1 = min(nt, t0 + s_chunk[p]);
+        const uint4 *__restrict__ q = P.q;
+        const uint4 *__restrict__ t = P.t;
         uint4 qa[kMQ], qc[kMQ];
         unsigned b1[kMQ], b2[kMQ];
 #pragma unroll
@@ -127,52 +160,76 @@ hamming_top2_kernel(const uint4 *__restrict__ q, int nq_cap, const int32_t *__re
     }
 }
 
+// One thread per query of every problem (problems laid end to end by q_off).
 __global__ void __launch_bounds__(256)
-merge_kernel(const uint2 *__restrict__ part, const int *__restrict__ plan, int nq_cap,
-             const int32_t *__restrict__ d_nq, int nt_cap, const int32_t *__restrict__ d_nt, int num, int den,
-             asift_match *__restrict__ out, uint8_t *__restrict__ accept, int32_t *__restrict__ n_acc)
+merge_kernel(const MatchProblem *__restrict__ many, int n_probs, const MatchProblem single, int total_q, int num,
+             int den)
 {
-    const int nq = d_nq ? min(*d_nq, nq_cap) : nq_cap;
-    const int nt = d_nt ? min(*d_nt, nt_cap) : nt_cap;
-    const int n_split = (plan && nt > 0) ? plan[0] : 0;
-    const int qi = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    int p = 0;
+    if (many) {
+        int lo = 0, hi = n_probs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (many[mid].q_off <= g) lo = mid; else hi = mid - 1;
+        }
+        p = lo;
+    }
+    const MatchProblem &P = prob(many, single, p);
+    const int qi = g - P.q_off;
+    const int nq = count_of(P.d_nq, P.nq_cap), nt = count_of(P.d_nt, P.nt_cap);
+    const int n_split = nt > 0 ? P.plan[0] : 0;
     bool acc = false;
-    if (qi < nq) {
+    if (g < total_q && qi < nq) {
         unsigned b1 = kNoKey, b2 = kNoKey;
         for (int s = 0; s < n_split; ++s) {
-            const uint2 p = part[(size_t)s * nq_cap + qi];
-            b2 = min(b2, max(b1, p.x));
-            b1 = min(b1, p.x);
-            b2 = min(b2, max(b1, p.y));
-            b1 = min(b1, p.y);
+            const uint2 pp = P.part[(size_t)s * P.nq_cap + qi];
+            b2 = min(b2, max(b1, pp.x));
+            b1 = min(b1, pp.x);
+            b2 = min(b2, max(b1, pp.y));
+            b1 = min(b1, pp.y);
         }
         asift_match m;
         m.best = (b1 == kNoKey) ? -1 : (int)(b1 & 0x7fffffu);
         m.d1 = (uint16_t)((b1 == kNoKey) ? 257 : (b1 >> 23));
         m.d2 = (uint16_t)((b2 == kNoKey) ? 257 : (b2 >> 23));
         acc = nt >= 2 && den * (int)m.d1 < num * (int)m.d2;
-        out[qi] = m;
-        if (accept) accept[qi] = (uint8_t)acc;
+        P.out[qi] = m;
+        if (P.accept) P.accept[qi] = (uint8_t)acc;
     }
-    if (n_acc) {
-        const unsigned bal = __ballot_sync(0xffffffffu, acc);
-        if ((threadIdx.x & 31) == 0 && bal) atomicAdd(n_acc, __popc(bal));
-    }
+    // one atomic per warp and problem (a warp can straddle two problems)
+    const unsigned same = __match_any_sync(0xffffffffu, p);
+    const unsigned bal = __ballot_sync(0xffffffffu, acc) & same;
+    const int leader = __ffs(same) - 1;
+    if ((int)(threadIdx.x & 31u) == leader && bal && P.n_acc) atomicAdd(P.n_acc, __popc(bal));
 }
 
 // ---------------------------------------------------------------- accepted pairs
 constexpr int kPairBlock = 1024;
 
+__device__ __forceinline__ int pair_problem(const MatchProblem *many, int n_probs, int block)
+{
+    if (!many) return 0;
+    int lo = 0, hi = n_probs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (many[mid].blk_off <= block) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 __global__ void __launch_bounds__(kPairBlock)
-pair_count_kernel(const uint8_t *__restrict__ accept, int nq_cap, const int32_t *__restrict__ d_nq,
+pair_count_kernel(const MatchProblem *__restrict__ many, int n_probs, const MatchProblem single,
                   int32_t *__restrict__ block_count)
 {
     __shared__ int s;
     if (threadIdx.x == 0) s = 0;
     __syncthreads();
-    const int nq = min(*d_nq, nq_cap);
-    const int i = blockIdx.x * kPairBlock + threadIdx.x;
-    const bool a = i < nq && accept[i];
+    const int p = pair_problem(many, n_probs, blockIdx.x);
+    const MatchProblem &P = prob(many, single, p);
+    const int nq = count_of(P.d_nq, P.nq_cap);
+    const int i = (blockIdx.x - P.blk_off) * kPairBlock + threadIdx.x;
+    const bool a = i < nq && P.accept[i];
     const unsigned bal = __ballot_sync(0xffffffffu, a);
     if ((threadIdx.x & 31) == 0 && bal) atomicAdd(&s, __popc(bal));
     __syncthreads();
@@ -195,22 +252,23 @@ __device__ void backproject(const DevView &V, int l, int x, int y, float *sx, fl
 }
 
 __global__ void __launch_bounds__(kPairBlock)
-pair_write_kernel(const uint8_t *__restrict__ accept, const asift_match *__restrict__ m, int nq_cap,
-                  const int32_t *__restrict__ d_nq, const int32_t *__restrict__ block_count,
-                  const asift_keypoint *__restrict__ kp1, const asift_keypoint *__restrict__ kp2,
-                  const DevView *__restrict__ views, asift_pair_match *__restrict__ out, int cap,
-                  int32_t *__restrict__ d_n, int32_t *__restrict__ status)
+pair_write_kernel(const MatchProblem *__restrict__ many, int n_probs, const MatchProblem single,
+                  const int32_t *__restrict__ block_count, const DevView *__restrict__ views,
+                  int32_t *__restrict__ status)
 {
     __shared__ int wsum[kPairBlock / 32];
     __shared__ int base;
-    const int nq = min(*d_nq, nq_cap);
+    const int p = pair_problem(many, n_probs, blockIdx.x);
+    const MatchProblem &P = prob(many, single, p);
+    const int lb = blockIdx.x - P.blk_off;
+    const int nq = count_of(P.d_nq, P.nq_cap);
     if (threadIdx.x == 0) {
         int b = 0;
-        for (int k = 0; k < (int)blockIdx.x; ++k) b += block_count[k];
+        for (int k = P.blk_off; k < (int)blockIdx.x; ++k) b += block_count[k];
         base = b;
     }
-    const int i = blockIdx.x * kPairBlock + threadIdx.x;
-    const bool a = i < nq && accept[i];
+    const int i = lb * kPairBlock + threadIdx.x;
+    const bool a = i < nq && P.accept[i];
     const unsigned lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
     const unsigned bal = __ballot_sync(0xffffffffu, a);
     if (lane == 0) wsum[w] = __popc(bal);
@@ -218,17 +276,17 @@ pair_write_kernel(const uint8_t *__restrict__ accept, const asift_match *__restr
     if (threadIdx.x == 0) {
         int acc = 0;
         for (int k = 0; k < kPairBlock / 32; ++k) { const int v = wsum[k]; wsum[k] = acc; acc += v; }
-        if (blockIdx.x == gridDim.x - 1) {
-            *d_n = base + acc;
-            if (base + acc > cap) set_status(status, ASIFT_ERR_CAPACITY);
+        if (lb == P.n_blk - 1) {
+            *P.d_n = base + acc;
+            if (base + acc > P.cap) set_status(status, ASIFT_ERR_CAPACITY);
         }
     }
     __syncthreads();
     if (a) {
         const int o = base + wsum[w] + __popc(bal & ((1u << lane) - 1u));
-        if (o < cap) {
-            const asift_match mm = m[i];
-            const asift_keypoint k1 = kp1[i], k2 = kp2[mm.best];
+        if (o < P.cap) {
+            const asift_match mm = P.out[i];
+            const asift_keypoint k1 = P.kp1[i], k2 = P.kp2[mm.best];
             asift_pair_match pm;
             backproject(views[k1.view], k1.level, k1.x, k1.y, &pm.x1, &pm.y1);
             backproject(views[k2.view], k2.level, k2.x, k2.y, &pm.x2, &pm.y2);
@@ -236,15 +294,13 @@ pair_write_kernel(const uint8_t *__restrict__ accept, const asift_match *__restr
             pm.t = mm.best;
             pm.d1 = mm.d1;
             pm.d2 = mm.d2;
-            out[o] = pm;
+            P.pairs[o] = pm;
         }
     }
 }
 
 // ---------------------------------------------------------------- host side
 constexpr int kMatchMaxSplits = 64;
-constexpr int kMatchGrid = 152 * 8;            // persistent CTAs (8 per SM at 64 registers)
-constexpr int kMatchTargetItems = 2 * kMatchGrid;
 constexpr size_t kPlanBytes = 256;             // the published plan precedes the partials
 
 int hamming_splits_alloc(int nt_cap) { return std::max(1, std::min(kMatchMaxSplits, (nt_cap + kMTile - 1) / kMTile)); }
@@ -254,21 +310,54 @@ size_t hamming_partial_bytes(int nq, int nt)
     return kPlanBytes + sizeof(uint2) * (size_t)hamming_splits_alloc(nt) * (size_t)std::max(nq, 1);
 }
 
-static cudaError_t launch_match_kernels(const uint8_t *q, int nq, const int32_t *d_nq, const uint8_t *t, int nt,
-                                        const int32_t *d_nt, int num, int den, asift_match *out, uint8_t *accept,
-                                        int32_t *n_acc, void *region, int s_alloc, cudaStream_t s)
+int pair_blocks(int nq) { return std::max(1, (nq + kPairBlock - 1) / kPairBlock); }
+
+void match_problem_init(MatchProblem &P, const uint8_t *q, int nq, const int32_t *d_nq, const uint8_t *t, int nt,
+                        const int32_t *d_nt, void *region, int s_alloc, asift_match *out, uint8_t *accept,
+                        int32_t *n_acc)
 {
-    if (nq <= 0) return cudaSuccess;
-    int *plan = static_cast<int *>(region);
-    uint2 *part = reinterpret_cast<uint2 *>(static_cast<char *>(region) + kPlanBytes);
-    if (nt > 0) {
-        hamming_top2_kernel<<<kMatchGrid, kMThreads, 0, s>>>(reinterpret_cast<const uint4 *>(q), nq, d_nq,
-                                                            reinterpret_cast<const uint4 *>(t), nt, d_nt, s_alloc,
-                                                            kMatchTargetItems, plan, part);
+    P = MatchProblem{};
+    P.q = reinterpret_cast<const uint4 *>(q);
+    P.t = reinterpret_cast<const uint4 *>(t);
+    P.d_nq = d_nq;
+    P.d_nt = d_nt;
+    P.nq_cap = nq;
+    P.nt_cap = nt;
+    P.s_alloc = s_alloc > 0 ? s_alloc : hamming_splits_alloc(nt);
+    P.plan = static_cast<int *>(region);
+    P.part = reinterpret_cast<uint2 *>(static_cast<char *>(region) + kPlanBytes);
+    P.out = out;
+    P.accept = accept;
+    P.n_acc = n_acc;
+    P.n_blk = pair_blocks(nq);
+}
+
+void match_problems_offsets(MatchProblem *probs, int n, int *total_q, int *total_blk)
+{
+    int q = 0, b = 0;
+    for (int i = 0; i < n; ++i) {
+        probs[i].q_off = q;
+        probs[i].blk_off = b;
+        q += probs[i].nq_cap;
+        b += probs[i].n_blk;
+    }
+    *total_q = q;
+    *total_blk = b;
+}
+
+int match_max_problems() { return kMaxMatchProblems; }
+
+cudaError_t launch_match(const MatchProblem *d_probs, int n_probs, const MatchProblem &single, int total_q,
+                         bool any_train, int num, int den, const MatchTuning &tune, cudaStream_t s)
+{
+    if (total_q <= 0) return cudaSuccess;
+    const int grid = tune.grid > 0 ? tune.grid : 152 * 7;
+    const int target = tune.target_items > 0 ? tune.target_items : 2 * grid;
+    if (any_train) {
+        hamming_top2_kernel<<<grid, kMThreads, 0, s>>>(d_probs, n_probs, single, target);
         note_launch();
     }
-    merge_kernel<<<(nq + 255) / 256, 256, 0, s>>>(part, nt > 0 ? plan : nullptr, nq, d_nq, nt, d_nt, num, den, out,
-                                                  accept, n_acc);
+    merge_kernel<<<(total_q + 255) / 256, 256, 0, s>>>(d_probs, n_probs, single, total_q, num, den);
     note_launch();
     return cudaGetLastError();
 }
@@ -277,8 +366,20 @@ cudaError_t launch_hamming(const uint8_t *q, int nq, const int32_t *d_nq, const 
                            const int32_t *d_nt, int num, int den, asift_match *out, uint8_t *accept,
                            int32_t *n_acc, void *part, cudaStream_t s)
 {
-    return launch_match_kernels(q, nq, d_nq, t, nt, d_nt, num, den, out, accept, n_acc, part,
-                                hamming_splits_alloc(nt), s);
+    if (nq <= 0) return cudaSuccess;
+    MatchProblem P;
+    match_problem_init(P, q, nq, d_nq, t, nt, d_nt, part, 0, out, accept, n_acc);
+    return launch_match(nullptr, 0, P, nq, nt > 0, num, den, MatchTuning{}, s);
+}
+
+cudaError_t launch_pairs(const MatchProblem *d_probs, int n_probs, const MatchProblem &single, int total_blk,
+                         int32_t *block_count, const DevView *views, int32_t *status, cudaStream_t s)
+{
+    if (total_blk <= 0) return cudaSuccess;
+    pair_count_kernel<<<total_blk, kPairBlock, 0, s>>>(d_probs, n_probs, single, block_count);
+    pair_write_kernel<<<total_blk, kPairBlock, 0, s>>>(d_probs, n_probs, single, block_count, views, status);
+    note_launch(2);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- allocation-free matcher
@@ -323,22 +424,9 @@ cudaError_t launch_hamming_noalloc(const uint8_t *q, int nq, const int32_t *d_nq
     // as many train slices as the fixed array holds for nq queries (at least one)
     const long long entries = (long long)((ASIFT_NOALLOC_SCRATCH_BYTES - kPlanBytes) / sizeof(uint2));
     const int s_alloc = (int)std::max(1LL, std::min<long long>(hamming_splits_alloc(nt), entries / nq));
-    return launch_match_kernels(q, nq, d_nq, t, nt, d_nt, num, den, out, accept, n_acc, region, s_alloc, s);
-}
-
-int pair_blocks(int nq) { return std::max(1, (nq + kPairBlock - 1) / kPairBlock); }
-
-cudaError_t launch_pairs(const uint8_t *accept, const asift_match *m, int nq_cap, const int32_t *d_nq,
-                         int32_t *block_count, const asift_keypoint *kp1, const asift_keypoint *kp2,
-                         const DevView *views, asift_pair_match *out, int cap, int32_t *d_n, int32_t *status,
-                         cudaStream_t s)
-{
-    const int nb = pair_blocks(nq_cap);
-    pair_count_kernel<<<nb, kPairBlock, 0, s>>>(accept, nq_cap, d_nq, block_count);
-    pair_write_kernel<<<nb, kPairBlock, 0, s>>>(accept, m, nq_cap, d_nq, block_count, kp1, kp2, views, out, cap, d_n,
-                                                status);
-    note_launch(2);
-    return cudaGetLastError();
+    MatchProblem P;
+    match_problem_init(P, q, nq, d_nq, t, nt, d_nt, region, s_alloc, out, accept, n_acc);
+    return launch_match(nullptr, 0, P, nq, nt > 0, num, den, MatchTuning{}, s);
 }
 
 }  // namespace asift

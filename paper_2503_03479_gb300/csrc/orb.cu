@@ -22,12 +22,10 @@ namespace asift {
 // Each CTA makes a kPyrTW x kPyrTH tile of level l.  The source columns and
 // weights of the tile's columns and rows are computed once (32-bit integer
 // divisions) and shared; each pixel is then four byte loads and integer FMAs.
-__global__ void __launch_bounds__(256)
-pyramid_kernel(const DevLevel *__restrict__ lv, int n)
+__device__ __forceinline__ void pyramid_tile(int tile, const DevLevel *__restrict__ lv, int n)
 {
     __shared__ int16_t sx0[kPyrTW], sx1[kPyrTW], sfx[kPyrTW];
     __shared__ int16_t sy0[kPyrTH], sy1[kPyrTH], sfy[kPyrTH];
-    const int tile = blockIdx.x;
     const int e = find_owner(lv, n, tile, [](const DevLevel &d) { return d.pyr_tile_start; });
     const DevLevel &L = lv[e];
     const int lt = tile - L.pyr_tile_start;
@@ -60,6 +58,16 @@ pyramid_kernel(const DevLevel *__restrict__ lv, int n)
         L.img_w[y * Wl + x] = (uint8_t)((s + (1u << 21)) >> 22);
         const uint8_t *m0 = L.prev_mask + y0 * Wp, *m1 = L.prev_mask + y1 * Wp;
         L.mask_w[y * Wl + x] = (uint8_t)(m0[x0] & m0[x1] & m1[x0] & m1[x1]);
+    }
+}
+
+// Grid-stride over the tiles: one CTA per tile, or a persistent grid.
+__global__ void __launch_bounds__(256)
+pyramid_kernel(int n_tiles, const DevLevel *__restrict__ lv, int n)
+{
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        pyramid_tile(tile, lv, n);
+        __syncthreads();
     }
 }
 
@@ -107,8 +115,7 @@ __device__ __forceinline__ bool fast9_staged(const uint8_t *p, int thr)
     return has_run9(bm) || has_run9(dm);
 }
 
-__global__ void __launch_bounds__(kDetCols * kDetRowsPar)
-detect_kernel(const DevLevel *__restrict__ lv, int n, int thr, Candidate *__restrict__ cand,
+__device__ __forceinline__ void detect_tile(int tile, const DevLevel *__restrict__ lv, int n, int thr, Candidate *__restrict__ cand,
               int32_t *__restrict__ cand_count)
 {
     __shared__ uint8_t img[kSH][kSW];
@@ -118,7 +125,6 @@ detect_kernel(const DevLevel *__restrict__ lv, int n, int thr, Candidate *__rest
     __shared__ int16_t clist[kRH * kRW];
     __shared__ int ncl;
 
-    const int tile = blockIdx.x;
     const int e = find_owner(lv, n, tile, [](const DevLevel &d) { return d.det_tile_start; });
     const DevLevel &L = lv[e];
     const int lt = tile - L.det_tile_start;
@@ -235,6 +241,17 @@ detect_kernel(const DevLevel *__restrict__ lv, int n, int thr, Candidate *__rest
                 }
             }
         }
+    }
+}
+
+// Grid-stride over the tiles: one CTA per tile, or a persistent grid.
+__global__ void __launch_bounds__(kDetCols * kDetRowsPar)
+detect_kernel(int n_tiles, const DevLevel *__restrict__ lv, int n, int thr, Candidate *__restrict__ cand,
+              int32_t *__restrict__ cand_count)
+{
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        detect_tile(tile, lv, n, thr, cand, cand_count);
+        __syncthreads();
     }
 }
 
@@ -542,19 +559,21 @@ orient_brief_kernel(const DevLevel *__restrict__ lv, int n_views, int n_levels, 
 }
 
 // ---------------------------------------------------------------- host side
-cudaError_t launch_pyramid(const DevLevel *d_lv, int n, int n_tiles, cudaStream_t s)
+cudaError_t launch_pyramid(const DevLevel *d_lv, int n, int n_tiles, cudaStream_t s, int grid)
 {
     if (n_tiles <= 0) return cudaSuccess;
-    pyramid_kernel<<<n_tiles, 256, 0, s>>>(d_lv, n);
+    const int g = (grid > 0 && grid < n_tiles) ? grid : n_tiles;
+    pyramid_kernel<<<g, 256, 0, s>>>(n_tiles, d_lv, n);
     note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_detect(const DevLevel *d_lv, int n, int n_tiles, int thr, Candidate *cand, int32_t *count,
-                          cudaStream_t s)
+                          cudaStream_t s, int grid)
 {
     if (n_tiles <= 0) return cudaSuccess;
-    detect_kernel<<<n_tiles, kDetCols * kDetRowsPar, 0, s>>>(d_lv, n, thr, cand, count);
+    const int g = (grid > 0 && grid < n_tiles) ? grid : n_tiles;
+    detect_kernel<<<g, kDetCols * kDetRowsPar, 0, s>>>(n_tiles, d_lv, n, thr, cand, count);
     note_launch();
     return cudaGetLastError();
 }

@@ -78,6 +78,18 @@ __global__ void u8_to_f32_kernel(const uint8_t *__restrict__ src, int pitch, int
     }
 }
 
+// Every image of a list: blockIdx.y selects the image, x strides its pixels.
+__global__ void convert_images_kernel(const ImageConv *__restrict__ list)
+{
+    const ImageConv c = list[blockIdx.y];
+    const long long n = (long long)c.W * c.H;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(i / c.W), x = (int)(i - (long long)y * c.W);
+        c.dst[i] = (float)c.src[(size_t)y * c.pitch + x];
+    }
+}
+
 struct CanvasGeom {           // Q32 map of canvas (i, j) to the source point
     long long cq, sq, ox, oy;  // p = (cq*dx2 + sq*dy2 + ox, -sq*dx2 + cq*dy2 + oy)
     int Wr, Hr;
@@ -89,8 +101,7 @@ struct CanvasGeom {           // Q32 map of canvas (i, j) to the source point
     }
 };
 
-__global__ void __launch_bounds__(kWarpThreads, 3)
-warp_view_kernel(const DevView *__restrict__ views, int n_views, int cw_max, int bw_max,
+__device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restrict__ views, int n_views, int cw_max, int bw_max,
                  uint8_t *__restrict__ out_u8, uint8_t *__restrict__ out_mask, float *__restrict__ out_f32)
 {
     extern __shared__ float smem[];
@@ -99,7 +110,6 @@ warp_view_kernel(const DevView *__restrict__ views, int n_views, int cw_max, int
     float *Ss = Bs + kWarpTH * bw_max;             // [kStage][kStagePitch] staged source
     __shared__ float gs[ASIFT_MAX_GAUSS];
 
-    const int tile = blockIdx.x;
     const int vi = find_owner(views, n_views, tile, [](const DevView &v) { return v.tile_start; });
     const DevView &V = views[vi];
     const int lt = tile - V.tile_start;
@@ -274,6 +284,17 @@ warp_view_kernel(const DevView *__restrict__ views, int n_views, int cw_max, int
     }
 }
 
+// Grid-stride over the tiles: one CTA per tile, or a persistent grid.
+__global__ void __launch_bounds__(kWarpThreads, 3)
+warp_view_kernel(int n_tiles, const DevView *__restrict__ views, int n_views, int cw_max, int bw_max,
+                 uint8_t *__restrict__ out_u8, uint8_t *__restrict__ out_mask, float *__restrict__ out_f32)
+{
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        warp_view_tile(tile, views, n_views, cw_max, bw_max, out_u8, out_mask, out_f32);
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- host side
 void warp_strip_widths(const asift_view_desc &v, int *cw, int *bw)
 {
@@ -298,8 +319,17 @@ cudaError_t launch_u8_to_f32(const uint8_t *src, int pitch, int W, int H, float 
     return cudaGetLastError();
 }
 
+cudaError_t launch_convert_images(const ImageConv *d_list, int n, long long max_px, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int bx = (int)std::max<long long>(1, std::min<long long>((max_px + 255) / 256, 152LL * 4));
+    convert_images_kernel<<<dim3(bx, n), 256, 0, s>>>(d_list);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_warp(const DevView *d_views, int n_views, int n_tiles, int cw_max, int bw_max,
-                        uint8_t *u8, uint8_t *mask, float *f32, cudaStream_t s)
+                        uint8_t *u8, uint8_t *mask, float *f32, cudaStream_t s, int grid)
 {
     if (n_tiles <= 0) return cudaSuccess;
     const size_t smem = warp_smem_bytes(cw_max, bw_max);
@@ -308,7 +338,8 @@ cudaError_t launch_warp(const DevView *d_views, int n_views, int n_tiles, int cw
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    warp_view_kernel<<<n_tiles, kWarpThreads, smem, s>>>(d_views, n_views, cw_max, bw_max, u8, mask, f32);
+    const int g = (grid > 0 && grid < n_tiles) ? grid : n_tiles;
+    warp_view_kernel<<<g, kWarpThreads, smem, s>>>(n_tiles, d_views, n_views, cw_max, bw_max, u8, mask, f32);
     note_launch();
     return cudaGetLastError();
 }

@@ -227,6 +227,28 @@ def pairs_mixed(seed: int, n_pairs: int, wmin=480, wmax=1920, hmin=360, hmax=108
     return out
 
 
+def mixed_pair(seed: int, index: int, wmin=480, wmax=1920, hmin=360, hmax=1080,
+               tilt_deg=(30.0, 85.0), ss: int = 2) -> Pair:
+    """Pair `index` of a mixed-size batch, generated independently of the
+    others (so a batch can be built in parallel): size uniform in
+    [wmin, wmax] x [hmin, hmax], absolute tilts of both images uniform in
+    ``tilt_deg``, random longitudes, a 2x canonical texture."""
+    rng = _rng(seed * 100003 + index)
+    W = int(rng.integers(wmin, wmax + 1))
+    H = int(rng.integers(hmin, hmax + 1))
+    a1, a2 = rng.uniform(*tilt_deg, size=2)
+    t1 = 1 / math.cos(math.radians(a1))
+    t2 = 1 / math.cos(math.radians(a2))
+    phi1, phi2 = rng.uniform(0, 180, size=2)
+    tex = texture(2 * H, 2 * W, seed * 1000 + index)
+    zoom = max(1.0, max(t1, t2) / 2.0)
+    A1 = tilt_about_centre(tex.shape, (H, W), t1, phi1, zoom)
+    A2 = tilt_about_centre(tex.shape, (H, W), t2, phi2, zoom)
+    img1 = np.clip(np.rint(render(tex, A1, (H, W), ss=ss)), 0, 255).astype(np.uint8)
+    img2 = np.clip(np.rint(render(tex, A2, (H, W), ss=ss)), 0, 255).astype(np.uint8)
+    return Pair(img1, img2, A2 @ np.linalg.inv(A1), f"mixed_{index}_{W}x{H}")
+
+
 def random_u8(shape, seed: int) -> np.ndarray:
     return _rng(seed).integers(0, 256, size=shape, dtype=np.uint8)
 
