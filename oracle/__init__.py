@@ -49,6 +49,12 @@ class OView(C.Structure):
                 ("cq", C.c_int64), ("sq", C.c_int64), ("tq", C.c_int64)]
 
 
+class ODView(C.Structure):
+    _fields_ = [("W", C.c_int32), ("H", C.c_int32), ("Wr", C.c_int32), ("Hr", C.c_int32),
+                ("Wv", C.c_int32), ("Hv", C.c_int32), ("K", C.c_int32), ("pad", C.c_int32),
+                ("t", C.c_double), ("phi", C.c_double), ("tx", C.c_double), ("ty", C.c_double)]
+
+
 KP_DTYPE = np.dtype([("x", np.int16), ("y", np.int16), ("level", np.uint8), ("bin", np.uint8),
                      ("pad", np.int16), ("r25", np.int64)])
 
@@ -101,6 +107,10 @@ def lib():
         L.oracle_orb_view.restype = C.c_int
         L.oracle_match.argtypes = [u8p, C.c_int, u8p, C.c_int, C.c_int, C.c_int, i32p, i32p, i32p, u8p]
         L.oracle_match.restype = C.c_int
+        L.oracle_sizeof_dview.restype = C.c_int
+        assert L.oracle_sizeof_dview() == C.sizeof(ODView)
+        L.oracle_dwarp_fwd.argtypes = [f64p, P(ODView), f64p]
+        L.oracle_dwarp_vjp.argtypes = [f64p, P(ODView), f64p, f64p, f64p]
         L.oracle_backproject.argtypes = [P(OView), C.c_int, C.c_double, C.c_double,
                                          P(C.c_double), P(C.c_double)]
         _lib = L
@@ -350,3 +360,34 @@ def match_pair(img1: np.ndarray, img2: np.ndarray, kmax: int, L: int, N: int, th
     p2 = image_pool(img2, kmax, L, N, thr, pat)
     m = match(p1.desc, p2.desc, num, den)
     return p1, p2, m
+
+
+# ---------------------------------------------------------------- differentiable warp
+def dview(H: int, W: int, t0: float, phi0: float, K: int, t=None, phi=None, tx=0.0, ty=0.0) -> ODView:
+    """Fixed sizes from (t0, phi0) (as the view table would give them), current
+    parameters (t, phi, tx, ty)."""
+    base = make_view(H, W, t0, phi0)
+    v = ODView()
+    v.W, v.H, v.Wr, v.Hr, v.Wv, v.Hv, v.K = W, H, base.Wr, base.Hr, base.Wv, base.Hv, K
+    v.t = t0 if t is None else t
+    v.phi = phi0 if phi is None else phi
+    v.tx, v.ty = tx, ty
+    return v
+
+
+def dwarp_fwd(u: np.ndarray, v: ODView) -> np.ndarray:
+    """Differentiable warp: clamped Lanczos-3 rotation, Gaussian, tilt (fp64)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.zeros((v.Hv, v.Wv), np.float64)
+    lib().oracle_dwarp_fwd(u, C.byref(v), out)
+    return out
+
+
+def dwarp_vjp(u: np.ndarray, v: ODView, vbar: np.ndarray):
+    """Exact transpose of dwarp_fwd: (ubar, [tbar, phibar, txbar, tybar])."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    vbar = np.ascontiguousarray(vbar, dtype=np.float64)
+    ub = np.zeros_like(u)
+    pb = np.zeros(4, np.float64)
+    lib().oracle_dwarp_vjp(u, C.byref(v), vbar, ub, pb)
+    return ub, pb

@@ -731,3 +731,235 @@ void oracle_backproject(const oracle_view *v, int l, double xl, double yl, doubl
 
 int oracle_sizeof_view(void) { return (int)sizeof(oracle_view); }
 int oracle_sizeof_kp(void) { return (int)sizeof(oracle_kp); }
+
+/* ------------------------------------------------------------------------ */
+/* Differentiable warp (the photometric refinement path) and its exact VJP   */
+/* ------------------------------------------------------------------------ */
+/*
+ * The same chain as oracle_warp_view -- Lanczos-3 rotation (Eq. (3)-(4)),
+ * Gaussian along canvas x, Lanczos-3 tilt -- with continuous parameters
+ * theta = (t, phi, tx, ty) and two changes that make it C^1 in theta:
+ *   - the source point is p = R(phi)^T (q - c_r) + c_s + (tx, ty) in plain
+ *     floating point (the translation T of Eq. (2) acting on the source), and
+ *     every tap is clamped to the image: no zero background;
+ *   - the Gaussian half width K is fixed by the caller (from the largest tilt
+ *     of the run), sigma = 0.8 sqrt(t^2 - 1) varies with t.
+ * Canvas and view sizes are fixed (taken from the initial parameters).
+ * L and L' both vanish at +-3 and the weights are normalised, so the map is
+ * continuously differentiable across the switches of floor(p).
+ */
+typedef struct {
+    int32_t W, H, Wr, Hr, Wv, Hv, K, pad;
+    double t, phi, tx, ty;
+} oracle_dview;
+
+static double dsinc(double x)
+{
+    if (fabs(x) < 1e-4) return -(M_PI * M_PI / 3.0) * x;      /* series: -pi^2 x / 3 + O(x^3) */
+    return (cos(M_PI * x) - sinc(x)) / x;
+}
+
+/* L'(x) for L(x) = sinc(x) sinc(x/3) on |x| < 3 (0 outside; L' -> 0 at +-3). */
+static double lanczos3_deriv(double x)
+{
+    if (!(fabs(x) < 3.0)) return 0.0;
+    return dsinc(x) * sinc(x / 3.0) + sinc(x) * dsinc(x / 3.0) / 3.0;
+}
+
+/* Normalised weights w_m(f) and their derivatives dw_m/df, m = -2..3. */
+static void weights_and_deriv(double f, double w[6], double dw[6])
+{
+    double L[6], dL[6], S = 0.0, dS = 0.0;
+    for (int m = -2; m <= 3; ++m) {
+        L[m + 2] = oracle_lanczos3(f - m);
+        dL[m + 2] = lanczos3_deriv(f - m);
+        S += L[m + 2];
+        dS += dL[m + 2];
+    }
+    for (int i = 0; i < 6; ++i) {
+        w[i] = L[i] / S;
+        dw[i] = (dL[i] - w[i] * dS) / S;
+    }
+}
+
+/* Gaussian taps g_0..g_K at sigma (delta at sigma = 0) and dg_k/dsigma. */
+static void gauss_and_deriv(double sigma, int K, double *g, double *dg)
+{
+    if (sigma <= 0.0) {
+        for (int k = 0; k <= K; ++k) { g[k] = (k == 0); dg[k] = 0.0; }
+        return;
+    }
+    double E = 0.0;
+    for (int k = 0; k <= K; ++k) {
+        g[k] = exp(-(double)k * k / (2.0 * sigma * sigma));
+        E += (k == 0) ? g[k] : 2.0 * g[k];
+    }
+    double m2 = 0.0;
+    for (int k = 0; k <= K; ++k) {
+        g[k] /= E;
+        m2 += (k == 0 ? 0.0 : 2.0 * g[k]) * (double)k * k;   /* sum_j g_j j^2 */
+    }
+    const double s3 = sigma * sigma * sigma;
+    for (int k = 0; k <= K; ++k) dg[k] = g[k] * ((double)k * k - m2) / s3;
+}
+
+static void dview_src(const oracle_dview *v, int i, int j, double c, double s, double *px, double *py)
+{
+    const double dx = i - (v->Wr - 1) * 0.5, dy = j - (v->Hr - 1) * 0.5;
+    *px = c * dx + s * dy + (v->W - 1) * 0.5 + v->tx;
+    *py = -s * dx + c * dy + (v->H - 1) * 0.5 + v->ty;
+}
+
+static double dview_canvas(const double *u, const oracle_dview *v, double px, double py)
+{
+    const int x0 = (int)floor(px), y0 = (int)floor(py);
+    double wx[6], wy[6], d6[6];
+    weights_and_deriv(px - x0, wx, d6);
+    weights_and_deriv(py - y0, wy, d6);
+    double acc = 0.0;
+    for (int n = 0; n < 6; ++n) {
+        const int yy = clampi(y0 + n - 2, 0, v->H - 1);
+        double row = 0.0;
+        for (int m = 0; m < 6; ++m) row += wx[m] * u[(size_t)yy * v->W + clampi(x0 + m - 2, 0, v->W - 1)];
+        acc += wy[n] * row;
+    }
+    return acc;
+}
+
+static double dview_sigma(double t) { return t > 1.0 ? 0.8 * sqrt(t * t - 1.0) : 0.0; }
+
+/* Forward: out (Hv x Wv) = tilt(gauss(rot(u))). */
+void oracle_dwarp_fwd(const double *u, const oracle_dview *v, double *out)
+{
+    const int Wr = v->Wr, Hr = v->Hr, Wv = v->Wv, K = v->K;
+    double g[256], dg[256];
+    gauss_and_deriv(dview_sigma(v->t), K, g, dg);
+    const double r = v->phi * (M_PI / 180.0), c = cos(r), s = sin(r);
+    double *C = (double *)malloc(sizeof(double) * (size_t)Wr);
+    double *B = (double *)malloc(sizeof(double) * (size_t)Wr);
+    for (int j = 0; j < Hr; ++j) {
+        for (int i = 0; i < Wr; ++i) {
+            double px, py;
+            dview_src(v, i, j, c, s, &px, &py);
+            C[i] = dview_canvas(u, v, px, py);
+        }
+        for (int i = 0; i < Wr; ++i) {
+            double acc = 0.0;
+            for (int k = -K; k <= K; ++k) acc += g[abs(k)] * C[clampi(i - k, 0, Wr - 1)];
+            B[i] = acc;
+        }
+        for (int x = 0; x < Wv; ++x) {
+            const double X = v->t * (x - (Wv - 1) * 0.5) + (Wr - 1) * 0.5;
+            const int X0 = (int)floor(X);
+            double w[6], d6[6];
+            weights_and_deriv(X - X0, w, d6);
+            double acc = 0.0;
+            for (int m = 0; m < 6; ++m) acc += w[m] * B[clampi(X0 + m - 2, 0, Wr - 1)];
+            out[(size_t)j * Wv + x] = acc;
+        }
+    }
+    free(C);
+    free(B);
+}
+
+/*
+ * Vector-Jacobian product of oracle_dwarp_fwd: given vbar (Hv x Wv), writes
+ * ubar (H x W) = J_u^T vbar and pbar = (dL/dt, dL/dphi [per degree], dL/dtx,
+ * dL/dty), each step the exact transpose of its forward step (canvas and
+ * blurred canvas recomputed).  dsigma/dt = 0.8 t / sqrt(t^2 - 1) enters only
+ * for t > 1.
+ */
+void oracle_dwarp_vjp(const double *u, const oracle_dview *v, const double *vbar, double *ubar, double pbar[4])
+{
+    const int W = v->W, H = v->H, Wr = v->Wr, Hr = v->Hr, Wv = v->Wv, K = v->K;
+    const double sigma = dview_sigma(v->t);
+    double g[256], dg[256];
+    gauss_and_deriv(sigma, K, g, dg);
+    const double r = v->phi * (M_PI / 180.0), c = cos(r), s = sin(r);
+    double *C = (double *)malloc(sizeof(double) * (size_t)Wr);
+    double *B = (double *)malloc(sizeof(double) * (size_t)Wr);
+    double *Bb = (double *)malloc(sizeof(double) * (size_t)Wr);
+    double *Cb = (double *)malloc(sizeof(double) * (size_t)Wr);
+    memset(ubar, 0, sizeof(double) * (size_t)W * H);
+    double tbar = 0.0, sbar = 0.0, phibar = 0.0, txbar = 0.0, tybar = 0.0;
+    for (int j = 0; j < Hr; ++j) {
+        /* recompute the canvas row and its blur */
+        for (int i = 0; i < Wr; ++i) {
+            double px, py;
+            dview_src(v, i, j, c, s, &px, &py);
+            C[i] = dview_canvas(u, v, px, py);
+        }
+        for (int i = 0; i < Wr; ++i) {
+            double acc = 0.0;
+            for (int k = -K; k <= K; ++k) acc += g[abs(k)] * C[clampi(i - k, 0, Wr - 1)];
+            B[i] = acc;
+        }
+        /* tilt: B-bar and the t-derivative through X */
+        memset(Bb, 0, sizeof(double) * (size_t)Wr);
+        for (int x = 0; x < Wv; ++x) {
+            const double vb = vbar[(size_t)j * Wv + x];
+            const double X = v->t * (x - (Wv - 1) * 0.5) + (Wr - 1) * 0.5;
+            const int X0 = (int)floor(X);
+            double w[6], dw[6];
+            weights_and_deriv(X - X0, w, dw);
+            double dvdX = 0.0;
+            for (int m = 0; m < 6; ++m) {
+                const int i = clampi(X0 + m - 2, 0, Wr - 1);
+                Bb[i] += w[m] * vb;
+                dvdX += dw[m] * B[i];
+            }
+            tbar += vb * dvdX * (x - (Wv - 1) * 0.5);
+        }
+        /* Gaussian: C-bar and the sigma-derivative */
+        memset(Cb, 0, sizeof(double) * (size_t)Wr);
+        for (int i = 0; i < Wr; ++i) {
+            for (int k = -K; k <= K; ++k) {
+                const int ic = clampi(i - k, 0, Wr - 1);
+                Cb[ic] += g[abs(k)] * Bb[i];
+                sbar += Bb[i] * dg[abs(k)] * C[ic];
+            }
+        }
+        /* rotation: u-bar and the derivatives through p */
+        for (int i = 0; i < Wr; ++i) {
+            const double cb = Cb[i];
+            if (cb == 0.0) continue;
+            double px, py;
+            dview_src(v, i, j, c, s, &px, &py);
+            const int x0 = (int)floor(px), y0 = (int)floor(py);
+            double wx[6], dwx[6], wy[6], dwy[6];
+            weights_and_deriv(px - x0, wx, dwx);
+            weights_and_deriv(py - y0, wy, dwy);
+            double dCdx = 0.0, dCdy = 0.0;
+            for (int n = 0; n < 6; ++n) {
+                const int yy = clampi(y0 + n - 2, 0, H - 1);
+                double row = 0.0, drow = 0.0;
+                for (int m = 0; m < 6; ++m) {
+                    const int xx = clampi(x0 + m - 2, 0, W - 1);
+                    const double val = u[(size_t)yy * W + xx];
+                    ubar[(size_t)yy * W + xx] += cb * wx[m] * wy[n];
+                    row += wx[m] * val;
+                    drow += dwx[m] * val;
+                }
+                dCdx += wy[n] * drow;
+                dCdy += dwy[n] * row;
+            }
+            const double dx = i - (Wr - 1) * 0.5, dy = j - (Hr - 1) * 0.5;
+            const double dpx_dphi = (-s * dx + c * dy) * (M_PI / 180.0);
+            const double dpy_dphi = (-c * dx - s * dy) * (M_PI / 180.0);
+            txbar += cb * dCdx;
+            tybar += cb * dCdy;
+            phibar += cb * (dCdx * dpx_dphi + dCdy * dpy_dphi);
+        }
+    }
+    if (v->t > 1.0) tbar += sbar * 0.8 * v->t / sqrt(v->t * v->t - 1.0);
+    pbar[0] = tbar;
+    pbar[1] = phibar;
+    pbar[2] = txbar;
+    pbar[3] = tybar;
+    free(C);
+    free(B);
+    free(Bb);
+    free(Cb);
+}
+
+int oracle_sizeof_dview(void) { return (int)sizeof(oracle_dview); }
