@@ -304,6 +304,36 @@ ASIFT_API asift_status asift_plan_get_tuning(const asift_plan *plan, asift_tunin
 ASIFT_API asift_status asift_plan_autotune(asift_plan *plan, int reps, asift_tuning *out);
 ASIFT_API void asift_plan_destroy(asift_plan *plan);
 
+/*
+ * Differentiable warp (the photometric refinement of a simulated view's
+ * parameters).  n images of H x W fp32 (image i at offset i*H*W of d_u), one
+ * view each, with device parameters d_params[4 i ..] = (t, phi in degrees, tx,
+ * ty) and fixed host shapes (asift_warp_shape_for: the canvas / view sizes of
+ * (t0, phi0) and K = ceil(4 * 0.8 sqrt(t_max^2 - 1))).  The map is Eq. (2)-(4)
+ * with p = R(phi)^T (q - c_r) + c_s + (tx, ty), every Lanczos tap clamped to
+ * the image (no zero background) and sigma = 0.8 sqrt(t^2 - 1) with the fixed
+ * K, so it is continuously differentiable in (u, t, phi, tx, ty).
+ * asift_warp_fwd writes view i at element offset h_voff[i] of d_v (pitch Wv).
+ * asift_warp_bwd takes the output gradient d_vbar (same layout) and writes the
+ * image gradient d_ubar (n x H x W, overwritten) and d_pbar[4 i ..] =
+ * dL/d(t, phi [per degree], tx, ty) (overwritten); the canvas and its blur are
+ * recomputed, nothing is kept from the forward.  A t above t_max sets the
+ * status word to ASIFT_ERR_CAPACITY.  Workspace: asift_warp_workspace_size(n).
+ */
+typedef struct {
+    int32_t Wr, Hr, Wv, Hv, K, pad;
+} asift_warp_shape;
+ASIFT_API asift_status asift_warp_shape_for(int H, int W, double t0, double phi0, double t_max,
+                                            asift_warp_shape *out);
+ASIFT_API size_t asift_warp_workspace_size(int n);
+ASIFT_API asift_status asift_warp_fwd(asift_ctx *ctx, const float *d_u, int H, int W, int n, const double *d_params,
+                                      const asift_warp_shape *h_shapes, double t_max, float *d_v,
+                                      const int64_t *h_voff, void *d_workspace, size_t ws_bytes, void *stream);
+ASIFT_API asift_status asift_warp_bwd(asift_ctx *ctx, const float *d_u, int H, int W, int n, const double *d_params,
+                                      const asift_warp_shape *h_shapes, double t_max, const float *d_vbar,
+                                      const int64_t *h_voff, float *d_ubar, double *d_pbar, void *d_workspace,
+                                      size_t ws_bytes, void *stream);
+
 /* Debug view into match_pair's workspace after a call: device pointers to the
  * pooled keypoints / descriptors / per-query matches of each image and the
  * host view tables used.  Any output pointer may be NULL. */

@@ -29,7 +29,8 @@ EXPORTED = ["asift_ctx_create", "asift_ctx_destroy", "asift_ctx_orb_cfg", "asift
             "asift_launch_count", "asift_pattern_table", "asift_bin_table", "asift_profile_enable",
             "asift_profile_read", "hamming_match_noalloc", "asift_plan_create", "asift_plan_run",
             "asift_plan_pairs", "asift_plan_workspace", "asift_plan_set_tuning", "asift_plan_get_tuning",
-            "asift_plan_autotune", "asift_plan_destroy"]
+            "asift_plan_autotune", "asift_plan_destroy", "asift_warp_shape_for", "asift_warp_workspace_size",
+            "asift_warp_fwd", "asift_warp_bwd"]
 PROF_STAGES = ["upload", "warp", "pyramid", "detect", "select", "orient_brief", "match", "pairs"]
 
 
@@ -68,6 +69,11 @@ class Tuning(C.Structure):
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+class WarpShape(C.Structure):
+    _fields_ = [("Wr", C.c_int32), ("Hr", C.c_int32), ("Wv", C.c_int32), ("Hv", C.c_int32),
+                ("K", C.c_int32), ("pad", C.c_int32)]
 
 
 KP_DTYPE = np.dtype([("x", np.int16), ("y", np.int16), ("level", np.uint8), ("bin", np.uint8),
@@ -123,6 +129,10 @@ def load_library():
         "asift_plan_get_tuning": (i32, [vp, P(Tuning)]),
         "asift_plan_autotune": (i32, [vp, i32, P(Tuning)]),
         "asift_plan_destroy": (None, [vp]),
+        "asift_warp_shape_for": (i32, [i32, i32, C.c_double, C.c_double, C.c_double, P(WarpShape)]),
+        "asift_warp_workspace_size": (sz, [i32]),
+        "asift_warp_fwd": (i32, [vp, vp, i32, i32, i32, vp, vp, C.c_double, vp, vp, vp, sz, vp]),
+        "asift_warp_bwd": (i32, [vp, vp, i32, i32, i32, vp, vp, C.c_double, vp, vp, vp, vp, vp, sz, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -490,3 +500,116 @@ class _DevPtr:
 def device_view(ptr: int, shape, typestr: str) -> torch.Tensor:
     torch.cuda.synchronize()
     return torch.as_tensor(_DevPtr(ptr, shape, typestr), device="cuda")
+
+
+# ---------------------------------------------------------------- differentiable warp
+@dataclass
+class WarpLayout:
+    """Fixed sizes of n differentiable views (from their initial parameters)."""
+    shapes: object          # ctypes array of WarpShape
+    voff: np.ndarray        # int64 element offsets of each view in the flat output
+    total: int
+    t_max: float
+    H: int
+    W: int
+
+    def view(self, flat: torch.Tensor, i: int) -> torch.Tensor:
+        s = self.shapes[i]
+        o = int(self.voff[i])
+        return flat[o:o + s.Wv * s.Hv].view(s.Hv, s.Wv)
+
+
+def warp_layout(H: int, W: int, t0, phi0, t_max: float) -> WarpLayout:
+    n = len(t0)
+    arr = (WarpShape * n)()
+    L = load_library()
+    for i in range(n):
+        _check("asift_warp_shape_for", L.asift_warp_shape_for(H, W, float(t0[i]), float(phi0[i]), float(t_max),
+                                                              C.byref(arr[i])))
+    sizes = np.array([arr[i].Wv * arr[i].Hv for i in range(n)], np.int64)
+    voff = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+    return WarpLayout(arr, voff, int(sizes.sum()), float(t_max), H, W)
+
+
+def warp_forward(ctx: Context, u: torch.Tensor, params: torch.Tensor, lay: WarpLayout) -> torch.Tensor:
+    """u: (n, H, W) fp32 CUDA; params: (n, 4) fp64 CUDA (t, phi deg, tx, ty) -> flat views."""
+    n = u.shape[0]
+    u = u.contiguous()
+    params = params.contiguous()
+    out = torch.empty(max(lay.total, 1), dtype=torch.float32, device=u.device)
+    ws = ctx.workspace("warp", ctx.L.asift_warp_workspace_size(n))
+    _check("asift_warp_fwd", ctx.L.asift_warp_fwd(ctx._ctx, _ptr(u), lay.H, lay.W, n, _ptr(params), lay.shapes,
+                                                  lay.t_max, _ptr(out), lay.voff.ctypes.data_as(C.c_void_p),
+                                                  _ptr(ws), ws.numel(), _stream()))
+    return out
+
+
+def warp_backward(ctx: Context, u: torch.Tensor, params: torch.Tensor, lay: WarpLayout, vbar: torch.Tensor):
+    n = u.shape[0]
+    u = u.contiguous()
+    params = params.contiguous()
+    vbar = vbar.contiguous().to(torch.float32)
+    ubar = torch.empty_like(u)
+    pbar = torch.empty((n, 4), dtype=torch.float64, device=u.device)
+    ws = ctx.workspace("warp_bwd", ctx.L.asift_warp_workspace_size(n))
+    _check("asift_warp_bwd", ctx.L.asift_warp_bwd(ctx._ctx, _ptr(u), lay.H, lay.W, n, _ptr(params), lay.shapes,
+                                                  lay.t_max, _ptr(vbar), lay.voff.ctypes.data_as(C.c_void_p),
+                                                  _ptr(ubar), _ptr(pbar), _ptr(ws), ws.numel(), _stream()))
+    return ubar, pbar
+
+
+class WarpFunction(torch.autograd.Function):
+    """Differentiable Gaussian + Lanczos-3 view warp; the backward is the
+    library's hand-written adjoint (canvas and blur recomputed)."""
+
+    @staticmethod
+    def forward(fctx, u, params, ctx: Context, lay: WarpLayout):
+        fctx.save_for_backward(u, params)
+        fctx.lib_ctx = ctx
+        fctx.lay = lay
+        return warp_forward(ctx, u, params, lay)
+
+    @staticmethod
+    def backward(fctx, vbar):
+        u, params = fctx.saved_tensors
+        ubar, pbar = warp_backward(fctx.lib_ctx, u, params, fctx.lay, vbar)
+        return (ubar if fctx.needs_input_grad[0] else None,
+                pbar if fctx.needs_input_grad[1] else None, None, None)
+
+
+def refine(ctx: Context, u: torch.Tensor, target: torch.Tensor, lay: WarpLayout, theta0: torch.Tensor,
+           steps: int = 20, lr=(0.1, 2.0, 1.0, 1.0), decay: float = 0.88, t_range=(1.0, None)):
+    """Photometric descent of the view parameters: Adam (step sizes lr for
+    t, phi in degrees, tx, ty, decayed by `decay` per step) on the mean squared
+    difference between warp(u, theta) and the target views (one loss per view,
+    summed).  Returns (theta history [steps+1, n, 4], loss history [steps+1, n])."""
+    theta = theta0.clone().to(torch.float64).requires_grad_(True)
+    lrs = torch.tensor(lr, dtype=torch.float64, device=theta.device)
+    m = torch.zeros_like(theta)
+    v = torch.zeros_like(theta)
+    b1, b2, eps = 0.9, 0.999, 1e-12
+    hist, losses = [theta.detach().clone()], []
+    tmax = lay.t_max if t_range[1] is None else t_range[1]
+    sizes = [lay.shapes[i].Wv * lay.shapes[i].Hv for i in range(len(lay.voff))]
+    seg = torch.repeat_interleave(torch.arange(len(sizes), device=u.device),
+                                  torch.tensor(sizes, device=u.device))
+    for k in range(steps + 1):
+        out = WarpFunction.apply(u, theta, ctx, lay)
+        d2 = (out[: lay.total] - target[: lay.total]) ** 2
+        per_view = torch.zeros(len(sizes), dtype=torch.float64, device=u.device).index_add_(0, seg, d2.double())
+        per_view = per_view / torch.tensor(sizes, dtype=torch.float64, device=u.device)
+        losses.append(per_view.detach().clone())
+        if k == steps:
+            break
+        g, = torch.autograd.grad(per_view.sum(), theta)
+        with torch.no_grad():
+            # a view whose gradient is not finite keeps its parameters this step
+            g = torch.where(torch.isfinite(g).all(1, keepdim=True), g, torch.zeros_like(g))
+            m.mul_(b1).add_(g, alpha=1 - b1)
+            v.mul_(b2).addcmul_(g, g, value=1 - b2)
+            mh = m / (1 - b1 ** (k + 1))
+            vh = v / (1 - b2 ** (k + 1))
+            theta -= (decay ** k) * lrs * mh / (vh.sqrt() + eps)
+            theta[:, 0].clamp_(t_range[0], tmax)
+        hist.append(theta.detach().clone())
+    return torch.stack(hist), torch.stack(losses)

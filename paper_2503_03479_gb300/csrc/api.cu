@@ -1111,3 +1111,97 @@ asift_status asift_plan_autotune(asift_plan *plan, int reps, asift_tuning *out)
 void asift_plan_destroy(asift_plan *plan) { plan_free(plan); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- differentiable warp
+extern "C" {
+
+asift_status asift_warp_shape_for(int H, int W, double t0, double phi0, double t_max, asift_warp_shape *out)
+{
+    if (H < 1 || W < 1 || H > 16384 || W > 16384 || !(t0 >= 1.0 && t0 < 11.4) || !(t_max >= t0 && t_max < 11.4) ||
+        !out || !(phi0 == phi0))
+        return ASIFT_ERR_ARG;
+    asift_view_desc v;
+    make_view_desc(H, W, t0, phi0, -1, -1, &v);
+    out->Wr = v.Wr;
+    out->Hr = v.Hr;
+    out->Wv = v.Wv;
+    out->Hv = v.Hv;
+    out->K = (int32_t)std::ceil(4.0 * (t_max > 1.0 ? 0.8 * std::sqrt(t_max * t_max - 1.0) : 0.0));
+    out->pad = 0;
+    if (out->K >= ASIFT_MAX_GAUSS) return ASIFT_ERR_ARG;
+    return ASIFT_OK;
+}
+
+size_t asift_warp_workspace_size(int n)
+{
+    Bump b(nullptr);
+    b.take<int32_t>(64);
+    b.take<DiffView>(std::max(n, 1));
+    return b.off + 256;
+}
+
+static asift_status warp_call(bool backward, asift_ctx *ctx, const float *d_u, int H, int W, int n,
+                              const double *d_params, const asift_warp_shape *h_shapes, double t_max,
+                              float *d_v, const float *d_vbar, const int64_t *h_voff, float *d_ubar, double *d_pbar,
+                              void *d_ws, size_t ws_bytes, void *stream)
+{
+    if (!ctx || !d_u || H < 1 || W < 1 || n < 1 || !d_params || !h_shapes || !h_voff || !d_ws ||
+        !(t_max >= 1.0 && t_max < 11.4) || (!backward && !d_v) || (backward && (!d_vbar || !d_ubar || !d_pbar)))
+        return ASIFT_ERR_ARG;
+    if (ws_bytes < asift_warp_workspace_size(n)) return ASIFT_ERR_ARG;
+    Bump b(d_ws);
+    int32_t *status = b.take<int32_t>(64);
+    DiffView *tab = b.take<DiffView>(n);
+    std::vector<DiffView> h(n);
+    int tiles = 0, cw_max = 1, bw_max = 1;
+    for (int i = 0; i < n; ++i) {
+        const asift_warp_shape &S = h_shapes[i];
+        if (S.Wr < 1 || S.Hr < 1 || S.Wv < 1 || S.Hv < 1 || S.K < 0 || S.K >= ASIFT_MAX_GAUSS || h_voff[i] < 0)
+            return ASIFT_ERR_ARG;
+        DiffView &d = h[i];
+        d = DiffView{};
+        d.u = d_u + (size_t)i * H * W;
+        d.ubar = backward ? d_ubar + (size_t)i * H * W : nullptr;
+        d.vbar = backward ? d_vbar + h_voff[i] : nullptr;
+        d.out = backward ? nullptr : d_v + h_voff[i];
+        d.param = d_params + 4 * (size_t)i;
+        d.pbar = backward ? d_pbar + 4 * (size_t)i : nullptr;
+        d.W = W;
+        d.H = H;
+        d.Wr = S.Wr;
+        d.Hr = S.Hr;
+        d.Wv = S.Wv;
+        d.Hv = S.Hv;
+        d.K = S.K;
+        d.tile_start = tiles;
+        tiles += dwarp_tiles(S.Wv, S.Hv, &d.ntx);
+        int cw, bw;
+        dwarp_strip_widths(S.Wv, t_max, S.K, &cw, &bw);
+        cw_max = std::max(cw_max, cw);
+        bw_max = std::max(bw_max, bw);
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = upload(ctx, tab, h.data(), sizeof(DiffView) * n, s);
+    if (e == cudaSuccess && backward) e = cudaMemsetAsync(d_ubar, 0, sizeof(float) * (size_t)n * H * W, s);
+    if (e == cudaSuccess && backward) e = cudaMemsetAsync(d_pbar, 0, sizeof(double) * 4 * (size_t)n, s);
+    if (e == cudaSuccess) e = launch_dwarp(backward, tab, n, tiles, cw_max, bw_max, status, s);
+    return cuda_status(e);
+}
+
+asift_status asift_warp_fwd(asift_ctx *ctx, const float *d_u, int H, int W, int n, const double *d_params,
+                            const asift_warp_shape *h_shapes, double t_max, float *d_v, const int64_t *h_voff,
+                            void *d_workspace, size_t ws_bytes, void *stream)
+{
+    return warp_call(false, ctx, d_u, H, W, n, d_params, h_shapes, t_max, d_v, nullptr, h_voff, nullptr, nullptr,
+                     d_workspace, ws_bytes, stream);
+}
+
+asift_status asift_warp_bwd(asift_ctx *ctx, const float *d_u, int H, int W, int n, const double *d_params,
+                            const asift_warp_shape *h_shapes, double t_max, const float *d_vbar, const int64_t *h_voff,
+                            float *d_ubar, double *d_pbar, void *d_workspace, size_t ws_bytes, void *stream)
+{
+    return warp_call(true, ctx, d_u, H, W, n, d_params, h_shapes, t_max, nullptr, d_vbar, h_voff, d_ubar, d_pbar,
+                     d_workspace, ws_bytes, stream);
+}
+
+}  // extern "C"

@@ -71,6 +71,18 @@ struct SlotKp {             // a selected keypoint before orientation / descript
 constexpr int kDetTW = 64, kDetTH = 16;   // FAST tile
 constexpr int kPyrTW = 64, kPyrTH = 16;   // pyramid tile (4 px per thread across x)
 
+// ---------------------------------------------------------------- differentiable warp
+// One view of the differentiable path (image i -> view i).
+struct DiffView {
+    const float *u;          // source image (pitch W)
+    float *ubar;             // its gradient (backward)
+    const float *vbar;       // output gradient (backward)
+    float *out;              // view (forward)
+    const double *param;     // t, phi (deg), tx, ty
+    double *pbar;            // dL/d(t, phi, tx, ty) (backward)
+    int32_t W, H, Wr, Hr, Wv, Hv, K, tile_start, ntx, pad;
+};
+
 // ---------------------------------------------------------------- matching
 // One brute-force matching problem (query pool vs train pool of one pair),
 // with where its results and, for match_pair, its accepted pairs go.

@@ -59,6 +59,13 @@ cudaError_t launch_hamming_noalloc(const uint8_t *q, int nq, const int32_t *d_nq
 cudaError_t launch_pairs(const MatchProblem *d_probs, int n_probs, const MatchProblem &single, int total_blk,
                          int32_t *block_count, const DevView *views, int32_t *status, cudaStream_t s);
 
+// dwarp.cu
+struct DiffView;
+void dwarp_strip_widths(int Wv, double t_max, int K, int *cw, int *bw);
+int dwarp_tiles(int Wv, int Hv, int *ntx);
+cudaError_t launch_dwarp(bool backward, const DiffView *d_views, int n_views, int n_tiles, int cw_max, int bw_max,
+                         int32_t *status, cudaStream_t s);
+
 // tables.cpp (host; each table generated from its written definition)
 void make_view_desc(int H, int W, double t, double phi_deg, int k, int j, asift_view_desc *v);
 int view_table(int H, int W, int kmax, asift_view_desc *out, int cap);
