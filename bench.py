@@ -344,6 +344,36 @@ def run_ours(args):
                    "plan_create_s": t_plan, "autotune_s": t_tune, "generate_s": t_gen}
         del b1, b2
 
+    # ---- differentiable warp: 256 views of 512x512 fp32 images, forward + backward
+    diff = None
+    if args.diff_views > 0:
+        from paper_2503_03479_gb300 import synth
+        nd, HD = args.diff_views, 512
+        gen = np.random.default_rng(4)
+        base = [synth.texture(HD, HD, 4000 + i % 16).astype(np.float32) / 255.0 for i in range(min(nd, 16))]
+        ud = torch.from_numpy(np.stack([base[i % len(base)] for i in range(nd)])).cuda()
+        ts = gen.uniform(1.05, 5.7, nd)
+        ph = gen.uniform(0, 180, nd)
+        grid_t = np.sqrt(2.0) ** np.round(np.log(ts) / np.log(np.sqrt(2.0)))
+        lay = A.warp_layout(HD, HD, grid_t, ph, 5.7)
+        th = torch.from_numpy(np.stack([ts, ph, gen.uniform(-8, 8, nd), gen.uniform(-8, 8, nd)], 1)).cuda()
+        vb = torch.randn(lay.total, device="cuda", generator=torch.Generator(device="cuda").manual_seed(1))
+        for _ in range(2):
+            A.warp_forward(ctx, ud, th, lay)
+            A.warp_backward(ctx, ud, th, lay, vb)
+        torch.cuda.synchronize()
+        ef = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ef[0].record(stream)
+        A.warp_forward(ctx, ud, th, lay)
+        ef[1].record(stream)
+        A.warp_backward(ctx, ud, th, lay, vb)
+        ef[2].record(stream)
+        torch.cuda.synchronize()
+        fms, bms = ef[0].elapsed_time(ef[1]), ef[1].elapsed_time(ef[2])
+        diff = {"views": nd, "image": f"{HD}x{HD} fp32", "fwd_ms": fms, "bwd_ms": bms,
+                "views_per_s_fwd_bwd": nd / ((fms + bms) / 1e3)}
+        del ud
+
     # ---- end to end through the C ABI with host buffers
     h1 = [torch.from_numpy(p.img1).pin_memory() for p in pairs]
     h2 = [torch.from_numpy(p.img2).pin_memory() for p in pairs]
@@ -383,6 +413,7 @@ def run_ours(args):
                 "plain_per_view": plain,
                 "batched_vs_plain": (value / world) / plain["value"] if plain else None,
                 "batched_mixed": batched,
+                "differentiable": diff,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
@@ -401,6 +432,7 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-pairs", type=int, default=64, help="pairs in the mixed-size batched run (0: skip)")
+    ap.add_argument("--diff-views", type=int, default=256, help="views of the differentiable-warp timing (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -145,8 +145,14 @@ __device__ void gauss_taps(float sigma, int K, float *g, float *dg)
     __syncthreads();
 }
 
+// A view tile's strips.  B is needed at strip positions bx0..bx1 (the tilt
+// taps, unclamped: position i holds B(clamp(i))); C is needed at the actual
+// canvas columns clo..chi that the clamped Gaussian taps of those B values
+// reach.  When t has grown past the t the sizes were fixed for, a tile's
+// positions can all lie beyond the canvas; indexing C by clamped columns keeps
+// every shared-memory access inside the strip.
 struct DTile {
-    int v, xa, xb, j0, j1, bx0, bx1, cx0, cw, bw;
+    int v, xa, xb, j0, j1, bx0, bx1, clo, chi, cw, bw;
     float t, crv;
 };
 
@@ -167,8 +173,9 @@ __device__ __forceinline__ DTile dtile(const DiffView *views, int n_views, int t
     T.bx0 = (int)floorf(T.t * ((float)T.xa - T.crv) + cr) - 2;
     T.bx1 = (int)floorf(T.t * ((float)T.xb - T.crv) + cr) + 3;
     T.bw = T.bx1 - T.bx0 + 1;
-    T.cx0 = T.bx0 - V.K;
-    T.cw = T.bw + 2 * V.K;
+    T.clo = max(0, clampi(T.bx0, 0, V.Wr - 1) - V.K);
+    T.chi = min(V.Wr - 1, clampi(T.bx1, 0, V.Wr - 1) + V.K);
+    T.cw = T.chi - T.clo + 1;
     return T;
 }
 
@@ -187,26 +194,26 @@ __device__ __forceinline__ DGeom dgeom(const DiffView &V)
     return G;
 }
 
-// Recomputes the canvas strip C (columns cx0.., value of clamp(i)) and its
-// blur B (columns bx0..) of a tile in shared memory.
+// Recomputes the canvas strip C (actual columns clo..chi) and its blur B
+// (strip positions bx0.., value of column clamp(i)) of a tile in shared memory.
 __device__ void strips(const DiffView &V, const DTile &T, const DGeom &G, const float *g, float *Cs, float *Bs,
                        int cw_max, int bw_max)
 {
     const int nrows = T.j1 - T.j0 + 1;
     for (int e = threadIdx.x; e < nrows * T.cw; e += blockDim.x) {
         const int r = e / T.cw, c = e - r * T.cw;
-        const int i = clampi(T.cx0 + c, 0, V.Wr - 1);
         float px, py;
-        G.map(i, T.j0 + r, px, py);
+        G.map(T.clo + c, T.j0 + r, px, py);
         Cs[r * cw_max + c] = canvas_at(V.u, V.W, V.H, px, py, nullptr, nullptr, 0.f, nullptr);
     }
     __syncthreads();
+    const int last = V.Wr - 1;
     for (int e = threadIdx.x; e < nrows * T.bw; e += blockDim.x) {
         const int r = e / T.bw, c = e - r * T.bw;
-        const int ic = clampi(T.bx0 + c, 0, V.Wr - 1);
-        const float *Crow = Cs + r * cw_max - T.cx0;
+        const int ic = clampi(T.bx0 + c, 0, last);
+        const float *Crow = Cs + r * cw_max - T.clo;
         float acc = g[0] * Crow[ic];
-        for (int k = 1; k <= V.K; ++k) acc = fmaf(g[k], Crow[ic - k] + Crow[ic + k], acc);
+        for (int k = 1; k <= V.K; ++k) acc = fmaf(g[k], Crow[max(ic - k, 0)] + Crow[min(ic + k, last)], acc);
         Bs[r * bw_max + c] = acc;
     }
     __syncthreads();
@@ -297,8 +304,8 @@ dwarp_bwd_kernel(const DiffView *__restrict__ views, int n_views, int cw_max, in
 #pragma unroll
         for (int m = 0; m < 6; ++m) {
             // strip position X0+m-2 holds column clamp(X0+m-2): the clamped
-            // taps of the forward accumulate on the strip's replicated ends,
-            // which the next step folds back onto the canvas border
+            // taps of the forward accumulate at their strip positions, which
+            // the next step maps onto canvas columns
             atomicAdd(Bbrow + X0 + m - 2, w[m] * vb);
             dvdX = fmaf(dw[m], Brow[X0 + m - 2], dvdX);
         }
@@ -313,8 +320,8 @@ dwarp_bwd_kernel(const DiffView *__restrict__ views, int n_views, int cw_max, in
         const float b = Bb[r * bw_max + c];
         if (b == 0.f) continue;
         const int ic = clampi(T.bx0 + c, 0, V.Wr - 1);
-        const float *Crow = Cs + r * cw_max - T.cx0;
-        float *Cbrow = Cb + r * cw_max - T.cx0;
+        const float *Crow = Cs + r * cw_max - T.clo;
+        float *Cbrow = Cb + r * cw_max - T.clo;
         atomicAdd(Cbrow + ic, g[0] * b);
         float ds = dg[0] * Crow[ic];
         for (int k = 1; k <= V.K; ++k) {
@@ -332,8 +339,7 @@ dwarp_bwd_kernel(const DiffView *__restrict__ views, int n_views, int cw_max, in
     const float dg2r = 0.017453292519943295f;
     for (int e = threadIdx.x; e < nrows * T.cw; e += blockDim.x) {
         const int r = e / T.cw, c = e - r * T.cw;
-        const int i = T.cx0 + c;
-        if (i < 0 || i >= V.Wr) continue;      // replicated ends were folded onto the border
+        const int i = T.clo + c;
         const float cb = Cb[r * cw_max + c];
         if (cb == 0.f) continue;
         const int j = T.j0 + r;

@@ -40,6 +40,9 @@ CASES = [  # (t0, phi0) of the fixed shape, then (t, phi, tx, ty)
     ((2.0, 36.0), (2.1037, 33.3, 0.71, -0.43)),
     ((2.8284271247461903, 127.28), (2.91, 131.6, -3.2, 5.1)),
     ((5.656854249492381, 89.1), (5.44, 92.0, 7.5, -6.3)),
+    # t far above the t the sizes were fixed for: whole view tiles map beyond
+    # the canvas and read only its clamped last column
+    ((1.4142135623730951, 101.8), (3.1, 101.8, 0.4, 0.0)),
 ]
 
 
