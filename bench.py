@@ -13,8 +13,9 @@ the pooled descriptors with ratio 4/5.  Every rank processes its own pairs
 The JSON line reports image pairs/s (views/s = 86 x pairs/s beside it), with
 inputs resident in HBM; `e2e` is the same metric through the C ABI with the
 images copied from pinned host memory and the accepted pairs copied back inside
-the timed region.  `roofline` is for the dominant kernel (the Hamming matcher,
-integer popc bound); `cpu_baseline` is the CPU oracle timed on a bounded
+the timed region.  `roofline` is for the stage that takes longest (the view
+simulation: FP32 arithmetic bound), `rooflines` for it and the matcher
+(tensor cores, fp8 dense peak); `cpu_baseline` is the CPU oracle timed on a bounded
 sample of the same workload.  `--impl reference` times the CPU oracle as the
 reference arm.
 """
@@ -128,6 +129,56 @@ def _peaks():
             return json.load(f)
     except (OSError, ValueError):
         return {}
+
+
+# ---------------------------------------------------------------- rooflines
+FP32_LANES_PER_SM = 128    # FP32 FMA lanes per SM (one FMA = 2 flops)
+FP8_PER_BF16 = 2.0         # nominal dense fp8 / bf16 tensor rate (4.5 / 2.25 PFLOP/s)
+
+
+def warp_flops(v) -> float:
+    """Algorithmic flops of one simulated view (Eq. (2)-(4)), multiply-add = 2:
+    the 6 x 6 Lanczos-3 interpolation of the rotation at every canvas pixel
+    (when phi != 0), the (2K+1)-tap Gaussian along the tilt axis at every canvas
+    pixel and the 6-tap Lanczos-3 resampling of the tilt at every view pixel
+    (both when t > 1).  Weight evaluation, staging and the mask are not counted."""
+    canvas = v.Wr * v.Hr
+    f = 0.0
+    if v.phi_deg != 0.0:
+        f += 36 * canvas
+    if v.t > 1.0:
+        f += (2 * v.K + 1) * canvas + 6 * v.Wv * v.Hv
+    return 2.0 * f
+
+
+def warp_roofline(views, n_images: int, ms: float, peaks: dict) -> dict:
+    f_clk = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * f_clk / 1e12
+    flops = n_images * sum(warp_flops(v) for v in views)
+    achieved = flops / (ms / 1e3) / 1e12
+    return {"bound": "alu", "kernel": "warp_view_kernel (+ convert_images_kernel)", "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "flops_per_launch": flops,
+            "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 FMA/clk x 2 x {f_clk/1e6:.0f} MHz"}
+
+
+def match_roofline(n1: int, n2: int, ms: float, tensor: bool, peaks: dict) -> dict:
+    if tensor:
+        bf16 = peaks.get("bf16_tflops")
+        peak = (bf16 or 1900.0) * FP8_PER_BF16
+        flops = 2.0 * 256 * n1 * n2                  # one +-1 dot product of length 256 per pair
+        achieved = flops / (ms / 1e3) / 1e12
+        src = (f"fp8 = measured bf16 {bf16} TFLOP/s x nominal fp8/bf16 ratio {FP8_PER_BF16}" if bf16 else
+               f"fp8 = fallback bf16 1900 TFLOP/s x nominal ratio {FP8_PER_BF16}")
+        return {"bound": "tensor", "kernel": "hamming_tc_kernel (+ expand_pm1_kernel, merge_kernel)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "flops_per_launch": flops, "peak_source": src}
+    f_clk = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
+    peak = SM_COUNT * POPC_PER_SM_CLK * f_clk / 1e12
+    achieved = n1 * n2 * POPC_PER_PAIR / (ms / 1e3) / 1e12
+    return {"bound": "alu", "kernel": "hamming_top2_kernel (+ merge_kernel)", "achieved": achieved,
+            "peak": peak, "unit": "Tpopc/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": f"derived: {SM_COUNT} SMs x {POPC_PER_SM_CLK} popc/clk x {f_clk/1e6:.0f} MHz"}
 
 
 # ---------------------------------------------------------------- CPU oracle sample
@@ -261,19 +312,18 @@ def run_ours(args):
         t_max = float(t.item())
     value = world * args.steps / (t_max / 1e3)
 
-    # ---- dominant kernel: the Hamming matcher, timed live by the stage events
+    # ---- rooflines of the two heaviest stages, timed live by the stage events
     st = {k: statistics.mean(s[k] for s in stage_ms) for k in stage_ms[0]}
     n_acc = int(n_out.item())
     kp1, dd1, kp2, dd2, _ = ctx.inspect_pair((H, W), (H, W), pc, ws)
     n1, n2 = len(kp1), len(kp2)
     peaks = _peaks()
     clocks = clk.summary()
-    f_clk = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
-    peak_popc = SM_COUNT * POPC_PER_SM_CLK * f_clk / 1e12          # T popc / s
-    achieved = n1 * n2 * POPC_PER_PAIR / (st["match"] / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": "hamming_top2_kernel+merge_kernel", "achieved": achieved,
-                "peak": peak_popc, "unit": "Tpopc/s", "frac": achieved / peak_popc, "traffic": None,
-                "peak_source": f"derived: {SM_COUNT} SMs x {POPC_PER_SM_CLK} popc/clk x {f_clk/1e6:.0f} MHz"}
+    views = A.view_table(H, W, KMAX)
+    rooflines = {"warp": warp_roofline(views, 2, st["warp"], peaks),
+                 "match": match_roofline(n1, n2, st["match"], ctx.match_engine == A.MATCH_TENSOR_CORES, peaks)}
+    dominant = max(rooflines, key=lambda k: st[k])
+    roofline = dict(rooflines[dominant], stage=dominant)
 
     # ---- plain per-view form (same kernels, one launch per view and stage)
     plain = None
@@ -414,7 +464,8 @@ def run_ours(args):
                 "batched_vs_plain": (value / world) / plain["value"] if plain else None,
                 "batched_mixed": batched,
                 "differentiable": diff,
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "roofline": roofline, "rooflines": rooflines, "match_engine": ctx.match_engine,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     if dist:

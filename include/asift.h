@@ -199,9 +199,32 @@ ASIFT_API asift_status orb_extract(asift_ctx *ctx, const uint8_t *d_view_u8, con
  * be NULL); *d_n_accepted (int32, may be NULL).
  * nq and nt may come from the device: if d_nq / d_nt are non-NULL they hold
  * the counts (int32) and nq / nt are only capacities.
- * Workspace: hamming_workspace_size(nq, nt).
+ * Workspace: hamming_workspace_size(nq, nt), 256-byte aligned; its first
+ * int32 is the status word (cleared by the call, read with asift_read_status).
  */
 ASIFT_API size_t hamming_workspace_size(int nq, int nt);
+/*
+ * Matcher engines (the same results bit for bit; the choice is speed only).
+ * ASIFT_MATCH_CUDA_CORES: each thread scans train descriptors with XOR and
+ * population counts.  ASIFT_MATCH_TENSOR_CORES: descriptors are expanded to
+ * +-1 (fp8 e4m3: +1 for a 0 bit, -1 for a 1 bit) so that the dot product is
+ * 256 - 2 x Hamming distance exactly, the dot products of all query / train
+ * pairs are computed as a matrix product on the tensor cores (tcgen05, fp32
+ * accumulators in tensor memory) and the nearest and second-nearest are
+ * selected from the accumulators.  ASIFT_MATCH_AUTO (the default): tensor
+ * cores when the device has them (compute capability 10.x), else CUDA cores.
+ * asift_ctx_set_match_engine sets the engine of hamming_match and match_pair
+ * on this context (ASIFT_ERR_ARG for an unknown value); asking for tensor
+ * cores on a device without them makes those calls return ASIFT_ERR_CUDA.
+ * asift_ctx_match_engine returns the engine a call would use now (1 or 2).
+ * A tensor-core launch that waits more than 4 s on one of its own pipeline
+ * stages gives up and records ASIFT_ERR_TIMEOUT in the workspace status word.
+ */
+#define ASIFT_MATCH_AUTO 0
+#define ASIFT_MATCH_CUDA_CORES 1
+#define ASIFT_MATCH_TENSOR_CORES 2
+ASIFT_API asift_status asift_ctx_set_match_engine(asift_ctx *ctx, int engine);
+ASIFT_API int asift_ctx_match_engine(const asift_ctx *ctx);
 ASIFT_API asift_status hamming_match(asift_ctx *ctx, const uint8_t *d_q, int nq, const int32_t *d_nq,
                            const uint8_t *d_t, int nt, const int32_t *d_nt,
                            int ratio_num, int ratio_den, asift_match *d_out, uint8_t *d_accept,
@@ -283,6 +306,7 @@ typedef struct {
  * A positive grid makes the stage's kernel persistent over its tile list. */
 typedef struct {
     int32_t warp_grid, pyramid_grid, detect_grid, match_grid, match_target_items;
+    int32_t match_engine;   /* ASIFT_MATCH_*; ASIFT_MATCH_AUTO = the context's engine */
 } asift_tuning;
 
 typedef struct asift_plan asift_plan;

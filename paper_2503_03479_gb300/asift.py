@@ -30,7 +30,8 @@ EXPORTED = ["asift_ctx_create", "asift_ctx_destroy", "asift_ctx_orb_cfg", "asift
             "asift_profile_read", "hamming_match_noalloc", "asift_plan_create", "asift_plan_run",
             "asift_plan_pairs", "asift_plan_workspace", "asift_plan_set_tuning", "asift_plan_get_tuning",
             "asift_plan_autotune", "asift_plan_destroy", "asift_warp_shape_for", "asift_warp_workspace_size",
-            "asift_warp_fwd", "asift_warp_bwd"]
+            "asift_warp_fwd", "asift_warp_bwd", "asift_ctx_set_match_engine", "asift_ctx_match_engine"]
+MATCH_AUTO, MATCH_CUDA_CORES, MATCH_TENSOR_CORES = 0, 1, 2
 PROF_STAGES = ["upload", "warp", "pyramid", "detect", "select", "orient_brief", "match", "pairs"]
 
 
@@ -65,7 +66,7 @@ class PairDesc(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("warp_grid", C.c_int32), ("pyramid_grid", C.c_int32), ("detect_grid", C.c_int32),
-                ("match_grid", C.c_int32), ("match_target_items", C.c_int32)]
+                ("match_grid", C.c_int32), ("match_target_items", C.c_int32), ("match_engine", C.c_int32)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -100,6 +101,8 @@ def load_library():
         "asift_ctx_create": (i32, [P(vp), P(OrbCfg), C.c_uint64]),
         "asift_ctx_destroy": (None, [vp]),
         "asift_ctx_orb_cfg": (i32, [vp, P(OrbCfg)]),
+        "asift_ctx_set_match_engine": (i32, [vp, i32]),
+        "asift_ctx_match_engine": (i32, [vp]),
         "asift_ctx_pattern": (i32, [vp, vp]),
         "asift_view_table": (i32, [i32, i32, i32, vp, i32, P(C.c_int)]),
         "asift_make_view": (i32, [i32, i32, C.c_double, C.c_double, P(ViewDesc)]),
@@ -280,6 +283,16 @@ class Context:
             w = torch.zeros(max(nbytes, 256), dtype=torch.uint8, device="cuda")
             self._ws[key] = w
         return w
+
+    # -- matcher engine (same results; speed only)
+    def set_match_engine(self, engine: int):
+        """MATCH_AUTO, MATCH_CUDA_CORES or MATCH_TENSOR_CORES for hamming_match and match_pair."""
+        _check("asift_ctx_set_match_engine", self.L.asift_ctx_set_match_engine(self._ctx, int(engine)))
+
+    @property
+    def match_engine(self) -> int:
+        """The engine a call would use now (MATCH_CUDA_CORES or MATCH_TENSOR_CORES)."""
+        return int(self.L.asift_ctx_match_engine(self._ctx))
 
     def profile(self, on: bool = True):
         _check("asift_profile_enable", self.L.asift_profile_enable(self._ctx, int(on)))

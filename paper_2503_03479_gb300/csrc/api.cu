@@ -201,7 +201,17 @@ struct asift_ctx {
     int ring_next = 0;
     bool prof = false;
     cudaEvent_t prof_ev[ASIFT_PROF_STAGES + 1] = {};
+    int match_engine = ASIFT_MATCH_AUTO;
 };
+
+// The matcher engine a call uses: the tuning's, else the context's; AUTO
+// resolves to tensor cores when the device has them.
+static int resolve_engine(const asift_ctx *ctx, const asift_tuning *tune)
+{
+    int e = (tune && tune->match_engine) ? tune->match_engine : ctx->match_engine;
+    if (e == ASIFT_MATCH_AUTO) e = tc_match_available() ? ASIFT_MATCH_TENSOR_CORES : ASIFT_MATCH_CUDA_CORES;
+    return e;
+}
 
 static void prof_mark(asift_ctx *ctx, int i, cudaStream_t s)
 {
@@ -281,6 +291,15 @@ void asift_ctx_destroy(asift_ctx *ctx)
     if (ctx->d_bins) cudaFree(ctx->d_bins);
     delete ctx;
 }
+
+asift_status asift_ctx_set_match_engine(asift_ctx *ctx, int engine)
+{
+    if (!ctx || engine < ASIFT_MATCH_AUTO || engine > ASIFT_MATCH_TENSOR_CORES) return ASIFT_ERR_ARG;
+    ctx->match_engine = engine;
+    return ASIFT_OK;
+}
+
+int asift_ctx_match_engine(const asift_ctx *ctx) { return ctx ? resolve_engine(ctx, nullptr) : 0; }
 
 asift_status asift_ctx_orb_cfg(const asift_ctx *ctx, asift_orb_cfg *out)
 {
@@ -572,13 +591,26 @@ asift_status orb_extract(asift_ctx *ctx, const uint8_t *d_view_u8, const uint8_t
 }
 
 // ---------------------------------------------------------------- hamming_match
-size_t hamming_workspace_size(int nq, int nt)
+// Workspace: status word, partial keys, then the expanded (+-1 fp8) queries
+// and trains of the tensor-core engine.
+struct HammingWs {
+    int32_t *status;
+    void *part;
+    uint8_t *xq, *xt;
+};
+
+static size_t hamming_ws(void *base, int nq, int nt, HammingWs *w)
 {
-    Bump b(nullptr);
-    b.take<int32_t>(64);
-    b.take<unsigned char>(hamming_partial_bytes(std::max(nq, 1), std::max(nt, 0)));
+    Bump b(base);
+    int32_t *status = b.take<int32_t>(64);
+    void *part = b.take<unsigned char>(hamming_partial_bytes(std::max(nq, 1), std::max(nt, 0)));
+    uint8_t *xq = b.take<uint8_t>(tc_expanded_bytes(nq));
+    uint8_t *xt = b.take<uint8_t>(tc_expanded_bytes(nt));
+    if (w) *w = HammingWs{status, part, xq, xt};
     return b.off + 256;
 }
+
+size_t hamming_workspace_size(int nq, int nt) { return hamming_ws(nullptr, std::max(nq, 0), std::max(nt, 0), nullptr); }
 
 asift_status hamming_match(asift_ctx *ctx, const uint8_t *d_q, int nq, const int32_t *d_nq, const uint8_t *d_t,
                            int nt, const int32_t *d_nt, int ratio_num, int ratio_den, asift_match *d_out,
@@ -588,15 +620,28 @@ asift_status hamming_match(asift_ctx *ctx, const uint8_t *d_q, int nq, const int
     if (!ctx || nq < 0 || nt < 0 || nt > (1 << 23) - 1 || (nq && (!d_q || !d_out)) || (nt && !d_t) ||
         ratio_num < 0 || ratio_den < 1 || ratio_num > (1 << 20) || ratio_den > (1 << 20) || !d_workspace)
         return ASIFT_ERR_ARG;
-    if (ws_bytes < hamming_workspace_size(nq, nt)) return ASIFT_ERR_ARG;
+    if (ws_bytes < hamming_workspace_size(nq, nt) || (reinterpret_cast<uintptr_t>(d_workspace) & 255))
+        return ASIFT_ERR_ARG;
+    const int engine = resolve_engine(ctx, nullptr);
+    if (engine == ASIFT_MATCH_TENSOR_CORES && !tc_match_available()) return ASIFT_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaSuccess;
-    if (d_n_accepted) e = cudaMemsetAsync(d_n_accepted, 0, sizeof(int32_t), s);
+    HammingWs w;
+    hamming_ws(d_workspace, nq, nt, &w);
+    cudaError_t e = cudaMemsetAsync(w.status, 0, sizeof(int32_t), s);
+    if (d_n_accepted && e == cudaSuccess) e = cudaMemsetAsync(d_n_accepted, 0, sizeof(int32_t), s);
     if (nq == 0 || e != cudaSuccess) return cuda_status(e);
-    Bump b(d_workspace);
-    b.take<int32_t>(64);
-    void *part = b.take<unsigned char>(hamming_partial_bytes(nq, nt));
-    e = launch_hamming(d_q, nq, d_nq, d_t, nt, d_nt, ratio_num, ratio_den, d_out, d_accept, d_n_accepted, part, s);
+    if (engine == ASIFT_MATCH_TENSOR_CORES && nt > 0) {
+        MatchProblem P;
+        match_problem_init(P, d_q, nq, d_nq, d_t, nt, d_nt, w.part, 0, d_out, d_accept, d_n_accepted);
+        e = launch_expand(d_q, w.xq, nullptr, 0, d_nq, nq, 1, s);
+        if (e == cudaSuccess) e = launch_expand(d_t, w.xt, nullptr, 0, d_nt, nt, 1, s);
+        if (e == cudaSuccess)
+            e = launch_match_tc(d_q, w.xq, nq, d_t, w.xt, nt, nullptr, 0, P, nq, ratio_num, ratio_den, MatchTuning{},
+                                w.status, s);
+    } else {
+        e = launch_hamming(d_q, nq, d_nq, d_t, nt, d_nt, ratio_num, ratio_den, d_out, d_accept, d_n_accepted, w.part,
+                           s);
+    }
     return cuda_status(e);
 }
 
@@ -646,6 +691,7 @@ struct Pipeline {
     int32_t *view_count = nullptr, *view_off = nullptr;
     asift_keypoint *kp = nullptr;
     uint8_t *desc = nullptr;
+    uint8_t *xdesc = nullptr;                // desc expanded to +-1 fp8 (tensor-core matcher)
     asift_match *match = nullptr;
     uint8_t *accept = nullptr;
     int32_t *n_acc = nullptr;
@@ -655,7 +701,8 @@ struct Pipeline {
     std::vector<DevView> h_dv;
     std::vector<MatchProblem> h_probs;
     std::vector<ImageConv> h_conv;
-    int n_tiles = 0, cw_max = 0, bw_max = 0, total_q = 0, total_blk = 0;
+    int n_tiles = 0, cw_max = 0, bw_max = 0, total_q = 0, total_blk = 0, n_per_view = 0;
+    long long cap_rows = 0;
     long long max_px = 0;
     size_t tab_bytes = 0;                    // bytes from dv to the end of the table region
     size_t bytes = 0;
@@ -724,8 +771,11 @@ static bool pipeline_layout(const asift_ctx *ctx, const PairSpec *ps, int P, int
     L.view_count = b.take<int32_t>(L.nv);
     L.view_off = b.take<int32_t>(L.nv);
     const size_t cap = (size_t)L.nv * N;
+    L.cap_rows = (long long)cap;
+    L.n_per_view = N;
     L.kp = b.take<asift_keypoint>(cap);
     L.desc = b.take<uint8_t>(cap * 32);
+    L.xdesc = b.take<uint8_t>(tc_expanded_bytes((long long)cap));
     L.match = b.take<asift_match>(cap);
     L.accept = b.take<uint8_t>(cap);
     L.n_acc = b.take<int32_t>(P);
@@ -809,7 +859,15 @@ static cudaError_t pipeline_run(asift_ctx *ctx, const Pipeline &L, const asift_p
     if (e == cudaSuccess) e = cudaMemsetAsync(L.n_acc, 0, sizeof(int32_t) * P, s);
     if (e == cudaSuccess) {
         MatchTuning mt{tune ? tune->match_grid : 0, tune ? tune->match_target_items : 0};
-        e = launch_match(L.probs, P, L.h_probs[0], L.total_q, true, pc.ratio_num, pc.ratio_den, mt, s);
+        if (resolve_engine(ctx, tune) == ASIFT_MATCH_TENSOR_CORES) {
+            if (!tc_match_available()) return cudaErrorNotSupported;
+            e = launch_expand(L.desc, L.xdesc, L.o.group_first, L.n_per_view, L.o.group_total, L.cap_rows, 2 * P, s);
+            if (e == cudaSuccess)
+                e = launch_match_tc(L.desc, L.xdesc, L.cap_rows, L.desc, L.xdesc, L.cap_rows, L.probs, P,
+                                    L.h_probs[0], L.total_q, pc.ratio_num, pc.ratio_den, mt, L.status, s);
+        } else {
+            e = launch_match(L.probs, P, L.h_probs[0], L.total_q, true, pc.ratio_num, pc.ratio_den, mt, s);
+        }
     }
     prof_mark(ctx, 7, s);
     if (e == cudaSuccess) e = launch_pairs(L.probs, P, L.h_probs[0], L.total_blk, L.block_count, L.dv, L.status, s);
@@ -885,6 +943,12 @@ asift_status match_pair_inspect(const asift_ctx *ctx, int H1, int W1, int H2, in
 }  // extern "C"
 
 // ---------------------------------------------------------------- batched plan
+static bool tuning_ok(const asift_tuning &t)
+{
+    return t.warp_grid >= 0 && t.pyramid_grid >= 0 && t.detect_grid >= 0 && t.match_grid >= 0 &&
+           t.match_target_items >= 0 && t.match_engine >= ASIFT_MATCH_AUTO && t.match_engine <= ASIFT_MATCH_TENSOR_CORES;
+}
+
 struct asift_plan {
     asift_ctx *ctx = nullptr;
     asift_pair_cfg pc{};
@@ -950,6 +1014,7 @@ asift_status asift_plan_create(asift_ctx *ctx, const asift_pair_desc *h_pairs, i
     *out = nullptr;
     const asift_pair_cfg pc = pair_cfg_or_default(cfg);
     if (pc.kmax < 0 || pc.kmax > 7 || pc.ratio_den < 1 || pc.ratio_num < 0 || pc.per_view) return ASIFT_ERR_ARG;
+    if (tuning && !tuning_ok(*tuning)) return ASIFT_ERR_ARG;
     std::vector<asift::PairSpec> ps(n_pairs);
     for (int i = 0; i < n_pairs; ++i) {
         const asift_pair_desc &d = h_pairs[i];
@@ -1031,9 +1096,7 @@ asift_status asift_plan_workspace(const asift_plan *plan, void **d_workspace, in
 asift_status asift_plan_set_tuning(asift_plan *plan, const asift_tuning *tuning)
 {
     if (!plan || !tuning) return ASIFT_ERR_ARG;
-    if (tuning->warp_grid < 0 || tuning->pyramid_grid < 0 || tuning->detect_grid < 0 || tuning->match_grid < 0 ||
-        tuning->match_target_items < 0)
-        return ASIFT_ERR_ARG;
+    if (!tuning_ok(*tuning)) return ASIFT_ERR_ARG;
     plan->tune = *tuning;
     if (cudaStreamSynchronize(plan->stream) != cudaSuccess) return ASIFT_ERR_CUDA;
     return cuda_status(plan_capture(plan));
@@ -1085,11 +1148,10 @@ asift_status asift_plan_autotune(asift_plan *plan, int reps, asift_tuning *out)
         {&t.warp_grid, {0, 2 * sms, 3 * sms}},
         {&t.pyramid_grid, {0, 4 * sms, 8 * sms}},
         {&t.detect_grid, {0, 4 * sms, 8 * sms}},
-        {&t.match_grid, {7 * sms, 4 * sms}},
-        {&t.match_target_items, {0, 4 * 7 * sms, 7 * sms}},
     };
+    if (tc_match_available()) knobs.push_back({&t.match_engine, {ASIFT_MATCH_TENSOR_CORES, ASIFT_MATCH_CUDA_CORES}});
     cudaError_t e = cudaSuccess;
-    for (auto &k : knobs) {
+    auto tune_knob = [&](const Knob &k) {
         int best = *k.field;
         float best_ms = 1e30f;
         for (int c : k.cands) {
@@ -1101,7 +1163,23 @@ asift_status asift_plan_autotune(asift_plan *plan, int reps, asift_tuning *out)
             if (ms < best_ms) { best_ms = ms; best = c; }
         }
         *k.field = best;
+    };
+    for (const Knob &k : knobs) {
+        tune_knob(k);
         if (e != cudaSuccess) break;
+    }
+    // the matcher's launch shape, for the engine chosen above
+    std::vector<Knob> mk;
+    if (resolve_engine(plan->ctx, &t) == ASIFT_MATCH_TENSOR_CORES) {
+        t.match_grid = 0;                                   // one CTA per SM
+        mk.push_back({&t.match_target_items, {0, 2 * sms, 8 * sms, 16 * sms}});
+    } else {
+        mk.push_back({&t.match_grid, {7 * sms, 4 * sms}});
+        mk.push_back({&t.match_target_items, {0, 4 * 7 * sms, 7 * sms}});
+    }
+    for (const Knob &k : mk) {
+        if (e != cudaSuccess) break;
+        tune_knob(k);
     }
     if (e == cudaSuccess) e = plan_capture(plan);
     if (out) *out = plan->tune;

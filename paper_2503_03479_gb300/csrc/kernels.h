@@ -50,6 +50,8 @@ void match_problem_init(MatchProblem &P, const uint8_t *q, int nq, const int32_t
 void match_problems_offsets(MatchProblem *probs, int n, int *total_q, int *total_blk);
 cudaError_t launch_match(const MatchProblem *d_probs, int n_probs, const MatchProblem &single, int total_q,
                          bool any_train, int num, int den, const MatchTuning &tune, cudaStream_t s);
+cudaError_t launch_merge(const MatchProblem *d_probs, int n_probs, const MatchProblem &single, int total_q, int num,
+                         int den, cudaStream_t s);
 cudaError_t launch_hamming(const uint8_t *q, int nq, const int32_t *d_nq, const uint8_t *t, int nt,
                            const int32_t *d_nt, int num, int den, asift_match *out, uint8_t *accept,
                            int32_t *n_acc, void *part, cudaStream_t s);
@@ -58,6 +60,16 @@ cudaError_t launch_hamming_noalloc(const uint8_t *q, int nq, const int32_t *d_nq
                                    int32_t *n_acc, cudaStream_t s);
 cudaError_t launch_pairs(const MatchProblem *d_probs, int n_probs, const MatchProblem &single, int total_blk,
                          int32_t *block_count, const DevView *views, int32_t *status, cudaStream_t s);
+
+// match_tc.cu (tensor-core matcher; same partials and merge as match.cu)
+bool tc_match_available();
+size_t tc_expanded_bytes(long long rows);
+cudaError_t launch_expand(const uint8_t *packed, uint8_t *out, const int32_t *d_first, int n_per_view,
+                          const int32_t *d_count, long long cap_rows, int n_groups, cudaStream_t s);
+cudaError_t launch_match_tc(const uint8_t *qbase, const uint8_t *qexp, long long q_rows, const uint8_t *tbase,
+                            const uint8_t *texp, long long t_rows, const MatchProblem *d_probs, int n_probs,
+                            const MatchProblem &single, int total_q, int num, int den, const MatchTuning &tune,
+                            int32_t *status, cudaStream_t s);
 
 // dwarp.cu
 struct DiffView;

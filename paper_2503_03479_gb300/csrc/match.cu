@@ -356,7 +356,16 @@ cudaError_t launch_match(const MatchProblem *d_probs, int n_probs, const MatchPr
     if (any_train) {
         hamming_top2_kernel<<<grid, kMThreads, 0, s>>>(d_probs, n_probs, single, target);
         note_launch();
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
+    return launch_merge(d_probs, n_probs, single, total_q, num, den, s);
+}
+
+cudaError_t launch_merge(const MatchProblem *d_probs, int n_probs, const MatchProblem &single, int total_q, int num,
+                         int den, cudaStream_t s)
+{
+    if (total_q <= 0) return cudaSuccess;
     merge_kernel<<<(total_q + 255) / 256, 256, 0, s>>>(d_probs, n_probs, single, total_q, num, den);
     note_launch();
     return cudaGetLastError();

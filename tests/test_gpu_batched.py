@@ -88,8 +88,12 @@ def test_autotuner_picks_valid_shapes_and_keeps_results(A):
     ref = _reference(A, ctx, pairs)
     plan = A.Plan(ctx, [p[0] for p in pairs], [p[1] for p in pairs], kmax=KMAX)
     t = plan.autotune(reps=2)
-    assert set(t) == {"warp_grid", "pyramid_grid", "detect_grid", "match_grid", "match_target_items"}
+    assert set(t) == {"warp_grid", "pyramid_grid", "detect_grid", "match_grid", "match_target_items",
+                      "match_engine"}
     assert all(v >= 0 for v in t.values())
+    # the tuner picks an engine explicitly when the device has tensor cores
+    major, _ = torch.cuda.get_device_capability()
+    assert t["match_engine"] in ((A.MATCH_CUDA_CORES, A.MATCH_TENSOR_CORES) if major == 10 else (0,))
     assert plan.tuning() == t
     plan.run()
     torch.cuda.synchronize()
