@@ -191,6 +191,63 @@ __global__ void expand_pm1_kernel(const uint8_t *__restrict__ packed, uint8_t *_
         dst[i] = expand_byte(src[i]);
 }
 
+// ---------------------------------------------------------------- epilogue
+__device__ __forceinline__ float max3f(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+__device__ __forceinline__ float max32(const float v[32])
+{
+    float m[11];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) m[i] = max3f(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
+    m[10] = fmaxf(v[30], v[31]);
+    const float a = max3f(m[0], m[1], m[2]), b = max3f(m[3], m[4], m[5]), c = max3f(m[6], m[7], m[8]);
+    return max3f(max3f(a, b, c), m[9], m[10]);
+}
+
+// Inserts the key of the score s = 64 v - j (v the dot product, j the column
+// in the chunk) into the running top two.  A key that is not below b2 leaves
+// both unchanged, so candidates need no pre-test.
+__device__ __forceinline__ void insert_score(float s, int col0, unsigned &b1, unsigned &b2)
+{
+    const int si = __float2int_rn(s);
+    const int v = (si + 63) >> 6;                         // ceil(s / 64): the dot product
+    const int j = (v << 6) - si;
+    const unsigned key = ((unsigned)((256 - v) >> 1) << 23) | (unsigned)(col0 + j);
+    b2 = min(b2, max(b1, key));
+    b1 = min(b1, key);
+}
+
+// One 32-column chunk of a thread's accumulator row (dot products, even
+// integers in [-256, 256]).  Only the chunk's two smallest keys (largest dot,
+// then lowest column) can enter the top two, and none can unless the chunk's
+// maximum beats the current second best: the common case costs 16 three-input
+// max and one compare.  kFull = false masks columns >= valid.
+template <bool kFull>
+__device__ __forceinline__ void epi_chunk(const uint32_t r[32], int valid, int col0, unsigned &b1, unsigned &b2,
+                                          float &thr)
+{
+    float v[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = (kFull || j < valid) ? __uint_as_float(r[j]) : -1.0e30f;
+    if (max32(v) > thr) {
+        float sc[32];                                     // 64 v - j: max gives the largest v, then lowest j
+#pragma unroll
+        for (int j = 0; j < 32; ++j) sc[j] = fmaf(v[j], 64.0f, -(float)j);
+        const float s1 = max32(sc);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) sc[j] = (sc[j] == s1) ? -3.0e30f : sc[j];
+        const float s2 = max32(sc);
+        insert_score(s1, col0, b1, b2);
+        if (s2 > -1.0e20f) insert_score(s2, col0, b1, b2);
+        thr = (b2 == kTcNoKey) ? -1.0e30f : 256.0f - 2.0f * (float)(b2 >> 23);
+    }
+}
+
 // ---------------------------------------------------------------- the matcher
 __device__ __forceinline__ int tc_count(const int32_t *d, int cap) { return d ? min(max(*d, 0), cap) : cap; }
 
@@ -395,27 +452,12 @@ hamming_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constan
                     tmem_ld32(taddr + (uint32_t)(c * 32), r[0]);
                     tmem_ld32(taddr + (uint32_t)(c * 32 + 32), r[1]);
                     tmem_wait_ld();
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        float v[32];
-                        const int cb = (c + h) * 32;
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) v[j] = (cb + j < valid) ? __uint_as_float(r[h][j]) : -1.0e30f;
-                        float m = v[0];
-#pragma unroll
-                        for (int j = 1; j < 32; ++j) m = fmaxf(m, v[j]);
-                        if (m > thr) {
-#pragma unroll
-                            for (int j = 0; j < 32; ++j) {
-                                if (v[j] > thr) {
-                                    const unsigned d = (unsigned)__float2int_rn((256.0f - v[j]) * 0.5f);
-                                    const unsigned key = (d << 23) | (unsigned)(tb + cb + j);
-                                    b2 = min(b2, max(b1, key));
-                                    b1 = min(b1, key);
-                                    thr = (b2 == kTcNoKey) ? -1.0e30f : 256.0f - 2.0f * (float)(b2 >> 23);
-                                }
-                            }
-                        }
+                    if (valid == kTcBN) {
+                        epi_chunk<true>(r[0], 32, tb + c * 32, b1, b2, thr);
+                        epi_chunk<true>(r[1], 32, tb + c * 32 + 32, b1, b2, thr);
+                    } else {
+                        epi_chunk<false>(r[0], valid - c * 32, tb + c * 32, b1, b2, thr);
+                        epi_chunk<false>(r[1], valid - c * 32 - 32, tb + c * 32 + 32, b1, b2, thr);
                     }
                 }
                 tc_fence_before();

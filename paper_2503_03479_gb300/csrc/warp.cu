@@ -10,10 +10,14 @@
 //      reach (the bounding box of the rotated chunk, at most 72 x 72) are
 //      first staged in shared memory, so every tap is a shared-memory load
 //      (Eq. (3)-(4); geometry in exact Q32 fixed point);
-//   2. blurs the strip along x with the Gaussian taps (B), four outputs per
-//      thread so each loaded C value serves four sums;
+//   2. blurs the strip along x with the Gaussian taps (B);
 //   3. resamples B at X = t (x' - (Wv-1)/2) + (Wr-1)/2 with Lanczos-3 and
-//      writes fp32 (optional), rint-to-u8 and the footprint mask.
+//      writes fp32 (optional), rint-to-u8 and the footprint mask (computed
+//      per canvas sample in step 1).
+// In every step a warp covers 32 consecutive columns of one row, so its
+// shared-memory accesses fall in distinct banks (step 1 up to the rotation's
+// rounding), and a thread walks down its column in steps of 4 rows, moving
+// its Q32 source point by a constant.
 // Strip position i holds the value of canvas column clamp(i, 0, Wr-1), which
 // realises the clamped borders of the Gaussian and of the tilt taps without
 // per-tap clamps.
@@ -26,8 +30,8 @@
 namespace asift {
 
 constexpr int kChunk = 64;              // canvas columns per staged chunk
-constexpr int kStage = 80;              // staged source box (rows, columns), >= 64|c| + 16|s| + 6
-constexpr int kStagePitch = kStage + 1; // odd pitch against bank conflicts
+constexpr int kStage = 72;              // staged source box (rows, columns), >= 64|c| + 16|s| + 6
+constexpr int kStagePitch = kStage + 1; // odd pitch
 
 // sin and cos on [0, pi/3] from their Taylor series (truncation below 5e-8).
 __device__ __forceinline__ void sincos_small(float x, float &s, float &c)
@@ -44,27 +48,80 @@ __device__ __forceinline__ void sincos_small(float x, float &s, float &c)
 // L(f - m) = 3 sin(pi (f - m)) sin(pi (f - m)/3) / (pi (f - m))^2 and
 // sin(pi (f - m)) = (-1)^m sin(pi f): the common factor 3 sin(pi f)/pi^2
 // cancels in the normalisation, leaving
-//   w_m  ~  (-1)^m sin(pi f/3 - pi m/3) / (f - m)^2,
-// whose six sines follow from sin and cos of pi f/3 by angle addition.
-// f = 0 (lo == 0) is the identity.
+//   w_m  ~  N_m / D_m,  N_m = (-1)^m sin(pi f/3 - pi m/3),  D_m = (f - m)^2,
+// whose six sines follow from sin and cos of pi f/3 by angle addition.  Over
+// the common denominator, w_m = N_m prod_{k != m} D_k / sum_n N_n prod_{k != n}
+// D_k: prefix and suffix products and one reciprocal.  f is the top 23
+// fraction bits (an error below 1.2e-7 px); f = 0 there is the identity.
 __device__ __forceinline__ void lanczos3_weights(uint32_t lo, float w[6])
 {
-    if (lo == 0u) {
+    const uint32_t m23 = lo >> 9;
+    if (m23 == 0u) {
         w[0] = w[1] = w[3] = w[4] = w[5] = 0.f;
         w[2] = 1.f;
         return;
     }
-    const float f = __uint2float_rz(lo) * 2.3283064365386963e-10f;   // < 1
+    const float f = __uint_as_float(0x3F800000u | m23) - 1.0f;   // exact: m23 * 2^-23
     float s, c;
     sincos_small(f * 1.04719755119659775f, s, c);
     const float hs = 0.5f * s, hc = 0.86602540378443864676f * c;
     const float a = hc - hs, b = -(hs + hc);
     const float d0 = f + 2.f, d1 = f + 1.f, d3 = f - 1.f, d4 = f - 2.f, d5 = f - 3.f;
-    const float w0 = __fdividef(a, d0 * d0), w1 = __fdividef(b, d1 * d1), w2 = __fdividef(s, f * f);
-    const float w3 = __fdividef(a, d3 * d3), w4 = __fdividef(b, d4 * d4), w5 = __fdividef(s, d5 * d5);
-    const float inv = __frcp_rn(((w0 + w1) + (w2 + w3)) + (w4 + w5));
-    w[0] = w0 * inv; w[1] = w1 * inv; w[2] = w2 * inv;
-    w[3] = w3 * inv; w[4] = w4 * inv; w[5] = w5 * inv;
+    const float D0 = d0 * d0, D1 = d1 * d1, D2 = f * f, D3 = d3 * d3, D4 = d4 * d4, D5 = d5 * d5;
+    const float p2 = D0 * D1, p3 = p2 * D2, p4 = p3 * D3;           // prefix products
+    const float s3 = D5 * D4, s2 = s3 * D3, s1 = s2 * D2;           // suffix products
+    const float u0 = a * (s1 * D1), u1 = b * (D0 * s1), u2 = s * (p2 * s2);
+    const float u3 = a * (p3 * s3), u4 = b * (p4 * D5), u5 = s * (p4 * D4);
+    const float inv = __frcp_rn(((u0 + u1) + (u2 + u3)) + (u4 + u5));
+    w[0] = u0 * inv; w[1] = u1 * inv; w[2] = u2 * inv;
+    w[3] = u3 * inv; w[4] = u4 * inv; w[5] = u5 * inv;
+}
+
+// Two weight sets at once in packed fp32 pairs (.x from lo_a, .y from lo_b),
+// the same arithmetic as lanczos3_weights component by component.  A zero fraction is
+// computed at 2^-23 (finite) and then replaced by the exact identity.
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+__device__ __forceinline__ void lanczos3_weights2(uint32_t lo_a, uint32_t lo_b, float2 w[6])
+{
+    const uint32_t ma = lo_a >> 9, mb = lo_b >> 9;
+    const float2 f = make_float2(__uint_as_float(0x3F800000u | max(ma, 1u)) - 1.0f,
+                                 __uint_as_float(0x3F800000u | max(mb, 1u)) - 1.0f);
+    const float2 x = __fmul2_rn(f, f2(1.04719755119659775f));
+    const float2 x2 = __fmul2_rn(x, x);
+    float2 ps = __ffma2_rn(x2, f2(2.75573192e-6f), f2(-1.98412698e-4f));
+    ps = __ffma2_rn(x2, ps, f2(8.33333333e-3f));
+    ps = __ffma2_rn(x2, ps, f2(-1.66666667e-1f));
+    ps = __ffma2_rn(x2, ps, f2(1.0f));
+    const float2 s = __fmul2_rn(x, ps);
+    float2 pc = __ffma2_rn(x2, f2(-2.75573192e-7f), f2(2.48015873e-5f));
+    pc = __ffma2_rn(x2, pc, f2(-1.38888889e-3f));
+    pc = __ffma2_rn(x2, pc, f2(4.16666667e-2f));
+    pc = __ffma2_rn(x2, pc, f2(-0.5f));
+    const float2 c = __ffma2_rn(x2, pc, f2(1.0f));
+    const float2 hs = __fmul2_rn(f2(0.5f), s), hc = __fmul2_rn(f2(0.86602540378443864676f), c);
+    const float2 a = __fadd2_rn(hc, __fmul2_rn(hs, f2(-1.0f)));
+    const float2 b = __fmul2_rn(__fadd2_rn(hs, hc), f2(-1.0f));
+    const float2 d0 = __fadd2_rn(f, f2(2.f)), d1 = __fadd2_rn(f, f2(1.f)), d3 = __fadd2_rn(f, f2(-1.f));
+    const float2 d4 = __fadd2_rn(f, f2(-2.f)), d5 = __fadd2_rn(f, f2(-3.f));
+    const float2 D0 = __fmul2_rn(d0, d0), D1 = __fmul2_rn(d1, d1), D2 = __fmul2_rn(f, f);
+    const float2 D3 = __fmul2_rn(d3, d3), D4 = __fmul2_rn(d4, d4), D5 = __fmul2_rn(d5, d5);
+    const float2 p2 = __fmul2_rn(D0, D1), p3 = __fmul2_rn(p2, D2), p4 = __fmul2_rn(p3, D3);
+    const float2 s3 = __fmul2_rn(D5, D4), s2 = __fmul2_rn(s3, D3), s1 = __fmul2_rn(s2, D2);
+    const float2 u0 = __fmul2_rn(a, __fmul2_rn(s1, D1)), u1 = __fmul2_rn(b, __fmul2_rn(D0, s1));
+    const float2 u2 = __fmul2_rn(s, __fmul2_rn(p2, s2)), u3 = __fmul2_rn(a, __fmul2_rn(p3, s3));
+    const float2 u4 = __fmul2_rn(b, __fmul2_rn(p4, D5)), u5 = __fmul2_rn(s, __fmul2_rn(p4, D4));
+    const float2 sum = __fadd2_rn(__fadd2_rn(__fadd2_rn(u0, u1), __fadd2_rn(u2, u3)), __fadd2_rn(u4, u5));
+    const float2 inv = make_float2(__frcp_rn(sum.x), __frcp_rn(sum.y));
+    w[0] = __fmul2_rn(u0, inv); w[1] = __fmul2_rn(u1, inv); w[2] = __fmul2_rn(u2, inv);
+    w[3] = __fmul2_rn(u3, inv); w[4] = __fmul2_rn(u4, inv); w[5] = __fmul2_rn(u5, inv);
+    if (ma == 0u || mb == 0u) {
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+            if (ma == 0u) w[m].x = m == 2 ? 1.f : 0.f;
+            if (mb == 0u) w[m].y = m == 2 ? 1.f : 0.f;
+        }
+    }
 }
 
 __global__ void u8_to_f32_kernel(const uint8_t *__restrict__ src, int pitch, int W, int H,
@@ -101,13 +158,38 @@ struct CanvasGeom {           // Q32 map of canvas (i, j) to the source point
     }
 };
 
-__device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restrict__ views, int n_views, int cw_max, int bw_max,
-                 uint8_t *__restrict__ out_u8, uint8_t *__restrict__ out_mask, float *__restrict__ out_f32)
+// The 36-tap interpolation of the staged source at the Q32 point (px, py),
+// all taps inside the staged box; the x and y weight sets are computed
+// together in packed fp32 pairs.
+__device__ __forceinline__ float interp_interior(const float *__restrict__ Ss, long long px, long long py, int sx0,
+                                                 int sy0)
+{
+    float2 w[6];
+    lanczos3_weights2((uint32_t)px, (uint32_t)py, w);
+    const float *b = Ss + ((int)(py >> 32) - 2 - sy0) * kStagePitch + ((int)(px >> 32) - 2 - sx0);
+    float rs[6];
+#pragma unroll
+    for (int n = 0; n < 6; ++n) {
+        const float *row = b + n * kStagePitch;
+        rs[n] = fmaf(w[0].x, row[0], fmaf(w[1].x, row[1], fmaf(w[2].x, row[2],
+                fmaf(w[3].x, row[3], fmaf(w[4].x, row[4], w[5].x * row[5])))));
+    }
+    return fmaf(w[0].y, rs[0], fmaf(w[1].y, rs[1], fmaf(w[2].y, rs[2],
+           fmaf(w[3].y, rs[3], fmaf(w[4].y, rs[4], w[5].y * rs[5])))));
+}
+
+__device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restrict__ views, int n_views, int cw_max,
+                                               int bw_max, uint8_t *__restrict__ out_u8,
+                                               uint8_t *__restrict__ out_mask, float *__restrict__ out_f32)
 {
     extern __shared__ float smem[];
-    float *Cs = smem;                              // [kWarpTH][cw_max]
-    float *Bs = Cs + kWarpTH * cw_max;             // [kWarpTH][bw_max]
-    float *Ss = Bs + kWarpTH * bw_max;             // [kStage][kStagePitch] staged source
+    // Cs [kWarpTH][cw_max] canvas strip, then one region that holds the staged
+    // source [kStage][kStagePitch] in step 1 and the blurred strip Bs
+    // [kWarpTH][bw_max] in steps 2-3, then the footprint mask Ms.
+    float *Cs = smem;
+    float *Ss = Cs + kWarpTH * cw_max;
+    float *Bs = Ss;
+    uint8_t *Ms = reinterpret_cast<uint8_t *>(Ss + max(kStage * kStagePitch, kWarpTH * bw_max));
     __shared__ float gs[ASIFT_MAX_GAUSS];
 
     const int vi = find_owner(views, n_views, tile, [](const DevView &v) { return v.tile_start; });
@@ -127,19 +209,30 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
     const int bx0 = (int)(Xa >> 32) - 2, bx1 = (int)(Xb >> 32) + 3;   // unclamped strip of B
     const int bw = bx1 - bx0 + 1;
     const int cx0 = bx0 - K;                // strip of C: [cx0, cx0 + cw), covering the Gaussian
-    const int cw = ((bw + 3) & ~3) + 2 * K; // taps of B computed four at a time
+    const int cw = ((bw + 3) & ~3) + 2 * K;
 
     for (int k = threadIdx.x; k <= K; k += blockDim.x) gs[k] = V.g[k];
 
-    // 1. rotated canvas strip, chunk by chunk through shared memory
+    // Thread layout of all three phases: column c of 64, rows rg, rg + 4, ...
+    // so a warp covers 32 consecutive columns of one row.
+    const int c = threadIdx.x & (kChunk - 1);
+    const int rg = threadIdx.x / kChunk;
+    constexpr int kRowStep = kWarpThreads / kChunk;
+
+    // 1. rotated canvas strip and its footprint mask, chunk by chunk through
+    //    shared memory.  Moving down kRowStep canvas rows adds
+    //    2 kRowStep (sq, cq) to the Q32 source point.
     const float *__restrict__ src = V.src;
     const int sp = V.src_pitch;
     const long long xlim = (long long)(2 * W - 1) * HALF, ylim = (long long)(2 * H - 1) * HALF;
+    const long long mxlo = HALF, mxhi = (long long)(2 * W - 3) * HALF;
+    const long long mylo = HALF, myhi = (long long)(2 * H - 3) * HALF;
+    const long long dpx = 2LL * kRowStep * V.sq, dpy = 2LL * kRowStep * V.cq;
     const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     for (int c0 = 0; c0 < cw; c0 += kChunk) {
         const int cn = min(kChunk, cw - c0);
         // source box of this chunk: the taps of the four corners of the
-        // (clamped) canvas region, clamped to the image
+        // (clamped) canvas region
         const int i_lo = clampi(cx0 + c0, 0, Wr - 1), i_hi = clampi(cx0 + c0 + cn - 1, 0, Wr - 1);
         int sx0 = 1 << 30, sx1 = -(1 << 30), sy0 = 1 << 30, sy1 = -(1 << 30);
 #pragma unroll
@@ -151,136 +244,114 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
             sy0 = min(sy0, (int)(py >> 32));
             sy1 = max(sy1, (int)(py >> 32));
         }
+        // all taps of all points inside the image: no clamps, no background
+        // (the points lie in the corners' convex hull)
+        const bool interior = sx0 >= 2 && sx1 + 3 <= W - 1 && sy0 >= 2 && sy1 + 3 <= H - 1;
         sx0 = clampi(sx0 - 2, 0, W - 1);
         sx1 = clampi(sx1 + 3, 0, W - 1);
         sy0 = clampi(sy0 - 2, 0, H - 1);
         sy1 = clampi(sy1 + 3, 0, H - 1);
         // a chunk spans at most 63 columns and 15 rows of the canvas, so the
-        // box spans at most sqrt(63^2 + 15^2) + 1 + 5 < 73 <= kStage source pixels
+        // box spans at most sqrt(63^2 + 15^2) + 1 + 5 < 72 = kStage source pixels
         const int bwid = sx1 - sx0 + 1, bhgt = sy1 - sy0 + 1;
         __syncthreads();   // previous chunk's reads of Ss are done
         for (int r = warp; r < bhgt; r += kWarpThreads / 32) {
             const float *srow = src + (size_t)(sy0 + r) * sp + sx0;
-            for (int c = lane; c < bwid; c += 32) Ss[r * kStagePitch + c] = __ldg(srow + c);
+            for (int cc = lane; cc < bwid; cc += 32) Ss[r * kStagePitch + cc] = __ldg(srow + cc);
         }
         __syncthreads();
-        // canvas pixels of the chunk; a warp covers 8 columns x 4 rows so its
-        // lanes' taps fall in a compact source region
-        const int nblk_c = (cn + 7) >> 3, nblk_r = (nrows + 3) >> 2;
-        for (int blk = warp; blk < nblk_c * nblk_r; blk += kWarpThreads / 32) {
-            const int c = ((blk % nblk_c) << 3) + (lane & 7u);
-            const int r = ((blk / nblk_c) << 2) + (lane >> 3);
-            if (c >= cn || r >= nrows) continue;
-            const int i = clampi(cx0 + c0 + c, 0, Wr - 1), j = j0 + r;
+        if (c < cn) {
+            const int iu = cx0 + c0 + c;                 // strip position -> canvas column (clamped)
+            const int i = clampi(iu, 0, Wr - 1);
+            const uint8_t col_ok = iu == i;
             long long px, py;
-            G.map(i, j, px, py);
-            float acc = 0.f;
-            if (px >= -HALF && px < xlim && py >= -HALF && py < ylim) {
-                float wx[6], wy[6];
-                lanczos3_weights((uint32_t)px, wx);
-                lanczos3_weights((uint32_t)py, wy);
-                const int x0 = (int)(px >> 32), y0 = (int)(py >> 32);
-                if (x0 >= 2 && x0 + 3 < W && y0 >= 2 && y0 + 3 < H) {
-                    // interior: no clamped taps, one base address and immediate offsets
-                    const float *b = Ss + (y0 - 2 - sy0) * kStagePitch + (x0 - 2 - sx0);
-                    float rs[6];
+            G.map(i, j0 + rg, px, py);
+            float *Cp = Cs + c0 + c;
+            uint8_t *Mp = Ms + c0 + c;
+            if (interior) {
+                for (int r = rg; r < nrows; r += kRowStep, px += dpx, py += dpy) {
+                    Cp[r * cw_max] = interp_interior(Ss, px, py, sx0, sy0);
+                    Mp[r * cw_max] = col_ok;
+                }
+            } else {
+                for (int r = rg; r < nrows; r += kRowStep, px += dpx, py += dpy) {
+                    float acc = 0.f;
+                    if (px >= -HALF && px < xlim && py >= -HALF && py < ylim) {
+                        float2 w[6];
+                        lanczos3_weights2((uint32_t)px, (uint32_t)py, w);
+                        const int x0 = (int)(px >> 32), y0 = (int)(py >> 32);
+                        int xs[6];
 #pragma unroll
-                    for (int n = 0; n < 6; ++n) {
-                        const float *row = b + n * kStagePitch;
-                        rs[n] = fmaf(wx[0], row[0], fmaf(wx[1], row[1], fmaf(wx[2], row[2],
-                                fmaf(wx[3], row[3], fmaf(wx[4], row[4], wx[5] * row[5])))));
+                        for (int m = 0; m < 6; ++m) xs[m] = clampi(x0 + m - 2, 0, W - 1) - sx0;
+#pragma unroll
+                        for (int n = 0; n < 6; ++n) {
+                            const float *row = Ss + (clampi(y0 + n - 2, 0, H - 1) - sy0) * kStagePitch;
+                            float a = 0.f;
+#pragma unroll
+                            for (int m = 0; m < 6; ++m) a = fmaf(w[m].x, row[xs[m]], a);
+                            acc = fmaf(w[n].y, a, acc);
+                        }
                     }
-                    acc = fmaf(wy[0], rs[0], fmaf(wy[1], rs[1], fmaf(wy[2], rs[2],
-                          fmaf(wy[3], rs[3], fmaf(wy[4], rs[4], wy[5] * rs[5])))));
-                } else {
-                    int xs[6];
-#pragma unroll
-                    for (int m = 0; m < 6; ++m) xs[m] = clampi(x0 + m - 2, 0, W - 1) - sx0;
-#pragma unroll
-                    for (int n = 0; n < 6; ++n) {
-                        const float *row = Ss + (clampi(y0 + n - 2, 0, H - 1) - sy0) * kStagePitch;
-                        float a = 0.f;
-#pragma unroll
-                        for (int m = 0; m < 6; ++m) a = fmaf(wx[m], row[xs[m]], a);
-                        acc = fmaf(wy[n], a, acc);
-                    }
+                    Cp[r * cw_max] = acc;
+                    Mp[r * cw_max] = col_ok & (uint8_t)(px >= mxlo && px <= mxhi && py >= mylo && py <= myhi);
                 }
             }
-            Cs[r * cw_max + c0 + c] = acc;
         }
     }
     __syncthreads();
 
-    // 2. Gaussian along canvas x: B(i) = sum_k g_|k| C(clamp(i) - k), four
-    //    consecutive outputs per thread.  Strip index of canvas column i is
-    //    i - cx0; clamp(i) - k stays inside [cx0, cx0 + cw).
-    const int nq4 = (bw + 3) >> 2;
-    for (int e = threadIdx.x; e < nrows * nq4; e += blockDim.x) {
-        const int r = e / nq4, q4 = e - r * nq4;
+    // 2. Gaussian along canvas x: B(i) = sum_k g_|k| C(clamp(i) - k).  A lane
+    //    computes up to four outputs kChunk apart, so a warp reads 32
+    //    consecutive C values per tap and output and each g_k load serves
+    //    four sums.  Strip index of canvas column i is i - cx0; clamp(i) - k
+    //    stays inside [cx0, cx0 + cw).
+    for (int r = rg; r < nrows; r += kRowStep) {
         const float *Crow = Cs + r * cw_max - cx0;
         float *Brow = Bs + r * bw_max - bx0;
-        const int ib = bx0 + 4 * q4;
-        const int ic0 = clampi(ib, 0, Wr - 1), ic1 = clampi(ib + 1, 0, Wr - 1);
-        const int ic2 = clampi(ib + 2, 0, Wr - 1), ic3 = clampi(ib + 3, 0, Wr - 1);
-        if (ic3 - ic0 == 3) {       // interior: a sliding window shared by the four outputs
-            float a0 = gs[0] * Crow[ic0], a1 = gs[0] * Crow[ic0 + 1];
-            float a2 = gs[0] * Crow[ic0 + 2], a3 = gs[0] * Crow[ic0 + 3];
+        for (int ib0 = bx0 + c; ib0 <= bx1; ib0 += 4 * kChunk) {
+            const float *cp0 = Crow + clampi(ib0, 0, Wr - 1);
+            const float *cp1 = Crow + clampi(min(ib0 + kChunk, bx1), 0, Wr - 1);
+            const float *cp2 = Crow + clampi(min(ib0 + 2 * kChunk, bx1), 0, Wr - 1);
+            const float *cp3 = Crow + clampi(min(ib0 + 3 * kChunk, bx1), 0, Wr - 1);
+            const float g0 = gs[0];
+            float a0 = g0 * cp0[0], a1 = g0 * cp1[0], a2 = g0 * cp2[0], a3 = g0 * cp3[0];
+#pragma unroll 2
             for (int k = 1; k <= K; ++k) {
                 const float g = gs[k];
-                const float l0 = Crow[ic0 - k], l1 = Crow[ic0 + 1 - k], l2 = Crow[ic0 + 2 - k], l3 = Crow[ic0 + 3 - k];
-                const float h0 = Crow[ic0 + k], h1 = Crow[ic0 + 1 + k], h2 = Crow[ic0 + 2 + k], h3 = Crow[ic0 + 3 + k];
-                a0 = fmaf(g, l0 + h0, a0);
-                a1 = fmaf(g, l1 + h1, a1);
-                a2 = fmaf(g, l2 + h2, a2);
-                a3 = fmaf(g, l3 + h3, a3);
+                a0 = fmaf(g, cp0[-k] + cp0[k], a0);
+                a1 = fmaf(g, cp1[-k] + cp1[k], a1);
+                a2 = fmaf(g, cp2[-k] + cp2[k], a2);
+                a3 = fmaf(g, cp3[-k] + cp3[k], a3);
             }
-            Brow[ib] = a0;
-            if (ib + 1 <= bx1) Brow[ib + 1] = a1;
-            if (ib + 2 <= bx1) Brow[ib + 2] = a2;
-            if (ib + 3 <= bx1) Brow[ib + 3] = a3;
-        } else {                    // the canvas border: each output on its own
-            const int icq[4] = {ic0, ic1, ic2, ic3};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (ib + q > bx1) break;
-                const int ic = icq[q];
-                float a = gs[0] * Crow[ic];
-                for (int k = 1; k <= K; ++k) a = fmaf(gs[k], Crow[ic - k] + Crow[ic + k], a);
-                Brow[ib + q] = a;
-            }
+            Brow[ib0] = a0;
+            if (ib0 + kChunk <= bx1) Brow[ib0 + kChunk] = a1;
+            if (ib0 + 2 * kChunk <= bx1) Brow[ib0 + 2 * kChunk] = a2;
+            if (ib0 + 3 * kChunk <= bx1) Brow[ib0 + 3 * kChunk] = a3;
         }
     }
     __syncthreads();
 
-    // 3. tilt resampling, quantisation and the footprint mask
-    const int ncols = xb - xa + 1;
-    const long long mxlo = HALF, mxhi = (long long)(2 * W - 3) * HALF;
-    const long long mylo = HALF, myhi = (long long)(2 * H - 3) * HALF;
-    for (int e = threadIdx.x; e < nrows * ncols; e += blockDim.x) {
-        const int r = e / ncols, c = e - r * ncols;
-        const int x = xa + c, j = j0 + r;
+    // 3. tilt resampling, quantisation and the footprint mask.  The tilt
+    //    position and weights depend on the view column only.
+    if (xa + c <= xb) {
+        const int x = xa + c;
         const long long X = V.tq * (2LL * x - V.Wv + 1) + xoff;
         const int x0 = (int)(X >> 32);
         float w[6];
         lanczos3_weights((uint32_t)X, w);
-        const float *Brow = Bs + r * bw_max - bx0;
-        float v = 0.f;
+        for (int r = rg; r < nrows; r += kRowStep) {
+            const int j = j0 + r;
+            const float *Brow = Bs + r * bw_max - bx0;
+            float v = 0.f;
 #pragma unroll
-        for (int m = 0; m < 6; ++m) v = fmaf(w[m], Brow[x0 + m - 2], v);
-        int valid = 1;
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int i = x0 + q;
-            if (i < 0 || i >= Wr) { valid = 0; continue; }
-            long long px, py;
-            G.map(i, j, px, py);
-            valid &= (px >= mxlo && px <= mxhi && py >= mylo && py <= myhi);
+            for (int m = 0; m < 6; ++m) v = fmaf(w[m], Brow[x0 + m - 2], v);
+            const uint8_t *Mrow = Ms + r * cw_max - cx0;
+            const size_t o = (size_t)V.out_off + (size_t)j * V.Wv + x;
+            if (out_f32) out_f32[o] = v;
+            const int q8 = __float2int_rn(v);
+            out_u8[o] = (uint8_t)min(255, max(0, q8));
+            out_mask[o] = Mrow[x0] & Mrow[x0 + 1];
         }
-        const size_t o = (size_t)V.out_off + (size_t)j * V.Wv + x;
-        if (out_f32) out_f32[o] = v;
-        const int q8 = __float2int_rn(v);
-        out_u8[o] = (uint8_t)min(255, max(0, q8));
-        out_mask[o] = (uint8_t)valid;
     }
 }
 
@@ -307,7 +378,8 @@ void warp_strip_widths(const asift_view_desc &v, int *cw, int *bw)
 
 size_t warp_smem_bytes(int cw_max, int bw_max)
 {
-    return sizeof(float) * ((size_t)kWarpTH * (cw_max + bw_max) + (size_t)kStage * kStagePitch);
+    return sizeof(float) * ((size_t)kWarpTH * cw_max + std::max((size_t)kStage * kStagePitch, (size_t)kWarpTH * bw_max)) +
+           (size_t)kWarpTH * cw_max;
 }
 
 cudaError_t launch_u8_to_f32(const uint8_t *src, int pitch, int W, int H, float *dst, cudaStream_t s)
