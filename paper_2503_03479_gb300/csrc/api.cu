@@ -152,6 +152,12 @@ static void build_views(const asift_view_desc *h, int nv, const float *const *sr
         d.tq = a.tq;
         d.out_off = out_off[v];
         d.ntx = (a.Wv + kWarpTW - 1) / kWarpTW;
+        {
+            int lx = 32, pitch = 72;
+            warp_lane_layout(a.cq, a.sq, &lx, &pitch);
+            d.lanes_x = (int16_t)lx;
+            d.stage_pitch = (int16_t)pitch;
+        }
         d.tile_start = per_view ? 0 : tiles;
         tiles += d.ntx * ((a.Hv + kWarpTH - 1) / kWarpTH);
         d.t = a.t;

@@ -21,7 +21,8 @@ struct DevView {
     int32_t Wr, Hr, Wv, Hv, K;
     int32_t tile_start;     // first linear tile of this view in the launch
     int32_t ntx;            // tiles along x
-    int32_t pad;
+    int16_t lanes_x;        // canvas columns of a warp's footprint in the rotation step (32, 16 or 8)
+    int16_t stage_pitch;    // row pitch (floats) of the staged source box
     long long cq, sq, tq;   // Q31 cos, sin, tilt
     long long out_off;      // byte offset of the view in the u8 / mask arenas
     double cosd, sind, t;   // fp64 geometry for back-projection

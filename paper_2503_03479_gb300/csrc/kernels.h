@@ -16,6 +16,7 @@ struct SlotKp;
 
 // warp.cu
 void warp_strip_widths(const asift_view_desc &v, int *cw, int *bw);
+void warp_lane_layout(long long cq, long long sq, int *lanes_x, int *pitch);
 cudaError_t launch_u8_to_f32(const uint8_t *src, int pitch, int W, int H, float *dst, cudaStream_t s);
 struct ImageConv;
 cudaError_t launch_convert_images(const ImageConv *d_list, int n, long long max_px, cudaStream_t s);

@@ -24,6 +24,9 @@
 // Every launch covers a list of views (one view for the per-view form, all
 // views of several images for the batched form); a CTA finds its view by a
 // binary search over the views' first tile index.
+#include <map>
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -31,7 +34,8 @@ namespace asift {
 
 constexpr int kChunk = 64;              // canvas columns per staged chunk
 constexpr int kStage = 72;              // staged source box (rows, columns), >= 64|c| + 16|s| + 6
-constexpr int kStagePitch = kStage + 1; // odd pitch
+constexpr int kPitchMin = 72, kPitchMax = 80;   // row pitch of the staged box, chosen per view
+constexpr int kStageBuf = kStage * kPitchMax;   // floats per staging buffer (two, double-buffered)
 
 // sin and cos on [0, pi/3] from their Taylor series (truncation below 5e-8).
 __device__ __forceinline__ void sincos_small(float x, float &s, float &c)
@@ -161,16 +165,16 @@ struct CanvasGeom {           // Q32 map of canvas (i, j) to the source point
 // The 36-tap interpolation of the staged source at the Q32 point (px, py),
 // all taps inside the staged box; the x and y weight sets are computed
 // together in packed fp32 pairs.
-__device__ __forceinline__ float interp_interior(const float *__restrict__ Ss, long long px, long long py, int sx0,
-                                                 int sy0)
+__device__ __forceinline__ float interp_interior(const float *__restrict__ Ss, int P, long long px, long long py,
+                                                 int sx0, int sy0)
 {
     float2 w[6];
     lanczos3_weights2((uint32_t)px, (uint32_t)py, w);
-    const float *b = Ss + ((int)(py >> 32) - 2 - sy0) * kStagePitch + ((int)(px >> 32) - 2 - sx0);
+    const float *b = Ss + ((int)(py >> 32) - 2 - sy0) * P + ((int)(px >> 32) - 2 - sx0);
     float rs[6];
 #pragma unroll
     for (int n = 0; n < 6; ++n) {
-        const float *row = b + n * kStagePitch;
+        const float *row = b + n * P;
         rs[n] = fmaf(w[0].x, row[0], fmaf(w[1].x, row[1], fmaf(w[2].x, row[2],
                 fmaf(w[3].x, row[3], fmaf(w[4].x, row[4], w[5].x * row[5])))));
     }
@@ -178,19 +182,71 @@ __device__ __forceinline__ float interp_interior(const float *__restrict__ Ss, l
            fmaf(w[3].y, rs[3], fmaf(w[4].y, rs[4], w[5].y * rs[5])))));
 }
 
+__device__ __forceinline__ void cp_async4(float *dst, const float *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Source box of one chunk of the canvas strip: the taps of the four corners
+// of the (clamped) canvas region, clamped to the image.  interior: every tap
+// of every point of the chunk lies inside the image (the points lie in the
+// corners' convex hull), so no clamps and no background test are needed.
+struct StageBox {
+    int sx0, sy0, bwid, bhgt;
+    bool interior;
+};
+
+__device__ __forceinline__ StageBox chunk_box(const CanvasGeom &G, int i_lo, int i_hi, int j0, int j1, int W, int H)
+{
+    int sx0 = 1 << 30, sx1 = -(1 << 30), sy0 = 1 << 30, sy1 = -(1 << 30);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        long long px, py;
+        G.map(q & 1 ? i_hi : i_lo, q & 2 ? j1 : j0, px, py);
+        sx0 = min(sx0, (int)(px >> 32));
+        sx1 = max(sx1, (int)(px >> 32));
+        sy0 = min(sy0, (int)(py >> 32));
+        sy1 = max(sy1, (int)(py >> 32));
+    }
+    StageBox b;
+    b.interior = sx0 >= 2 && sx1 + 3 <= W - 1 && sy0 >= 2 && sy1 + 3 <= H - 1;
+    b.sx0 = clampi(sx0 - 2, 0, W - 1);
+    b.sy0 = clampi(sy0 - 2, 0, H - 1);
+    // a chunk spans at most 63 columns and 15 rows of the canvas, so the box
+    // spans at most sqrt(63^2 + 15^2) + 1 + 5 < 72 = kStage source pixels
+    b.bwid = clampi(sx1 + 3, 0, W - 1) - b.sx0 + 1;
+    b.bhgt = clampi(sy1 + 3, 0, H - 1) - b.sy0 + 1;
+    return b;
+}
+
+// Issues the asynchronous copies of a box into a staging buffer (pitch P).
+__device__ __forceinline__ void stage_box(float *dst, int P, const float *__restrict__ src, int sp, const StageBox &b,
+                                          unsigned warp, unsigned lane)
+{
+    for (int r = warp; r < b.bhgt; r += kWarpThreads / 32) {
+        const float *srow = src + (size_t)(b.sy0 + r) * sp + b.sx0;
+        for (int cc = lane; cc < b.bwid; cc += 32) cp_async4(dst + r * P + cc, srow + cc);
+    }
+}
+
 __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restrict__ views, int n_views, int cw_max,
                                                int bw_max, uint8_t *__restrict__ out_u8,
                                                uint8_t *__restrict__ out_mask, float *__restrict__ out_f32)
 {
-    extern __shared__ float smem[];
-    // Cs [kWarpTH][cw_max] canvas strip, then one region that holds the staged
-    // source [kStage][kStagePitch] in step 1 and the blurred strip Bs
-    // [kWarpTH][bw_max] in steps 2-3, then the footprint mask Ms.
+    extern __shared__ float4 smem4[];
+    float *smem = reinterpret_cast<float *>(smem4);
+    // Cs [kWarpTH][cw_max] canvas strip, then one region that holds the two
+    // staging buffers [kStage][pitch] in step 1 and the blurred strip Bs
+    // [kWarpTH][bw_max] in steps 2-3.
     float *Cs = smem;
-    float *Ss = Cs + kWarpTH * cw_max;
-    float *Bs = Ss;
-    uint8_t *Ms = reinterpret_cast<uint8_t *>(Ss + max(kStage * kStagePitch, kWarpTH * bw_max));
-    __shared__ float gs[ASIFT_MAX_GAUSS];
+    float *Sbuf = Cs + kWarpTH * cw_max;
+    float *Bs = Sbuf;
+    __shared__ float4 gs4[ASIFT_MAX_GAUSS / 4];
 
     const int vi = find_owner(views, n_views, tile, [](const DevView &v) { return v.tile_start; });
     const DevView &V = views[vi];
@@ -208,149 +264,177 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
     const long long Xb = V.tq * (2LL * xb - V.Wv + 1) + xoff;
     const int bx0 = (int)(Xa >> 32) - 2, bx1 = (int)(Xb >> 32) + 3;   // unclamped strip of B
     const int bw = bx1 - bx0 + 1;
-    const int cx0 = bx0 - K;                // strip of C: [cx0, cx0 + cw), covering the Gaussian
-    const int cw = ((bw + 3) & ~3) + 2 * K;
+    const int K4 = (K + 3) & ~3;            // taps in blocks of four (zero weights past K)
+    const int cx0 = bx0 - K4;               // strip of C: [cx0, cx0 + cw), covering the Gaussian
+    const int cw = ((bw + 3) & ~3) + 2 * K4;
 
-    for (int k = threadIdx.x; k <= K; k += blockDim.x) gs[k] = V.g[k];
+    // gs4[q] = (g_{4q+1}, .., g_{4q+4}), zero past K; g_0 apart
+    float *gsh = reinterpret_cast<float *>(gs4);
+    for (int k = threadIdx.x; k < K4; k += blockDim.x) gsh[k] = k < K ? V.g[k + 1] : 0.f;
+    const float g0 = V.g[0];
 
-    // Thread layout of all three phases: column c of 64, rows rg, rg + 4, ...
-    // so a warp covers 32 consecutive columns of one row.
-    const int c = threadIdx.x & (kChunk - 1);
-    const int rg = threadIdx.x / kChunk;
-    constexpr int kRowStep = kWarpThreads / kChunk;
-
-    // 1. rotated canvas strip and its footprint mask, chunk by chunk through
-    //    shared memory.  Moving down kRowStep canvas rows adds
-    //    2 kRowStep (sq, cq) to the Q32 source point.
-    const float *__restrict__ src = V.src;
-    const int sp = V.src_pitch;
-    const long long xlim = (long long)(2 * W - 1) * HALF, ylim = (long long)(2 * H - 1) * HALF;
-    const long long mxlo = HALF, mxhi = (long long)(2 * W - 3) * HALF;
-    const long long mylo = HALF, myhi = (long long)(2 * H - 3) * HALF;
-    const long long dpx = 2LL * kRowStep * V.sq, dpy = 2LL * kRowStep * V.cq;
     const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    for (int c0 = 0; c0 < cw; c0 += kChunk) {
-        const int cn = min(kChunk, cw - c0);
-        // source box of this chunk: the taps of the four corners of the
-        // (clamped) canvas region
-        const int i_lo = clampi(cx0 + c0, 0, Wr - 1), i_hi = clampi(cx0 + c0 + cn - 1, 0, Wr - 1);
-        int sx0 = 1 << 30, sx1 = -(1 << 30), sy0 = 1 << 30, sy1 = -(1 << 30);
+    constexpr int kRowStep = kWarpThreads / kChunk;   // a thread walks its column in steps of 4 rows
+
+    // 1. rotated canvas strip, chunk by chunk: the source box of chunk k + 1
+    //    is copied asynchronously into one staging buffer while chunk k is
+    //    computed from the other.  A warp covers a lanes_x x (32 / lanes_x)
+    //    block of the chunk (the shape and the staging pitch are chosen per
+    //    view to spread its taps over the shared-memory banks); every thread
+    //    walks down one canvas column, where moving kRowStep rows adds
+    //    2 kRowStep (sq, cq) to the Q32 source point.
+    {
+        const float *__restrict__ src = V.src;
+        const int sp = V.src_pitch, P = V.stage_pitch, ax = V.lanes_x;
+        const int cpb = kChunk / ax;
+        const int c = (int)(warp % cpb) * ax + (int)(lane % ax);
+        const int rg = (int)(warp / cpb) * (32 / ax) + (int)(lane / ax);
+        const long long xlim = (long long)(2 * W - 1) * HALF, ylim = (long long)(2 * H - 1) * HALF;
+        const long long dpx = 2LL * kRowStep * V.sq, dpy = 2LL * kRowStep * V.cq;
+        const int nch = (cw + kChunk - 1) / kChunk;
+        auto box_of = [&](int k) {
+            const int c0 = k * kChunk, cn = min(kChunk, cw - c0);
+            return chunk_box(G, clampi(cx0 + c0, 0, Wr - 1), clampi(cx0 + c0 + cn - 1, 0, Wr - 1), j0, j1, W, H);
+        };
+        StageBox bx = box_of(0);
+        stage_box(Sbuf, P, src, sp, bx, warp, lane);
+        cp_async_commit();
+        for (int k = 0; k < nch; ++k) {
+            StageBox nb = bx;
+            if (k + 1 < nch) {
+                nb = box_of(k + 1);
+                stage_box(Sbuf + ((k + 1) & 1) * kStageBuf, P, src, sp, nb, warp, lane);
+            }
+            cp_async_commit();
+            cp_async_wait<1>();      // this thread's copies of chunk k have landed
+            __syncthreads();         // and everyone's
+            const float *Ss = Sbuf + (k & 1) * kStageBuf;
+            const int c0 = k * kChunk, cn = min(kChunk, cw - c0);
+            if (c < cn) {
+                const int i = clampi(cx0 + c0 + c, 0, Wr - 1);   // strip position -> canvas column (clamped)
+                long long px, py;
+                G.map(i, j0 + rg, px, py);
+                float *Cp = Cs + c0 + c;
+                if (bx.interior) {
+                    for (int r = rg; r < nrows; r += kRowStep, px += dpx, py += dpy)
+                        Cp[r * cw_max] = interp_interior(Ss, P, px, py, bx.sx0, bx.sy0);
+                } else {
+                    for (int r = rg; r < nrows; r += kRowStep, px += dpx, py += dpy) {
+                        float acc = 0.f;
+                        if (px >= -HALF && px < xlim && py >= -HALF && py < ylim) {
+                            float2 w[6];
+                            lanczos3_weights2((uint32_t)px, (uint32_t)py, w);
+                            const int x0 = (int)(px >> 32), y0 = (int)(py >> 32);
+                            int xs[6];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            long long px, py;
-            G.map(q & 1 ? i_hi : i_lo, q & 2 ? j1 : j0, px, py);
-            sx0 = min(sx0, (int)(px >> 32));
-            sx1 = max(sx1, (int)(px >> 32));
-            sy0 = min(sy0, (int)(py >> 32));
-            sy1 = max(sy1, (int)(py >> 32));
-        }
-        // all taps of all points inside the image: no clamps, no background
-        // (the points lie in the corners' convex hull)
-        const bool interior = sx0 >= 2 && sx1 + 3 <= W - 1 && sy0 >= 2 && sy1 + 3 <= H - 1;
-        sx0 = clampi(sx0 - 2, 0, W - 1);
-        sx1 = clampi(sx1 + 3, 0, W - 1);
-        sy0 = clampi(sy0 - 2, 0, H - 1);
-        sy1 = clampi(sy1 + 3, 0, H - 1);
-        // a chunk spans at most 63 columns and 15 rows of the canvas, so the
-        // box spans at most sqrt(63^2 + 15^2) + 1 + 5 < 72 = kStage source pixels
-        const int bwid = sx1 - sx0 + 1, bhgt = sy1 - sy0 + 1;
-        __syncthreads();   // previous chunk's reads of Ss are done
-        for (int r = warp; r < bhgt; r += kWarpThreads / 32) {
-            const float *srow = src + (size_t)(sy0 + r) * sp + sx0;
-            for (int cc = lane; cc < bwid; cc += 32) Ss[r * kStagePitch + cc] = __ldg(srow + cc);
-        }
-        __syncthreads();
-        if (c < cn) {
-            const int iu = cx0 + c0 + c;                 // strip position -> canvas column (clamped)
-            const int i = clampi(iu, 0, Wr - 1);
-            const uint8_t col_ok = iu == i;
-            long long px, py;
-            G.map(i, j0 + rg, px, py);
-            float *Cp = Cs + c0 + c;
-            uint8_t *Mp = Ms + c0 + c;
-            if (interior) {
-                for (int r = rg; r < nrows; r += kRowStep, px += dpx, py += dpy) {
-                    Cp[r * cw_max] = interp_interior(Ss, px, py, sx0, sy0);
-                    Mp[r * cw_max] = col_ok;
-                }
-            } else {
-                for (int r = rg; r < nrows; r += kRowStep, px += dpx, py += dpy) {
-                    float acc = 0.f;
-                    if (px >= -HALF && px < xlim && py >= -HALF && py < ylim) {
-                        float2 w[6];
-                        lanczos3_weights2((uint32_t)px, (uint32_t)py, w);
-                        const int x0 = (int)(px >> 32), y0 = (int)(py >> 32);
-                        int xs[6];
+                            for (int m = 0; m < 6; ++m) xs[m] = clampi(x0 + m - 2, 0, W - 1) - bx.sx0;
 #pragma unroll
-                        for (int m = 0; m < 6; ++m) xs[m] = clampi(x0 + m - 2, 0, W - 1) - sx0;
+                            for (int n = 0; n < 6; ++n) {
+                                const float *row = Ss + (clampi(y0 + n - 2, 0, H - 1) - bx.sy0) * P;
+                                float a = 0.f;
 #pragma unroll
-                        for (int n = 0; n < 6; ++n) {
-                            const float *row = Ss + (clampi(y0 + n - 2, 0, H - 1) - sy0) * kStagePitch;
-                            float a = 0.f;
-#pragma unroll
-                            for (int m = 0; m < 6; ++m) a = fmaf(w[m].x, row[xs[m]], a);
-                            acc = fmaf(w[n].y, a, acc);
+                                for (int m = 0; m < 6; ++m) a = fmaf(w[m].x, row[xs[m]], a);
+                                acc = fmaf(w[n].y, a, acc);
+                            }
                         }
+                        Cp[r * cw_max] = acc;
                     }
-                    Cp[r * cw_max] = acc;
-                    Mp[r * cw_max] = col_ok & (uint8_t)(px >= mxlo && px <= mxhi && py >= mylo && py <= myhi);
                 }
             }
+            __syncthreads();         // buffer k & 1 is free for chunk k + 2
+            bx = nb;
         }
+        cp_async_wait<0>();
     }
-    __syncthreads();
 
     // 2. Gaussian along canvas x: B(i) = sum_k g_|k| C(clamp(i) - k).  A lane
-    //    computes up to four outputs kChunk apart, so a warp reads 32
-    //    consecutive C values per tap and output and each g_k load serves
-    //    four sums.  Strip index of canvas column i is i - cx0; clamp(i) - k
-    //    stays inside [cx0, cx0 + cw).
-    for (int r = rg; r < nrows; r += kRowStep) {
-        const float *Crow = Cs + r * cw_max - cx0;
-        float *Brow = Bs + r * bw_max - bx0;
-        for (int ib0 = bx0 + c; ib0 <= bx1; ib0 += 4 * kChunk) {
-            const float *cp0 = Crow + clampi(ib0, 0, Wr - 1);
-            const float *cp1 = Crow + clampi(min(ib0 + kChunk, bx1), 0, Wr - 1);
-            const float *cp2 = Crow + clampi(min(ib0 + 2 * kChunk, bx1), 0, Wr - 1);
-            const float *cp3 = Crow + clampi(min(ib0 + 3 * kChunk, bx1), 0, Wr - 1);
-            const float g0 = gs[0];
-            float a0 = g0 * cp0[0], a1 = g0 * cp1[0], a2 = g0 * cp2[0], a3 = g0 * cp3[0];
-#pragma unroll 2
-            for (int k = 1; k <= K; ++k) {
-                const float g = gs[k];
-                a0 = fmaf(g, cp0[-k] + cp0[k], a0);
-                a1 = fmaf(g, cp1[-k] + cp1[k], a1);
-                a2 = fmaf(g, cp2[-k] + cp2[k], a2);
-                a3 = fmaf(g, cp3[-k] + cp3[k], a3);
+    //    computes four consecutive outputs i0..i0+3 (strip index of i0 a
+    //    multiple of 4): taps go in blocks of four, each block needing one
+    //    new aligned float4 of C on either side, kept in a sliding register
+    //    window (lanes read consecutive 16-byte words).  Groups whose centres
+    //    would be clamped (the canvas border) take one output at a time.
+    //    Strip index of canvas column i is i - cx0; clamp(i) - k stays inside
+    //    [cx0, cx0 + cw).
+    {
+        const int ng = (bw + 3) >> 2;
+        for (int e = threadIdx.x; e < nrows * ng; e += blockDim.x) {
+            const int r = e / ng, gi = e - r * ng;
+            const int i0 = bx0 + 4 * gi;
+            const float *Crow = Cs + r * cw_max - cx0;
+            float *Brow = Bs + r * bw_max - bx0;
+            if (i0 >= 0 && i0 + 3 <= Wr - 1) {
+                const float4 *cq = reinterpret_cast<const float4 *>(Crow + i0);   // 16-byte aligned
+                const float4 cen = cq[0];
+                float4 a = make_float4(g0 * cen.x, g0 * cen.y, g0 * cen.z, g0 * cen.w);
+                float4 lp = cen, rp = cen;
+                for (int kb = 0; kb < K4; kb += 4) {
+                    const float4 ln = cq[-(kb >> 2) - 1];      // C[i0-kb-4 .. i0-kb-1]
+                    const float4 rn = cq[(kb >> 2) + 1];       // C[i0+kb+4 .. i0+kb+7]
+                    const float4 g = gs4[kb >> 2];
+                    // window L = (ln, lp) holds C[i0-kb-4+u], R = (rp, rn) holds C[i0+kb+u], u = 0..7
+                    const float L[8] = {ln.x, ln.y, ln.z, ln.w, lp.x, lp.y, lp.z, lp.w};
+                    const float R[8] = {rp.x, rp.y, rp.z, rp.w, rn.x, rn.y, rn.z, rn.w};
+                    const float gt[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+                    for (int t = 1; t <= 4; ++t) {          // tap k = kb + t
+                        a.x = fmaf(gt[t - 1], L[4 - t] + R[t], a.x);
+                        a.y = fmaf(gt[t - 1], L[5 - t] + R[1 + t], a.y);
+                        a.z = fmaf(gt[t - 1], L[6 - t] + R[2 + t], a.z);
+                        a.w = fmaf(gt[t - 1], L[7 - t] + R[3 + t], a.w);
+                    }
+                    lp = ln;
+                    rp = rn;
+                }
+                *reinterpret_cast<float4 *>(Brow + i0) = a;   // outputs past bx1 stay in the row, unread
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int i = i0 + q;
+                    if (i > bx1) break;
+                    const float *cp = Crow + clampi(i, 0, Wr - 1);
+                    float a = g0 * cp[0];
+                    for (int k = 1; k <= K; ++k) a = fmaf(gsh[k - 1], cp[-k] + cp[k], a);
+                    Brow[i] = a;
+                }
             }
-            Brow[ib0] = a0;
-            if (ib0 + kChunk <= bx1) Brow[ib0 + kChunk] = a1;
-            if (ib0 + 2 * kChunk <= bx1) Brow[ib0 + 2 * kChunk] = a2;
-            if (ib0 + 3 * kChunk <= bx1) Brow[ib0 + 3 * kChunk] = a3;
         }
     }
     __syncthreads();
 
-    // 3. tilt resampling, quantisation and the footprint mask.  The tilt
-    //    position and weights depend on the view column only.
-    if (xa + c <= xb) {
-        const int x = xa + c;
-        const long long X = V.tq * (2LL * x - V.Wv + 1) + xoff;
-        const int x0 = (int)(X >> 32);
-        float w[6];
-        lanczos3_weights((uint32_t)X, w);
-        for (int r = rg; r < nrows; r += kRowStep) {
-            const int j = j0 + r;
-            const float *Brow = Bs + r * bw_max - bx0;
-            float v = 0.f;
+    // 3. tilt resampling, quantisation and the footprint mask.  Thread =
+    //    view column (tilt position and weights fixed) walking down its rows;
+    //    the mask needs canvas columns x0 and x0 + 1 inside the canvas and
+    //    their source points inside the shrunk footprint, tracked in Q32 as
+    //    in step 1.
+    {
+        const int c = threadIdx.x & (kChunk - 1), rg = threadIdx.x / kChunk;
+        if (xa + c <= xb) {
+            const int x = xa + c;
+            const long long X = V.tq * (2LL * x - V.Wv + 1) + xoff;
+            const int x0 = (int)(X >> 32);
+            float w[6];
+            lanczos3_weights((uint32_t)X, w);
+            const long long mxlo = HALF, mxhi = (long long)(2 * W - 3) * HALF;
+            const long long mylo = HALF, myhi = (long long)(2 * H - 3) * HALF;
+            const long long dpx = 2LL * kRowStep * V.sq, dpy = 2LL * kRowStep * V.cq;
+            const bool cols_ok = x0 >= 0 && x0 + 1 <= Wr - 1;
+            long long pxa, pya, pxb, pyb;
+            G.map(clampi(x0, 0, Wr - 1), j0 + rg, pxa, pya);
+            G.map(clampi(x0 + 1, 0, Wr - 1), j0 + rg, pxb, pyb);
+            for (int r = rg; r < nrows; r += kRowStep, pxa += dpx, pya += dpy, pxb += dpx, pyb += dpy) {
+                const int j = j0 + r;
+                const float *Brow = Bs + r * bw_max - bx0;
+                float v = 0.f;
 #pragma unroll
-            for (int m = 0; m < 6; ++m) v = fmaf(w[m], Brow[x0 + m - 2], v);
-            const uint8_t *Mrow = Ms + r * cw_max - cx0;
-            const size_t o = (size_t)V.out_off + (size_t)j * V.Wv + x;
-            if (out_f32) out_f32[o] = v;
-            const int q8 = __float2int_rn(v);
-            out_u8[o] = (uint8_t)min(255, max(0, q8));
-            out_mask[o] = Mrow[x0] & Mrow[x0 + 1];
+                for (int m = 0; m < 6; ++m) v = fmaf(w[m], Brow[x0 + m - 2], v);
+                const bool valid = cols_ok && pxa >= mxlo && pxa <= mxhi && pya >= mylo && pya <= myhi &&
+                                   pxb >= mxlo && pxb <= mxhi && pyb >= mylo && pyb <= myhi;
+                const size_t o = (size_t)V.out_off + (size_t)j * V.Wv + x;
+                if (out_f32) out_f32[o] = v;
+                const int q8 = __float2int_rn(v);
+                out_u8[o] = (uint8_t)min(255, max(0, q8));
+                out_mask[o] = (uint8_t)valid;
+            }
         }
     }
 }
@@ -370,16 +454,83 @@ warp_view_kernel(int n_tiles, const DevView *__restrict__ views, int n_views, in
 void warp_strip_widths(const asift_view_desc &v, int *cw, int *bw)
 {
     // B strip: floor(X) - 2 .. floor(X) + 3 over kWarpTW view columns spaced
-    // t apart (+1 for the rounding of tq); C strip adds K on both sides.
+    // t apart (+1 for the rounding of tq), rounded up to whole groups of four;
+    // C strip adds K rounded up to a multiple of 4 on both sides.
     const int span = (int)std::ceil(v.t * (kWarpTW - 1)) + 2;
-    *bw = span + 6;
-    *cw = ((*bw + 3) & ~3) + 2 * v.K;
+    *bw = ((span + 6) + 3) & ~3;
+    *cw = *bw + 2 * ((v.K + 3) & ~3);
 }
 
 size_t warp_smem_bytes(int cw_max, int bw_max)
 {
-    return sizeof(float) * ((size_t)kWarpTH * cw_max + std::max((size_t)kStage * kStagePitch, (size_t)kWarpTH * bw_max)) +
-           (size_t)kWarpTH * cw_max;
+    return sizeof(float) * ((size_t)kWarpTH * cw_max + std::max((size_t)2 * kStageBuf, (size_t)kWarpTH * bw_max));
+}
+
+// The rotation step's warp footprint (lanes_x canvas columns x 32 / lanes_x
+// rows) and staging pitch for a rotation (cq, sq): the pair whose 32 tap
+// base addresses fall on the fewest distinct addresses per shared-memory bank
+// (the worst bank decides a load's wavefronts), averaged over 64 sub-pixel
+// offsets of the footprint.  Ties go to the smaller pitch, then wider rows.
+static void lane_layout_search(long long cq, long long sq, int *lanes_x, int *pitch)
+{
+    const double c = (double)cq / 2147483648.0, s = (double)sq / 2147483648.0;
+    double best = 1e30;
+    *lanes_x = 32;
+    *pitch = kPitchMin;
+    for (int ax : {32, 16, 8}) {
+        for (int P = kPitchMin; P <= kPitchMax; ++P) {
+            double tot = 0.0;
+            for (int o = 0; o < 64; ++o) {
+                const double ox = ((o & 7) + 0.5) / 8.0, oy = ((o >> 3) + 0.5) / 8.0;
+                long long addr[32];
+                for (int L = 0; L < 32; ++L) {
+                    const int di = L % ax, dj = L / ax;
+                    const long long x = (long long)std::floor(c * di + s * dj + ox);
+                    const long long y = (long long)std::floor(-s * di + c * dj + oy);
+                    addr[L] = y * P + x;
+                }
+                int worst = 0;
+                for (int b = 0; b < 32; ++b) {
+                    long long seen[32];
+                    int n = 0;
+                    for (int L = 0; L < 32; ++L) {
+                        if ((((addr[L] % 32) + 32) % 32) != b) continue;
+                        bool dup = false;
+                        for (int q = 0; q < n; ++q) dup |= seen[q] == addr[L];
+                        if (!dup) seen[n++] = addr[L];
+                    }
+                    worst = std::max(worst, n);
+                }
+                tot += worst;
+            }
+            if (tot < best - 1e-9) {
+                best = tot;
+                *lanes_x = ax;
+                *pitch = P;
+            }
+        }
+    }
+}
+
+// The search is memoised by rotation: view tables repeat the same few dozen
+// angles for every image.
+void warp_lane_layout(long long cq, long long sq, int *lanes_x, int *pitch)
+{
+    static std::mutex mu;
+    static std::map<std::pair<long long, long long>, std::pair<int, int>> memo;
+    const auto key = std::make_pair(cq, sq);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        const auto it = memo.find(key);
+        if (it != memo.end()) {
+            *lanes_x = it->second.first;
+            *pitch = it->second.second;
+            return;
+        }
+    }
+    lane_layout_search(cq, sq, lanes_x, pitch);
+    std::lock_guard<std::mutex> lock(mu);
+    memo.emplace(key, std::make_pair(*lanes_x, *pitch));
 }
 
 cudaError_t launch_u8_to_f32(const uint8_t *src, int pitch, int W, int H, float *dst, cudaStream_t s)
