@@ -182,12 +182,6 @@ __device__ __forceinline__ float interp_interior(const float *__restrict__ Ss, i
            fmaf(w[3].y, rs[3], fmaf(w[4].y, rs[4], w[5].y * rs[5])))));
 }
 
-__device__ __forceinline__ void cp_async4(float *dst, const float *src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-                 "l"(src)
-                 : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -196,25 +190,36 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // of the (clamped) canvas region, clamped to the image.  interior: every tap
 // of every point of the chunk lies inside the image (the points lie in the
 // corners' convex hull), so no clamps and no background test are needed.
+// outside: every point lies outside [-1/2, W-1/2) x [-1/2, H-1/2) (all four
+// corners beyond one edge), so the chunk is background.  Lanes 0..3 of each
+// warp map one corner each and the warp reduces them with shuffles.
 struct StageBox {
     int sx0, sy0, bwid, bhgt;
-    bool interior;
+    bool interior, outside;
 };
 
-__device__ __forceinline__ StageBox chunk_box(const CanvasGeom &G, int i_lo, int i_hi, int j0, int j1, int W, int H)
+__device__ __forceinline__ StageBox chunk_box(const CanvasGeom &G, int i_lo, int i_hi, int j0, int j1, int W, int H,
+                                              unsigned lane)
 {
-    int sx0 = 1 << 30, sx1 = -(1 << 30), sy0 = 1 << 30, sy1 = -(1 << 30);
+    const int q = lane & 3;
+    long long px, py;
+    G.map(q & 1 ? i_hi : i_lo, q & 2 ? j1 : j0, px, py);
+    int fx = (int)(px >> 32), fy = (int)(py >> 32);
+    const long long HALF = 2147483648LL;
+    unsigned side = (px < -HALF ? 1u : 0u) | (px >= (long long)(2 * W - 1) * HALF ? 2u : 0u) |
+                    (py < -HALF ? 4u : 0u) | (py >= (long long)(2 * H - 1) * HALF ? 8u : 0u);
+    int sx0 = fx, sx1 = fx, sy0 = fy, sy1 = fy;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        long long px, py;
-        G.map(q & 1 ? i_hi : i_lo, q & 2 ? j1 : j0, px, py);
-        sx0 = min(sx0, (int)(px >> 32));
-        sx1 = max(sx1, (int)(px >> 32));
-        sy0 = min(sy0, (int)(py >> 32));
-        sy1 = max(sy1, (int)(py >> 32));
+    for (int o = 1; o <= 2; o <<= 1) {
+        sx0 = min(sx0, __shfl_xor_sync(0xffffffffu, sx0, o));
+        sx1 = max(sx1, __shfl_xor_sync(0xffffffffu, sx1, o));
+        sy0 = min(sy0, __shfl_xor_sync(0xffffffffu, sy0, o));
+        sy1 = max(sy1, __shfl_xor_sync(0xffffffffu, sy1, o));
+        side &= __shfl_xor_sync(0xffffffffu, side, o);
     }
     StageBox b;
     b.interior = sx0 >= 2 && sx1 + 3 <= W - 1 && sy0 >= 2 && sy1 + 3 <= H - 1;
+    b.outside = side != 0u;
     b.sx0 = clampi(sx0 - 2, 0, W - 1);
     b.sy0 = clampi(sy0 - 2, 0, H - 1);
     // a chunk spans at most 63 columns and 15 rows of the canvas, so the box
@@ -224,13 +229,21 @@ __device__ __forceinline__ StageBox chunk_box(const CanvasGeom &G, int i_lo, int
     return b;
 }
 
-// Issues the asynchronous copies of a box into a staging buffer (pitch P).
+// Issues the asynchronous copies of a box into a staging buffer (pitch P):
+// warp w copies rows w, w + 8, ..., lane l columns l, l + 32, ...
 __device__ __forceinline__ void stage_box(float *dst, int P, const float *__restrict__ src, int sp, const StageBox &b,
                                           unsigned warp, unsigned lane)
 {
-    for (int r = warp; r < b.bhgt; r += kWarpThreads / 32) {
-        const float *srow = src + (size_t)(b.sy0 + r) * sp + b.sx0;
-        for (int cc = lane; cc < b.bwid; cc += 32) cp_async4(dst + r * P + cc, srow + cc);
+    if (b.outside) return;
+    const float *srow = src + (size_t)(b.sy0 + (int)warp) * sp + b.sx0 + lane;
+    uint32_t drow = (uint32_t)__cvta_generic_to_shared(dst + (int)warp * P + (int)lane);
+    const size_t sstep = (size_t)(kWarpThreads / 32) * sp;
+    const uint32_t dstep = (uint32_t)((kWarpThreads / 32) * P * 4);
+    const int ncol = b.bwid - (int)lane;             // columns this lane copies: lane, lane + 32, ... < bwid
+    for (int r = warp; r < b.bhgt; r += kWarpThreads / 32, srow += sstep, drow += dstep) {
+        for (int cc = 0; cc < ncol; cc += 32)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(drow + 4u * cc), "l"(srow + cc)
+                         : "memory");
     }
 }
 
@@ -294,7 +307,8 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
         const int nch = (cw + kChunk - 1) / kChunk;
         auto box_of = [&](int k) {
             const int c0 = k * kChunk, cn = min(kChunk, cw - c0);
-            return chunk_box(G, clampi(cx0 + c0, 0, Wr - 1), clampi(cx0 + c0 + cn - 1, 0, Wr - 1), j0, j1, W, H);
+            return chunk_box(G, clampi(cx0 + c0, 0, Wr - 1), clampi(cx0 + c0 + cn - 1, 0, Wr - 1), j0, j1, W, H,
+                             lane);
         };
         StageBox bx = box_of(0);
         stage_box(Sbuf, P, src, sp, bx, warp, lane);
@@ -315,16 +329,20 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
                 long long px, py;
                 G.map(i, j0 + rg, px, py);
                 float *Cp = Cs + c0 + c;
-                if (bx.interior) {
+                if (bx.outside) {
+                    for (int r = rg; r < nrows; r += kRowStep) Cp[r * cw_max] = 0.f;
+                } else if (bx.interior) {
                     for (int r = rg; r < nrows; r += kRowStep, px += dpx, py += dpy)
                         Cp[r * cw_max] = interp_interior(Ss, P, px, py, bx.sx0, bx.sy0);
                 } else {
                     for (int r = rg; r < nrows; r += kRowStep, px += dpx, py += dpy) {
                         float acc = 0.f;
-                        if (px >= -HALF && px < xlim && py >= -HALF && py < ylim) {
+                        const int x0 = (int)(px >> 32), y0 = (int)(py >> 32);
+                        if (x0 >= 2 && x0 + 3 <= W - 1 && y0 >= 2 && y0 + 3 <= H - 1) {
+                            acc = interp_interior(Ss, P, px, py, bx.sx0, bx.sy0);
+                        } else if (px >= -HALF && px < xlim && py >= -HALF && py < ylim) {
                             float2 w[6];
                             lanczos3_weights2((uint32_t)px, (uint32_t)py, w);
-                            const int x0 = (int)(px >> 32), y0 = (int)(py >> 32);
                             int xs[6];
 #pragma unroll
                             for (int m = 0; m < 6; ++m) xs[m] = clampi(x0 + m - 2, 0, W - 1) - bx.sx0;
@@ -357,8 +375,9 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
     //    [cx0, cx0 + cw).
     {
         const int ng = (bw + 3) >> 2;
-        for (int e = threadIdx.x; e < nrows * ng; e += blockDim.x) {
-            const int r = e / ng, gi = e - r * ng;
+        const int dr = kWarpThreads / ng, dg = kWarpThreads - dr * ng;   // stride kWarpThreads in (r, gi)
+        int r = (int)threadIdx.x / ng, gi = (int)threadIdx.x - r * ng;
+        for (; r < nrows; r += dr, gi += dg, r += gi >= ng ? 1 : 0, gi -= gi >= ng ? ng : 0) {
             const int i0 = bx0 + 4 * gi;
             const float *Crow = Cs + r * cw_max - cx0;
             float *Brow = Bs + r * bw_max - bx0;
