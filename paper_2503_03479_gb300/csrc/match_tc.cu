@@ -24,6 +24,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tma.cuh"
 
 namespace asift {
 
@@ -42,75 +43,11 @@ constexpr int kTcSmem = kTcABytes + kTcStages * kTcBBytes + 256 + 1024;
 constexpr int kTcCols = 2 * kTcQB * kTcBN;       // TMEM columns: 2 accumulator stages
 constexpr unsigned kTcNoKey = 0xffffffffu;
 constexpr int kMaxTcProblems = 512;
-constexpr unsigned long long kWaitNs = 4000000000ull;   // a wait gives up after 4 s
 
 static_assert(kTcCols == 512, "the accumulators fill TMEM");
 static_assert(kTcSmem <= 227 * 1024 - 8 * 1024, "shared memory budget");
 
 // ---------------------------------------------------------------- PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t done;
-    asm volatile(
-        "{\n.reg .pred P1;\nmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\nselp.b32 %0, 1, 0, P1;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-// Waits for the phase of `bar` with the given parity.  Gives up when another
-// role of the CTA has aborted, or after kWaitNs (then raises the abort flag
-// and records the timeout).  With abort_flag NULL only the time limit applies.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
-                                          int32_t *status)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    for (;;) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (abort_flag && *abort_flag) return false;
-        if (global_ns() - t0 > kWaitNs) {
-            if (abort_flag) *abort_flag = 1;
-            set_status(status, ASIFT_ERR_TIMEOUT);
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
-
 // Shared-memory matrix descriptor of a K-major operand with the 128-byte
 // swizzle: start address (16-byte units, bits 0-13), leading byte offset
 // (unused by this layout, 1), stride byte offset 1024 (8-row groups, bits

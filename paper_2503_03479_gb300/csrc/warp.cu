@@ -310,28 +310,38 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
             return chunk_box(G, clampi(cx0 + c0, 0, Wr - 1), clampi(cx0 + c0 + cn - 1, 0, Wr - 1), j0, j1, W, H,
                              lane);
         };
-        StageBox bx = box_of(0);
-        stage_box(Sbuf, P, src, sp, bx, warp, lane);
-        cp_async_commit();
-        for (int k = 0; k < nch; ++k) {
-            StageBox nb = bx;
-            if (k + 1 < nch) {
-                nb = box_of(k + 1);
-                stage_box(Sbuf + ((k + 1) & 1) * kStageBuf, P, src, sp, nb, warp, lane);
+        // Chunks whose source lies wholly outside the image are background:
+        // they are written as zeros on the way and take no staging buffer, so
+        // the copies of the next staged chunk always overlap a computed one.
+        auto next_staged = [&](int k, StageBox &b) {
+            for (; k < nch; ++k) {
+                b = box_of(k);
+                if (!b.outside) break;
+                const int c0 = k * kChunk, cn = min(kChunk, cw - c0);
+                if (c < cn)
+                    for (int r = rg; r < nrows; r += kRowStep) Cs[r * cw_max + c0 + c] = 0.f;
             }
+            return k;
+        };
+        StageBox bx;
+        int k = next_staged(0, bx), buf = 0;
+        if (k < nch) stage_box(Sbuf, P, src, sp, bx, warp, lane);
+        cp_async_commit();
+        while (k < nch) {
+            StageBox nb;
+            const int kn = next_staged(k + 1, nb);
+            if (kn < nch) stage_box(Sbuf + (buf ^ 1) * kStageBuf, P, src, sp, nb, warp, lane);
             cp_async_commit();
             cp_async_wait<1>();      // this thread's copies of chunk k have landed
             __syncthreads();         // and everyone's
-            const float *Ss = Sbuf + (k & 1) * kStageBuf;
+            const float *Ss = Sbuf + buf * kStageBuf;
             const int c0 = k * kChunk, cn = min(kChunk, cw - c0);
             if (c < cn) {
                 const int i = clampi(cx0 + c0 + c, 0, Wr - 1);   // strip position -> canvas column (clamped)
                 long long px, py;
                 G.map(i, j0 + rg, px, py);
                 float *Cp = Cs + c0 + c;
-                if (bx.outside) {
-                    for (int r = rg; r < nrows; r += kRowStep) Cp[r * cw_max] = 0.f;
-                } else if (bx.interior) {
+                if (bx.interior) {
                     for (int r = rg; r < nrows; r += kRowStep, px += dpx, py += dpy)
                         Cp[r * cw_max] = interp_interior(Ss, P, px, py, bx.sx0, bx.sy0);
                 } else {
@@ -359,10 +369,13 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
                     }
                 }
             }
-            __syncthreads();         // buffer k & 1 is free for chunk k + 2
+            __syncthreads();         // buffer buf is free for the chunk after next
+            k = kn;
             bx = nb;
+            buf ^= 1;
         }
         cp_async_wait<0>();
+        __syncthreads();             // zero-filled columns written after the last staged chunk
     }
 
     // 2. Gaussian along canvas x: B(i) = sum_k g_|k| C(clamp(i) - k).  A lane
