@@ -114,15 +114,23 @@ struct MatchTuning {
 // ---------------------------------------------------------------- helpers
 __host__ __device__ inline int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-// Binary search of the last entry with start <= idx in a monotone array
-// reached through a strided field accessor.
+// The last entry with start <= idx in a monotone table (entries with equal
+// starts: the last of them), searched by a whole warp: each round the 32 lanes
+// test evenly spaced entries of the remaining range and a ballot keeps the
+// highest one that qualifies, so n entries take ceil(log32 n) dependent loads.
+// Every lane of the warp must call it with the same arguments.
 template <class T, class F>
 __device__ inline int find_owner(const T *tab, int n, int idx, F start_of)
 {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (start_of(tab[mid]) <= idx) lo = mid; else hi = mid - 1;
+    const int lane = (int)(threadIdx.x & 31u);
+    int lo = 0, hi = n;   // answer in [lo, hi); start_of(tab[lo]) <= idx
+    while (hi - lo > 1) {
+        const int step = (hi - lo + 31) >> 5;
+        const int pos = lo + lane * step;
+        const bool ok = pos < hi && start_of(tab[pos]) <= idx;
+        const unsigned b = __ballot_sync(0xffffffffu, ok);
+        lo += (31 - __clz(b)) * step;
+        hi = min(hi, lo + step);
     }
     return lo;
 }
