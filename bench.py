@@ -181,6 +181,79 @@ def match_roofline(n1: int, n2: int, ms: float, tensor: bool, peaks: dict) -> di
             "peak_source": f"derived: {SM_COUNT} SMs x {POPC_PER_SM_CLK} popc/clk x {f_clk/1e6:.0f} MHz"}
 
 
+def _sha256(path: str) -> str:
+    import hashlib
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+    `kernel` from the table in profiles/roofline_traffic.md, used only while
+    the kernel's source file still has the sha256 recorded beside the number;
+    None otherwise."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.md")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    for l in lines:
+        f = [x.strip() for x in l.strip().strip("|").split("|")]
+        if len(f) >= 4 and f[0] == kernel:
+            src, sha, nbytes = f[1], f[2], f[3]
+            try:
+                if _sha256(os.path.join(ROOT, src)) == sha:
+                    return float(nbytes)
+            except (OSError, ValueError):
+                return None
+    return None
+
+
+def match_engines(A, ctx, dd1, dd2, stream, reps: int = 5):
+    """Times hamming_match on the pair's two pools with each engine (inputs
+    and outputs in device memory, CUDA events on the stream) and checks that
+    both return the same bytes."""
+    import ctypes as C
+    import torch
+    q = torch.from_numpy(np.ascontiguousarray(dd1)).cuda()
+    t = torch.from_numpy(np.ascontiguousarray(dd2)).cuda()
+    nq, nt = q.shape[0], t.shape[0]
+    L = ctx.L
+    ws = torch.zeros(L.hamming_workspace_size(nq, nt), dtype=torch.uint8, device="cuda")
+    res, outs = {}, {}
+    for name, eng in (("tensor_cores", A.MATCH_TENSOR_CORES), ("cuda_cores", A.MATCH_CUDA_CORES)):
+        if eng == A.MATCH_TENSOR_CORES and ctx.match_engine != A.MATCH_TENSOR_CORES:
+            continue
+        ctx.set_match_engine(eng)
+        out = torch.zeros(max(nq, 1) * 8, dtype=torch.uint8, device="cuda")
+        acc = torch.zeros(max(nq, 1), dtype=torch.uint8, device="cuda")
+        nacc = torch.zeros(1, dtype=torch.int32, device="cuda")
+        args = (ctx._ctx, C.c_void_p(q.data_ptr()), nq, None, C.c_void_p(t.data_ptr()), nt, None, 4, 5,
+                C.c_void_p(out.data_ptr()), C.c_void_p(acc.data_ptr()), C.c_void_p(nacc.data_ptr()),
+                C.c_void_p(ws.data_ptr()), ws.numel(), C.c_void_p(stream.cuda_stream))
+        for _ in range(2):
+            assert L.hamming_match(*args) == 0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h0 = time.perf_counter()
+        for _ in range(reps):
+            L.hamming_match(*args)
+        h1 = time.perf_counter()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name + "_host_enqueue_ms"] = (h1 - h0) * 1e3 / reps
+        res[name + "_ms"] = ms
+        res[name + "_tops"] = 2.0 * 256 * nq * nt / (ms / 1e3) / 1e12
+        outs[name] = (out.cpu().numpy().tobytes(), int(nacc.item()))
+    ctx.set_match_engine(A.MATCH_AUTO)
+    if len(outs) == 2:
+        res["identical"] = outs["tensor_cores"] == outs["cuda_cores"]
+        res["speedup"] = res["cuda_cores_ms"] / res["tensor_cores_ms"]
+    res["queries"], res["trains"] = nq, nt
+    return res
+
+
 # ---------------------------------------------------------------- CPU oracle sample
 def oracle_sample(rank: int = 0):
     """Times the CPU oracle on a bounded sample of one pair and scales it to a
@@ -322,8 +395,13 @@ def run_ours(args):
     views = A.view_table(H, W, KMAX)
     rooflines = {"warp": warp_roofline(views, 2, st["warp"], peaks),
                  "match": match_roofline(n1, n2, st["match"], ctx.match_engine == A.MATCH_TENSOR_CORES, peaks)}
+    for k, r in rooflines.items():
+        r["traffic"] = profiled_traffic(r["kernel"].split()[0])
     dominant = max(rooflines, key=lambda k: st[k])
     roofline = dict(rooflines[dominant], stage=dominant)
+
+    # ---- the two matcher engines on this pair's pools (device buffers, same result)
+    engines = match_engines(A, ctx, dd1, dd2, stream)
 
     # ---- plain per-view form (same kernels, one launch per view and stage)
     plain = None
@@ -465,6 +543,7 @@ def run_ours(args):
                 "batched_mixed": batched,
                 "differentiable": diff,
                 "roofline": roofline, "rooflines": rooflines, "match_engine": ctx.match_engine,
+                "match_engines": engines,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clocks}
         print(json.dumps(line), flush=True)

@@ -4,6 +4,8 @@
 #include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -14,6 +16,42 @@ namespace asift {
 
 static std::atomic<long long> g_launches{0};
 void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Per-device, per-kernel memo of the dynamic shared-memory limit already set,
+// so launches pay for cudaFuncSetAttribute only when a larger size is needed.
+// (The opt-in matters below 48 KB of dynamic memory too: the 48 KB default
+// covers static plus dynamic shared memory.)
+cudaError_t ensure_dynamic_smem(const void *func, size_t bytes)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, size_t> set;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_pair(func, dev);
+    const auto it = set.find(key);
+    if (it != set.end() && it->second >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) set[key] = bytes;
+    return e;
+}
+
+// SM count of the current device (cached per device).
+int device_sm_count()
+{
+    static std::atomic<int> cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+    if (dev >= 0 && dev < 64) {
+        const int c = cache[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) return 152;
+    if (dev >= 0 && dev < 64) cache[dev].store(sms, std::memory_order_relaxed);
+    return sms;
+}
 
 // ---------------------------------------------------------------- workspace bump allocator
 struct Bump {
@@ -1138,12 +1176,7 @@ static cudaError_t plan_time(asift_plan *p, int reps, float *ms)
 asift_status asift_plan_autotune(asift_plan *plan, int reps, asift_tuning *out)
 {
     if (!plan || reps < 1) return ASIFT_ERR_ARG;
-    int sms = 152;
-    {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
+    const int sms = asift::device_sm_count();
     // coordinate descent over one knob at a time, the others at their best
     struct Knob {
         int32_t *field;

@@ -146,4 +146,6 @@ __device__ inline void set_status(int32_t *status, int32_t code)
 // Host-side helpers shared by the API translation units.
 namespace asift {
 void note_launch(int n = 1);
+cudaError_t ensure_dynamic_smem(const void *func, size_t bytes);
+int device_sm_count();
 }

@@ -388,18 +388,12 @@ cudaError_t launch_dwarp(bool backward, const DiffView *d_views, int n_views, in
     if (n_tiles <= 0) return cudaSuccess;
     const size_t smem = sizeof(float) * (size_t)kDTH * (backward ? 2 * (cw_max + bw_max) : (cw_max + bw_max));
     if (backward) {
-        if (smem > 48 * 1024) {
-            cudaError_t e =
-                cudaFuncSetAttribute(dwarp_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-        }
+        const cudaError_t e = ensure_dynamic_smem((const void *)dwarp_bwd_kernel, smem);
+        if (e != cudaSuccess) return e;
         dwarp_bwd_kernel<<<n_tiles, kDThreads, smem, s>>>(d_views, n_views, cw_max, bw_max, status);
     } else {
-        if (smem > 48 * 1024) {
-            cudaError_t e =
-                cudaFuncSetAttribute(dwarp_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-        }
+        const cudaError_t e = ensure_dynamic_smem((const void *)dwarp_fwd_kernel, smem);
+        if (e != cudaSuccess) return e;
         dwarp_fwd_kernel<<<n_tiles, kDThreads, smem, s>>>(d_views, n_views, cw_max, bw_max, status);
     }
     note_launch();

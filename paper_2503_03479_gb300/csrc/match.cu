@@ -351,7 +351,7 @@ cudaError_t launch_match(const MatchProblem *d_probs, int n_probs, const MatchPr
                          bool any_train, int num, int den, const MatchTuning &tune, cudaStream_t s)
 {
     if (total_q <= 0) return cudaSuccess;
-    const int grid = tune.grid > 0 ? tune.grid : 152 * 7;
+    const int grid = tune.grid > 0 ? tune.grid : device_sm_count() * 7;
     const int target = tune.target_items > 0 ? tune.target_items : 2 * grid;
     if (any_train) {
         hamming_top2_kernel<<<grid, kMThreads, 0, s>>>(d_probs, n_probs, single, target);

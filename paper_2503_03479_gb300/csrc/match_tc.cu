@@ -20,6 +20,8 @@
 // kernel finishes the job.  Every mbarrier wait is bounded by the global
 // timer: on expiry the CTA records ASIFT_ERR_TIMEOUT, stops issuing, waits
 // (bounded) for its own copies and MMAs in flight and frees its TMEM.
+#include <atomic>
+
 #include <cuda.h>
 
 #include "common.cuh"
@@ -451,12 +453,21 @@ static cudaError_t make_map(CUtensorMap *m, const void *ptr, long long rows, int
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// Compute capability 10.x and the tensor-map encoder present (cached per device).
 bool tc_match_available()
 {
-    int dev = 0, major = 0;
+    static std::atomic<int> cache[64] = {};   // 0 unknown, 1 no, 2 yes
+    int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (dev >= 0 && dev < 64) {
+        const int c = cache[dev].load(std::memory_order_relaxed);
+        if (c) return c == 2;
+    }
+    int major = 0;
     if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) return false;
-    return major == 10 && encode_fn() != nullptr;
+    const bool ok = major == 10 && encode_fn() != nullptr;
+    if (dev >= 0 && dev < 64) cache[dev].store(ok ? 2 : 1, std::memory_order_relaxed);
+    return ok;
 }
 
 size_t tc_expanded_bytes(long long rows) { return (size_t)std::max<long long>(rows, 1) * kTcK; }
@@ -466,7 +477,7 @@ cudaError_t launch_expand(const uint8_t *packed, uint8_t *out, const int32_t *d_
 {
     if (cap_rows <= 0 || n_groups <= 0) return cudaSuccess;
     const long long per_group = cap_rows * 32 / n_groups;
-    const int bx = (int)std::max<long long>(1, std::min<long long>((per_group + 255) / 256, 152LL * 8 / n_groups + 1));
+    const int bx = (int)std::max<long long>(1, std::min<long long>((per_group + 255) / 256, 8LL * device_sm_count() / n_groups + 1));
     expand_pm1_kernel<<<dim3(bx, n_groups), 256, 0, s>>>(packed, out, d_first, n_per_view, d_count, cap_rows);
     note_launch();
     return cudaGetLastError();
@@ -486,12 +497,9 @@ cudaError_t launch_match_tc(const uint8_t *qbase, const uint8_t *qexp, long long
     cudaError_t e = make_map(&qm, qexp, q_rows, kTcQB * kTcBM);
     if (e == cudaSuccess) e = make_map(&tm, texp, t_rows, kTcBN);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(hamming_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    e = ensure_dynamic_smem((const void *)hamming_tc_kernel, kTcSmem);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
+    const int sms = device_sm_count();
     const int grid = tune.grid > 0 ? std::min(tune.grid, sms) : sms;   // one CTA per SM: it holds all of TMEM
     const int target = tune.target_items > 0 ? tune.target_items : 4 * grid;
     hamming_tc_kernel<<<grid, kTcThreads, kTcSmem, s>>>(qm, tm, reinterpret_cast<const uint4 *>(qbase),

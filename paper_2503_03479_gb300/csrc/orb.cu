@@ -584,13 +584,9 @@ cudaError_t launch_select(const DevLevel *d_lv, int n, const Candidate *cand, co
                           SlotKp *slots, int32_t *taken, int32_t *status, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    static bool attr_set = false;
     const size_t smem = select_smem_bytes();
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    const cudaError_t e = ensure_dynamic_smem((const void *)select_kernel, smem);
+    if (e != cudaSuccess) return e;
     select_kernel<<<n, kSelThreads, smem, s>>>(d_lv, cand, count, n_features, slots, taken, status);
     note_launch();
     return cudaGetLastError();

@@ -568,7 +568,7 @@ void warp_lane_layout(long long cq, long long sq, int *lanes_x, int *pitch)
 cudaError_t launch_u8_to_f32(const uint8_t *src, int pitch, int W, int H, float *dst, cudaStream_t s)
 {
     const long long n = (long long)W * H;
-    int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 8);
+    int blocks = (int)std::min<long long>((n + 255) / 256, 8LL * device_sm_count());
     u8_to_f32_kernel<<<blocks, 256, 0, s>>>(src, pitch, W, H, dst);
     note_launch();
     return cudaGetLastError();
@@ -577,7 +577,7 @@ cudaError_t launch_u8_to_f32(const uint8_t *src, int pitch, int W, int H, float 
 cudaError_t launch_convert_images(const ImageConv *d_list, int n, long long max_px, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    const int bx = (int)std::max<long long>(1, std::min<long long>((max_px + 255) / 256, 152LL * 4));
+    const int bx = (int)std::max<long long>(1, std::min<long long>((max_px + 255) / 256, 4LL * device_sm_count()));
     convert_images_kernel<<<dim3(bx, n), 256, 0, s>>>(d_list);
     note_launch();
     return cudaGetLastError();
@@ -588,11 +588,8 @@ cudaError_t launch_warp(const DevView *d_views, int n_views, int n_tiles, int cw
 {
     if (n_tiles <= 0) return cudaSuccess;
     const size_t smem = warp_smem_bytes(cw_max, bw_max);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(warp_view_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    const cudaError_t e = ensure_dynamic_smem((const void *)warp_view_kernel, smem);
+    if (e != cudaSuccess) return e;
     const int g = (grid > 0 && grid < n_tiles) ? grid : n_tiles;
     warp_view_kernel<<<g, kWarpThreads, smem, s>>>(n_tiles, d_views, n_views, cw_max, bw_max, u8, mask, f32);
     note_launch();
