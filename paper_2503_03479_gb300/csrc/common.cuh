@@ -69,7 +69,7 @@ struct SlotKp {             // a selected keypoint before orientation / descript
     int32_t e;              // level entry (relative to the select launch)
 };
 
-constexpr int kDetTW = 64, kDetTH = 16;   // FAST tile
+constexpr int kDetTW = 64, kDetTH = 32;   // FAST tile
 constexpr int kPyrTW = 64, kPyrTH = 16;   // pyramid tile (4 px per thread across x)
 
 // ---------------------------------------------------------------- differentiable warp

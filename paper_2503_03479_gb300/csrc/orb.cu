@@ -21,11 +21,17 @@ namespace asift {
 // ---------------------------------------------------------------- pyramid
 // Each CTA makes a kPyrTW x kPyrTH tile of level l.  The source columns and
 // weights of the tile's columns and rows are computed once (32-bit integer
-// divisions) and shared; each pixel is then four byte loads and integer FMAs.
+// divisions) and shared; the parent region the tile reads (at most
+// kPyrSW x kPyrSH: 63 steps of at most 1.22 parent pixels plus the second
+// tap) is staged in shared memory, image and mask, with coalesced loads; each
+// output pixel is then four shared-memory reads and integer FMAs per plane.
+constexpr int kPyrSW = 84, kPyrSH = 24;
+
 __device__ __forceinline__ void pyramid_tile(int tile, const DevLevel *__restrict__ lv, int n)
 {
     __shared__ int16_t sx0[kPyrTW], sx1[kPyrTW], sfx[kPyrTW];
     __shared__ int16_t sy0[kPyrTH], sy1[kPyrTH], sfy[kPyrTH];
+    __shared__ uint8_t pimg[kPyrSH][kPyrSW], pmask[kPyrSH][kPyrSW];
     const int e = find_owner(lv, n, tile, [](const DevLevel &d) { return d.pyr_tile_start; });
     const DevLevel &L = lv[e];
     const int lt = tile - L.pyr_tile_start;
@@ -45,19 +51,45 @@ __device__ __forceinline__ void pyramid_tile(int tile, const DevLevel *__restric
         else { sy0[i - kPyrTW] = (int16_t)q0; sy1[i - kPyrTW] = (int16_t)q1; sfy[i - kPyrTW] = (int16_t)f; }
     }
     __syncthreads();
-    for (int p = threadIdx.x; p < kPyrTW * kPyrTH; p += blockDim.x) {
+    // parent region: columns sx0[0] .. sx1[last], rows sy0[0] .. sy1[last]
+    const int nx = min(kPyrTW, Wl - xb), ny = min(kPyrTH, Hl - yb);
+    const int px0 = sx0[0], py0 = sy0[0];
+    const int pw = sx1[nx - 1] - px0 + 1, ph = sy1[ny - 1] - py0 + 1;
+    const bool staged = pw <= kPyrSW && ph <= kPyrSH;   // always, for level ratios up to 1.3
+    if (staged) {
+        const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5;
+        for (int r = wrp; r < ph; r += 8) {
+            const size_t g = (size_t)(py0 + r) * Wp + px0;
+            for (int c = lane; c < pw; c += 32) {
+                pimg[r][c] = L.prev[g + c];
+                pmask[r][c] = L.prev_mask[g + c];
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < (kPyrTW * kPyrTH) / 256; ++k) {
+        const int p = threadIdx.x + k * 256;
         const int cx = p % kPyrTW, cy = p / kPyrTW;
+        if (cx >= nx || cy >= ny) continue;
         const int x = xb + cx, y = yb + cy;
-        if (x >= Wl || y >= Hl) continue;
         const int x0 = sx0[cx], x1 = sx1[cx], fx = sfx[cx];
         const int y0 = sy0[cy], y1 = sy1[cy], fy = sfy[cy];
-        const uint8_t *r0 = L.prev + y0 * Wp, *r1 = L.prev + y1 * Wp;
-        const unsigned a = r0[x0], b = r0[x1], c = r1[x0], d = r1[x1];
+        unsigned a, b, c, d, ma, mb, mc, md;
+        if (staged) {
+            const int u0 = x0 - px0, u1 = x1 - px0, v0 = y0 - py0, v1 = y1 - py0;
+            a = pimg[v0][u0]; b = pimg[v0][u1]; c = pimg[v1][u0]; d = pimg[v1][u1];
+            ma = pmask[v0][u0]; mb = pmask[v0][u1]; mc = pmask[v1][u0]; md = pmask[v1][u1];
+        } else {
+            const uint8_t *r0 = L.prev + y0 * Wp, *r1 = L.prev + y1 * Wp;
+            a = r0[x0]; b = r0[x1]; c = r1[x0]; d = r1[x1];
+            const uint8_t *m0 = L.prev_mask + y0 * Wp, *m1 = L.prev_mask + y1 * Wp;
+            ma = m0[x0]; mb = m0[x1]; mc = m1[x0]; md = m1[x1];
+        }
         const unsigned gx = 2048 - fx, gy = 2048 - fy;
         const unsigned s = gx * gy * a + (unsigned)fx * gy * b + gx * (unsigned)fy * c + (unsigned)fx * (unsigned)fy * d;
         L.img_w[y * Wl + x] = (uint8_t)((s + (1u << 21)) >> 22);
-        const uint8_t *m0 = L.prev_mask + y0 * Wp, *m1 = L.prev_mask + y1 * Wp;
-        L.mask_w[y * Wl + x] = (uint8_t)(m0[x0] & m0[x1] & m1[x0] & m1[x1]);
+        L.mask_w[y * Wl + x] = (uint8_t)(ma & mb & mc & md);
     }
 }
 
