@@ -167,12 +167,23 @@ static int det_tiles_of(const DevLevel &d) { return d.det_ntx * ((d.H + kDetTH -
 static int pyr_tiles_of(const DevLevel &d) { return d.pyr_ntx * ((d.H + kPyrTH - 1) / kPyrTH); }
 
 // View tables for the warp kernel.
+// Floats of the per-column Gaussian + tilt filters of a view list.
+static size_t tilt_filter_floats(const asift_view_desc *h, int nv)
+{
+    size_t n = 0;
+    for (int v = 0; v < nv; ++v) n += (size_t)h[v].Wv * tilt_filter_pitch(h[v].K);
+    return n;
+}
+
+// H: device array of tilt_filter_floats(h, nv) floats (the views' filters,
+// view after view).
 static void build_views(const asift_view_desc *h, int nv, const float *const *src, const int *src_pitch,
-                        const int64_t *out_off, bool per_view, std::vector<DevView> &out, int *n_tiles,
-                        int *cw_max, int *bw_max)
+                        const int64_t *out_off, bool per_view, float *H, std::vector<DevView> &out, int *n_tiles,
+                        int *cw_max, int *hp_max, int *max_wv)
 {
     out.assign(nv, DevView{});
-    int tiles = 0, cwm = 1, bwm = 1;
+    int tiles = 0, cwm = 1, hpm = 4, wvm = 0;
+    size_t hoff = 0;
     for (int v = 0; v < nv; ++v) {
         const asift_view_desc &a = h[v];
         DevView &d = out[v];
@@ -210,14 +221,19 @@ static void build_views(const asift_view_desc *h, int nv, const float *const *sr
             }
         }
         for (int k = 0; k < ASIFT_MAX_GAUSS; ++k) d.g[k] = (k <= a.K) ? a.g[k] : 0.f;
+        d.hp = tilt_filter_pitch(a.K);
+        d.filt = H ? H + hoff : nullptr;
+        hoff += (size_t)a.Wv * d.hp;
         int cw, bw;
         warp_strip_widths(a, &cw, &bw);
         cwm = std::max(cwm, cw);
-        bwm = std::max(bwm, bw);
+        hpm = std::max(hpm, d.hp);
+        wvm = std::max(wvm, a.Wv);
     }
     *n_tiles = tiles;
     *cw_max = cwm;
-    *bw_max = bwm;
+    *hp_max = hpm;
+    *max_wv = wvm;
 }
 
 static bool view_ok(const asift_view_desc &v)
@@ -432,21 +448,26 @@ asift_status asift_read_status(void *d_workspace, int clear, int32_t *h_status, 
 }
 
 // ---------------------------------------------------------------- asift_views
-static size_t views_layout(void *base, int H, int W, int nv, int32_t **status, DevView **tab, float **src)
+static size_t views_layout(void *base, int H, int W, int nv, size_t n_filter, int32_t **status, DevView **tab,
+                           float **src, float **filt)
 {
     Bump b(base);
     *status = b.take<int32_t>(64);
     *tab = b.take<DevView>(std::max(nv, 1));
     *src = b.take<float>((size_t)W * H);
+    *filt = b.take<float>(std::max<size_t>(n_filter, 1));
     return b.off + 256;
 }
 
 size_t asift_views_workspace_size(int H, int W, int n_views)
 {
+    // filters: at most Wv * pitch(K) floats per view, bounded by the largest
+    // view of the image (Wv <= (W + H) / t + 1, K <= ASIFT_MAX_GAUSS - 1)
+    const size_t per_view = (size_t)(W + H + 2) * tilt_filter_pitch(ASIFT_MAX_GAUSS - 1);
     int32_t *s;
     DevView *t;
-    float *f;
-    return views_layout(nullptr, H, W, n_views, &s, &t, &f);
+    float *f, *g;
+    return views_layout(nullptr, H, W, n_views, per_view * std::max(n_views, 1), &s, &t, &f, &g);
 }
 
 asift_status asift_views(asift_ctx *ctx, const uint8_t *d_img, int H, int W, int pitch,
@@ -464,16 +485,17 @@ asift_status asift_views(asift_ctx *ctx, const uint8_t *d_img, int H, int W, int
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int32_t *status;
     DevView *tab;
-    float *src;
-    views_layout(d_workspace, H, W, n_views, &status, &tab, &src);
+    float *src, *filt;
+    views_layout(d_workspace, H, W, n_views, tilt_filter_floats(h_views, n_views), &status, &tab, &src, &filt);
     std::vector<const float *> srcs(n_views, src);
     std::vector<int> pitches(n_views, W);
     std::vector<DevView> dv;
-    int n_tiles, cwm, bwm;
-    build_views(h_views, n_views, srcs.data(), pitches.data(), h_offsets, false, dv, &n_tiles, &cwm, &bwm);
+    int n_tiles, cwm, hpm, wvm;
+    build_views(h_views, n_views, srcs.data(), pitches.data(), h_offsets, false, filt, dv, &n_tiles, &cwm, &hpm, &wvm);
     cudaError_t e = upload(ctx, tab, dv.data(), sizeof(DevView) * n_views, s);
     if (e == cudaSuccess) e = launch_u8_to_f32(d_img, pitch, W, H, src, s);
-    if (e == cudaSuccess) e = launch_warp(tab, n_views, n_tiles, cwm, bwm, d_view_u8, d_mask, d_view_f32, s);
+    if (e == cudaSuccess) e = launch_tilt_filter(tab, n_views, wvm, s);
+    if (e == cudaSuccess) e = launch_warp(tab, n_views, n_tiles, cwm, hpm, d_view_u8, d_mask, d_view_f32, s);
     return cuda_status(e);
 }
 
@@ -745,7 +767,8 @@ struct Pipeline {
     std::vector<DevView> h_dv;
     std::vector<MatchProblem> h_probs;
     std::vector<ImageConv> h_conv;
-    int n_tiles = 0, cw_max = 0, bw_max = 0, total_q = 0, total_blk = 0, n_per_view = 0;
+    int n_tiles = 0, cw_max = 0, hp_max = 0, max_wv = 0, total_q = 0, total_blk = 0, n_per_view = 0;
+    float *tilt_filters = nullptr;           // per view column: Gaussian + tilt filter
     long long cap_rows = 0;
     long long max_px = 0;
     size_t tab_bytes = 0;                    // bytes from dv to the end of the table region
@@ -805,6 +828,7 @@ static bool pipeline_layout(const asift_ctx *ctx, const PairSpec *ps, int P, int
         for (int l = 0; l < cfg.n_levels; ++l)
             off += ((long long)level_size(L.views[v].Wv, l) * level_size(L.views[v].Hv, l) + 15) & ~15LL;
     }
+    L.tilt_filters = b.take<float>(std::max<size_t>(tilt_filter_floats(L.views.data(), L.nv), 1));
     L.src.assign(2 * P, nullptr);
     L.max_px = 0;
     for (int p = 0; p < P; ++p) {
@@ -868,8 +892,8 @@ static void pipeline_tables(Pipeline &L, const asift_pair_desc *pairs, asift_pai
         L.h_probs[p].cap = caps[p];
         L.h_probs[p].d_n = d_ns[p];
     }
-    build_views(L.views.data(), L.nv, srcs.data(), pitches.data(), L.level0_off.data(), per_view, L.h_dv, &L.n_tiles,
-                &L.cw_max, &L.bw_max);
+    build_views(L.views.data(), L.nv, srcs.data(), pitches.data(), L.level0_off.data(), per_view, L.tilt_filters,
+                L.h_dv, &L.n_tiles, &L.cw_max, &L.hp_max, &L.max_wv);
     blob.assign(L.tab_bytes, 0);
     char *b0 = (char *)L.dv;
     std::memcpy(blob.data(), L.h_dv.data(), sizeof(DevView) * L.nv);
@@ -888,12 +912,16 @@ static cudaError_t pipeline_run(asift_ctx *ctx, const Pipeline &L, const asift_p
     prof_mark(ctx, 1, s);
     if (e == cudaSuccess) {
         if (!per_view) {
-            e = launch_warp(L.dv, L.nv, L.n_tiles, L.cw_max, L.bw_max, L.o.arena_u8, L.o.arena_mask, nullptr, s,
-                            tune ? tune->warp_grid : 0);
+            e = launch_tilt_filter(L.dv, L.nv, L.max_wv, s);
+            if (e == cudaSuccess)
+                e = launch_warp(L.dv, L.nv, L.n_tiles, L.cw_max, L.hp_max, L.o.arena_u8, L.o.arena_mask, nullptr, s,
+                                tune ? tune->warp_grid : 0);
         } else {
             for (int v = 0; v < L.nv && e == cudaSuccess; ++v) {
                 const int tiles = L.h_dv[v].ntx * ((L.views[v].Hv + kWarpTH - 1) / kWarpTH);
-                e = launch_warp(L.dv + v, 1, tiles, L.cw_max, L.bw_max, L.o.arena_u8, L.o.arena_mask, nullptr, s);
+                e = launch_tilt_filter(L.dv + v, 1, L.views[v].Wv, s);
+                if (e == cudaSuccess)
+                    e = launch_warp(L.dv + v, 1, tiles, L.cw_max, L.hp_max, L.o.arena_u8, L.o.arena_mask, nullptr, s);
             }
         }
     }

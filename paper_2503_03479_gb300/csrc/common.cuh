@@ -23,6 +23,8 @@ struct DevView {
     int32_t ntx;            // tiles along x
     int16_t lanes_x;        // canvas columns of a warp's footprint in the rotation step (32, 16 or 8)
     int16_t stage_pitch;    // row pitch (floats) of the staged source box
+    int32_t hp, pad2;       // floats per view column in filt (>= 2K + 6, a multiple of 4)
+    float *filt;            // per view column x: the Gaussian + tilt filter over canvas columns x0-2-K .. x0+3+K
     long long cq, sq, tq;   // Q31 cos, sin, tilt
     long long out_off;      // byte offset of the view in the u8 / mask arenas
     double cosd, sind, t;   // fp64 geometry for back-projection

@@ -20,7 +20,9 @@ void warp_lane_layout(long long cq, long long sq, int *lanes_x, int *pitch);
 cudaError_t launch_u8_to_f32(const uint8_t *src, int pitch, int W, int H, float *dst, cudaStream_t s);
 struct ImageConv;
 cudaError_t launch_convert_images(const ImageConv *d_list, int n, long long max_px, cudaStream_t s);
-cudaError_t launch_warp(const DevView *d_views, int n_views, int n_tiles, int cw_max, int bw_max, uint8_t *u8,
+int tilt_filter_pitch(int K);
+cudaError_t launch_tilt_filter(const DevView *d_views, int n_views, int max_wv, cudaStream_t s);
+cudaError_t launch_warp(const DevView *d_views, int n_views, int n_tiles, int cw_max, int hp_max, uint8_t *u8,
                         uint8_t *mask, float *f32, cudaStream_t s, int grid = 0);
 
 // orb.cu

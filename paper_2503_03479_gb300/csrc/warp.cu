@@ -247,19 +247,16 @@ __device__ __forceinline__ void stage_box(float *dst, int P, const float *__rest
     }
 }
 
-__device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restrict__ views, int n_views, int cw_max,
-                                               int bw_max, uint8_t *__restrict__ out_u8,
+__device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restrict__ views, int n_views, int cwp,
+                                               uint8_t *__restrict__ out_u8,
                                                uint8_t *__restrict__ out_mask, float *__restrict__ out_f32)
 {
     extern __shared__ float4 smem4[];
     float *smem = reinterpret_cast<float *>(smem4);
-    // Cs [kWarpTH][cw_max] canvas strip, then one region that holds the two
-    // staging buffers [kStage][pitch] in step 1 and the blurred strip Bs
-    // [kWarpTH][bw_max] in steps 2-3.
+    // Cs [kWarpTH][cwp] canvas strip (odd row pitch), then the two staging
+    // buffers [kStage][pitch] of step 1.
     float *Cs = smem;
-    float *Sbuf = Cs + kWarpTH * cw_max;
-    float *Bs = Sbuf;
-    __shared__ float4 gs4[ASIFT_MAX_GAUSS / 4];
+    float *Sbuf = Cs + kWarpTH * cwp;
 
     const int vi = find_owner(views, n_views, tile, [](const DevView &v) { return v.tile_start; });
     const DevView &V = views[vi];
@@ -277,14 +274,8 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
     const long long Xb = V.tq * (2LL * xb - V.Wv + 1) + xoff;
     const int bx0 = (int)(Xa >> 32) - 2, bx1 = (int)(Xb >> 32) + 3;   // unclamped strip of B
     const int bw = bx1 - bx0 + 1;
-    const int K4 = (K + 3) & ~3;            // taps in blocks of four (zero weights past K)
-    const int cx0 = bx0 - K4;               // strip of C: [cx0, cx0 + cw), covering the Gaussian
-    const int cw = ((bw + 3) & ~3) + 2 * K4;
-
-    // gs4[q] = (g_{4q+1}, .., g_{4q+4}), zero past K; g_0 apart
-    float *gsh = reinterpret_cast<float *>(gs4);
-    for (int k = threadIdx.x; k < K4; k += blockDim.x) gsh[k] = k < K ? V.g[k + 1] : 0.f;
-    const float g0 = V.g[0];
+    const int cx0 = bx0 - K;                // strip of C: [cx0, cx0 + cw), covering the Gaussian
+    const int cw = bw + 2 * K;
 
     const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     constexpr int kRowStep = kWarpThreads / kChunk;   // a thread walks its column in steps of 4 rows
@@ -319,7 +310,7 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
                 if (!b.outside) break;
                 const int c0 = k * kChunk, cn = min(kChunk, cw - c0);
                 if (c < cn)
-                    for (int r = rg; r < nrows; r += kRowStep) Cs[r * cw_max + c0 + c] = 0.f;
+                    for (int r = rg; r < nrows; r += kRowStep) Cs[r * cwp + c0 + c] = 0.f;
             }
             return k;
         };
@@ -343,7 +334,7 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
                 float *Cp = Cs + c0 + c;
                 if (bx.interior) {
                     for (int r = rg; r < nrows; r += kRowStep, px += dpx, py += dpy)
-                        Cp[r * cw_max] = interp_interior(Ss, P, px, py, bx.sx0, bx.sy0);
+                        Cp[r * cwp] = interp_interior(Ss, P, px, py, bx.sx0, bx.sy0);
                 } else {
                     for (int r = rg; r < nrows; r += kRowStep, px += dpx, py += dpy) {
                         float acc = 0.f;
@@ -365,7 +356,7 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
                                 acc = fmaf(w[n].y, a, acc);
                             }
                         }
-                        Cp[r * cw_max] = acc;
+                        Cp[r * cwp] = acc;
                     }
                 }
             }
@@ -378,74 +369,36 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
         __syncthreads();             // zero-filled columns written after the last staged chunk
     }
 
-    // 2. Gaussian along canvas x: B(i) = sum_k g_|k| C(clamp(i) - k).  A lane
-    //    computes four consecutive outputs i0..i0+3 (strip index of i0 a
-    //    multiple of 4): taps go in blocks of four, each block needing one
-    //    new aligned float4 of C on either side, kept in a sliding register
-    //    window (lanes read consecutive 16-byte words).  Groups whose centres
-    //    would be clamped (the canvas border) take one output at a time.
-    //    Strip index of canvas column i is i - cx0; clamp(i) - k stays inside
-    //    [cx0, cx0 + cw).
+    // 2. Gaussian along canvas x, tilt resampling, quantisation and the
+    //    footprint mask.  Both filters act along canvas x of one row, so
+    //    per view column x they are one filter h_x over the canvas columns
+    //    x0-2-K .. x0+3+K (computed once per view by tilt_filter_kernel):
+    //    v(x, j) = sum_u h_x[u] C(x0 - 2 - K + u, j).  A warp covers 8 view
+    //    columns x 4 rows and each thread its column's rows rg, rg + 4,
+    //    rg + 8, rg + 12 (one filter load serves four rows).  The mask
+    //    needs canvas columns x0 and x0 + 1 inside the canvas and their
+    //    source points inside the shrunk footprint, tracked in Q32 as in
+    //    step 1.
     {
-        const int ng = (bw + 3) >> 2;
-        const int dr = kWarpThreads / ng, dg = kWarpThreads - dr * ng;   // stride kWarpThreads in (r, gi)
-        int r = (int)threadIdx.x / ng, gi = (int)threadIdx.x - r * ng;
-        for (; r < nrows; r += dr, gi += dg, r += gi >= ng ? 1 : 0, gi -= gi >= ng ? ng : 0) {
-            const int i0 = bx0 + 4 * gi;
-            const float *Crow = Cs + r * cw_max - cx0;
-            float *Brow = Bs + r * bw_max - bx0;
-            if (i0 >= 0 && i0 + 3 <= Wr - 1) {
-                const float4 *cq = reinterpret_cast<const float4 *>(Crow + i0);   // 16-byte aligned
-                const float4 cen = cq[0];
-                float4 a = make_float4(g0 * cen.x, g0 * cen.y, g0 * cen.z, g0 * cen.w);
-                float4 lp = cen, rp = cen;
-                for (int kb = 0; kb < K4; kb += 4) {
-                    const float4 ln = cq[-(kb >> 2) - 1];      // C[i0-kb-4 .. i0-kb-1]
-                    const float4 rn = cq[(kb >> 2) + 1];       // C[i0+kb+4 .. i0+kb+7]
-                    const float4 g = gs4[kb >> 2];
-                    // window L = (ln, lp) holds C[i0-kb-4+u], R = (rp, rn) holds C[i0+kb+u], u = 0..7
-                    const float L[8] = {ln.x, ln.y, ln.z, ln.w, lp.x, lp.y, lp.z, lp.w};
-                    const float R[8] = {rp.x, rp.y, rp.z, rp.w, rn.x, rn.y, rn.z, rn.w};
-                    const float gt[4] = {g.x, g.y, g.z, g.w};
-#pragma unroll
-                    for (int t = 1; t <= 4; ++t) {          // tap k = kb + t
-                        a.x = fmaf(gt[t - 1], L[4 - t] + R[t], a.x);
-                        a.y = fmaf(gt[t - 1], L[5 - t] + R[1 + t], a.y);
-                        a.z = fmaf(gt[t - 1], L[6 - t] + R[2 + t], a.z);
-                        a.w = fmaf(gt[t - 1], L[7 - t] + R[3 + t], a.w);
-                    }
-                    lp = ln;
-                    rp = rn;
-                }
-                *reinterpret_cast<float4 *>(Brow + i0) = a;   // outputs past bx1 stay in the row, unread
-            } else {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int i = i0 + q;
-                    if (i > bx1) break;
-                    const float *cp = Crow + clampi(i, 0, Wr - 1);
-                    float a = g0 * cp[0];
-                    for (int k = 1; k <= K; ++k) a = fmaf(gsh[k - 1], cp[-k] + cp[k], a);
-                    Brow[i] = a;
-                }
-            }
-        }
-    }
-    __syncthreads();
-
-    // 3. tilt resampling, quantisation and the footprint mask.  Thread =
-    //    view column (tilt position and weights fixed) walking down its rows;
-    //    the mask needs canvas columns x0 and x0 + 1 inside the canvas and
-    //    their source points inside the shrunk footprint, tracked in Q32 as
-    //    in step 1.
-    {
-        const int c = threadIdx.x & (kChunk - 1), rg = threadIdx.x / kChunk;
-        if (xa + c <= xb) {
+        const int hp = V.hp, nh = 2 * K + 6;
+        const int ncols = xb - xa + 1;
+        const int c = (int)(warp * 8 + (lane & 7u)), rg = (int)(lane >> 3);
+        if (c < ncols) {
             const int x = xa + c;
             const long long X = V.tq * (2LL * x - V.Wv + 1) + xoff;
             const int x0 = (int)(X >> 32);
-            float w[6];
-            lanczos3_weights((uint32_t)X, w);
+            const float *__restrict__ h = V.filt + (size_t)x * hp;   // read through L1 (the tile's 64 filters)
+            const float *Cb = Cs + (x0 - 2 - K - cx0) + rg * cwp;
+            float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+#pragma unroll 4
+            for (int u = 0; u < nh; ++u) {
+                const float hu = __ldg(h + u);
+                acc0 = fmaf(hu, Cb[u], acc0);
+                acc1 = fmaf(hu, Cb[4 * cwp + u], acc1);
+                acc2 = fmaf(hu, Cb[8 * cwp + u], acc2);
+                acc3 = fmaf(hu, Cb[12 * cwp + u], acc3);
+            }
+            const float accs[4] = {acc0, acc1, acc2, acc3};
             const long long mxlo = HALF, mxhi = (long long)(2 * W - 3) * HALF;
             const long long mylo = HALF, myhi = (long long)(2 * H - 3) * HALF;
             const long long dpx = 2LL * kRowStep * V.sq, dpy = 2LL * kRowStep * V.cq;
@@ -453,12 +406,12 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
             long long pxa, pya, pxb, pyb;
             G.map(clampi(x0, 0, Wr - 1), j0 + rg, pxa, pya);
             G.map(clampi(x0 + 1, 0, Wr - 1), j0 + rg, pxb, pyb);
-            for (int r = rg; r < nrows; r += kRowStep, pxa += dpx, pya += dpy, pxb += dpx, pyb += dpy) {
-                const int j = j0 + r;
-                const float *Brow = Bs + r * bw_max - bx0;
-                float v = 0.f;
 #pragma unroll
-                for (int m = 0; m < 6; ++m) v = fmaf(w[m], Brow[x0 + m - 2], v);
+            for (int q = 0; q < kWarpTH / kRowStep; ++q, pxa += dpx, pya += dpy, pxb += dpx, pyb += dpy) {
+                const int r = rg + q * kRowStep;
+                if (r >= nrows) break;
+                const int j = j0 + r;
+                const float v = accs[q];
                 const bool valid = cols_ok && pxa >= mxlo && pxa <= mxhi && pya >= mylo && pya <= myhi &&
                                    pxb >= mxlo && pxb <= mxhi && pyb >= mylo && pyb <= myhi;
                 const size_t o = (size_t)V.out_off + (size_t)j * V.Wv + x;
@@ -471,13 +424,46 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
     }
 }
 
+// The Gaussian + tilt filter of every view column (one thread per column;
+// blockIdx.y = view): X = t (x - (Wv-1)/2) + (Wr-1)/2 in Q32, Lanczos-3 weights
+// w_m of the tilt taps at the canvas columns clamp(x0 - 2 + m), and
+// h[u] = sum_m w_m g_|off_m + K - u| with off_m = clamp(x0 - 2 + m) - (x0 - 2),
+// so that sum_u h[u] C(x0 - 2 - K + u) = sum_m w_m B(clamp(x0 - 2 + m)) with
+// B(i) = sum_k g_|k| C(clamp(i - k)) exactly (the canvas strip holds clamped
+// columns).  Entries past 2K + 5 are zero.
+__global__ void tilt_filter_kernel(const DevView *__restrict__ views)
+{
+    const DevView &V = views[blockIdx.y];
+    const int Wv = V.Wv, Wr = V.Wr, K = V.K, hp = V.hp;
+    const long long xoff = (long long)(Wr - 1) * 2147483648LL;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < Wv; x += gridDim.x * blockDim.x) {
+        const long long X = V.tq * (2LL * x - Wv + 1) + xoff;
+        const int x0 = (int)(X >> 32);
+        float w[6];
+        lanczos3_weights((uint32_t)X, w);
+        int off[6];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) off[m] = clampi(x0 - 2 + m, 0, Wr - 1) - (x0 - 2);
+        float *h = V.filt + (size_t)x * hp;
+        for (int u = 0; u < hp; ++u) {
+            float s = 0.f;
+#pragma unroll
+            for (int m = 0; m < 6; ++m) {
+                const int k = abs(off[m] + K - u);
+                if (k <= K) s = fmaf(w[m], V.g[k], s);
+            }
+            h[u] = s;
+        }
+    }
+}
+
 // Grid-stride over the tiles: one CTA per tile, or a persistent grid.
 __global__ void __launch_bounds__(kWarpThreads, 3)
-warp_view_kernel(int n_tiles, const DevView *__restrict__ views, int n_views, int cw_max, int bw_max,
+warp_view_kernel(int n_tiles, const DevView *__restrict__ views, int n_views, int cwp,
                  uint8_t *__restrict__ out_u8, uint8_t *__restrict__ out_mask, float *__restrict__ out_f32)
 {
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        warp_view_tile(tile, views, n_views, cw_max, bw_max, out_u8, out_mask, out_f32);
+        warp_view_tile(tile, views, n_views, cwp, out_u8, out_mask, out_f32);
         __syncthreads();
     }
 }
@@ -485,17 +471,22 @@ warp_view_kernel(int n_tiles, const DevView *__restrict__ views, int n_views, in
 // ---------------------------------------------------------------- host side
 void warp_strip_widths(const asift_view_desc &v, int *cw, int *bw)
 {
-    // B strip: floor(X) - 2 .. floor(X) + 3 over kWarpTW view columns spaced
-    // t apart (+1 for the rounding of tq), rounded up to whole groups of four;
-    // C strip adds K rounded up to a multiple of 4 on both sides.
+    // tilt taps: floor(X) - 2 .. floor(X) + 3 over kWarpTW view columns
+    // spaced t apart (+1 for the rounding of tq); the C strip adds K on both
+    // sides for the Gaussian.
     const int span = (int)std::ceil(v.t * (kWarpTW - 1)) + 2;
-    *bw = ((span + 6) + 3) & ~3;
-    *cw = *bw + 2 * ((v.K + 3) & ~3);
+    *bw = span + 6;
+    *cw = *bw + 2 * v.K;
 }
 
-size_t warp_smem_bytes(int cw_max, int bw_max)
+int tilt_filter_pitch(int K) { return (2 * K + 6 + 3) & ~3; }
+
+static int strip_pitch(int cw_max) { return ((cw_max + 3) & ~3) + 1; }
+
+size_t warp_smem_bytes(int cw_max, int hp_max)
 {
-    return sizeof(float) * ((size_t)kWarpTH * cw_max + std::max((size_t)2 * kStageBuf, (size_t)kWarpTH * bw_max));
+    (void)hp_max;
+    return sizeof(float) * ((size_t)kWarpTH * strip_pitch(cw_max) + (size_t)2 * kStageBuf);
 }
 
 // The rotation step's warp footprint (lanes_x canvas columns x 32 / lanes_x
@@ -583,15 +574,23 @@ cudaError_t launch_convert_images(const ImageConv *d_list, int n, long long max_
     return cudaGetLastError();
 }
 
-cudaError_t launch_warp(const DevView *d_views, int n_views, int n_tiles, int cw_max, int bw_max,
+cudaError_t launch_tilt_filter(const DevView *d_views, int n_views, int max_wv, cudaStream_t s)
+{
+    if (n_views <= 0 || max_wv <= 0) return cudaSuccess;
+    tilt_filter_kernel<<<dim3((max_wv + 127) / 128, n_views), 128, 0, s>>>(d_views);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_warp(const DevView *d_views, int n_views, int n_tiles, int cw_max, int hp_max,
                         uint8_t *u8, uint8_t *mask, float *f32, cudaStream_t s, int grid)
 {
     if (n_tiles <= 0) return cudaSuccess;
-    const size_t smem = warp_smem_bytes(cw_max, bw_max);
+    const size_t smem = warp_smem_bytes(cw_max, hp_max);
     const cudaError_t e = ensure_dynamic_smem((const void *)warp_view_kernel, smem);
     if (e != cudaSuccess) return e;
     const int g = (grid > 0 && grid < n_tiles) ? grid : n_tiles;
-    warp_view_kernel<<<g, kWarpThreads, smem, s>>>(n_tiles, d_views, n_views, cw_max, bw_max, u8, mask, f32);
+    warp_view_kernel<<<g, kWarpThreads, smem, s>>>(n_tiles, d_views, n_views, strip_pitch(cw_max), u8, mask, f32);
     note_launch();
     return cudaGetLastError();
 }
