@@ -167,34 +167,44 @@ __device__ __forceinline__ void detect_tile(int tile, const DevLevel *__restrict
     if (x0 + kDetTW + 1 <= kBorder || y0 + kDetTH + 1 <= kBorder || x0 - 1 >= W - kBorder || y0 - 1 >= H - kBorder)
         return;
     const int tc = threadIdx.x % kDetCols, tr = threadIdx.x / kDetCols;
+    constexpr int kThreads = kDetCols * kDetRowsPar;
 
     if (threadIdx.x == 0) ncl = 0;
+    // staging, ring flags and Sobel walk their boxes as flat index ranges so
+    // that every lane has work (box widths are not multiples of the block)
     const uint8_t *__restrict__ I = L.img;
     const bool interior = x0 - kHalo >= 0 && y0 - kHalo >= 0 && x0 + kDetTW + kHalo <= W && y0 + kDetTH + kHalo <= H;
-    for (int r = tr; r < kSH; r += kDetRowsPar) {
+    for (int el = threadIdx.x; el < kSH * kSW; el += kThreads) {
+        const int r = el / kSW, c = el - r * kSW;
         const int gyy = interior ? y0 - kHalo + r : clampi(y0 - kHalo + r, 0, H - 1);
-        const uint8_t *row = I + gyy * W;
-        for (int c = tc; c < kSW; c += kDetCols) {
-            const int gxx = interior ? x0 - kHalo + c : clampi(x0 - kHalo + c, 0, W - 1);
-            img[r][c] = row[gxx];
-        }
+        const int gxx = interior ? x0 - kHalo + c : clampi(x0 - kHalo + c, 0, W - 1);
+        img[r][c] = I[gyy * W + gxx];
     }
     __syncthreads();
 
-    // corner flags on the tile + ring
+    // corner flags on the tile + ring; corners appended with one shared
+    // atomic per warp (every lane runs every iteration)
     const int xlo = kBorder, xhi = W - kBorder, ylo = kBorder, yhi = H - kBorder;
-    for (int r = tr; r < kRH; r += kDetRowsPar) {
-        const int y = y0 - 1 + r;
-        for (int c = tc; c < kRW; c += kDetCols) {
-            const int x = x0 - 1 + c;
-            uint8_t flag = 0;
-            if (x >= xlo && x < xhi && y >= ylo && y < yhi && fast9_staged(&img[r - 1 + kHalo][c - 1 + kHalo], thr)) {
-                const uint8_t *M = L.mask;
-                const int b = kBorder;
-                flag = M[(y - b) * W + x - b] & M[(y - b) * W + x + b] & M[(y + b) * W + x - b] & M[(y + b) * W + x + b];
-            }
-            isc[r][c] = flag;
-            if (flag) clist[atomicAdd(&ncl, 1)] = (int16_t)(r * kRW + c);
+    const unsigned lane_id = threadIdx.x & 31u;
+#pragma unroll 1
+    for (int k = 0; k < (kRH * kRW + kThreads - 1) / kThreads; ++k) {
+        const int el = (int)threadIdx.x + k * kThreads;
+        const int r = el / kRW, c = el - r * kRW;
+        const int x = x0 - 1 + c, y = y0 - 1 + r;
+        uint8_t flag = 0;
+        if (el < kRH * kRW && x >= xlo && x < xhi && y >= ylo && y < yhi &&
+            fast9_staged(&img[r - 1 + kHalo][c - 1 + kHalo], thr)) {
+            const uint8_t *M = L.mask;
+            const int b = kBorder;
+            flag = M[(y - b) * W + x - b] & M[(y - b) * W + x + b] & M[(y + b) * W + x - b] & M[(y + b) * W + x + b];
+        }
+        if (el < kRH * kRW) isc[r][c] = flag;
+        const unsigned bal = __ballot_sync(0xffffffffu, flag != 0);
+        if (bal) {
+            int base = 0;
+            if (lane_id == 0) base = atomicAdd(&ncl, __popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (flag) clist[base + __popc(bal & ((1u << lane_id) - 1u))] = (int16_t)(r * kRW + c);
         }
     }
     __syncthreads();
@@ -203,14 +213,13 @@ __device__ __forceinline__ void detect_tile(int tile, const DevLevel *__restrict
 
     // Sobel derivatives once per pixel of the ring's windows; gradient (r, c)
     // is image pixel (x0 - 4 + c, y0 - 4 + r), staged pixel (c + 1, r + 1)
-    for (int r = tr; r < kGH; r += kDetRowsPar) {
-        for (int c = tc; c < kGW; c += kDetCols) {
-            const int X = c + 1, Y = r + 1;
-            gx[r][c] = (int16_t)((img[Y - 1][X + 1] + 2 * img[Y][X + 1] + img[Y + 1][X + 1]) -
-                                 (img[Y - 1][X - 1] + 2 * img[Y][X - 1] + img[Y + 1][X - 1]));
-            gy[r][c] = (int16_t)((img[Y + 1][X - 1] + 2 * img[Y + 1][X] + img[Y + 1][X + 1]) -
-                                 (img[Y - 1][X - 1] + 2 * img[Y - 1][X] + img[Y - 1][X + 1]));
-        }
+    for (int el = threadIdx.x; el < kGH * kGW; el += kThreads) {
+        const int r = el / kGW, c = el - r * kGW;
+        const int X = c + 1, Y = r + 1;
+        gx[r][c] = (int16_t)((img[Y - 1][X + 1] + 2 * img[Y][X + 1] + img[Y + 1][X + 1]) -
+                             (img[Y - 1][X - 1] + 2 * img[Y][X - 1] + img[Y + 1][X - 1]));
+        gy[r][c] = (int16_t)((img[Y + 1][X - 1] + 2 * img[Y + 1][X] + img[Y + 1][X + 1]) -
+                             (img[Y - 1][X - 1] + 2 * img[Y - 1][X] + img[Y - 1][X + 1]));
     }
     __syncthreads();
 
