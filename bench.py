@@ -36,6 +36,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 H, W, KMAX, LEVELS, NFEAT, THR = 768, 1024, 5, 8, 1000, 20
+LARGE_H, LARGE_W, LARGE_KMAX, LARGE_NFEAT = 3072, 4096, 6, 2000
 WORKLOAD = "asift_pair_1024x768_extreme_tilt_43views_orb8x1000"
 SM_COUNT = 152
 POPC_PER_SM_CLK = 16       # 32-bit population count: 16 results / clock / SM
@@ -58,6 +59,31 @@ def _mixed_one(seed: int, index: int):
     from paper_2503_03479_gb300 import synth
     p = synth.mixed_pair(seed, index)
     return p.img1, p.img2
+
+
+def _large_one(seed: int, index: int):
+    """A 4096x3072 pair of the large extreme-tilt batch: the texture generator
+    at half size upsampled 2x (the full-size 2x canonical texture takes
+    minutes to draw), image 2 = image 1 under an affine tilt t ~ U[2, 8.2]
+    (absolute tilt up to 83 deg) at a random angle."""
+    import math
+    from paper_2503_03479_gb300 import synth
+    rng = np.random.default_rng(seed * 1000 + index)
+    base = synth.texture(LARGE_H // 2, LARGE_W // 2, seed * 1000 + index)
+    img1 = np.kron(base, np.ones((2, 2), np.uint8))
+    t = float(rng.uniform(2.0, 1 / math.cos(math.radians(83))))
+    A = synth.tilt_about_centre(img1.shape, img1.shape, t, float(rng.uniform(0, 180)), 1.0)
+    img2 = np.clip(np.rint(synth.render(img1, A, img1.shape, ss=1)), 0, 255).astype(np.uint8)
+    return img1, img2
+
+
+def large_batch(n_pairs: int, seed: int):
+    import multiprocessing as mp
+    if n_pairs <= 0:
+        return []
+    workers = max(1, min(16, os.cpu_count() or 1, n_pairs))
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.starmap(_large_one, [(seed, i) for i in range(n_pairs)])
 
 
 def mixed_batch(n_pairs: int, seed: int):
@@ -317,6 +343,7 @@ def run_ours(args):
     rank, world, local = _dist_env()
     t_gen = time.perf_counter()
     batch = mixed_batch(args.batch_pairs, 3000 + rank)
+    big = large_batch(args.large_pairs, 5000 + rank)
     t_gen = time.perf_counter() - t_gen
     import torch
     torch.cuda.set_device(local)
@@ -472,6 +499,38 @@ def run_ours(args):
                    "plan_create_s": t_plan, "autotune_s": t_tune, "generate_s": t_gen}
         del b1, b2
 
+    # ---- large extreme-tilt batch: 4096x3072 pairs, 63 views per image, 2000 keypoints per view
+    large = None
+    if big:
+        ctx_l = A.Context(n_levels=LEVELS, n_features=LARGE_NFEAT, fast_threshold=THR)
+        g1 = [torch.from_numpy(a).cuda() for a, _ in big]
+        g2 = [torch.from_numpy(b).cuda() for _, b in big]
+        nv_l = len(A.view_table(LARGE_H, LARGE_W, LARGE_KMAX))
+        planl = A.Plan(ctx_l, g1, g2, kmax=LARGE_KMAX)
+        tun_l = planl.autotune(reps=1)
+        planl.run()
+        torch.cuda.synchronize()
+        if planl.status() != 0:
+            raise RuntimeError("device status word set in the large batch")
+        cnt_l = planl.pool_counts()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps_l = 3
+        e0.record(stream)
+        for _ in range(reps_l):
+            planl.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_l = e0.elapsed_time(e1) / reps_l
+        npl = len(big)
+        pairs_desc = float(sum(int(cnt_l[2 * i]) * int(cnt_l[2 * i + 1]) for i in range(npl)))
+        large = {"pairs": npl, "image": f"{LARGE_W}x{LARGE_H}", "views_per_image": nv_l,
+                 "features_per_view": LARGE_NFEAT, "ms_per_batch": ms_l, "pairs_per_s": npl / (ms_l / 1e3),
+                 "views_per_s": 2 * nv_l * npl / (ms_l / 1e3),
+                 "descriptors_per_image_mean": float(cnt_l.mean()),
+                 "hamming_pairs_per_batch": pairs_desc, "tuning": tun_l}
+        planl.close()
+        del g1, g2, ctx_l
+
     # ---- differentiable warp: 256 views of 512x512 fp32 images, forward + backward
     diff = None
     if args.diff_views > 0:
@@ -541,6 +600,7 @@ def run_ours(args):
                 "plain_per_view": plain,
                 "batched_vs_plain": (value / world) / plain["value"] if plain else None,
                 "batched_mixed": batched,
+                "large_batched": large,
                 "differentiable": diff,
                 "roofline": roofline, "rooflines": rooflines, "match_engine": ctx.match_engine,
                 "match_engines": engines,
@@ -562,6 +622,7 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-pairs", type=int, default=64, help="pairs in the mixed-size batched run (0: skip)")
+    ap.add_argument("--large-pairs", type=int, default=8, help="pairs in the 4096x3072 batched run (0: skip)")
     ap.add_argument("--diff-views", type=int, default=256, help="views of the differentiable-warp timing (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":

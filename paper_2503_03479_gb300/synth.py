@@ -184,10 +184,11 @@ def pair_affine_small(seed: int = 1000, H: int = 240, W: int = 320,
 
 def pair_extreme_tilt(seed: int = 2000, H: int = 768, W: int = 1024,
                       t1: float = 2.97, t2: float = 1 / math.cos(math.radians(75)),
-                      phi1: float | None = None, noise_sigma: float = 2.0) -> Pair:
+                      phi1: float | None = None, noise_sigma: float = 2.0, ss: int = 4) -> Pair:
     """A large canonical texture seen twice: image 1 with absolute tilt t1 along
     phi1, image 2 under a homography with local tilt t2 along phi1 + 90 deg
-    (transition tilt t1*t2), plus Gaussian noise on image 2."""
+    (transition tilt t1*t2), plus Gaussian noise on image 2.  ss: supersampling
+    per axis of the rendering."""
     rng = _rng(seed + 7)
     if phi1 is None:
         phi1 = float(rng.uniform(0, 180))
@@ -197,8 +198,8 @@ def pair_extreme_tilt(seed: int = 2000, H: int = 768, W: int = 1024,
     zoom2 = zoom1
     A1 = tilt_about_centre(tex.shape, (H, W), t1, phi1, zoom1)
     H2 = perspective_tilt(tex.shape, (H, W), t2, phi1 + 90.0, zoom2, persp=1e-4)
-    img1 = np.clip(np.rint(render(tex, A1, (H, W))), 0, 255).astype(np.uint8)
-    im2 = render(tex, H2, (H, W))
+    img1 = np.clip(np.rint(render(tex, A1, (H, W), ss=ss)), 0, 255).astype(np.uint8)
+    im2 = render(tex, H2, (H, W), ss=ss)
     if noise_sigma > 0:
         im2 = im2 + rng.standard_normal(im2.shape) * noise_sigma
     img2 = np.clip(np.rint(im2), 0, 255).astype(np.uint8)
@@ -256,3 +257,15 @@ def random_u8(shape, seed: int) -> np.ndarray:
 def random_descriptors(n: int, seed: int) -> np.ndarray:
     """n x 32 uint8 random 256-bit descriptors."""
     return _rng(seed).integers(0, 256, size=(n, 32), dtype=np.uint8)
+
+
+def large_pair(seed: int, index: int, H: int = 3072, W: int = 4096, ss: int = 1) -> Pair:
+    """Pair `index` of the large extreme-tilt batch: pair_extreme_tilt at
+    H x W with absolute tilts t1, t2 drawn from [1/cos 60 deg, 1/cos 83 deg]
+    (t up to 8.2), generated independently of the other pairs."""
+    rng = _rng(seed * 1000 + index)
+    tmax = 1 / math.cos(math.radians(83))
+    t1 = float(rng.uniform(2.0, tmax))
+    t2 = float(rng.uniform(2.0, tmax))
+    return pair_extreme_tilt(seed * 1000 + index, H, W, t1=t1, t2=t2, ss=ss)
+
