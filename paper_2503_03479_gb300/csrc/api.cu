@@ -200,7 +200,8 @@ static void build_views(const asift_view_desc *h, int nv, const float *const *sr
         d.sq = a.sq;
         d.tq = a.tq;
         d.out_off = out_off[v];
-        d.ntx = (a.Wv + kWarpTW - 1) / kWarpTW;
+        d.tw = warp_tile_width(a);
+        d.ntx = (a.Wv + d.tw - 1) / d.tw;
         {
             int lx = 32, pitch = 72;
             warp_lane_layout(a.cq, a.sq, &lx, &pitch);
@@ -225,7 +226,7 @@ static void build_views(const asift_view_desc *h, int nv, const float *const *sr
         d.filt = H ? H + hoff : nullptr;
         hoff += (size_t)a.Wv * d.hp;
         int cw, bw;
-        warp_strip_widths(a, &cw, &bw);
+        warp_strip_widths(a, d.tw, &cw, &bw);
         cwm = std::max(cwm, cw);
         hpm = std::max(hpm, d.hp);
         wvm = std::max(wvm, a.Wv);

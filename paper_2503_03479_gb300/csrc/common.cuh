@@ -23,7 +23,8 @@ struct DevView {
     int32_t ntx;            // tiles along x
     int16_t lanes_x;        // canvas columns of a warp's footprint in the rotation step (32, 16 or 8)
     int16_t stage_pitch;    // row pitch (floats) of the staged source box
-    int32_t hp, pad2;       // floats per view column in filt (>= 2K + 6, a multiple of 4)
+    int32_t hp;             // floats per view column in filt (>= 2K + 6, a multiple of 4)
+    int32_t tw;             // view columns per tile (<= kWarpTW, chosen per view)
     float *filt;            // per view column x: the Gaussian + tilt filter over canvas columns x0-2-K .. x0+3+K
     long long cq, sq, tq;   // Q31 cos, sin, tilt
     long long out_off;      // byte offset of the view in the u8 / mask arenas
@@ -31,7 +32,7 @@ struct DevView {
     float g[ASIFT_MAX_GAUSS];
 };
 
-constexpr int kWarpTW = 64;   // view columns per warp tile
+constexpr int kWarpTW = 64;   // most view columns per warp tile
 constexpr int kWarpTH = 16;   // view rows per warp tile
 constexpr int kWarpThreads = 256;
 

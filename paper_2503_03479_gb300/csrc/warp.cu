@@ -1,6 +1,7 @@
 // warp.cu -- affine view simulation (Eq. (2)-(4)) on sm_103a.
 //
-// One CTA produces a kWarpTW x kWarpTH tile of one view.  A view row j only
+// One CTA produces a tw x kWarpTH tile of one view (tw <= kWarpTW chosen per
+// view, see warp_tile_width).  A view row j only
 // depends on canvas row j (the tilt acts along canvas x), so the tile needs a
 // canvas strip of kWarpTH rows and columns [bx0 - K, bx1 + K], where
 // [bx0, bx1] = [floor(X(x'_first)) - 2, floor(X(x'_last)) + 3] are the columns
@@ -262,7 +263,7 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
     const DevView &V = views[vi];
     const int lt = tile - V.tile_start;
     const int ty = lt / V.ntx, tx = lt - ty * V.ntx;
-    const int xa = tx * kWarpTW, xb = min(xa + kWarpTW, V.Wv) - 1;
+    const int xa = tx * V.tw, xb = min(xa + V.tw, V.Wv) - 1;
     const int j0 = ty * kWarpTH, j1 = min(j0 + kWarpTH, V.Hv) - 1;
     const int nrows = j1 - j0 + 1;
     const int Wr = V.Wr, K = V.K, W = V.W, H = V.H;
@@ -469,14 +470,35 @@ warp_view_kernel(int n_tiles, const DevView *__restrict__ views, int n_views, in
 }
 
 // ---------------------------------------------------------------- host side
-void warp_strip_widths(const asift_view_desc &v, int *cw, int *bw)
+void warp_strip_widths(const asift_view_desc &v, int tw, int *cw, int *bw)
 {
-    // tilt taps: floor(X) - 2 .. floor(X) + 3 over kWarpTW view columns
-    // spaced t apart (+1 for the rounding of tq); the C strip adds K on both
-    // sides for the Gaussian.
-    const int span = (int)std::ceil(v.t * (kWarpTW - 1)) + 2;
+    // tilt taps: floor(X) - 2 .. floor(X) + 3 over tw view columns spaced t
+    // apart (+1 for the rounding of tq); the C strip adds K on both sides for
+    // the Gaussian.
+    const int span = (int)std::ceil(v.t * (tw - 1)) + 2;
     *bw = span + 6;
     *cw = *bw + 2 * v.K;
+}
+
+// View columns per tile: the rotation step works in chunks of kChunk canvas
+// columns, so a strip just past a multiple of kChunk leaves most lanes of its
+// last chunk idle.  Pick tw in [32, kWarpTW] minimising the lane-columns of
+// all the view's tiles plus a per-tile overhead (worth half a chunk).
+int warp_tile_width(const asift_view_desc &v)
+{
+    int best = kWarpTW;
+    long long best_cost = -1;
+    for (int tw = kWarpTW; tw >= 32; --tw) {
+        int cw, bw;
+        warp_strip_widths(v, tw, &cw, &bw);
+        const long long tiles = (v.Wv + tw - 1) / tw;
+        const long long cost = tiles * ((long long)((cw + kChunk - 1) / kChunk) * kChunk + kChunk / 2);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = tw;
+        }
+    }
+    return best;
 }
 
 int tilt_filter_pitch(int K) { return (2 * K + 6 + 3) & ~3; }
