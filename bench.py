@@ -28,6 +28,7 @@ import os
 import statistics
 import subprocess
 import sys
+import threading
 import time
 
 import numpy as np
@@ -98,7 +99,9 @@ def mixed_batch(n_pairs: int, seed: int):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms during the timed
+    region: the sampler is started, its first line awaited (nvidia-smi takes a
+    moment to start), and only lines read after that count."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -107,29 +110,46 @@ class ClockSampler:
     def __init__(self, gpu: int):
         self.gpu = gpu
         self.p = None
+        self.lines = []
+        self._buf = []
+        self._first = threading.Event()
+        self._t = None
+
+    def _read(self):
+        for l in self.p.stdout:
+            if l.strip():
+                self._buf.append(l)
+                self._first.set()
 
     def __enter__(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (FileNotFoundError, OSError):
             self.p = None
+            return self
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+        self._first.wait(timeout=5.0)
+        self._start = len(self._buf)
         return self
 
     def __exit__(self, *a):
-        self.lines = []
-        if self.p is not None:
-            self.p.terminate()
-            try:
-                out, _ = self.p.communicate(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.p.kill()
-                out, _ = self.p.communicate()
-            self.lines = [l for l in out.splitlines() if l.strip()]
+        if self.p is None:
+            return
+        n = len(self._buf)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            self.p.wait()
+        self._t.join(timeout=5)
+        self.lines = self._buf[self._start:n]
 
     def summary(self):
-        if not getattr(self, "lines", None):
+        if not self.lines:
             return None
         sm, smax, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -188,11 +208,15 @@ def warp_roofline(views, n_images: int, ms: float, peaks: dict) -> dict:
             "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 FMA/clk x 2 x {f_clk/1e6:.0f} MHz"}
 
 
-def match_roofline(n1: int, n2: int, ms: float, tensor: bool, peaks: dict) -> dict:
+def match_roofline(sizes, ms: float, tensor: bool, peaks: dict) -> dict:
+    """Matcher roofline over the step's pairs: `sizes` holds (n1, n2) of each
+    pair the steps cycle through and `ms` is the mean stage time over those
+    steps, so the work per step is the mean of n1 x n2."""
+    pairs = statistics.mean(n1 * n2 for n1, n2 in sizes)
     if tensor:
         bf16 = peaks.get("bf16_tflops")
         peak = (bf16 or 1900.0) * FP8_PER_BF16
-        flops = 2.0 * 256 * n1 * n2                  # one +-1 dot product of length 256 per pair
+        flops = 2.0 * 256 * pairs                    # one +-1 dot product of length 256 per pair
         achieved = flops / (ms / 1e3) / 1e12
         src = (f"fp8 = measured bf16 {bf16} TFLOP/s x nominal fp8/bf16 ratio {FP8_PER_BF16}" if bf16 else
                f"fp8 = fallback bf16 1900 TFLOP/s x nominal ratio {FP8_PER_BF16}")
@@ -201,7 +225,7 @@ def match_roofline(n1: int, n2: int, ms: float, tensor: bool, peaks: dict) -> di
                 "flops_per_launch": flops, "peak_source": src}
     f_clk = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
     peak = SM_COUNT * POPC_PER_SM_CLK * f_clk / 1e12
-    achieved = n1 * n2 * POPC_PER_PAIR / (ms / 1e3) / 1e12
+    achieved = pairs * POPC_PER_PAIR / (ms / 1e3) / 1e12
     return {"bound": "alu", "kernel": "hamming_top2_kernel (+ merge_kernel)", "achieved": achieved,
             "peak": peak, "unit": "Tpopc/s", "frac": achieved / peak, "traffic": None,
             "peak_source": f"derived: {SM_COUNT} SMs x {POPC_PER_SM_CLK} popc/clk x {f_clk/1e6:.0f} MHz"}
@@ -415,13 +439,19 @@ def run_ours(args):
     # ---- rooflines of the two heaviest stages, timed live by the stage events
     st = {k: statistics.mean(s[k] for s in stage_ms) for k in stage_ms[0]}
     n_acc = int(n_out.item())
-    kp1, dd1, kp2, dd2, _ = ctx.inspect_pair((H, W), (H, W), pc, ws)
-    n1, n2 = len(kp1), len(kp2)
+    # pool sizes of each pair the steps alternate over; the last pair's pools
+    # feed the engine comparison below
+    sizes = []
+    for i in range(n_pairs):
+        step(i)
+        kp1, dd1, kp2, dd2, _ = ctx.inspect_pair((H, W), (H, W), pc, ws)
+        sizes.append((len(kp1), len(kp2)))
+    n1, n2 = sizes[-1]
     peaks = _peaks()
     clocks = clk.summary()
     views = A.view_table(H, W, KMAX)
     rooflines = {"warp": warp_roofline(views, 2, st["warp"], peaks),
-                 "match": match_roofline(n1, n2, st["match"], ctx.match_engine == A.MATCH_TENSOR_CORES, peaks)}
+                 "match": match_roofline(sizes, st["match"], ctx.match_engine == A.MATCH_TENSOR_CORES, peaks)}
     for k, r in rooflines.items():
         r["traffic"] = profiled_traffic(r["kernel"].split()[0])
     dominant = max(rooflines, key=lambda k: st[k])
@@ -596,7 +626,7 @@ def run_ours(args):
                            "l2": "flushed between steps (256 MB write)", "form": "batched: one launch per stage"},
                 "views_per_s": value * 2 * nv,
                 "stage_ms": st,
-                "keypoints": [n1, n2], "accepted": n_acc,
+                "keypoints": [list(x) for x in sizes], "accepted": n_acc,
                 "plain_per_view": plain,
                 "batched_vs_plain": (value / world) / plain["value"] if plain else None,
                 "batched_mixed": batched,
@@ -616,7 +646,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--plain-steps", type=int, default=3)

@@ -3,8 +3,12 @@
 //
 // A 256-bit descriptor becomes 256 fp8 (e4m3) values, +1 for a 0 bit and -1 for
 // a 1 bit; then q.t = 256 - 2 H(q, t) exactly (every product is +-1 and an fp32
-// sum of at most 256 of them is exact).  A CTA owns one SM and works through
-// items of (problem, 256 queries, train slice):
+// sum of at most 256 of them is exact).  A CTA owns one SM and works through a
+// contiguous range of items of (problem, 256 queries, train slice), numbered
+// query-block-major: consecutive items of one query block (a run) share the
+// query tile, loaded once, and the epilogue's running top two, so that its
+// threshold is not reset at every slice boundary (slices folded into a run
+// leave empty partial keys):
 //   warp 0     TMA producer: the item's query tile (2 x 128 rows) once, then
 //              128-row train tiles through a kTcStages-deep ring (K-major,
 //              128-byte swizzle, two 128-byte column halves per tile),
@@ -164,26 +168,36 @@ __device__ __forceinline__ void insert_score(float s, int col0, unsigned &b1, un
 // One 32-column chunk of a thread's accumulator row (dot products, even
 // integers in [-256, 256]).  Only the chunk's two smallest keys (largest dot,
 // then lowest column) can enter the top two, and none can unless the chunk's
-// maximum beats the current second best: the common case costs 16 three-input
-// max and one compare.  kFull = false masks columns >= valid.
+// maximum beats the current second best (thr, its dot product): the common
+// case costs 16 three-input max and one compare.  Columns only grow along a
+// run, so the chunk's best key k1 is below b1 iff its dot beats b1's (best,
+// its dot product); otherwise k1 becomes at most the new b2 and the chunk's
+// second key, above k1, cannot enter, so the second pass runs only when the
+// chunk beats the best.  kFull = false masks columns >= valid.
 template <bool kFull>
 __device__ __forceinline__ void epi_chunk(const uint32_t r[32], int valid, int col0, unsigned &b1, unsigned &b2,
-                                          float &thr)
+                                          float &thr, float &best)
 {
     float v[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) v[j] = (kFull || j < valid) ? __uint_as_float(r[j]) : -1.0e30f;
-    if (max32(v) > thr) {
+    const float mx = max32(v);
+    if (mx > thr) {
         float sc[32];                                     // 64 v - j: max gives the largest v, then lowest j
 #pragma unroll
         for (int j = 0; j < 32; ++j) sc[j] = fmaf(v[j], 64.0f, -(float)j);
         const float s1 = max32(sc);
+        if (mx > best) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) sc[j] = (sc[j] == s1) ? -3.0e30f : sc[j];
-        const float s2 = max32(sc);
-        insert_score(s1, col0, b1, b2);
-        if (s2 > -1.0e20f) insert_score(s2, col0, b1, b2);
+            for (int j = 0; j < 32; ++j) sc[j] = (sc[j] == s1) ? -3.0e30f : sc[j];
+            const float s2 = max32(sc);
+            insert_score(s1, col0, b1, b2);
+            if (s2 > -1.0e20f) insert_score(s2, col0, b1, b2);
+        } else {
+            insert_score(s1, col0, b1, b2);
+        }
         thr = (b2 == kTcNoKey) ? -1.0e30f : 256.0f - 2.0f * (float)(b2 >> 23);
+        best = (b1 == kTcNoKey) ? -1.0e30f : 256.0f - 2.0f * (float)(b1 >> 23);
     }
 }
 
@@ -193,6 +207,8 @@ __device__ __forceinline__ int tc_count(const int32_t *d, int cap) { return d ? 
 struct TcItem {
     int p, split, qblk, t0, t1;
 };
+
+__device__ __forceinline__ bool same_run(const TcItem &a, const TcItem &b) { return a.p == b.p && a.qblk == b.qblk; }
 
 __global__ void __launch_bounds__(kTcThreads, 1)
 hamming_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap tmap,
@@ -209,7 +225,7 @@ hamming_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constan
     uint64_t *a_full = acc_empty + 2, *a_empty = a_full + 1;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_sh;
-    __shared__ int s_items[kMaxTcProblems + 1], s_chunk[kMaxTcProblems], s_qblocks[kMaxTcProblems];
+    __shared__ int s_items[kMaxTcProblems + 1], s_chunk[kMaxTcProblems], s_nsplit[kMaxTcProblems];
     volatile int *abort_flag = &abort_sh;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -249,7 +265,7 @@ hamming_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constan
                 ns = (nt + ch - 1) / ch;
             }
             s_chunk[p] = ch;
-            s_qblocks[p] = qb;
+            s_nsplit[p] = ns;
             s_items[p] = acc;
             acc += ns * qb;
             if (blockIdx.x == 0) {
@@ -269,20 +285,32 @@ hamming_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constan
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
     const int items = s_items[np];
+    // this CTA's items: a contiguous range (equal shares, one item apart at most)
+    const int i_lo = (int)((long long)items * blockIdx.x / gridDim.x);
+    const int i_hi = (int)((long long)items * (blockIdx.x + 1) / gridDim.x);
 
-    // items are visited in increasing order, so the owning problem only moves forward
+    // items are visited in increasing order, so the owning problem only moves
+    // forward; within a problem item = query block * slices + slice
     auto item_of = [&](int item, int &p) {
         while (s_items[p + 1] <= item) ++p;
         const MatchProblem &P = many ? many[p] : single;
         const int nt = tc_count(P.d_nt, P.nt_cap);
-        const int local = item - s_items[p], qb = s_qblocks[p];
+        const int local = item - s_items[p], ns = s_nsplit[p];
         TcItem it;
         it.p = p;
-        it.split = local / qb;
-        it.qblk = local - it.split * qb;
+        it.qblk = local / ns;
+        it.split = local - it.qblk * ns;
         it.t0 = it.split * s_chunk[p];
         it.t1 = min(nt, it.t0 + s_chunk[p]);
         return it;
+    };
+    // whether item (> i_lo) continues the run of item - 1, and whether item
+    // (< i_hi - 1) is followed by one of its run
+    auto continues = [&](int item, int p) {
+        if (item <= i_lo) return false;
+        int q = p;
+        const TcItem a = item_of(item - 1, q), b = item_of(item, q);
+        return same_run(a, b);
     };
 
     if (warp == 0) {
@@ -292,17 +320,20 @@ hamming_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constan
             uint32_t ph = 0, a_ph = 0;
             unsigned used = 0, par = 0;        // stages with a load issued, parity of their last load
             bool a_used = false;
-            for (int item = blockIdx.x; item < items && !*abort_flag; item += gridDim.x) {
+            for (int item = i_lo; item < i_hi && !*abort_flag; ++item) {
+                const bool cont = continues(item, p);
                 const TcItem it = item_of(item, p);
                 const MatchProblem &P = many ? many[it.p] : single;
                 const int qrow = (int)((P.q - qbase) >> 1) + it.qblk * kTcQB * kTcBM;
                 const int trow = (int)((P.t - tbase) >> 1);
-                if (!mbar_wait(a_empty, a_ph ^ 1, abort_flag, status)) break;
-                mbar_expect_tx(a_full, kTcABytes);
-                tma_load_2d(smA, &qmap, 0, qrow, a_full);
-                tma_load_2d(smA + kTcAHalf, &qmap, 128, qrow, a_full);
-                a_used = true;
-                a_ph ^= 1;
+                if (!cont) {   // a new run: its query tile, once the previous run's MMAs are done with smA
+                    if (!mbar_wait(a_empty, a_ph ^ 1, abort_flag, status)) break;
+                    mbar_expect_tx(a_full, kTcABytes);
+                    tma_load_2d(smA, &qmap, 0, qrow, a_full);
+                    tma_load_2d(smA + kTcAHalf, &qmap, 128, qrow, a_full);
+                    a_used = true;
+                    a_ph ^= 1;
+                }
                 bool ok = true;
                 for (int tb = it.t0; tb < it.t1; tb += kTcBN) {
                     if (!mbar_wait(&empty[stage], ph ^ 1, abort_flag, status)) { ok = false; break; }
@@ -327,10 +358,14 @@ hamming_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constan
             int stage = 0, acc = 0, p = 0, last_acc = -1;
             uint32_t ph = 0, acc_ph = 0, a_ph = 0, last_par = 0;
             const uint32_t a0 = smem_u32(smA), b0 = smem_u32(smB);
-            for (int item = blockIdx.x; item < items && !*abort_flag; item += gridDim.x) {
+            for (int item = i_lo; item < i_hi && !*abort_flag; ++item) {
+                const bool cont = continues(item, p);
+                const bool last_of_run = item + 1 >= i_hi || !continues(item + 1, p);
                 const TcItem it = item_of(item, p);
-                if (!mbar_wait(a_full, a_ph, abort_flag, status)) break;
-                a_ph ^= 1;
+                if (!cont) {
+                    if (!mbar_wait(a_full, a_ph, abort_flag, status)) break;
+                    a_ph ^= 1;
+                }
                 tc_fence_after();
                 bool ok = true;
                 for (int tb = it.t0; tb < it.t1; tb += kTcBN) {
@@ -358,7 +393,7 @@ hamming_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constan
                     if (++stage == kTcStages) { stage = 0; ph ^= 1; }
                     if (++acc == 2) { acc = 0; acc_ph ^= 1; }
                 }
-                umma_commit(a_empty);
+                if (last_of_run || !ok) umma_commit(a_empty);   // the run's MMAs release smA
                 if (!ok) break;
             }
             // the MMAs issued have finished before TMEM is freed
@@ -371,12 +406,18 @@ hamming_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constan
         const int row = qb * kTcBM + quarter * 32 + lane;
         int acc = 0, p = 0;
         uint32_t acc_ph = 0;
-        for (int item = blockIdx.x; item < items && !*abort_flag; item += gridDim.x) {
+        unsigned b1 = kTcNoKey, b2 = kTcNoKey;
+        float thr = -1.0e30f, best = -1.0e30f;           // dot products of b2 and b1 (-inf: none)
+        for (int item = i_lo; item < i_hi && !*abort_flag; ++item) {
+            const bool cont = continues(item, p);
+            const bool last_of_run = item + 1 >= i_hi || !continues(item + 1, p);
             const TcItem it = item_of(item, p);
             const MatchProblem &P = many ? many[it.p] : single;
             const int nq = tc_count(P.d_nq, P.nq_cap);
-            unsigned b1 = kTcNoKey, b2 = kTcNoKey;
-            float thr = -1.0e30f;                        // a dot product must exceed this to enter the top two
+            if (!cont) {
+                b1 = b2 = kTcNoKey;
+                thr = best = -1.0e30f;
+            }
             bool ok = true;
             for (int tb = it.t0; tb < it.t1; tb += kTcBN) {
                 if (!mbar_wait(&acc_full[acc], acc_ph, abort_flag, status)) { ok = false; break; }
@@ -392,11 +433,11 @@ hamming_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constan
                     tmem_ld32(taddr + (uint32_t)(c * 32 + 32), r[1]);
                     tmem_wait_ld();
                     if (valid == kTcBN) {
-                        epi_chunk<true>(r[0], 32, tb + c * 32, b1, b2, thr);
-                        epi_chunk<true>(r[1], 32, tb + c * 32 + 32, b1, b2, thr);
+                        epi_chunk<true>(r[0], 32, tb + c * 32, b1, b2, thr, best);
+                        epi_chunk<true>(r[1], 32, tb + c * 32 + 32, b1, b2, thr, best);
                     } else {
-                        epi_chunk<false>(r[0], valid - c * 32, tb + c * 32, b1, b2, thr);
-                        epi_chunk<false>(r[1], valid - c * 32 - 32, tb + c * 32 + 32, b1, b2, thr);
+                        epi_chunk<false>(r[0], valid - c * 32, tb + c * 32, b1, b2, thr, best);
+                        epi_chunk<false>(r[1], valid - c * 32 - 32, tb + c * 32 + 32, b1, b2, thr, best);
                     }
                 }
                 tc_fence_before();
@@ -405,8 +446,10 @@ hamming_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constan
                 if (++acc == 2) { acc = 0; acc_ph ^= 1; }
             }
             if (!ok) break;
+            // a run's top two go to its last slice; the slices folded into it get none
             const int qi = it.qblk * kTcQB * kTcBM + row;
-            if (qi < nq) P.part[(size_t)it.split * P.nq_cap + qi] = make_uint2(b1, b2);
+            if (qi < nq)
+                P.part[(size_t)it.split * P.nq_cap + qi] = last_of_run ? make_uint2(b1, b2) : make_uint2(kTcNoKey, kTcNoKey);
         }
     }
     tc_fence_before();

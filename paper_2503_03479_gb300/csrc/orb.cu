@@ -103,6 +103,37 @@ pyramid_kernel(int n_tiles, const DevLevel *__restrict__ lv, int n)
     }
 }
 
+// ---------------------------------------------------------------- staging
+// A row copy of the bytes [g, g + n) to shared memory at s, where s and g are
+// congruent mod 4, moves aligned words: word k starts at byte 4k - (g mod 4)
+// of the row (relative to g; a copy has at most (n + 6) / 4 words), and each
+// helper takes that offset from its own pointer.  A word inside the range is
+// one 32-bit load and store, the partial words at the two ends predicated
+// byte loads and stores, so nothing outside [g, g + n) is read and nothing
+// outside [s, s + n) written.
+__device__ __forceinline__ uint32_t load_word(const uint8_t *__restrict__ g, int n, int k)
+{
+    const int lo = 4 * k - (int)((uintptr_t)g & 3u);
+    if (lo >= 0 && lo + 4 <= n) return __ldg(reinterpret_cast<const uint32_t *>(g + lo));
+    uint32_t v = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (lo + j >= 0 && lo + j < n) v |= (uint32_t)__ldg(g + lo + j) << (8 * j);
+    return v;
+}
+
+__device__ __forceinline__ void store_word(uint8_t *s, int n, int k, uint32_t v)
+{
+    const int lo = 4 * k - (int)((uintptr_t)s & 3u);
+    if (lo >= 0 && lo + 4 <= n) {
+        *reinterpret_cast<uint32_t *>(s + lo) = v;
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (lo + j >= 0 && lo + j < n) s[lo + j] = (uint8_t)(v >> (8 * j));
+}
+
 // ---------------------------------------------------------------- detection
 constexpr int kHalo = 5;                        // FAST (3) / Harris (4) at the ring pixels + 1
 constexpr int kSW = kDetTW + 2 * kHalo;         // staged image
@@ -111,6 +142,20 @@ constexpr int kRW = kDetTW + 2, kRH = kDetTH + 2;   // tile + one-pixel ring
 constexpr int kGW = kDetTW + 8, kGH = kDetTH + 8;   // Sobel gradients for the ring's 7x7 windows
 constexpr int kDetCols = 64;                    // threads along x; blockDim = kDetCols * kDetRowsPar
 constexpr int kDetRowsPar = 4;
+// The staged image has a row pitch P in 77..80 congruent to the level's width
+// mod 4 and starts at the address of its first pixel mod 4, so that interior
+// tiles stage with 32-bit loads (load_word); the tile code is instantiated
+// once per pitch so that the stencil offsets stay compile-time constants.
+constexpr int kSPMin = kSW + 3, kSPMax = kSPMin + 3;
+
+struct DetSmem {
+    long long R[kRH][kRW];
+    int16_t gx[kGH][kGW], gy[kGH][kGW];
+    int16_t clist[kRH * kRW];
+    __align__(16) uint8_t img[kSH * kSPMax];
+    uint8_t isc[kRH][kRW];
+    int ncl;
+};
 
 // 1 iff 9 cyclically consecutive bits of the 16-bit mask m are set.
 __device__ __forceinline__ bool has_run9(unsigned m)
@@ -123,21 +168,22 @@ __device__ __forceinline__ bool has_run9(unsigned m)
     return r != 0u;
 }
 
-// FAST-9 at the staged pixel p (row pitch kSW): the Bresenham circle of radius
+// FAST-9 at the staged pixel p (row pitch P): the Bresenham circle of radius
 // 3 from (0,-3) clockwise, with compile-time offsets.  A 9-arc holds at least
 // 2 of the 4 compass points, so pixels with fewer bright and fewer dark
 // compass points are rejected before the full test.
+template <int P>
 __device__ __forceinline__ bool fast9_staged(const uint8_t *p, int thr)
 {
     const int ctr = p[0];
     const int hi = ctr + thr, lo = ctr - thr;
-    const int n0 = p[-3 * kSW], n4 = p[3], n8 = p[3 * kSW], n12 = p[-3];
+    const int n0 = p[-3 * P], n4 = p[3], n8 = p[3 * P], n12 = p[-3];
     const int nb = (n0 > hi) + (n4 > hi) + (n8 > hi) + (n12 > hi);
     const int nd = (n0 < lo) + (n4 < lo) + (n8 < lo) + (n12 < lo);
     if (nb < 2 && nd < 2) return false;
-    const int v[16] = {n0, p[-3 * kSW + 1], p[-2 * kSW + 2], p[-kSW + 3], n4, p[kSW + 3], p[2 * kSW + 2],
-                       p[3 * kSW + 1], n8, p[3 * kSW - 1], p[2 * kSW - 2], p[kSW - 3], n12, p[-kSW - 3],
-                       p[-2 * kSW - 2], p[-3 * kSW - 1]};
+    const int v[16] = {n0, p[-3 * P + 1], p[-2 * P + 2], p[-P + 3], n4, p[P + 3], p[2 * P + 2],
+                       p[3 * P + 1], n8, p[3 * P - 1], p[2 * P - 2], p[P - 3], n12, p[-P - 3],
+                       p[-2 * P - 2], p[-3 * P - 1]};
     unsigned bm = 0, dm = 0;
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
@@ -147,17 +193,17 @@ __device__ __forceinline__ bool fast9_staged(const uint8_t *p, int thr)
     return has_run9(bm) || has_run9(dm);
 }
 
-__device__ __forceinline__ void detect_tile(int tile, const DevLevel *__restrict__ lv, int n, int thr, Candidate *__restrict__ cand,
-              int32_t *__restrict__ cand_count)
+template <int P>
+__device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__restrict__ lv, int thr, Candidate *__restrict__ cand,
+              int32_t *__restrict__ cand_count, DetSmem &sm)
 {
-    __shared__ uint8_t img[kSH][kSW];
-    __shared__ uint8_t isc[kRH][kRW];
-    __shared__ long long R[kRH][kRW];
-    __shared__ int16_t gx[kGH][kGW], gy[kGH][kGW];
-    __shared__ int16_t clist[kRH * kRW];
-    __shared__ int ncl;
+    auto &isc = sm.isc;
+    auto &R = sm.R;
+    auto &gx = sm.gx;
+    auto &gy = sm.gy;
+    int16_t *clist = sm.clist;
+    int &ncl = sm.ncl;
 
-    const int e = find_owner(lv, n, tile, [](const DevLevel &d) { return d.det_tile_start; });
     const DevLevel &L = lv[e];
     const int lt = tile - L.det_tile_start;
     const int ty = lt / L.det_ntx, tx = lt - ty * L.det_ntx;
@@ -170,15 +216,24 @@ __device__ __forceinline__ void detect_tile(int tile, const DevLevel *__restrict
     constexpr int kThreads = kDetCols * kDetRowsPar;
 
     if (threadIdx.x == 0) ncl = 0;
-    // staging, ring flags and Sobel walk their boxes as flat index ranges so
-    // that every lane has work (box widths are not multiples of the block)
+    // staged pixel (r, c) = image (x0 - kHalo + c, y0 - kHalo + r), clamped,
+    // at S[r * P + c]; interior tiles copy rows as words, the others bytes
     const uint8_t *__restrict__ I = L.img;
     const bool interior = x0 - kHalo >= 0 && y0 - kHalo >= 0 && x0 + kDetTW + kHalo <= W && y0 + kDetTH + kHalo <= H;
-    for (int el = threadIdx.x; el < kSH * kSW; el += kThreads) {
-        const int r = el / kSW, c = el - r * kSW;
-        const int gyy = interior ? y0 - kHalo + r : clampi(y0 - kHalo + r, 0, H - 1);
-        const int gxx = interior ? x0 - kHalo + c : clampi(x0 - kHalo + c, 0, W - 1);
-        img[r][c] = I[gyy * W + gxx];
+    const uint8_t *g0 = interior ? I + (size_t)(y0 - kHalo) * W + (x0 - kHalo) : I;
+    const int s0 = interior ? (int)((uintptr_t)g0 & 3u) : 0;
+    uint8_t *S = sm.img + s0;
+    if (interior) {
+        constexpr int kNW = (kSW + 6) / 4;   // words of a row copy
+        for (int el = threadIdx.x; el < kSH * kNW; el += kThreads) {
+            const int r = el / kNW, k = el - r * kNW;
+            store_word(S + r * P, kSW, k, load_word(g0 + (size_t)r * W, kSW, k));
+        }
+    } else {
+        for (int el = threadIdx.x; el < kSH * kSW; el += kThreads) {
+            const int r = el / kSW, c = el - r * kSW;
+            S[r * P + c] = I[clampi(y0 - kHalo + r, 0, H - 1) * W + clampi(x0 - kHalo + c, 0, W - 1)];
+        }
     }
     __syncthreads();
 
@@ -193,7 +248,7 @@ __device__ __forceinline__ void detect_tile(int tile, const DevLevel *__restrict
         const int x = x0 - 1 + c, y = y0 - 1 + r;
         uint8_t flag = 0;
         if (el < kRH * kRW && x >= xlo && x < xhi && y >= ylo && y < yhi &&
-            fast9_staged(&img[r - 1 + kHalo][c - 1 + kHalo], thr)) {
+            fast9_staged<P>(&S[(r - 1 + kHalo) * P + c - 1 + kHalo], thr)) {
             const uint8_t *M = L.mask;
             const int b = kBorder;
             flag = M[(y - b) * W + x - b] & M[(y - b) * W + x + b] & M[(y + b) * W + x - b] & M[(y + b) * W + x + b];
@@ -216,10 +271,9 @@ __device__ __forceinline__ void detect_tile(int tile, const DevLevel *__restrict
     for (int el = threadIdx.x; el < kGH * kGW; el += kThreads) {
         const int r = el / kGW, c = el - r * kGW;
         const int X = c + 1, Y = r + 1;
-        gx[r][c] = (int16_t)((img[Y - 1][X + 1] + 2 * img[Y][X + 1] + img[Y + 1][X + 1]) -
-                             (img[Y - 1][X - 1] + 2 * img[Y][X - 1] + img[Y + 1][X - 1]));
-        gy[r][c] = (int16_t)((img[Y + 1][X - 1] + 2 * img[Y + 1][X] + img[Y + 1][X + 1]) -
-                             (img[Y - 1][X - 1] + 2 * img[Y - 1][X] + img[Y - 1][X + 1]));
+        const uint8_t *q = S + Y * P + X;
+        gx[r][c] = (int16_t)((q[-P + 1] + 2 * q[1] + q[P + 1]) - (q[-P - 1] + 2 * q[-1] + q[P - 1]));
+        gy[r][c] = (int16_t)((q[P - 1] + 2 * q[P] + q[P + 1]) - (q[-P - 1] + 2 * q[-P] + q[-P + 1]));
     }
     __syncthreads();
 
@@ -285,13 +339,21 @@ __device__ __forceinline__ void detect_tile(int tile, const DevLevel *__restrict
     }
 }
 
-// Grid-stride over the tiles: one CTA per tile, or a persistent grid.
-__global__ void __launch_bounds__(kDetCols * kDetRowsPar)
+// Grid-stride over the tiles: one CTA per tile, or a persistent grid.  Five
+// CTAs per SM, what the 39.6 KB of shared memory allows.
+__global__ void __launch_bounds__(kDetCols * kDetRowsPar, 5)
 detect_kernel(int n_tiles, const DevLevel *__restrict__ lv, int n, int thr, Candidate *__restrict__ cand,
               int32_t *__restrict__ cand_count)
 {
+    __shared__ DetSmem sm;
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        detect_tile(tile, lv, n, thr, cand, cand_count);
+        const int e = find_owner(lv, n, tile, [](const DevLevel &d) { return d.det_tile_start; });
+        switch (lv[e].W & 3) {   // P = W mod 4
+        case 1: detect_tile<kSPMin>(tile, e, lv, thr, cand, cand_count, sm); break;
+        case 2: detect_tile<kSPMin + 1>(tile, e, lv, thr, cand, cand_count, sm); break;
+        case 3: detect_tile<kSPMin + 2>(tile, e, lv, thr, cand, cand_count, sm); break;
+        default: detect_tile<kSPMin + 3>(tile, e, lv, thr, cand, cand_count, sm); break;
+        }
         __syncthreads();
     }
 }
