@@ -19,7 +19,9 @@
  *    before the call returns.
  *  - The hot-path calls allocate no device memory: scratch comes from a
  *    caller-provided workspace whose size is returned by the *_workspace_size
- *    queries.  Only asift_ctx_create / asift_plan_create allocate.
+ *    queries, 256-byte aligned (as cudaMalloc returns it; asift_views,
+ *    match_pair and hamming_match return ASIFT_ERR_ARG otherwise).  Only
+ *    asift_ctx_create / asift_plan_create allocate.
  *  - Return value: ASIFT_OK when the work was enqueued; ASIFT_ERR_ARG for a bad
  *    argument (nothing enqueued); ASIFT_ERR_CUDA for a CUDA launch/copy error.
  *    Conditions found on the device while the work runs (a candidate buffer

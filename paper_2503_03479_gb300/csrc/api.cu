@@ -455,7 +455,7 @@ static size_t views_layout(void *base, int H, int W, int nv, size_t n_filter, in
     Bump b(base);
     *status = b.take<int32_t>(64);
     *tab = b.take<DevView>(std::max(nv, 1));
-    *src = b.take<float>((size_t)W * H);
+    *src = b.take<float>((size_t)src_pitch_of(W) * H);
     *filt = b.take<float>(std::max<size_t>(n_filter, 1));
     return b.off + 256;
 }
@@ -477,7 +477,7 @@ asift_status asift_views(asift_ctx *ctx, const uint8_t *d_img, int H, int W, int
                          size_t ws_bytes, void *stream)
 {
     if (!ctx || !d_img || H < 1 || W < 1 || pitch < W || n_views < 0 || (n_views && (!h_views || !h_offsets)) ||
-        !d_view_u8 || !d_mask || !d_workspace)
+        !d_view_u8 || !d_mask || !d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255))
         return ASIFT_ERR_ARG;
     if (ws_bytes < asift_views_workspace_size(H, W, n_views)) return ASIFT_ERR_ARG;
     for (int v = 0; v < n_views; ++v)
@@ -489,12 +489,12 @@ asift_status asift_views(asift_ctx *ctx, const uint8_t *d_img, int H, int W, int
     float *src, *filt;
     views_layout(d_workspace, H, W, n_views, tilt_filter_floats(h_views, n_views), &status, &tab, &src, &filt);
     std::vector<const float *> srcs(n_views, src);
-    std::vector<int> pitches(n_views, W);
+    std::vector<int> pitches(n_views, src_pitch_of(W));
     std::vector<DevView> dv;
     int n_tiles, cwm, hpm, wvm;
     build_views(h_views, n_views, srcs.data(), pitches.data(), h_offsets, false, filt, dv, &n_tiles, &cwm, &hpm, &wvm);
     cudaError_t e = upload(ctx, tab, dv.data(), sizeof(DevView) * n_views, s);
-    if (e == cudaSuccess) e = launch_u8_to_f32(d_img, pitch, W, H, src, s);
+    if (e == cudaSuccess) e = launch_u8_to_f32(d_img, pitch, W, H, src, src_pitch_of(W), s);
     if (e == cudaSuccess) e = launch_tilt_filter(tab, n_views, wvm, s);
     if (e == cudaSuccess) e = launch_warp(tab, n_views, n_tiles, cwm, hpm, d_view_u8, d_mask, d_view_f32, s);
     return cuda_status(e);
@@ -833,8 +833,8 @@ static bool pipeline_layout(const asift_ctx *ctx, const PairSpec *ps, int P, int
     L.src.assign(2 * P, nullptr);
     L.max_px = 0;
     for (int p = 0; p < P; ++p) {
-        L.src[2 * p] = b.take<float>((size_t)ps[p].W1 * ps[p].H1);
-        L.src[2 * p + 1] = b.take<float>((size_t)ps[p].W2 * ps[p].H2);
+        L.src[2 * p] = b.take<float>((size_t)src_pitch_of(ps[p].W1) * ps[p].H1);
+        L.src[2 * p + 1] = b.take<float>((size_t)src_pitch_of(ps[p].W2) * ps[p].H2);
         L.max_px = std::max(L.max_px, std::max((long long)ps[p].W1 * ps[p].H1, (long long)ps[p].W2 * ps[p].H2));
     }
     L.view_count = b.take<int32_t>(L.nv);
@@ -880,7 +880,7 @@ static void pipeline_tables(Pipeline &L, const asift_pair_desc *pairs, asift_pai
             const int g = 2 * p + im;
             for (int v = L.first[g]; v < L.first[g + 1]; ++v) {
                 srcs[v] = L.src[g];
-                pitches[v] = im ? pairs[p].W2 : pairs[p].W1;
+                pitches[v] = src_pitch_of(im ? pairs[p].W2 : pairs[p].W1);
             }
             ImageConv &c = L.h_conv[g];
             c.src = im ? pairs[p].d_img2 : pairs[p].d_img1;
@@ -888,6 +888,7 @@ static void pipeline_tables(Pipeline &L, const asift_pair_desc *pairs, asift_pai
             c.pitch = im ? pairs[p].pitch2 : pairs[p].pitch1;
             c.W = im ? pairs[p].W2 : pairs[p].W1;
             c.H = im ? pairs[p].H2 : pairs[p].H1;
+            c.dpitch = src_pitch_of(c.W);
         }
         L.h_probs[p].pairs = outs[p];
         L.h_probs[p].cap = caps[p];
@@ -976,7 +977,8 @@ asift_status match_pair(asift_ctx *ctx, const uint8_t *d_img1, int H1, int W1, i
     const asift_pair_cfg pc = pair_cfg_or_default(cfg);
     if (!ctx || !d_img1 || !d_img2 || H1 < 1 || W1 < 1 || H2 < 1 || W2 < 1 || H1 > 16384 || W1 > 16384 ||
         H2 > 16384 || W2 > 16384 || pitch1 < W1 || pitch2 < W2 || pc.kmax < 0 || pc.kmax > 7 || pc.ratio_den < 1 ||
-        pc.ratio_num < 0 || cap < 0 || (cap && !d_out) || !d_n || !d_workspace)
+        pc.ratio_num < 0 || cap < 0 || (cap && !d_out) || !d_n || !d_workspace ||
+        (reinterpret_cast<uintptr_t>(d_workspace) & 255))
         return ASIFT_ERR_ARG;
     const bool per_view = pc.per_view != 0;
     Pipeline L;

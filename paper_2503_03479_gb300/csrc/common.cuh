@@ -40,8 +40,12 @@ constexpr int kWarpThreads = 256;
 struct ImageConv {
     const uint8_t *src;
     float *dst;
-    int32_t pitch, W, H, pad;
+    int32_t pitch, W, H, dpitch;   // dst rows: dpitch floats, columns >= W zero
 };
+
+// Row pitch (floats) of the fp32 source images: a multiple of 4, so that the
+// warp kernel stages them with 16-byte copies.
+__host__ __device__ inline int src_pitch_of(int W) { return (W + 3) & ~3; }
 
 // ---------------------------------------------------------------- ORB stage
 // One (view, pyramid level) as the ORB kernels read it.

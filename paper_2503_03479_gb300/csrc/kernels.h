@@ -18,7 +18,7 @@ struct SlotKp;
 void warp_strip_widths(const asift_view_desc &v, int tw, int *cw, int *bw);
 int warp_tile_width(const asift_view_desc &v);
 void warp_lane_layout(long long cq, long long sq, int *lanes_x, int *pitch);
-cudaError_t launch_u8_to_f32(const uint8_t *src, int pitch, int W, int H, float *dst, cudaStream_t s);
+cudaError_t launch_u8_to_f32(const uint8_t *src, int pitch, int W, int H, float *dst, int dpitch, cudaStream_t s);
 struct ImageConv;
 cudaError_t launch_convert_images(const ImageConv *d_list, int n, long long max_px, cudaStream_t s);
 int tilt_filter_pitch(int K);

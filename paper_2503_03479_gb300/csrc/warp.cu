@@ -34,8 +34,8 @@
 namespace asift {
 
 constexpr int kChunk = 64;              // canvas columns per staged chunk
-constexpr int kStage = 72;              // staged source box (rows, columns), >= 64|c| + 16|s| + 6
-constexpr int kPitchMin = 72, kPitchMax = 80;   // row pitch of the staged box, chosen per view
+constexpr int kStage = 72;              // staged source box (rows), >= 64|c| + 16|s| + 6
+constexpr int kPitchMin = 76, kPitchMax = 80;   // row pitch of the staged box (76 or 80), chosen per view
 constexpr int kStageBuf = kStage * kPitchMax;   // floats per staging buffer (two, double-buffered)
 
 // sin and cos on [0, pi/3] from their Taylor series (truncation below 5e-8).
@@ -129,14 +129,15 @@ __device__ __forceinline__ void lanczos3_weights2(uint32_t lo_a, uint32_t lo_b, 
     }
 }
 
+// dst: H rows of dpitch floats; the columns from W on are written as zeros.
 __global__ void u8_to_f32_kernel(const uint8_t *__restrict__ src, int pitch, int W, int H,
-                                 float *__restrict__ dst)
+                                 float *__restrict__ dst, int dpitch)
 {
-    const long long n = (long long)W * H;
+    const long long n = (long long)dpitch * H;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(i / W), x = (int)(i - (long long)y * W);
-        dst[i] = (float)src[(size_t)y * pitch + x];
+        const int y = (int)(i / dpitch), x = (int)(i - (long long)y * dpitch);
+        dst[i] = x < W ? (float)src[(size_t)y * pitch + x] : 0.f;
     }
 }
 
@@ -144,11 +145,11 @@ __global__ void u8_to_f32_kernel(const uint8_t *__restrict__ src, int pitch, int
 __global__ void convert_images_kernel(const ImageConv *__restrict__ list)
 {
     const ImageConv c = list[blockIdx.y];
-    const long long n = (long long)c.W * c.H;
+    const long long n = (long long)c.dpitch * c.H;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(i / c.W), x = (int)(i - (long long)y * c.W);
-        c.dst[i] = (float)c.src[(size_t)y * c.pitch + x];
+        const int y = (int)(i / c.dpitch), x = (int)(i - (long long)y * c.dpitch);
+        c.dst[i] = x < c.W ? (float)c.src[(size_t)y * c.pitch + x] : 0.f;
     }
 }
 
@@ -221,30 +222,44 @@ __device__ __forceinline__ StageBox chunk_box(const CanvasGeom &G, int i_lo, int
     StageBox b;
     b.interior = sx0 >= 2 && sx1 + 3 <= W - 1 && sy0 >= 2 && sy1 + 3 <= H - 1;
     b.outside = side != 0u;
-    b.sx0 = clampi(sx0 - 2, 0, W - 1);
+    // columns rounded out to whole 16-byte groups of the source rows (pitch a
+    // multiple of 4 floats, columns >= W of the last group zero)
+    b.sx0 = clampi(sx0 - 2, 0, W - 1) & ~3;
     b.sy0 = clampi(sy0 - 2, 0, H - 1);
     // a chunk spans at most 63 columns and 15 rows of the canvas, so the box
-    // spans at most sqrt(63^2 + 15^2) + 1 + 5 < 72 = kStage source pixels
-    b.bwid = clampi(sx1 + 3, 0, W - 1) - b.sx0 + 1;
+    // spans at most sqrt(63^2 + 15^2) + 1 + 5 < 72 = kStage source pixels,
+    // 72 + 3 + 3 -> at most 76 = kPitchMin columns once rounded out
+    b.bwid = ((clampi(sx1 + 3, 0, W - 1) - b.sx0 + 1) + 3) & ~3;
     b.bhgt = clampi(sy1 + 3, 0, H - 1) - b.sy0 + 1;
     return b;
 }
 
-// Issues the asynchronous copies of a box into a staging buffer (pitch P):
-// warp w copies rows w, w + 8, ..., lane l columns l, l + 32, ...
+// Issues the asynchronous copies of a box into a staging buffer (pitch P, a
+// multiple of 4): 16-byte groups, the box's (row, group) pairs dealt out to
+// the block's threads in order (thread t takes t, t + 256, ...).
 __device__ __forceinline__ void stage_box(float *dst, int P, const float *__restrict__ src, int sp, const StageBox &b,
                                           unsigned warp, unsigned lane)
 {
     if (b.outside) return;
-    const float *srow = src + (size_t)(b.sy0 + (int)warp) * sp + b.sx0 + lane;
-    uint32_t drow = (uint32_t)__cvta_generic_to_shared(dst + (int)warp * P + (int)lane);
-    const size_t sstep = (size_t)(kWarpThreads / 32) * sp;
-    const uint32_t dstep = (uint32_t)((kWarpThreads / 32) * P * 4);
-    const int ncol = b.bwid - (int)lane;             // columns this lane copies: lane, lane + 32, ... < bwid
-    for (int r = warp; r < b.bhgt; r += kWarpThreads / 32, srow += sstep, drow += dstep) {
-        for (int cc = 0; cc < ncol; cc += 32)
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(drow + 4u * cc), "l"(srow + cc)
-                         : "memory");
+    const int nf4 = b.bwid >> 2, tot = b.bhgt * nf4;
+    const int t = (int)(warp * 32u + lane);
+    // integer quotients by nf4 <= 19 through a float reciprocal: (n + 1/2) / nf4
+    // stays 1/38 away from an integer, far above the product's rounding error
+    const float inv = __fdividef(1.0f, (float)nf4);
+    const int dr = __float2int_rz((kWarpThreads + 0.5f) * inv), dc = kWarpThreads - dr * nf4;   // stride in (row, group)
+    int r = __float2int_rz(((float)t + 0.5f) * inv), g = t - r * nf4;
+    const float *sbase = src + (size_t)b.sy0 * sp + b.sx0;
+    const uint32_t dbase = (uint32_t)__cvta_generic_to_shared(dst);
+    for (int el = t; el < tot; el += kWarpThreads) {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dbase + 4u * (uint32_t)(r * P + 4 * g)),
+                     "l"(sbase + (size_t)r * sp + 4 * g)
+                     : "memory");
+        r += dr;
+        g += dc;
+        if (g >= nf4) {
+            g -= nf4;
+            ++r;
+        }
     }
 }
 
@@ -523,7 +538,7 @@ static void lane_layout_search(long long cq, long long sq, int *lanes_x, int *pi
     *lanes_x = 32;
     *pitch = kPitchMin;
     for (int ax : {32, 16, 8}) {
-        for (int P = kPitchMin; P <= kPitchMax; ++P) {
+        for (int P = kPitchMin; P <= kPitchMax; P += 4) {
             double tot = 0.0;
             for (int o = 0; o < 64; ++o) {
                 const double ox = ((o & 7) + 0.5) / 8.0, oy = ((o >> 3) + 0.5) / 8.0;
@@ -578,11 +593,11 @@ void warp_lane_layout(long long cq, long long sq, int *lanes_x, int *pitch)
     memo.emplace(key, std::make_pair(*lanes_x, *pitch));
 }
 
-cudaError_t launch_u8_to_f32(const uint8_t *src, int pitch, int W, int H, float *dst, cudaStream_t s)
+cudaError_t launch_u8_to_f32(const uint8_t *src, int pitch, int W, int H, float *dst, int dpitch, cudaStream_t s)
 {
-    const long long n = (long long)W * H;
+    const long long n = (long long)dpitch * H;
     int blocks = (int)std::min<long long>((n + 255) / 256, 8LL * device_sm_count());
-    u8_to_f32_kernel<<<blocks, 256, 0, s>>>(src, pitch, W, H, dst);
+    u8_to_f32_kernel<<<blocks, 256, 0, s>>>(src, pitch, W, H, dst, dpitch);
     note_launch();
     return cudaGetLastError();
 }

@@ -193,3 +193,30 @@ def test_engine_argument_checks(A):
         ctx.set_match_engine(3)
     with pytest.raises(A.AsiftError):
         ctx.set_match_engine(-1)
+
+
+def test_workspace_alignment_checked(A):
+    """Workspaces are 256-byte aligned; an offset one is an argument error
+    (nothing enqueued), for match_pair and asift_views alike."""
+    import ctypes as C
+    ctx = A.Context(n_levels=4, n_features=200)
+    img = torch.zeros((96, 128), dtype=torch.uint8, device="cuda")
+    pc = ctx.pair_cfg(kmax=1)
+    ws = ctx.match_pair_workspace((96, 128), (96, 128), pc)
+    big = torch.zeros(ws.numel() + 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(A.AsiftError):
+        ctx.match_pair(img, img, pc, ws=big[16:16 + ws.numel()])
+    ctx.match_pair(img, img, pc, ws=big[256:256 + ws.numel()])
+    torch.cuda.synchronize()
+    views = A.view_table(96, 128, 1)
+    nb = ctx.L.asift_views_workspace_size(96, 128, len(views))
+    wsv = torch.zeros(nb + 256, dtype=torch.uint8, device="cuda")
+    offs, total = A.view_offsets(views)
+    u8 = torch.empty(total, dtype=torch.uint8, device="cuda")
+    mask = torch.empty_like(u8)
+    arr = A._view_array(views)
+    for off, ok in ((16, False), (256, True)):
+        st = ctx.L.asift_views(ctx._ctx, A._ptr(img), 96, 128, 128, arr, len(views), offs.ctypes.data_as(C.c_void_p),
+                               None, A._ptr(u8), A._ptr(mask), C.c_void_p(wsv.data_ptr() + off), nb, A._stream())
+        assert (st == 0) == ok, (off, st)
+    torch.cuda.synchronize()
