@@ -38,6 +38,14 @@ constexpr int kStage = 72;              // staged source box (rows), >= 64|c| + 
 constexpr int kPitchMin = 76, kPitchMax = 80;   // row pitch of the staged box (76 or 80), chosen per view
 constexpr int kStageBuf = kStage * kPitchMax;   // floats per staging buffer (two, double-buffered)
 
+// The hardware reciprocal (rcp.approx: relative error within one ulp).
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // sin and cos on [0, pi/3] from their Taylor series (truncation below 5e-8).
 __device__ __forceinline__ void sincos_small(float x, float &s, float &c)
 {
@@ -117,7 +125,7 @@ __device__ __forceinline__ void lanczos3_weights2(uint32_t lo_a, uint32_t lo_b, 
     const float2 u2 = __fmul2_rn(s, __fmul2_rn(p2, s2)), u3 = __fmul2_rn(a, __fmul2_rn(p3, s3));
     const float2 u4 = __fmul2_rn(b, __fmul2_rn(p4, D5)), u5 = __fmul2_rn(s, __fmul2_rn(p4, D4));
     const float2 sum = __fadd2_rn(__fadd2_rn(__fadd2_rn(u0, u1), __fadd2_rn(u2, u3)), __fadd2_rn(u4, u5));
-    const float2 inv = make_float2(__frcp_rn(sum.x), __frcp_rn(sum.y));
+    const float2 inv = make_float2(rcp_approx(sum.x), rcp_approx(sum.y));   // within 1 ulp: far below the warp's tolerance
     w[0] = __fmul2_rn(u0, inv); w[1] = __fmul2_rn(u1, inv); w[2] = __fmul2_rn(u2, inv);
     w[3] = __fmul2_rn(u3, inv); w[4] = __fmul2_rn(u4, inv); w[5] = __fmul2_rn(u5, inv);
     if (ma == 0u || mb == 0u) {
