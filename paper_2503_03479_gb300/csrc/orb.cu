@@ -541,7 +541,10 @@ pool_scan_kernel(const int32_t *__restrict__ taken, int n_views, int n_levels, c
 // ---------------------------------------------------------------- orientation + BRIEF
 constexpr int kObWarps = 8;
 constexpr int kPatch = 37;          // raw patch: radius 15 + smoothing radius 3
+constexpr int kPP = 40;             // its row pitch in shared memory (10 words)
 constexpr int kSm = 31;             // smoothed patch
+// the smoothing taps [18 34 49 54 49 34 18] packed for dp4a: taps 0-3, taps 4-6 (and 0)
+constexpr unsigned kTapsLo = 18u | 34u << 8 | 49u << 16 | 54u << 24, kTapsHi = 49u | 34u << 8 | 18u << 16;
 
 __constant__ int c_smooth[7] = {18, 34, 49, 54, 49, 34, 18};
 
@@ -552,7 +555,7 @@ orient_brief_kernel(const DevLevel *__restrict__ lv, int n_views, int n_levels, 
                     const long long *__restrict__ bins /* [30][2] Q30 */, asift_keypoint *__restrict__ kp_out,
                     uint4 *__restrict__ desc_out)
 {
-    __shared__ uint8_t P[kObWarps][kPatch * kPatch];
+    __shared__ __align__(16) uint8_t P[kObWarps][kPatch * kPP];
     __shared__ uint16_t Hs[kObWarps][kPatch * kSm];
     __shared__ uint8_t S[kObWarps][kSm * kSm];
     __shared__ long long eb[kBins][2];
@@ -577,29 +580,48 @@ orient_brief_kernel(const DevLevel *__restrict__ lv, int n_views, int n_levels, 
     const int x = s.yx & 0xffff, y = s.yx >> 16;
     const int W = L.W, H = L.H;
 
+    // patch (rr, cc) = image (x - 18 + cc, y - 18 + rr), clamped, at p[rr * kPP + cc]
     uint8_t *p = P[w];
-    for (int i = lane; i < kPatch * kPatch; i += 32) {
-        const int rr = i / kPatch, cc = i - rr * kPatch;
-        const int gx = clampi(x - 18 + cc, 0, W - 1), gy = clampi(y - 18 + rr, 0, H - 1);
-        p[i] = L.img[(size_t)gy * W + gx];
+    if (x >= 22 && x + 26 < W && y >= 18 && y + 18 < H) {
+        // rows as words: lane 10 q + j writes word j of rows q, q + 3, ..., each
+        // from the two aligned words of the image row around it (both inside
+        // the row for keypoints at least 22 px from its ends)
+        const int q = (int)lane / 10, j = (int)lane - 10 * q;
+        for (int rr = q; rr < kPatch; rr += 3) {
+            if (lane >= 30) break;
+            const uint8_t *g = L.img + (size_t)(y - 18 + rr) * W + (x - 18);
+            const uint32_t *ga = reinterpret_cast<const uint32_t *>(reinterpret_cast<uintptr_t>(g) & ~(uintptr_t)3);
+            const unsigned sh = 8u * (unsigned)(reinterpret_cast<uintptr_t>(g) & 3u);
+            reinterpret_cast<uint32_t *>(p + rr * kPP)[j] = __funnelshift_r(__ldg(ga + j), __ldg(ga + j + 1), sh);
+        }
+    } else {
+        for (int i = lane; i < kPatch * kPatch; i += 32) {
+            const int rr = i / kPatch, cc = i - rr * kPatch;
+            const int gx = clampi(x - 18 + cc, 0, W - 1), gy = clampi(y - 18 + rr, 0, H - 1);
+            p[rr * kPP + cc] = L.img[(size_t)gy * W + gx];
+        }
     }
     __syncwarp();
-    // horizontal smoothing pass (exact sums)
+    // horizontal smoothing pass (exact sums): lane item = (row, 4 consecutive
+    // outputs), taps from three aligned words through byte permutes and dp4a
     uint16_t *h = Hs[w];
-    for (int i = lane; i < kPatch * kSm; i += 32) {
-        const int rr = i / kSm, cc = i - rr * kSm;
-        const uint8_t *row = p + rr * kPatch + cc;   // taps cc..cc+6 = offsets -3..3 around cc+3
-        unsigned a = 0;
+    for (int i = lane; i < kPatch * 8; i += 32) {
+        const int rr = i >> 3, c4 = (i & 7) * 4;
+        const uint32_t *row = reinterpret_cast<const uint32_t *>(p + rr * kPP) + (c4 >> 2);
+        const uint32_t w0 = row[0], w1 = row[1], w2 = row[2];   // bytes c4 .. c4 + 11 (< kPP)
 #pragma unroll
-        for (int t = 0; t < 7; ++t) a += (unsigned)c_smooth[t] * row[t];
-        h[i] = (uint16_t)a;
+        for (int k = 0; k < 4; ++k) {
+            const unsigned sel = 0x3210u + 0x1111u * (unsigned)k;
+            const unsigned a = __dp4a(__byte_perm(w1, w2, sel), kTapsHi, __dp4a(__byte_perm(w0, w1, sel), kTapsLo, 0u));
+            if (c4 + k < kSm) h[rr * kSm + c4 + k] = (uint16_t)a;
+        }
     }
     // centroid moments on the raw patch (disc of radius 15)
     int m10 = 0, m01 = 0;
     for (int i = lane; i < kSm * kSm; i += 32) {
         const int dy = i / kSm - 15, dx = i % kSm - 15;
         if (dx * dx + dy * dy <= kPatchR2) {
-            const int val = p[(dy + 18) * kPatch + dx + 18];
+            const int val = p[(dy + 18) * kPP + dx + 18];
             m10 += dx * val;
             m01 += dy * val;
         }
