@@ -248,6 +248,11 @@ static bool view_ok(const asift_view_desc &v)
 using namespace asift;
 
 // ---------------------------------------------------------------- context
+namespace asift {
+struct PairCache;                       // match_pair's host tables of recent calls (below)
+static void pair_cache_free(PairCache *c);
+}  // namespace asift
+
 struct asift_ctx {
     int device = 0;
     asift_orb_cfg cfg{};
@@ -263,6 +268,7 @@ struct asift_ctx {
     bool prof = false;
     cudaEvent_t prof_ev[ASIFT_PROF_STAGES + 1] = {};
     int match_engine = ASIFT_MATCH_AUTO;
+    PairCache *pair_cache = nullptr;
 };
 
 // The matcher engine a call uses: the tuning's, else the context's; AUTO
@@ -350,6 +356,7 @@ void asift_ctx_destroy(asift_ctx *ctx)
         if (ctx->prof_ev[i]) cudaEventDestroy(ctx->prof_ev[i]);
     if (ctx->d_pat) cudaFree(ctx->d_pat);
     if (ctx->d_bins) cudaFree(ctx->d_bins);
+    pair_cache_free(ctx->pair_cache);
     delete ctx;
 }
 
@@ -776,6 +783,41 @@ struct Pipeline {
     size_t bytes = 0;
 };
 
+// match_pair's layout and host tables are a function of its arguments and of
+// the context's (fixed) ORB configuration.  The context keeps those of its
+// last few distinct calls, so a call that repeats one (a caller streaming
+// pairs through the same buffers) goes straight to the upload and launches.
+struct PairKey {
+    const uint8_t *img1, *img2;
+    int H1, W1, pitch1, H2, W2, pitch2;
+    int32_t kmax, ratio_num, ratio_den, per_view;
+    asift_pair_match *out;
+    int cap;
+    int32_t *d_n;
+    void *ws;
+    bool operator==(const PairKey &o) const
+    {
+        return img1 == o.img1 && img2 == o.img2 && H1 == o.H1 && W1 == o.W1 && pitch1 == o.pitch1 && H2 == o.H2 &&
+               W2 == o.W2 && pitch2 == o.pitch2 && kmax == o.kmax && ratio_num == o.ratio_num &&
+               ratio_den == o.ratio_den && per_view == o.per_view && out == o.out && cap == o.cap && d_n == o.d_n &&
+               ws == o.ws;
+    }
+};
+
+struct PairCache {
+    static constexpr size_t kEntries = 4;
+    struct Entry {
+        PairKey key;
+        Pipeline L;
+        std::vector<unsigned char> blob;
+        unsigned long long used = 0;
+    };
+    std::vector<Entry> e;
+    unsigned long long clock = 0;
+};
+
+static void pair_cache_free(PairCache *c) { delete c; }
+
 static bool pipeline_layout(const asift_ctx *ctx, const PairSpec *ps, int P, int kmax, bool per_view, void *base,
                             Pipeline &L)
 {
@@ -981,16 +1023,38 @@ asift_status match_pair(asift_ctx *ctx, const uint8_t *d_img1, int H1, int W1, i
         (reinterpret_cast<uintptr_t>(d_workspace) & 255))
         return ASIFT_ERR_ARG;
     const bool per_view = pc.per_view != 0;
-    Pipeline L;
-    PairSpec ps{H1, W1, H2, W2};
-    if (!pipeline_layout(ctx, &ps, 1, pc.kmax, per_view, d_workspace, L)) return ASIFT_ERR_ARG;
+    const PairKey key{d_img1, d_img2, H1, W1, pitch1, H2, W2, pitch2, pc.kmax, pc.ratio_num, pc.ratio_den,
+                      pc.per_view, d_out, cap, d_n, d_workspace};
+    if (!ctx->pair_cache) ctx->pair_cache = new (std::nothrow) PairCache;
+    if (!ctx->pair_cache) return ASIFT_ERR_NOMEM;
+    PairCache &C = *ctx->pair_cache;
+    PairCache::Entry *hit = nullptr;
+    for (auto &en : C.e)
+        if (en.key == key) hit = &en;
+    if (!hit) {
+        PairCache::Entry fresh;
+        fresh.key = key;
+        PairSpec ps{H1, W1, H2, W2};
+        if (!pipeline_layout(ctx, &ps, 1, pc.kmax, per_view, d_workspace, fresh.L)) return ASIFT_ERR_ARG;
+        if (ws_bytes < fresh.L.bytes) return ASIFT_ERR_ARG;
+        asift_pair_desc pd{d_img1, H1, W1, pitch1, d_img2, H2, W2, pitch2};
+        pipeline_tables(fresh.L, &pd, &d_out, &cap, &d_n, per_view, fresh.blob);
+        if (C.e.size() < PairCache::kEntries) {
+            C.e.push_back(std::move(fresh));
+            hit = &C.e.back();
+        } else {
+            hit = &C.e[0];
+            for (auto &en : C.e)
+                if (en.used < hit->used) hit = &en;
+            *hit = std::move(fresh);
+        }
+    }
+    hit->used = ++C.clock;
+    const Pipeline &L = hit->L;
     if (ws_bytes < L.bytes) return ASIFT_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    asift_pair_desc pd{d_img1, H1, W1, pitch1, d_img2, H2, W2, pitch2};
-    std::vector<unsigned char> blob;
-    pipeline_tables(L, &pd, &d_out, &cap, &d_n, per_view, blob);
     prof_mark(ctx, 0, s);
-    cudaError_t e = upload(ctx, L.dv, blob.data(), blob.size(), s);
+    cudaError_t e = upload(ctx, L.dv, hit->blob.data(), hit->blob.size(), s);
     if (e == cudaSuccess) e = pipeline_run(ctx, L, pc, per_view, nullptr, s);
     return cuda_status(e);
 }
