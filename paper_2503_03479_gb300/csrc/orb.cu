@@ -154,7 +154,7 @@ struct DetSmem {
     int16_t clist[kRH * kRW];
     __align__(16) uint8_t img[kSH * kSPMax];
     uint8_t isc[kRH][kRW];
-    int ncl;
+    int ncl, ncand;
 };
 
 // 1 iff 9 cyclically consecutive bits of the 16-bit mask m are set.
@@ -171,18 +171,25 @@ __device__ __forceinline__ bool has_run9(unsigned m)
 // FAST-9 at the staged pixel p (row pitch P): the Bresenham circle of radius
 // 3 from (0,-3) clockwise, with compile-time offsets.  A 9-arc holds at least
 // 2 of the 4 compass points, so pixels with fewer bright and fewer dark
-// compass points are rejected before the full test.
+// compass points cannot pass (fast9_compass); fast9_ring is the full test.
 template <int P>
-__device__ __forceinline__ bool fast9_staged(const uint8_t *p, int thr)
+__device__ __forceinline__ bool fast9_compass(const uint8_t *p, int thr)
 {
     const int ctr = p[0];
     const int hi = ctr + thr, lo = ctr - thr;
     const int n0 = p[-3 * P], n4 = p[3], n8 = p[3 * P], n12 = p[-3];
     const int nb = (n0 > hi) + (n4 > hi) + (n8 > hi) + (n12 > hi);
     const int nd = (n0 < lo) + (n4 < lo) + (n8 < lo) + (n12 < lo);
-    if (nb < 2 && nd < 2) return false;
-    const int v[16] = {n0, p[-3 * P + 1], p[-2 * P + 2], p[-P + 3], n4, p[P + 3], p[2 * P + 2],
-                       p[3 * P + 1], n8, p[3 * P - 1], p[2 * P - 2], p[P - 3], n12, p[-P - 3],
+    return nb >= 2 || nd >= 2;
+}
+
+template <int P>
+__device__ __forceinline__ bool fast9_ring(const uint8_t *p, int thr)
+{
+    const int ctr = p[0];
+    const int hi = ctr + thr, lo = ctr - thr;
+    const int v[16] = {p[-3 * P], p[-3 * P + 1], p[-2 * P + 2], p[-P + 3], p[3], p[P + 3], p[2 * P + 2],
+                       p[3 * P + 1], p[3 * P], p[3 * P - 1], p[2 * P - 2], p[P - 3], p[-3], p[-P - 3],
                        p[-2 * P - 2], p[-3 * P - 1]};
     unsigned bm = 0, dm = 0;
 #pragma unroll
@@ -215,7 +222,10 @@ __device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__r
     const int tc = threadIdx.x % kDetCols, tr = threadIdx.x / kDetCols;
     constexpr int kThreads = kDetCols * kDetRowsPar;
 
-    if (threadIdx.x == 0) ncl = 0;
+    if (threadIdx.x == 0) {
+        ncl = 0;
+        sm.ncand = 0;
+    }
     // staged pixel (r, c) = image (x0 - kHalo + c, y0 - kHalo + r), clamped,
     // at S[r * P + c]; interior tiles copy rows as words, the others bytes
     const uint8_t *__restrict__ I = L.img;
@@ -237,23 +247,51 @@ __device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__r
     }
     __syncthreads();
 
-    // corner flags on the tile + ring; corners appended with one shared
-    // atomic per warp (every lane runs every iteration)
+    // corner flags on the tile + ring in two passes, so that the full ring test
+    // runs with every lane busy: (a) border and compass test for every pixel,
+    // survivors listed (in the Sobel buffer, unused until the gradients);
+    // (b) the full test and the mask corners on the list.  Both passes append
+    // with one shared atomic per warp (every lane runs every iteration).
     const int xlo = kBorder, xhi = W - kBorder, ylo = kBorder, yhi = H - kBorder;
     const unsigned lane_id = threadIdx.x & 31u;
+    static_assert(kRH * kRW <= kGH * kGW, "the survivor list fits the Sobel buffer");
+    int16_t *surv = &gx[0][0];
 #pragma unroll 1
     for (int k = 0; k < (kRH * kRW + kThreads - 1) / kThreads; ++k) {
         const int el = (int)threadIdx.x + k * kThreads;
         const int r = el / kRW, c = el - r * kRW;
         const int x = x0 - 1 + c, y = y0 - 1 + r;
-        uint8_t flag = 0;
-        if (el < kRH * kRW && x >= xlo && x < xhi && y >= ylo && y < yhi &&
-            fast9_staged<P>(&S[(r - 1 + kHalo) * P + c - 1 + kHalo], thr)) {
-            const uint8_t *M = L.mask;
-            const int b = kBorder;
-            flag = M[(y - b) * W + x - b] & M[(y - b) * W + x + b] & M[(y + b) * W + x - b] & M[(y + b) * W + x + b];
+        const bool pass = el < kRH * kRW && x >= xlo && x < xhi && y >= ylo && y < yhi &&
+                          fast9_compass<P>(&S[(r - 1 + kHalo) * P + c - 1 + kHalo], thr);
+        if (el < kRH * kRW) isc[r][c] = 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, pass);
+        if (bal) {
+            int base = 0;
+            if (lane_id == 0) base = atomicAdd(&sm.ncand, __popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (pass) surv[base + __popc(bal & ((1u << lane_id) - 1u))] = (int16_t)el;
         }
-        if (el < kRH * kRW) isc[r][c] = flag;
+    }
+    __syncthreads();
+    const int nca = sm.ncand;
+#pragma unroll 1
+    for (int q0 = (int)(threadIdx.x & ~31u); q0 < nca; q0 += kThreads) {
+        const int q = q0 + (int)lane_id;
+        uint8_t flag = 0;
+        int r = 0, c = 0;
+        if (q < nca) {
+            const int el = surv[q];
+            r = el / kRW;
+            c = el - r * kRW;
+            if (fast9_ring<P>(&S[(r - 1 + kHalo) * P + c - 1 + kHalo], thr)) {
+                const int x = x0 - 1 + c, y = y0 - 1 + r;
+                const uint8_t *M = L.mask;
+                const int b = kBorder;
+                flag = M[(y - b) * W + x - b] & M[(y - b) * W + x + b] & M[(y + b) * W + x - b] &
+                       M[(y + b) * W + x + b];
+            }
+            if (flag) isc[r][c] = flag;
+        }
         const unsigned bal = __ballot_sync(0xffffffffu, flag != 0);
         if (bal) {
             int base = 0;
