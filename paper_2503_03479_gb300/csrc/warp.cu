@@ -242,6 +242,12 @@ __device__ __forceinline__ StageBox chunk_box(const CanvasGeom &G, int i_lo, int
     return b;
 }
 
+__device__ __forceinline__ void cp_async16(float *dst, const float *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+
 // Issues the asynchronous copies of a box into a staging buffer (pitch P, a
 // multiple of 4): 16-byte groups, the box's (row, group) pairs dealt out to
 // the block's threads in order (thread t takes t, t + 256, ...).
@@ -278,9 +284,11 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
     extern __shared__ float4 smem4[];
     float *smem = reinterpret_cast<float *>(smem4);
     // Cs [kWarpTH][cwp] canvas strip (odd row pitch), then the two staging
-    // buffers [kStage][pitch] of step 1.
+    // buffers [kStage][pitch] of step 1 (one of them holds the tile's filters
+    // for step 2), then the source boxes of the tile's chunks.
     float *Cs = smem;
     float *Sbuf = Cs + kWarpTH * cwp;
+    StageBox *Bx = reinterpret_cast<StageBox *>(Sbuf + 2 * kStageBuf);
 
     const int vi = find_owner(views, n_views, tile, [](const DevView &v) { return v.tile_start; });
     const DevView &V = views[vi];
@@ -303,6 +311,7 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
 
     const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     constexpr int kRowStep = kWarpThreads / kChunk;   // a thread walks its column in steps of 4 rows
+    int fbuf = -1;                                    // staging buffer holding the step-2 filters, or -1
 
     // 1. rotated canvas strip, chunk by chunk: the source box of chunk k + 1
     //    is copied asynchronously into one staging buffer while chunk k is
@@ -320,10 +329,26 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
         const long long xlim = (long long)(2 * W - 1) * HALF, ylim = (long long)(2 * H - 1) * HALF;
         const long long dpx = 2LL * kRowStep * V.sq, dpy = 2LL * kRowStep * V.cq;
         const int nch = (cw + kChunk - 1) / kChunk;
-        auto box_of = [&](int k) {
-            const int c0 = k * kChunk, cn = min(kChunk, cw - c0);
-            return chunk_box(G, clampi(cx0 + c0, 0, Wr - 1), clampi(cx0 + c0 + cn - 1, 0, Wr - 1), j0, j1, W, H,
-                             lane);
+        // the chunks' source boxes, once per tile: lane group g (four lanes,
+        // one corner each) of warp w makes the box of chunk 8 w + g
+        for (int base = 0; base < nch; base += kWarpThreads / 4) {
+            const int kc = base + (int)(warp * 8u + (lane >> 2)), kk = min(kc, nch - 1);
+            const int c0 = kk * kChunk, cn = min(kChunk, cw - c0);
+            const StageBox b = chunk_box(G, clampi(cx0 + c0, 0, Wr - 1), clampi(cx0 + c0 + cn - 1, 0, Wr - 1), j0,
+                                         j1, W, H, lane);
+            if (kc < nch && (lane & 3u) == 0u) Bx[kc] = b;
+        }
+        __syncthreads();
+        auto box_of = [&](int k) { return Bx[k]; };
+        // The tile's step-2 filters (column c at Fs + c fp, fp = 4 mod 8 so
+        // that a warp's 8 columns fall on distinct banks) are copied into the
+        // staging buffer that the last staged chunk leaves idle.
+        const int ncols = xb - xa + 1, hp = V.hp, fp = (hp & 7) ? hp : hp + 4;
+        const bool fpre = ncols * fp <= kStageBuf;
+        auto stage_filters = [&](float *dst) {
+            for (int cc = (int)warp; cc < ncols; cc += kWarpThreads / 32)
+                for (int g = (int)lane; g < (hp >> 2); g += 32)
+                    cp_async16(dst + cc * fp + 4 * g, V.filt + (size_t)(xa + cc) * hp + 4 * g);
         };
         // Chunks whose source lies wholly outside the image are background:
         // they are written as zeros on the way and take no staging buffer, so
@@ -340,12 +365,18 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
         };
         StageBox bx;
         int k = next_staged(0, bx), buf = 0;
+        fbuf = -1;
         if (k < nch) stage_box(Sbuf, P, src, sp, bx, warp, lane);
         cp_async_commit();
         while (k < nch) {
             StageBox nb;
             const int kn = next_staged(k + 1, nb);
-            if (kn < nch) stage_box(Sbuf + (buf ^ 1) * kStageBuf, P, src, sp, nb, warp, lane);
+            if (kn < nch) {
+                stage_box(Sbuf + (buf ^ 1) * kStageBuf, P, src, sp, nb, warp, lane);
+            } else if (fpre) {
+                stage_filters(Sbuf + (buf ^ 1) * kStageBuf);
+                fbuf = buf ^ 1;
+            }
             cp_async_commit();
             cp_async_wait<1>();      // this thread's copies of chunk k have landed
             __syncthreads();         // and everyone's
@@ -389,8 +420,13 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
             bx = nb;
             buf ^= 1;
         }
+        if (fpre && fbuf < 0) {      // no staged chunk: the filters go to buffer 0
+            stage_filters(Sbuf);
+            fbuf = 0;
+            cp_async_commit();
+        }
         cp_async_wait<0>();
-        __syncthreads();             // zero-filled columns written after the last staged chunk
+        __syncthreads();             // zero-filled columns written after the last staged chunk, filters landed
     }
 
     // 2. Gaussian along canvas x, tilt resampling, quantisation and the
@@ -405,22 +441,34 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
     //    step 1.
     {
         const int hp = V.hp, nh = 2 * K + 6;
-        const int ncols = xb - xa + 1;
+        const int ncols = xb - xa + 1, fp = (hp & 7) ? hp : hp + 4;
         const int c = (int)(warp * 8 + (lane & 7u)), rg = (int)(lane >> 3);
         if (c < ncols) {
             const int x = xa + c;
             const long long X = V.tq * (2LL * x - V.Wv + 1) + xoff;
             const int x0 = (int)(X >> 32);
-            const float *__restrict__ h = V.filt + (size_t)x * hp;   // read through L1 (the tile's 64 filters)
             const float *Cb = Cs + (x0 - 2 - K - cx0) + rg * cwp;
             float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+            if (fbuf >= 0) {
+                const float *h = Sbuf + fbuf * kStageBuf + c * fp;   // staged during step 1
 #pragma unroll 4
-            for (int u = 0; u < nh; ++u) {
-                const float hu = __ldg(h + u);
-                acc0 = fmaf(hu, Cb[u], acc0);
-                acc1 = fmaf(hu, Cb[4 * cwp + u], acc1);
-                acc2 = fmaf(hu, Cb[8 * cwp + u], acc2);
-                acc3 = fmaf(hu, Cb[12 * cwp + u], acc3);
+                for (int u = 0; u < nh; ++u) {
+                    const float hu = h[u];
+                    acc0 = fmaf(hu, Cb[u], acc0);
+                    acc1 = fmaf(hu, Cb[4 * cwp + u], acc1);
+                    acc2 = fmaf(hu, Cb[8 * cwp + u], acc2);
+                    acc3 = fmaf(hu, Cb[12 * cwp + u], acc3);
+                }
+            } else {
+                const float *__restrict__ h = V.filt + (size_t)x * hp;   // too wide to stage: through L1
+#pragma unroll 4
+                for (int u = 0; u < nh; ++u) {
+                    const float hu = __ldg(h + u);
+                    acc0 = fmaf(hu, Cb[u], acc0);
+                    acc1 = fmaf(hu, Cb[4 * cwp + u], acc1);
+                    acc2 = fmaf(hu, Cb[8 * cwp + u], acc2);
+                    acc3 = fmaf(hu, Cb[12 * cwp + u], acc3);
+                }
             }
             const float accs[4] = {acc0, acc1, acc2, acc3};
             const long long mxlo = HALF, mxhi = (long long)(2 * W - 3) * HALF;
@@ -531,7 +579,8 @@ static int strip_pitch(int cw_max) { return ((cw_max + 3) & ~3) + 1; }
 size_t warp_smem_bytes(int cw_max, int hp_max)
 {
     (void)hp_max;
-    return sizeof(float) * ((size_t)kWarpTH * strip_pitch(cw_max) + (size_t)2 * kStageBuf);
+    const size_t nch = (size_t)(cw_max + kChunk - 1) / kChunk;
+    return sizeof(float) * ((size_t)kWarpTH * strip_pitch(cw_max) + (size_t)2 * kStageBuf) + sizeof(StageBox) * nch;
 }
 
 // The rotation step's warp footprint (lanes_x canvas columns x 32 / lanes_x
