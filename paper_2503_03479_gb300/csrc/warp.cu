@@ -315,10 +315,12 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
 
     // 1. rotated canvas strip, chunk by chunk: the source box of chunk k + 1
     //    is copied asynchronously into one staging buffer while chunk k is
-    //    computed from the other.  A warp covers a lanes_x x (32 / lanes_x)
-    //    block of the chunk (the shape and the staging pitch are chosen per
-    //    view to spread its taps over the shared-memory banks); every thread
-    //    walks down one canvas column, where moving kRowStep rows adds
+    //    computed from the other, with one barrier per chunk (once chunk k's
+    //    copies have landed, everyone is also done with chunk k - 1's
+    //    buffer).  A warp covers a lanes_x x (32 / lanes_x) block of the
+    //    chunk (the shape and the staging pitch are chosen per view to
+    //    spread its taps over the shared-memory banks); every thread walks
+    //    down one canvas column, where moving kRowStep rows adds
     //    2 kRowStep (sq, cq) to the Q32 source point.
     {
         const float *__restrict__ src = V.src;
@@ -369,6 +371,8 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
         if (k < nch) stage_box(Sbuf, P, src, sp, bx, warp, lane);
         cp_async_commit();
         while (k < nch) {
+            cp_async_wait<0>();      // this thread's copies of chunk k have landed
+            __syncthreads();         // and everyone's; everyone is done with the other buffer (chunk k - 1)
             StageBox nb;
             const int kn = next_staged(k + 1, nb);
             if (kn < nch) {
@@ -378,8 +382,6 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
                 fbuf = buf ^ 1;
             }
             cp_async_commit();
-            cp_async_wait<1>();      // this thread's copies of chunk k have landed
-            __syncthreads();         // and everyone's
             const float *Ss = Sbuf + buf * kStageBuf;
             const int c0 = k * kChunk, cn = min(kChunk, cw - c0);
             if (c < cn) {
@@ -415,7 +417,6 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
                     }
                 }
             }
-            __syncthreads();         // buffer buf is free for the chunk after next
             k = kn;
             bx = nb;
             buf ^= 1;
