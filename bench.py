@@ -22,6 +22,7 @@ reference arm.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import math
 import os
@@ -409,22 +410,30 @@ def run_ours(args):
     # ---- timed region: K steps, L2 flushed between steps (outside the events).
     # No synchronisation inside: the host builds and enqueues step i + 1 while
     # the GPU runs step i, as a caller streaming pairs would.
+    # The Python garbage collector is off inside (as timeit does): a
+    # collection pass would stall the enqueueing host mid-step.
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     l0 = A.launch_count()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            ev[i][0].record(stream)
-            step(i)
-            ev[i][1].record(stream)
-            flush.zero_()
-        torch.cuda.synchronize()
+    gc.collect()
+    gc.disable()
+    try:
+        with ClockSampler(local) as clk:
+            for i in range(args.steps):
+                ev[i][0].record(stream)
+                step(i)
+                ev[i][1].record(stream)
+                flush.zero_()
+            torch.cuda.synchronize()
+    finally:
+        gc.enable()
     launches = A.launch_count() - l0
     if dist:
         dist.barrier()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms)
     if ctx.read_status(ws) != 0:
         raise RuntimeError("device status word set during the timed region")
 
@@ -637,6 +646,7 @@ def run_ours(args):
                 "views_per_s": value * 2 * nv,
                 "stage_ms": st,
                 "host_ms_per_call": statistics.median(host_t) * 1e3,
+                "step_ms_median": statistics.median(step_ms), "step_ms_max": max(step_ms),
                 "keypoints": [list(x) for x in sizes], "accepted": n_acc,
                 "plain_per_view": plain,
                 "batched_vs_plain": (value / world) / plain["value"] if plain else None,
