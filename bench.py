@@ -52,9 +52,31 @@ def _dist_env():
     return rank, world, local
 
 
+def pair_seed(rank: int, i: int) -> int:
+    """Seed of pair i of a rank: every rank processes its own pairs."""
+    return 2000 + 97 * rank + i
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over the job's ranks (x itself without a process group):
+    the job takes as long as its slowest rank."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput: each of `world` ranks processed units_per_rank
+    units, the slowest of them in `seconds`."""
+    return world * units_per_rank / seconds
+
+
 def _pair(rank: int, i: int):
     from paper_2503_03479_gb300 import synth
-    return synth.pair_extreme_tilt(seed=2000 + 97 * rank + i)
+    return synth.pair_extreme_tilt(seed=pair_seed(rank, i))
 
 
 def _mixed_one(seed: int, index: int):
@@ -446,12 +468,8 @@ def run_ours(args):
         stage_ms.append(ctx.profile_read())
         flush.zero_()
     ctx.profile(False)
-    t_max = ms
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * args.steps / (t_max / 1e3)
+    t_max = max_over_ranks(ms, dist, "cuda")
+    value = job_rate(world, args.steps, t_max / 1e3)
 
     # ---- rooflines of the two heaviest stages, timed live by the stage events
     st = {k: statistics.mean(s[k] for s in stage_ms) for k in stage_ms[0]}
@@ -628,7 +646,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         if i >= args.warmup:
             e2e_t.append(time.perf_counter() - t0)
-    e2e = {"value": world / statistics.mean(e2e_t), "unit": "pairs/s",
+    e2e = {"value": job_rate(world, 1, max_over_ranks(statistics.mean(e2e_t), dist, "cuda")), "unit": "pairs/s",
            "h2d_bytes_per_step": 2 * H * W, "d2h_bytes_per_step": int(hout.numel() + 4)}
 
     if rank == 0:
