@@ -181,15 +181,26 @@ __device__ __forceinline__ float interp_interior(const float *__restrict__ Ss, i
     float2 w[6];
     lanczos3_weights2((uint32_t)px, (uint32_t)py, w);
     const float *b = Ss + ((int)(py >> 32) - 2 - sy0) * P + ((int)(px >> 32) - 2 - sx0);
-    float rs[6];
-#pragma unroll
-    for (int n = 0; n < 6; ++n) {
-        const float *row = b + n * P;
-        rs[n] = fmaf(w[0].x, row[0], fmaf(w[1].x, row[1], fmaf(w[2].x, row[2],
-                fmaf(w[3].x, row[3], fmaf(w[4].x, row[4], w[5].x * row[5])))));
+    // rows (0, 1), (2, 3), (4, 5) as packed pairs: one FFMA2 per column and pair,
+    // then the vertical weights as three more
+    float2 a01, a23, a45;
+    {
+        const float2 wx = make_float2(w[0].x, w[0].x);
+        a01 = __fmul2_rn(wx, make_float2(b[0], b[P]));
+        a23 = __fmul2_rn(wx, make_float2(b[2 * P], b[3 * P]));
+        a45 = __fmul2_rn(wx, make_float2(b[4 * P], b[5 * P]));
     }
-    return fmaf(w[0].y, rs[0], fmaf(w[1].y, rs[1], fmaf(w[2].y, rs[2],
-           fmaf(w[3].y, rs[3], fmaf(w[4].y, rs[4], w[5].y * rs[5])))));
+#pragma unroll
+    for (int m = 1; m < 6; ++m) {
+        const float2 wx = make_float2(w[m].x, w[m].x);
+        a01 = __ffma2_rn(wx, make_float2(b[m], b[P + m]), a01);
+        a23 = __ffma2_rn(wx, make_float2(b[2 * P + m], b[3 * P + m]), a23);
+        a45 = __ffma2_rn(wx, make_float2(b[4 * P + m], b[5 * P + m]), a45);
+    }
+    float2 t = __fmul2_rn(make_float2(w[0].y, w[1].y), a01);
+    t = __ffma2_rn(make_float2(w[2].y, w[3].y), a23, t);
+    t = __ffma2_rn(make_float2(w[4].y, w[5].y), a45, t);
+    return t.x + t.y;
 }
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
