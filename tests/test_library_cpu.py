@@ -97,3 +97,18 @@ def test_workspace_sizes_are_monotone(A):
     L = A.load_library()
     assert L.hamming_workspace_size(1000, 2000) < L.hamming_workspace_size(40000, 40000)
     assert L.asift_views_workspace_size(240, 320, 10) < L.asift_views_workspace_size(768, 1024, 43)
+
+
+def test_view_sampling_matches_the_printed_rule(A):
+    """The (t, phi) list of k <= 5 equals the table written out from the
+    sampling rule printed in Sec. III-B (tests/golden), for the oracle and for
+    the library alike."""
+    import json
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "view_sampling_sec3b.json")))
+    want = [(v["k"], v["j"], v["t"], v["phi_deg"]) for v in gold["views"]]
+    assert len(want) == 43
+    for tab in (O.view_table(768, 1024, 5), A.view_table(768, 1024, 5)):
+        got = [(v.k, v.j, v.t, v.phi_deg) for v in tab]
+        assert [(k, j) for k, j, _, _ in got] == [(k, j) for k, j, _, _ in want]
+        for (_, _, t, phi), (_, _, tw, phiw) in zip(got, want):
+            assert abs(t - tw) < 1e-12 and abs(phi - phiw) < 1e-9
