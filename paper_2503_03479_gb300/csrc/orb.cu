@@ -142,11 +142,13 @@ constexpr int kRW = kDetTW + 2, kRH = kDetTH + 2;   // tile + one-pixel ring
 constexpr int kGW = kDetTW + 8, kGH = kDetTH + 8;   // Sobel gradients for the ring's 7x7 windows
 constexpr int kDetCols = 64;                    // threads along x; blockDim = kDetCols * kDetRowsPar
 constexpr int kDetRowsPar = 4;
-// The staged image has a row pitch P in 77..80 congruent to the level's width
-// mod 4 and starts at the address of its first pixel mod 4, so that interior
-// tiles stage with 32-bit loads (load_word); the tile code is instantiated
-// once per pitch so that the stencil offsets stay compile-time constants.
-constexpr int kSPMin = kSW + 3, kSPMax = kSPMin + 3;
+// The staged image has a row pitch P in 80..83 congruent to the level's width
+// mod 4 and starts at the address of its first pixel mod 4, so that aligned
+// words of a level row land on aligned words of the stage; a row's whole
+// containing words (up to 3 bytes either side) fit between the rows.  The
+// tile code is instantiated once per pitch so that the stencil offsets stay
+// compile-time constants.
+constexpr int kSPMin = kSW + 6, kSPMax = kSPMin + 3;
 
 struct DetSmem {
     long long R[kRH][kRW];
@@ -227,13 +229,30 @@ __device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__r
         sm.ncand = 0;
     }
     // staged pixel (r, c) = image (x0 - kHalo + c, y0 - kHalo + r), clamped,
-    // at S[r * P + c]; interior tiles copy rows as words, the others bytes
+    // at S[r * P + c].  Interior tiles with 3 spare columns of the level on
+    // either side copy each row's whole containing words asynchronously
+    // (every word inside the level row); other interior tiles copy words
+    // with byte-exact edges; the rest copy bytes with clamping.
     const uint8_t *__restrict__ I = L.img;
     const bool interior = x0 - kHalo >= 0 && y0 - kHalo >= 0 && x0 + kDetTW + kHalo <= W && y0 + kDetTH + kHalo <= H;
+    const bool wide = interior && x0 - kHalo >= 3 && x0 + kDetTW + kHalo + 3 <= W;
     const uint8_t *g0 = interior ? I + (size_t)(y0 - kHalo) * W + (x0 - kHalo) : I;
     const int s0 = interior ? (int)((uintptr_t)g0 & 3u) : 0;
     uint8_t *S = sm.img + s0;
-    if (interior) {
+    if (wide) {
+        constexpr int kNW = (kSW + 6) / 4;   // words of a row copy
+        for (int el = threadIdx.x; el < kSH * kNW; el += kThreads) {
+            const int r = el / kNW, k = el - r * kNW;
+            const uint8_t *g = g0 + (size_t)r * W;
+            const int mis = (int)((uintptr_t)g & 3u);
+            if (4 * k < mis + kSW)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                                 (uint32_t)__cvta_generic_to_shared(S + r * P - mis + 4 * k)),
+                             "l"(g - mis + 4 * k)
+                             : "memory");
+        }
+        asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    } else if (interior) {
         constexpr int kNW = (kSW + 6) / 4;   // words of a row copy
         for (int el = threadIdx.x; el < kSH * kNW; el += kThreads) {
             const int r = el / kNW, k = el - r * kNW;
@@ -386,10 +405,11 @@ detect_kernel(int n_tiles, const DevLevel *__restrict__ lv, int n, int thr, Cand
     __shared__ DetSmem sm;
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int e = find_owner(lv, n, tile, [](const DevLevel &d) { return d.det_tile_start; });
+        static_assert(kSPMin % 4 == 0, "pitch kSPMin + i is = i mod 4");
         switch (lv[e].W & 3) {   // P = W mod 4
-        case 1: detect_tile<kSPMin>(tile, e, lv, thr, cand, cand_count, sm); break;
-        case 2: detect_tile<kSPMin + 1>(tile, e, lv, thr, cand, cand_count, sm); break;
-        case 3: detect_tile<kSPMin + 2>(tile, e, lv, thr, cand, cand_count, sm); break;
+        case 0: detect_tile<kSPMin>(tile, e, lv, thr, cand, cand_count, sm); break;
+        case 1: detect_tile<kSPMin + 1>(tile, e, lv, thr, cand, cand_count, sm); break;
+        case 2: detect_tile<kSPMin + 2>(tile, e, lv, thr, cand, cand_count, sm); break;
         default: detect_tile<kSPMin + 3>(tile, e, lv, thr, cand, cand_count, sm); break;
         }
         __syncthreads();
