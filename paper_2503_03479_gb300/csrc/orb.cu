@@ -690,14 +690,21 @@ orient_brief_kernel(const DevLevel *__restrict__ lv, int n_views, int n_levels, 
         m01 += __shfl_xor_sync(0xffffffffu, m01, o);
     }
     __syncwarp();
-    // vertical pass, rounded half up
+    // vertical pass, rounded half up: lane item = (column, 4 consecutive
+    // rows), the 10 intermediate values loaded once
     uint8_t *sm = S[w];
-    for (int i = lane; i < kSm * kSm; i += 32) {
-        const int rr = i / kSm, cc = i - rr * kSm;
-        unsigned a = 0;
+    for (int i = lane; i < kSm * 8; i += 32) {
+        const int g = i / kSm, cc = i - g * kSm, r0 = 4 * g;
+        unsigned hv[10];
 #pragma unroll
-        for (int t = 0; t < 7; ++t) a += (unsigned)c_smooth[t] * h[(rr + t) * kSm + cc];
-        sm[i] = (uint8_t)((a + 32768u) >> 16);
+        for (int t = 0; t < 10; ++t) hv[t] = (r0 + t < kPatch) ? h[(r0 + t) * kSm + cc] : 0u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            unsigned a = 0;
+#pragma unroll
+            for (int t = 0; t < 7; ++t) a += (unsigned)c_smooth[t] * hv[q + t];
+            if (r0 + q < kSm) sm[(r0 + q) * kSm + cc] = (uint8_t)((a + 32768u) >> 16);
+        }
     }
     // orientation sector: on or left of e_b, strictly right of e_{b+1}
     int bin = 0;
