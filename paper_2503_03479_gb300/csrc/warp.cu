@@ -1,30 +1,26 @@
 // warp.cu -- affine view simulation (Eq. (2)-(4)) on sm_103a.
 //
 // One CTA produces a tw x kWarpTH tile of one view (tw <= kWarpTW chosen per
-// view, see warp_tile_width).  A view row j only
-// depends on canvas row j (the tilt acts along canvas x), so the tile needs a
-// canvas strip of kWarpTH rows and columns [bx0 - K, bx1 + K], where
-// [bx0, bx1] = [floor(X(x'_first)) - 2, floor(X(x'_last)) + 3] are the columns
-// the tilt taps read.  The CTA:
+// view, see warp_tile_width).  A view row j only depends on canvas row j (the
+// tilt acts along canvas x), so the tile needs a canvas strip of kWarpTH rows
+// and columns [bx0 - K, bx1 + K], where [bx0, bx1] = [floor(X(x'_first)) - 2,
+// floor(X(x'_last)) + 3] are the columns the tilt taps read.  The CTA:
 //   1. computes the rotated canvas C on that strip in chunks of kChunk
 //      columns; for each chunk the source pixels its 6x6 Lanczos-3 taps can
-//      reach (the bounding box of the rotated chunk, at most 72 x 72) are
-//      first staged in shared memory, so every tap is a shared-memory load
+//      reach (the bounding box of the rotated chunk, at most 72 x 72, rounded
+//      out to 16-byte groups) are staged in shared memory with asynchronous
+//      copies, double-buffered, so every tap is a shared-memory load
 //      (Eq. (3)-(4); geometry in exact Q32 fixed point);
-//   2. blurs the strip along x with the Gaussian taps (B);
-//   3. resamples B at X = t (x' - (Wv-1)/2) + (Wr-1)/2 with Lanczos-3 and
-//      writes fp32 (optional), rint-to-u8 and the footprint mask (computed
-//      per canvas sample in step 1).
-// In every step a warp covers 32 consecutive columns of one row, so its
-// shared-memory accesses fall in distinct banks (step 1 up to the rotation's
-// rounding), and a thread walks down its column in steps of 4 rows, moving
-// its Q32 source point by a constant.
+//   2. applies the Gaussian along x and the Lanczos-3 tilt resampling at
+//      X = t (x' - (Wv-1)/2) + (Wr-1)/2 as one filter per view column
+//      (computed once per view by tilt_filter_kernel), and writes fp32
+//      (optional), rint-to-u8 and the footprint mask.
 // Strip position i holds the value of canvas column clamp(i, 0, Wr-1), which
 // realises the clamped borders of the Gaussian and of the tilt taps without
 // per-tap clamps.
 // Every launch covers a list of views (one view for the per-view form, all
 // views of several images for the batched form); a CTA finds its view by a
-// binary search over the views' first tile index.
+// warp-wide search over the views' first tile index.
 #include <map>
 #include <mutex>
 
