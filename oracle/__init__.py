@@ -45,7 +45,7 @@ class OView(C.Structure):
     _fields_ = [("k", C.c_int32), ("j", C.c_int32), ("W", C.c_int32), ("H", C.c_int32),
                 ("Wr", C.c_int32), ("Hr", C.c_int32), ("Wv", C.c_int32), ("Hv", C.c_int32),
                 ("K", C.c_int32), ("pad", C.c_int32),
-                ("t", C.c_double), ("phi_deg", C.c_double), ("sigma", C.c_double),
+                ("t", C.c_double), ("phi_deg", C.c_double), ("sigma", C.c_double), ("scale", C.c_double),
                 ("cq", C.c_int64), ("sq", C.c_int64), ("tq", C.c_int64)]
 
 
@@ -85,6 +85,9 @@ def lib():
         L.oracle_warp_view.argtypes = [u8p, C.c_int, P(OView), C.c_void_p, C.c_void_p, C.c_void_p]
         L.oracle_warp_view_f64.argtypes = [f64p, C.c_int, P(OView), C.c_void_p, C.c_void_p, C.c_void_p]
         L.oracle_make_view.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, P(OView)]
+        L.oracle_make_view_scaled.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, P(OView)]
+        L.oracle_view_table_scaled.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, P(OView), C.c_int]
+        L.oracle_view_table_scaled.restype = C.c_int
         L.oracle_level_size.argtypes = [C.c_int, C.c_int]
         L.oracle_level_size.restype = C.c_int
         L.oracle_downscale.argtypes = [u8p, C.c_void_p, C.c_int, C.c_int, u8p, C.c_void_p, C.c_int, C.c_int]
@@ -126,11 +129,21 @@ def view_table(H: int, W: int, kmax: int) -> list[OView]:
     return list(arr)
 
 
-def make_view(H: int, W: int, t: float, phi_deg: float) -> OView:
-    """A view descriptor for any tilt t >= 1 and longitude phi (degrees)."""
+def make_view(H: int, W: int, t: float, phi_deg: float, scale: float = 1.0) -> OView:
+    """A view descriptor for any tilt t >= 1, longitude phi (degrees) and
+    scale s > 0 (Eq. (2)'s S: the canvas magnifies the source by s)."""
     v = OView()
-    lib().oracle_make_view(H, W, float(t), float(phi_deg), C.byref(v))
+    lib().oracle_make_view_scaled(H, W, float(t), float(phi_deg), float(scale), C.byref(v))
     return v
+
+
+def view_table_scaled(H: int, W: int, kmax: int, ds: float) -> list[OView]:
+    """The coarse stage's parameter groups (Sec. III-B): the (t, phi) list with
+    the scale s = 1 + k ds tied to the tilt exponent k."""
+    n = lib().oracle_view_table_scaled(H, W, kmax, float(ds), None, 0)
+    arr = (OView * n)()
+    lib().oracle_view_table_scaled(H, W, kmax, float(ds), arr, n)
+    return list(arr)
 
 
 def gauss_taps(sigma: float, K: int) -> np.ndarray:

@@ -69,7 +69,8 @@ typedef struct {
     int32_t K;               /* Gaussian half width ceil(4 sigma)              */
     int32_t pad;
     double t, phi_deg, sigma;
-    int64_t cq, sq, tq;      /* round(cos phi 2^31), round(sin phi 2^31), round(t 2^31) */
+    double scale;            /* s of Eq. (2): the canvas magnifies the source by s */
+    int64_t cq, sq, tq;      /* round(cos phi / s 2^31), round(sin phi / s 2^31), round(t 2^31) */
 } oracle_view;
 
 static double tilt_of(int k)
@@ -78,7 +79,14 @@ static double tilt_of(int k)
 }
 
 /* Fills a view descriptor for a tilt t >= 1 and longitude phi (degrees). */
-void oracle_make_view(int H, int W, double t, double phi, oracle_view *v)
+/*
+ * A view with scale: Eq. (2)'s S magnifies the rotated source by `scale`
+ * before the tilt, so canvas pixel (i, j) samples
+ *   p = R(phi)^T ((i, j) - c_r) / scale + c_s
+ * and the canvas is the scaled bounding box of the rotated image.  The
+ * Gaussian anti-alias depends on t only.
+ */
+void oracle_make_view_scaled(int H, int W, double t, double phi, double scale, oracle_view *v)
 {
     memset(v, 0, sizeof *v);
     double s, c;
@@ -88,22 +96,29 @@ void oracle_make_view(int H, int W, double t, double phi, oracle_view *v)
     v->H = H;
     v->t = t;
     v->phi_deg = phi;
-    v->Wr = (int32_t)ceil((double)W * fabs(c) + (double)H * fabs(s) - 1e-9);
-    v->Hr = (int32_t)ceil((double)W * fabs(s) + (double)H * fabs(c) - 1e-9);
+    v->scale = scale;
+    v->Wr = (int32_t)ceil(scale * ((double)W * fabs(c) + (double)H * fabs(s)) - 1e-9);
+    v->Hr = (int32_t)ceil(scale * ((double)W * fabs(s) + (double)H * fabs(c)) - 1e-9);
     v->Wv = (int32_t)ceil((double)v->Wr / t);
     v->Hv = v->Hr;
     v->sigma = (t == 1.0) ? 0.0 : 0.8 * sqrt(t * t - 1.0);
     v->K = (int32_t)ceil(4.0 * v->sigma);
-    v->cq = llrint(c * Q31);
-    v->sq = llrint(s * Q31);
+    v->cq = llrint(c / scale * Q31);
+    v->sq = llrint(s / scale * Q31);
     v->tq = llrint(t * Q31);
 }
 
-/* View (k, j) of the sampling rule: t = sqrt(2)^k, phi = j 72 / t degrees. */
-static void make_view(int H, int W, int k, int j, oracle_view *v)
+void oracle_make_view(int H, int W, double t, double phi, oracle_view *v)
+{
+    oracle_make_view_scaled(H, W, t, phi, 1.0, v);
+}
+
+/* View (k, j) of the sampling rule: t = sqrt(2)^k, phi = j 72 / t degrees,
+ * scale 1 + k ds. */
+static void make_view(int H, int W, int k, int j, double ds, oracle_view *v)
 {
     double t = tilt_of(k);
-    oracle_make_view(H, W, t, (k == 0) ? 0.0 : (double)j * 72.0 / t, v);
+    oracle_make_view_scaled(H, W, t, (k == 0) ? 0.0 : (double)j * 72.0 / t, 1.0 + (double)k * ds, v);
     v->k = k;
     v->j = j;
 }
@@ -115,7 +130,7 @@ static void make_view(int H, int W, int k, int j, oracle_view *v)
  * similarity that ORB's own orientation already absorbs (the ASIFT convention).
  * Returns the number of views; writes at most cap descriptors.
  */
-int oracle_view_table(int H, int W, int kmax, oracle_view *out, int cap)
+static int view_table_ds(int H, int W, int kmax, double ds, oracle_view *out, int cap)
 {
     int n = 0;
     for (int k = 0; k <= kmax; ++k) {
@@ -123,11 +138,26 @@ int oracle_view_table(int H, int W, int kmax, oracle_view *out, int cap)
         for (int j = 0;; ++j) {
             if (k == 0 && j > 0) break;
             if (k > 0 && !((double)j * 72.0 / t < 180.0)) break;
-            if (n < cap) make_view(H, W, k, j, &out[n]);
+            if (n < cap) make_view(H, W, k, j, ds, &out[n]);
             ++n;
         }
     }
     return n;
+}
+
+int oracle_view_table(int H, int W, int kmax, oracle_view *out, int cap)
+{
+    return view_table_ds(H, W, kmax, 0.0, out, cap);
+}
+
+/*
+ * The coarse stage's parameter groups (Sec. III-B): the same (t, phi) list
+ * with the scale s = 1 + k ds tied to the tilt exponent k (the paper takes
+ * ds = 0.5 and n = 5, so s runs 1, 1.5, ..., 3.5).
+ */
+int oracle_view_table_scaled(int H, int W, int kmax, double ds, oracle_view *out, int cap)
+{
+    return view_table_ds(H, W, kmax, ds, out, cap);
 }
 
 /* Gaussian taps g_0..g_K along the tilt axis, g_k ~ exp(-k^2 / 2 sigma^2),
@@ -714,7 +744,7 @@ int oracle_match(const uint8_t (*q)[32], int nq, const uint8_t (*t)[32], int nt,
 
 /* Back-projection of a keypoint at (xl, yl) of pyramid level l of a view to the
  * source image: level -> level 0 (centre-aligned scale W_0/W_l), -> canvas
- * (x = t (x0 - (Wv-1)/2) + (Wr-1)/2), -> source p = R^T (canvas - c_r) + c_s. */
+ * (x = t (x0 - (Wv-1)/2) + (Wr-1)/2), -> source p = R^T (canvas - c_r) / s + c_s. */
 void oracle_backproject(const oracle_view *v, int l, double xl, double yl, double *sx, double *sy)
 {
     int W0 = v->Wv, H0 = v->Hv;
@@ -725,8 +755,9 @@ void oracle_backproject(const oracle_view *v, int l, double xl, double yl, doubl
     double dx = X - (v->Wr - 1) * 0.5, dy = y0 - (v->Hr - 1) * 0.5;
     double s, c;
     sincos_deg(v->phi_deg, &s, &c);
-    *sx = c * dx + s * dy + (v->W - 1) * 0.5;
-    *sy = -s * dx + c * dy + (v->H - 1) * 0.5;
+    const double z = (v->scale > 0.0) ? v->scale : 1.0;
+    *sx = (c * dx + s * dy) / z + (v->W - 1) * 0.5;
+    *sy = (-s * dx + c * dy) / z + (v->H - 1) * 0.5;
 }
 
 int oracle_sizeof_view(void) { return (int)sizeof(oracle_view); }

@@ -612,3 +612,74 @@ def test_end_to_end_reprojection_small_pair():
     err = np.hypot(*(h[:, :2] / h[:, 2:] - x2).T)
     assert np.median(err) < 1.5
     assert (err <= math.sqrt(3)).mean() >= 0.5
+
+
+# --------------------------------------------------------------------------
+# Scaled views (Eq. (2)'s S, the coarse stage's parameter groups)
+# --------------------------------------------------------------------------
+def _scaled_source_points(v):
+    """Source coordinates of every view pixel of a scaled view, written
+    independently in numpy: p = R^T (q - c_r) / s + c_s."""
+    xs = np.arange(v.Wv)
+    X = v.t * (xs - (v.Wv - 1) / 2) + (v.Wr - 1) / 2
+    J = np.arange(v.Hv)
+    XX, JJ = np.meshgrid(X, J)
+    dx, dy = XX - (v.Wr - 1) / 2, JJ - (v.Hr - 1) / 2
+    r = math.radians(v.phi_deg)
+    c, s = math.cos(r), math.sin(r)
+    return (c * dx + s * dy) / v.scale + (v.W - 1) / 2, (-s * dx + c * dy) / v.scale + (v.H - 1) / 2
+
+
+@pytest.mark.parametrize("t,phi,scale", [(1.0, 0.0, 2.0), (2.0, 30.0, 1.5), (2.8284271247461903, 101.8, 2.0),
+                                         (1.4142135623730951, 50.91, 3.5)])
+def test_scaled_warp_cosine_closed_form(t, phi, scale):
+    """u = 128 + 100 cos(2 pi f.p) with f = s R^T (w, 0): the canvas sees the
+    frequency (w, 0) (magnified by s), the Gaussian along canvas x multiplies
+    the amplitude by exp(-2 pi^2 sigma^2 w^2), the Lanczos resamplings are
+    near-exact.  Pins the scale, centres and rotation of scaled views."""
+    H, W = 120, 150
+    sigma = 0.8 * math.sqrt(t * t - 1)
+    w = 0.11 / scale                    # source frequency s w = 0.11 cycles / px
+    r = math.radians(phi)
+    fx, fy = scale * math.cos(r) * w, -scale * math.sin(r) * w
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+    u = 128 + 100 * np.cos(2 * math.pi * (fx * xx + fy * yy) + 0.3)
+    v = O.make_view(H, W, t, phi, scale)
+    assert v.scale == scale
+    o = O.warp_view(u, v)
+    px, py = _scaled_source_points(v)
+    G = math.exp(-2 * math.pi ** 2 * sigma ** 2 * w ** 2)
+    expect = 128 + 100 * G * np.cos(2 * math.pi * (fx * px + fy * py) + 0.3)
+    m = (px > 12) & (px < W - 13) & (py > 12) & (py < H - 13)
+    assert m.sum() > 500
+    err = np.abs(o.f64[m] - expect[m]).max()
+    assert err < 1.5, err
+    # a wrong scale (or none) misplaces the pattern by far more than that
+    px1, py1 = _view_source_points(v)
+    wrong = 128 + 100 * G * np.cos(2 * math.pi * (fx * px1 + fy * py1) + 0.3)
+    assert np.abs(o.f64[m] - wrong[m]).max() > 20
+
+
+def test_scaled_backprojection_finds_a_dot():
+    H, W = 120, 140
+    yy, xx = np.mgrid[0:H, 0:W]
+    cx, cy = 61.3, 57.8
+    u = 200 * np.exp(-((xx - cx) ** 2 + (yy - cy) ** 2) / (2 * 3.0 ** 2))
+    for v in O.view_table_scaled(H, W, 3, 0.5):
+        o = O.warp_view(u, v)
+        j, i = np.unravel_index(np.argmax(o.f64), o.f64.shape)
+        sx, sy = O.backproject(v, 0, float(i), float(j))
+        # half a view pixel: t / (2 s) source px along the tilt axis, 1 / (2 s) across
+        assert math.hypot(sx - cx, sy - cy) <= v.t / (2 * v.scale) + 0.75
+
+
+def test_scaled_table_keeps_the_sampling_and_ties_s_to_k():
+    a, b = O.view_table(768, 1024, 5), O.view_table_scaled(768, 1024, 5, 0.5)
+    assert len(a) == len(b) == 43
+    for x, y in zip(a, b):
+        assert (x.k, x.j, x.t, x.phi_deg, x.sigma, x.K) == (y.k, y.j, y.t, y.phi_deg, y.sigma, y.K)
+        assert x.scale == 1.0 and y.scale == 1.0 + 0.5 * y.k
+        assert y.Wr >= x.Wr and y.Hr >= x.Hr
+    # ds = 0 is the plain table
+    for x, y in zip(a, O.view_table_scaled(768, 1024, 5, 0.0)):
+        assert (x.Wr, x.Hr, x.Wv, x.cq, x.sq, x.tq) == (y.Wr, y.Hr, y.Wv, y.cq, y.sq, y.tq)
