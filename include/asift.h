@@ -60,10 +60,12 @@ typedef enum {
 #define ASIFT_MAX_LEVELS 12  /* ORB pyramid levels                              */
 
 /*
- * One simulated view (Eq. (2) with psi = 0, s = 1, no translation).
+ * One simulated view (Eq. (2) with psi = 0, scale s (1 for the views of
+ * match_pair; 1 + k ds for the coarse stage), no translation).
  * Geometry, as both this library and any independent check define it:
- *   canvas pixel (i, j) of the Wr x Hr rotated canvas takes the source point
- *   p = R(phi)^T ((i, j) - c_r) + c_s, c = (size - 1)/2, in Q32 fixed point:
+ *   canvas pixel (i, j) of the Wr x Hr rotated, s-times magnified canvas
+ *   takes the source point p = R(phi)^T ((i, j) - c_r) / s + c_s,
+ *   c = (size - 1)/2, in Q32 fixed point:
  *     px = cq (2i - Wr + 1) + sq (2j - Hr + 1) + (W - 1) 2^31
  *     py = -sq (2i - Wr + 1) + cq (2j - Hr + 1) + (H - 1) 2^31
  *   view pixel (x', j) samples canvas row j at X = tq (2x' - Wv + 1) + (Wr - 1) 2^31.
@@ -71,13 +73,14 @@ typedef enum {
 typedef struct {
     int32_t k, j;           /* tilt exponent (t = sqrt2^k), longitude index      */
     int32_t W, H;           /* source image size                                  */
-    int32_t Wr, Hr;         /* canvas size: ceil(W|cos|+H|sin| - 1e-9), ceil(W|sin|+H|cos| - 1e-9) */
+    int32_t Wr, Hr;         /* canvas size: ceil(s (W|cos|+H|sin|) - 1e-9), ceil(s (W|sin|+H|cos|) - 1e-9) */
     int32_t Wv, Hv;         /* view size: ceil(Wr / t), Hr                        */
     int32_t K;              /* Gaussian half width ceil(4 sigma)                  */
     int32_t pad0;
     double t, phi_deg;      /* tilt, longitude (degrees)                          */
     double sigma;           /* 0.8 sqrt(t^2 - 1) (0 at t = 1)                     */
-    int64_t cq, sq, tq;     /* rint(cos phi 2^31), rint(sin phi 2^31), rint(t 2^31) */
+    double s;               /* scale: the canvas magnifies the source by s        */
+    int64_t cq, sq, tq;     /* rint(cos phi / s 2^31), rint(sin phi / s 2^31), rint(t 2^31) */
     float g[ASIFT_MAX_GAUSS]; /* normalised Gaussian taps g_0..g_K (fp32 of fp64) */
 } asift_view_desc;
 
@@ -131,6 +134,14 @@ ASIFT_API asift_status asift_ctx_pattern(const asift_ctx *ctx, int8_t *h_out);
 ASIFT_API asift_status asift_view_table(int H, int W, int kmax, asift_view_desc *h_out, int cap, int *n_views);
 /* One descriptor for an arbitrary tilt t in [1, 11.4) and longitude phi (deg). */
 ASIFT_API asift_status asift_make_view(int H, int W, double t, double phi_deg, asift_view_desc *h_out);
+/* The coarse stage's parameter groups (Sec. III-B): the (t, phi) list of
+ * asift_view_table with the scale s = 1 + k ds tied to the tilt exponent k
+ * (the paper takes ds = 0.5, so s runs 1 .. 3.5 for k <= 5).  ds in [0, 2]. */
+ASIFT_API asift_status asift_view_table_scaled(int H, int W, int kmax, double ds, asift_view_desc *h_out, int cap,
+                                               int *n_views);
+/* One descriptor with a scale s in [1, 8] (asift_make_view is s = 1). */
+ASIFT_API asift_status asift_make_view_scaled(int H, int W, double t, double phi_deg, double s,
+                                              asift_view_desc *h_out);
 
 /* Host-only copies of the tables a context uploads: the seeded steered rBRIEF
  * pattern (int8 [30][256][4] = {px, py, qx, qy}; SplitMix64 -> Box-Muller

@@ -23,7 +23,7 @@ MAX_GAUSS = 48
 PATTERN_SEED = 250303479
 
 EXPORTED = ["asift_ctx_create", "asift_ctx_destroy", "asift_ctx_orb_cfg", "asift_ctx_pattern", "asift_view_table",
-            "asift_make_view", "asift_level_size", "asift_views_bytes", "asift_views_workspace_size", "asift_views",
+            "asift_make_view", "asift_view_table_scaled", "asift_make_view_scaled", "asift_level_size", "asift_views_bytes", "asift_views_workspace_size", "asift_views",
             "orb_workspace_size", "orb_extract", "hamming_workspace_size", "hamming_match",
             "match_pair_workspace_size", "match_pair", "match_pair_inspect", "asift_read_status",
             "asift_launch_count", "asift_pattern_table", "asift_bin_table", "asift_profile_enable",
@@ -45,7 +45,7 @@ class ViewDesc(C.Structure):
     _fields_ = [("k", C.c_int32), ("j", C.c_int32), ("W", C.c_int32), ("H", C.c_int32),
                 ("Wr", C.c_int32), ("Hr", C.c_int32), ("Wv", C.c_int32), ("Hv", C.c_int32),
                 ("K", C.c_int32), ("pad0", C.c_int32),
-                ("t", C.c_double), ("phi_deg", C.c_double), ("sigma", C.c_double),
+                ("t", C.c_double), ("phi_deg", C.c_double), ("sigma", C.c_double), ("s", C.c_double),
                 ("cq", C.c_int64), ("sq", C.c_int64), ("tq", C.c_int64),
                 ("g", C.c_float * MAX_GAUSS)]
 
@@ -106,6 +106,8 @@ def load_library():
         "asift_ctx_pattern": (i32, [vp, vp]),
         "asift_view_table": (i32, [i32, i32, i32, vp, i32, P(C.c_int)]),
         "asift_make_view": (i32, [i32, i32, C.c_double, C.c_double, P(ViewDesc)]),
+        "asift_view_table_scaled": (i32, [i32, i32, i32, C.c_double, vp, i32, P(C.c_int)]),
+        "asift_make_view_scaled": (i32, [i32, i32, C.c_double, C.c_double, C.c_double, P(ViewDesc)]),
         "asift_level_size": (i32, [i32, i32]),
         "asift_views_bytes": (i64, [vp, i32]),
         "asift_views_workspace_size": (sz, [i32, i32, i32]),
@@ -166,12 +168,19 @@ def level_size(n0: int, l: int) -> int:
     return int(load_library().asift_level_size(n0, l))
 
 
-def view_table(H: int, W: int, kmax: int) -> list[ViewDesc]:
+def view_table(H: int, W: int, kmax: int, ds: float | None = None) -> list[ViewDesc]:
+    """The views of the sampling rule (scale 1), or with ds the coarse stage's
+    parameter groups (scale 1 + k ds)."""
     L = load_library()
     n = C.c_int()
-    _check("asift_view_table", L.asift_view_table(H, W, kmax, None, 0, C.byref(n)))
-    arr = (ViewDesc * n.value)()
-    _check("asift_view_table", L.asift_view_table(H, W, kmax, arr, n.value, C.byref(n)))
+    if ds is None:
+        _check("asift_view_table", L.asift_view_table(H, W, kmax, None, 0, C.byref(n)))
+        arr = (ViewDesc * n.value)()
+        _check("asift_view_table", L.asift_view_table(H, W, kmax, arr, n.value, C.byref(n)))
+    else:
+        _check("asift_view_table_scaled", L.asift_view_table_scaled(H, W, kmax, float(ds), None, 0, C.byref(n)))
+        arr = (ViewDesc * n.value)()
+        _check("asift_view_table_scaled", L.asift_view_table_scaled(H, W, kmax, float(ds), arr, n.value, C.byref(n)))
     return list(arr)
 
 
@@ -187,9 +196,10 @@ def bin_table() -> np.ndarray:
     return out
 
 
-def make_view(H: int, W: int, t: float, phi_deg: float) -> ViewDesc:
+def make_view(H: int, W: int, t: float, phi_deg: float, s: float = 1.0) -> ViewDesc:
     v = ViewDesc()
-    _check("asift_make_view", load_library().asift_make_view(H, W, float(t), float(phi_deg), C.byref(v)))
+    _check("asift_make_view_scaled",
+           load_library().asift_make_view_scaled(H, W, float(t), float(phi_deg), float(s), C.byref(v)))
     return v
 
 

@@ -211,15 +211,18 @@ static void build_views(const asift_view_desc *h, int nv, const float *const *sr
         d.tile_start = per_view ? 0 : tiles;
         tiles += d.ntx * ((a.Hv + kWarpTH - 1) / kWarpTH);
         d.t = a.t;
-        // exact trig at multiples of 90 degrees, as in the view table
-        d.cosd = (double)a.cq / 2147483648.0;
-        d.sind = (double)a.sq / 2147483648.0;
+        // cos phi / s and sin phi / s for the back-projection, exact trig at
+        // multiples of 90 degrees as in the view table
         {
-            const double r = a.phi_deg * (3.14159265358979323846 / 180.0);
-            if (std::fmod(a.phi_deg, 90.0) != 0.0) {
-                d.cosd = std::cos(r);
-                d.sind = std::sin(r);
+            double c = std::cos(a.phi_deg * (3.14159265358979323846 / 180.0));
+            double sn = std::sin(a.phi_deg * (3.14159265358979323846 / 180.0));
+            if (std::fmod(a.phi_deg, 90.0) == 0.0) {
+                const long q = ((long)(a.phi_deg / 90.0) % 4 + 4) % 4;
+                c = (q == 0) ? 1.0 : (q == 2 ? -1.0 : 0.0);
+                sn = (q == 1) ? 1.0 : (q == 3 ? -1.0 : 0.0);
             }
+            d.cosd = c / a.s;
+            d.sind = sn / a.s;
         }
         for (int k = 0; k < ASIFT_MAX_GAUSS; ++k) d.g[k] = (k <= a.K) ? a.g[k] : 0.f;
         d.hp = tilt_filter_pitch(a.K);
@@ -240,7 +243,7 @@ static void build_views(const asift_view_desc *h, int nv, const float *const *sr
 static bool view_ok(const asift_view_desc &v)
 {
     return v.W >= 1 && v.H >= 1 && v.Wr >= 1 && v.Hr >= 1 && v.Wv >= 1 && v.Hv >= 1 && v.K >= 0 &&
-           v.K < ASIFT_MAX_GAUSS && v.Wv < 32768 && v.Hv < 32768 && v.t >= 1.0;
+           v.K < ASIFT_MAX_GAUSS && v.Wv < 32768 && v.Hv < 32768 && v.t >= 1.0 && v.s >= 1.0 && v.s <= 8.0;
 }
 
 }  // namespace asift
@@ -395,7 +398,26 @@ asift_status asift_make_view(int H, int W, double t, double phi_deg, asift_view_
 {
     if (H < 1 || W < 1 || H > 16384 || W > 16384 || !(t >= 1.0 && t < 11.4) || !h_out || !(phi_deg == phi_deg))
         return ASIFT_ERR_ARG;
-    make_view_desc(H, W, t, phi_deg, -1, -1, h_out);
+    make_view_desc(H, W, t, phi_deg, -1, -1, 1.0, h_out);
+    return ASIFT_OK;
+}
+
+asift_status asift_view_table_scaled(int H, int W, int kmax, double ds, asift_view_desc *h_out, int cap,
+                                     int *n_views)
+{
+    if (H < 1 || W < 1 || H > 16384 || W > 16384 || kmax < 0 || kmax > 7 || !n_views || cap < 0 ||
+        !(ds >= 0.0 && ds <= 2.0))
+        return ASIFT_ERR_ARG;
+    *n_views = view_table_scaled(H, W, kmax, ds, h_out, cap);
+    return ASIFT_OK;
+}
+
+asift_status asift_make_view_scaled(int H, int W, double t, double phi_deg, double s, asift_view_desc *h_out)
+{
+    if (H < 1 || W < 1 || H > 16384 || W > 16384 || !(t >= 1.0 && t < 11.4) || !h_out || !(phi_deg == phi_deg) ||
+        !(s >= 1.0 && s <= 8.0))
+        return ASIFT_ERR_ARG;
+    make_view_desc(H, W, t, phi_deg, -1, -1, s, h_out);
     return ASIFT_OK;
 }
 
@@ -1333,7 +1355,7 @@ asift_status asift_warp_shape_for(int H, int W, double t0, double phi0, double t
         !out || !(phi0 == phi0))
         return ASIFT_ERR_ARG;
     asift_view_desc v;
-    make_view_desc(H, W, t0, phi0, -1, -1, &v);
+    make_view_desc(H, W, t0, phi0, -1, -1, 1.0, &v);
     out->Wr = v.Wr;
     out->Hr = v.Hr;
     out->Wv = v.Wv;

@@ -83,8 +83,9 @@ cudaError_t launch_dwarp(bool backward, const DiffView *d_views, int n_views, in
                          int32_t *status, cudaStream_t s);
 
 // tables.cpp (host; each table generated from its written definition)
-void make_view_desc(int H, int W, double t, double phi_deg, int k, int j, asift_view_desc *v);
+void make_view_desc(int H, int W, double t, double phi_deg, int k, int j, double scale, asift_view_desc *v);
 int view_table(int H, int W, int kmax, asift_view_desc *out, int cap);
+int view_table_scaled(int H, int W, int kmax, double ds, asift_view_desc *out, int cap);
 int level_size(int n0, int l);
 void make_pattern(uint64_t seed, int8_t pat[30][256][4]);
 void make_bin_table(long long e[30][2]);

@@ -59,7 +59,7 @@ double unit_open0(uint64_t &state)   // uniform in (0, 1]
 
 }  // namespace
 
-void make_view_desc(int H, int W, double t, double phi_deg, int k, int j, asift_view_desc *v)
+void make_view_desc(int H, int W, double t, double phi_deg, int k, int j, double scale, asift_view_desc *v)
 {
     std::memset(v, 0, sizeof(*v));
     double s, c;
@@ -70,14 +70,16 @@ void make_view_desc(int H, int W, double t, double phi_deg, int k, int j, asift_
     v->H = H;
     v->t = t;
     v->phi_deg = phi_deg;
-    v->Wr = (int32_t)std::ceil((double)W * std::fabs(c) + (double)H * std::fabs(s) - 1e-9);
-    v->Hr = (int32_t)std::ceil((double)W * std::fabs(s) + (double)H * std::fabs(c) - 1e-9);
+    v->s = scale;
+    // the canvas is the bounding box of the rotated image magnified by scale
+    v->Wr = (int32_t)std::ceil(scale * ((double)W * std::fabs(c) + (double)H * std::fabs(s)) - 1e-9);
+    v->Hr = (int32_t)std::ceil(scale * ((double)W * std::fabs(s) + (double)H * std::fabs(c)) - 1e-9);
     v->Wv = (int32_t)std::ceil((double)v->Wr / t);
     v->Hv = v->Hr;
     v->sigma = (t == 1.0) ? 0.0 : 0.8 * std::sqrt(t * t - 1.0);
     v->K = (int32_t)std::ceil(4.0 * v->sigma);
-    v->cq = std::llrint(c * 2147483648.0);
-    v->sq = std::llrint(s * 2147483648.0);
+    v->cq = std::llrint(c / scale * 2147483648.0);
+    v->sq = std::llrint(s / scale * 2147483648.0);
     v->tq = std::llrint(t * 2147483648.0);
     if (v->K == 0) {
         v->g[0] = 1.0f;
@@ -92,7 +94,7 @@ void make_view_desc(int H, int W, double t, double phi_deg, int k, int j, asift_
     }
 }
 
-int view_table(int H, int W, int kmax, asift_view_desc *out, int cap)
+int view_table_scaled(int H, int W, int kmax, double ds, asift_view_desc *out, int cap)
 {
     int n = 0;
     for (int k = 0; k <= kmax; ++k) {
@@ -101,12 +103,14 @@ int view_table(int H, int W, int kmax, asift_view_desc *out, int cap)
         for (int j = 0; j < jmax; ++j) {
             const double phi = (k == 0) ? 0.0 : (double)j * 72.0 / t;
             if (!(phi < 180.0)) break;
-            if (out && n < cap) make_view_desc(H, W, t, phi, k, j, &out[n]);
+            if (out && n < cap) make_view_desc(H, W, t, phi, k, j, 1.0 + (double)k * ds, &out[n]);
             ++n;
         }
     }
     return n;
 }
+
+int view_table(int H, int W, int kmax, asift_view_desc *out, int cap) { return view_table_scaled(H, W, kmax, 0.0, out, cap); }
 
 int level_size(int n0, int l)
 {

@@ -112,3 +112,27 @@ def test_view_sampling_matches_the_printed_rule(A):
         assert [(k, j) for k, j, _, _ in got] == [(k, j) for k, j, _, _ in want]
         for (_, _, t, phi), (_, _, tw, phiw) in zip(got, want):
             assert abs(t - tw) < 1e-12 and abs(phi - phiw) < 1e-9
+
+
+@pytest.mark.parametrize("H,W,kmax,ds", [(768, 1024, 5, 0.5), (361, 487, 5, 0.5), (240, 320, 2, 1.25), (96, 128, 3, 0.0)])
+def test_scaled_view_table_equals_oracle(A, H, W, kmax, ds):
+    a = A.view_table(H, W, kmax, ds)
+    b = O.view_table_scaled(H, W, kmax, ds)
+    assert len(a) == len(b)
+    for x, y in zip(a, b):
+        assert (x.k, x.j, x.W, x.H, x.Wr, x.Hr, x.Wv, x.Hv, x.K) == (y.k, y.j, y.W, y.H, y.Wr, y.Hr, y.Wv, y.Hv, y.K)
+        assert (x.t, x.phi_deg, x.sigma, x.s, x.cq, x.sq, x.tq) == (y.t, y.phi_deg, y.sigma, y.scale, y.cq, y.sq, y.tq)
+    for t, phi, s in [(1.0, 0.0, 2.0), (3.3, 47.0, 1.75), (11.0, 90.0, 3.5)]:
+        x, y = A.make_view(123, 77, t, phi, s), O.make_view(123, 77, t, phi, s)
+        assert (x.Wr, x.Hr, x.Wv, x.Hv, x.K, x.cq, x.sq, x.tq, x.s) == (y.Wr, y.Hr, y.Wv, y.Hv, y.K, y.cq, y.sq, y.tq,
+                                                                         y.scale)
+
+
+def test_scaled_view_arguments_are_checked(A):
+    L = A.load_library()
+    n = C.c_int()
+    assert L.asift_view_table_scaled(100, 100, 3, -0.5, None, 0, C.byref(n)) == A.ASIFT_ERR_ARG
+    assert L.asift_view_table_scaled(100, 100, 3, 2.5, None, 0, C.byref(n)) == A.ASIFT_ERR_ARG
+    v = A.ViewDesc()
+    assert L.asift_make_view_scaled(100, 100, 2.0, 10.0, 0.5, C.byref(v)) == A.ASIFT_ERR_ARG
+    assert L.asift_make_view_scaled(100, 100, 2.0, 10.0, 9.0, C.byref(v)) == A.ASIFT_ERR_ARG
