@@ -39,6 +39,7 @@ sys.path.insert(0, ROOT)
 
 H, W, KMAX, LEVELS, NFEAT, THR = 768, 1024, 5, 8, 1000, 20
 LARGE_H, LARGE_W, LARGE_KMAX, LARGE_NFEAT = 3072, 4096, 6, 2000
+DS = 0.5                   # scale step of the coarse stage (s = 1 + k DS)
 WORKLOAD = "asift_pair_1024x768_extreme_tilt_43views_orb8x1000"
 SM_COUNT = 152
 POPC_PER_SM_CLK = 16       # 32-bit population count: 16 results / clock / SM
@@ -208,12 +209,12 @@ FP8_PER_BF16 = 2.0         # nominal dense fp8 / bf16 tensor rate (4.5 / 2.25 PF
 def warp_flops(v) -> float:
     """Algorithmic flops of one simulated view (Eq. (2)-(4)), multiply-add = 2:
     the 6 x 6 Lanczos-3 interpolation of the rotation at every canvas pixel
-    (when phi != 0), the (2K+1)-tap Gaussian along the tilt axis at every canvas
+    (when phi != 0 or s != 1), the (2K+1)-tap Gaussian along the tilt axis at every canvas
     pixel and the 6-tap Lanczos-3 resampling of the tilt at every view pixel
     (both when t > 1).  Weight evaluation, staging and the mask are not counted."""
     canvas = v.Wr * v.Hr
     f = 0.0
-    if v.phi_deg != 0.0:
+    if v.phi_deg != 0.0 or v.s != 1.0:
         f += 36 * canvas
     if v.t > 1.0:
         f += (2 * v.K + 1) * canvas + 6 * v.Wv * v.Hv
@@ -224,6 +225,10 @@ def warp_roofline(views, n_images: int, ms: float, peaks: dict) -> dict:
     f_clk = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * f_clk / 1e12
     flops = n_images * sum(warp_flops(v) for v in views)
+    return _alu_roofline(flops, ms, peak, f_clk)
+
+
+def _alu_roofline(flops: float, ms: float, peak: float, f_clk: float) -> dict:
     achieved = flops / (ms / 1e3) / 1e12
     return {"bound": "alu", "kernel": "warp_view_kernel (+ convert_images_kernel)", "achieved": achieved,
             "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
@@ -626,6 +631,57 @@ def run_ours(args):
                 "views_per_s_fwd_bwd": nd / ((fms + bms) / 1e3)}
         del ud
 
+    # ---- coarse stage (Sec. III-B): the reference's (t, phi, s) parameter
+    # groups against the unwarped target, matches counted per view and the
+    # best group taken on the device
+    coarse = None
+    if args.coarse_steps > 0:
+        pcc = ctx.pair_cfg(kmax=KMAX, coarse=True, ds=DS)
+        wsc = ctx.match_pair_workspace((H, W), (H, W), pcc)
+        vc = ctx.pair_views((H, W), pcc, 0)
+        outc = torch.zeros(len(vc) * NFEAT * A.PAIR_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+
+        def cstep(i):
+            ctx.match_pair(d1[i % n_pairs], d2[i % n_pairs], pcc, outc, n_out, wsc)
+            return ctx.view_counts((H, W), (H, W), pcc, wsc)
+
+        for i in range(2):
+            cstep(i)
+        torch.cuda.synchronize()
+        evc = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.coarse_steps)]
+        for i in range(args.coarse_steps):
+            evc[i][0].record(stream)
+            cstep(i)
+            evc[i][1].record(stream)
+            flush.zero_()
+        torch.cuda.synchronize()
+        if ctx.read_status(wsc) != 0:
+            raise RuntimeError("device status word set in the coarse stage")
+        msc = sum(a.elapsed_time(b) for a, b in evc) / args.coarse_steps
+        ctx.profile(True)
+        stc = []
+        for i in range(min(args.coarse_steps, 10)):
+            cstep(i)
+            stc.append(ctx.profile_read())
+            flush.zero_()
+        ctx.profile(False)
+        stc = {k: statistics.mean(x[k] for x in stc) for k in stc[0]}
+        best_of = []
+        for i in range(n_pairs):
+            counts, best = cstep(i)
+            b = int(best.item())
+            v = vc[b]
+            best_of.append({"view": b, "t": v.t, "phi_deg": v.phi_deg, "s": v.s, "matches": int(counts[b].item())})
+        f_clk = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
+        flops = sum(warp_flops(v) for v in vc)     # the target's identity view costs no arithmetic
+        coarse = {"pairs_per_s": 1e3 / msc, "ms_per_pair": msc, "ds": DS, "views_reference": len(vc),
+                  "views_target": 1, "view_pixels": int(sum(v.Wv * v.Hv for v in vc)), "stage_ms": stc,
+                  "best": best_of,
+                  "roofline_warp": _alu_roofline(flops, stc["warp"], SM_COUNT * FP32_LANES_PER_SM * 2 * f_clk / 1e12,
+                                                 f_clk)}
+        del wsc, outc
+
     # ---- end to end through the C ABI with host buffers
     h1 = [torch.from_numpy(p.img1).pin_memory() for p in pairs]
     h2 = [torch.from_numpy(p.img2).pin_memory() for p in pairs]
@@ -671,6 +727,7 @@ def run_ours(args):
                 "batched_mixed": batched,
                 "large_batched": large,
                 "differentiable": diff,
+                "coarse_stage": coarse,
                 "roofline": roofline, "rooflines": rooflines, "match_engine": ctx.match_engine,
                 "match_engines": engines,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
@@ -693,6 +750,7 @@ def main():
     ap.add_argument("--batch-pairs", type=int, default=64, help="pairs in the mixed-size batched run (0: skip)")
     ap.add_argument("--large-pairs", type=int, default=8, help="pairs in the 4096x3072 batched run (0: skip)")
     ap.add_argument("--diff-views", type=int, default=256, help="views of the differentiable-warp timing (0: skip)")
+    ap.add_argument("--coarse-steps", type=int, default=20, help="steps of the coarse-stage timing (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

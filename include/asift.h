@@ -278,6 +278,13 @@ typedef struct {
     int32_t per_view;       /* 1 = launch every stage once per view (the plain
                                per-view form); 0 = one launch per stage over all
                                views of both images                            */
+    int32_t coarse;         /* 1 = the coarse stage of Sec. III-B: image 1 (the
+                               reference) takes the parameter groups of
+                               asift_view_table_scaled(kmax, ds), image 2 (the
+                               target) its single unwarped view; 0 = both images
+                               the views of asift_view_table(kmax)             */
+    int32_t pad0;
+    double ds;              /* scale step of the coarse stage (default 0.5)     */
 } asift_pair_cfg;
 
 /*
@@ -379,6 +386,21 @@ ASIFT_API asift_status match_pair_inspect(const asift_ctx *ctx, int H1, int W1, 
                                 asift_keypoint **d_kp1, uint8_t **d_desc1, int32_t **d_n1,
                                 asift_keypoint **d_kp2, uint8_t **d_desc2, int32_t **d_n2,
                                 asift_match **d_match);
+
+/* Coarse stage, best-parameter selection (Sec. III-B): after a match_pair call
+ * on d_workspace with the same sizes and configuration, d_counts[v] (v = 0 ..
+ * n1 - 1, n1 = the number of image 1's views, in table order) receives the
+ * number of accepted matches whose image-1 keypoint was detected in view v,
+ * and *d_best (when d_best is not NULL) the view with the most, the lowest v
+ * among equal counts.  With cfg->coarse = 1 the views are the parameter groups
+ * (t, phi, s) of asift_view_table_scaled and image 2 is the unwarped target, so
+ * d_counts[*d_best] names the best parameter group.  Device outputs, written
+ * on `stream` in order after the match_pair launches; the caller owns them.
+ * Errors: ASIFT_ERR_ARG for NULL pointers, a per-view configuration, n_counts
+ * below n1, or n1 above 8192. */
+ASIFT_API asift_status match_pair_view_counts(asift_ctx *ctx, int H1, int W1, int H2, int W2,
+                                              const asift_pair_cfg *cfg, void *d_workspace, int32_t *d_counts,
+                                              int n_counts, int32_t *d_best, void *stream);
 
 /* Synchronises `stream` and copies the status word at the start of a
  * workspace to *h_status (ASIFT_OK, ASIFT_ERR_CAPACITY or ASIFT_ERR_TIMEOUT);

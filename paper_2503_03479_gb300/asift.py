@@ -25,7 +25,7 @@ PATTERN_SEED = 250303479
 EXPORTED = ["asift_ctx_create", "asift_ctx_destroy", "asift_ctx_orb_cfg", "asift_ctx_pattern", "asift_view_table",
             "asift_make_view", "asift_view_table_scaled", "asift_make_view_scaled", "asift_level_size", "asift_views_bytes", "asift_views_workspace_size", "asift_views",
             "orb_workspace_size", "orb_extract", "hamming_workspace_size", "hamming_match",
-            "match_pair_workspace_size", "match_pair", "match_pair_inspect", "asift_read_status",
+            "match_pair_workspace_size", "match_pair", "match_pair_inspect", "match_pair_view_counts", "asift_read_status",
             "asift_launch_count", "asift_pattern_table", "asift_bin_table", "asift_profile_enable",
             "asift_profile_read", "hamming_match_noalloc", "asift_plan_create", "asift_plan_run",
             "asift_plan_pairs", "asift_plan_workspace", "asift_plan_set_tuning", "asift_plan_get_tuning",
@@ -56,7 +56,8 @@ class OrbCfg(C.Structure):
 
 
 class PairCfg(C.Structure):
-    _fields_ = [("kmax", C.c_int32), ("ratio_num", C.c_int32), ("ratio_den", C.c_int32), ("per_view", C.c_int32)]
+    _fields_ = [("kmax", C.c_int32), ("ratio_num", C.c_int32), ("ratio_den", C.c_int32), ("per_view", C.c_int32),
+                ("coarse", C.c_int32), ("pad0", C.c_int32), ("ds", C.c_double)]
 
 
 class PairDesc(C.Structure):
@@ -119,6 +120,7 @@ def load_library():
         "match_pair_workspace_size": (sz, [vp, i32, i32, i32, i32, P(PairCfg)]),
         "match_pair": (i32, [vp, vp, i32, i32, i32, vp, i32, i32, i32, P(PairCfg), vp, i32, vp, vp, sz, vp]),
         "match_pair_inspect": (i32, [vp, i32, i32, i32, i32, P(PairCfg), vp, vp, vp, vp, vp, vp, vp, vp]),
+        "match_pair_view_counts": (i32, [vp, i32, i32, i32, i32, P(PairCfg), vp, vp, i32, vp, vp]),
         "asift_read_status": (i32, [vp, i32, P(C.c_int32), vp]),
         "asift_launch_count": (i64, []),
         "asift_pattern_table": (i32, [C.c_uint64, vp]),
@@ -381,14 +383,25 @@ class Context:
         return hamming_match_noalloc(q, t, num, den)
 
     # -- match_pair
-    def pair_cfg(self, kmax: int = 5, num: int = 4, den: int = 5, per_view: bool = False) -> PairCfg:
-        return PairCfg(kmax, num, den, int(per_view))
+    def pair_cfg(self, kmax: int = 5, num: int = 4, den: int = 5, per_view: bool = False, coarse: bool = False,
+                 ds: float = 0.5) -> PairCfg:
+        """coarse=True: image 1 takes the (t, phi, s) parameter groups with s = 1 + k ds, image 2 the
+        identity view only (the coarse stage of Sec. 3)."""
+        return PairCfg(kmax, num, den, int(per_view), int(coarse), 0, float(ds))
+
+    @staticmethod
+    def pair_views(shape, pc: PairCfg, image: int) -> list:
+        """View table of image 0 or 1 of a pair under pc."""
+        H, W = shape
+        if not pc.coarse:
+            return view_table(H, W, pc.kmax)
+        return view_table(H, W, 0) if image else view_table(H, W, pc.kmax, pc.ds)
 
     def match_pair_workspace(self, shape1, shape2, pc: PairCfg) -> torch.Tensor:
         n = self.L.match_pair_workspace_size(self._ctx, shape1[0], shape1[1], shape2[0], shape2[1], C.byref(pc))
         if n == 0:
             raise AsiftError("match_pair_workspace_size", ASIFT_ERR_ARG)
-        return self.workspace(("pair", tuple(shape1), tuple(shape2), pc.kmax, pc.per_view), n)
+        return self.workspace(("pair", tuple(shape1), tuple(shape2), pc.kmax, pc.per_view, pc.coarse, pc.ds), n)
 
     def match_pair(self, img1: torch.Tensor, img2: torch.Tensor, pc: PairCfg, out: torch.Tensor | None = None,
                    n_out: torch.Tensor | None = None, ws: torch.Tensor | None = None):
@@ -397,7 +410,7 @@ class Context:
         H2, W2 = img2.shape
         if ws is None:
             ws = self.match_pair_workspace((H1, W1), (H2, W2), pc)
-        n1 = len(view_table(H1, W1, pc.kmax))
+        n1 = len(self.pair_views((H1, W1), pc, 0))
         cap = n1 * self.cfg.n_features
         if out is None:
             out = torch.zeros(max(cap, 1) * PAIR_DTYPE.itemsize, dtype=torch.uint8, device=img1.device)
@@ -413,6 +426,17 @@ class Context:
         n = int(n_out.item())
         cap = out.numel() // PAIR_DTYPE.itemsize
         return out[: min(n, cap) * PAIR_DTYPE.itemsize].cpu().numpy().view(PAIR_DTYPE)
+
+    def view_counts(self, shape1, shape2, pc: PairCfg, ws: torch.Tensor):
+        """Accepted matches per image-1 view of the last match_pair on ws, and the
+        view with the most (lowest index on ties): device int32 tensors."""
+        n1 = len(self.pair_views(shape1, pc, 0))
+        counts = torch.empty(n1, dtype=torch.int32, device=ws.device)
+        best = torch.empty(1, dtype=torch.int32, device=ws.device)
+        _check("match_pair_view_counts",
+               self.L.match_pair_view_counts(self._ctx, shape1[0], shape1[1], shape2[0], shape2[1], C.byref(pc),
+                                             _ptr(ws), _ptr(counts), n1, _ptr(best), _stream()))
+        return counts, best
 
     def inspect_pair(self, shape1, shape2, pc: PairCfg, ws: torch.Tensor):
         """Pooled keypoints / descriptors / matches of the last match_pair on ws (host copies)."""
@@ -451,7 +475,7 @@ class Plan:
             assert a.is_cuda and a.dtype == torch.uint8 and b.is_cuda and b.dtype == torch.uint8
             arr[i] = PairDesc(a.data_ptr(), a.shape[0], a.shape[1], a.stride(0),
                               b.data_ptr(), b.shape[0], b.shape[1], b.stride(0))
-        pc = PairCfg(kmax, num, den, 0)
+        pc = PairCfg(kmax, num, den, 0, 0, 0, 0.5)
         tn = Tuning(**tuning) if tuning else None
         self._p = C.c_void_p()
         torch.cuda.synchronize()

@@ -812,7 +812,8 @@ struct Pipeline {
 struct PairKey {
     const uint8_t *img1, *img2;
     int H1, W1, pitch1, H2, W2, pitch2;
-    int32_t kmax, ratio_num, ratio_den, per_view;
+    int32_t kmax, ratio_num, ratio_den, per_view, coarse;
+    double ds;
     asift_pair_match *out;
     int cap;
     int32_t *d_n;
@@ -821,8 +822,8 @@ struct PairKey {
     {
         return img1 == o.img1 && img2 == o.img2 && H1 == o.H1 && W1 == o.W1 && pitch1 == o.pitch1 && H2 == o.H2 &&
                W2 == o.W2 && pitch2 == o.pitch2 && kmax == o.kmax && ratio_num == o.ratio_num &&
-               ratio_den == o.ratio_den && per_view == o.per_view && out == o.out && cap == o.cap && d_n == o.d_n &&
-               ws == o.ws;
+               ratio_den == o.ratio_den && per_view == o.per_view && coarse == o.coarse && ds == o.ds && out == o.out &&
+               cap == o.cap && d_n == o.d_n && ws == o.ws;
     }
 };
 
@@ -840,8 +841,24 @@ struct PairCache {
 
 static void pair_cache_free(PairCache *c) { delete c; }
 
-static bool pipeline_layout(const asift_ctx *ctx, const PairSpec *ps, int P, int kmax, bool per_view, void *base,
-                            Pipeline &L)
+// The views of one pair: both images the sampling rule's (kmax), or for the
+// coarse stage image 1 the scaled parameter groups (kmax, ds) and image 2 its
+// single unwarped view.
+static int pair_views(const PairSpec &p, const asift_pair_cfg &pc, int image, asift_view_desc *out, int cap)
+{
+    const int H = image ? p.H2 : p.H1, W = image ? p.W2 : p.W1;
+    if (!pc.coarse) return view_table(H, W, pc.kmax, out, cap);
+    return image ? view_table(H, W, 0, out, cap) : view_table_scaled(H, W, pc.kmax, pc.ds, out, cap);
+}
+
+static bool pair_cfg_ok(const asift_pair_cfg &pc)
+{
+    return pc.kmax >= 0 && pc.kmax <= 7 && pc.ratio_den >= 1 && pc.ratio_num >= 0 && (pc.coarse == 0 || pc.coarse == 1) &&
+           (!pc.coarse || (pc.ds >= 0.0 && pc.ds <= 2.0));
+}
+
+static bool pipeline_layout(const asift_ctx *ctx, const PairSpec *ps, int P, const asift_pair_cfg &pc, bool per_view,
+                            void *base, Pipeline &L)
 {
     const asift_orb_cfg &cfg = ctx->cfg;
     const int N = cfg.n_features;
@@ -851,14 +868,14 @@ static bool pipeline_layout(const asift_ctx *ctx, const PairSpec *ps, int P, int
     L.first.assign(2 * P + 1, 0);
     L.views.clear();
     for (int p = 0; p < P; ++p) {
-        const int a = view_table(ps[p].H1, ps[p].W1, kmax, nullptr, 0);
-        const int b = view_table(ps[p].H2, ps[p].W2, kmax, nullptr, 0);
+        const int a = pair_views(ps[p], pc, 0, nullptr, 0);
+        const int b = pair_views(ps[p], pc, 1, nullptr, 0);
         L.nv1[p] = a;
         L.nv2[p] = b;
         const size_t o = L.views.size();
         L.views.resize(o + a + b);
-        view_table(ps[p].H1, ps[p].W1, kmax, L.views.data() + o, a);
-        view_table(ps[p].H2, ps[p].W2, kmax, L.views.data() + o + a, b);
+        pair_views(ps[p], pc, 0, L.views.data() + o, a);
+        pair_views(ps[p], pc, 1, L.views.data() + o + a, b);
         L.first[2 * p + 1] = (int)o + a;
         L.first[2 * p + 2] = (int)o + a + b;
     }
@@ -1019,7 +1036,7 @@ extern "C" {
 
 static asift_pair_cfg pair_cfg_or_default(const asift_pair_cfg *c)
 {
-    asift_pair_cfg d{5, 4, 5, 0};
+    asift_pair_cfg d{5, 4, 5, 0, 0, 0, 0.5};
     return c ? *c : d;
 }
 
@@ -1027,10 +1044,10 @@ size_t match_pair_workspace_size(const asift_ctx *ctx, int H1, int W1, int H2, i
 {
     if (!ctx || H1 < 1 || W1 < 1 || H2 < 1 || W2 < 1) return 0;
     const asift_pair_cfg pc = pair_cfg_or_default(cfg);
-    if (pc.kmax < 0 || pc.kmax > 7) return 0;
+    if (!pair_cfg_ok(pc)) return 0;
     Pipeline L;
     PairSpec ps{H1, W1, H2, W2};
-    if (!pipeline_layout(ctx, &ps, 1, pc.kmax, pc.per_view != 0, nullptr, L)) return 0;
+    if (!pipeline_layout(ctx, &ps, 1, pc, pc.per_view != 0, nullptr, L)) return 0;
     return L.bytes;
 }
 
@@ -1040,13 +1057,12 @@ asift_status match_pair(asift_ctx *ctx, const uint8_t *d_img1, int H1, int W1, i
 {
     const asift_pair_cfg pc = pair_cfg_or_default(cfg);
     if (!ctx || !d_img1 || !d_img2 || H1 < 1 || W1 < 1 || H2 < 1 || W2 < 1 || H1 > 16384 || W1 > 16384 ||
-        H2 > 16384 || W2 > 16384 || pitch1 < W1 || pitch2 < W2 || pc.kmax < 0 || pc.kmax > 7 || pc.ratio_den < 1 ||
-        pc.ratio_num < 0 || cap < 0 || (cap && !d_out) || !d_n || !d_workspace ||
-        (reinterpret_cast<uintptr_t>(d_workspace) & 255))
+        H2 > 16384 || W2 > 16384 || pitch1 < W1 || pitch2 < W2 || !pair_cfg_ok(pc) || cap < 0 ||
+        (cap && !d_out) || !d_n || !d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255))
         return ASIFT_ERR_ARG;
     const bool per_view = pc.per_view != 0;
     const PairKey key{d_img1, d_img2, H1, W1, pitch1, H2, W2, pitch2, pc.kmax, pc.ratio_num, pc.ratio_den,
-                      pc.per_view, d_out, cap, d_n, d_workspace};
+                      pc.per_view, pc.coarse, pc.ds, d_out, cap, d_n, d_workspace};
     if (!ctx->pair_cache) ctx->pair_cache = new (std::nothrow) PairCache;
     if (!ctx->pair_cache) return ASIFT_ERR_NOMEM;
     PairCache &C = *ctx->pair_cache;
@@ -1057,7 +1073,7 @@ asift_status match_pair(asift_ctx *ctx, const uint8_t *d_img1, int H1, int W1, i
         PairCache::Entry fresh;
         fresh.key = key;
         PairSpec ps{H1, W1, H2, W2};
-        if (!pipeline_layout(ctx, &ps, 1, pc.kmax, per_view, d_workspace, fresh.L)) return ASIFT_ERR_ARG;
+        if (!pipeline_layout(ctx, &ps, 1, pc, per_view, d_workspace, fresh.L)) return ASIFT_ERR_ARG;
         if (ws_bytes < fresh.L.bytes) return ASIFT_ERR_ARG;
         asift_pair_desc pd{d_img1, H1, W1, pitch1, d_img2, H2, W2, pitch2};
         pipeline_tables(fresh.L, &pd, &d_out, &cap, &d_n, per_view, fresh.blob);
@@ -1089,7 +1105,7 @@ asift_status match_pair_inspect(const asift_ctx *ctx, int H1, int W1, int H2, in
     const asift_pair_cfg pc = pair_cfg_or_default(cfg);
     Pipeline L;
     PairSpec ps{H1, W1, H2, W2};
-    if (!pipeline_layout(ctx, &ps, 1, pc.kmax, pc.per_view != 0, d_workspace, L)) return ASIFT_ERR_ARG;
+    if (!pair_cfg_ok(pc) || !pipeline_layout(ctx, &ps, 1, pc, pc.per_view != 0, d_workspace, L)) return ASIFT_ERR_ARG;
     const size_t off2 = (size_t)L.first[1] * ctx->cfg.n_features;
     if (d_kp1) *d_kp1 = L.kp;
     if (d_desc1) *d_desc1 = L.desc;
@@ -1099,6 +1115,21 @@ asift_status match_pair_inspect(const asift_ctx *ctx, int H1, int W1, int H2, in
     if (d_n2) *d_n2 = L.o.group_total + 1;
     if (d_match) *d_match = L.match;
     return ASIFT_OK;
+}
+
+asift_status match_pair_view_counts(asift_ctx *ctx, int H1, int W1, int H2, int W2, const asift_pair_cfg *cfg,
+                                    void *d_workspace, int32_t *d_counts, int n_counts, int32_t *d_best, void *stream)
+{
+    if (!ctx || !d_workspace || !d_counts || n_counts < 1) return ASIFT_ERR_ARG;
+    const asift_pair_cfg pc = pair_cfg_or_default(cfg);
+    if (!pair_cfg_ok(pc) || pc.per_view) return ASIFT_ERR_ARG;
+    Pipeline L;
+    PairSpec ps{H1, W1, H2, W2};
+    if (!pipeline_layout(ctx, &ps, 1, pc, false, d_workspace, L)) return ASIFT_ERR_ARG;
+    const int nv1 = L.nv1[0];
+    if (n_counts < nv1 || nv1 > view_count_max_views()) return ASIFT_ERR_ARG;
+    return cuda_status(launch_view_counts(L.kp, L.accept, L.o.group_total, L.first[1] * ctx->cfg.n_features,
+                                          L.first[0], nv1, d_counts, d_best, static_cast<cudaStream_t>(stream)));
 }
 
 }  // extern "C"
@@ -1174,7 +1205,7 @@ asift_status asift_plan_create(asift_ctx *ctx, const asift_pair_desc *h_pairs, i
     if (!ctx || !h_pairs || n_pairs < 1 || n_pairs > asift::match_max_problems() || !out) return ASIFT_ERR_ARG;
     *out = nullptr;
     const asift_pair_cfg pc = pair_cfg_or_default(cfg);
-    if (pc.kmax < 0 || pc.kmax > 7 || pc.ratio_den < 1 || pc.ratio_num < 0 || pc.per_view) return ASIFT_ERR_ARG;
+    if (!pair_cfg_ok(pc) || pc.per_view) return ASIFT_ERR_ARG;
     if (tuning && !tuning_ok(*tuning)) return ASIFT_ERR_ARG;
     std::vector<asift::PairSpec> ps(n_pairs);
     for (int i = 0; i < n_pairs; ++i) {
@@ -1191,7 +1222,7 @@ asift_status asift_plan_create(asift_ctx *ctx, const asift_pair_desc *h_pairs, i
     if (tuning) p->tune = *tuning;
     p->use_graph = use_graph != 0;
     p->pairs.assign(h_pairs, h_pairs + n_pairs);
-    if (!asift::pipeline_layout(ctx, ps.data(), n_pairs, pc.kmax, false, nullptr, p->L)) {
+    if (!asift::pipeline_layout(ctx, ps.data(), n_pairs, pc, false, nullptr, p->L)) {
         plan_free(p);
         return ASIFT_ERR_ARG;
     }
@@ -1199,7 +1230,7 @@ asift_status asift_plan_create(asift_ctx *ctx, const asift_pair_desc *h_pairs, i
     if (cudaMalloc(&p->ws, bytes) != cudaSuccess) { plan_free(p); return ASIFT_ERR_NOMEM; }
     if (cudaMemset(p->ws, 0, 256) != cudaSuccess) { plan_free(p); return ASIFT_ERR_CUDA; }
     p->L = asift::Pipeline{};
-    asift::pipeline_layout(ctx, ps.data(), n_pairs, pc.kmax, false, p->ws, p->L);
+    asift::pipeline_layout(ctx, ps.data(), n_pairs, pc, false, p->ws, p->L);
     p->outs.assign(n_pairs, nullptr);
     p->caps.assign(n_pairs, 0);
     if (cudaMalloc(&p->d_ns, sizeof(int32_t) * n_pairs) != cudaSuccess) { plan_free(p); return ASIFT_ERR_NOMEM; }

@@ -64,6 +64,9 @@ cudaError_t launch_hamming_noalloc(const uint8_t *q, int nq, const int32_t *d_nq
                                    int32_t *n_acc, cudaStream_t s);
 cudaError_t launch_pairs(const MatchProblem *d_probs, int n_probs, const MatchProblem &single, int total_blk,
                          int32_t *block_count, const DevView *views, int32_t *status, cudaStream_t s);
+int view_count_max_views();
+cudaError_t launch_view_counts(const asift_keypoint *kp, const uint8_t *accept, const int32_t *d_nq, int nq_cap,
+                               int view0, int n_views, int32_t *counts, int32_t *best, cudaStream_t s);
 
 // match_tc.cu (tensor-core matcher; same partials and merge as match.cu)
 bool tc_match_available();

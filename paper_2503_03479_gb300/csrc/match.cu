@@ -10,6 +10,8 @@
 // lowest index on distance ties and d2 counts equal distances.  merge_kernel
 // takes the two smallest keys over a problem's slices (exact: keys are unique).
 // How a problem is sliced is decided on the device from its actual pool sizes.
+// The coarse stage's per-view match counts and their argmax live here too.
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -388,6 +390,76 @@ cudaError_t launch_pairs(const MatchProblem *d_probs, int n_probs, const MatchPr
     pair_count_kernel<<<total_blk, kPairBlock, 0, s>>>(d_probs, n_probs, single, block_count);
     pair_write_kernel<<<total_blk, kPairBlock, 0, s>>>(d_probs, n_probs, single, block_count, views, status);
     note_launch(2);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- coarse stage: matches per view
+// Best-parameter selection of Sec. III-B: the parameter group whose simulated
+// view of the reference gathers the most accepted matches against the target.
+// view_count_kernel histograms the accepted queries of one pool by the view
+// they were detected in (shared-memory bins, one global add per bin and
+// block); view_argmax_kernel (one block) takes the largest count, the lowest
+// view index among equal counts.
+constexpr int kCountBlock = 256;
+
+__global__ void __launch_bounds__(kCountBlock)
+view_count_kernel(const asift_keypoint *__restrict__ kp, const uint8_t *__restrict__ accept,
+                  const int32_t *__restrict__ d_nq, int nq_cap, int view0, int n_views, int32_t *__restrict__ counts)
+{
+    extern __shared__ int bins[];
+    for (int v = threadIdx.x; v < n_views; v += blockDim.x) bins[v] = 0;
+    __syncthreads();
+    const int nq = count_of(d_nq, nq_cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += gridDim.x * blockDim.x) {
+        if (!accept[i]) continue;
+        const int v = (int)kp[i].view - view0;
+        if (v >= 0 && v < n_views) atomicAdd(&bins[v], 1);
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < n_views; v += blockDim.x)
+        if (bins[v]) atomicAdd(&counts[v], bins[v]);
+}
+
+__device__ __forceinline__ bool count_better(int c, int v, int bc, int bv) { return c > bc || (c == bc && v < bv); }
+
+__global__ void __launch_bounds__(kCountBlock)
+view_argmax_kernel(const int32_t *__restrict__ counts, int n_views, int32_t *__restrict__ best)
+{
+    __shared__ int sc[kCountBlock / 32], sv[kCountBlock / 32];
+    int bc = -1, bv = n_views;
+    for (int v = threadIdx.x; v < n_views; v += blockDim.x)
+        if (count_better(counts[v], v, bc, bv)) { bc = counts[v]; bv = v; }
+    for (int o = 16; o; o >>= 1) {
+        const int c = __shfl_xor_sync(0xffffffffu, bc, o), v = __shfl_xor_sync(0xffffffffu, bv, o);
+        if (count_better(c, v, bc, bv)) { bc = c; bv = v; }
+    }
+    if ((threadIdx.x & 31) == 0) { sc[threadIdx.x >> 5] = bc; sv[threadIdx.x >> 5] = bv; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kCountBlock / 32; ++w)
+            if (count_better(sc[w], sv[w], bc, bv)) { bc = sc[w]; bv = sv[w]; }
+        *best = bv;
+    }
+}
+
+int view_count_max_views() { return 8192; }
+
+cudaError_t launch_view_counts(const asift_keypoint *kp, const uint8_t *accept, const int32_t *d_nq, int nq_cap,
+                               int view0, int n_views, int32_t *counts, int32_t *best, cudaStream_t s)
+{
+    if (n_views < 1 || n_views > view_count_max_views() || nq_cap < 0) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)n_views, s);
+    if (e != cudaSuccess) return e;
+    if (nq_cap > 0) {
+        const int grid = std::min((nq_cap + kCountBlock - 1) / kCountBlock, 2 * 152);
+        view_count_kernel<<<grid, kCountBlock, sizeof(int) * (size_t)n_views, s>>>(kp, accept, d_nq, nq_cap, view0,
+                                                                                 n_views, counts);
+        note_launch();
+    }
+    if (best) {
+        view_argmax_kernel<<<1, kCountBlock, 0, s>>>(counts, n_views, best);
+        note_launch();
+    }
     return cudaGetLastError();
 }
 

@@ -1,0 +1,150 @@
+"""GPU parity of the coarse stage (Sec. III-B): views carrying Eq. (2)'s scale
+s = 1 + k ds, ORB on them, matching of the reference's parameter groups
+against the unwarped target, and the per-view match counts with their argmax.
+
+Bars: the warp within 1e-4 of full scale; ORB, matches, counts and the argmax
+bit-exact against the oracle fed the GPU's own u8 views and descriptor pools.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2503_03479_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+WARP_TOL = 1e-4 * 255
+
+
+@pytest.fixture(scope="module")
+def A():
+    from paper_2503_03479_gb300 import build as B
+    B.build()
+    from paper_2503_03479_gb300 import asift
+    assert torch.cuda.is_available()
+    return asift
+
+
+def _oracle_view(v):
+    return O.make_view(v.H, v.W, v.t, v.phi_deg, scale=v.s)
+
+
+def test_scaled_warp_parity(A):
+    ctx = A.Context()
+    img = synth.texture(101, 143, 31)
+    views = A.view_table(101, 143, 3, 0.5) + [A.make_view(101, 143, 2.6, 33.0, s) for s in (1.25, 2.75, 4.0)]
+    t = torch.from_numpy(img).cuda()
+    vo = ctx.views(t, views, with_f32=True)
+    torch.cuda.synchronize()
+    for i, v in enumerate(views):
+        ov = _oracle_view(v)
+        assert (ov.Wr, ov.Hr, ov.Wv, ov.Hv, ov.cq, ov.sq, ov.tq, ov.K) == (v.Wr, v.Hr, v.Wv, v.Hv, v.cq, v.sq, v.tq, v.K)
+        ref = O.warp_view(img, ov)
+        f = vo.view(i, "f32").cpu().numpy().astype(np.float64)
+        assert f.shape == ref.f64.shape
+        assert np.abs(f - ref.f64).max() <= WARP_TOL, i
+        assert np.array_equal(vo.view(i, "mask").cpu().numpy(), ref.mask), i
+        du = np.abs(vo.view(i, "u8").cpu().numpy().astype(int) - ref.u8.astype(int))
+        near_tie = np.abs(np.abs(ref.f64 - np.floor(ref.f64)) - 0.5) < 3e-3
+        assert (du[~near_tie] == 0).all() and (du <= 1).all(), i
+
+
+def test_scaled_orb_parity(A):
+    L, N = 4, 300
+    ctx = A.Context(n_levels=L, n_features=N)
+    img = synth.texture(120, 160, 32)
+    views = A.view_table(120, 160, 2, 0.5)
+    vo = ctx.views(torch.from_numpy(img).cuda(), views)
+    orb = ctx.orb_extract(vo)
+    torch.cuda.synchronize()
+    kp, desc, vc, _ = orb.host()
+    pat = O.pattern()
+    total = 0
+    for i in range(len(views)):
+        u = vo.view(i, "u8").cpu().numpy()
+        m = vo.view(i, "mask").cpu().numpy()
+        ref = O.orb_view(u, m, L, N, 20, pat)
+        n = len(ref.kps)
+        assert vc[i] == n
+        for f in ("x", "y", "level", "bin", "r25"):
+            assert np.array_equal(kp[total:total + n][f], ref.kps[f]), (i, f)
+        assert np.array_equal(desc[total:total + n], ref.desc), i
+        total += n
+    assert total > 1000
+
+
+def _coarse_run(A, ctx, img1, img2, kmax, ds):
+    pc = ctx.pair_cfg(kmax=kmax, coarse=True, ds=ds)
+    t1, t2 = torch.from_numpy(img1).cuda(), torch.from_numpy(img2).cuda()
+    out, n, ws = ctx.match_pair(t1, t2, pc)
+    counts, best = ctx.view_counts(img1.shape, img2.shape, pc, ws)
+    torch.cuda.synchronize()
+    assert ctx.read_status(ws) == 0
+    return pc, ctx.pairs_host(out, n), ws, counts.cpu().numpy(), int(best.item())
+
+
+@pytest.mark.parametrize("kmax,ds", [(2, 0.5), (3, 0.25), (0, 0.5)])
+def test_coarse_counts_and_argmax_equal_oracle(A, kmax, ds):
+    L, N = 4, 400
+    ctx = A.Context(n_levels=L, n_features=N)
+    p = synth.pair_affine_small(seed=1003)
+    pc, pairs, ws, counts, best = _coarse_run(A, ctx, p.img1, p.img2, kmax, ds)
+    views1 = A.view_table(*p.img1.shape, kmax, ds)
+    assert len(counts) == len(views1)
+    kp1, d1, kp2, d2, m = ctx.inspect_pair(p.img1.shape, p.img2.shape, pc, ws)
+    # image 1's pool is the scaled views' ORB, image 2's the single identity view
+    vo = ctx.views(torch.from_numpy(p.img1).cuda(), views1)
+    rk1, rd1, _, _ = ctx.orb_extract(vo).host()
+    assert np.array_equal(kp1, rk1) and np.array_equal(d1, rd1)
+    assert (kp2["view"] == len(views1)).all()
+    u2 = ctx.views(torch.from_numpy(p.img2).cuda(), A.view_table(*p.img2.shape, 0))
+    torch.cuda.synchronize()
+    assert np.array_equal(u2.view(0, "u8").cpu().numpy(), p.img2)
+    ref2 = O.orb_view(p.img2, u2.view(0, "mask").cpu().numpy(), L, N, 20, O.pattern())
+    for f in ("x", "y", "level", "bin", "r25"):
+        assert np.array_equal(kp2[f], ref2.kps[f]), f
+    assert np.array_equal(d2, ref2.desc)
+    # matches, counts per view and the best parameter group
+    ref = O.match(d1, d2, 4, 5)
+    assert np.array_equal(m["best"], ref.best)
+    acc = np.flatnonzero(ref.accepted)
+    assert np.array_equal(pairs["q"], acc)
+    want = np.bincount(kp1["view"][acc].astype(np.int64), minlength=len(views1))
+    assert np.array_equal(counts, want)
+    assert best == int(np.argmax(want))           # first maximum: the lowest view index
+    # back-projection through the scaled views
+    ov1 = O.view_table_scaled(*p.img1.shape, kmax, ds)
+    for r in pairs[:: max(1, len(pairs) // 100)]:
+        k1 = kp1[r["q"]]
+        x1, y1 = O.backproject(ov1[k1["view"]], int(k1["level"]), float(k1["x"]), float(k1["y"]))
+        assert abs(r["x1"] - x1) < 1e-3 and abs(r["y1"] - y1) < 1e-3
+
+
+def test_coarse_finds_the_simulated_view(A):
+    """A target that is exactly one parameter group's simulated view of the
+    reference (made by the oracle) draws the most matches to that group."""
+    L, N, kmax, ds = 4, 400, 2, 0.5
+    ctx = A.Context(n_levels=L, n_features=N)
+    img1 = synth.texture(150, 190, 33)
+    table = O.view_table_scaled(150, 190, kmax, ds)
+    for star in (3, 7):
+        img2 = np.ascontiguousarray(O.warp_view(img1, table[star]).u8)
+        _, pairs, _, counts, best = _coarse_run(A, ctx, img1, img2, kmax, ds)
+        assert best == star, (star, counts.tolist())
+        assert counts[star] > 2 * np.delete(counts, star).max()
+
+
+def test_view_counts_rejects_short_output(A):
+    ctx = A.Context(n_levels=3, n_features=100)
+    p = synth.pair_affine_small(seed=1004, H=64, W=80)
+    pc, _, ws, counts, _ = _coarse_run(A, ctx, p.img1, p.img2, 1, 0.5)
+    short = torch.empty(len(counts) - 1, dtype=torch.int32, device="cuda")
+    import ctypes as C
+    rc = ctx.L.match_pair_view_counts(ctx._ctx, 64, 80, 64, 80, C.byref(pc), ws.data_ptr(), short.data_ptr(),
+                                      short.numel(), None, None)
+    assert rc == A.ASIFT_ERR_ARG
+    pv = ctx.pair_cfg(kmax=1, per_view=True)
+    rc = ctx.L.match_pair_view_counts(ctx._ctx, 64, 80, 64, 80, C.byref(pv), ws.data_ptr(), short.data_ptr(),
+                                      short.numel(), None, None)
+    assert rc == A.ASIFT_ERR_ARG

@@ -80,6 +80,7 @@ def test_bad_arguments_are_rejected(A):
     assert L.match_pair_workspace_size(None, 10, 10, 10, 10, None) == 0
     assert L.hamming_match(None, None, 0, None, None, 0, None, 4, 5, None, None, None, None, 0, None) == A.ASIFT_ERR_ARG
     assert L.asift_read_status(None, 0, None, None) == A.ASIFT_ERR_ARG
+    assert L.match_pair_view_counts(None, 10, 10, 10, 10, None, None, None, 0, None, None) == A.ASIFT_ERR_ARG
 
 
 def test_context_without_gpu_fails_loudly(A):
