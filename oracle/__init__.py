@@ -84,6 +84,8 @@ def lib():
         L.oracle_lanczos3_weights.argtypes = [C.c_double, f64p]
         L.oracle_warp_view.argtypes = [u8p, C.c_int, P(OView), C.c_void_p, C.c_void_p, C.c_void_p]
         L.oracle_warp_view_f64.argtypes = [f64p, C.c_int, P(OView), C.c_void_p, C.c_void_p, C.c_void_p]
+        L.oracle_warp_view_nn.argtypes = [u8p, C.c_int, P(OView), C.c_void_p, C.c_void_p, C.c_void_p]
+        L.oracle_warp_view_nn_f64.argtypes = [f64p, C.c_int, P(OView), C.c_void_p, C.c_void_p, C.c_void_p]
         L.oracle_make_view.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, P(OView)]
         L.oracle_make_view_scaled.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, P(OView)]
         L.oracle_view_table_scaled.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, P(OView), C.c_int]
@@ -186,6 +188,24 @@ def warp_view(u: np.ndarray, v: OView) -> ViewOut:
     else:
         u = np.ascontiguousarray(u, dtype=np.float64)
         lib().oracle_warp_view_f64(u, W, C.byref(v), f.ctypes.data, b.ctypes.data, m.ctypes.data)
+    return ViewOut(f, b, m)
+
+
+def warp_view_nn(u: np.ndarray, v: OView) -> ViewOut:
+    """The nearest-neighbour form of the coarse stage (Sec. III-B): nearest
+    source pixel for the rotation, Gaussian along x, nearest canvas column for
+    the tilt.  ``u`` is uint8 or float64 (H, W)."""
+    H, W = u.shape
+    assert (H, W) == (v.H, v.W)
+    f = np.zeros((v.Hv, v.Wv), dtype=np.float64)
+    b = np.zeros((v.Hv, v.Wv), dtype=np.uint8)
+    m = np.zeros((v.Hv, v.Wv), dtype=np.uint8)
+    if u.dtype == np.uint8:
+        u = np.ascontiguousarray(u)
+        lib().oracle_warp_view_nn(u, W, C.byref(v), f.ctypes.data, b.ctypes.data, m.ctypes.data)
+    else:
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        lib().oracle_warp_view_nn_f64(u, W, C.byref(v), f.ctypes.data, b.ctypes.data, m.ctypes.data)
     return ViewOut(f, b, m)
 
 

@@ -22,6 +22,7 @@
  *   Eq. (3), (4)   Lanczos interpolation, L(x;a) = sinc(x) sinc(x/a) on |x| < a
  *   Sec. III-B     ORB (oFAST + rBRIEF) coarse extraction, brute-force Hamming matcher
  *   Sec. IV-C      nearest / second-nearest distance ratio test
+ *   Sec. III-B     nearest-neighbour interpolation and scale s of the coarse stage
  * ORB internals the paper does not state (pyramid, FAST-9, Harris, centroid
  * orientation, steered BRIEF) follow the ORB paper cited as [23]; where that is
  * silent, the reading chosen is stated at each function.
@@ -315,6 +316,63 @@ void oracle_warp_view(const uint8_t *u, int pitch, const oracle_view *v,
     for (int y = 0; y < v->H; ++y)
         for (int x = 0; x < v->W; ++x) d[(size_t)y * v->W + x] = (double)u[(size_t)y * pitch + x];
     oracle_warp_view_f64(d, v->W, v, out_f64, out_u8, out_mask);
+    free(d);
+}
+
+/* Nearest-neighbour form of the view, the interpolation the coarse stage
+ * uses (Sec. III-B): the Lanczos-3 samples of the rotation and of the tilt
+ * become the value of the nearest pixel, round(p) = floor(p + 1/2) taken in
+ * Q32, with the same background rule (0 outside [-0.5, W-0.5) x
+ * [-0.5, H-0.5)), the same Gaussian along canvas x before the tilt, the same
+ * quantisation and the same mask.  The tilt's nearest canvas column is
+ * clamped to [0, Wr-1]. */
+static double canvas_value_nn(const double *u, int pitch, const oracle_view *v, int i, int jrow)
+{
+    int64_t px, py;
+    canvas_to_src(v, i, jrow, &px, &py);
+    const int64_t half = 2147483648LL;
+    if (px < -half || px >= (int64_t)(2 * v->W - 1) * half) return 0.0;
+    if (py < -half || py >= (int64_t)(2 * v->H - 1) * half) return 0.0;
+    const int xs = (int)q32_floor(px + half), ys = (int)q32_floor(py + half);
+    return u[(size_t)ys * pitch + xs];
+}
+
+void oracle_warp_view_nn_f64(const double *u, int pitch, const oracle_view *v,
+                             double *out_f64, uint8_t *out_u8, uint8_t *out_mask)
+{
+    const int Wr = v->Wr, Hr = v->Hr, Wv = v->Wv, K = v->K;
+    const int64_t half = 2147483648LL;
+    double g[128];
+    oracle_gauss_taps(v->sigma, K, g);
+    double *Crow = (double *)malloc(sizeof(double) * (size_t)Wr);
+    for (int j = 0; j < Hr; ++j) {
+        for (int i = 0; i < Wr; ++i) Crow[i] = canvas_value_nn(u, pitch, v, i, j);
+        for (int x = 0; x < Wv; ++x) {
+            int64_t X = v->tq * (2 * (int64_t)x - Wv + 1) + (int64_t)(Wr - 1) * half;
+            const int xn = clampi((int)q32_floor(X + half), 0, Wr - 1);
+            /* B(xn) = sum_k g_|k| C(clamp(xn - k)) */
+            double acc = 0.0;
+            for (int k = -K; k <= K; ++k) acc += g[abs(k)] * Crow[clampi(xn - k, 0, Wr - 1)];
+            const int x0 = (int)q32_floor(X);
+            size_t o = (size_t)j * Wv + x;
+            if (out_f64) out_f64[o] = acc;
+            if (out_u8) {
+                double r = nearbyint(acc);
+                out_u8[o] = (uint8_t)(r < 0.0 ? 0.0 : (r > 255.0 ? 255.0 : r));
+            }
+            if (out_mask) out_mask[o] = (uint8_t)(canvas_valid(v, x0, j) && canvas_valid(v, x0 + 1, j));
+        }
+    }
+    free(Crow);
+}
+
+void oracle_warp_view_nn(const uint8_t *u, int pitch, const oracle_view *v,
+                         double *out_f64, uint8_t *out_u8, uint8_t *out_mask)
+{
+    double *d = (double *)malloc(sizeof(double) * (size_t)v->W * v->H);
+    for (int y = 0; y < v->H; ++y)
+        for (int x = 0; x < v->W; ++x) d[(size_t)y * v->W + x] = (double)u[(size_t)y * pitch + x];
+    oracle_warp_view_nn_f64(d, v->W, v, out_f64, out_u8, out_mask);
     free(d);
 }
 

@@ -683,3 +683,107 @@ def test_scaled_table_keeps_the_sampling_and_ties_s_to_k():
     # ds = 0 is the plain table
     for x, y in zip(a, O.view_table_scaled(768, 1024, 5, 0.0)):
         assert (x.Wr, x.Hr, x.Wv, x.cq, x.sq, x.tq) == (y.Wr, y.Hr, y.Wv, y.cq, y.sq, y.tq)
+
+
+# --------------------------------------------------------------------------
+# Nearest-neighbour views of the coarse stage (Sec. III-B)
+# --------------------------------------------------------------------------
+def test_nn_identity_and_right_angles_are_exact():
+    u = synth.random_u8((29, 41), 13)
+    o = O.warp_view_nn(u, O.view_table(29, 41, 0)[0])
+    assert np.array_equal(o.f64, u.astype(np.float64)) and np.array_equal(o.u8, u)
+    for phi, k in ((90.0, -1), (180.0, 2), (270.0, 1)):
+        o = O.warp_view_nn(u, O.make_view(29, 41, 1.0, phi))
+        assert np.array_equal(o.u8, np.rot90(u, k)), phi
+
+
+@pytest.mark.parametrize("scale", [2, 3])
+def test_nn_integer_magnification_replicates_pixels(scale):
+    """phi = 0, t = 1, s integer: canvas pixel i maps to source i/s - (s-1)/(2s),
+    whose nearest pixel is i // s, so the view is every pixel repeated s x s."""
+    u = synth.random_u8((23, 31), 14)
+    v = O.make_view(23, 31, 1.0, 0.0, float(scale))
+    o = O.warp_view_nn(u, v)
+    assert np.array_equal(o.u8, np.kron(u, np.ones((scale, scale), np.uint8)))
+
+
+@pytest.mark.parametrize("phi,scale", [(23.0, 1.0), (61.7, 1.5), (127.3, 2.25), (200.0, 3.0)])
+def test_nn_picks_a_pixel_within_half_a_pixel(phi, scale):
+    """u encodes its own coordinates; at t = 1 every view pixel inside the
+    footprint holds a source pixel at most half a pixel from the exact source
+    point per axis (computed in floating point, not from the Q32 geometry),
+    and every pixel outside holds 0."""
+    H, W = 47, 59
+    yy, xx = np.mgrid[0:H, 0:W]
+    u = (1 + xx + 1000 * yy).astype(np.float64)
+    v = O.make_view(H, W, 1.0, phi, scale)
+    assert v.Wv == v.Wr and v.K == 0
+    o = O.warp_view_nn(u, v)
+    px, py = _scaled_source_points(v)
+    eps = 1e-6
+    inside = (px >= -0.5 + eps) & (px < W - 0.5 - eps) & (py >= -0.5 + eps) & (py < H - 0.5 - eps)
+    outside = (px < -0.5 - eps) | (px >= W - 0.5 + eps) | (py < -0.5 - eps) | (py >= H - 0.5 + eps)
+    val = o.f64.astype(np.int64)
+    xs, ys = (val - 1) % 1000, (val - 1) // 1000
+    assert inside.sum() > 1000
+    assert (val[inside] > 0).all()
+    assert (np.abs(xs[inside] - px[inside]) <= 0.5 + eps).all()
+    assert (np.abs(ys[inside] - py[inside]) <= 0.5 + eps).all()
+    assert (val[outside] == 0).all()
+
+
+@pytest.mark.parametrize("t", [2.0, 2.8284271247461903, 4.0])
+def test_nn_tilt_takes_the_nearest_blurred_column(t):
+    """phi = 0, s = 1, u = 128 + 100 cos(2 pi w x): the canvas is u, the Gaussian
+    along x multiplies the amplitude by exp(-2 pi^2 sigma^2 w^2), and view
+    column x' takes canvas column round(t (x' - (Wv-1)/2) + (Wr-1)/2)."""
+    H, W = 40, 240
+    sigma = 0.8 * math.sqrt(t * t - 1)
+    w = math.sqrt(math.log(2) / (2 * math.pi ** 2 * sigma ** 2))
+    xx = np.broadcast_to(np.arange(W, dtype=np.float64), (H, W))
+    u = 128 + 100 * np.cos(2 * math.pi * w * xx + 0.3)
+    v = O.make_view(H, W, t, 0.0)
+    o = O.warp_view_nn(u, v)
+    X = t * (np.arange(v.Wv) - (v.Wv - 1) / 2) + (v.Wr - 1) / 2
+    G = math.exp(-2 * math.pi ** 2 * sigma ** 2 * w ** 2)
+    expect = 128 + 100 * G * np.cos(2 * math.pi * w * np.floor(X + 0.5) + 0.3)
+    lanczos_like = 128 + 100 * G * np.cos(2 * math.pi * w * X + 0.3)
+    inner = (X > 4 * sigma + 3) & (X < W - 4 * sigma - 4)
+    assert inner.sum() > 20
+    err = np.abs(o.f64[:, inner] - expect[inner]).max()
+    assert err < 1.0, err
+    # the nearest column, not the exact position
+    assert np.abs(o.f64[:, inner] - lanczos_like[inner]).max() > 3.0
+
+
+def test_nn_stays_near_the_lanczos_view_on_a_smooth_image():
+    """On a smooth image the nearest-neighbour view differs from the (pinned)
+    Lanczos-3 view by at most the gradient times the rounding distance
+    (half a source pixel per axis, plus half a canvas column) where the
+    Gaussian window lies inside the footprint; masks agree."""
+    H, W = 110, 140
+    yy, xx = np.mgrid[0:H, 0:W]
+    u = 128 + 90 * np.exp(-((xx - 70.3) ** 2 + (yy - 52.6) ** 2) / (2 * 14.0 ** 2))
+    gmax = 90 / (14.0 * math.sqrt(math.e))          # largest slope of the blob
+    for v in O.view_table_scaled(H, W, 3, 0.5)[1:]:
+        a, b = O.warp_view_nn(u, v), O.warp_view(u, v)
+        assert np.array_equal(a.mask, b.mask)
+        px, py = _scaled_source_points(v)
+        r = (v.K + 4) * v.t / v.scale + 2
+        deep = (px > r) & (px < W - 1 - r) & (py > r) & (py < H - 1 - r)
+        assert deep.sum() > 50
+        bound = gmax * (math.sqrt(0.5) + 0.5 / v.scale) + 0.5
+        d = np.abs(a.f64[deep] - b.f64[deep])
+        assert d.max() <= bound, (v.k, v.j, d.max(), bound)
+        assert d.max() > 1e-3
+
+
+def test_nn_constant_image_stays_constant_inside():
+    u = np.full((90, 120), 181, np.uint8)
+    for v in O.view_table_scaled(90, 120, 3, 0.5)[1:]:
+        o = O.warp_view_nn(u, v)
+        px, py = _scaled_source_points(v)
+        r = (v.K + 2) * v.t / v.scale + 2
+        deep = (px > r) & (px < v.W - 1 - r) & (py > r) & (py < v.H - 1 - r)
+        assert deep.sum() > 50
+        assert np.abs(o.f64[deep] - 181).max() < 1e-12
