@@ -633,54 +633,62 @@ def run_ours(args):
 
     # ---- coarse stage (Sec. III-B): the reference's (t, phi, s) parameter
     # groups against the unwarped target, matches counted per view and the
-    # best group taken on the device
+    # best group taken on the device; nearest-neighbour views as the paper's
+    # coarse stage, and the same with Lanczos-3 views
     coarse = None
     if args.coarse_steps > 0:
-        pcc = ctx.pair_cfg(kmax=KMAX, coarse=True, ds=DS)
-        wsc = ctx.match_pair_workspace((H, W), (H, W), pcc)
-        vc = ctx.pair_views((H, W), pcc, 0)
-        outc = torch.zeros(len(vc) * NFEAT * A.PAIR_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        coarse = {"ds": DS}
+        for name, nearest in (("nearest", True), ("lanczos3", False)):
+            pcc = ctx.pair_cfg(kmax=KMAX, coarse=True, ds=DS, nearest=nearest)
+            wsc = ctx.match_pair_workspace((H, W), (H, W), pcc)
+            vc = ctx.pair_views((H, W), pcc, 0)
+            outc = torch.zeros(len(vc) * NFEAT * A.PAIR_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
 
-        def cstep(i):
-            ctx.match_pair(d1[i % n_pairs], d2[i % n_pairs], pcc, outc, n_out, wsc)
-            return ctx.view_counts((H, W), (H, W), pcc, wsc)
+            def cstep(i):
+                ctx.match_pair(d1[i % n_pairs], d2[i % n_pairs], pcc, outc, n_out, wsc)
+                return ctx.view_counts((H, W), (H, W), pcc, wsc)
 
-        for i in range(2):
-            cstep(i)
-        torch.cuda.synchronize()
-        evc = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.coarse_steps)]
-        for i in range(args.coarse_steps):
-            evc[i][0].record(stream)
-            cstep(i)
-            evc[i][1].record(stream)
-            flush.zero_()
-        torch.cuda.synchronize()
-        if ctx.read_status(wsc) != 0:
-            raise RuntimeError("device status word set in the coarse stage")
-        msc = sum(a.elapsed_time(b) for a, b in evc) / args.coarse_steps
-        ctx.profile(True)
-        stc = []
-        for i in range(min(args.coarse_steps, 10)):
-            cstep(i)
-            stc.append(ctx.profile_read())
-            flush.zero_()
-        ctx.profile(False)
-        stc = {k: statistics.mean(x[k] for x in stc) for k in stc[0]}
-        best_of = []
-        for i in range(n_pairs):
-            counts, best = cstep(i)
-            b = int(best.item())
-            v = vc[b]
-            best_of.append({"view": b, "t": v.t, "phi_deg": v.phi_deg, "s": v.s, "matches": int(counts[b].item())})
-        f_clk = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
-        flops = sum(warp_flops(v) for v in vc)     # the target's identity view costs no arithmetic
-        coarse = {"pairs_per_s": 1e3 / msc, "ms_per_pair": msc, "ds": DS, "views_reference": len(vc),
-                  "views_target": 1, "view_pixels": int(sum(v.Wv * v.Hv for v in vc)), "stage_ms": stc,
-                  "best": best_of,
-                  "roofline_warp": _alu_roofline(flops, stc["warp"], SM_COUNT * FP32_LANES_PER_SM * 2 * f_clk / 1e12,
-                                                 f_clk)}
-        del wsc, outc
+            for i in range(2):
+                cstep(i)
+            torch.cuda.synchronize()
+            evc = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.coarse_steps)]
+            for i in range(args.coarse_steps):
+                evc[i][0].record(stream)
+                cstep(i)
+                evc[i][1].record(stream)
+                flush.zero_()
+            torch.cuda.synchronize()
+            if ctx.read_status(wsc) != 0:
+                raise RuntimeError("device status word set in the coarse stage")
+            msc = sum(a.elapsed_time(b) for a, b in evc) / args.coarse_steps
+            ctx.profile(True)
+            stc = []
+            for i in range(min(args.coarse_steps, 10)):
+                cstep(i)
+                stc.append(ctx.profile_read())
+                flush.zero_()
+            ctx.profile(False)
+            stc = {k: statistics.mean(x[k] for x in stc) for k in stc[0]}
+            best_of = []
+            for i in range(n_pairs):
+                counts, best = cstep(i)
+                b = int(best.item())
+                v = vc[b]
+                best_of.append({"view": b, "t": v.t, "phi_deg": v.phi_deg, "s": v.s,
+                                "matches": int(counts[b].item())})
+            px = sum(v.Wv * v.Hv for v in vc)
+            line = {"pairs_per_s": 1e3 / msc, "ms_per_pair": msc, "views_reference": len(vc), "views_target": 1,
+                    "view_pixels": int(px), "stage_ms": stc, "best": best_of}
+            if nearest:
+                line["warp_gpix_per_s"] = px / (stc["warp"] / 1e3) / 1e9
+            else:
+                f_clk = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
+                flops = sum(warp_flops(v) for v in vc)     # the target's identity view costs no arithmetic
+                line["roofline_warp"] = _alu_roofline(flops, stc["warp"],
+                                                      SM_COUNT * FP32_LANES_PER_SM * 2 * f_clk / 1e12, f_clk)
+            coarse[name] = line
+            del wsc, outc
 
     # ---- end to end through the C ABI with host buffers
     h1 = [torch.from_numpy(p.img1).pin_memory() for p in pairs]

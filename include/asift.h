@@ -178,6 +178,16 @@ ASIFT_API asift_status asift_views(asift_ctx *ctx, const uint8_t *d_img, int H, 
                          float *d_view_f32, uint8_t *d_view_u8, uint8_t *d_mask,
                          void *d_workspace, size_t ws_bytes, void *stream);
 
+/* asift_views_nearest -- the same views with the coarse stage's
+ * nearest-neighbour interpolation (Sec. III-B): canvas C(i, j) = the source
+ * pixel at floor(p + 1/2) per axis (Q32; 0 outside the same footprint), B as
+ * above, v = B at canvas column clamp(floor(X + 1/2), 0, Wr-1); quantisation,
+ * mask, layout, workspace and errors as asift_views. */
+ASIFT_API asift_status asift_views_nearest(asift_ctx *ctx, const uint8_t *d_img, int H, int W, int pitch,
+                         const asift_view_desc *h_views, int n_views, const int64_t *h_offsets,
+                         float *d_view_f32, uint8_t *d_view_u8, uint8_t *d_mask,
+                         void *d_workspace, size_t ws_bytes, void *stream);
+
 /*
  * orb_extract -- ORB on n_views views (ORB [23] as used in Sec. III-B).
  * Inputs: views as written by asift_views (d_view_u8 / d_mask at h_offsets).
@@ -272,6 +282,10 @@ ASIFT_API asift_status hamming_match_noalloc(const uint8_t *d_q, int nq, const i
                                              void *stream);
 
 /* View-set configuration of match_pair. */
+/* Interpolation of the simulated views. */
+#define ASIFT_INTERP_LANCZOS3 0
+#define ASIFT_INTERP_NEAREST 1
+
 typedef struct {
     int32_t kmax;           /* t = sqrt2^k, k = 0..kmax (default 5)             */
     int32_t ratio_num, ratio_den; /* ratio test (default 4/5)                   */
@@ -283,7 +297,9 @@ typedef struct {
                                asift_view_table_scaled(kmax, ds), image 2 (the
                                target) its single unwarped view; 0 = both images
                                the views of asift_view_table(kmax)             */
-    int32_t pad0;
+    int32_t interp;         /* ASIFT_INTERP_LANCZOS3 (default) or
+                               ASIFT_INTERP_NEAREST, the coarse stage's
+                               nearest-neighbour views (asift_views_nearest) */
     double ds;              /* scale step of the coarse stage (default 0.5)     */
 } asift_pair_cfg;
 

@@ -23,7 +23,7 @@ MAX_GAUSS = 48
 PATTERN_SEED = 250303479
 
 EXPORTED = ["asift_ctx_create", "asift_ctx_destroy", "asift_ctx_orb_cfg", "asift_ctx_pattern", "asift_view_table",
-            "asift_make_view", "asift_view_table_scaled", "asift_make_view_scaled", "asift_level_size", "asift_views_bytes", "asift_views_workspace_size", "asift_views",
+            "asift_make_view", "asift_view_table_scaled", "asift_make_view_scaled", "asift_level_size", "asift_views_bytes", "asift_views_workspace_size", "asift_views", "asift_views_nearest",
             "orb_workspace_size", "orb_extract", "hamming_workspace_size", "hamming_match",
             "match_pair_workspace_size", "match_pair", "match_pair_inspect", "match_pair_view_counts", "asift_read_status",
             "asift_launch_count", "asift_pattern_table", "asift_bin_table", "asift_profile_enable",
@@ -32,6 +32,7 @@ EXPORTED = ["asift_ctx_create", "asift_ctx_destroy", "asift_ctx_orb_cfg", "asift
             "asift_plan_autotune", "asift_plan_destroy", "asift_warp_shape_for", "asift_warp_workspace_size",
             "asift_warp_fwd", "asift_warp_bwd", "asift_ctx_set_match_engine", "asift_ctx_match_engine"]
 MATCH_AUTO, MATCH_CUDA_CORES, MATCH_TENSOR_CORES = 0, 1, 2
+INTERP_LANCZOS3, INTERP_NEAREST = 0, 1
 PROF_STAGES = ["upload", "warp", "pyramid", "detect", "select", "orient_brief", "match", "pairs"]
 
 
@@ -57,7 +58,7 @@ class OrbCfg(C.Structure):
 
 class PairCfg(C.Structure):
     _fields_ = [("kmax", C.c_int32), ("ratio_num", C.c_int32), ("ratio_den", C.c_int32), ("per_view", C.c_int32),
-                ("coarse", C.c_int32), ("pad0", C.c_int32), ("ds", C.c_double)]
+                ("coarse", C.c_int32), ("interp", C.c_int32), ("ds", C.c_double)]
 
 
 class PairDesc(C.Structure):
@@ -113,6 +114,7 @@ def load_library():
         "asift_views_bytes": (i64, [vp, i32]),
         "asift_views_workspace_size": (sz, [i32, i32, i32]),
         "asift_views": (i32, [vp, vp, i32, i32, i32, vp, i32, vp, vp, vp, vp, vp, sz, vp]),
+        "asift_views_nearest": (i32, [vp, vp, i32, i32, i32, vp, i32, vp, vp, vp, vp, vp, sz, vp]),
         "orb_workspace_size": (sz, [vp, vp, i32]),
         "orb_extract": (i32, [vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
         "hamming_workspace_size": (sz, [i32, i32]),
@@ -325,7 +327,7 @@ class Context:
         return st.value
 
     # -- asift_views
-    def views(self, img: torch.Tensor, views, with_f32: bool = False) -> ViewsOut:
+    def views(self, img: torch.Tensor, views, with_f32: bool = False, nearest: bool = False) -> ViewsOut:
         assert img.is_cuda and img.dtype == torch.uint8 and img.dim() == 2
         H, W = img.shape
         pitch = img.stride(0)
@@ -336,9 +338,10 @@ class Context:
         nbytes = self.L.asift_views_workspace_size(H, W, len(views))
         ws = self.workspace("views", nbytes)
         arr = _view_array(views)
-        _check("asift_views", self.L.asift_views(self._ctx, _ptr(img), H, W, pitch, arr, len(views),
-                                                 offs.ctypes.data_as(C.c_void_p), _ptr(f32), _ptr(u8), _ptr(mask),
-                                                 _ptr(ws), ws.numel(), _stream()))
+        fn = "asift_views_nearest" if nearest else "asift_views"
+        _check(fn, getattr(self.L, fn)(self._ctx, _ptr(img), H, W, pitch, arr, len(views),
+                                       offs.ctypes.data_as(C.c_void_p), _ptr(f32), _ptr(u8), _ptr(mask),
+                                       _ptr(ws), ws.numel(), _stream()))
         return ViewsOut(u8, mask, f32, offs, list(views))
 
     # -- orb_extract
@@ -384,10 +387,11 @@ class Context:
 
     # -- match_pair
     def pair_cfg(self, kmax: int = 5, num: int = 4, den: int = 5, per_view: bool = False, coarse: bool = False,
-                 ds: float = 0.5) -> PairCfg:
+                 ds: float = 0.5, nearest: bool = False) -> PairCfg:
         """coarse=True: image 1 takes the (t, phi, s) parameter groups with s = 1 + k ds, image 2 the
-        identity view only (the coarse stage of Sec. 3)."""
-        return PairCfg(kmax, num, den, int(per_view), int(coarse), 0, float(ds))
+        identity view only (the coarse stage of Sec. 3); nearest=True: nearest-neighbour views."""
+        return PairCfg(kmax, num, den, int(per_view), int(coarse), INTERP_NEAREST if nearest else INTERP_LANCZOS3,
+                       float(ds))
 
     @staticmethod
     def pair_views(shape, pc: PairCfg, image: int) -> list:
@@ -401,7 +405,8 @@ class Context:
         n = self.L.match_pair_workspace_size(self._ctx, shape1[0], shape1[1], shape2[0], shape2[1], C.byref(pc))
         if n == 0:
             raise AsiftError("match_pair_workspace_size", ASIFT_ERR_ARG)
-        return self.workspace(("pair", tuple(shape1), tuple(shape2), pc.kmax, pc.per_view, pc.coarse, pc.ds), n)
+        return self.workspace(("pair", tuple(shape1), tuple(shape2), pc.kmax, pc.per_view, pc.coarse, pc.ds,
+                               pc.interp), n)
 
     def match_pair(self, img1: torch.Tensor, img2: torch.Tensor, pc: PairCfg, out: torch.Tensor | None = None,
                    n_out: torch.Tensor | None = None, ws: torch.Tensor | None = None):
@@ -475,7 +480,7 @@ class Plan:
             assert a.is_cuda and a.dtype == torch.uint8 and b.is_cuda and b.dtype == torch.uint8
             arr[i] = PairDesc(a.data_ptr(), a.shape[0], a.shape[1], a.stride(0),
                               b.data_ptr(), b.shape[0], b.shape[1], b.stride(0))
-        pc = PairCfg(kmax, num, den, 0, 0, 0, 0.5)
+        pc = PairCfg(kmax, num, den, 0, 0, INTERP_LANCZOS3, 0.5)
         tn = Tuning(**tuning) if tuning else None
         self._p = C.c_void_p()
         torch.cuda.synchronize()

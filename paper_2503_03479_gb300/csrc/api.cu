@@ -500,10 +500,10 @@ size_t asift_views_workspace_size(int H, int W, int n_views)
     return views_layout(nullptr, H, W, n_views, per_view * std::max(n_views, 1), &s, &t, &f, &g);
 }
 
-asift_status asift_views(asift_ctx *ctx, const uint8_t *d_img, int H, int W, int pitch,
-                         const asift_view_desc *h_views, int n_views, const int64_t *h_offsets,
-                         float *d_view_f32, uint8_t *d_view_u8, uint8_t *d_mask, void *d_workspace,
-                         size_t ws_bytes, void *stream)
+static asift_status views_impl(asift_ctx *ctx, const uint8_t *d_img, int H, int W, int pitch,
+                               const asift_view_desc *h_views, int n_views, const int64_t *h_offsets,
+                               float *d_view_f32, uint8_t *d_view_u8, uint8_t *d_mask, void *d_workspace,
+                               size_t ws_bytes, void *stream, bool nearest)
 {
     if (!ctx || !d_img || H < 1 || W < 1 || pitch < W || n_views < 0 || (n_views && (!h_views || !h_offsets)) ||
         !d_view_u8 || !d_mask || !d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255))
@@ -524,9 +524,31 @@ asift_status asift_views(asift_ctx *ctx, const uint8_t *d_img, int H, int W, int
     build_views(h_views, n_views, srcs.data(), pitches.data(), h_offsets, false, filt, dv, &n_tiles, &cwm, &hpm, &wvm);
     cudaError_t e = upload(ctx, tab, dv.data(), sizeof(DevView) * n_views, s);
     if (e == cudaSuccess) e = launch_u8_to_f32(d_img, pitch, W, H, src, src_pitch_of(W), s);
+    if (nearest) {
+        if (e == cudaSuccess) e = launch_warp_nn(tab, n_views, n_tiles, cwm, d_view_u8, d_mask, d_view_f32, s);
+        return cuda_status(e);
+    }
     if (e == cudaSuccess) e = launch_tilt_filter(tab, n_views, wvm, s);
     if (e == cudaSuccess) e = launch_warp(tab, n_views, n_tiles, cwm, hpm, d_view_u8, d_mask, d_view_f32, s);
     return cuda_status(e);
+}
+
+asift_status asift_views(asift_ctx *ctx, const uint8_t *d_img, int H, int W, int pitch,
+                         const asift_view_desc *h_views, int n_views, const int64_t *h_offsets,
+                         float *d_view_f32, uint8_t *d_view_u8, uint8_t *d_mask, void *d_workspace,
+                         size_t ws_bytes, void *stream)
+{
+    return views_impl(ctx, d_img, H, W, pitch, h_views, n_views, h_offsets, d_view_f32, d_view_u8, d_mask,
+                      d_workspace, ws_bytes, stream, false);
+}
+
+asift_status asift_views_nearest(asift_ctx *ctx, const uint8_t *d_img, int H, int W, int pitch,
+                                 const asift_view_desc *h_views, int n_views, const int64_t *h_offsets,
+                                 float *d_view_f32, uint8_t *d_view_u8, uint8_t *d_mask, void *d_workspace,
+                                 size_t ws_bytes, void *stream)
+{
+    return views_impl(ctx, d_img, H, W, pitch, h_views, n_views, h_offsets, d_view_f32, d_view_u8, d_mask,
+                      d_workspace, ws_bytes, stream, true);
 }
 
 }  // extern "C"
@@ -812,7 +834,7 @@ struct Pipeline {
 struct PairKey {
     const uint8_t *img1, *img2;
     int H1, W1, pitch1, H2, W2, pitch2;
-    int32_t kmax, ratio_num, ratio_den, per_view, coarse;
+    int32_t kmax, ratio_num, ratio_den, per_view, coarse, interp;
     double ds;
     asift_pair_match *out;
     int cap;
@@ -822,7 +844,8 @@ struct PairKey {
     {
         return img1 == o.img1 && img2 == o.img2 && H1 == o.H1 && W1 == o.W1 && pitch1 == o.pitch1 && H2 == o.H2 &&
                W2 == o.W2 && pitch2 == o.pitch2 && kmax == o.kmax && ratio_num == o.ratio_num &&
-               ratio_den == o.ratio_den && per_view == o.per_view && coarse == o.coarse && ds == o.ds && out == o.out &&
+               ratio_den == o.ratio_den && per_view == o.per_view && coarse == o.coarse && interp == o.interp && ds == o.ds &&
+               out == o.out &&
                cap == o.cap && d_n == o.d_n && ws == o.ws;
     }
 };
@@ -854,7 +877,8 @@ static int pair_views(const PairSpec &p, const asift_pair_cfg &pc, int image, as
 static bool pair_cfg_ok(const asift_pair_cfg &pc)
 {
     return pc.kmax >= 0 && pc.kmax <= 7 && pc.ratio_den >= 1 && pc.ratio_num >= 0 && (pc.coarse == 0 || pc.coarse == 1) &&
-           (!pc.coarse || (pc.ds >= 0.0 && pc.ds <= 2.0));
+           (!pc.coarse || (pc.ds >= 0.0 && pc.ds <= 2.0)) &&
+           (pc.interp == ASIFT_INTERP_LANCZOS3 || pc.interp == ASIFT_INTERP_NEAREST);
 }
 
 static bool pipeline_layout(const asift_ctx *ctx, const PairSpec *ps, int P, const asift_pair_cfg &pc, bool per_view,
@@ -994,14 +1018,24 @@ static cudaError_t pipeline_run(asift_ctx *ctx, const Pipeline &L, const asift_p
     cudaError_t e = launch_convert_images(L.conv, 2 * P, L.max_px, s);
     prof_mark(ctx, 1, s);
     if (e == cudaSuccess) {
+        const bool nearest = pc.interp == ASIFT_INTERP_NEAREST;
         if (!per_view) {
-            e = launch_tilt_filter(L.dv, L.nv, L.max_wv, s);
-            if (e == cudaSuccess)
-                e = launch_warp(L.dv, L.nv, L.n_tiles, L.cw_max, L.hp_max, L.o.arena_u8, L.o.arena_mask, nullptr, s,
-                                tune ? tune->warp_grid : 0);
+            if (nearest) {
+                e = launch_warp_nn(L.dv, L.nv, L.n_tiles, L.cw_max, L.o.arena_u8, L.o.arena_mask, nullptr, s,
+                                   tune ? tune->warp_grid : 0);
+            } else {
+                e = launch_tilt_filter(L.dv, L.nv, L.max_wv, s);
+                if (e == cudaSuccess)
+                    e = launch_warp(L.dv, L.nv, L.n_tiles, L.cw_max, L.hp_max, L.o.arena_u8, L.o.arena_mask, nullptr,
+                                    s, tune ? tune->warp_grid : 0);
+            }
         } else {
             for (int v = 0; v < L.nv && e == cudaSuccess; ++v) {
                 const int tiles = L.h_dv[v].ntx * ((L.views[v].Hv + kWarpTH - 1) / kWarpTH);
+                if (nearest) {
+                    e = launch_warp_nn(L.dv + v, 1, tiles, L.cw_max, L.o.arena_u8, L.o.arena_mask, nullptr, s);
+                    continue;
+                }
                 e = launch_tilt_filter(L.dv + v, 1, L.views[v].Wv, s);
                 if (e == cudaSuccess)
                     e = launch_warp(L.dv + v, 1, tiles, L.cw_max, L.hp_max, L.o.arena_u8, L.o.arena_mask, nullptr, s);
@@ -1036,7 +1070,7 @@ extern "C" {
 
 static asift_pair_cfg pair_cfg_or_default(const asift_pair_cfg *c)
 {
-    asift_pair_cfg d{5, 4, 5, 0, 0, 0, 0.5};
+    asift_pair_cfg d{5, 4, 5, 0, 0, ASIFT_INTERP_LANCZOS3, 0.5};
     return c ? *c : d;
 }
 
@@ -1062,7 +1096,7 @@ asift_status match_pair(asift_ctx *ctx, const uint8_t *d_img1, int H1, int W1, i
         return ASIFT_ERR_ARG;
     const bool per_view = pc.per_view != 0;
     const PairKey key{d_img1, d_img2, H1, W1, pitch1, H2, W2, pitch2, pc.kmax, pc.ratio_num, pc.ratio_den,
-                      pc.per_view, pc.coarse, pc.ds, d_out, cap, d_n, d_workspace};
+                      pc.per_view, pc.coarse, pc.interp, pc.ds, d_out, cap, d_n, d_workspace};
     if (!ctx->pair_cache) ctx->pair_cache = new (std::nothrow) PairCache;
     if (!ctx->pair_cache) return ASIFT_ERR_NOMEM;
     PairCache &C = *ctx->pair_cache;

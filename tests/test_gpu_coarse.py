@@ -50,6 +50,44 @@ def test_scaled_warp_parity(A):
         assert (du[~near_tie] == 0).all() and (du <= 1).all(), i
 
 
+@pytest.mark.parametrize("H,W,kmax,ds", [(101, 143, 3, 0.5), (157, 201, 6, 0.0), (64, 80, 2, 1.0)])
+def test_nearest_warp_parity(A, H, W, kmax, ds):
+    """asift_views_nearest against the oracle's nearest-neighbour views: fp32
+    within 1e-4 of full scale (the only rounding is the Gaussian's fp32 sum),
+    the mask bit-exact, u8 equal except at rounding ties."""
+    ctx = A.Context()
+    img = synth.texture(H, W, 40 + kmax)
+    views = A.view_table(H, W, kmax, ds) + [A.make_view(H, W, t, phi, s) for t, phi, s in
+                                             ((1.0, 37.0, 1.0), (2.6, 33.0, 2.75), (7.9, 151.0, 1.0))]
+    vo = ctx.views(torch.from_numpy(img).cuda(), views, with_f32=True, nearest=True)
+    torch.cuda.synchronize()
+    for i, v in enumerate(views):
+        ref = O.warp_view_nn(img, _oracle_view(v))
+        f = vo.view(i, "f32").cpu().numpy().astype(np.float64)
+        assert f.shape == ref.f64.shape
+        assert np.abs(f - ref.f64).max() <= WARP_TOL, i
+        if v.K == 0:
+            assert np.array_equal(f, ref.f64), i       # no arithmetic: the pixels themselves
+        assert np.array_equal(vo.view(i, "mask").cpu().numpy(), ref.mask), i
+        du = np.abs(vo.view(i, "u8").cpu().numpy().astype(int) - ref.u8.astype(int))
+        near_tie = np.abs(np.abs(ref.f64 - np.floor(ref.f64)) - 0.5) < 3e-3
+        assert (du[~near_tie] == 0).all() and (du <= 1).all(), i
+
+
+def test_nearest_per_view_and_batched_forms_agree(A):
+    ctx = A.Context(n_levels=4, n_features=300)
+    p = synth.pair_affine_small(seed=1005)
+    t1, t2 = torch.from_numpy(p.img1).cuda(), torch.from_numpy(p.img2).cuda()
+    got = []
+    for per_view in (False, True):
+        pc = ctx.pair_cfg(kmax=2, per_view=per_view, coarse=True, nearest=True)
+        out, n, ws = ctx.match_pair(t1, t2, pc)
+        torch.cuda.synchronize()
+        assert ctx.read_status(ws) == 0
+        got.append(ctx.pairs_host(out, n).tobytes())
+    assert got[0] == got[1] and len(got[0]) > 0
+
+
 def test_scaled_orb_parity(A):
     L, N = 4, 300
     ctx = A.Context(n_levels=L, n_features=N)
@@ -74,8 +112,8 @@ def test_scaled_orb_parity(A):
     assert total > 1000
 
 
-def _coarse_run(A, ctx, img1, img2, kmax, ds):
-    pc = ctx.pair_cfg(kmax=kmax, coarse=True, ds=ds)
+def _coarse_run(A, ctx, img1, img2, kmax, ds, nearest=False):
+    pc = ctx.pair_cfg(kmax=kmax, coarse=True, ds=ds, nearest=nearest)
     t1, t2 = torch.from_numpy(img1).cuda(), torch.from_numpy(img2).cuda()
     out, n, ws = ctx.match_pair(t1, t2, pc)
     counts, best = ctx.view_counts(img1.shape, img2.shape, pc, ws)
@@ -84,17 +122,18 @@ def _coarse_run(A, ctx, img1, img2, kmax, ds):
     return pc, ctx.pairs_host(out, n), ws, counts.cpu().numpy(), int(best.item())
 
 
-@pytest.mark.parametrize("kmax,ds", [(2, 0.5), (3, 0.25), (0, 0.5)])
-def test_coarse_counts_and_argmax_equal_oracle(A, kmax, ds):
+@pytest.mark.parametrize("kmax,ds,nearest", [(2, 0.5, False), (3, 0.25, False), (0, 0.5, False), (2, 0.5, True),
+                                             (3, 0.5, True)])
+def test_coarse_counts_and_argmax_equal_oracle(A, kmax, ds, nearest):
     L, N = 4, 400
     ctx = A.Context(n_levels=L, n_features=N)
     p = synth.pair_affine_small(seed=1003)
-    pc, pairs, ws, counts, best = _coarse_run(A, ctx, p.img1, p.img2, kmax, ds)
+    pc, pairs, ws, counts, best = _coarse_run(A, ctx, p.img1, p.img2, kmax, ds, nearest)
     views1 = A.view_table(*p.img1.shape, kmax, ds)
     assert len(counts) == len(views1)
     kp1, d1, kp2, d2, m = ctx.inspect_pair(p.img1.shape, p.img2.shape, pc, ws)
     # image 1's pool is the scaled views' ORB, image 2's the single identity view
-    vo = ctx.views(torch.from_numpy(p.img1).cuda(), views1)
+    vo = ctx.views(torch.from_numpy(p.img1).cuda(), views1, nearest=nearest)
     rk1, rd1, _, _ = ctx.orb_extract(vo).host()
     assert np.array_equal(kp1, rk1) and np.array_equal(d1, rd1)
     assert (kp2["view"] == len(views1)).all()
@@ -121,16 +160,18 @@ def test_coarse_counts_and_argmax_equal_oracle(A, kmax, ds):
         assert abs(r["x1"] - x1) < 1e-3 and abs(r["y1"] - y1) < 1e-3
 
 
-def test_coarse_finds_the_simulated_view(A):
+@pytest.mark.parametrize("nearest", [False, True])
+def test_coarse_finds_the_simulated_view(A, nearest):
     """A target that is exactly one parameter group's simulated view of the
     reference (made by the oracle) draws the most matches to that group."""
     L, N, kmax, ds = 4, 400, 2, 0.5
     ctx = A.Context(n_levels=L, n_features=N)
     img1 = synth.texture(150, 190, 33)
     table = O.view_table_scaled(150, 190, kmax, ds)
+    warp = O.warp_view_nn if nearest else O.warp_view
     for star in (3, 7):
-        img2 = np.ascontiguousarray(O.warp_view(img1, table[star]).u8)
-        _, pairs, _, counts, best = _coarse_run(A, ctx, img1, img2, kmax, ds)
+        img2 = np.ascontiguousarray(warp(img1, table[star]).u8)
+        _, pairs, _, counts, best = _coarse_run(A, ctx, img1, img2, kmax, ds, nearest)
         assert best == star, (star, counts.tolist())
         assert counts[star] > 2 * np.delete(counts, star).max()
 
