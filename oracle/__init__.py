@@ -113,6 +113,18 @@ def lib():
         L.oracle_match.argtypes = [u8p, C.c_int, u8p, C.c_int, C.c_int, C.c_int, i32p, i32p, i32p, u8p]
         L.oracle_match.restype = C.c_int
         L.oracle_sizeof_dview.restype = C.c_int
+        f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+        u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+        L.oracle_dedup.argtypes = [f32p, f32p, f32p, f32p, C.c_int, u8p]
+        L.oracle_dedup.restype = C.c_int
+        L.oracle_reproj_sq.argtypes = [f64p, C.c_double, C.c_double, C.c_double, C.c_double]
+        L.oracle_reproj_sq.restype = C.c_double
+        L.oracle_precision_count.argtypes = [f32p, f32p, f32p, f32p, C.c_int, f64p, C.c_double]
+        L.oracle_precision_count.restype = C.c_int
+        L.oracle_homography4.argtypes = [f64p, f64p, f64p, f64p, f64p]
+        L.oracle_homography4.restype = C.c_int
+        L.oracle_ransac.argtypes = [f32p, f32p, f32p, f32p, C.c_int, u32p, C.c_int, C.c_double, i32p, f64p, u8p]
+        L.oracle_ransac.restype = C.c_int
         assert L.oracle_sizeof_dview() == C.sizeof(ODView)
         L.oracle_dwarp_fwd.argtypes = [f64p, P(ODView), f64p]
         L.oracle_dwarp_vjp.argtypes = [f64p, P(ODView), f64p, f64p, f64p]
@@ -424,3 +436,65 @@ def dwarp_vjp(u: np.ndarray, v: ODView, vbar: np.ndarray):
     pb = np.zeros(4, np.float64)
     lib().oracle_dwarp_vjp(u, C.byref(v), vbar, ub, pb)
     return ub, pb
+
+
+# ---------------------------------------------------------------- evaluation on the accepted pairs
+def _xy(pairs):
+    """(x1, y1, x2, y2) float32 arrays of a pair list (structured array with those fields,
+    or an (n, 4) array)."""
+    if getattr(pairs, "dtype", None) is not None and pairs.dtype.names:
+        cols = [pairs[f] for f in ("x1", "y1", "x2", "y2")]
+    else:
+        a = np.asarray(pairs, dtype=np.float32).reshape(-1, 4)
+        cols = [a[:, k] for k in range(4)]
+    return [np.ascontiguousarray(c, dtype=np.float32) for c in cols]
+
+
+def dedup(pairs) -> np.ndarray:
+    """Keep mask: a pair is kept iff no earlier pair has the same nearest pixels
+    of (x1, y1, x2, y2) (duplicate correspondences from several views)."""
+    x1, y1, x2, y2 = _xy(pairs)
+    keep = np.zeros(len(x1), np.uint8)
+    lib().oracle_dedup(x1, y1, x2, y2, len(x1), keep)
+    return keep.astype(bool)
+
+
+def reproj_sq(H: np.ndarray, x: float, y: float, u: float, v: float) -> float:
+    return lib().oracle_reproj_sq(np.ascontiguousarray(H, np.float64).reshape(9), x, y, u, v)
+
+
+def precision_count(pairs, H: np.ndarray, th_sq: float = 3.0) -> int:
+    """Eq. (6): pairs within sqrt(th_sq) of the true mapping (R_Num of Eq. (5))."""
+    x1, y1, x2, y2 = _xy(pairs)
+    return lib().oracle_precision_count(x1, y1, x2, y2, len(x1), np.ascontiguousarray(H, np.float64).reshape(9),
+                                        th_sq)
+
+
+def homography4(src: np.ndarray, dst: np.ndarray):
+    """H (3x3, h8 = 1) from 4 correspondences src[k] -> dst[k], or None when degenerate."""
+    src, dst = np.asarray(src, np.float64), np.asarray(dst, np.float64)
+    H = np.zeros(9)
+    ok = lib().oracle_homography4(np.ascontiguousarray(src[:, 0]), np.ascontiguousarray(src[:, 1]),
+                                  np.ascontiguousarray(dst[:, 0]), np.ascontiguousarray(dst[:, 1]), H)
+    return H.reshape(3, 3) if ok else None
+
+
+@dataclass
+class RansacOut:
+    best: int
+    counts: np.ndarray      # int32 per hypothesis (-1: repeated pair or degenerate fit)
+    Hs: np.ndarray          # (n_hyp, 9)
+    inlier: np.ndarray      # bool per pair
+
+
+def ransac(pairs, rnd: np.ndarray, th_sq: float = 9.0) -> RansacOut:
+    """RANSAC [28] with the random numbers given: rnd is uint32 (n_hyp, 4)."""
+    x1, y1, x2, y2 = _xy(pairs)
+    rnd = np.ascontiguousarray(rnd, dtype=np.uint32).reshape(-1, 4)
+    n_hyp = len(rnd)
+    counts = np.zeros(n_hyp, np.int32)
+    Hs = np.zeros(9 * n_hyp)
+    inl = np.zeros(len(x1), np.uint8)
+    best = lib().oracle_ransac(x1, y1, x2, y2, len(x1), rnd.reshape(-1), n_hyp, th_sq, counts, Hs, inl)
+    return RansacOut(best, counts, Hs.reshape(n_hyp, 9), inl.astype(bool))
+

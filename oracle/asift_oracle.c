@@ -23,6 +23,7 @@
  *   Sec. III-B     ORB (oFAST + rBRIEF) coarse extraction, brute-force Hamming matcher
  *   Sec. IV-C      nearest / second-nearest distance ratio test
  *   Sec. III-B     nearest-neighbour interpolation and scale s of the coarse stage
+ *   Eq. (5)-(7)    precision, reprojection threshold, inlier ratio; RANSAC [28] (Sec. III-C)
  * ORB internals the paper does not state (pyramid, FAST-9, Harris, centroid
  * orientation, steered BRIEF) follow the ORB paper cited as [23]; where that is
  * silent, the reading chosen is stated at each function.
@@ -1052,3 +1053,146 @@ void oracle_dwarp_vjp(const double *u, const oracle_dview *v, const double *vbar
 }
 
 int oracle_sizeof_dview(void) { return (int)sizeof(oracle_dview); }
+
+/* ------------------------------------------------------------------------ */
+/* Evaluation on the accepted pairs: duplicate removal, precision (Eq. (5),  */
+/* (6)), homography by RANSAC [28] and the inlier ratio (Eq. (7))            */
+/* ------------------------------------------------------------------------ */
+/* The accepted pairs come as four fp32 coordinate arrays (image 1 point x1,
+ * y1; image 2 point x2, y2), back-projected to the original images.  Every
+ * floating-point step below is a single IEEE operation in the order written
+ * (compiled without contraction). */
+
+/* Nearest integer pixel of an fp32 coordinate, floor(x + 1/2) in fp32. */
+static int32_t pix_of(float x) { return (int32_t)floorf(x + 0.5f); }
+
+/* Duplicate removal in original coordinates: pair i is kept iff no earlier
+ * pair has the same four nearest pixels (x1, y1, x2, y2); keep[i] = 0/1.
+ * Several views can detect the same physical correspondence, and the
+ * evaluation counts each once.  Returns the number kept. */
+int oracle_dedup(const float *x1, const float *y1, const float *x2, const float *y2, int n, uint8_t *keep)
+{
+    int kept = 0;
+    for (int i = 0; i < n; ++i) {
+        int dup = 0;
+        for (int j = 0; j < i && !dup; ++j)
+            dup = pix_of(x1[i]) == pix_of(x1[j]) && pix_of(y1[i]) == pix_of(y1[j]) &&
+                  pix_of(x2[i]) == pix_of(x2[j]) && pix_of(y2[i]) == pix_of(y2[j]);
+        keep[i] = (uint8_t)!dup;
+        kept += !dup;
+    }
+    return kept;
+}
+
+/* Squared distance between H (x, y) and (u, v) (Eq. (6) before the root):
+ * (x', y') = (h0 x + h1 y + h2, h3 x + h4 y + h5) / (h6 x + h7 y + h8). */
+double oracle_reproj_sq(const double H[9], double x, double y, double u, double v)
+{
+    const double X = H[0] * x + H[1] * y + H[2];
+    const double Y = H[3] * x + H[4] * y + H[5];
+    const double Z = H[6] * x + H[7] * y + H[8];
+    const double dx = X / Z - u, dy = Y / Z - v;
+    return dx * dx + dy * dy;
+}
+
+/* Eq. (6): number of pairs whose image-1 point, mapped by the true H,
+ * lands within sqrt(th_sq) of its matched image-2 point. */
+int oracle_precision_count(const float *x1, const float *y1, const float *x2, const float *y2, int n,
+                           const double H[9], double th_sq)
+{
+    int r = 0;
+    for (int i = 0; i < n; ++i) r += oracle_reproj_sq(H, x1[i], y1[i], x2[i], y2[i]) <= th_sq;
+    return r;
+}
+
+/* Homography from four correspondences (x_k, y_k) -> (u_k, v_k) with
+ * h8 = 1: the eight linear equations
+ *   h0 x + h1 y + h2 - h6 x u - h7 y u = u,  h3 x + h4 y + h5 - h6 x v - h7 y v = v
+ * solved by Gaussian elimination with partial pivoting (the first row with
+ * the largest |entry| in the column) and back substitution.  Returns 0 (and
+ * leaves H unspecified) when a pivot is at most 1e-10 times the largest
+ * |entry| of the system: collinear or coincident points. */
+int oracle_homography4(const double *x, const double *y, const double *u, const double *v, double H[9])
+{
+    double A[8][9];
+    for (int k = 0; k < 4; ++k) {
+        double *r0 = A[2 * k], *r1 = A[2 * k + 1];
+        r0[0] = x[k]; r0[1] = y[k]; r0[2] = 1.0; r0[3] = 0.0; r0[4] = 0.0; r0[5] = 0.0;
+        r0[6] = -(x[k] * u[k]); r0[7] = -(y[k] * u[k]); r0[8] = u[k];
+        r1[0] = 0.0; r1[1] = 0.0; r1[2] = 0.0; r1[3] = x[k]; r1[4] = y[k]; r1[5] = 1.0;
+        r1[6] = -(x[k] * v[k]); r1[7] = -(y[k] * v[k]); r1[8] = v[k];
+    }
+    double amax = 0.0;
+    for (int r = 0; r < 8; ++r)
+        for (int c = 0; c < 8; ++c) amax = fmax(amax, fabs(A[r][c]));
+    for (int k = 0; k < 8; ++k) {
+        int p = k;
+        for (int r = k + 1; r < 8; ++r)
+            if (fabs(A[r][k]) > fabs(A[p][k])) p = r;
+        if (!(fabs(A[p][k]) > 1e-10 * amax)) return 0;
+        if (p != k)
+            for (int c = 0; c < 9; ++c) {
+                const double tmp = A[k][c];
+                A[k][c] = A[p][c];
+                A[p][c] = tmp;
+            }
+        for (int r = k + 1; r < 8; ++r) {
+            const double f = A[r][k] / A[k][k];
+            for (int c = k + 1; c < 9; ++c) A[r][c] = A[r][c] - f * A[k][c];
+            A[r][k] = 0.0;
+        }
+    }
+    double h[8];
+    for (int k = 7; k >= 0; --k) {
+        double s = A[k][8];
+        for (int c = k + 1; c < 8; ++c) s = s - A[k][c] * h[c];
+        h[k] = s / A[k][k];
+    }
+    for (int k = 0; k < 8; ++k) {
+        if (!isfinite(h[k])) return 0;
+        H[k] = h[k];
+    }
+    H[8] = 1.0;
+    return 1;
+}
+
+/* RANSAC [28] for the homography from image 1 to image 2 over n pairs.
+ * Hypothesis h draws the four pairs rnd[4h + k] mod n (k = 0..3; the random
+ * numbers are inputs), fits H by oracle_homography4 and counts the pairs with
+ * squared reprojection error <= th_sq.  counts[h] = -1 for a hypothesis with
+ * a repeated pair or a degenerate fit; Hs[9h ..] holds each fit.  The best
+ * hypothesis has the largest count, the lowest h among equal counts; its
+ * inliers are marked in inlier[] (Eq. (7): In_Num = their number).  Returns
+ * the best h, or -1 when no hypothesis fits (n < 4 included). */
+int oracle_ransac(const float *x1, const float *y1, const float *x2, const float *y2, int n, const uint32_t *rnd,
+                  int n_hyp, double th_sq, int32_t *counts, double *Hs, uint8_t *inlier)
+{
+    int best = -1;
+    for (int h = 0; h < n_hyp; ++h) {
+        counts[h] = -1;
+        for (int c = 0; c < 9; ++c) Hs[9 * h + c] = 0.0;
+        if (n < 4) continue;
+        int idx[4];
+        for (int k = 0; k < 4; ++k) idx[k] = (int)(rnd[4 * h + k] % (uint32_t)n);
+        int distinct = 1;
+        for (int a = 0; a < 4; ++a)
+            for (int b = a + 1; b < 4; ++b) distinct &= idx[a] != idx[b];
+        if (!distinct) continue;
+        double xs[4], ys[4], us[4], vs[4];
+        for (int k = 0; k < 4; ++k) {
+            xs[k] = x1[idx[k]];
+            ys[k] = y1[idx[k]];
+            us[k] = x2[idx[k]];
+            vs[k] = y2[idx[k]];
+        }
+        if (!oracle_homography4(xs, ys, us, vs, Hs + 9 * h)) {
+            for (int c = 0; c < 9; ++c) Hs[9 * h + c] = 0.0;
+            continue;
+        }
+        counts[h] = oracle_precision_count(x1, y1, x2, y2, n, Hs + 9 * h, th_sq);
+        if (best < 0 || counts[h] > counts[best]) best = h;
+    }
+    for (int i = 0; i < n; ++i)
+        inlier[i] = (uint8_t)(best >= 0 && oracle_reproj_sq(Hs + 9 * best, x1[i], y1[i], x2[i], y2[i]) <= th_sq);
+    return best;
+}

@@ -787,3 +787,126 @@ def test_nn_constant_image_stays_constant_inside():
         deep = (px > r) & (px < v.W - 1 - r) & (py > r) & (py < v.H - 1 - r)
         assert deep.sum() > 50
         assert np.abs(o.f64[deep] - 181).max() < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Evaluation on the accepted pairs: duplicates, Eq. (5)-(7), RANSAC [28]
+# --------------------------------------------------------------------------
+def _random_h(rng):
+    return np.array([[1 + rng.uniform(-0.2, 0.2), rng.uniform(-0.2, 0.2), rng.uniform(-20, 20)],
+                     [rng.uniform(-0.2, 0.2), 1 + rng.uniform(-0.2, 0.2), rng.uniform(-20, 20)],
+                     [rng.uniform(-3e-4, 3e-4), rng.uniform(-3e-4, 3e-4), 1.0]])
+
+
+def _apply_h(H, pts):
+    p = np.c_[pts, np.ones(len(pts))] @ H.T
+    return p[:, :2] / p[:, 2:]
+
+
+def test_dedup_keeps_the_first_of_each_pixel_quadruple():
+    """Base pairs at distinct pixel quadruples; copies jittered inside the same
+    pixels (|jitter| < 0.45) are duplicates of the earliest one."""
+    rng = np.random.default_rng(70)
+    base = rng.integers(0, 500, size=(60, 4)).astype(np.float64)
+    base[:, 0] = np.arange(60) * 7          # distinct quadruples
+    rows, want = [], []
+    seen = set()
+    for _ in range(400):
+        b = int(rng.integers(0, 60))
+        rows.append(base[b] + rng.uniform(-0.45, 0.45, 4))
+        want.append(b not in seen)
+        seen.add(b)
+    keep = O.dedup(np.array(rows, np.float32))
+    assert np.array_equal(keep, np.array(want))
+    # a copy one pixel away in any coordinate is not a duplicate
+    for k in range(4):
+        r = np.array([base[0], base[0]], np.float32)
+        r[1, k] += 1.0
+        assert O.dedup(r).tolist() == [True, True]
+    # the nearest pixel of a half-way coordinate is the upper one: 2.5 -> 3, -0.5 -> 0
+    assert O.dedup(np.array([[2.5, 0, 0, 0], [3.4, 0, 0, 0]], np.float32)).tolist() == [True, False]
+    assert O.dedup(np.array([[-0.5, 0, 0, 0], [0.49, 0, 0, 0]], np.float32)).tolist() == [True, False]
+
+
+def test_precision_counts_pairs_by_planted_distance():
+    """x2 = H(x1) + d (cos a, sin a) with d planted on either side of sqrt(3)."""
+    rng = np.random.default_rng(71)
+    H = _random_h(rng)
+    p1 = rng.uniform(0, 800, size=(500, 2))
+    d = np.where(rng.random(500) < 0.6, rng.uniform(0, np.sqrt(3) - 0.01, 500), rng.uniform(np.sqrt(3) + 0.01, 9, 500))
+    a = rng.uniform(0, 2 * np.pi, 500)
+    p2 = _apply_h(H, p1) + np.c_[d * np.cos(a), d * np.sin(a)]
+    pairs = np.c_[p1, p2].astype(np.float32)
+    # the fp32 storage moves the points by < 1e-4 px, far inside the 0.01 margin
+    assert O.precision_count(pairs, H, 3.0) == int((d <= np.sqrt(3)).sum())
+    assert O.precision_count(pairs, H, 0.0) == 0
+    assert O.precision_count(pairs, H, 1e6) == 500
+    # the identity on identical points: every pair, distance exactly 0
+    same = np.c_[p1, p1].astype(np.float32)
+    assert O.precision_count(same, np.eye(3), 0.0) == 500
+
+
+def test_homography4_recovers_a_known_homography():
+    rng = np.random.default_rng(72)
+    for _ in range(50):
+        H = _random_h(rng)
+        src = rng.uniform(0, 1000, size=(4, 2))
+        dst = _apply_h(H, src)
+        G = O.homography4(src, dst)
+        assert G is not None
+        assert np.abs(G / G[2, 2] - H / H[2, 2]).max() < 1e-7
+        # the order of the four correspondences does not matter
+        perm = rng.permutation(4)
+        G2 = O.homography4(src[perm], dst[perm])
+        assert np.abs(G2 - G).max() < 1e-7 * np.abs(G).max()
+
+
+def test_homography4_rejects_degenerate_samples():
+    src = np.array([[0, 0], [10, 10], [20, 20], [5, 40.0]])       # three collinear
+    assert O.homography4(src, src * 2) is None
+    src = np.array([[0, 0], [0, 0], [20, 5], [5, 40.0]])          # coincident
+    assert O.homography4(src, src + 3) is None
+
+
+def _ransac_set(rng, n=300, frac=0.7, noise=0.5):
+    H = _random_h(rng)
+    p1 = rng.uniform(0, 900, size=(n, 2))
+    inl = rng.random(n) < frac
+    noise = rng.uniform(-noise, noise, size=(n, 2))
+    far = rng.uniform(20, 200, n)[:, None] * np.c_[np.cos(a := rng.uniform(0, 6.3, n)), np.sin(a)]
+    p2 = _apply_h(H, p1) + np.where(inl[:, None], noise, far)
+    return H, np.c_[p1, p2].astype(np.float32), inl
+
+
+def test_ransac_finds_the_planted_inliers():
+    rng = np.random.default_rng(73)
+    H, pairs, inl = _ransac_set(rng)
+    rnd = rng.integers(0, 2 ** 32, size=(256, 4), dtype=np.uint64).astype(np.uint32)
+    r = O.ransac(pairs, rnd, th_sq=9.0)
+    assert r.best >= 0
+    assert np.array_equal(r.inlier, inl)
+    assert r.counts[r.best] == inl.sum() == r.counts.max()
+    # Eq. (7): In_Num / Pt_Num
+    assert abs(r.inlier.sum() / len(pairs) - inl.mean()) == 0
+    Hb = r.Hs[r.best].reshape(3, 3)
+    q = rng.uniform(100, 800, size=(20, 2))
+    assert np.abs(_apply_h(Hb, q) - _apply_h(H, q)).max() < 3.0
+
+
+def test_ransac_sampling_ties_and_degenerate_draws():
+    rng = np.random.default_rng(74)
+    H, pairs, inl = _ransac_set(rng, n=40, frac=1.0, noise=0.0)     # every fit is exact: all counts tie
+    n = len(pairs)
+    rnd = np.array([[1, 2, 3, 3],                 # repeated pair: no hypothesis
+                    [5 + n, 9, 13 + 2 * n, 21],   # indices taken mod n
+                    [9, 21, 5, 13],               # the same four pairs: the same count, later index
+                    [0, 1, 2, 3],
+                    [n - 1, 0, 5, 6],             # n - 1 is a pair of its own (not 0 again)
+                    [2 * n, 0, 5, 6]], np.uint32) # 2n is pair 0 again
+    r = O.ransac(pairs, rnd, th_sq=9.0)
+    assert r.counts[0] == -1 and r.counts[5] == -1
+    assert r.counts[1] == r.counts[2] == r.counts[3] == r.counts[4] == n
+    assert r.best == 1                            # the lowest hypothesis among equal counts
+    # fewer than four pairs: nothing to fit
+    r = O.ransac(pairs[:3], rnd, th_sq=9.0)
+    assert r.best == -1 and (r.counts == -1).all() and not r.inlier.any()
