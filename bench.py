@@ -690,6 +690,33 @@ def run_ours(args):
             coarse[name] = line
             del wsc, outc
 
+    # ---- evaluation of the accepted pairs (Sec. III-C, Sec. IV-B): duplicate
+    # removal, Eq. (5)-(6) precision against the pair's true homography, RANSAC
+    # with 1024 hypotheses and the Eq. (7) inlier ratio
+    evaluation = None
+    if args.eval_hyp > 0:
+        gen = np.random.default_rng(6000 + rank)
+        rnd = torch.from_numpy(gen.integers(0, 2 ** 32, size=(args.eval_hyp, 4), dtype=np.uint64)
+                               .astype(np.uint32).view(np.int32)).cuda()
+        evaluation = {"hypotheses": args.eval_hyp, "ransac_threshold_px": 3.0, "precision_threshold_px": "sqrt(3)",
+                      "pairs": []}
+        for i in range(n_pairs):
+            step(i)
+            for _ in range(2):
+                ctx.eval_pairs(out, n_out, H_true=pairs[i].H12, rnd=rnd)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 10
+            e0.record(stream)
+            for _ in range(reps):
+                _, _, _, res = ctx.eval_pairs(out, n_out, H_true=pairs[i].H12, rnd=rnd)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            r = ctx.eval_result(res)
+            evaluation["pairs"].append({
+                "accepted": r.n_pairs, "unique": r.n_unique, "precision": r.r_num / max(r.n_unique, 1),
+                "inlier_ratio": r.n_inliers / max(r.n_unique, 1), "ms": e0.elapsed_time(e1) / reps})
+
     # ---- end to end through the C ABI with host buffers
     h1 = [torch.from_numpy(p.img1).pin_memory() for p in pairs]
     h2 = [torch.from_numpy(p.img2).pin_memory() for p in pairs]
@@ -736,6 +763,7 @@ def run_ours(args):
                 "large_batched": large,
                 "differentiable": diff,
                 "coarse_stage": coarse,
+                "evaluation": evaluation,
                 "roofline": roofline, "rooflines": rooflines, "match_engine": ctx.match_engine,
                 "match_engines": engines,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
@@ -759,6 +787,7 @@ def main():
     ap.add_argument("--large-pairs", type=int, default=8, help="pairs in the 4096x3072 batched run (0: skip)")
     ap.add_argument("--diff-views", type=int, default=256, help="views of the differentiable-warp timing (0: skip)")
     ap.add_argument("--coarse-steps", type=int, default=20, help="steps of the coarse-stage timing (0: skip)")
+    ap.add_argument("--eval-hyp", type=int, default=1024, help="RANSAC hypotheses of the evaluation timing (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -418,6 +418,52 @@ ASIFT_API asift_status match_pair_view_counts(asift_ctx *ctx, int H1, int W1, in
                                               const asift_pair_cfg *cfg, void *d_workspace, int32_t *d_counts,
                                               int n_counts, int32_t *d_best, void *stream);
 
+/*
+ * Evaluation of the accepted pairs of a match_pair call (Sec. III-C, Sec. IV-B):
+ *   1. duplicate removal in original coordinates: pair i is dropped when an
+ *      earlier pair has the same nearest pixels floor(c + 1/2) (fp32) of all
+ *      four coordinates (x1, y1, x2, y2) -- several views can detect the same
+ *      correspondence; the kept pairs are written, in order, to d_unique;
+ *   2. precision (Eq. (5)-(6)): with a true homography h_H_true (host, 9
+ *      doubles, row-major, image 1 -> image 2), r_num = the kept pairs with
+ *      |H (x1, y1) - (x2, y2)|^2 <= th_sq (th_sq = 3 for the paper's sqrt 3);
+ *      precision = r_num / n_unique;
+ *   3. RANSAC [28]: hypothesis h fits a homography (h8 = 1, Gaussian
+ *      elimination with partial pivoting on the eight DLT equations) to the
+ *      kept pairs d_rnd[4h + k] mod n_unique (k = 0..3; d_rnd: device uint32,
+ *      4 n_hyp, the caller's random numbers); a repeated pair or a pivot at
+ *      most 1e-10 times the system's largest |entry| leaves it out (count -1);
+ *      its count is the kept pairs with squared reprojection error <=
+ *      ransac_th_sq; the best has the largest count, the lowest h on ties;
+ *   4. inliers (Eq. (7)): d_inlier[i] (cap bytes, may be NULL) = kept pair i
+ *      is within the threshold of the best H; n_inliers = their number,
+ *      inlier ratio = n_inliers / n_unique.
+ * Every fp64 step is one correctly rounded operation in the order written
+ * above (reprojection: ((h0 x + h1 y) + h2) / ((h6 x + h7 y) + h8) - x2, ...).
+ * d_pairs / d_n: match_pair's output (count clamped to cap).  d_hyp_counts
+ * (n_hyp int32, may be NULL) receives the per-hypothesis counts.  Results go
+ * to the device struct d_result, in stream order.  Workspace:
+ * asift_eval_workspace_size(cap, n_hyp) bytes, 256-byte aligned.
+ * Errors: ASIFT_ERR_ARG for NULL or misaligned buffers, cap outside
+ * [0, 2^26], n_hyp outside [0, 2^20] or negative thresholds.
+ */
+typedef struct {
+    int32_t n_pairs;        /* accepted pairs read: min(*d_n, cap)               */
+    int32_t n_unique;       /* Pt_Num: pairs left after duplicate removal        */
+    int32_t r_num;          /* R_Num of Eq. (5)-(6); -1 without a true H         */
+    int32_t best_hyp;       /* best RANSAC hypothesis; -1 if none fits           */
+    int32_t n_inliers;      /* In_Num of Eq. (7)                                 */
+    int32_t status;         /* ASIFT_OK (ASIFT_ERR_CAPACITY: table overflow)     */
+    double ransac_th_sq;    /* the squared RANSAC threshold used                 */
+    double H[9];            /* the best hypothesis, row-major; zeros if none     */
+} asift_eval_result;
+ASIFT_API size_t asift_eval_workspace_size(int cap, int n_hyp);
+ASIFT_API asift_status asift_eval_pairs(asift_ctx *ctx, const asift_pair_match *d_pairs, const int32_t *d_n, int cap,
+                                        const double *h_H_true, double th_sq, const uint32_t *d_rnd, int n_hyp,
+                                        double ransac_th_sq, asift_pair_match *d_unique, uint8_t *d_inlier,
+                                        int32_t *d_hyp_counts, asift_eval_result *d_result, void *d_workspace,
+                                        size_t ws_bytes, void *stream);
+
 /* Synchronises `stream` and copies the status word at the start of a
  * workspace to *h_status (ASIFT_OK, ASIFT_ERR_CAPACITY or ASIFT_ERR_TIMEOUT);
  * clears it when clear != 0. */

@@ -25,7 +25,8 @@ PATTERN_SEED = 250303479
 EXPORTED = ["asift_ctx_create", "asift_ctx_destroy", "asift_ctx_orb_cfg", "asift_ctx_pattern", "asift_view_table",
             "asift_make_view", "asift_view_table_scaled", "asift_make_view_scaled", "asift_level_size", "asift_views_bytes", "asift_views_workspace_size", "asift_views", "asift_views_nearest",
             "orb_workspace_size", "orb_extract", "hamming_workspace_size", "hamming_match",
-            "match_pair_workspace_size", "match_pair", "match_pair_inspect", "match_pair_view_counts", "asift_read_status",
+            "match_pair_workspace_size", "match_pair", "match_pair_inspect", "match_pair_view_counts", "asift_eval_workspace_size",
+            "asift_eval_pairs", "asift_read_status",
             "asift_launch_count", "asift_pattern_table", "asift_bin_table", "asift_profile_enable",
             "asift_profile_read", "hamming_match_noalloc", "asift_plan_create", "asift_plan_run",
             "asift_plan_pairs", "asift_plan_workspace", "asift_plan_set_tuning", "asift_plan_get_tuning",
@@ -59,6 +60,12 @@ class OrbCfg(C.Structure):
 class PairCfg(C.Structure):
     _fields_ = [("kmax", C.c_int32), ("ratio_num", C.c_int32), ("ratio_den", C.c_int32), ("per_view", C.c_int32),
                 ("coarse", C.c_int32), ("interp", C.c_int32), ("ds", C.c_double)]
+
+
+class EvalResult(C.Structure):
+    _fields_ = [("n_pairs", C.c_int32), ("n_unique", C.c_int32), ("r_num", C.c_int32), ("best_hyp", C.c_int32),
+                ("n_inliers", C.c_int32), ("status", C.c_int32), ("ransac_th_sq", C.c_double),
+                ("H", C.c_double * 9)]
 
 
 class PairDesc(C.Structure):
@@ -123,6 +130,9 @@ def load_library():
         "match_pair": (i32, [vp, vp, i32, i32, i32, vp, i32, i32, i32, P(PairCfg), vp, i32, vp, vp, sz, vp]),
         "match_pair_inspect": (i32, [vp, i32, i32, i32, i32, P(PairCfg), vp, vp, vp, vp, vp, vp, vp, vp]),
         "match_pair_view_counts": (i32, [vp, i32, i32, i32, i32, P(PairCfg), vp, vp, i32, vp, vp]),
+        "asift_eval_workspace_size": (sz, [i32, i32]),
+        "asift_eval_pairs": (i32, [vp, vp, vp, i32, vp, C.c_double, vp, i32, C.c_double, vp, vp, vp, vp, vp, sz,
+                                   vp]),
         "asift_read_status": (i32, [vp, i32, P(C.c_int32), vp]),
         "asift_launch_count": (i64, []),
         "asift_pattern_table": (i32, [C.c_uint64, vp]),
@@ -431,6 +441,38 @@ class Context:
         n = int(n_out.item())
         cap = out.numel() // PAIR_DTYPE.itemsize
         return out[: min(n, cap) * PAIR_DTYPE.itemsize].cpu().numpy().view(PAIR_DTYPE)
+
+    def eval_pairs(self, out: torch.Tensor, n_out: torch.Tensor, H_true=None, th_sq: float = 3.0,
+                   rnd: torch.Tensor | None = None, ransac_th_sq: float = 9.0, counts: bool = False):
+        """Duplicate removal, Eq. (5)-(6) precision count against H_true (3x3, image 1 -> 2), RANSAC
+        over rnd (device int32 (n_hyp, 4), read as uint32) and the Eq. (7) inliers, on match_pair's
+        output.  Returns (unique pairs, inlier mask, per-hypothesis counts or None, result bytes);
+        read the result with eval_result()."""
+        cap = out.numel() // PAIR_DTYPE.itemsize
+        n_hyp = 0 if rnd is None else rnd.shape[0]
+        nbytes = self.L.asift_eval_workspace_size(cap, n_hyp)
+        if nbytes == 0:
+            raise AsiftError("asift_eval_workspace_size", ASIFT_ERR_ARG)
+        ws = self.workspace(("eval", cap, n_hyp), nbytes)
+        dev = out.device
+        unique = torch.empty(max(cap, 1) * PAIR_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        inl = torch.empty(max(cap, 1), dtype=torch.uint8, device=dev)
+        cnt = torch.empty(max(n_hyp, 1), dtype=torch.int32, device=dev) if counts else None
+        res = torch.empty(C.sizeof(EvalResult), dtype=torch.uint8, device=dev)
+        Hh = None
+        if H_true is not None:
+            Hh = (C.c_double * 9)(*[float(x) for x in np.asarray(H_true, dtype=np.float64).reshape(9)])
+        _check("asift_eval_pairs",
+               self.L.asift_eval_pairs(self._ctx, _ptr(out), _ptr(n_out), cap, Hh, float(th_sq),
+                                       _ptr(rnd) if rnd is not None else None, n_hyp, float(ransac_th_sq),
+                                       _ptr(unique), _ptr(inl), _ptr(cnt) if cnt is not None else None, _ptr(res),
+                                       _ptr(ws), ws.numel(), _stream()))
+        return unique, inl, cnt, res
+
+    @staticmethod
+    def eval_result(res: torch.Tensor) -> EvalResult:
+        b = res.cpu().numpy().tobytes()
+        return EvalResult.from_buffer_copy(b)
 
     def view_counts(self, shape1, shape2, pc: PairCfg, ws: torch.Tensor):
         """Accepted matches per image-1 view of the last match_pair on ws, and the

@@ -1151,6 +1151,27 @@ asift_status match_pair_inspect(const asift_ctx *ctx, int H1, int W1, int H2, in
     return ASIFT_OK;
 }
 
+size_t asift_eval_workspace_size(int cap, int n_hyp)
+{
+    if (cap < 0 || cap > (1 << 26) || n_hyp < 0 || n_hyp > (1 << 20)) return 0;
+    return eval_workspace_bytes(cap, n_hyp);
+}
+
+asift_status asift_eval_pairs(asift_ctx *ctx, const asift_pair_match *d_pairs, const int32_t *d_n, int cap,
+                              const double *h_H_true, double th_sq, const uint32_t *d_rnd, int n_hyp,
+                              double ransac_th_sq, asift_pair_match *d_unique, uint8_t *d_inlier,
+                              int32_t *d_hyp_counts, asift_eval_result *d_result, void *d_workspace, size_t ws_bytes,
+                              void *stream)
+{
+    if (!ctx || !d_n || !d_result || !d_workspace || cap < 0 || cap > (1 << 26) || n_hyp < 0 || n_hyp > (1 << 20) ||
+        (cap > 0 && (!d_pairs || !d_unique)) || (n_hyp > 0 && !d_rnd) || !(th_sq >= 0.0) ||
+        !(ransac_th_sq >= 0.0) || (reinterpret_cast<uintptr_t>(d_workspace) & 255) ||
+        ws_bytes < eval_workspace_bytes(cap, n_hyp))
+        return ASIFT_ERR_ARG;
+    return cuda_status(launch_eval(d_pairs, d_n, cap, h_H_true, th_sq, d_rnd, n_hyp, ransac_th_sq, d_unique, d_inlier,
+                                   d_hyp_counts, d_result, d_workspace, static_cast<cudaStream_t>(stream)));
+}
+
 asift_status match_pair_view_counts(asift_ctx *ctx, int H1, int W1, int H2, int W2, const asift_pair_cfg *cfg,
                                     void *d_workspace, int32_t *d_counts, int n_counts, int32_t *d_best, void *stream)
 {

@@ -67,6 +67,12 @@ cudaError_t launch_hamming_noalloc(const uint8_t *q, int nq, const int32_t *d_nq
                                    int32_t *n_acc, cudaStream_t s);
 cudaError_t launch_pairs(const MatchProblem *d_probs, int n_probs, const MatchProblem &single, int total_blk,
                          int32_t *block_count, const DevView *views, int32_t *status, cudaStream_t s);
+// eval.cu
+size_t eval_workspace_bytes(int cap, int n_hyp);
+cudaError_t launch_eval(const asift_pair_match *d_pairs, const int32_t *d_n, int cap, const double *h_H_true,
+                        double th_sq, const uint32_t *d_rnd, int n_hyp, double ransac_th_sq,
+                        asift_pair_match *d_unique, uint8_t *d_inlier, int32_t *d_hyp_counts,
+                        asift_eval_result *d_res, void *d_ws, cudaStream_t s);
 int view_count_max_views();
 cudaError_t launch_view_counts(const asift_keypoint *kp, const uint8_t *accept, const int32_t *d_nq, int nq_cap,
                                int view0, int n_views, int32_t *counts, int32_t *best, cudaStream_t s);
