@@ -247,7 +247,7 @@ __device__ bool homography4(const double *x, const double *y, const double *u, c
     return true;
 }
 
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(32)
 ransac_fit_kernel(const asift_pair_match *__restrict__ up, const uint32_t *__restrict__ rnd, int n_hyp,
                   double *__restrict__ Hs, int32_t *__restrict__ counts, const asift_eval_result *__restrict__ res)
 {
@@ -279,7 +279,7 @@ ransac_fit_kernel(const asift_pair_match *__restrict__ up, const uint32_t *__res
 
 __global__ void __launch_bounds__(kEvalBlock)
 ransac_count_kernel(const asift_pair_match *__restrict__ up, int n_hyp, const double *__restrict__ Hs,
-                    int32_t *__restrict__ counts, int chunk, const asift_eval_result *__restrict__ res)
+                    int32_t *__restrict__ counts, const asift_eval_result *__restrict__ res)
 {
     __shared__ double sH[kHypPerCta][9];
     __shared__ int sv[kHypPerCta];
@@ -294,11 +294,11 @@ ransac_count_kernel(const asift_pair_match *__restrict__ up, int n_hyp, const do
     }
     __syncthreads();
     const int n = res->n_unique;
-    const int i0 = blockIdx.y * chunk, i1 = min(n, i0 + chunk);
     int c[kHypPerCta];
 #pragma unroll
     for (int k = 0; k < kHypPerCta; ++k) c[k] = 0;
-    for (int i = i0 + (int)threadIdx.x; i < i1; i += blockDim.x) {
+    // the CTAs of one hypothesis group stride over the kept pairs together
+    for (int i = blockIdx.y * blockDim.x + threadIdx.x; i < n; i += gridDim.y * blockDim.x) {
         const asift_pair_match p = up[i];
         const double x = p.x1, y = p.y1, u = p.x2, v = p.y2;
 #pragma unroll
@@ -438,13 +438,12 @@ cudaError_t launch_eval(const asift_pair_match *d_pairs, const int32_t *d_n, int
         note_launch();
     }
     if (n_hyp > 0) {
-        ransac_fit_kernel<<<(n_hyp + 127) / 128, 128, 0, s>>>(d_unique, d_rnd, n_hyp, Hs, counts, d_res);
-        // pairs per CTA: enough CTAs to fill the GPU a few times over
+        ransac_fit_kernel<<<(n_hyp + 31) / 32, 32, 0, s>>>(d_unique, d_rnd, n_hyp, Hs, counts, d_res);
+        // hypothesis groups x CTAs per group: about two CTAs per SM, no more
+        // CTAs per group than the capacity's blocks of pairs
         const int hyp_blocks = (n_hyp + kHypPerCta - 1) / kHypPerCta;
-        const int want_y = std::max(1, (4 * 152 + hyp_blocks - 1) / hyp_blocks);
-        const int chunk = std::max(kEvalBlock, (cap + want_y - 1) / want_y);
-        const int gy = std::max(1, (cap + chunk - 1) / chunk);
-        ransac_count_kernel<<<dim3(hyp_blocks, gy), kEvalBlock, 0, s>>>(d_unique, n_hyp, Hs, counts, chunk, d_res);
+        const int gy = std::max(1, std::min((2 * 152 + hyp_blocks - 1) / hyp_blocks, blocks));
+        ransac_count_kernel<<<dim3(hyp_blocks, gy), kEvalBlock, 0, s>>>(d_unique, n_hyp, Hs, counts, d_res);
         ransac_best_kernel<<<1, kEvalBlock, 0, s>>>(counts, n_hyp, Hs, d_res);
         note_launch(3);
     }
