@@ -85,6 +85,12 @@ def lib():
         L.oracle_warp_view.argtypes = [u8p, C.c_int, P(OView), C.c_void_p, C.c_void_p, C.c_void_p]
         L.oracle_warp_view_f64.argtypes = [f64p, C.c_int, P(OView), C.c_void_p, C.c_void_p, C.c_void_p]
         L.oracle_warp_view_nn.argtypes = [u8p, C.c_int, P(OView), C.c_void_p, C.c_void_p, C.c_void_p]
+        L.oracle_lanczos.argtypes = [C.c_double, C.c_int]
+        L.oracle_lanczos.restype = C.c_double
+        L.oracle_lanczos_weights.argtypes = [C.c_double, C.c_int, f64p]
+        L.oracle_warp_view_lanczos.argtypes = [u8p, C.c_int, P(OView), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.oracle_warp_view_lanczos_f64.argtypes = [f64p, C.c_int, P(OView), C.c_int, C.c_void_p, C.c_void_p,
+                                                   C.c_void_p]
         L.oracle_warp_view_nn_f64.argtypes = [f64p, C.c_int, P(OView), C.c_void_p, C.c_void_p, C.c_void_p]
         L.oracle_make_view.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, P(OView)]
         L.oracle_make_view_scaled.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, P(OView)]
@@ -218,6 +224,36 @@ def warp_view_nn(u: np.ndarray, v: OView) -> ViewOut:
     else:
         u = np.ascontiguousarray(u, dtype=np.float64)
         lib().oracle_warp_view_nn_f64(u, W, C.byref(v), f.ctypes.data, b.ctypes.data, m.ctypes.data)
+    return ViewOut(f, b, m)
+
+
+def lanczos(x: float, a: int) -> float:
+    """Eq. (4): L(x; a)."""
+    return lib().oracle_lanczos(float(x), int(a))
+
+
+def lanczos_weights(f: float, a: int) -> np.ndarray:
+    """Normalised Eq. (3) weights of taps floor(p) - a + 1 .. floor(p) + a."""
+    w = np.zeros(2 * a)
+    lib().oracle_lanczos_weights(float(f), int(a), w)
+    return w
+
+
+def warp_view_lanczos(u: np.ndarray, v: OView, a: int) -> ViewOut:
+    """The view with Lanczos-a resampling (a = 4: the precise stage's 8 x 8
+    reproduction of the best view, Sec. III-C)."""
+    assert 1 <= a <= 8
+    H, W = u.shape
+    assert (H, W) == (v.H, v.W)
+    f = np.zeros((v.Hv, v.Wv), dtype=np.float64)
+    b = np.zeros((v.Hv, v.Wv), dtype=np.uint8)
+    m = np.zeros((v.Hv, v.Wv), dtype=np.uint8)
+    if u.dtype == np.uint8:
+        u = np.ascontiguousarray(u)
+        lib().oracle_warp_view_lanczos(u, W, C.byref(v), a, f.ctypes.data, b.ctypes.data, m.ctypes.data)
+    else:
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        lib().oracle_warp_view_lanczos_f64(u, W, C.byref(v), a, f.ctypes.data, b.ctypes.data, m.ctypes.data)
     return ViewOut(f, b, m)
 
 

@@ -24,6 +24,7 @@
  *   Sec. IV-C      nearest / second-nearest distance ratio test
  *   Sec. III-B     nearest-neighbour interpolation and scale s of the coarse stage
  *   Eq. (5)-(7)    precision, reprojection threshold, inlier ratio; RANSAC [28] (Sec. III-C)
+ *   Sec. III-C     Lanczos reproduction of the best view with n = 4 (8 x 8 window)
  * ORB internals the paper does not state (pyramid, FAST-9, Harris, centroid
  * orientation, steered BRIEF) follow the ORB paper cited as [23]; where that is
  * silent, the reading chosen is stated at each function.
@@ -374,6 +375,98 @@ void oracle_warp_view_nn(const uint8_t *u, int pitch, const oracle_view *v,
     for (int y = 0; y < v->H; ++y)
         for (int x = 0; x < v->W; ++x) d[(size_t)y * v->W + x] = (double)u[(size_t)y * pitch + x];
     oracle_warp_view_nn_f64(d, v->W, v, out_f64, out_u8, out_mask);
+    free(d);
+}
+
+/* Lanczos-a views for the precise stage's reproduction of the best view
+ * (Sec. III-C: Lanczos with n = 4, an 8 x 8 window): Eq. (3)-(4) with a
+ * general a, otherwise the view of oracle_warp_view_f64 (same geometry,
+ * background, Gaussian, quantisation and mask). */
+double oracle_lanczos(double x, int a)
+{
+    if (!(fabs(x) < (double)a)) return 0.0;
+    return sinc(x) * sinc(x / (double)a);
+}
+
+/* Normalised weights of taps floor(p) + m, m = -a+1 .. a (2a taps), at
+ * fractional part f in [0, 1). */
+void oracle_lanczos_weights(double f, int a, double *w)
+{
+    double sum = 0.0;
+    for (int m = -a + 1; m <= a; ++m) {
+        w[m + a - 1] = oracle_lanczos(f - (double)m, a);
+        sum += w[m + a - 1];
+    }
+    for (int i = 0; i < 2 * a; ++i) w[i] /= sum;
+}
+
+static double canvas_value_a(const double *u, int pitch, const oracle_view *v, int i, int jrow, int a)
+{
+    int64_t px, py;
+    canvas_to_src(v, i, jrow, &px, &py);
+    const int64_t half = 2147483648LL;
+    if (px < -half || px >= (int64_t)(2 * v->W - 1) * half) return 0.0;
+    if (py < -half || py >= (int64_t)(2 * v->H - 1) * half) return 0.0;
+    int x0 = (int)q32_floor(px), y0 = (int)q32_floor(py);
+    double wx[16], wy[16];
+    oracle_lanczos_weights(q32_frac(px), a, wx);
+    oracle_lanczos_weights(q32_frac(py), a, wy);
+    double acc = 0.0;
+    for (int n = -a + 1; n <= a; ++n) {
+        int yy = clampi(y0 + n, 0, v->H - 1);
+        double row = 0.0;
+        for (int m = -a + 1; m <= a; ++m) {
+            int xx = clampi(x0 + m, 0, v->W - 1);
+            row += wx[m + a - 1] * u[(size_t)yy * pitch + xx];
+        }
+        acc += wy[n + a - 1] * row;
+    }
+    return acc;
+}
+
+/* a in [1, 8]. */
+void oracle_warp_view_lanczos_f64(const double *u, int pitch, const oracle_view *v, int a,
+                                  double *out_f64, uint8_t *out_u8, uint8_t *out_mask)
+{
+    const int Wr = v->Wr, Hr = v->Hr, Wv = v->Wv, K = v->K;
+    double g[128];
+    oracle_gauss_taps(v->sigma, K, g);
+    double *Crow = (double *)malloc(sizeof(double) * (size_t)Wr);
+    double *B = (double *)malloc(sizeof(double) * (size_t)Wr);
+    for (int j = 0; j < Hr; ++j) {
+        for (int i = 0; i < Wr; ++i) Crow[i] = canvas_value_a(u, pitch, v, i, j, a);
+        for (int i = 0; i < Wr; ++i) {
+            double acc = 0.0;
+            for (int k = -K; k <= K; ++k) acc += g[abs(k)] * Crow[clampi(i - k, 0, Wr - 1)];
+            B[i] = acc;
+        }
+        for (int x = 0; x < Wv; ++x) {
+            int64_t X = v->tq * (2 * (int64_t)x - Wv + 1) + (int64_t)(Wr - 1) * (int64_t)2147483648LL;
+            int x0 = (int)q32_floor(X);
+            double w[16];
+            oracle_lanczos_weights(q32_frac(X), a, w);
+            double acc = 0.0;
+            for (int m = -a + 1; m <= a; ++m) acc += w[m + a - 1] * B[clampi(x0 + m, 0, Wr - 1)];
+            size_t o = (size_t)j * Wv + x;
+            if (out_f64) out_f64[o] = acc;
+            if (out_u8) {
+                double r = nearbyint(acc);
+                out_u8[o] = (uint8_t)(r < 0.0 ? 0.0 : (r > 255.0 ? 255.0 : r));
+            }
+            if (out_mask) out_mask[o] = (uint8_t)(canvas_valid(v, x0, j) && canvas_valid(v, x0 + 1, j));
+        }
+    }
+    free(Crow);
+    free(B);
+}
+
+void oracle_warp_view_lanczos(const uint8_t *u, int pitch, const oracle_view *v, int a,
+                              double *out_f64, uint8_t *out_u8, uint8_t *out_mask)
+{
+    double *d = (double *)malloc(sizeof(double) * (size_t)v->W * v->H);
+    for (int y = 0; y < v->H; ++y)
+        for (int x = 0; x < v->W; ++x) d[(size_t)y * v->W + x] = (double)u[(size_t)y * pitch + x];
+    oracle_warp_view_lanczos_f64(d, v->W, v, a, out_f64, out_u8, out_mask);
     free(d);
 }
 
