@@ -682,6 +682,19 @@ def run_ours(args):
                     "view_pixels": int(px), "stage_ms": stc, "best": best_of}
             if nearest:
                 line["warp_gpix_per_s"] = px / (stc["warp"] / 1e3) / 1e9
+                # the precise stage's Lanczos-4 (8 x 8) reproduction of pair 0's best group (Sec. III-C)
+                bv = [vc[best_of[0]["view"]]]
+                for _ in range(2):
+                    ctx.views(d1[0], bv, lanczos=4)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(10):
+                    ctx.views(d1[0], bv, lanczos=4)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                line["precise_lanczos4_view"] = {"ms": e0.elapsed_time(e1) / 10, "pixels": bv[0].Wv * bv[0].Hv,
+                                                 "canvas_pixels": bv[0].Wr * bv[0].Hr}
             else:
                 f_clk = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
                 flops = sum(warp_flops(v) for v in vc)     # the target's identity view costs no arithmetic

@@ -188,6 +188,17 @@ ASIFT_API asift_status asift_views_nearest(asift_ctx *ctx, const uint8_t *d_img,
                          float *d_view_f32, uint8_t *d_view_u8, uint8_t *d_mask,
                          void *d_workspace, size_t ws_bytes, void *stream);
 
+/* asift_views_lanczos -- the same views with Lanczos-a resampling, a = 4 for
+ * the precise stage's reproduction of the best view (Sec. III-C: an 8 x 8
+ * window) or a = 3: Eq. (3)-(4) with 2a normalised taps per axis for the
+ * rotation and 2a taps for the tilt, otherwise as asift_views (geometry,
+ * background, Gaussian, quantisation, mask, layout, workspace, errors; a
+ * outside {3, 4} is ASIFT_ERR_ARG). */
+ASIFT_API asift_status asift_views_lanczos(asift_ctx *ctx, int a, const uint8_t *d_img, int H, int W, int pitch,
+                                           const asift_view_desc *h_views, int n_views, const int64_t *h_offsets,
+                                           float *d_view_f32, uint8_t *d_view_u8, uint8_t *d_mask,
+                                           void *d_workspace, size_t ws_bytes, void *stream);
+
 /*
  * orb_extract -- ORB on n_views views (ORB [23] as used in Sec. III-B).
  * Inputs: views as written by asift_views (d_view_u8 / d_mask at h_offsets).

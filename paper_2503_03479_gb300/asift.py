@@ -23,7 +23,7 @@ MAX_GAUSS = 48
 PATTERN_SEED = 250303479
 
 EXPORTED = ["asift_ctx_create", "asift_ctx_destroy", "asift_ctx_orb_cfg", "asift_ctx_pattern", "asift_view_table",
-            "asift_make_view", "asift_view_table_scaled", "asift_make_view_scaled", "asift_level_size", "asift_views_bytes", "asift_views_workspace_size", "asift_views", "asift_views_nearest",
+            "asift_make_view", "asift_view_table_scaled", "asift_make_view_scaled", "asift_level_size", "asift_views_bytes", "asift_views_workspace_size", "asift_views", "asift_views_nearest", "asift_views_lanczos",
             "orb_workspace_size", "orb_extract", "hamming_workspace_size", "hamming_match",
             "match_pair_workspace_size", "match_pair", "match_pair_inspect", "match_pair_view_counts", "asift_eval_workspace_size",
             "asift_eval_pairs", "asift_read_status",
@@ -122,6 +122,7 @@ def load_library():
         "asift_views_workspace_size": (sz, [i32, i32, i32]),
         "asift_views": (i32, [vp, vp, i32, i32, i32, vp, i32, vp, vp, vp, vp, vp, sz, vp]),
         "asift_views_nearest": (i32, [vp, vp, i32, i32, i32, vp, i32, vp, vp, vp, vp, vp, sz, vp]),
+        "asift_views_lanczos": (i32, [vp, i32, vp, i32, i32, i32, vp, i32, vp, vp, vp, vp, vp, sz, vp]),
         "orb_workspace_size": (sz, [vp, vp, i32]),
         "orb_extract": (i32, [vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
         "hamming_workspace_size": (sz, [i32, i32]),
@@ -337,7 +338,10 @@ class Context:
         return st.value
 
     # -- asift_views
-    def views(self, img: torch.Tensor, views, with_f32: bool = False, nearest: bool = False) -> ViewsOut:
+    def views(self, img: torch.Tensor, views, with_f32: bool = False, nearest: bool = False,
+              lanczos: int | None = None) -> ViewsOut:
+        """The views of one uint8 image: Lanczos-3 (default), nearest=True for the coarse stage's
+        nearest-neighbour views, lanczos=a (3 or 4) for the precise stage's Lanczos-a kernel."""
         assert img.is_cuda and img.dtype == torch.uint8 and img.dim() == 2
         H, W = img.shape
         pitch = img.stride(0)
@@ -348,10 +352,13 @@ class Context:
         nbytes = self.L.asift_views_workspace_size(H, W, len(views))
         ws = self.workspace("views", nbytes)
         arr = _view_array(views)
-        fn = "asift_views_nearest" if nearest else "asift_views"
-        _check(fn, getattr(self.L, fn)(self._ctx, _ptr(img), H, W, pitch, arr, len(views),
-                                       offs.ctypes.data_as(C.c_void_p), _ptr(f32), _ptr(u8), _ptr(mask),
-                                       _ptr(ws), ws.numel(), _stream()))
+        rest = (_ptr(img), H, W, pitch, arr, len(views), offs.ctypes.data_as(C.c_void_p), _ptr(f32), _ptr(u8),
+                _ptr(mask), _ptr(ws), ws.numel(), _stream())
+        if lanczos is not None:
+            _check("asift_views_lanczos", self.L.asift_views_lanczos(self._ctx, int(lanczos), *rest))
+        else:
+            fn = "asift_views_nearest" if nearest else "asift_views"
+            _check(fn, getattr(self.L, fn)(self._ctx, *rest))
         return ViewsOut(u8, mask, f32, offs, list(views))
 
     # -- orb_extract

@@ -503,7 +503,7 @@ size_t asift_views_workspace_size(int H, int W, int n_views)
 static asift_status views_impl(asift_ctx *ctx, const uint8_t *d_img, int H, int W, int pitch,
                                const asift_view_desc *h_views, int n_views, const int64_t *h_offsets,
                                float *d_view_f32, uint8_t *d_view_u8, uint8_t *d_mask, void *d_workspace,
-                               size_t ws_bytes, void *stream, bool nearest)
+                               size_t ws_bytes, void *stream, int interp)
 {
     if (!ctx || !d_img || H < 1 || W < 1 || pitch < W || n_views < 0 || (n_views && (!h_views || !h_offsets)) ||
         !d_view_u8 || !d_mask || !d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255))
@@ -524,8 +524,15 @@ static asift_status views_impl(asift_ctx *ctx, const uint8_t *d_img, int H, int 
     build_views(h_views, n_views, srcs.data(), pitches.data(), h_offsets, false, filt, dv, &n_tiles, &cwm, &hpm, &wvm);
     cudaError_t e = upload(ctx, tab, dv.data(), sizeof(DevView) * n_views, s);
     if (e == cudaSuccess) e = launch_u8_to_f32(d_img, pitch, W, H, src, src_pitch_of(W), s);
-    if (nearest) {
+    if (interp == ASIFT_INTERP_NEAREST) {
         if (e == cudaSuccess) e = launch_warp_nn(tab, n_views, n_tiles, cwm, d_view_u8, d_mask, d_view_f32, s);
+        return cuda_status(e);
+    }
+    if (interp == 3 || interp == 4) {       // Lanczos-a, the precise stage's kernel
+        int lzw = 1;
+        for (int v = 0; v < n_views; ++v) lzw = std::max(lzw, warp_lz_strip_width(h_views[v], dv[v].tw, interp));
+        if (e == cudaSuccess)
+            e = launch_warp_lanczos(interp, tab, n_views, n_tiles, lzw, d_view_u8, d_mask, d_view_f32, s);
         return cuda_status(e);
     }
     if (e == cudaSuccess) e = launch_tilt_filter(tab, n_views, wvm, s);
@@ -539,7 +546,7 @@ asift_status asift_views(asift_ctx *ctx, const uint8_t *d_img, int H, int W, int
                          size_t ws_bytes, void *stream)
 {
     return views_impl(ctx, d_img, H, W, pitch, h_views, n_views, h_offsets, d_view_f32, d_view_u8, d_mask,
-                      d_workspace, ws_bytes, stream, false);
+                      d_workspace, ws_bytes, stream, ASIFT_INTERP_LANCZOS3);
 }
 
 asift_status asift_views_nearest(asift_ctx *ctx, const uint8_t *d_img, int H, int W, int pitch,
@@ -548,7 +555,17 @@ asift_status asift_views_nearest(asift_ctx *ctx, const uint8_t *d_img, int H, in
                                  size_t ws_bytes, void *stream)
 {
     return views_impl(ctx, d_img, H, W, pitch, h_views, n_views, h_offsets, d_view_f32, d_view_u8, d_mask,
-                      d_workspace, ws_bytes, stream, true);
+                      d_workspace, ws_bytes, stream, ASIFT_INTERP_NEAREST);
+}
+
+asift_status asift_views_lanczos(asift_ctx *ctx, int a, const uint8_t *d_img, int H, int W, int pitch,
+                                 const asift_view_desc *h_views, int n_views, const int64_t *h_offsets,
+                                 float *d_view_f32, uint8_t *d_view_u8, uint8_t *d_mask, void *d_workspace,
+                                 size_t ws_bytes, void *stream)
+{
+    if (a != 3 && a != 4) return ASIFT_ERR_ARG;
+    return views_impl(ctx, d_img, H, W, pitch, h_views, n_views, h_offsets, d_view_f32, d_view_u8, d_mask,
+                      d_workspace, ws_bytes, stream, a);
 }
 
 }  // extern "C"

@@ -26,6 +26,10 @@ cudaError_t launch_tilt_filter(const DevView *d_views, int n_views, int max_wv, 
 cudaError_t launch_warp(const DevView *d_views, int n_views, int n_tiles, int cw_max, int hp_max, uint8_t *u8,
                         uint8_t *mask, float *f32, cudaStream_t s, int grid = 0);
 int warp_nn_strip_width(const asift_view_desc &v, int tw);
+// warp_precise.cu
+int warp_lz_strip_width(const asift_view_desc &v, int tw, int a);
+cudaError_t launch_warp_lanczos(int a, const DevView *d_views, int n_views, int n_tiles, int cw_max, uint8_t *u8,
+                                uint8_t *mask, float *f32, cudaStream_t s);
 cudaError_t launch_warp_nn(const DevView *d_views, int n_views, int n_tiles, int cw_max, uint8_t *u8, uint8_t *mask,
                            float *f32, cudaStream_t s, int grid = 0);
 

@@ -1,0 +1,95 @@
+"""GPU parity of the precise stage's reproduction of the best view (Sec. III-C:
+Lanczos with n = 4, an 8 x 8 window), asift_views_lanczos, against the
+oracle's Lanczos-a views.
+
+Bar: fp32 within 1e-4 of full scale (1e-4 x 255) of the fp64 oracle, the mask
+bit-exact, u8 equal except within 3e-3 of a rounding tie.  The fp32 weights
+(sinpi-based, normalised) and the fp32 sums of 64 + (2K+1) + 8 taps stay two
+orders inside the bar.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2503_03479_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+WARP_TOL = 1e-4 * 255
+
+
+@pytest.fixture(scope="module")
+def A():
+    from paper_2503_03479_gb300 import build as B
+    B.build()
+    from paper_2503_03479_gb300 import asift
+    assert torch.cuda.is_available()
+    return asift
+
+
+def _check(A, ctx, img, views, a):
+    vo = ctx.views(torch.from_numpy(img).cuda(), views, with_f32=True, lanczos=a)
+    torch.cuda.synchronize()
+    worst = 0.0
+    for i, v in enumerate(views):
+        ov = O.make_view(v.H, v.W, v.t, v.phi_deg, scale=v.s)
+        ref = O.warp_view_lanczos(img, ov, a)
+        f = vo.view(i, "f32").cpu().numpy().astype(np.float64)
+        assert f.shape == ref.f64.shape
+        d = np.abs(f - ref.f64).max()
+        worst = max(worst, d)
+        assert d <= WARP_TOL, (i, d)
+        assert np.array_equal(vo.view(i, "mask").cpu().numpy(), ref.mask), i
+        du = np.abs(vo.view(i, "u8").cpu().numpy().astype(int) - ref.u8.astype(int))
+        near_tie = np.abs(np.abs(ref.f64 - np.floor(ref.f64)) - 0.5) < 3e-3
+        assert (du[~near_tie] == 0).all() and (du <= 1).all(), i
+    return vo, worst
+
+
+@pytest.mark.parametrize("a", [4, 3])
+@pytest.mark.parametrize("H,W,kmax,ds", [(101, 143, 3, 0.5), (157, 201, 6, 0.0)])
+def test_lanczos_views_parity(A, a, H, W, kmax, ds):
+    ctx = A.Context()
+    img = synth.texture(H, W, 60 + kmax)
+    views = A.view_table(H, W, kmax, ds) + [A.make_view(H, W, t, phi, s) for t, phi, s in
+                                             ((1.0, 90.0, 1.0), (2.6, 33.0, 2.75), (7.9, 151.0, 1.0))]
+    _, worst = _check(A, ctx, img, views, a)
+    assert worst < 3e-3
+
+
+def test_lanczos3_kernel_agrees_with_the_main_warp(A):
+    """Two independent GPU kernels for the same Lanczos-3 view."""
+    ctx = A.Context()
+    img = synth.texture(120, 160, 61)
+    views = A.view_table(120, 160, 4)
+    t = torch.from_numpy(img).cuda()
+    a = ctx.views(t, views, with_f32=True, lanczos=3)
+    b = ctx.views(t, views, with_f32=True)
+    torch.cuda.synchronize()
+    for i in range(len(views)):
+        assert np.abs(a.view(i, "f32").cpu().numpy() - b.view(i, "f32").cpu().numpy()).max() < 5e-3
+        assert np.array_equal(a.view(i, "mask").cpu().numpy(), b.view(i, "mask").cpu().numpy())
+
+
+def test_precise_reproduction_of_the_coarse_best_view(A):
+    """Coarse stage -> best parameter group -> its Lanczos-4 reproduction
+    (Sec. III-B, III-C), the reproduction equal to the oracle's."""
+    ctx = A.Context(n_levels=4, n_features=400)
+    img1 = synth.texture(150, 190, 33)
+    table = O.view_table_scaled(150, 190, 2, 0.5)
+    img2 = np.ascontiguousarray(O.warp_view_nn(img1, table[7]).u8)
+    pc = ctx.pair_cfg(kmax=2, coarse=True, ds=0.5, nearest=True)
+    _, _, ws = ctx.match_pair(torch.from_numpy(img1).cuda(), torch.from_numpy(img2).cuda(), pc)
+    _, best = ctx.view_counts(img1.shape, img2.shape, pc, ws)
+    b = int(best.item())
+    assert b == 7
+    view = ctx.pair_views(img1.shape, pc, 0)[b]
+    _check(A, ctx, img1, [view], 4)
+
+
+def test_lanczos_rejects_other_orders(A):
+    ctx = A.Context()
+    img = torch.from_numpy(synth.texture(40, 50, 62)).cuda()
+    with pytest.raises(A.AsiftError):
+        ctx.views(img, A.view_table(40, 50, 1), lanczos=5)
