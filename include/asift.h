@@ -364,6 +364,11 @@ ASIFT_API asift_status asift_plan_run(asift_plan *plan, void *stream);
 /* Device pointers of pair i's accepted matches, their capacity and count. */
 ASIFT_API asift_status asift_plan_pairs(const asift_plan *plan, int i, asift_pair_match **d_pairs, int *cap,
                                         int32_t **d_n);
+/* match_pair_view_counts for pair i of the plan's last run (on `stream`, in
+ * order after asift_plan_run): accepted matches per image-1 view of pair i
+ * (its view table order) and the view with the most. */
+ASIFT_API asift_status asift_plan_view_counts(const asift_plan *plan, int i, int32_t *d_counts, int n_counts,
+                                              int32_t *d_best, void *stream);
 /* The plan's workspace (status word first) and the pooled keypoint counts
  * (int32 [2 n_pairs]: image 1, image 2 of each pair). */
 ASIFT_API asift_status asift_plan_workspace(const asift_plan *plan, void **d_workspace, int32_t **d_pool_counts);

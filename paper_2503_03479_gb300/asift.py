@@ -29,7 +29,7 @@ EXPORTED = ["asift_ctx_create", "asift_ctx_destroy", "asift_ctx_orb_cfg", "asift
             "asift_eval_pairs", "asift_read_status",
             "asift_launch_count", "asift_pattern_table", "asift_bin_table", "asift_profile_enable",
             "asift_profile_read", "hamming_match_noalloc", "asift_plan_create", "asift_plan_run",
-            "asift_plan_pairs", "asift_plan_workspace", "asift_plan_set_tuning", "asift_plan_get_tuning",
+            "asift_plan_pairs", "asift_plan_view_counts", "asift_plan_workspace", "asift_plan_set_tuning", "asift_plan_get_tuning",
             "asift_plan_autotune", "asift_plan_destroy", "asift_warp_shape_for", "asift_warp_workspace_size",
             "asift_warp_fwd", "asift_warp_bwd", "asift_ctx_set_match_engine", "asift_ctx_match_engine"]
 MATCH_AUTO, MATCH_CUDA_CORES, MATCH_TENSOR_CORES = 0, 1, 2
@@ -144,6 +144,7 @@ def load_library():
         "asift_plan_create": (i32, [vp, vp, i32, P(PairCfg), P(Tuning), i32, P(vp)]),
         "asift_plan_run": (i32, [vp, vp]),
         "asift_plan_pairs": (i32, [vp, i32, P(vp), P(C.c_int), P(vp)]),
+        "asift_plan_view_counts": (i32, [vp, i32, vp, i32, vp, vp]),
         "asift_plan_workspace": (i32, [vp, P(vp), P(vp)]),
         "asift_plan_set_tuning": (i32, [vp, P(Tuning)]),
         "asift_plan_get_tuning": (i32, [vp, P(Tuning)]),
@@ -520,7 +521,8 @@ class Plan:
     address: update them in place between runs."""
 
     def __init__(self, ctx: Context, imgs1, imgs2, kmax: int = 5, num: int = 4, den: int = 5,
-                 tuning: dict | None = None, use_graph: bool = True):
+                 tuning: dict | None = None, use_graph: bool = True, coarse: bool = False, ds: float = 0.5,
+                 nearest: bool = False):
         self.ctx = ctx
         self.L = ctx.L
         self.imgs = list(zip(imgs1, imgs2))      # keep the tensors alive
@@ -529,7 +531,8 @@ class Plan:
             assert a.is_cuda and a.dtype == torch.uint8 and b.is_cuda and b.dtype == torch.uint8
             arr[i] = PairDesc(a.data_ptr(), a.shape[0], a.shape[1], a.stride(0),
                               b.data_ptr(), b.shape[0], b.shape[1], b.stride(0))
-        pc = PairCfg(kmax, num, den, 0, 0, INTERP_LANCZOS3, 0.5)
+        pc = PairCfg(kmax, num, den, 0, int(coarse), INTERP_NEAREST if nearest else INTERP_LANCZOS3, float(ds))
+        self.pc = pc
         tn = Tuning(**tuning) if tuning else None
         self._p = C.c_void_p()
         torch.cuda.synchronize()
@@ -579,6 +582,16 @@ class Plan:
     def pool_counts(self) -> np.ndarray:
         _, cnt = self.workspace()
         return device_view(cnt, (2 * len(self.imgs),), "<i4").cpu().numpy()
+
+    def view_counts(self, i: int):
+        """Accepted matches per image-1 view of pair i and the view with the most (device int32)."""
+        a, _ = self.imgs[i]
+        n1 = len(Context.pair_views(tuple(a.shape), self.pc, 0))
+        counts = torch.empty(n1, dtype=torch.int32, device=a.device)
+        best = torch.empty(1, dtype=torch.int32, device=a.device)
+        _check("asift_plan_view_counts",
+               self.L.asift_plan_view_counts(self._p, i, _ptr(counts), n1, _ptr(best), _stream()))
+        return counts, best
 
     def pairs(self, i: int) -> np.ndarray:
         ptr, cap, dn = C.c_void_p(), C.c_int(), C.c_void_p()

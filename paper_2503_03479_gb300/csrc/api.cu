@@ -1349,6 +1349,19 @@ asift_status asift_plan_pairs(const asift_plan *plan, int i, asift_pair_match **
     return ASIFT_OK;
 }
 
+asift_status asift_plan_view_counts(const asift_plan *plan, int i, int32_t *d_counts, int n_counts, int32_t *d_best,
+                                    void *stream)
+{
+    if (!plan || i < 0 || i >= (int)plan->outs.size() || !d_counts) return ASIFT_ERR_ARG;
+    const asift::Pipeline &L = plan->L;
+    const int nv1 = L.nv1[i];
+    if (n_counts < nv1 || nv1 > view_count_max_views()) return ASIFT_ERR_ARG;
+    const size_t q0 = (size_t)L.first[2 * i] * plan->ctx->cfg.n_features;
+    return cuda_status(launch_view_counts(L.kp + q0, L.accept + q0, L.o.group_total + 2 * i,
+                                          nv1 * plan->ctx->cfg.n_features, L.first[2 * i], nv1, d_counts, d_best,
+                                          static_cast<cudaStream_t>(stream)));
+}
+
 asift_status asift_plan_workspace(const asift_plan *plan, void **d_workspace, int32_t **d_pool_counts)
 {
     if (!plan) return ASIFT_ERR_ARG;

@@ -189,3 +189,31 @@ def test_view_counts_rejects_short_output(A):
     rc = ctx.L.match_pair_view_counts(ctx._ctx, 64, 80, 64, 80, C.byref(pv), ws.data_ptr(), short.data_ptr(),
                                       short.numel(), None, None)
     assert rc == A.ASIFT_ERR_ARG
+
+
+def test_batched_coarse_plan_equals_match_pair(A):
+    """The coarse stage of several pairs of different sizes in one plan (one
+    launch per stage, CUDA graph): every pair's accepted pairs, per-view counts
+    and best group equal match_pair's on that pair alone."""
+    ctx = A.Context(n_levels=4, n_features=300)
+    rng = np.random.default_rng(600)
+    imgs1, imgs2 = [], []
+    for k, (H, W) in enumerate(((120, 160), (97, 131), (150, 190))):
+        img1 = synth.texture(H, W, 610 + k)
+        table = O.view_table_scaled(H, W, 2, 0.5)
+        star = int(rng.integers(1, len(table)))
+        imgs1.append(torch.from_numpy(img1).cuda())
+        imgs2.append(torch.from_numpy(np.ascontiguousarray(O.warp_view_nn(img1, table[star]).u8)).cuda())
+    plan = A.Plan(ctx, imgs1, imgs2, kmax=2, coarse=True, ds=0.5, nearest=True)
+    plan.run()
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    for i in range(len(imgs1)):
+        pc = ctx.pair_cfg(kmax=2, coarse=True, ds=0.5, nearest=True)
+        out, n, ws = ctx.match_pair(imgs1[i], imgs2[i], pc)
+        c1, b1 = ctx.view_counts(tuple(imgs1[i].shape), tuple(imgs2[i].shape), pc, ws)
+        c2, b2 = plan.view_counts(i)
+        torch.cuda.synchronize()
+        assert plan.pairs(i).tobytes() == ctx.pairs_host(out, n).tobytes()
+        assert np.array_equal(c1.cpu().numpy(), c2.cpu().numpy()) and int(b1.item()) == int(b2.item())
+    plan.close()
