@@ -15,7 +15,8 @@
 //      (caller's random numbers mod n) and solves the 8x8 system by Gaussian
 //      elimination with partial pivoting.
 //   5. ransac_count_kernel: hypotheses x pairs, eight hypotheses per CTA
-//      staged in shared memory.
+//      staged in shared memory; each test is decided in fp32 with an error
+//      bound, in fp64 only within the bound of the threshold.
 //   6. ransac_best_kernel (the largest count, the lowest hypothesis on ties)
 //      and inlier_kernel.
 // Every fp64 step is one IEEE operation (the _rn intrinsics are never fused),
@@ -277,16 +278,57 @@ ransac_fit_kernel(const asift_pair_match *__restrict__ up, const uint32_t *__res
     counts[h] = 0;
 }
 
+// The threshold test of one pair, decided as reproj_sq(H, ...) <= th_sq is,
+// but mostly in fp32: an fp32 evaluation with a rigorous error bound decides
+// every pair whose distance is clearly inside or outside the threshold, and
+// only pairs within the bound of it take the fp64 path.  With unit roundoff
+// u = 2^-24, the rounding of H to fp32 and the products and sums leave |X32 -
+// X| <= 4u SX (SX = |h0 x| + |h1 y| + |h2|), likewise for Y and Z; the
+// quotient and the difference add a few u more.  The bound below takes 16u
+// (four times that) and rejects near-zero denominators, so a decision taken
+// in fp32 is the fp64 decision.
+// The rare undecided case, out of line so the fp32 loop stays small.
+__device__ __noinline__ bool within_threshold_exact(const double *Hd, float x, float y, float u, float v, double th_sq)
+{
+    return reproj_sq(Hd, x, y, u, v) <= th_sq;
+}
+
+__device__ __forceinline__ bool within_threshold(const double *Hd, const float *Hf, float x, float y, float u, float v,
+                                                 double th_sq, float th_lo, float th_hi)
+{
+    constexpr float kU = 16.0f / 16777216.0f;
+    const float a0 = Hf[0] * x, a1 = Hf[1] * y, b0 = Hf[3] * x, b1 = Hf[4] * y, c0 = Hf[6] * x, c1 = Hf[7] * y;
+    const float X = (a0 + a1) + Hf[2], Y = (b0 + b1) + Hf[5], Z = (c0 + c1) + Hf[8];
+    const float SX = fabsf(a0) + fabsf(a1) + fabsf(Hf[2]);
+    const float SY = fabsf(b0) + fabsf(b1) + fabsf(Hf[5]);
+    const float SZ = fabsf(c0) + fabsf(c1) + fabsf(Hf[8]);
+    if (fabsf(Z) > 4.0f * kU * SZ) {
+        const float iz = 1.0f / Z;
+        const float px = X * iz, py = Y * iz;
+        const float dx = fabsf(px - u), dy = fabsf(py - v);
+        const float ex = kU * ((SX + fabsf(px) * SZ) * fabsf(iz) + fabsf(px) + fabsf(u));
+        const float ey = kU * ((SY + fabsf(py) * SZ) * fabsf(iz) + fabsf(py) + fabsf(v));
+        const float hx = dx + ex, hy = dy + ey;
+        const float lx = fmaxf(dx - ex, 0.f), ly = fmaxf(dy - ey, 0.f);
+        if (hx * hx + hy * hy < th_lo) return true;      // NaN and infinity fall through
+        if (lx * lx + ly * ly > th_hi) return false;
+    }
+    return within_threshold_exact(Hd, x, y, u, v, th_sq);
+}
+
 __global__ void __launch_bounds__(kEvalBlock)
 ransac_count_kernel(const asift_pair_match *__restrict__ up, int n_hyp, const double *__restrict__ Hs,
                     int32_t *__restrict__ counts, const asift_eval_result *__restrict__ res)
 {
     __shared__ double sH[kHypPerCta][9];
+    __shared__ float sHf[kHypPerCta][9];
     __shared__ int sv[kHypPerCta];
     const int h0 = blockIdx.x * kHypPerCta;
     for (int k = threadIdx.x; k < kHypPerCta * 9; k += blockDim.x) {
         const int h = h0 + k / 9;
-        sH[k / 9][k % 9] = h < n_hyp ? Hs[9 * (size_t)h + k % 9] : 0.0;
+        const double hv = h < n_hyp ? Hs[9 * (size_t)h + k % 9] : 0.0;
+        sH[k / 9][k % 9] = hv;
+        sHf[k / 9][k % 9] = (float)hv;
     }
     if (threadIdx.x < kHypPerCta) {
         const int h = h0 + (int)threadIdx.x;
@@ -294,16 +336,18 @@ ransac_count_kernel(const asift_pair_match *__restrict__ up, int n_hyp, const do
     }
     __syncthreads();
     const int n = res->n_unique;
+    const double th_sq = res->ransac_th_sq;
+    // fp32 thresholds strictly inside / outside th_sq by more than their own rounding
+    const float th_lo = (float)th_sq * (1.0f - 1e-5f), th_hi = (float)th_sq * (1.0f + 1e-5f);
     int c[kHypPerCta];
 #pragma unroll
     for (int k = 0; k < kHypPerCta; ++k) c[k] = 0;
     // the CTAs of one hypothesis group stride over the kept pairs together
     for (int i = blockIdx.y * blockDim.x + threadIdx.x; i < n; i += gridDim.y * blockDim.x) {
         const asift_pair_match p = up[i];
-        const double x = p.x1, y = p.y1, u = p.x2, v = p.y2;
 #pragma unroll
         for (int k = 0; k < kHypPerCta; ++k)
-            if (sv[k]) c[k] += reproj_sq(sH[k], x, y, u, v) <= res->ransac_th_sq;
+            if (sv[k]) c[k] += within_threshold(sH[k], sHf[k], p.x1, p.y1, p.x2, p.y2, th_sq, th_lo, th_hi);
     }
 #pragma unroll
     for (int k = 0; k < kHypPerCta; ++k) {
