@@ -543,6 +543,23 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         ms_b = e0.elapsed_time(e1) / reps
+        # the evaluation of every pair's accepted pairs, one launch per stage
+        # (duplicates, RANSAC with 1024 hypotheses, inliers; the mix stores no
+        # true homographies, so no precision count)
+        gen_e = np.random.default_rng(6100 + rank)
+        rnd_b = torch.from_numpy(gen_e.integers(0, 2 ** 32, size=(1024, 4), dtype=np.uint64)
+                                 .astype(np.uint32).view(np.int32)).cuda()
+        plan.evaluate(rnd=rnd_b, read=False)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            plan.evaluate(rnd=rnd_b, read=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_eval_b = e0.elapsed_time(e1) / reps
+        res_b = plan.evaluate(rnd=rnd_b)
+        eval_b = {"ms": ms_eval_b, "hypotheses": 1024, "kept_pairs": int(sum(r.n_unique for r in res_b)),
+                  "inliers": int(sum(r.n_inliers for r in res_b))}
         # the plain per-view form and the one-pair-per-call form on the same batch
         def per_pair(per_view):
             pcx = ctx.pair_cfg(kmax=KMAX, per_view=per_view)
@@ -566,7 +583,8 @@ def run_ours(args):
                    "plain_per_view_pairs_per_s": nb / (ms_plain / 1e3),
                    "one_pair_per_call_pairs_per_s": nb / (ms_single / 1e3),
                    "batched_vs_plain": ms_plain / ms_b, "tuning": tuning,
-                   "plan_create_s": t_plan, "autotune_s": t_tune, "generate_s": t_gen}
+                   "plan_create_s": t_plan, "autotune_s": t_tune, "generate_s": t_gen,
+                   "evaluation": eval_b}
         del b1, b2
 
     # ---- large extreme-tilt batch: 4096x3072 pairs, 63 views per image, 2000 keypoints per view

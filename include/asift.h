@@ -480,6 +480,21 @@ ASIFT_API asift_status asift_eval_pairs(asift_ctx *ctx, const asift_pair_match *
                                         int32_t *d_hyp_counts, asift_eval_result *d_result, void *d_workspace,
                                         size_t ws_bytes, void *stream);
 
+/* asift_eval_pairs for every pair of the plan's last run, one launch per
+ * stage over all pairs: h_H_true holds 9 doubles per pair (or NULL: no
+ * precision), the n_hyp hypotheses' random numbers d_rnd are shared by all
+ * pairs.  Outputs (kept pairs, inlier mask, per-hypothesis counts, result)
+ * live in d_workspace (asift_plan_eval_workspace_size(plan, n_hyp) bytes,
+ * 256-byte aligned); asift_plan_eval_outputs returns pair i's (any output
+ * pointer may be NULL).  Results equal asift_eval_pairs on each pair. */
+ASIFT_API size_t asift_plan_eval_workspace_size(const asift_plan *plan, int n_hyp);
+ASIFT_API asift_status asift_plan_eval(asift_plan *plan, const double *h_H_true, double th_sq, const uint32_t *d_rnd,
+                                       int n_hyp, double ransac_th_sq, void *d_workspace, size_t ws_bytes,
+                                       void *stream);
+ASIFT_API asift_status asift_plan_eval_outputs(const asift_plan *plan, void *d_workspace, int n_hyp, int i,
+                                               asift_pair_match **d_unique, uint8_t **d_inlier,
+                                               int32_t **d_hyp_counts, asift_eval_result **d_result);
+
 /* Synchronises `stream` and copies the status word at the start of a
  * workspace to *h_status (ASIFT_OK, ASIFT_ERR_CAPACITY or ASIFT_ERR_TIMEOUT);
  * clears it when clear != 0. */

@@ -29,7 +29,8 @@ EXPORTED = ["asift_ctx_create", "asift_ctx_destroy", "asift_ctx_orb_cfg", "asift
             "asift_eval_pairs", "asift_read_status",
             "asift_launch_count", "asift_pattern_table", "asift_bin_table", "asift_profile_enable",
             "asift_profile_read", "hamming_match_noalloc", "asift_plan_create", "asift_plan_run",
-            "asift_plan_pairs", "asift_plan_view_counts", "asift_plan_workspace", "asift_plan_set_tuning", "asift_plan_get_tuning",
+            "asift_plan_pairs", "asift_plan_view_counts", "asift_plan_eval_workspace_size", "asift_plan_eval",
+            "asift_plan_eval_outputs", "asift_plan_workspace", "asift_plan_set_tuning", "asift_plan_get_tuning",
             "asift_plan_autotune", "asift_plan_destroy", "asift_warp_shape_for", "asift_warp_workspace_size",
             "asift_warp_fwd", "asift_warp_bwd", "asift_ctx_set_match_engine", "asift_ctx_match_engine"]
 MATCH_AUTO, MATCH_CUDA_CORES, MATCH_TENSOR_CORES = 0, 1, 2
@@ -145,6 +146,9 @@ def load_library():
         "asift_plan_run": (i32, [vp, vp]),
         "asift_plan_pairs": (i32, [vp, i32, P(vp), P(C.c_int), P(vp)]),
         "asift_plan_view_counts": (i32, [vp, i32, vp, i32, vp, vp]),
+        "asift_plan_eval_workspace_size": (sz, [vp, i32]),
+        "asift_plan_eval": (i32, [vp, vp, C.c_double, vp, i32, C.c_double, vp, sz, vp]),
+        "asift_plan_eval_outputs": (i32, [vp, vp, i32, i32, P(vp), P(vp), P(vp), P(vp)]),
         "asift_plan_workspace": (i32, [vp, P(vp), P(vp)]),
         "asift_plan_set_tuning": (i32, [vp, P(Tuning)]),
         "asift_plan_get_tuning": (i32, [vp, P(Tuning)]),
@@ -592,6 +596,51 @@ class Plan:
         _check("asift_plan_view_counts",
                self.L.asift_plan_view_counts(self._p, i, _ptr(counts), n1, _ptr(best), _stream()))
         return counts, best
+
+    def evaluate(self, H_true=None, th_sq: float = 3.0, rnd: torch.Tensor | None = None,
+                 ransac_th_sq: float = 9.0, read: bool = True):
+        """asift_eval_pairs on every pair of the last run, one launch per stage.  H_true: a list
+        of 3x3 homographies (one per pair) or None; rnd: device int32 (n_hyp, 4), read as uint32.
+        Returns the per-pair EvalResult list; eval_outputs(i) gives pair i's device outputs."""
+        n_hyp = 0 if rnd is None else rnd.shape[0]
+        nbytes = self.L.asift_plan_eval_workspace_size(self._p, n_hyp)
+        if nbytes == 0:
+            raise AsiftError("asift_plan_eval_workspace_size", ASIFT_ERR_ARG)
+        if getattr(self, "_eval_ws", None) is None or self._eval_ws.numel() < nbytes:
+            self._eval_ws = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+        self._eval_hyp = n_hyp
+        Hh = None
+        if H_true is not None:
+            flat = np.concatenate([np.asarray(h, dtype=np.float64).reshape(9) for h in H_true])
+            Hh = (C.c_double * len(flat))(*flat.tolist())
+        _check("asift_plan_eval", self.L.asift_plan_eval(self._p, Hh, float(th_sq), _ptr(rnd), n_hyp,
+                                                         float(ransac_th_sq), _ptr(self._eval_ws),
+                                                         self._eval_ws.numel(), _stream()))
+        if not read:
+            return None
+        torch.cuda.synchronize()
+        return [self._eval_result(i) for i in range(len(self.imgs))]
+
+    def _eval_outputs(self, i: int):
+        ptrs = [C.c_void_p() for _ in range(4)]
+        _check("asift_plan_eval_outputs",
+               self.L.asift_plan_eval_outputs(self._p, _ptr(self._eval_ws), self._eval_hyp, i,
+                                              *[C.byref(q) for q in ptrs]))
+        return [q.value for q in ptrs]
+
+    def _eval_result(self, i: int) -> EvalResult:
+        base = self._eval_ws.data_ptr()
+        o = self._eval_outputs(i)[3] - base
+        return EvalResult.from_buffer_copy(self._eval_ws[o:o + C.sizeof(EvalResult)].cpu().numpy().tobytes())
+
+    def eval_outputs(self, i: int, n_unique: int):
+        """Pair i's kept pairs (PAIR_DTYPE), inlier mask and per-hypothesis counts (host copies)."""
+        base = self._eval_ws.data_ptr()
+        u, m, c, _ = self._eval_outputs(i)
+        uq = self._eval_ws[u - base:u - base + n_unique * PAIR_DTYPE.itemsize].cpu().numpy().view(PAIR_DTYPE)
+        inl = self._eval_ws[m - base:m - base + n_unique].cpu().numpy().astype(bool)
+        cnt = self._eval_ws[c - base:c - base + 4 * self._eval_hyp].cpu().numpy().view(np.int32)
+        return uq, inl, cnt
 
     def pairs(self, i: int) -> np.ndarray:
         ptr, cap, dn = C.c_void_p(), C.c_int(), C.c_void_p()

@@ -1362,6 +1362,35 @@ asift_status asift_plan_view_counts(const asift_plan *plan, int i, int32_t *d_co
                                           static_cast<cudaStream_t>(stream)));
 }
 
+size_t asift_plan_eval_workspace_size(const asift_plan *plan, int n_hyp)
+{
+    if (!plan || n_hyp < 0 || n_hyp > (1 << 20)) return 0;
+    return eval_batch_workspace_bytes(plan->caps.data(), (int)plan->caps.size(), n_hyp);
+}
+
+asift_status asift_plan_eval(asift_plan *plan, const double *h_H_true, double th_sq, const uint32_t *d_rnd, int n_hyp,
+                             double ransac_th_sq, void *d_workspace, size_t ws_bytes, void *stream)
+{
+    if (!plan || !d_workspace || n_hyp < 0 || n_hyp > (1 << 20) || (n_hyp > 0 && !d_rnd) || !(th_sq >= 0.0) ||
+        !(ransac_th_sq >= 0.0) || (reinterpret_cast<uintptr_t>(d_workspace) & 255) ||
+        ws_bytes < eval_batch_workspace_bytes(plan->caps.data(), (int)plan->caps.size(), n_hyp))
+        return ASIFT_ERR_ARG;
+    return cuda_status(launch_eval_batch(plan->outs.data(), plan->d_ns, plan->caps.data(), (int)plan->caps.size(),
+                                         h_H_true, th_sq, d_rnd, n_hyp, ransac_th_sq, d_workspace,
+                                         static_cast<cudaStream_t>(stream)));
+}
+
+asift_status asift_plan_eval_outputs(const asift_plan *plan, void *d_workspace, int n_hyp, int i,
+                                     asift_pair_match **d_unique, uint8_t **d_inlier, int32_t **d_hyp_counts,
+                                     asift_eval_result **d_result)
+{
+    if (!plan || !d_workspace || i < 0 || i >= (int)plan->caps.size() || n_hyp < 0 || n_hyp > (1 << 20))
+        return ASIFT_ERR_ARG;
+    eval_batch_outputs(d_workspace, plan->caps.data(), (int)plan->caps.size(), n_hyp, i, d_unique, d_inlier,
+                       d_hyp_counts, d_result);
+    return ASIFT_OK;
+}
+
 asift_status asift_plan_workspace(const asift_plan *plan, void **d_workspace, int32_t **d_pool_counts)
 {
     if (!plan) return ASIFT_ERR_ARG;

@@ -23,6 +23,7 @@
 // so each decision is taken on exactly the values the written order gives.
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -60,83 +61,143 @@ __device__ __forceinline__ unsigned hash_key(const PairKey4 &k)
 
 __device__ __forceinline__ int pair_count(const int32_t *d_n, int cap) { return min(max(*d_n, 0), cap); }
 
-__global__ void __launch_bounds__(kEvalBlock)
-dedup_insert_kernel(const asift_pair_match *__restrict__ pairs, const int32_t *__restrict__ d_n, int cap,
-                    int *__restrict__ table, unsigned tmask, asift_eval_result *__restrict__ res)
+// One evaluation problem (the accepted pairs of one image pair) and its
+// scratch.  A launch serves a list of problems: the pair-parallel kernels run
+// blk_off .. blk_off + n_blk - 1 of a common block range, the per-hypothesis
+// ones take the problem from blockIdx.z (or .y) and the per-problem ones
+// from blockIdx.x.  A single problem can also be passed by value.
+struct EvalProblem {
+    const asift_pair_match *pairs;
+    const int32_t *d_n;
+    int cap;
+    int blk_off, n_blk;           // blocks of kEvalBlock pairs
+    unsigned tmask;               // table slots - 1
+    int *table;
+    uint8_t *keep;
+    int32_t *bcount;
+    asift_pair_match *unique;
+    uint8_t *inlier;              // may be null
+    double *Hs;
+    int32_t *counts;
+    asift_eval_result *res;
+    int has_H;
+    double Ht[9];
+};
+
+__device__ __forceinline__ const EvalProblem &eprob(const EvalProblem *many, const EvalProblem &single, int p)
 {
-    const int n = pair_count(d_n, cap);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const PairKey4 k = key_of(pairs[i]);
-        unsigned s = hash_key(k) & tmask;
-        bool done = false;
-        // the table has at least twice as many slots as pairs: a free slot or
-        // the key's slot is always reached within tmask + 1 probes
-        for (unsigned probe = 0; probe <= tmask && !done; ++probe, s = (s + 1) & tmask) {
-            const int prev = atomicCAS(&table[s], kEmpty, i);
-            if (prev == kEmpty) {
-                done = true;
-            } else if (same_key(key_of(pairs[prev]), k)) {
-                atomicMin(&table[s], i);
-                done = true;
-            }
-        }
-        if (!done) res->status = ASIFT_ERR_CAPACITY;
+    return many ? many[p] : single;
+}
+
+__device__ __forceinline__ int eval_problem_of_block(const EvalProblem *many, int n, int block)
+{
+    if (!many) return 0;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (many[mid].blk_off <= block) lo = mid; else hi = mid - 1;
     }
+    return lo;
+}
+
+__global__ void eval_init_kernel(const EvalProblem *__restrict__ many, const EvalProblem single, double ransac_th_sq)
+{
+    const EvalProblem &P = eprob(many, single, blockIdx.x);
+    asift_eval_result *res = P.res;
+    if (threadIdx.x == 0) {
+        res->n_pairs = 0;
+        res->n_unique = 0;
+        res->r_num = P.has_H ? 0 : -1;
+        res->best_hyp = -1;
+        res->n_inliers = 0;
+        res->status = ASIFT_OK;
+        res->ransac_th_sq = ransac_th_sq;
+    }
+    if (threadIdx.x < 9) res->H[threadIdx.x] = 0.0;
+    for (unsigned s = threadIdx.x; s <= P.tmask; s += blockDim.x) P.table[s] = kEmpty;
 }
 
 __global__ void __launch_bounds__(kEvalBlock)
-dedup_keep_kernel(const asift_pair_match *__restrict__ pairs, const int32_t *__restrict__ d_n, int cap,
-                  const int *__restrict__ table, unsigned tmask, uint8_t *__restrict__ keep)
+dedup_insert_kernel(const EvalProblem *__restrict__ many, int n_probs, const EvalProblem single)
 {
-    const int n = pair_count(d_n, cap);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const PairKey4 k = key_of(pairs[i]);
-        unsigned s = hash_key(k) & tmask;
-        int owner = i;
-        for (unsigned probe = 0; probe <= tmask; ++probe, s = (s + 1) & tmask) {
-            const int v = table[s];
-            if (v == kEmpty) break;           // not reached: the pair itself was inserted
-            if (same_key(key_of(pairs[v]), k)) {
-                owner = v;
-                break;
-            }
+    const EvalProblem &P = eprob(many, single, eval_problem_of_block(many, n_probs, blockIdx.x));
+    const int n = pair_count(P.d_n, P.cap);
+    const int i = (blockIdx.x - P.blk_off) * kEvalBlock + threadIdx.x;
+    if (i >= n) return;
+    const asift_pair_match *__restrict__ pairs = P.pairs;
+    int *__restrict__ table = P.table;
+    const unsigned tmask = P.tmask;
+    const PairKey4 k = key_of(pairs[i]);
+    unsigned s = hash_key(k) & tmask;
+    bool done = false;
+    // the table has at least twice as many slots as pairs: a free slot or
+    // the key's slot is always reached within tmask + 1 probes
+    for (unsigned probe = 0; probe <= tmask && !done; ++probe, s = (s + 1) & tmask) {
+        const int prev = atomicCAS(&table[s], kEmpty, i);
+        if (prev == kEmpty) {
+            done = true;
+        } else if (same_key(key_of(pairs[prev]), k)) {
+            atomicMin(&table[s], i);
+            done = true;
         }
-        keep[i] = (uint8_t)(owner == i);
     }
+    if (!done) P.res->status = ASIFT_ERR_CAPACITY;
+}
+
+__global__ void __launch_bounds__(kEvalBlock)
+dedup_keep_kernel(const EvalProblem *__restrict__ many, int n_probs, const EvalProblem single)
+{
+    const EvalProblem &P = eprob(many, single, eval_problem_of_block(many, n_probs, blockIdx.x));
+    const int n = pair_count(P.d_n, P.cap);
+    const int i = (blockIdx.x - P.blk_off) * kEvalBlock + threadIdx.x;
+    if (i >= n) return;
+    const PairKey4 k = key_of(P.pairs[i]);
+    unsigned s = hash_key(k) & P.tmask;
+    int owner = i;
+    for (unsigned probe = 0; probe <= P.tmask; ++probe, s = (s + 1) & P.tmask) {
+        const int v = P.table[s];
+        if (v == kEmpty) break;               // not reached: the pair itself was inserted
+        if (same_key(key_of(P.pairs[v]), k)) {
+            owner = v;
+            break;
+        }
+    }
+    P.keep[i] = (uint8_t)(owner == i);
 }
 
 // Kept pairs per block of kEvalBlock pairs, then each block writes its kept
-// pairs after those of the blocks before it.
+// pairs after those of its problem's blocks before it.
 __global__ void __launch_bounds__(kEvalBlock)
-block_count_kernel(const int32_t *__restrict__ d_n, int cap, const uint8_t *__restrict__ keep,
-                   int32_t *__restrict__ block_count)
+block_count_kernel(const EvalProblem *__restrict__ many, int n_probs, const EvalProblem single)
 {
     __shared__ int s;
     if (threadIdx.x == 0) s = 0;
     __syncthreads();
-    const int n = pair_count(d_n, cap);
-    const int i = blockIdx.x * kEvalBlock + threadIdx.x;
-    const unsigned bal = __ballot_sync(0xffffffffu, i < n && keep[i]);
+    const EvalProblem &P = eprob(many, single, eval_problem_of_block(many, n_probs, blockIdx.x));
+    const int n = pair_count(P.d_n, P.cap);
+    const int lb = blockIdx.x - P.blk_off;
+    const int i = lb * kEvalBlock + threadIdx.x;
+    const unsigned bal = __ballot_sync(0xffffffffu, i < n && P.keep[i]);
     if ((threadIdx.x & 31u) == 0 && bal) atomicAdd(&s, __popc(bal));
     __syncthreads();
-    if (threadIdx.x == 0) block_count[blockIdx.x] = s;
+    if (threadIdx.x == 0) P.bcount[lb] = s;
 }
 
 __global__ void __launch_bounds__(kEvalBlock)
-compact_kernel(const asift_pair_match *__restrict__ pairs, const int32_t *__restrict__ d_n, int cap,
-               const uint8_t *__restrict__ keep, const int32_t *__restrict__ block_count,
-               asift_pair_match *__restrict__ out, asift_eval_result *__restrict__ res)
+compact_kernel(const EvalProblem *__restrict__ many, int n_probs, const EvalProblem single)
 {
     __shared__ int wsum[kEvalBlock / 32];
     __shared__ int base;
-    const int n = pair_count(d_n, cap);
+    const EvalProblem &P = eprob(many, single, eval_problem_of_block(many, n_probs, blockIdx.x));
+    const int n = pair_count(P.d_n, P.cap);
+    const int lb = blockIdx.x - P.blk_off;
     if (threadIdx.x == 0) {
         int b = 0;
-        for (int k = 0; k < (int)blockIdx.x; ++k) b += block_count[k];
+        for (int k = 0; k < lb; ++k) b += P.bcount[k];
         base = b;
     }
-    const int i = blockIdx.x * kEvalBlock + threadIdx.x;
-    const bool a = i < n && keep[i];
+    const int i = lb * kEvalBlock + threadIdx.x;
+    const bool a = i < n && P.keep[i];
     const unsigned lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
     const unsigned bal = __ballot_sync(0xffffffffu, a);
     if (lane == 0) wsum[w] = __popc(bal);
@@ -148,13 +209,13 @@ compact_kernel(const asift_pair_match *__restrict__ pairs, const int32_t *__rest
             wsum[k] = acc;
             acc += v;
         }
-        if (blockIdx.x == gridDim.x - 1) {
-            res->n_pairs = n;
-            res->n_unique = base + acc;
+        if (lb == P.n_blk - 1) {
+            P.res->n_pairs = n;
+            P.res->n_unique = base + acc;
         }
     }
     __syncthreads();
-    if (a) out[base + wsum[w] + __popc(bal & ((1u << lane) - 1u))] = pairs[i];
+    if (a) P.unique[base + wsum[w] + __popc(bal & ((1u << lane) - 1u))] = P.pairs[i];
 }
 
 // Squared distance between H (x, y) and (u, v), one rounding per operation
@@ -167,10 +228,6 @@ __device__ __forceinline__ double reproj_sq(const double *H, double x, double y,
     const double dx = __dsub_rn(__ddiv_rn(X, Z), u), dy = __dsub_rn(__ddiv_rn(Y, Z), v);
     return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
 }
-
-struct Hom9 {
-    double h[9];
-};
 
 __device__ __forceinline__ int block_sum(int v)
 {
@@ -185,20 +242,22 @@ __device__ __forceinline__ int block_sum(int v)
     return t;                                   // valid in thread 0
 }
 
+// Eq. (6) over the kept pairs: every block of the problem's range takes a
+// stride of them.
 __global__ void __launch_bounds__(kEvalBlock)
-precision_kernel(const asift_pair_match *__restrict__ up, const Hom9 Ht, double th_sq,
-                 asift_eval_result *__restrict__ res)
+precision_kernel(const EvalProblem *__restrict__ many, int n_probs, const EvalProblem single, double th_sq)
 {
-    const int n = res->n_unique;
+    const EvalProblem &P = eprob(many, single, eval_problem_of_block(many, n_probs, blockIdx.x));
+    if (!P.has_H) return;                       // uniform over the block
+    const int n = P.res->n_unique;
     int c = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const asift_pair_match p = up[i];
-        c += reproj_sq(Ht.h, p.x1, p.y1, p.x2, p.y2) <= th_sq;
+    for (int i = (blockIdx.x - P.blk_off) * kEvalBlock + threadIdx.x; i < n; i += P.n_blk * kEvalBlock) {
+        const asift_pair_match p = P.unique[i];
+        c += reproj_sq(P.Ht, p.x1, p.y1, p.x2, p.y2) <= th_sq;
     }
     const int t = block_sum(c);
-    if (threadIdx.x == 0 && t) atomicAdd(&res->r_num, t);
+    if (threadIdx.x == 0 && t) atomicAdd(&P.res->r_num, t);
 }
-
 // Homography from four correspondences with h8 = 1 (eight linear equations,
 // Gaussian elimination with partial pivoting: the first row with the largest
 // |entry|; a pivot at most 1e-10 times the largest |entry| is degenerate).
@@ -249,15 +308,16 @@ __device__ bool homography4(const double *x, const double *y, const double *u, c
 }
 
 __global__ void __launch_bounds__(32)
-ransac_fit_kernel(const asift_pair_match *__restrict__ up, const uint32_t *__restrict__ rnd, int n_hyp,
-                  double *__restrict__ Hs, int32_t *__restrict__ counts, const asift_eval_result *__restrict__ res)
+ransac_fit_kernel(const EvalProblem *__restrict__ many, const EvalProblem single, const uint32_t *__restrict__ rnd,
+                  int n_hyp)
 {
+    const EvalProblem &P = eprob(many, single, blockIdx.y);
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= n_hyp) return;
-    const int n = res->n_unique;
-    double *Hh = Hs + 9 * (size_t)h;
+    const int n = P.res->n_unique;
+    double *Hh = P.Hs + 9 * (size_t)h;
     for (int c = 0; c < 9; ++c) Hh[c] = 0.0;
-    counts[h] = -1;
+    P.counts[h] = -1;
     if (n < 4) return;
     int idx[4];
     for (int k = 0; k < 4; ++k) idx[k] = (int)(rnd[4 * (size_t)h + k] % (uint32_t)n);
@@ -266,7 +326,7 @@ ransac_fit_kernel(const asift_pair_match *__restrict__ up, const uint32_t *__res
             if (idx[a] == idx[b]) return;
     double xs[4], ys[4], us[4], vs[4];
     for (int k = 0; k < 4; ++k) {
-        const asift_pair_match p = up[idx[k]];
+        const asift_pair_match p = P.unique[idx[k]];
         xs[k] = p.x1;
         ys[k] = p.y1;
         us[k] = p.x2;
@@ -275,7 +335,7 @@ ransac_fit_kernel(const asift_pair_match *__restrict__ up, const uint32_t *__res
     double H[9];
     if (!homography4(xs, ys, us, vs, H)) return;
     for (int c = 0; c < 9; ++c) Hh[c] = H[c];
-    counts[h] = 0;
+    P.counts[h] = 0;
 }
 
 // The threshold test of one pair, decided as reproj_sq(H, ...) <= th_sq is,
@@ -286,8 +346,8 @@ ransac_fit_kernel(const asift_pair_match *__restrict__ up, const uint32_t *__res
 // X| <= 4u SX (SX = |h0 x| + |h1 y| + |h2|), likewise for Y and Z; the
 // quotient and the difference add a few u more.  The bound below takes 16u
 // (four times that) and rejects near-zero denominators, so a decision taken
-// in fp32 is the fp64 decision.
-// The rare undecided case, out of line so the fp32 loop stays small.
+// in fp32 is the fp64 decision.  The rare undecided case runs out of line,
+// so the fp32 loop stays small.
 __device__ __noinline__ bool within_threshold_exact(const double *Hd, float x, float y, float u, float v, double th_sq)
 {
     return reproj_sq(Hd, x, y, u, v) <= th_sq;
@@ -316,27 +376,27 @@ __device__ __forceinline__ bool within_threshold(const double *Hd, const float *
     return within_threshold_exact(Hd, x, y, u, v, th_sq);
 }
 
+// grid (hypothesis groups, CTAs per group, problems)
 __global__ void __launch_bounds__(kEvalBlock)
-ransac_count_kernel(const asift_pair_match *__restrict__ up, int n_hyp, const double *__restrict__ Hs,
-                    int32_t *__restrict__ counts, const asift_eval_result *__restrict__ res)
+ransac_count_kernel(const EvalProblem *__restrict__ many, const EvalProblem single, int n_hyp, double th_sq)
 {
     __shared__ double sH[kHypPerCta][9];
     __shared__ float sHf[kHypPerCta][9];
     __shared__ int sv[kHypPerCta];
+    const EvalProblem &P = eprob(many, single, blockIdx.z);
     const int h0 = blockIdx.x * kHypPerCta;
     for (int k = threadIdx.x; k < kHypPerCta * 9; k += blockDim.x) {
         const int h = h0 + k / 9;
-        const double hv = h < n_hyp ? Hs[9 * (size_t)h + k % 9] : 0.0;
+        const double hv = h < n_hyp ? P.Hs[9 * (size_t)h + k % 9] : 0.0;
         sH[k / 9][k % 9] = hv;
         sHf[k / 9][k % 9] = (float)hv;
     }
     if (threadIdx.x < kHypPerCta) {
         const int h = h0 + (int)threadIdx.x;
-        sv[threadIdx.x] = h < n_hyp && counts[h] >= 0;
+        sv[threadIdx.x] = h < n_hyp && P.counts[h] >= 0;
     }
     __syncthreads();
-    const int n = res->n_unique;
-    const double th_sq = res->ransac_th_sq;
+    const int n = P.res->n_unique;
     // fp32 thresholds strictly inside / outside th_sq by more than their own rounding
     const float th_lo = (float)th_sq * (1.0f - 1e-5f), th_hi = (float)th_sq * (1.0f + 1e-5f);
     int c[kHypPerCta];
@@ -344,7 +404,7 @@ ransac_count_kernel(const asift_pair_match *__restrict__ up, int n_hyp, const do
     for (int k = 0; k < kHypPerCta; ++k) c[k] = 0;
     // the CTAs of one hypothesis group stride over the kept pairs together
     for (int i = blockIdx.y * blockDim.x + threadIdx.x; i < n; i += gridDim.y * blockDim.x) {
-        const asift_pair_match p = up[i];
+        const asift_pair_match p = P.unique[i];
 #pragma unroll
         for (int k = 0; k < kHypPerCta; ++k)
             if (sv[k]) c[k] += within_threshold(sH[k], sHf[k], p.x1, p.y1, p.x2, p.y2, th_sq, th_lo, th_hi);
@@ -352,21 +412,22 @@ ransac_count_kernel(const asift_pair_match *__restrict__ up, int n_hyp, const do
 #pragma unroll
     for (int k = 0; k < kHypPerCta; ++k) {
         const int t = block_sum(c[k]);
-        if (threadIdx.x == 0 && sv[k] && t) atomicAdd(&counts[h0 + k], t);
+        if (threadIdx.x == 0 && sv[k] && t) atomicAdd(&P.counts[h0 + k], t);
     }
 }
 
 __device__ __forceinline__ bool hyp_better(int c, int h, int bc, int bh) { return c > bc || (c == bc && h < bh); }
 
+// one block per problem
 __global__ void __launch_bounds__(kEvalBlock)
-ransac_best_kernel(const int32_t *__restrict__ counts, int n_hyp, const double *__restrict__ Hs,
-                   asift_eval_result *__restrict__ res)
+ransac_best_kernel(const EvalProblem *__restrict__ many, const EvalProblem single, int n_hyp)
 {
     __shared__ int sc[kEvalBlock / 32], sh[kEvalBlock / 32];
+    const EvalProblem &P = eprob(many, single, blockIdx.x);
     int bc = -1, bh = n_hyp;
     for (int h = threadIdx.x; h < n_hyp; h += blockDim.x)
-        if (counts[h] >= 0 && hyp_better(counts[h], h, bc, bh)) {
-            bc = counts[h];
+        if (P.counts[h] >= 0 && hyp_better(P.counts[h], h, bc, bh)) {
+            bc = P.counts[h];
             bh = h;
         }
     for (int o = 16; o; o >>= 1) {
@@ -388,45 +449,32 @@ ransac_best_kernel(const int32_t *__restrict__ counts, int n_hyp, const double *
                 bh = sh[w];
             }
         const bool any = bc >= 0;
-        res->best_hyp = any ? bh : -1;
-        for (int c = 0; c < 9; ++c) res->H[c] = any ? Hs[9 * (size_t)bh + c] : 0.0;
+        P.res->best_hyp = any ? bh : -1;
+        for (int c = 0; c < 9; ++c) P.res->H[c] = any ? P.Hs[9 * (size_t)bh + c] : 0.0;
     }
 }
 
+// Over the problem's block range (the whole capacity: the mask beyond the
+// kept pairs is cleared).
 __global__ void __launch_bounds__(kEvalBlock)
-inlier_kernel(const asift_pair_match *__restrict__ up, int cap, uint8_t *__restrict__ inlier,
-              asift_eval_result *__restrict__ res)
+inlier_kernel(const EvalProblem *__restrict__ many, int n_probs, const EvalProblem single)
 {
+    const EvalProblem &P = eprob(many, single, eval_problem_of_block(many, n_probs, blockIdx.x));
+    const asift_eval_result *res = P.res;
     const int n = res->n_unique;
     const bool any = res->best_hyp >= 0;
+    const double th_sq = res->ransac_th_sq;
     double H[9];
     for (int c = 0; c < 9; ++c) H[c] = res->H[c];
-    int cnt = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x) {
-        bool in = false;
-        if (i < n && any) {
-            const asift_pair_match p = up[i];
-            in = reproj_sq(H, p.x1, p.y1, p.x2, p.y2) <= res->ransac_th_sq;
-        }
-        if (inlier) inlier[i] = (uint8_t)in;
-        cnt += in;
+    const int i = (blockIdx.x - P.blk_off) * kEvalBlock + threadIdx.x;
+    bool in = false;
+    if (i < n && any) {
+        const asift_pair_match p = P.unique[i];
+        in = reproj_sq(H, p.x1, p.y1, p.x2, p.y2) <= th_sq;
     }
-    const int t = block_sum(cnt);
-    if (threadIdx.x == 0 && t) atomicAdd(&res->n_inliers, t);
-}
-
-__global__ void eval_init_kernel(asift_eval_result *res, int r_num, double ransac_th_sq)
-{
-    if (threadIdx.x == 0) {
-        res->n_pairs = 0;
-        res->n_unique = 0;
-        res->r_num = r_num;
-        res->best_hyp = -1;
-        res->n_inliers = 0;
-        res->status = ASIFT_OK;
-        res->ransac_th_sq = ransac_th_sq;
-    }
-    if (threadIdx.x < 9) res->H[threadIdx.x] = 0.0;
+    if (P.inlier && i < P.cap) P.inlier[i] = (uint8_t)in;
+    const int t = block_sum(in);
+    if (threadIdx.x == 0 && t) atomicAdd(&P.res->n_inliers, t);
 }
 
 // ---------------------------------------------------------------- host side
@@ -438,13 +486,86 @@ static unsigned table_slots(int cap)
 }
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+static int eval_blocks(int cap) { return std::max(1, (cap + kEvalBlock - 1) / kEvalBlock); }
+
+// Scratch of one problem, carved from w (advanced): the duplicate table, the
+// keep mask, block counts, the hypotheses' homographies and counts and, with
+// own_outputs, the kept pairs, the inlier mask and the result.
+static size_t carve_problem(char *&w, bool carve, EvalProblem &P, int cap, int n_hyp, bool own_outputs)
+{
+    const unsigned slots = table_slots(cap);
+    const int blocks = eval_blocks(cap);
+    const size_t sizes[8] = {align256(sizeof(int) * slots), align256((size_t)std::max(cap, 1)),
+                             align256(sizeof(int32_t) * blocks),
+                             align256(sizeof(double) * 9 * (size_t)std::max(n_hyp, 1)),
+                             align256(sizeof(int32_t) * (size_t)std::max(n_hyp, 1)),
+                             own_outputs ? align256(sizeof(asift_pair_match) * (size_t)std::max(cap, 1)) : 0,
+                             own_outputs ? align256((size_t)std::max(cap, 1)) : 0,
+                             own_outputs ? align256(sizeof(asift_eval_result)) : 0};
+    size_t total = 0;
+    for (size_t b : sizes) total += b;
+    if (!carve) return total;
+    P.cap = cap;
+    P.n_blk = blocks;
+    P.tmask = slots - 1;
+    P.table = reinterpret_cast<int *>(w);
+    w += sizes[0];
+    P.keep = reinterpret_cast<uint8_t *>(w);
+    w += sizes[1];
+    P.bcount = reinterpret_cast<int32_t *>(w);
+    w += sizes[2];
+    P.Hs = reinterpret_cast<double *>(w);
+    w += sizes[3];
+    P.counts = reinterpret_cast<int32_t *>(w);
+    w += sizes[4];
+    if (own_outputs) {
+        P.unique = reinterpret_cast<asift_pair_match *>(w);
+        w += sizes[5];
+        P.inlier = reinterpret_cast<uint8_t *>(w);
+        w += sizes[6];
+        P.res = reinterpret_cast<asift_eval_result *>(w);
+        w += sizes[7];
+    }
+    return total;
+}
 
 size_t eval_workspace_bytes(int cap, int n_hyp)
 {
-    const size_t blocks = (size_t)std::max(1, (cap + kEvalBlock - 1) / kEvalBlock);
-    return align256(sizeof(int) * table_slots(cap)) + align256((size_t)std::max(cap, 1)) +
-           align256(sizeof(int32_t) * blocks) + align256(sizeof(double) * 9 * (size_t)std::max(n_hyp, 1)) +
-           align256(sizeof(int32_t) * (size_t)std::max(n_hyp, 1));
+    EvalProblem P{};
+    char *w = nullptr;
+    return carve_problem(w, false, P, cap, n_hyp, false);
+}
+
+// The launch sequence for P problems (many: device copy of the list, or
+// null with the single problem by value).
+static cudaError_t launch_eval_list(const EvalProblem *many, const EvalProblem &single, int P, int total_blk,
+                                    int max_blk, int n_hyp, const uint32_t *d_rnd, double th_sq, double ransac_th_sq,
+                                    bool any_H, cudaStream_t s)
+{
+    eval_init_kernel<<<P, 1024, 0, s>>>(many, single, ransac_th_sq);
+    dedup_insert_kernel<<<total_blk, kEvalBlock, 0, s>>>(many, P, single);
+    dedup_keep_kernel<<<total_blk, kEvalBlock, 0, s>>>(many, P, single);
+    block_count_kernel<<<total_blk, kEvalBlock, 0, s>>>(many, P, single);
+    compact_kernel<<<total_blk, kEvalBlock, 0, s>>>(many, P, single);
+    note_launch(5);
+    if (any_H) {
+        precision_kernel<<<total_blk, kEvalBlock, 0, s>>>(many, P, single, th_sq);
+        note_launch();
+    }
+    if (n_hyp > 0) {
+        ransac_fit_kernel<<<dim3((n_hyp + 31) / 32, P), 32, 0, s>>>(many, single, d_rnd, n_hyp);
+        // hypothesis groups x CTAs per group x problems: about two CTAs per
+        // SM, no more CTAs per group than a problem's blocks of pairs
+        const int hyp_blocks = (n_hyp + kHypPerCta - 1) / kHypPerCta;
+        const long long per = (long long)hyp_blocks * P;
+        const int gy = (int)std::max(1LL, std::min((2LL * 152 + per - 1) / per, (long long)max_blk));
+        ransac_count_kernel<<<dim3(hyp_blocks, gy, P), kEvalBlock, 0, s>>>(many, single, n_hyp, ransac_th_sq);
+        ransac_best_kernel<<<P, kEvalBlock, 0, s>>>(many, single, n_hyp);
+        note_launch(3);
+    }
+    inlier_kernel<<<total_blk, kEvalBlock, 0, s>>>(many, P, single);
+    note_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_eval(const asift_pair_match *d_pairs, const int32_t *d_n, int cap, const double *h_H_true,
@@ -452,48 +573,77 @@ cudaError_t launch_eval(const asift_pair_match *d_pairs, const int32_t *d_n, int
                         asift_pair_match *d_unique, uint8_t *d_inlier, int32_t *d_hyp_counts,
                         asift_eval_result *d_res, void *d_ws, cudaStream_t s)
 {
-    const unsigned slots = table_slots(cap);
-    const int blocks = std::max(1, (cap + kEvalBlock - 1) / kEvalBlock);
+    EvalProblem P{};
     char *w = static_cast<char *>(d_ws);
-    int *table = reinterpret_cast<int *>(w);
-    w += align256(sizeof(int) * slots);
-    uint8_t *keep = reinterpret_cast<uint8_t *>(w);
-    w += align256((size_t)std::max(cap, 1));
-    int32_t *bcount = reinterpret_cast<int32_t *>(w);
-    w += align256(sizeof(int32_t) * blocks);
-    double *Hs = reinterpret_cast<double *>(w);
-    w += align256(sizeof(double) * 9 * (size_t)std::max(n_hyp, 1));
-    int32_t *counts = d_hyp_counts ? d_hyp_counts : reinterpret_cast<int32_t *>(w);
+    carve_problem(w, true, P, cap, n_hyp, false);
+    P.pairs = d_pairs;
+    P.d_n = d_n;
+    P.blk_off = 0;
+    P.unique = d_unique;
+    P.inlier = d_inlier;
+    P.res = d_res;
+    if (d_hyp_counts) P.counts = d_hyp_counts;
+    P.has_H = h_H_true != nullptr;
+    for (int c = 0; c < 9; ++c) P.Ht[c] = h_H_true ? h_H_true[c] : 0.0;
+    return launch_eval_list(nullptr, P, 1, P.n_blk, P.n_blk, n_hyp, d_rnd, th_sq, ransac_th_sq, P.has_H, s);
+}
 
-    eval_init_kernel<<<1, 32, 0, s>>>(d_res, h_H_true ? 0 : -1, ransac_th_sq);
-    note_launch();
-    cudaError_t e = cudaMemsetAsync(table, 0xff, sizeof(int) * slots, s);
+// ---- batched form: the pairs of a plan, one launch per stage
+size_t eval_batch_workspace_bytes(const int *caps, int n, int n_hyp)
+{
+    size_t b = align256(sizeof(EvalProblem) * (size_t)std::max(n, 1));
+    EvalProblem P{};
+    char *w = nullptr;
+    for (int i = 0; i < n; ++i) b += carve_problem(w, false, P, caps[i], n_hyp, true);
+    return b;
+}
+
+static void carve_batch(void *d_ws, const int *caps, int n, int n_hyp, std::vector<EvalProblem> &probs)
+{
+    probs.assign(n, EvalProblem{});
+    char *w = static_cast<char *>(d_ws) + align256(sizeof(EvalProblem) * (size_t)std::max(n, 1));
+    int off = 0;
+    for (int i = 0; i < n; ++i) {
+        carve_problem(w, true, probs[i], caps[i], n_hyp, true);
+        probs[i].blk_off = off;
+        off += probs[i].n_blk;
+    }
+}
+
+void eval_batch_outputs(void *d_ws, const int *caps, int n, int n_hyp, int i, asift_pair_match **unique,
+                        uint8_t **inlier, int32_t **counts, asift_eval_result **res)
+{
+    std::vector<EvalProblem> probs;
+    carve_batch(d_ws, caps, n, n_hyp, probs);
+    if (unique) *unique = probs[i].unique;
+    if (inlier) *inlier = probs[i].inlier;
+    if (counts) *counts = probs[i].counts;
+    if (res) *res = probs[i].res;
+}
+
+cudaError_t launch_eval_batch(asift_pair_match *const *pairs, int32_t *d_ns, const int *caps, int n,
+                              const double *h_H_true, double th_sq, const uint32_t *d_rnd, int n_hyp,
+                              double ransac_th_sq, void *d_ws, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    std::vector<EvalProblem> probs;
+    carve_batch(d_ws, caps, n, n_hyp, probs);
+    int total = 0, max_blk = 1;
+    for (int i = 0; i < n; ++i) {
+        EvalProblem &P = probs[i];
+        P.pairs = pairs[i];
+        P.d_n = d_ns + i;
+        P.has_H = h_H_true != nullptr;
+        for (int c = 0; c < 9; ++c) P.Ht[c] = h_H_true ? h_H_true[9 * (size_t)i + c] : 0.0;
+        total += P.n_blk;
+        max_blk = std::max(max_blk, P.n_blk);
+    }
+    EvalProblem *d_probs = static_cast<EvalProblem *>(d_ws);
+    // pageable source: the copy is staged before the call returns
+    const cudaError_t e = cudaMemcpyAsync(d_probs, probs.data(), sizeof(EvalProblem) * n, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
-    const int grid = std::min(blocks, 4 * 152);
-    dedup_insert_kernel<<<grid, kEvalBlock, 0, s>>>(d_pairs, d_n, cap, table, slots - 1, d_res);
-    dedup_keep_kernel<<<grid, kEvalBlock, 0, s>>>(d_pairs, d_n, cap, table, slots - 1, keep);
-    block_count_kernel<<<blocks, kEvalBlock, 0, s>>>(d_n, cap, keep, bcount);
-    compact_kernel<<<blocks, kEvalBlock, 0, s>>>(d_pairs, d_n, cap, keep, bcount, d_unique, d_res);
-    note_launch(4);
-    if (h_H_true) {
-        Hom9 Ht;
-        for (int c = 0; c < 9; ++c) Ht.h[c] = h_H_true[c];
-        precision_kernel<<<grid, kEvalBlock, 0, s>>>(d_unique, Ht, th_sq, d_res);
-        note_launch();
-    }
-    if (n_hyp > 0) {
-        ransac_fit_kernel<<<(n_hyp + 31) / 32, 32, 0, s>>>(d_unique, d_rnd, n_hyp, Hs, counts, d_res);
-        // hypothesis groups x CTAs per group: about two CTAs per SM, no more
-        // CTAs per group than the capacity's blocks of pairs
-        const int hyp_blocks = (n_hyp + kHypPerCta - 1) / kHypPerCta;
-        const int gy = std::max(1, std::min((2 * 152 + hyp_blocks - 1) / hyp_blocks, blocks));
-        ransac_count_kernel<<<dim3(hyp_blocks, gy), kEvalBlock, 0, s>>>(d_unique, n_hyp, Hs, counts, d_res);
-        ransac_best_kernel<<<1, kEvalBlock, 0, s>>>(counts, n_hyp, Hs, d_res);
-        note_launch(3);
-    }
-    inlier_kernel<<<grid, kEvalBlock, 0, s>>>(d_unique, cap, d_inlier, d_res);
-    note_launch();
-    return cudaGetLastError();
+    return launch_eval_list(d_probs, probs[0], n, total, max_blk, n_hyp, d_rnd, th_sq, ransac_th_sq,
+                            h_H_true != nullptr, s);
 }
 
 }  // namespace asift

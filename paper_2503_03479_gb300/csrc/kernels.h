@@ -77,6 +77,12 @@ cudaError_t launch_eval(const asift_pair_match *d_pairs, const int32_t *d_n, int
                         double th_sq, const uint32_t *d_rnd, int n_hyp, double ransac_th_sq,
                         asift_pair_match *d_unique, uint8_t *d_inlier, int32_t *d_hyp_counts,
                         asift_eval_result *d_res, void *d_ws, cudaStream_t s);
+size_t eval_batch_workspace_bytes(const int *caps, int n, int n_hyp);
+cudaError_t launch_eval_batch(asift_pair_match *const *pairs, int32_t *d_ns, const int *caps, int n,
+                              const double *h_H_true, double th_sq, const uint32_t *d_rnd, int n_hyp,
+                              double ransac_th_sq, void *d_ws, cudaStream_t s);
+void eval_batch_outputs(void *d_ws, const int *caps, int n, int n_hyp, int i, asift_pair_match **unique,
+                        uint8_t **inlier, int32_t **counts, asift_eval_result **res);
 int view_count_max_views();
 cudaError_t launch_view_counts(const asift_keypoint *kp, const uint8_t *accept, const int32_t *d_nq, int nq_cap,
                                int view0, int n_views, int32_t *counts, int32_t *best, cudaStream_t s);

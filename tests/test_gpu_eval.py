@@ -4,8 +4,9 @@ Eq. (7) inliers, through asift_eval_pairs against the oracle on the same
 pairs and the same random numbers.
 
 Bars: kept pairs, counts, the best hypothesis and the inlier mask bit-exact
-(both sides take every decision in fp64 with one rounding per operation in
-the same order); the fitted homographies within 1e-9 relative.
+(every decision is the fp64 one, one rounding per operation in the same
+order; the GPU takes most of them in fp32 under a rigorous error bound); the
+fitted homographies within 1e-9 relative.
 """
 import numpy as np
 import pytest
@@ -168,3 +169,39 @@ def test_eval_on_match_pair_output(A):
     prec = r.r_num / r.n_unique
     assert prec > 0.5
     assert r.n_inliers >= 0.8 * r.r_num
+
+
+def test_batched_evaluation_of_a_plan(A):
+    """The evaluation of all pairs of a plan in one launch per stage equals the
+    oracle's on each pair's accepted pairs (and so asift_eval_pairs')."""
+    ctx = A.Context(n_levels=4, n_features=300)
+    ps = [synth.pair_affine_small(seed=1100 + k, H=H, W=W) for k, (H, W) in enumerate(((240, 320), (200, 260),
+                                                                                          (180, 300)))]
+    imgs1 = [torch.from_numpy(p.img1).cuda() for p in ps]
+    imgs2 = [torch.from_numpy(p.img2).cuda() for p in ps]
+    plan = A.Plan(ctx, imgs1, imgs2, kmax=2)
+    plan.run()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(530)
+    rnd_np, rnd_t = _rnd(rng, 256)
+    res = plan.evaluate(H_true=[p.H12 for p in ps], rnd=rnd_t)
+    for i, p in enumerate(ps):
+        pairs = plan.pairs(i)
+        r = res[i]
+        kept = pairs[O.dedup(pairs)]
+        assert r.status == 0 and r.n_pairs == len(pairs) and r.n_unique == len(kept)
+        uq, inl, cnt = plan.eval_outputs(i, r.n_unique)
+        assert uq.tobytes() == kept.tobytes()
+        assert r.r_num == O.precision_count(kept, p.H12, 3.0)
+        ref = O.ransac(kept, rnd_np, 9.0)
+        assert np.array_equal(cnt, ref.counts) and r.best_hyp == ref.best
+        assert np.array_equal(inl, ref.inlier) and r.n_inliers == int(ref.inlier.sum())
+        # and the single-pair entry point gives the same result
+        out, n = _upload(A, pairs)
+        _, _, _, res1 = ctx.eval_pairs(out, n, H_true=p.H12, rnd=rnd_t)
+        r1 = ctx.eval_result(res1)
+        assert (r1.n_unique, r1.r_num, r1.best_hyp, r1.n_inliers) == (r.n_unique, r.r_num, r.best_hyp, r.n_inliers)
+    # no true homographies, no hypotheses
+    res = plan.evaluate()
+    assert all(r.r_num == -1 and r.best_hyp == -1 and r.n_inliers == 0 for r in res)
+    plan.close()
