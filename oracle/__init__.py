@@ -131,6 +131,8 @@ def lib():
         L.oracle_homography4.restype = C.c_int
         L.oracle_ransac.argtypes = [f32p, f32p, f32p, f32p, C.c_int, u32p, C.c_int, C.c_double, i32p, f64p, u8p]
         L.oracle_ransac.restype = C.c_int
+        L.oracle_scale_coefficient.argtypes = [f32p, f32p, f32p, f32p, i32p, C.c_int]
+        L.oracle_scale_coefficient.restype = C.c_double
         assert L.oracle_sizeof_dview() == C.sizeof(ODView)
         L.oracle_dwarp_fwd.argtypes = [f64p, P(ODView), f64p]
         L.oracle_dwarp_vjp.argtypes = [f64p, P(ODView), f64p, f64p, f64p]
@@ -533,4 +535,15 @@ def ransac(pairs, rnd: np.ndarray, th_sq: float = 9.0) -> RansacOut:
     inl = np.zeros(len(x1), np.uint8)
     best = lib().oracle_ransac(x1, y1, x2, y2, len(x1), rnd.reshape(-1), n_hyp, th_sq, counts, Hs, inl)
     return RansacOut(best, counts, Hs.reshape(n_hyp, 9), inl.astype(bool))
+
+
+def scale_coefficient(pairs, des=None) -> float:
+    """Eq. (1): the scaling coefficient f from image 1 to image 2 over the pairs
+    in list order; des: per-pair descriptor distances (default: the pairs'
+    'd1' field, the nearest Hamming distance)."""
+    x1, y1, x2, y2 = _xy(pairs)
+    if des is None:
+        des = pairs["d1"]
+    des = np.ascontiguousarray(des, dtype=np.int32)
+    return lib().oracle_scale_coefficient(x1, y1, x2, y2, des, len(x1))
 

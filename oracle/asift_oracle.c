@@ -25,6 +25,7 @@
  *   Sec. III-B     nearest-neighbour interpolation and scale s of the coarse stage
  *   Eq. (5)-(7)    precision, reprojection threshold, inlier ratio; RANSAC [28] (Sec. III-C)
  *   Sec. III-C     Lanczos reproduction of the best view with n = 4 (8 x 8 window)
+ *   Eq. (1)        scaling coefficient of the base-image selection (Sec. III-A)
  * ORB internals the paper does not state (pyramid, FAST-9, Harris, centroid
  * orientation, steered BRIEF) follow the ORB paper cited as [23]; where that is
  * silent, the reading chosen is stated at each function.
@@ -1288,4 +1289,26 @@ int oracle_ransac(const float *x1, const float *y1, const float *x2, const float
     for (int i = 0; i < n; ++i)
         inlier[i] = (uint8_t)(best >= 0 && oracle_reproj_sq(Hs + 9 * best, x1[i], y1[i], x2[i], y2[i]) <= th_sq);
     return best;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Base-image selection, Eq. (1) (Sec. III-A)                                */
+/* ------------------------------------------------------------------------ */
+/* Scaling coefficient from image 1 to image 2 over n matched pairs in list
+ * order: f = sum over consecutive pairs i, i+1 (i + 1 < n) of
+ *   (Dis(a_i, a_{i+1}) - Dis(b_i, b_{i+1})) * (1 - (Des(i) + Des(i+1)) / 1000)
+ * with Dis the Euclidean pixel length of the segment in each image and Des a
+ * pair's descriptor distance.  f > 0: a segment is longer in image 1, whose
+ * camera is closer to the scene.  Summed in list order in fp64. */
+double oracle_scale_coefficient(const float *x1, const float *y1, const float *x2, const float *y2,
+                                const int32_t *des, int n)
+{
+    double f = 0.0;
+    for (int i = 0; i + 1 < n; ++i) {
+        const double da = hypot((double)x1[i + 1] - (double)x1[i], (double)y1[i + 1] - (double)y1[i]);
+        const double db = hypot((double)x2[i + 1] - (double)x2[i], (double)y2[i + 1] - (double)y2[i]);
+        const double w = 1.0 - (double)(des[i] + des[i + 1]) / 1000.0;
+        f += (da - db) * w;
+    }
+    return f;
 }

@@ -985,3 +985,49 @@ def test_lanczos_a3_is_the_main_view_and_a4_differs():
         a4 = O.warp_view_lanczos(u, v, 4)
         assert np.array_equal(a4.mask, ref.mask)
         assert np.abs(a4.f64 - ref.f64).max() > 0.1
+
+
+# --------------------------------------------------------------------------
+# Base-image selection: Eq. (1)
+# --------------------------------------------------------------------------
+def _pairs_from(p1, p2, des):
+    pairs = np.zeros(len(p1), np.dtype([("x1", np.float32), ("y1", np.float32), ("x2", np.float32),
+                                         ("y2", np.float32), ("d1", np.uint16)]))
+    pairs["x1"], pairs["y1"] = p1[:, 0], p1[:, 1]
+    pairs["x2"], pairs["y2"] = p2[:, 0], p2[:, 1]
+    pairs["d1"] = des
+    return pairs
+
+
+def test_scale_coefficient_closed_form_under_a_similarity():
+    """Image 2 = image 1 scaled by k (rotated and shifted): every segment is k
+    times as long in image 2, so f = (1 - k) sum_i Dis(a_i, a_i+1) w_i, with
+    the weights w_i = 1 - (Des(i) + Des(i+1)) / 1000."""
+    rng = np.random.default_rng(95)
+    p1 = rng.uniform(0, 500, size=(300, 2)).astype(np.float32).astype(np.float64)
+    des = rng.integers(0, 120, 300)
+    for k in (0.5, 0.8, 1.0, 1.25, 2.0):
+        th = 0.7
+        R = k * np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+        p2 = p1 @ R.T + np.array([13.0, -7.0])
+        pairs = _pairs_from(p1, p2, des)
+        seg = np.hypot(*np.diff(p1, axis=0).T)
+        w = 1 - (des[:-1] + des[1:]) / 1000.0
+        expect = (1 - k) * float((seg * w).sum())
+        f = O.scale_coefficient(pairs)
+        # the fp32 storage of image 2's points moves each length by < 1e-4
+        assert abs(f - expect) <= 1e-4 * len(p1) + 1e-9 * abs(expect), (k, f, expect)
+        if k < 1:
+            assert f > 0          # image 1 shows the scene larger: it is the closer camera
+        if k > 1:
+            assert f < 0
+
+
+def test_scale_coefficient_weights_and_degenerate_lists():
+    p1 = np.array([[0, 0], [3, 4], [3, 10]], np.float64)
+    p2 = np.array([[0, 0], [0, 0], [0, 0]], np.float64)
+    # segments of length 5 and 6, weights 1 - (10 + 20)/1000 and 1 - (20 + 40)/1000
+    f = O.scale_coefficient(_pairs_from(p1, p2, np.array([10, 20, 40])))
+    assert abs(f - (5 * 0.97 + 6 * 0.94)) < 1e-12
+    assert O.scale_coefficient(_pairs_from(p1[:1], p2[:1], np.array([3]))) == 0.0
+    assert O.scale_coefficient(_pairs_from(p1[:0], p2[:0], np.zeros(0, int))) == 0.0
