@@ -419,6 +419,23 @@ ASIFT_API asift_status match_pair_inspect(const asift_ctx *ctx, int H1, int W1, 
                                 asift_keypoint **d_kp2, uint8_t **d_desc2, int32_t **d_n2,
                                 asift_match **d_match);
 
+/* Base-image selection, Eq. (1) (Sec. III-A): the scaling coefficient from
+ * image 1 to image 2 over the pairs d_pairs[0 .. min(*d_n, cap) - 1] in list
+ * order,
+ *   f = sum_{i + 1 < n} (|a_i+1 - a_i| - |b_i+1 - b_i|) (1 - (Des_i + Des_i+1) / 1000)
+ * with a_i = (x1, y1), b_i = (x2, y2) and Des_i = d1 (the pair's descriptor
+ * distance; the Hamming distance of the rBRIEF descriptors here), in fp64,
+ * summed in a fixed order.  f > 0: the scene appears larger in image 1.
+ * Computing f1 on image 1 -> 2's pairs and f2 on image 2 -> 1's, image 1 is
+ * the reference when f1 > f2.  *d_f (device) is written on `stream`.
+ * Workspace: asift_scale_coefficient_workspace_size(cap) bytes, 256-byte
+ * aligned.  d_n may point into another call's output (e.g. n_unique of an
+ * asift_eval_result, with its kept pairs as d_pairs). */
+ASIFT_API size_t asift_scale_coefficient_workspace_size(int cap);
+ASIFT_API asift_status asift_scale_coefficient(asift_ctx *ctx, const asift_pair_match *d_pairs, const int32_t *d_n,
+                                               int cap, double *d_f, void *d_workspace, size_t ws_bytes,
+                                               void *stream);
+
 /* Coarse stage, best-parameter selection (Sec. III-B): after a match_pair call
  * on d_workspace with the same sizes and configuration, d_counts[v] (v = 0 ..
  * n1 - 1, n1 = the number of image 1's views, in table order) receives the

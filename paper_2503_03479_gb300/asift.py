@@ -25,7 +25,8 @@ PATTERN_SEED = 250303479
 EXPORTED = ["asift_ctx_create", "asift_ctx_destroy", "asift_ctx_orb_cfg", "asift_ctx_pattern", "asift_view_table",
             "asift_make_view", "asift_view_table_scaled", "asift_make_view_scaled", "asift_level_size", "asift_views_bytes", "asift_views_workspace_size", "asift_views", "asift_views_nearest", "asift_views_lanczos",
             "orb_workspace_size", "orb_extract", "hamming_workspace_size", "hamming_match",
-            "match_pair_workspace_size", "match_pair", "match_pair_inspect", "match_pair_view_counts", "asift_eval_workspace_size",
+            "match_pair_workspace_size", "match_pair", "match_pair_inspect", "match_pair_view_counts", "asift_scale_coefficient_workspace_size",
+            "asift_scale_coefficient", "asift_eval_workspace_size",
             "asift_eval_pairs", "asift_read_status",
             "asift_launch_count", "asift_pattern_table", "asift_bin_table", "asift_profile_enable",
             "asift_profile_read", "hamming_match_noalloc", "asift_plan_create", "asift_plan_run",
@@ -132,6 +133,8 @@ def load_library():
         "match_pair": (i32, [vp, vp, i32, i32, i32, vp, i32, i32, i32, P(PairCfg), vp, i32, vp, vp, sz, vp]),
         "match_pair_inspect": (i32, [vp, i32, i32, i32, i32, P(PairCfg), vp, vp, vp, vp, vp, vp, vp, vp]),
         "match_pair_view_counts": (i32, [vp, i32, i32, i32, i32, P(PairCfg), vp, vp, i32, vp, vp]),
+        "asift_scale_coefficient_workspace_size": (sz, [i32]),
+        "asift_scale_coefficient": (i32, [vp, vp, vp, i32, vp, vp, sz, vp]),
         "asift_eval_workspace_size": (sz, [i32, i32]),
         "asift_eval_pairs": (i32, [vp, vp, vp, i32, vp, C.c_double, vp, i32, C.c_double, vp, vp, vp, vp, vp, sz,
                                    vp]),
@@ -480,6 +483,24 @@ class Context:
                                        _ptr(unique), _ptr(inl), _ptr(cnt) if cnt is not None else None, _ptr(res),
                                        _ptr(ws), ws.numel(), _stream()))
         return unique, inl, cnt, res
+
+    def scale_coefficient(self, out: torch.Tensor, n_out: torch.Tensor) -> torch.Tensor:
+        """Eq. (1) over match_pair's output: a device float64 tensor of one element."""
+        cap = out.numel() // PAIR_DTYPE.itemsize
+        ws = self.workspace(("scale", cap), self.L.asift_scale_coefficient_workspace_size(cap))
+        f = torch.empty(1, dtype=torch.float64, device=out.device)
+        _check("asift_scale_coefficient", self.L.asift_scale_coefficient(self._ctx, _ptr(out), _ptr(n_out), cap,
+                                                                         _ptr(f), _ptr(ws), ws.numel(), _stream()))
+        return f
+
+    def base_image(self, img1: torch.Tensor, img2: torch.Tensor, pc: PairCfg):
+        """Sec. III-A: f1 on image 1 -> 2's accepted pairs, f2 on image 2 -> 1's; the reference is
+        image 0 when f1 > f2, else image 1.  Returns (f1, f2, reference index)."""
+        f = []
+        for a, b in ((img1, img2), (img2, img1)):
+            out, n, _ = self.match_pair(a, b, pc)
+            f.append(float(self.scale_coefficient(out, n).item()))
+        return f[0], f[1], 0 if f[0] > f[1] else 1
 
     @staticmethod
     def eval_result(res: torch.Tensor) -> EvalResult:

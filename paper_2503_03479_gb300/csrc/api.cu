@@ -1189,6 +1189,21 @@ asift_status asift_eval_pairs(asift_ctx *ctx, const asift_pair_match *d_pairs, c
                                    d_hyp_counts, d_result, d_workspace, static_cast<cudaStream_t>(stream)));
 }
 
+size_t asift_scale_coefficient_workspace_size(int cap)
+{
+    if (cap < 0 || cap > (1 << 26)) return 0;
+    return scale_coeff_workspace_bytes(cap);
+}
+
+asift_status asift_scale_coefficient(asift_ctx *ctx, const asift_pair_match *d_pairs, const int32_t *d_n, int cap,
+                                     double *d_f, void *d_workspace, size_t ws_bytes, void *stream)
+{
+    if (!ctx || !d_n || !d_f || !d_workspace || cap < 0 || cap > (1 << 26) || (cap > 0 && !d_pairs) ||
+        (reinterpret_cast<uintptr_t>(d_workspace) & 255) || ws_bytes < scale_coeff_workspace_bytes(cap))
+        return ASIFT_ERR_ARG;
+    return cuda_status(launch_scale_coeff(d_pairs, d_n, cap, d_f, d_workspace, static_cast<cudaStream_t>(stream)));
+}
+
 asift_status match_pair_view_counts(asift_ctx *ctx, int H1, int W1, int H2, int W2, const asift_pair_cfg *cfg,
                                     void *d_workspace, int32_t *d_counts, int n_counts, int32_t *d_best, void *stream)
 {

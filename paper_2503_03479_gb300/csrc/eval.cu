@@ -477,6 +477,50 @@ inlier_kernel(const EvalProblem *__restrict__ many, int n_probs, const EvalProbl
     if (threadIdx.x == 0 && t) atomicAdd(&P.res->n_inliers, t);
 }
 
+// Eq. (1): the scaling coefficient over consecutive pairs of the list (Sec.
+// III-A).  Each block sums the terms of its 256 segments in a fixed tree
+// order; one block then sums the partials in block order, so the result does
+// not depend on scheduling.
+__device__ __forceinline__ double block_sum_fixed(double v, double *sh)
+{
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = kEvalBlock / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    return sh[0];
+}
+
+__global__ void __launch_bounds__(kEvalBlock)
+scale_coeff_partial_kernel(const asift_pair_match *__restrict__ pairs, const int32_t *__restrict__ d_n, int cap,
+                           double *__restrict__ partials)
+{
+    __shared__ double sh[kEvalBlock];
+    const int n = pair_count(d_n, cap);
+    const int i = blockIdx.x * kEvalBlock + threadIdx.x;
+    double term = 0.0;
+    if (i + 1 < n) {
+        const asift_pair_match a = pairs[i], b = pairs[i + 1];
+        const double da = hypot((double)b.x1 - (double)a.x1, (double)b.y1 - (double)a.y1);
+        const double db = hypot((double)b.x2 - (double)a.x2, (double)b.y2 - (double)a.y2);
+        const double w = 1.0 - (double)((int)a.d1 + (int)b.d1) / 1000.0;
+        term = (da - db) * w;
+    }
+    const double t = block_sum_fixed(term, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kEvalBlock)
+scale_coeff_final_kernel(const double *__restrict__ partials, int n_part, double *__restrict__ f)
+{
+    __shared__ double sh[kEvalBlock];
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < n_part; k += kEvalBlock) acc += partials[k];
+    const double t = block_sum_fixed(acc, sh);
+    if (threadIdx.x == 0) *f = t;
+}
+
 // ---------------------------------------------------------------- host side
 static unsigned table_slots(int cap)
 {
@@ -586,6 +630,19 @@ cudaError_t launch_eval(const asift_pair_match *d_pairs, const int32_t *d_n, int
     P.has_H = h_H_true != nullptr;
     for (int c = 0; c < 9; ++c) P.Ht[c] = h_H_true ? h_H_true[c] : 0.0;
     return launch_eval_list(nullptr, P, 1, P.n_blk, P.n_blk, n_hyp, d_rnd, th_sq, ransac_th_sq, P.has_H, s);
+}
+
+size_t scale_coeff_workspace_bytes(int cap) { return sizeof(double) * (size_t)eval_blocks(cap); }
+
+cudaError_t launch_scale_coeff(const asift_pair_match *d_pairs, const int32_t *d_n, int cap, double *d_f, void *d_ws,
+                               cudaStream_t s)
+{
+    const int blocks = eval_blocks(cap);
+    double *partials = static_cast<double *>(d_ws);
+    scale_coeff_partial_kernel<<<blocks, kEvalBlock, 0, s>>>(d_pairs, d_n, cap, partials);
+    scale_coeff_final_kernel<<<1, kEvalBlock, 0, s>>>(partials, blocks, d_f);
+    note_launch(2);
+    return cudaGetLastError();
 }
 
 // ---- batched form: the pairs of a plan, one launch per stage

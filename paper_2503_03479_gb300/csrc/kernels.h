@@ -77,6 +77,9 @@ cudaError_t launch_eval(const asift_pair_match *d_pairs, const int32_t *d_n, int
                         double th_sq, const uint32_t *d_rnd, int n_hyp, double ransac_th_sq,
                         asift_pair_match *d_unique, uint8_t *d_inlier, int32_t *d_hyp_counts,
                         asift_eval_result *d_res, void *d_ws, cudaStream_t s);
+size_t scale_coeff_workspace_bytes(int cap);
+cudaError_t launch_scale_coeff(const asift_pair_match *d_pairs, const int32_t *d_n, int cap, double *d_f, void *d_ws,
+                               cudaStream_t s);
 size_t eval_batch_workspace_bytes(const int *caps, int n, int n_hyp);
 cudaError_t launch_eval_batch(asift_pair_match *const *pairs, int32_t *d_ns, const int *caps, int n,
                               const double *h_H_true, double th_sq, const uint32_t *d_rnd, int n_hyp,

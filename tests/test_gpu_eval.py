@@ -205,3 +205,52 @@ def test_batched_evaluation_of_a_plan(A):
     res = plan.evaluate()
     assert all(r.r_num == -1 and r.best_hyp == -1 and r.n_inliers == 0 for r in res)
     plan.close()
+
+
+def _scale_terms_abs(pairs):
+    x1, y1 = pairs["x1"].astype(np.float64), pairs["y1"].astype(np.float64)
+    x2, y2 = pairs["x2"].astype(np.float64), pairs["y2"].astype(np.float64)
+    return float(np.abs(np.hypot(np.diff(x1), np.diff(y1)) - np.hypot(np.diff(x2), np.diff(y2))).sum())
+
+
+@pytest.mark.parametrize("n,k", [(0, 1.0), (1, 1.0), (2, 0.5), (257, 0.8), (5000, 1.3)])
+def test_scale_coefficient_parity(A, n, k):
+    """Eq. (1) on the GPU against the oracle (fp64 on both sides, different
+    summation orders: within 1e-9 of the sum of |terms|)."""
+    ctx = A.Context()
+    rng = np.random.default_rng(540 + n)
+    p1 = rng.uniform(0, 900, size=(n, 2))
+    th = 0.4
+    R = k * np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    p2 = p1 @ R.T + rng.normal(0, 0.5, size=(n, 2))
+    pairs = np.zeros(n, A.PAIR_DTYPE)
+    pairs["x1"], pairs["y1"], pairs["x2"], pairs["y2"] = p1[:, 0], p1[:, 1], p2[:, 0], p2[:, 1]
+    pairs["d1"] = rng.integers(0, 100, n)
+    out, cnt = _upload(A, pairs, cap=max(n, 4))
+    f = float(ctx.scale_coefficient(out, cnt).item())
+    ref = O.scale_coefficient(pairs)
+    assert abs(f - ref) <= 1e-9 * _scale_terms_abs(pairs) + 1e-9, (f, ref)
+    if n > 100:
+        assert (f > 0) == (k < 1)
+
+
+def test_base_image_selection_on_match_pair_outputs(A):
+    """f1 and f2 on the accepted pairs of both matching directions equal the
+    oracle's on the same pairs, and the image showing the scene larger (a
+    1.6x magnified view of a texture, against the texture) is chosen as the
+    reference (Sec. III-A)."""
+    ctx = A.Context(n_levels=8, n_features=500)
+    tex = synth.texture(240, 320, 77)
+    big = np.ascontiguousarray(O.warp_view(tex, O.make_view(240, 320, 1.0, 0.0, 1.6)).u8)
+    pc = ctx.pair_cfg(kmax=0)
+    f = []
+    for a, b in ((big, tex), (tex, big)):
+        out, n, _ = ctx.match_pair(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), pc)
+        fg = float(ctx.scale_coefficient(out, n).item())
+        pairs = ctx.pairs_host(out, n)
+        ref = O.scale_coefficient(pairs)
+        assert abs(fg - ref) <= 1e-9 * _scale_terms_abs(pairs) + 1e-9
+        f.append(fg)
+    f1, f2, reference = ctx.base_image(torch.from_numpy(big).cuda(), torch.from_numpy(tex).cuda(), pc)
+    assert (f1, f2) == (f[0], f[1])
+    assert reference == 0 and f1 > 0 > f2
