@@ -696,10 +696,10 @@ def run_ours(args):
                 best_of.append({"view": b, "t": v.t, "phi_deg": v.phi_deg, "s": v.s,
                                 "matches": int(counts[b].item())})
             px = sum(v.Wv * v.Hv for v in vc)
-            line = {"pairs_per_s": 1e3 / msc, "ms_per_pair": msc, "views_reference": len(vc), "views_target": 1,
+            cline = {"pairs_per_s": 1e3 / msc, "ms_per_pair": msc, "views_reference": len(vc), "views_target": 1,
                     "view_pixels": int(px), "stage_ms": stc, "best": best_of}
             if nearest:
-                line["warp_gpix_per_s"] = px / (stc["warp"] / 1e3) / 1e9
+                cline["warp_gpix_per_s"] = px / (stc["warp"] / 1e3) / 1e9
                 # the precise stage's Lanczos-4 (8 x 8) reproduction of pair 0's best group (Sec. III-C)
                 bv = [vc[best_of[0]["view"]]]
                 for _ in range(2):
@@ -711,14 +711,14 @@ def run_ours(args):
                     ctx.views(d1[0], bv, lanczos=4)
                 e1.record(stream)
                 torch.cuda.synchronize()
-                line["precise_lanczos4_view"] = {"ms": e0.elapsed_time(e1) / 10, "pixels": bv[0].Wv * bv[0].Hv,
+                cline["precise_lanczos4_view"] = {"ms": e0.elapsed_time(e1) / 10, "pixels": bv[0].Wv * bv[0].Hv,
                                                  "canvas_pixels": bv[0].Wr * bv[0].Hr}
             else:
                 f_clk = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
                 flops = sum(warp_flops(v) for v in vc)     # the target's identity view costs no arithmetic
-                line["roofline_warp"] = _alu_roofline(flops, stc["warp"],
+                cline["roofline_warp"] = _alu_roofline(flops, stc["warp"],
                                                       SM_COUNT * FP32_LANES_PER_SM * 2 * f_clk / 1e12, f_clk)
-            coarse[name] = line
+            coarse[name] = cline
             del wsc, outc
 
     # ---- evaluation of the accepted pairs (Sec. III-C, Sec. IV-B): duplicate

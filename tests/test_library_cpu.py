@@ -81,6 +81,18 @@ def test_bad_arguments_are_rejected(A):
     assert L.hamming_match(None, None, 0, None, None, 0, None, 4, 5, None, None, None, None, 0, None) == A.ASIFT_ERR_ARG
     assert L.asift_read_status(None, 0, None, None) == A.ASIFT_ERR_ARG
     assert L.match_pair_view_counts(None, 10, 10, 10, 10, None, None, None, 0, None, None) == A.ASIFT_ERR_ARG
+    assert L.asift_views_nearest(None, None, 10, 10, 10, None, 0, None, None, None, None, None, 0,
+                                 None) == A.ASIFT_ERR_ARG
+    for a in (3, 4, 2, 5):
+        assert L.asift_views_lanczos(None, a, None, 10, 10, 10, None, 0, None, None, None, None, None, 0,
+                                     None) == A.ASIFT_ERR_ARG
+    assert L.asift_eval_pairs(None, None, None, 0, None, 3.0, None, 0, 9.0, None, None, None, None, None, 0,
+                              None) == A.ASIFT_ERR_ARG
+    assert L.asift_scale_coefficient(None, None, None, 0, None, None, 0, None) == A.ASIFT_ERR_ARG
+    assert L.asift_plan_view_counts(None, 0, None, 0, None, None) == A.ASIFT_ERR_ARG
+    assert L.asift_plan_eval(None, None, 3.0, None, 0, 9.0, None, 0, None) == A.ASIFT_ERR_ARG
+    assert L.asift_plan_eval_outputs(None, None, 0, 0, None, None, None, None) == A.ASIFT_ERR_ARG
+    assert L.asift_plan_eval_workspace_size(None, 16) == 0
 
 
 def test_context_without_gpu_fails_loudly(A):
@@ -98,6 +110,12 @@ def test_workspace_sizes_are_monotone(A):
     L = A.load_library()
     assert L.hamming_workspace_size(1000, 2000) < L.hamming_workspace_size(40000, 40000)
     assert L.asift_views_workspace_size(240, 320, 10) < L.asift_views_workspace_size(768, 1024, 43)
+    assert 0 < L.asift_eval_workspace_size(0, 0) <= L.asift_eval_workspace_size(1000, 64) \
+        < L.asift_eval_workspace_size(43000, 1024)
+    assert L.asift_eval_workspace_size(-1, 0) == 0 and L.asift_eval_workspace_size(10, -1) == 0
+    assert L.asift_eval_workspace_size(1 << 27, 1) == 0 and L.asift_eval_workspace_size(10, (1 << 20) + 1) == 0
+    assert 0 < L.asift_scale_coefficient_workspace_size(0) <= L.asift_scale_coefficient_workspace_size(43000)
+    assert L.asift_scale_coefficient_workspace_size(-5) == 0
 
 
 def test_view_sampling_matches_the_printed_rule(A):
