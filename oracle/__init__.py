@@ -21,7 +21,7 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "asift_oracle.c")
+_SRCS = [os.path.join(_HERE, "asift_oracle.c"), os.path.join(_HERE, "sift_oracle.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
@@ -33,10 +33,11 @@ PATTERN_SEED = 250303479
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction, no fast-math)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(f) for f in _SRCS)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off",
-                               "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+                               "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, *_SRCS, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -54,6 +55,9 @@ class ODView(C.Structure):
                 ("Wv", C.c_int32), ("Hv", C.c_int32), ("K", C.c_int32), ("pad", C.c_int32),
                 ("t", C.c_double), ("phi", C.c_double), ("tx", C.c_double), ("ty", C.c_double)]
 
+
+SIFT_KP_DTYPE = np.dtype([("x", np.float64), ("y", np.float64), ("sigma", np.float64), ("angle", np.float64),
+                          ("response", np.float64), ("octave", np.int32), ("layer", np.int32)])
 
 KP_DTYPE = np.dtype([("x", np.int16), ("y", np.int16), ("level", np.uint8), ("bin", np.uint8),
                      ("pad", np.int16), ("r25", np.int64)])
@@ -133,6 +137,12 @@ def lib():
         L.oracle_ransac.restype = C.c_int
         L.oracle_scale_coefficient.argtypes = [f32p, f32p, f32p, f32p, i32p, C.c_int]
         L.oracle_scale_coefficient.restype = C.c_double
+        L.oracle_gauss_blur.argtypes = [f64p, C.c_int, C.c_int, C.c_double, f64p]
+        L.oracle_sift.argtypes = [u8p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
+        L.oracle_sift.restype = C.c_int
+        L.oracle_sift_match.argtypes = [f32p, C.c_int, f32p, C.c_int, C.c_double, i32p, f64p, f64p, u8p]
+        L.oracle_sizeof_sift_kp.restype = C.c_int
+        assert L.oracle_sizeof_sift_kp() == SIFT_KP_DTYPE.itemsize
         assert L.oracle_sizeof_dview() == C.sizeof(ODView)
         L.oracle_dwarp_fwd.argtypes = [f64p, P(ODView), f64p]
         L.oracle_dwarp_vjp.argtypes = [f64p, P(ODView), f64p, f64p, f64p]
@@ -546,4 +556,51 @@ def scale_coefficient(pairs, des=None) -> float:
         des = pairs["d1"]
     des = np.ascontiguousarray(des, dtype=np.int32)
     return lib().oracle_scale_coefficient(x1, y1, x2, y2, des, len(x1))
+
+
+# ---------------------------------------------------------------- SIFT (the precise stage's detector)
+def gauss_blur(u: np.ndarray, sigma: float) -> np.ndarray:
+    """Separable Gaussian, radius int(4 sigma + 0.5), normalised taps, edge pixels replicated."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    H, W = u.shape
+    out = np.zeros_like(u)
+    lib().oracle_gauss_blur(u, W, H, float(sigma), out)
+    return out
+
+
+@dataclass
+class SiftOut:
+    kps: np.ndarray          # SIFT_KP_DTYPE
+    desc: np.ndarray         # float32 (n, 128), unit L2 norm
+
+
+def sift(img: np.ndarray, max_kp: int = 5000) -> SiftOut:
+    """Lowe's SIFT on an 8-bit image: the strongest max_kp keypoints and their descriptors."""
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    H, W = img.shape
+    kps = np.zeros(max_kp, SIFT_KP_DTYPE)
+    desc = np.zeros((max_kp, 128), np.float32)
+    n = lib().oracle_sift(img, W, H, max_kp, kps.ctypes.data, desc.ctypes.data)
+    return SiftOut(kps[:n].copy(), desc[:n].copy())
+
+
+@dataclass
+class SiftMatchOut:
+    best: np.ndarray
+    d1: np.ndarray           # squared L2 distances
+    d2: np.ndarray
+    accepted: np.ndarray
+
+
+def sift_match(q: np.ndarray, t: np.ndarray, ratio: float = 0.8) -> SiftMatchOut:
+    q = np.ascontiguousarray(q, dtype=np.float32)
+    t = np.ascontiguousarray(t, dtype=np.float32)
+    nq, nt = len(q), len(t)
+    best = np.zeros(nq, np.int32)
+    d1 = np.zeros(nq)
+    d2 = np.zeros(nq)
+    acc = np.zeros(nq, np.uint8)
+    lib().oracle_sift_match(q.reshape(-1) if nq else np.zeros(1, np.float32), nq,
+                            t.reshape(-1) if nt else np.zeros(1, np.float32), nt, float(ratio), best, d1, d2, acc)
+    return SiftMatchOut(best, d1, d2, acc.astype(bool))
 
