@@ -748,6 +748,20 @@ def run_ours(args):
                 "accepted": r.n_pairs, "unique": r.n_unique, "precision": r.r_num / max(r.n_unique, 1),
                 "inlier_ratio": r.n_inliers / max(r.n_unique, 1), "ms": e0.elapsed_time(e1) / reps})
 
+    # ---- SIFT of the precise stage (Sec. III-C) on image 1 of pair 0
+    sift_line = None
+    if args.sift_reps > 0:
+        for _ in range(2):
+            ctx.sift_raw(d1[0])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.sift_reps):
+            _, _, n_sift = ctx.sift_raw(d1[0])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sift_line = {"image": f"{W}x{H}", "ms": e0.elapsed_time(e1) / args.sift_reps, "keypoints": int(n_sift.item())}
+
     # ---- end to end through the C ABI with host buffers
     h1 = [torch.from_numpy(p.img1).pin_memory() for p in pairs]
     h2 = [torch.from_numpy(p.img2).pin_memory() for p in pairs]
@@ -795,6 +809,7 @@ def run_ours(args):
                 "differentiable": diff,
                 "coarse_stage": coarse,
                 "evaluation": evaluation,
+                "sift": sift_line,
                 "roofline": roofline, "rooflines": rooflines, "match_engine": ctx.match_engine,
                 "match_engines": engines,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
@@ -819,6 +834,7 @@ def main():
     ap.add_argument("--diff-views", type=int, default=256, help="views of the differentiable-warp timing (0: skip)")
     ap.add_argument("--coarse-steps", type=int, default=20, help="steps of the coarse-stage timing (0: skip)")
     ap.add_argument("--eval-hyp", type=int, default=1024, help="RANSAC hypotheses of the evaluation timing (0: skip)")
+    ap.add_argument("--sift-reps", type=int, default=5, help="repetitions of the SIFT timing (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

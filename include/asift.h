@@ -419,6 +419,42 @@ ASIFT_API asift_status match_pair_inspect(const asift_ctx *ctx, int H1, int W1, 
                                 asift_keypoint **d_kp2, uint8_t **d_desc2, int32_t **d_n2,
                                 asift_match **d_match);
 
+/*
+ * asift_sift -- SIFT (Lowe 2004) keypoints and descriptors of one 8-bit image,
+ * the detector of the precise stage (Sec. III-C), fp32: the image / 255
+ * doubled (centre-aligned bilinear), blurred to sigma0 = 1.6 from an assumed
+ * 2 x 0.5; S = 3 intervals per octave, floor(log2 min(2W, 2H)) - 3 octaves
+ * (at most 12), each started from image S of the previous subsampled by 2;
+ * strict 26-neighbour DoG extrema 5 px from the border with |D| > 0.5 x 0.04 /
+ * S; quadratic refinement (at most 5 moves), |D^| >= 0.04 / S, edge ratio
+ * tr^2 / det < 11^2 / 10; 36-bin orientation histograms (window 1.5 sigma,
+ * radius 3 x 1.5 sigma, [1 4 6 4 1] / 16 smoothing, every peak within 80% of
+ * the highest, parabolic refinement; angle of the gradient atan2(gy, gx) in
+ * degrees, y down); 4 x 4 x 8 descriptors over the window rotated to the
+ * orientation (bins 3 sigma wide, trilinear spreading, Gaussian weight of
+ * half the window), unit-normalised, clamped at 0.2, renormalised.
+ * d_kp[max_kp] and d_desc[max_kp x 128] (device) receive the keypoints in
+ * an unspecified order; *d_n (device) the number found: when it exceeds
+ * max_kp, which max_kp are written is unspecified (refined extrema are held
+ * up to max(max_kp, W H / 2 + 1024) before their orientations).  Workspace:
+ * asift_sift_workspace_size(H, W, max_kp) bytes, 256-byte aligned.  Errors:
+ * ASIFT_ERR_ARG for NULL or misaligned buffers, W or H below 16 or above
+ * 16384, max_kp outside [1, 2^20].
+ */
+typedef struct {
+    float x, y;             /* original image coordinates                      */
+    float sigma;            /* scale in original image pixels                  */
+    float angle;            /* degrees, [0, 360)                               */
+    float response;         /* |D| at the refined extremum                     */
+    int32_t octave, layer;
+    float xo, yo, so;       /* position and scale in the octave's pixels       */
+    int32_t pad[2];
+} asift_sift_kp;
+ASIFT_API size_t asift_sift_workspace_size(int H, int W, int max_kp);
+ASIFT_API asift_status asift_sift(asift_ctx *ctx, const uint8_t *d_img, int H, int W, int pitch, int max_kp,
+                                  asift_sift_kp *d_kp, float *d_desc, int32_t *d_n, void *d_workspace,
+                                  size_t ws_bytes, void *stream);
+
 /* Base-image selection, Eq. (1) (Sec. III-A): the scaling coefficient from
  * image 1 to image 2 over the pairs d_pairs[0 .. min(*d_n, cap) - 1] in list
  * order,

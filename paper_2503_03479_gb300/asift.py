@@ -25,7 +25,7 @@ PATTERN_SEED = 250303479
 EXPORTED = ["asift_ctx_create", "asift_ctx_destroy", "asift_ctx_orb_cfg", "asift_ctx_pattern", "asift_view_table",
             "asift_make_view", "asift_view_table_scaled", "asift_make_view_scaled", "asift_level_size", "asift_views_bytes", "asift_views_workspace_size", "asift_views", "asift_views_nearest", "asift_views_lanczos",
             "orb_workspace_size", "orb_extract", "hamming_workspace_size", "hamming_match",
-            "match_pair_workspace_size", "match_pair", "match_pair_inspect", "match_pair_view_counts", "asift_scale_coefficient_workspace_size",
+            "match_pair_workspace_size", "match_pair", "match_pair_inspect", "match_pair_view_counts", "asift_sift_workspace_size", "asift_sift", "asift_scale_coefficient_workspace_size",
             "asift_scale_coefficient", "asift_eval_workspace_size",
             "asift_eval_pairs", "asift_read_status",
             "asift_launch_count", "asift_pattern_table", "asift_bin_table", "asift_profile_enable",
@@ -90,6 +90,9 @@ class WarpShape(C.Structure):
 
 KP_DTYPE = np.dtype([("x", np.int16), ("y", np.int16), ("level", np.uint8), ("bin", np.uint8),
                      ("view", np.uint16), ("r25", np.int64)])
+SIFT_KP_DTYPE = np.dtype([("x", np.float32), ("y", np.float32), ("sigma", np.float32), ("angle", np.float32),
+                          ("response", np.float32), ("octave", np.int32), ("layer", np.int32), ("xo", np.float32),
+                          ("yo", np.float32), ("so", np.float32), ("pad", np.int32, 2)])
 MATCH_DTYPE = np.dtype([("best", np.int32), ("d1", np.uint16), ("d2", np.uint16)])
 PAIR_DTYPE = np.dtype([("x1", np.float32), ("y1", np.float32), ("x2", np.float32), ("y2", np.float32),
                        ("q", np.int32), ("t", np.int32), ("d1", np.uint16), ("d2", np.uint16)])
@@ -133,6 +136,8 @@ def load_library():
         "match_pair": (i32, [vp, vp, i32, i32, i32, vp, i32, i32, i32, P(PairCfg), vp, i32, vp, vp, sz, vp]),
         "match_pair_inspect": (i32, [vp, i32, i32, i32, i32, P(PairCfg), vp, vp, vp, vp, vp, vp, vp, vp]),
         "match_pair_view_counts": (i32, [vp, i32, i32, i32, i32, P(PairCfg), vp, vp, i32, vp, vp]),
+        "asift_sift_workspace_size": (sz, [i32, i32, i32]),
+        "asift_sift": (i32, [vp, vp, i32, i32, i32, i32, vp, vp, vp, vp, sz, vp]),
         "asift_scale_coefficient_workspace_size": (sz, [i32]),
         "asift_scale_coefficient": (i32, [vp, vp, vp, i32, vp, vp, sz, vp]),
         "asift_eval_workspace_size": (sz, [i32, i32]),
@@ -483,6 +488,31 @@ class Context:
                                        _ptr(unique), _ptr(inl), _ptr(cnt) if cnt is not None else None, _ptr(res),
                                        _ptr(ws), ws.numel(), _stream()))
         return unique, inl, cnt, res
+
+    def sift_raw(self, img: torch.Tensor, max_kp: int = 20000):
+        """asift_sift on a uint8 CUDA image: device (keypoints, descriptors, count) in append order."""
+        assert img.is_cuda and img.dtype == torch.uint8 and img.dim() == 2
+        H, W = img.shape
+        nbytes = self.L.asift_sift_workspace_size(H, W, max_kp)
+        if nbytes == 0:
+            raise AsiftError("asift_sift_workspace_size", ASIFT_ERR_ARG)
+        ws = self.workspace(("sift", H, W, max_kp), nbytes)
+        kp = torch.empty(max_kp * SIFT_KP_DTYPE.itemsize, dtype=torch.uint8, device=img.device)
+        desc = torch.empty((max_kp, 128), dtype=torch.float32, device=img.device)
+        n = torch.zeros(1, dtype=torch.int32, device=img.device)
+        _check("asift_sift", self.L.asift_sift(self._ctx, _ptr(img), H, W, img.stride(0), max_kp, _ptr(kp),
+                                               _ptr(desc), _ptr(n), _ptr(ws), ws.numel(), _stream()))
+        return kp, desc, n
+
+    def sift(self, img: torch.Tensor, max_kp: int = 20000):
+        """SIFT keypoints (SIFT_KP_DTYPE) and descriptors (float32, n x 128), host copies sorted by
+        response (descending), then y, x, angle."""
+        kp, desc, n = self.sift_raw(img, max_kp)
+        k = min(int(n.item()), max_kp)
+        kps = kp[: k * SIFT_KP_DTYPE.itemsize].cpu().numpy().view(SIFT_KP_DTYPE)
+        d = desc[:k].cpu().numpy()
+        order = np.lexsort((kps["angle"], kps["x"], kps["y"], -kps["response"]))
+        return kps[order], d[order]
 
     def scale_coefficient(self, out: torch.Tensor, n_out: torch.Tensor) -> torch.Tensor:
         """Eq. (1) over match_pair's output: a device float64 tensor of one element."""

@@ -1189,6 +1189,23 @@ asift_status asift_eval_pairs(asift_ctx *ctx, const asift_pair_match *d_pairs, c
                                    d_hyp_counts, d_result, d_workspace, static_cast<cudaStream_t>(stream)));
 }
 
+size_t asift_sift_workspace_size(int H, int W, int max_kp)
+{
+    if (H < 16 || W < 16 || H > 16384 || W > 16384 || max_kp < 1 || max_kp > (1 << 20)) return 0;
+    return sift_workspace_bytes(W, H, max_kp);
+}
+
+asift_status asift_sift(asift_ctx *ctx, const uint8_t *d_img, int H, int W, int pitch, int max_kp, asift_sift_kp *d_kp,
+                        float *d_desc, int32_t *d_n, void *d_workspace, size_t ws_bytes, void *stream)
+{
+    if (!ctx || !d_img || !d_kp || !d_desc || !d_n || !d_workspace || H < 16 || W < 16 || H > 16384 || W > 16384 ||
+        pitch < W || max_kp < 1 || max_kp > (1 << 20) || (reinterpret_cast<uintptr_t>(d_workspace) & 255) ||
+        ws_bytes < sift_workspace_bytes(W, H, max_kp))
+        return ASIFT_ERR_ARG;
+    return cuda_status(launch_sift(d_img, W, H, pitch, max_kp, d_kp, d_desc, d_n, d_workspace,
+                                   static_cast<cudaStream_t>(stream)));
+}
+
 size_t asift_scale_coefficient_workspace_size(int cap)
 {
     if (cap < 0 || cap > (1 << 26)) return 0;

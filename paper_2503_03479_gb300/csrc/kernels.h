@@ -77,6 +77,10 @@ cudaError_t launch_eval(const asift_pair_match *d_pairs, const int32_t *d_n, int
                         double th_sq, const uint32_t *d_rnd, int n_hyp, double ransac_th_sq,
                         asift_pair_match *d_unique, uint8_t *d_inlier, int32_t *d_hyp_counts,
                         asift_eval_result *d_res, void *d_ws, cudaStream_t s);
+// sift.cu
+size_t sift_workspace_bytes(int W, int H, int max_kp);
+cudaError_t launch_sift(const uint8_t *d_img, int W, int H, int pitch, int max_kp, asift_sift_kp *d_kp, float *d_desc,
+                        int32_t *d_n, void *d_ws, cudaStream_t s);
 size_t scale_coeff_workspace_bytes(int cap);
 cudaError_t launch_scale_coeff(const asift_pair_match *d_pairs, const int32_t *d_n, int cap, double *d_f, void *d_ws,
                                cudaStream_t s);
