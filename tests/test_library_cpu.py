@@ -93,6 +93,9 @@ def test_bad_arguments_are_rejected(A):
     assert L.asift_plan_eval(None, None, 3.0, None, 0, 9.0, None, 0, None) == A.ASIFT_ERR_ARG
     assert L.asift_plan_eval_outputs(None, None, 0, 0, None, None, None, None) == A.ASIFT_ERR_ARG
     assert L.asift_plan_eval_workspace_size(None, 16) == 0
+    assert L.asift_sift(None, None, 100, 100, 100, 10, None, None, None, None, 0, None) == A.ASIFT_ERR_ARG
+    assert L.asift_sift_workspace_size(8, 100, 10) == 0 and L.asift_sift_workspace_size(100, 100, 0) == 0
+    assert 0 < L.asift_sift_workspace_size(240, 320, 100) < L.asift_sift_workspace_size(768, 1024, 100)
 
 
 def test_context_without_gpu_fails_loudly(A):
