@@ -570,6 +570,47 @@ class Context:
         return kp1, d1, kp2, d2, m
 
 
+class TuningCache:
+    """Autotuner results kept across runs in a JSON file: one launch-shape choice
+    (Plan.tuning()) per workload key, so that a later plan over the same
+    workload skips the search (Plan(..., tuning=cache.get(key)))."""
+
+    FIELDS = ("warp_grid", "pyramid_grid", "detect_grid", "match_grid", "match_target_items", "match_engine")
+
+    def __init__(self, path: str):
+        self.path = path
+        self._d: dict = {}
+        if os.path.exists(path):
+            import json
+            with open(path) as f:
+                self._d = json.load(f)
+
+    @staticmethod
+    def key(shapes, kmax: int, n_levels: int, n_features: int, device: str, coarse: bool = False,
+            nearest: bool = False) -> str:
+        """The workload: every pair's (H1, W1, H2, W2), the view and ORB configuration and the device."""
+        dims = ";".join(",".join(str(int(v)) for v in s) for s in shapes)
+        return f"{device}|k{kmax}|L{n_levels}|N{n_features}|c{int(coarse)}|n{int(nearest)}|{dims}"
+
+    def get(self, key: str):
+        t = self._d.get(key)
+        if t is None:
+            return None
+        if set(t) != set(self.FIELDS) or not all(isinstance(v, int) and v >= 0 for v in t.values()):
+            return None                      # written by another version: search again
+        return dict(t)
+
+    def put(self, key: str, tuning: dict):
+        if set(tuning) != set(self.FIELDS):
+            raise ValueError("not a plan tuning")
+        self._d[key] = {k: int(tuning[k]) for k in self.FIELDS}
+        import json
+        tmp = f"{self.path}.tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(self._d, f, indent=1, sort_keys=True)
+        os.replace(tmp, self.path)
+
+
 class Plan:
     """Batched form: all views of many pairs, one launch per stage, replayed
     from a CUDA graph.  The images (uint8 CUDA tensors) are captured by

@@ -158,3 +158,26 @@ def test_scaled_view_arguments_are_checked(A):
     v = A.ViewDesc()
     assert L.asift_make_view_scaled(100, 100, 2.0, 10.0, 0.5, C.byref(v)) == A.ASIFT_ERR_ARG
     assert L.asift_make_view_scaled(100, 100, 2.0, 10.0, 9.0, C.byref(v)) == A.ASIFT_ERR_ARG
+
+
+def test_tuning_cache_round_trip(A, tmp_path):
+    """The autotuner's choice persists per workload key; entries of another
+    shape are ignored (searched again)."""
+    path = str(tmp_path / "tuning.json")
+    c = A.TuningCache(path)
+    key = A.TuningCache.key([(768, 1024, 768, 1024), (480, 640, 360, 480)], 5, 8, 1000, "GB300")
+    other = A.TuningCache.key([(768, 1024, 768, 1024)], 5, 8, 1000, "GB300", coarse=True)
+    assert key != other and c.get(key) is None
+    t = {"warp_grid": 456, "pyramid_grid": 0, "detect_grid": 912, "match_grid": 152, "match_target_items": 4,
+         "match_engine": A.MATCH_TENSOR_CORES}
+    c.put(key, t)
+    assert A.TuningCache(path).get(key) == t and A.TuningCache(path).get(other) is None
+    # the fields of the C struct, nothing else
+    assert set(A.TuningCache.FIELDS) == set(A.Tuning().as_dict())
+    with pytest.raises(ValueError):
+        c.put(other, {"warp_grid": 1})
+    import json
+    raw = json.load(open(path))
+    raw[other] = {"warp_grid": -1}
+    json.dump(raw, open(path, "w"))
+    assert A.TuningCache(path).get(other) is None
