@@ -21,6 +21,10 @@
 //      and inlier_kernel.
 // Every fp64 step is one IEEE operation (the _rn intrinsics are never fused),
 // so each decision is taken on exactly the values the written order gives.
+// Each launch serves a list of problems (one per image pair: all pairs of a
+// plan, or one pair passed by value), so a batch costs one launch per stage.
+// Also here: the scaling coefficient of Eq. (1) (Sec. III-A), a fixed-order
+// fp64 reduction over consecutive pairs.
 #include <algorithm>
 #include <cmath>
 #include <vector>
