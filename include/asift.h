@@ -436,7 +436,9 @@ ASIFT_API asift_status match_pair_inspect(const asift_ctx *ctx, int H1, int W1, 
  * d_kp[max_kp] and d_desc[max_kp x 128] (device) receive the keypoints in
  * an unspecified order; *d_n (device) the number found: when it exceeds
  * max_kp, which max_kp are written is unspecified (refined extrema are held
- * up to max(max_kp, W H / 2 + 1024) before their orientations).  Workspace:
+ * up to max(max_kp, W H / 2 + 1024) before their orientations).  Descriptor
+ * histograms accumulate with shared-memory atomics, so their last bits can
+ * differ between runs; keypoints do not.  Workspace:
  * asift_sift_workspace_size(H, W, max_kp) bytes, 256-byte aligned.  Errors:
  * ASIFT_ERR_ARG for NULL or misaligned buffers, W or H below 16 or above
  * 16384, max_kp outside [1, 2^20].

@@ -17,7 +17,9 @@
 //   5. sift_desc_kernel: one CTA per keypoint: the 4 x 4 x 8 histogram of
 //      the rotated window in shared memory (trilinear spreading), normalised,
 //      clamped at 0.2, renormalised.
-// The keypoint order is that of the appends; callers sort by response.
+// The keypoint order is that of the appends; callers sort by response.  The
+// descriptor sums are shared-memory float atomics: their last bits depend on
+// the order of the adds.
 #include <algorithm>
 #include <cmath>
 #include <vector>
