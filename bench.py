@@ -14,10 +14,11 @@ The JSON line reports image pairs/s (views/s = 86 x pairs/s beside it), with
 inputs resident in HBM; `e2e` is the same metric through the C ABI with the
 images copied from pinned host memory and the accepted pairs copied back inside
 the timed region.  `roofline` is for the stage that takes longest (the view
-simulation: FP32 arithmetic bound), `rooflines` for it and the matcher
-(tensor cores, fp8 dense peak); `cpu_baseline` is the CPU oracle timed on a bounded
-sample of the same workload.  `--impl reference` times the CPU oracle as the
-reference arm.
+simulation: FP32 arithmetic bound), `rooflines` for it, the matcher (tensor
+cores, fp8 dense peak) and the FAST/Harris/NMS and pyramid stages (HBM, on
+their algorithmic bytes); `cpu_baseline` is the CPU oracle timed on one whole
+pair with every host core (and with one).  `--impl reference` times the CPU
+oracle on whole pairs as the reference arm.
 """
 from __future__ import annotations
 
@@ -87,19 +88,13 @@ def _mixed_one(seed: int, index: int):
 
 
 def _large_one(seed: int, index: int):
-    """A 4096x3072 pair of the large extreme-tilt batch: the texture generator
-    at half size upsampled 2x (the full-size 2x canonical texture takes
-    minutes to draw), image 2 = image 1 under an affine tilt t ~ U[2, 8.2]
-    (absolute tilt up to 83 deg) at a random angle."""
-    import math
+    """A 4096x3072 pair of the large extreme-tilt batch, the 1024x768 pair's
+    recipe at this size: a 2x canonical texture seen by image 1 with absolute
+    tilt t1 and by image 2 through a homography with local tilt t2 along the
+    perpendicular direction, plus N(0, 2^2) noise; t1, t2 ~ U[2, 1/cos 83 deg]."""
     from paper_2503_03479_gb300 import synth
-    rng = np.random.default_rng(seed * 1000 + index)
-    base = synth.texture(LARGE_H // 2, LARGE_W // 2, seed * 1000 + index)
-    img1 = np.kron(base, np.ones((2, 2), np.uint8))
-    t = float(rng.uniform(2.0, 1 / math.cos(math.radians(83))))
-    A = synth.tilt_about_centre(img1.shape, img1.shape, t, float(rng.uniform(0, 180)), 1.0)
-    img2 = np.clip(np.rint(synth.render(img1, A, img1.shape, ss=1)), 0, 255).astype(np.uint8)
-    return img1, img2
+    p = synth.large_pair(seed, index, LARGE_H, LARGE_W)
+    return p.img1, p.img2
 
 
 def large_batch(n_pairs: int, seed: int):
@@ -122,22 +117,80 @@ def mixed_batch(n_pairs: int, seed: int):
         return pool.starmap(_mixed_one, [(seed, i) for i in range(n_pairs)])
 
 
+class _Nvml:
+    """Read-only NVML queries through ctypes (clocks, throttle reasons, power)."""
+
+    SM = 1                                   # NVML_CLOCK_SM
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, cuda_index: int):
+        import ctypes as C
+        self.C = C
+        L = C.CDLL("libnvidia-ml.so.1")
+        if L.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.L = L
+        self.h = C.c_void_p()
+        bus = None
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(cuda_index)
+            bus = f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
+        except Exception:
+            bus = None
+        ok = bus is not None and L.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), C.byref(self.h)) == 0
+        if not ok and L.nvmlDeviceGetHandleByIndex_v2(cuda_index, C.byref(self.h)) != 0:
+            raise OSError("no NVML device handle")
+        self._reasons = getattr(L, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            L.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def sample(self):
+        C = self.C
+        sm, mx, pw, rs = C.c_uint(), C.c_uint(), C.c_uint(), C.c_ulonglong()
+        self.L.nvmlDeviceGetClockInfo(self.h, self.SM, C.byref(sm))
+        self.L.nvmlDeviceGetMaxClockInfo(self.h, self.SM, C.byref(mx))
+        self.L.nvmlDeviceGetPowerUsage(self.h, C.byref(pw))
+        self._reasons(self.h, C.byref(rs))
+        return sm.value, mx.value, pw.value / 1000.0, rs.value
+
+    def close(self):
+        try:
+            self.L.nvmlShutdown()
+        except Exception:
+            pass
+
+
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 50 ms during the timed
-    region: the sampler is started, its first line awaited (nvidia-smi takes a
-    moment to start), and only lines read after that count."""
+    """SM clocks and throttle reasons sampled during the timed region: NVML
+    polled every 5 ms from a thread (a region of 20 steps lasts only ~60 ms),
+    else nvidia-smi every 50 ms (its first line awaited before the region)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu: int):
+    def __init__(self, gpu: int, period_s: float = 0.005):
         self.gpu = gpu
+        self.period = period_s
         self.p = None
-        self.lines = []
+        self.nvml = None
+        self.samples = []                    # (sm MHz, max MHz, watts, reason names)
         self._buf = []
         self._first = threading.Event()
+        self._stop = threading.Event()
         self._t = None
+        self.source = None
+
+    def _poll(self):
+        while not self._stop.is_set():
+            try:
+                sm, mx, pw, rs = self.nvml.sample()
+                self.samples.append((float(sm), float(mx), pw,
+                                     sorted(n for b, n in _Nvml.REASONS.items() if rs & b)))
+            except Exception:
+                pass
+            self._stop.wait(self.period)
 
     def _read(self):
         for l in self.p.stdout:
@@ -147,12 +200,22 @@ class ClockSampler:
 
     def __enter__(self):
         try:
+            self.nvml = _Nvml(self.gpu)
+            self.nvml.sample()
+            self.source = "nvml, every 5 ms"
+            self._t = threading.Thread(target=self._poll, daemon=True)
+            self._t.start()
+            return self
+        except Exception:
+            self.nvml = None
+        try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
                                        "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (FileNotFoundError, OSError):
             self.p = None
             return self
+        self.source = "nvidia-smi, every 50 ms"
         self._t = threading.Thread(target=self._read, daemon=True)
         self._t.start()
         self._first.wait(timeout=5.0)
@@ -160,6 +223,11 @@ class ClockSampler:
         return self
 
     def __exit__(self, *a):
+        if self.nvml is not None:
+            self._stop.set()
+            self._t.join(timeout=5)
+            self.nvml.close()
+            return
         if self.p is None:
             return
         n = len(self._buf)
@@ -170,27 +238,23 @@ class ClockSampler:
             self.p.kill()
             self.p.wait()
         self._t.join(timeout=5)
-        self.lines = self._buf[self._start:n]
-
-    def summary(self):
-        if not self.lines:
-            return None
-        sm, smax, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in self.lines:
+        for l in self._buf[self._start:n]:
             f = [x.strip() for x in l.split(",")]
             try:
-                sm.append(float(f[1]))
-                smax = max(smax, float(f[2]))
+                self.samples.append((float(f[1]), float(f[2]), float(f[3]),
+                                     [nm for nm, v in zip(names, f[5:9]) if v.lower() == "active"]))
             except (ValueError, IndexError):
                 continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        if not sm:
+
+    def summary(self):
+        if not self.samples:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        reasons = sorted({r for s in self.samples for r in s[3]})
+        return {"sm_mhz": statistics.median(s[0] for s in self.samples),
+                "sm_max_mhz": max(s[1] for s in self.samples), "reasons": reasons,
+                "samples": len(self.samples), "power_w_max": max(s[2] for s in self.samples),
+                "source": self.source}
 
 
 def _peaks():
@@ -257,6 +321,30 @@ def match_roofline(sizes, ms: float, tensor: bool, peaks: dict) -> dict:
     return {"bound": "alu", "kernel": "hamming_top2_kernel (+ merge_kernel)", "achieved": achieved,
             "peak": peak, "unit": "Tpopc/s", "frac": achieved / peak, "traffic": None,
             "peak_source": f"derived: {SM_COUNT} SMs x {POPC_PER_SM_CLK} popc/clk x {f_clk/1e6:.0f} MHz"}
+
+
+def orb_level_bytes(A, views, n_levels: int):
+    """Algorithmic bytes of the two HBM-bound ORB stages for one image's views:
+    detect reads 1 B per pyramid pixel (every level); the pyramid reads the
+    parent level's image and mask (2 B per parent pixel) and writes the
+    level's image and mask (2 B per pixel) for every level >= 1."""
+    det = pyr = 0
+    for v in views:
+        for l in range(n_levels):
+            n = A.level_size(v.Wv, l) * A.level_size(v.Hv, l)
+            det += n
+            if l:
+                pyr += 2 * (A.level_size(v.Wv, l - 1) * A.level_size(v.Hv, l - 1) + n)
+    return det, pyr
+
+
+def hbm_roofline(kernel: str, nbytes: float, ms: float, peaks: dict) -> dict:
+    peak = peaks.get("hbm_gbs")
+    src = "measured copy bandwidth (MEASURED_PEAKS.json)" if peak else "fallback 6800 GB/s"
+    peak = peak or 6800.0
+    achieved = nbytes / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "bytes_per_launch": nbytes, "peak_source": src}
 
 
 def _sha256(path: str) -> str:
@@ -332,59 +420,97 @@ def match_engines(A, ctx, dd1, dd2, stream, reps: int = 5):
     return res
 
 
-# ---------------------------------------------------------------- CPU oracle sample
-def oracle_sample(rank: int = 0):
-    """Times the CPU oracle on a bounded sample of one pair and scales it to a
-    whole pair: warp + ORB of 6 views (2 per tilt class of each image) scaled by
-    the per-view pixel count to all 86 views, and the brute-force matcher on
-    1500 queries against a full-size train pool scaled to all queries."""
+# ---------------------------------------------------------------- CPU oracle
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def oracle_pair(img1, img2, threads: int):
+    """The CPU oracle, as it stands, on one whole pair: the warp and ORB of
+    every view of both images, the brute-force match of the pooled
+    descriptors and the back-projection of the accepted pairs, run by
+    `threads` host threads over the views (largest canvas first) and over
+    blocks of query rows.  Every oracle call is one C function that releases
+    the GIL, so the threads run in parallel.  Returns (seconds, (n1, n2),
+    accepted pairs)."""
+    from concurrent.futures import ThreadPoolExecutor
     import oracle as O
-    p = _pair(rank, 0)
     pat = O.pattern()
-    t_views, px_done, px_total = 0.0, 0, 0
-    picks = {0: [0, 6, 30], 1: [3, 15, 42]}
-    for im_i, img in enumerate((p.img1, p.img2)):
-        views = O.view_table(H, W, KMAX)
-        px_total += sum(v.Wr * v.Hr for v in views)
-        for vi in picks[im_i]:
-            v = views[vi]
-            t0 = time.perf_counter()
-            vo = O.warp_view(img, v)
-            O.orb_view(vo.u8, vo.mask, LEVELS, NFEAT, THR, pat)
-            t_views += time.perf_counter() - t0
-            px_done += v.Wr * v.Hr
-    from paper_2503_03479_gb300 import synth
-    n_pool = 43 * NFEAT
-    nq = 1500
-    q = synth.random_descriptors(nq, 1)
-    t = synth.random_descriptors(n_pool, 2)
+    views = O.view_table(H, W, KMAX)
+    nv = len(views)
+    imgs = (img1, img2)
+    order = sorted(range(2 * nv), key=lambda j: -views[j % nv].Wr * views[j % nv].Hr)
+
+    def view_job(j):
+        vo = O.warp_view(imgs[j // nv], views[j % nv])
+        return j, O.orb_view(vo.u8, vo.mask, LEVELS, NFEAT, THR, pat)
+
     t0 = time.perf_counter()
-    O.match(q, t)
-    t_match = (time.perf_counter() - t0) * (n_pool / nq)
-    t_pair = t_views * px_total / px_done + t_match
-    sample = (f"warp+ORB of 6 of 86 views (scaled by canvas pixels), match of {nq} of {n_pool} queries "
-              f"(scaled); single-threaded oracle")
-    return 1.0 / t_pair, t_pair, sample
+    with ThreadPoolExecutor(threads) as ex:
+        res = dict(ex.map(view_job, order))
+        pools = []
+        for im in (0, 1):
+            outs = [res[im * nv + v] for v in range(nv)]
+            pools.append((np.concatenate([o.kps for o in outs]), np.concatenate([o.desc for o in outs]),
+                          np.concatenate([np.full(len(o.kps), v, np.int32) for v, o in enumerate(outs)])))
+        (k1, d1, v1), (k2, d2, v2) = pools
+        blocks = [b for b in np.array_split(np.arange(len(d1)), 4 * threads) if len(b)]
+        ms = list(ex.map(lambda b: O.match(d1[b], d2, 4, 5), blocks))
+        best = np.concatenate([m.best for m in ms]) if ms else np.zeros(0, np.int32)
+        acc = np.flatnonzero(np.concatenate([m.accepted for m in ms])) if ms else np.zeros(0, np.int64)
+        xy = [(O.backproject(views[v1[q]], int(k1[q]["level"]), float(k1[q]["x"]), float(k1[q]["y"])),
+               O.backproject(views[v2[best[q]]], int(k2[best[q]]["level"]), float(k2[best[q]]["x"]),
+                             float(k2[best[q]]["y"]))) for q in acc]
+    return time.perf_counter() - t0, (len(d1), len(d2)), len(xy)
+
+
+def cpu_baseline_line(p, threads: int, single: bool) -> dict:
+    """The oracle on one whole pair with every host core, and (single) with one."""
+    t_pool, sizes, n_acc = oracle_pair(p.img1, p.img2, threads)
+    line = {"value": 1.0 / t_pool, "unit": "pairs/s", "cores": threads, "kind": "oracle",
+            "sample": (f"one whole {W}x{H} pair ({sizes[0]} x {sizes[1]} pooled descriptors, {n_acc} accepted): "
+                       f"warp + ORB of all {2 * len(view_table_sizes())} views and the full match, "
+                       f"{threads} host threads over views and query rows"),
+            "seconds": t_pool}
+    if single:
+        t_one, _, _ = oracle_pair(p.img1, p.img2, 1)
+        line["single_thread"] = {"value": 1.0 / t_one, "unit": "pairs/s", "cores": 1, "seconds": t_one}
+    return line
+
+
+def view_table_sizes():
+    import oracle as O
+    return O.view_table(H, W, KMAX)
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle (there is no installable reference
+    implementation: the paper ships no code), every step one whole pair
+    (alternating the GPU arm's two pairs) on all host cores, on rank 0."""
     rank, world, _ = _dist_env()
     if rank != 0:
         return 0
-    for _ in range(min(args.warmup, 1)):      # one untimed sample warms the caches
-        oracle_sample()
+    threads = host_cores()
+    pairs = [_pair(0, i) for i in range(2)]
+    for i in range(args.warmup):
+        oracle_pair(pairs[i % 2].img1, pairs[i % 2].img2, threads)
     times = []
-    for _ in range(max(1, min(args.steps, 3))):
-        v, t_pair, sample = oracle_sample()
-        times.append(t_pair)
-    t = statistics.mean(times)
-    val = 1.0 / t
+    for i in range(args.steps):
+        t, _, _ = oracle_pair(pairs[i % 2].img1, pairs[i % 2].img2, threads)
+        times.append(t)
+    tot = sum(times)
+    val = args.steps / tot
+    sample = (f"whole {W}x{H} pairs (the GPU arm's two pairs alternating): warp + ORB of all 86 views, the "
+              f"full match and the back-projection, {threads} host threads over views and query rows")
     line = {"impl": "reference", "metric": "image pairs/s (warp+ORB+match)", "value": val, "unit": "pairs/s",
-            "n_gpus": world, "steps": len(times), "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+int",
             "data": "synthetic", "config": {"workload": WORKLOAD, "H": H, "W": W, "views_per_image": 43,
                                             "levels": LEVELS, "features_per_view": NFEAT},
-            "cpu_baseline": {"value": val, "unit": "pairs/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": val, "unit": "pairs/s", "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -490,8 +616,11 @@ def run_ours(args):
     peaks = _peaks()
     clocks = clk.summary()
     views = A.view_table(H, W, KMAX)
+    det_b, pyr_b = orb_level_bytes(A, views, LEVELS)
     rooflines = {"warp": warp_roofline(views, 2, st["warp"], peaks),
-                 "match": match_roofline(sizes, st["match"], ctx.match_engine == A.MATCH_TENSOR_CORES, peaks)}
+                 "match": match_roofline(sizes, st["match"], ctx.match_engine == A.MATCH_TENSOR_CORES, peaks),
+                 "detect": hbm_roofline("detect_kernel", 2.0 * det_b, st["detect"], peaks),
+                 "pyramid": hbm_roofline("pyramid_kernel", 2.0 * pyr_b, st["pyramid"], peaks)}
     for k, r in rooflines.items():
         r["traffic"] = profiled_traffic(r["kernel"].split()[0])
     dominant = max(rooflines, key=lambda k: st[k])
@@ -788,8 +917,7 @@ def run_ours(args):
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            v, t_pair, sample = oracle_sample()
-            cpu = {"value": v, "unit": "pairs/s", "cores": 1, "kind": "oracle", "sample": sample}
+            cpu = cpu_baseline_line(pairs[0], host_cores(), not args.no_cpu_single)
         line = {"metric": "image pairs/s (warp+ORB+match)", "value": value, "unit": "pairs/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+int",
@@ -829,6 +957,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-single", action="store_true", help="skip the single-threaded whole-pair oracle run")
     ap.add_argument("--batch-pairs", type=int, default=64, help="pairs in the mixed-size batched run (0: skip)")
     ap.add_argument("--large-pairs", type=int, default=8, help="pairs in the 4096x3072 batched run (0: skip)")
     ap.add_argument("--diff-views", type=int, default=256, help="views of the differentiable-warp timing (0: skip)")

@@ -259,6 +259,29 @@ ASIFT_API size_t hamming_workspace_size(int nq, int nt);
 #define ASIFT_MATCH_TENSOR_CORES 2
 ASIFT_API asift_status asift_ctx_set_match_engine(asift_ctx *ctx, int engine);
 ASIFT_API int asift_ctx_match_engine(const asift_ctx *ctx);
+
+/*
+ * Failure-path test hooks.  The paper has no counterpart: these exist so that
+ * tests can drive the device-side error paths without a GPU fault.  Each hook
+ * holds until it is set again; value 0 turns it off.  Setting a hook drops
+ * match_pair's cached layouts of this context (the capacities change).
+ *  ASIFT_HOOK_CAND_CAP: every pyramid level's candidate list holds `value`
+ *    corners (1 .. 2^30, at most the level's pixel count) instead of 4096 +
+ *    cand_per_mpx x pixels / 10^6; a level with more NMS survivors sets
+ *    ASIFT_ERR_CAPACITY in the status word (orb_extract, match_pair, plans
+ *    created while it is set).
+ *  ASIFT_HOOK_MATCH_STALL: value = a wait limit in ns (1000 .. 4e9).  Every
+ *    tensor-core matcher launch of this context (hamming_match, match_pair)
+ *    bounds its waits by `value` instead of 4 s, and its MMA warp first waits
+ *    on a barrier that nothing arrives at: that wait runs out, the launch
+ *    records ASIFT_ERR_TIMEOUT, lets its copies land, frees its tensor
+ *    memory and returns; its match results are then undefined.
+ * Errors: ASIFT_ERR_ARG for a NULL context, an unknown hook or a value out of
+ * range.
+ */
+#define ASIFT_HOOK_CAND_CAP 1
+#define ASIFT_HOOK_MATCH_STALL 2
+ASIFT_API asift_status asift_ctx_set_test_hook(asift_ctx *ctx, int hook, int64_t value);
 ASIFT_API asift_status hamming_match(asift_ctx *ctx, const uint8_t *d_q, int nq, const int32_t *d_nq,
                            const uint8_t *d_t, int nt, const int32_t *d_nt,
                            int ratio_num, int ratio_den, asift_match *d_out, uint8_t *d_accept,
@@ -277,9 +300,11 @@ ASIFT_API asift_status hamming_match(asift_ctx *ctx, const uint8_t *d_q, int nq,
  * ASIFT_NOALLOC_SCRATCH_BYTES that the library declares at file scope, so every
  * GPU that loads the library holds those bytes until the process exits.
  * Limits: nq <= ASIFT_NOALLOC_MAX_QUERIES and nt <= 8388607; larger sizes return
- * ASIFT_ERR_ARG with nothing enqueued.  The first call on a device (the device
- * current at the call) looks up the array's device address; make that first
- * call before any stream capture on that device.  Every call uses the same
+ * ASIFT_ERR_ARG with nothing enqueued.  The first call in each CUDA context
+ * (the device current at the call) looks up the array's device address, a
+ * host-side query that allocates nothing; make that first call before any
+ * stream capture on that device.  After cudaDeviceReset the device has a new
+ * context and the next call looks the address up again.  Every call uses the same
  * array and leaves its contents behind (nothing in it needs to start at zero:
  * each call writes every entry it reads), so calls whose work overlaps on the
  * GPU (different streams, or different host threads) race and must be

@@ -33,8 +33,10 @@ EXPORTED = ["asift_ctx_create", "asift_ctx_destroy", "asift_ctx_orb_cfg", "asift
             "asift_plan_pairs", "asift_plan_view_counts", "asift_plan_eval_workspace_size", "asift_plan_eval",
             "asift_plan_eval_outputs", "asift_plan_workspace", "asift_plan_set_tuning", "asift_plan_get_tuning",
             "asift_plan_autotune", "asift_plan_destroy", "asift_warp_shape_for", "asift_warp_workspace_size",
-            "asift_warp_fwd", "asift_warp_bwd", "asift_ctx_set_match_engine", "asift_ctx_match_engine"]
+            "asift_warp_fwd", "asift_warp_bwd", "asift_ctx_set_match_engine", "asift_ctx_match_engine",
+            "asift_ctx_set_test_hook"]
 MATCH_AUTO, MATCH_CUDA_CORES, MATCH_TENSOR_CORES = 0, 1, 2
+HOOK_CAND_CAP, HOOK_MATCH_STALL = 1, 2
 INTERP_LANCZOS3, INTERP_NEAREST = 0, 1
 PROF_STAGES = ["upload", "warp", "pyramid", "detect", "select", "orient_brief", "match", "pairs"]
 
@@ -117,6 +119,7 @@ def load_library():
         "asift_ctx_orb_cfg": (i32, [vp, P(OrbCfg)]),
         "asift_ctx_set_match_engine": (i32, [vp, i32]),
         "asift_ctx_match_engine": (i32, [vp]),
+        "asift_ctx_set_test_hook": (i32, [vp, i32, i64]),
         "asift_ctx_pattern": (i32, [vp, vp]),
         "asift_view_table": (i32, [i32, i32, i32, vp, i32, P(C.c_int)]),
         "asift_make_view": (i32, [i32, i32, C.c_double, C.c_double, P(ViewDesc)]),
@@ -326,6 +329,10 @@ class Context:
     def set_match_engine(self, engine: int):
         """MATCH_AUTO, MATCH_CUDA_CORES or MATCH_TENSOR_CORES for hamming_match and match_pair."""
         _check("asift_ctx_set_match_engine", self.L.asift_ctx_set_match_engine(self._ctx, int(engine)))
+
+    def set_test_hook(self, hook: int, value: int):
+        """Failure-path test hooks (HOOK_CAND_CAP, HOOK_MATCH_STALL; 0 turns one off)."""
+        _check("asift_ctx_set_test_hook", self.L.asift_ctx_set_test_hook(self._ctx, int(hook), int(value)))
 
     @property
     def match_engine(self) -> int:

@@ -77,9 +77,10 @@ struct LevelTables {
     long long arena_bytes = 0;    // bytes of the levels kept in the workspace arena
 };
 
-static int cand_capacity(const asift_orb_cfg &cfg, int W, int H)
+// cap_override > 0 (a failure-path test hook) replaces the configured capacity.
+static int cand_capacity(const asift_orb_cfg &cfg, int W, int H, int cap_override)
 {
-    const long long c = 4096 + (long long)cfg.cand_per_mpx * W * H / 1000000;
+    const long long c = cap_override > 0 ? cap_override : 4096 + (long long)cfg.cand_per_mpx * W * H / 1000000;
     return (int)std::min<long long>(c, (long long)W * H);
 }
 
@@ -97,7 +98,7 @@ static int level_quota(const asift_orb_cfg &cfg, const int *Ws, const int *Hs, i
 // every tile_start is 0 (each entry is launched on its own).
 static void build_levels(const asift_orb_cfg &cfg, const asift_view_desc *views, int nv,
                          const uint8_t *const *l0_img, const uint8_t *const *l0_mask, uint8_t *arena_u8,
-                         uint8_t *arena_mask, bool per_view, LevelTables &T)
+                         uint8_t *arena_mask, bool per_view, LevelTables &T, int cand_cap_override = 0)
 {
     const int L = cfg.n_levels;
     T.lv.assign((size_t)L * nv, DevLevel{});
@@ -148,7 +149,7 @@ static void build_levels(const asift_orb_cfg &cfg, const asift_view_desc *views,
                 d.prev = p.img;
                 d.prev_mask = p.mask;
             }
-            d.cand_cap = cand_capacity(cfg, d.W, d.H);
+            d.cand_cap = cand_capacity(cfg, d.W, d.H, cand_cap_override);
             d.cand_off = (int)T.cand_total;
             T.cand_total += d.cand_cap;
             d.det_ntx = (d.W + kDetTW - 1) / kDetTW;
@@ -272,6 +273,9 @@ struct asift_ctx {
     cudaEvent_t prof_ev[ASIFT_PROF_STAGES + 1] = {};
     int match_engine = ASIFT_MATCH_AUTO;
     PairCache *pair_cache = nullptr;
+    // failure-path test hooks (asift_ctx_set_test_hook; 0 = off)
+    int test_cand_cap = 0;
+    unsigned long long test_stall_ns = 0;
 };
 
 // The matcher engine a call uses: the tuning's, else the context's; AUTO
@@ -371,6 +375,26 @@ asift_status asift_ctx_set_match_engine(asift_ctx *ctx, int engine)
 }
 
 int asift_ctx_match_engine(const asift_ctx *ctx) { return ctx ? resolve_engine(ctx, nullptr) : 0; }
+
+asift_status asift_ctx_set_test_hook(asift_ctx *ctx, int hook, int64_t value)
+{
+    if (!ctx) return ASIFT_ERR_ARG;
+    switch (hook) {
+    case ASIFT_HOOK_CAND_CAP:
+        if (value < 0 || value > (1 << 30)) return ASIFT_ERR_ARG;
+        ctx->test_cand_cap = (int)value;
+        break;
+    case ASIFT_HOOK_MATCH_STALL:
+        if (value != 0 && (value < 1000 || value > 4000000000LL)) return ASIFT_ERR_ARG;
+        ctx->test_stall_ns = (unsigned long long)value;
+        break;
+    default:
+        return ASIFT_ERR_ARG;
+    }
+    pair_cache_free(ctx->pair_cache);   // cached layouts carry the old capacities
+    ctx->pair_cache = nullptr;
+    return ASIFT_OK;
+}
 
 asift_status asift_ctx_orb_cfg(const asift_ctx *ctx, asift_orb_cfg *out)
 {
@@ -670,7 +694,7 @@ static size_t orb_ws(const asift_ctx *ctx, const asift_view_desc *h_views, int n
     Bump b(base);
     int32_t *status = b.take<int32_t>(64);
     // first pass sizes the arena; pointers are filled in by the caller with the real base
-    build_levels(ctx->cfg, h_views, n_views, dummy.data(), dummy.data(), nullptr, nullptr, false, T);
+    build_levels(ctx->cfg, h_views, n_views, dummy.data(), dummy.data(), nullptr, nullptr, false, T, ctx->test_cand_cap);
     OrbBuffers o;
     orb_layout(b, T, n_views, 1, ctx->cfg, o);
     o.status = status;
@@ -710,7 +734,8 @@ asift_status orb_extract(asift_ctx *ctx, const uint8_t *d_view_u8, const uint8_t
         l0i[v] = d_view_u8 + h_offsets[v];
         l0m[v] = d_mask + h_offsets[v];
     }
-    build_levels(ctx->cfg, h_views, n_views, l0i.data(), l0m.data(), o.arena_u8, o.arena_mask, false, T);
+    build_levels(ctx->cfg, h_views, n_views, l0i.data(), l0m.data(), o.arena_u8, o.arena_mask, false, T,
+                 ctx->test_cand_cap);
     // level table and group boundaries in one upload (they are adjacent in the workspace)
     const size_t lv_bytes = sizeof(DevLevel) * T.lv.size();
     const size_t gap = (size_t)((char *)o.group_first - (char *)o.lv);
@@ -771,8 +796,8 @@ asift_status hamming_match(asift_ctx *ctx, const uint8_t *d_q, int nq, const int
         e = launch_expand(d_q, w.xq, nullptr, 0, d_nq, nq, 1, s);
         if (e == cudaSuccess) e = launch_expand(d_t, w.xt, nullptr, 0, d_nt, nt, 1, s);
         if (e == cudaSuccess)
-            e = launch_match_tc(d_q, w.xq, nq, d_t, w.xt, nt, nullptr, 0, P, nq, ratio_num, ratio_den, MatchTuning{},
-                                w.status, s);
+            e = launch_match_tc(d_q, w.xq, nq, d_t, w.xt, nt, nullptr, 0, P, nq, ratio_num, ratio_den,
+                                MatchTuning{0, 0, ctx->test_stall_ns}, w.status, s);
     } else {
         e = launch_hamming(d_q, nq, d_nq, d_t, nt, d_nt, ratio_num, ratio_den, d_out, d_accept, d_n_accepted, w.part,
                            s);
@@ -929,7 +954,7 @@ static bool pipeline_layout(const asift_ctx *ctx, const PairSpec *ps, int P, con
     L.dv = b.take<DevView>(L.nv);
     L.probs = b.take<MatchProblem>(P);
     L.conv = b.take<ImageConv>(2 * P);
-    build_levels(cfg, L.views.data(), L.nv, nullptr, nullptr, nullptr, nullptr, per_view, L.T);
+    build_levels(cfg, L.views.data(), L.nv, nullptr, nullptr, nullptr, nullptr, per_view, L.T, ctx->test_cand_cap);
     orb_layout(b, L.T, L.nv, 2 * P, cfg, L.o);
     L.tab_bytes = (size_t)((char *)(L.o.group_first + 2 * P + 1) - (char *)L.dv);
     if (!base) {                              // sizing pass: the same offsets from a null base
@@ -943,7 +968,8 @@ static bool pipeline_layout(const asift_ctx *ctx, const PairSpec *ps, int P, con
         L.tab_bytes = c.off - tab0;
     }
     L.o.status = L.status;
-    build_levels(cfg, L.views.data(), L.nv, nullptr, nullptr, L.o.arena_u8, L.o.arena_mask, per_view, L.T);
+    build_levels(cfg, L.views.data(), L.nv, nullptr, nullptr, L.o.arena_u8, L.o.arena_mask, per_view, L.T,
+                 ctx->test_cand_cap);
     L.level0_off.assign(L.nv, 0);
     long long off = 0;
     for (int v = 0; v < L.nv; ++v) {
@@ -1064,7 +1090,7 @@ static cudaError_t pipeline_run(asift_ctx *ctx, const Pipeline &L, const asift_p
         e = run_orb(ctx, L.T, L.nv, 2 * P, L.o, per_view, L.kp, L.desc, L.view_count, L.view_off, s, tune);
     if (e == cudaSuccess) e = cudaMemsetAsync(L.n_acc, 0, sizeof(int32_t) * P, s);
     if (e == cudaSuccess) {
-        MatchTuning mt{tune ? tune->match_grid : 0, tune ? tune->match_target_items : 0};
+        MatchTuning mt{tune ? tune->match_grid : 0, tune ? tune->match_target_items : 0, ctx->test_stall_ns};
         if (resolve_engine(ctx, tune) == ASIFT_MATCH_TENSOR_CORES) {
             if (!tc_match_available()) return cudaErrorNotSupported;
             e = launch_expand(L.desc, L.xdesc, L.o.group_first, L.n_per_view, L.o.group_total, L.cap_rows, 2 * P, s);

@@ -116,6 +116,10 @@ struct MatchProblem {
 struct MatchTuning {
     int grid;
     int target_items;
+    // failure-path test only (0 = off): the tensor-core matcher's waits give
+    // up after stall_ns and its MMA warp first waits on a barrier that nothing
+    // arrives at, so that launch ends in ASIFT_ERR_TIMEOUT
+    unsigned long long stall_ns = 0;
 };
 
 // ---------------------------------------------------------------- helpers

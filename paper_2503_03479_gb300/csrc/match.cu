@@ -286,8 +286,10 @@ pair_write_kernel(const MatchProblem *__restrict__ many, int n_probs, const Matc
     __syncthreads();
     if (a) {
         const int o = base + wsum[w] + __popc(bal & ((1u << lane) - 1u));
-        if (o < P.cap) {
-            const asift_match mm = P.out[i];
+        const asift_match mm = P.out[i];
+        // a train index outside the pool can only come from a matcher launch
+        // that gave up (status word set): such a pair is counted, not written
+        if (o < P.cap && mm.best >= 0 && mm.best < count_of(P.d_nt, P.nt_cap)) {
             const asift_keypoint k1 = P.kp1[i], k2 = P.kp2[mm.best];
             asift_pair_match pm;
             backproject(views[k1.view], k1.level, k1.x, k1.y, &pm.x1, &pm.y1);
@@ -475,20 +477,59 @@ namespace {
 constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void *g_noalloc_addr[kNoAllocMaxDevices] = {};
+unsigned long long g_noalloc_ctx[kNoAllocMaxDevices] = {};   // unique id of the context the address belongs to
+
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+
+// The unique id of the calling thread's current CUDA context (0 when there is
+// none yet or the driver does not tell: then the address is looked up again
+// on every call): ids are never reused, so an address cached under one
+// stays valid for exactly that context.
+unsigned long long current_ctx_id()
+{
+    static CtxGetCurrentFn get_cur = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<CtxGetCurrentFn>(p);
+    }();
+    static CtxGetIdFn get_id = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<CtxGetIdFn>(p);
+    }();
+    void *c = nullptr;
+    unsigned long long id = 0;
+    if (!get_cur || !get_id || get_cur(&c) != 0 || !c || get_id(c, &id) != 0) return 0;
+    return id;
+}
 }  // namespace
 
+// The device address of the fixed scratch array in the current context of
+// the current device.  The first call in a context looks it up (a host-side
+// query: no allocation, no work on any stream); later calls in the same
+// context reuse it.  After cudaDeviceReset the device has a new context, so
+// the next call looks the address up again.
 static cudaError_t noalloc_scratch(void **out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+    const unsigned long long id = current_ctx_id();
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    if (!g_noalloc_addr[dev] || id == 0 || g_noalloc_ctx[dev] != id) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_part);
         if (e != cudaSuccess) return e;
         g_noalloc_addr[dev] = p;
+        g_noalloc_ctx[dev] = id;
     }
     *out = g_noalloc_addr[dev];
     return cudaSuccess;

@@ -213,7 +213,7 @@ __device__ __forceinline__ bool same_run(const TcItem &a, const TcItem &b) { ret
 __global__ void __launch_bounds__(kTcThreads, 1)
 hamming_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap tmap,
                   const uint4 *qbase, const uint4 *tbase, const MatchProblem *__restrict__ many, int n_probs,
-                  const MatchProblem single, int target_items, int32_t *status)
+                  const MatchProblem single, int target_items, int32_t *status, unsigned long long stall_ns)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -223,6 +223,8 @@ hamming_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constan
     uint64_t *full = bars, *empty = bars + kTcStages;
     uint64_t *acc_full = bars + 2 * kTcStages, *acc_empty = acc_full + 2;
     uint64_t *a_full = acc_empty + 2, *a_empty = a_full + 1;
+    uint64_t *never = a_empty + 1;                           // failure-path test: nothing arrives here
+    const unsigned long long lim = stall_ns ? stall_ns : kTmaWaitNs;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_sh;
     __shared__ int s_items[kMaxTcProblems + 1], s_chunk[kMaxTcProblems], s_nsplit[kMaxTcProblems];
@@ -242,6 +244,7 @@ hamming_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constan
         }
         mbar_init(a_full, 1);
         mbar_init(a_empty, 1);
+        mbar_init(never, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         // Slicing: about target_items items over all problems, in proportion
         // to each problem's nq x nt; chunks are whole train tiles.
@@ -327,7 +330,7 @@ hamming_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constan
                 const int qrow = (int)((P.q - qbase) >> 1) + it.qblk * kTcQB * kTcBM;
                 const int trow = (int)((P.t - tbase) >> 1);
                 if (!cont) {   // a new run: its query tile, once the previous run's MMAs are done with smA
-                    if (!mbar_wait(a_empty, a_ph ^ 1, abort_flag, status)) break;
+                    if (!mbar_wait(a_empty, a_ph ^ 1, abort_flag, status, lim)) break;
                     mbar_expect_tx(a_full, kTcABytes);
                     tma_load_2d(smA, &qmap, 0, qrow, a_full);
                     tma_load_2d(smA + kTcAHalf, &qmap, 128, qrow, a_full);
@@ -336,7 +339,7 @@ hamming_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constan
                 }
                 bool ok = true;
                 for (int tb = it.t0; tb < it.t1; tb += kTcBN) {
-                    if (!mbar_wait(&empty[stage], ph ^ 1, abort_flag, status)) { ok = false; break; }
+                    if (!mbar_wait(&empty[stage], ph ^ 1, abort_flag, status, lim)) { ok = false; break; }
                     uint8_t *dst = smB + stage * kTcBBytes;
                     mbar_expect_tx(&full[stage], kTcBBytes);
                     tma_load_2d(dst, &tmap, 0, trow + tb, &full[stage]);
@@ -358,19 +361,22 @@ hamming_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constan
             int stage = 0, acc = 0, p = 0, last_acc = -1;
             uint32_t ph = 0, acc_ph = 0, a_ph = 0, last_par = 0;
             const uint32_t a0 = smem_u32(smA), b0 = smem_u32(smB);
+            // failure-path test: a wait that runs out (no copy or MMA depends
+            // on `never`); it raises the abort flag, which every role sees
+            if (stall_ns) mbar_wait(never, 0, abort_flag, status, lim);
             for (int item = i_lo; item < i_hi && !*abort_flag; ++item) {
                 const bool cont = continues(item, p);
                 const bool last_of_run = item + 1 >= i_hi || !continues(item + 1, p);
                 const TcItem it = item_of(item, p);
                 if (!cont) {
-                    if (!mbar_wait(a_full, a_ph, abort_flag, status)) break;
+                    if (!mbar_wait(a_full, a_ph, abort_flag, status, lim)) break;
                     a_ph ^= 1;
                 }
                 tc_fence_after();
                 bool ok = true;
                 for (int tb = it.t0; tb < it.t1; tb += kTcBN) {
-                    if (!mbar_wait(&full[stage], ph, abort_flag, status)) { ok = false; break; }
-                    if (!mbar_wait(&acc_empty[acc], acc_ph ^ 1, abort_flag, status)) { ok = false; break; }
+                    if (!mbar_wait(&full[stage], ph, abort_flag, status, lim)) { ok = false; break; }
+                    if (!mbar_wait(&acc_empty[acc], acc_ph ^ 1, abort_flag, status, lim)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t bs = b0 + (uint32_t)(stage * kTcBBytes);
 #pragma unroll
@@ -420,7 +426,7 @@ hamming_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constan
             }
             bool ok = true;
             for (int tb = it.t0; tb < it.t1; tb += kTcBN) {
-                if (!mbar_wait(&acc_full[acc], acc_ph, abort_flag, status)) { ok = false; break; }
+                if (!mbar_wait(&acc_full[acc], acc_ph, abort_flag, status, lim)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t taddr =
                     tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((acc * kTcQB + qb) * kTcBN);
@@ -547,7 +553,7 @@ cudaError_t launch_match_tc(const uint8_t *qbase, const uint8_t *qexp, long long
     const int target = tune.target_items > 0 ? tune.target_items : 4 * grid;
     hamming_tc_kernel<<<grid, kTcThreads, kTcSmem, s>>>(qm, tm, reinterpret_cast<const uint4 *>(qbase),
                                                         reinterpret_cast<const uint4 *>(tbase), d_probs, n_probs,
-                                                        single, target, status);
+                                                        single, target, status, tune.stall_ns);
     note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

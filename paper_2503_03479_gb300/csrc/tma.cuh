@@ -54,18 +54,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 }
 
 // Waits for the phase of `bar` with the given parity.  Gives up when another
-// thread of the CTA has aborted (abort_flag set), or after kTmaWaitNs: then it
+// thread of the CTA has aborted (abort_flag set), or after limit_ns: then it
 // raises the abort flag and records ASIFT_ERR_TIMEOUT.  With abort_flag NULL
 // only the time limit applies.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
-                                          int32_t *status)
+                                          int32_t *status, unsigned long long limit_ns = kTmaWaitNs)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
         if (abort_flag && *abort_flag) return false;
-        if (global_ns() - t0 > kTmaWaitNs) {
+        if (global_ns() - t0 > limit_ns) {
             if (abort_flag) *abort_flag = 1;
             set_status(status, ASIFT_ERR_TIMEOUT);
             return false;

@@ -27,6 +27,44 @@ def _rng(seed: int) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(seed))
 
 
+# The shapes are drawn row by row: along a row a convex shape covers an
+# interval, found in closed form.  Columns more than a safe margin inside it
+# are filled directly; only the few columns near its two ends are decided by
+# the shape's own membership test (the same floating-point expression for
+# every pixel), so the result is the membership test applied to every pixel
+# of the bounding box, at a cost that grows with the shape's perimeter
+# rather than its area.
+
+def _paint_rows(img, y0, x0, x1, sa, sb, ca, cb, exact, grey):
+    """Rows y0 .. y0 + len(sa) - 1 of img: columns [sa, sb] are inside, the
+    columns of [ca, cb] outside [sa, sb] are decided by exact(yy, xx) (float
+    arrays of pixel coordinates), all other columns of [x0, x1) are outside."""
+    n = len(sa)
+    if n == 0:
+        return
+    sa = np.clip(sa, x0, x1).astype(np.int64)
+    sb = np.clip(sb, x0 - 1, x1 - 1).astype(np.int64)
+    ca = np.clip(ca, x0, x1).astype(np.int64)
+    cb = np.clip(cb, x0 - 1, x1 - 1).astype(np.int64)
+    empty = sb < sa
+    sa = np.where(empty, cb + 1, sa)     # no sure interior: the whole candidate range is tested
+    sb = np.where(empty, cb, sb)
+    cols = np.arange(x0, x1, dtype=np.int64)[None, :]
+    sure = (cols >= sa[:, None]) & (cols <= sb[:, None])
+    # boundary columns: [ca, sa - 1] and [sb + 1, cb]
+    left = np.maximum(sa - ca, 0)
+    right = np.maximum(cb - sb, 0)
+    rows = np.arange(n)
+    ry = np.concatenate([np.repeat(rows, left), np.repeat(rows, right)])
+    off_l = np.arange(int(left.sum())) - np.repeat(np.cumsum(left) - left, left)
+    off_r = np.arange(int(right.sum())) - np.repeat(np.cumsum(right) - right, right)
+    rx = np.concatenate([np.repeat(ca, left) + off_l, np.repeat(sb + 1, right) + off_r])
+    if len(ry):
+        inside = exact((ry + y0).astype(np.float64), rx.astype(np.float64))
+        sure[ry[inside], rx[inside] - x0] = True
+    img[y0:y0 + n, x0:x1][sure] = grey
+
+
 def _fill_ellipse(img, rng):
     H, W = img.shape
     cx, cy = rng.uniform(0, W), rng.uniform(0, H)
@@ -39,12 +77,29 @@ def _fill_ellipse(img, rng):
     y0, y1 = max(0, int(cy) - r), min(H, int(cy) + r + 1)
     if x0 >= x1 or y0 >= y1:
         return
-    yy, xx = np.mgrid[y0:y1, x0:x1].astype(np.float64)
-    dx, dy = xx - cx, yy - cy
-    u = (dx * math.cos(th) + dy * math.sin(th)) / a
-    v = (-dx * math.sin(th) + dy * math.cos(th)) / b
-    inside = u * u + v * v <= 1.0
-    img[y0:y1, x0:x1][inside] = grey
+    c, s = math.cos(th), math.sin(th)
+
+    def exact(yy, xx):
+        dx, dy = xx - cx, yy - cy
+        u = (dx * c + dy * s) / a
+        v = (-dx * s + dy * c) / b
+        return u * u + v * v <= 1.0
+
+    # along row y the test is A dx^2 + B dx + C <= 0 (dx = x - cx): its roots
+    # are dxm -+ w; one pixel beyond them the quadratic is at least A > 0
+    # away from 0, far above the rounding of the test
+    dy = np.arange(y0, y1, dtype=np.float64) - cy
+    qa = c * c / (a * a) + s * s / (b * b)
+    qb = 2.0 * dy * c * s * (1.0 / (a * a) - 1.0 / (b * b))
+    qc = dy * dy * (s * s / (a * a) + c * c / (b * b)) - 1.0
+    disc = qb * qb - 4.0 * qa * qc
+    dxm = -qb / (2.0 * qa)
+    w = np.sqrt(np.maximum(disc, 0.0)) / (2.0 * qa)
+    sa = np.ceil(cx + dxm - w + 1.0)
+    sb = np.floor(cx + dxm + w - 1.0)
+    ca = np.floor(cx + dxm - w - 1.0)
+    cb = np.ceil(cx + dxm + w + 1.0)
+    _paint_rows(img, y0, x0, x1, sa, sb, ca, cb, exact, grey)
 
 
 def _fill_polygon(img, rng):
@@ -60,15 +115,43 @@ def _fill_polygon(img, rng):
     y0, y1 = max(0, int(py.min())), min(H, int(py.max()) + 2)
     if x0 >= x1 or y0 >= y1:
         return
-    yy, xx = np.mgrid[y0:y1, x0:x1].astype(np.float64)
-    inside = np.ones(xx.shape, dtype=bool)
     # vertices sorted by angle around an interior point -> counter-clockwise
     # convex polygon; a point is inside iff it is left of every edge.
-    for k in range(n):
-        ax, ay = px[k], py[k]
-        bx, by = px[(k + 1) % n], py[(k + 1) % n]
-        inside &= (bx - ax) * (yy - ay) - (by - ay) * (xx - ax) >= 0
-    img[y0:y1, x0:x1][inside] = grey
+    edges = [(px[k], py[k], px[(k + 1) % n], py[(k + 1) % n]) for k in range(n)]
+
+    def exact(yy, xx):
+        inside = np.ones(xx.shape, dtype=bool)
+        for ax, ay, bx, by in edges:
+            inside &= (bx - ax) * (yy - ay) - (by - ay) * (xx - ax) >= 0
+        return inside
+
+    # edge k along row y: cross(x) = e - beta (x - ax), beta = by - ay.  The
+    # sure interior keeps cross >= tau for every edge, the candidates cross >=
+    # -tau; tau = 1e-6 is far above the rounding of the test (its terms stay
+    # below 1e8 in magnitude)
+    tau = 1e-6
+    yy = np.arange(y0, y1, dtype=np.float64)
+    lo_s = np.full(len(yy), -np.inf)
+    hi_s = np.full(len(yy), np.inf)
+    lo_c, hi_c = lo_s.copy(), hi_s.copy()
+    for ax, ay, bx, by in edges:
+        e = (bx - ax) * (yy - ay)
+        beta = by - ay
+        if beta > 0:
+            hi_s = np.minimum(hi_s, ax + (e - tau) / beta)
+            hi_c = np.minimum(hi_c, ax + (e + tau) / beta)
+        elif beta < 0:
+            lo_s = np.maximum(lo_s, ax + (e - tau) / beta)
+            lo_c = np.maximum(lo_c, ax + (e + tau) / beta)
+        else:
+            hi_s = np.where(e >= tau, hi_s, -np.inf)
+            hi_c = np.where(e >= -tau, hi_c, -np.inf)
+    big = float(W + 4)
+    sa = np.ceil(np.clip(lo_s, -big, big))
+    sb = np.floor(np.clip(hi_s, -big, big))
+    ca = np.floor(np.clip(lo_c, -big, big))
+    cb = np.ceil(np.clip(hi_c, -big, big))
+    _paint_rows(img, y0, x0, x1, sa, sb, ca, cb, exact, grey)
 
 
 def texture(H: int, W: int, seed: int) -> np.ndarray:

@@ -2,7 +2,8 @@
 s = 1 + k ds, ORB on them, matching of the reference's parameter groups
 against the unwarped target, and the per-view match counts with their argmax.
 
-Bars: the warp within 1e-4 of full scale; ORB, matches, counts and the argmax
+Bars: the warp within 3e-3 grey levels (its error bound; the configuration's
+outer bar is 1e-4 of full scale); ORB, matches, counts and the argmax
 bit-exact against the oracle fed the GPU's own u8 views and descriptor pools.
 """
 import numpy as np
@@ -14,7 +15,7 @@ from paper_2503_03479_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-WARP_TOL = 1e-4 * 255
+WARP_TOL = 3e-3          # grey levels: the warp's error bound (outer bar of the configuration: 1e-4 * 255)
 
 
 @pytest.fixture(scope="module")
@@ -53,7 +54,7 @@ def test_scaled_warp_parity(A):
 @pytest.mark.parametrize("H,W,kmax,ds", [(101, 143, 3, 0.5), (157, 201, 6, 0.0), (64, 80, 2, 1.0)])
 def test_nearest_warp_parity(A, H, W, kmax, ds):
     """asift_views_nearest against the oracle's nearest-neighbour views: fp32
-    within 1e-4 of full scale (the only rounding is the Gaussian's fp32 sum),
+    within 3e-3 grey levels (the only rounding is the Gaussian's fp32 sum),
     the mask bit-exact, u8 equal except at rounding ties."""
     ctx = A.Context()
     img = synth.texture(H, W, 40 + kmax)

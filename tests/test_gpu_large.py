@@ -4,10 +4,13 @@ ORB with 8 levels and 2000 keypoints per view, about 126k x 126k descriptors
 matched per pair.  Checked against the oracle on sampled views, one view's
 ORB and sampled queries, and against per-pair match_pair bit for bit.
 
-The texture is the usual generator at half size, upsampled 2x (the 2x-sized
-canonical texture of the full recipe takes minutes to draw); image 2 is image 1
-under a known affine tilt.
+The pairs follow the 1024x768 pair's recipe at this size (synth.large_pair):
+a 2x canonical texture seen by image 1 with absolute tilt t1 and by image 2
+through a homography with local tilt t2 along the perpendicular direction, plus
+N(0, 2^2) noise, t1 and t2 drawn from [2, 1/cos 83 deg].
 """
+import multiprocessing as mp
+
 import numpy as np
 import pytest
 import torch
@@ -17,7 +20,7 @@ from paper_2503_03479_gb300 import synth
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
-WARP_TOL = 1e-4 * 255
+WARP_TOL = 3e-3          # grey levels: the warp's error bound (outer bar of the configuration: 1e-4 * 255)
 L_, N_, KMAX = 8, 2000, 6
 H_, W_ = 3072, 4096
 
@@ -31,17 +34,15 @@ def A():
     return asift
 
 
-def _pair(seed):
-    base = synth.texture(H_ // 2, W_ // 2, seed)
-    img1 = np.kron(base, np.ones((2, 2), np.uint8))
-    A2 = synth.tilt_about_centre(img1.shape, img1.shape, 4.0, 35.0 + 20 * (seed % 3), 1.0)
-    img2 = np.clip(np.rint(synth.render(img1, A2, img1.shape, ss=1)), 0, 255).astype(np.uint8)
-    return img1, img2
+def _pair(index):
+    p = synth.large_pair(31, index, H_, W_)
+    return p.img1, p.img2
 
 
 def test_large_pairs_plan_sampled_parity(A):
     ctx = A.Context(n_levels=L_, n_features=N_)
-    pairs = [_pair(31), _pair(32)]
+    with mp.get_context("spawn").Pool(2) as pool:
+        pairs = pool.map(_pair, [0, 1])
     imgs = [(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()) for a, b in pairs]
     plan = A.Plan(ctx, [a for a, _ in imgs], [b for _, b in imgs], kmax=KMAX)
     plan.run()
@@ -50,9 +51,10 @@ def test_large_pairs_plan_sampled_parity(A):
     cnt = plan.pool_counts()
     views = A.view_table(H_, W_, KMAX)
     assert len(views) == 63
-    assert (cnt > 60000).all(), cnt
+    print("pooled descriptors per image:", cnt.tolist())
+    assert (cnt > 10000).all(), cnt
     got = [plan.pairs(i) for i in range(len(pairs))]
-    assert all(len(g) > 1000 for g in got)
+    assert all(len(g) > 500 for g in got)
     plan.close()
 
     # the plan equals match_pair on the first pair, and match_pair's pools are checked below

@@ -2,13 +2,18 @@
 same seeded inputs.
 
 Bars:
-  * warp: |gpu_f32 - oracle_f64| <= 1e-4 * 255 (1e-4 relative to the full
-    scale of the 8-bit input).  The GPU evaluates three normalised fp32
-    weighted sums (36, 2K+1 and 6 taps, sum |w| <= 1.3 each) plus fp32 weight
-    evaluation (~1e-6 relative); the accumulated rounding is below 3e-3 in
-    absolute value, an order of magnitude inside the bar.  u8 equal except
-    within 3e-3 of a rounding tie (then at most 1 apart); mask bit-exact (its
-    decisions are exact Q32 integer comparisons on both sides).
+  * warp: |gpu_f32 - oracle_f64| <= WARP_TOL = 3e-3 grey levels on every view.
+    The outer bar, 1e-4 relative to the 8-bit full scale (0.0255), is the
+    configuration's; 3e-3 is the kernel's own error bound.  The GPU evaluates
+    a 36-tap normalised fp32 sum (the rotation) and one fused filter of 2K + 6
+    taps (Gaussian and tilt); with sum |w| <= 1.25 per Lanczos axis, fp32 unit
+    roundoff u = 2^-24 and weights within ~1e-6 relative, the forward error is
+    at most 255 (gamma_12 S^2 + 2e-6 S) ~ 1e-3 for the rotation and 255
+    gamma_(2K+6) S_h ~ 1.3e-3 for the filter at K = 18 (t = 5.66): below
+    3e-3 up to K = 36 (t = 11); rounding errors add as a random walk, so the
+    observed errors are several times smaller.  u8 equal except within 3e-3 of a rounding tie (then at most
+    1 apart); mask bit-exact (its decisions are exact Q32 integer comparisons
+    on both sides).
   * ORB keypoints, orientation bins, Harris responses and descriptors:
     bit-exact when the oracle is fed the GPU's own uint8 view and mask.
   * matching: bit-exact (integers).
@@ -24,7 +29,7 @@ from paper_2503_03479_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-WARP_TOL = 1e-4 * 255
+WARP_TOL = 3e-3          # grey levels (outer bar of the configuration: 1e-4 * 255)
 
 
 @pytest.fixture(scope="module")
@@ -66,6 +71,7 @@ def _check_warp(A, ctx, img, views):
         du = np.abs(u.astype(int) - ref.u8.astype(int))
         assert (du[~near_tie] == 0).all(), i
         assert (du <= 1).all(), i
+    print(f"warp worst |gpu - oracle| over {len(views)} views: {worst:.3e}")
     return vo, worst
 
 
@@ -74,8 +80,7 @@ def test_warp_parity_small_pair(A):
     p = synth.pair_affine_small()
     for img in (p.img1, p.img2):
         views = A.view_table(*img.shape, 2)
-        _, worst = _check_warp(A, ctx, img, views)
-        assert worst < 3e-3
+        _check_warp(A, ctx, img, views)
 
 
 def test_warp_parity_ragged_sizes_and_all_tilts(A):
@@ -274,7 +279,9 @@ def test_full_size_pair_sampled_parity(A):
     for i in (0, 2, 7, 20, 42):
         ref = O.warp_view(p.img1, ov[i])
         f = vo.view(i, "f32").cpu().numpy().astype(np.float64)
-        assert np.abs(f - ref.f64).max() <= WARP_TOL
+        err = float(np.abs(f - ref.f64).max())
+        print(f"warp worst |gpu - oracle| on view {i} of the 1024x768 pair: {err:.3e}")
+        assert err <= WARP_TOL, (i, err)
         u, mk = vo.view(i, "u8").cpu().numpy(), vo.view(i, "mask").cpu().numpy()
         assert np.array_equal(mk, ref.mask)
         r = O.orb_view(u, mk, L, N, 20, pat)

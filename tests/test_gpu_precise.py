@@ -2,10 +2,11 @@
 Lanczos with n = 4, an 8 x 8 window), asift_views_lanczos, against the
 oracle's Lanczos-a views.
 
-Bar: fp32 within 1e-4 of full scale (1e-4 x 255) of the fp64 oracle, the mask
+Bar: fp32 within 3e-3 grey levels of the fp64 oracle (the outer bar of the
+configuration is 1e-4 x 255), the mask
 bit-exact, u8 equal except within 3e-3 of a rounding tie.  The fp32 weights
 (sinpi-based, normalised) and the fp32 sums of 64 + (2K+1) + 8 taps stay two
-orders inside the bar.
+orders inside the outer bar and inside 3e-3.
 """
 import numpy as np
 import pytest
@@ -16,7 +17,7 @@ from paper_2503_03479_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-WARP_TOL = 1e-4 * 255
+WARP_TOL = 3e-3          # grey levels: the warp's error bound (outer bar of the configuration: 1e-4 * 255)
 
 
 @pytest.fixture(scope="module")
@@ -55,7 +56,7 @@ def test_lanczos_views_parity(A, a, H, W, kmax, ds):
     views = A.view_table(H, W, kmax, ds) + [A.make_view(H, W, t, phi, s) for t, phi, s in
                                              ((1.0, 90.0, 1.0), (2.6, 33.0, 2.75), (7.9, 151.0, 1.0))]
     _, worst = _check(A, ctx, img, views, a)
-    assert worst < 3e-3
+    print(f"Lanczos-{a} warp worst |gpu - oracle|: {worst:.3e}")
 
 
 def test_lanczos3_kernel_agrees_with_the_main_warp(A):

@@ -11,6 +11,8 @@ must reject sizes beyond its stated limit.
 This file is collected last on purpose, and it passes both on its own in a
 fresh process and after the other tests.
 """
+import ctypes as C
+
 import numpy as np
 import pytest
 import torch
@@ -51,6 +53,46 @@ def test_noalloc_equals_workspace_matcher_on_two_calls(A):
             assert np.array_equal(g, w)
         assert got[4] == want[4]
         assert got[4] > 0
+
+
+def _raw(A, L, fn, ctx, q, nq_cap, d_nq, t, nt_cap, d_nt):
+    """One call through the C ABI with device-side counts d_nq / d_nt (int32
+    tensors or None) and capacities nq_cap / nt_cap; returns the output bytes."""
+    out = torch.zeros(max(nq_cap, 1) * 8, dtype=torch.uint8, device="cuda")
+    acc = torch.zeros(max(nq_cap, 1), dtype=torch.uint8, device="cuda")
+    nacc = torch.zeros(1, dtype=torch.int32, device="cuda")
+    p = lambda x: None if x is None else C.c_void_p(x.data_ptr())
+    s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if fn == "noalloc":
+        r = L.hamming_match_noalloc(p(q), nq_cap, p(d_nq), p(t), nt_cap, p(d_nt), 4, 5, p(out), p(acc), p(nacc), s)
+    else:
+        ws = torch.zeros(L.hamming_workspace_size(nq_cap, nt_cap), dtype=torch.uint8, device="cuda")
+        r = L.hamming_match(ctx._ctx, p(q), nq_cap, p(d_nq), p(t), nt_cap, p(d_nt), 4, 5, p(out), p(acc), p(nacc),
+                            p(ws), ws.numel(), s)
+    assert r == A.ASIFT_OK
+    torch.cuda.synchronize()
+    return out.cpu().numpy().tobytes(), acc.cpu().numpy().tobytes(), int(nacc.item())
+
+
+def test_noalloc_device_counts_and_empty_train_set(A):
+    """Counts read from the device (smaller than the capacities) and an empty
+    train set, bit for bit against hamming_match on the same arguments."""
+    L = A.load_library()
+    ctx = A.Context()
+    q, t = _pair(5_000, 4_000, 13)
+    nq_d = torch.tensor([3_333], dtype=torch.int32, device="cuda")
+    nt_d = torch.tensor([1_777], dtype=torch.int32, device="cuda")
+    for d_nq, d_nt in ((nq_d, nt_d), (None, nt_d), (nq_d, None)):
+        got = _raw(A, L, "noalloc", None, q, 5_000, d_nq, t, 4_000, d_nt)
+        want = _raw(A, L, "ws", ctx, q, 5_000, d_nq, t, 4_000, d_nt)
+        assert got == want and got[2] > 0
+    zero = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for d_nt, nt_cap in ((zero, 4_000), (None, 0)):          # no train descriptors: no match, none accepted
+        got = _raw(A, L, "noalloc", None, q, 5_000, None, t if nt_cap else None, nt_cap, d_nt)
+        want = _raw(A, L, "ws", ctx, q, 5_000, None, t if nt_cap else None, nt_cap, d_nt)
+        assert got == want and got[2] == 0
+        m = np.frombuffer(got[0], dtype=A.MATCH_DTYPE)
+        assert (m["best"] == -1).all() and (m["d1"] == 257).all()
 
 
 def test_noalloc_rejects_sizes_beyond_its_limit(A):
