@@ -482,12 +482,50 @@ ASIFT_API asift_status asift_sift(asift_ctx *ctx, const uint8_t *d_img, int H, i
                                   asift_sift_kp *d_kp, float *d_desc, int32_t *d_n, void *d_workspace,
                                   size_t ws_bytes, void *stream);
 
+/*
+ * asift_sift_match -- brute-force L2 matching of SIFT descriptors with the
+ * ratio test: the matching of the precise stage (Sec. III-C, SIFT on the
+ * reproduced best view against the target) and the match list that Eq. (1)
+ * takes (Sec. III-A).  For each of the queries d_q (nq x 128 fp32, as
+ * asift_sift writes them) over the trains d_t (nt x 128): the squared
+ * distance is the fp32 sum over c = 0..127, in that order, of e_c^2 with
+ * e_c = q_c - t_c rounded to fp32, each term added by one fused multiply-add
+ * (the decisions are taken in fp32 in this fixed order, so any implementation
+ * of it gives the same bits); best = the lowest index among the smallest
+ * distances, d2 = the second smallest (d2 = d1 on a tie; INFINITY when there
+ * is none); accepted iff nt >= 2 and d1 < r2 * d2 in fp32 with r2 =
+ * (float)(ratio * ratio) (Lowe's ratio test on distances; 0.8 by default).
+ * d_out[nq] (asift_l2_match) receives every query's result.  With keypoints
+ * d_kq / d_kt (asift_sift_kp, may be NULL) and d_n_pairs non-NULL, the
+ * accepted queries are written in query order to d_pairs (up to cap) as
+ * asift_pair_match: x1, y1 = d_kq[q], x2, y2 = d_kt[best], d1 / d2 = the L2
+ * distances at the scale of integer SIFT descriptors (512 sqrt(d), rounded),
+ * which is the scale Eq. (1)'s weight 1 - (Des_i + Des_i+1) / 1000 is written
+ * for; *d_n_pairs = their count (above cap: status ASIFT_ERR_CAPACITY).
+ * nq / nt may come from the device (d_nq / d_nt, clamped to nq / nt, e.g.
+ * asift_sift's count).  Workspace: asift_sift_match_workspace_size(nq, nt),
+ * 256-byte aligned, status word first.  Errors: ASIFT_ERR_ARG for NULL or
+ * misaligned buffers, nq or nt outside [0, 2^22], a ratio outside (0, 1].
+ */
+typedef struct {
+    int32_t best;           /* nearest train descriptor (-1 if none)              */
+    float d1, d2;           /* nearest / second-nearest squared distance (fp32)   */
+} asift_l2_match;
+ASIFT_API size_t asift_sift_match_workspace_size(int nq, int nt);
+ASIFT_API asift_status asift_sift_match(asift_ctx *ctx, const float *d_q, int nq, const int32_t *d_nq, const float *d_t,
+                                        int nt, const int32_t *d_nt, double ratio, const asift_sift_kp *d_kq,
+                                        const asift_sift_kp *d_kt, asift_l2_match *d_out, asift_pair_match *d_pairs,
+                                        int cap, int32_t *d_n_pairs, void *d_workspace, size_t ws_bytes,
+                                        void *stream);
+
 /* Base-image selection, Eq. (1) (Sec. III-A): the scaling coefficient from
  * image 1 to image 2 over the pairs d_pairs[0 .. min(*d_n, cap) - 1] in list
  * order,
  *   f = sum_{i + 1 < n} (|a_i+1 - a_i| - |b_i+1 - b_i|) (1 - (Des_i + Des_i+1) / 1000)
  * with a_i = (x1, y1), b_i = (x2, y2) and Des_i = d1 (the pair's descriptor
- * distance; the Hamming distance of the rBRIEF descriptors here), in fp64,
+ * distance: the SIFT L2 distance at integer-descriptor scale for the pairs of
+ * asift_sift_match, as the paper defines it, or the rBRIEF Hamming distance
+ * for those of match_pair), in fp64,
  * summed in a fixed order.  f > 0: the scene appears larger in image 1.
  * Computing f1 on image 1 -> 2's pairs and f2 on image 2 -> 1's, image 1 is
  * the reference when f1 > f2.  *d_f (device) is written on `stream`.

@@ -141,6 +141,7 @@ def lib():
         L.oracle_sift.argtypes = [u8p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
         L.oracle_sift.restype = C.c_int
         L.oracle_sift_match.argtypes = [f32p, C.c_int, f32p, C.c_int, C.c_double, i32p, f64p, f64p, u8p]
+        L.oracle_sift_match_f32.argtypes = [f32p, C.c_int, f32p, C.c_int, C.c_double, i32p, f32p, f32p, u8p]
         L.oracle_sizeof_sift_kp.restype = C.c_int
         assert L.oracle_sizeof_sift_kp() == SIFT_KP_DTYPE.itemsize
         assert L.oracle_sizeof_dview() == C.sizeof(ODView)
@@ -603,4 +604,21 @@ def sift_match(q: np.ndarray, t: np.ndarray, ratio: float = 0.8) -> SiftMatchOut
     lib().oracle_sift_match(q.reshape(-1) if nq else np.zeros(1, np.float32), nq,
                             t.reshape(-1) if nt else np.zeros(1, np.float32), nt, float(ratio), best, d1, d2, acc)
     return SiftMatchOut(best, d1, d2, acc.astype(bool))
+
+
+def sift_match_f32(q: np.ndarray, t: np.ndarray, ratio: float = 0.8) -> SiftMatchOut:
+    """Brute-force L2 SIFT matching with the ratio test, decisions in fp32 in the
+    fixed order of sift_oracle.c (the precision the GPU decides in); d1, d2 are
+    the fp32 squared distances."""
+    q = np.ascontiguousarray(q, dtype=np.float32)
+    t = np.ascontiguousarray(t, dtype=np.float32)
+    nq, nt = len(q), len(t)
+    best = np.zeros(max(nq, 1), np.int32)
+    d1 = np.zeros(max(nq, 1), np.float32)
+    d2 = np.zeros(max(nq, 1), np.float32)
+    acc = np.zeros(max(nq, 1), np.uint8)
+    if nq:
+        lib().oracle_sift_match_f32(q.reshape(-1), nq, t.reshape(-1) if nt else np.zeros(1, np.float32), nt,
+                                    float(ratio), best, d1, d2, acc)
+    return SiftMatchOut(best[:nq], d1[:nq], d2[:nq], acc[:nq].astype(bool))
 

@@ -24,7 +24,8 @@
  *   5. descriptor: 4 x 4 x 8 histograms over a window rotated to the
  *      orientation (bin width 3 sigma, Gaussian weight of half the window,
  *      trilinear spreading), unit-normalised, clamped at 0.2, renormalised;
- *   6. brute-force L2 matching with the ratio test.
+ *   6. brute-force L2 matching with the ratio test (in fp64, and with its
+ *      decisions taken in fp32 in a fixed order, as the GPU takes them).
  * Angles are those of the image gradient (gx, gy) with x to the right and y
  * down: atan2(gy, gx) in degrees, in [0, 360).
  */
@@ -496,3 +497,40 @@ void oracle_sift_match(const float *q, int nq, const float *t, int nt, double ra
 }
 
 int oracle_sizeof_sift_kp(void) { return (int)sizeof(oracle_sift_kp); }
+
+/* Step 6 with the decisions taken in single precision, as the GPU matcher
+ * takes them (an argmax decided in floating point is decided in the same
+ * precision on both sides).  The squared distance of query i and train j is
+ * the fp32 sum over c = 0, 1, ..., 127 in that order of e_c^2, e_c = q_c - t_c
+ * rounded to fp32, each term added by one fused multiply-add (d = fma(e_c,
+ * e_c, d)), so every implementation that keeps this order gets the same bits.
+ * best = the lowest index among the smallest distances, d2 = the second
+ * smallest (d2 = d1 on a tie), both INFINITY when there is none; accepted when
+ * nt >= 2 and d1 < r2 * d2 in fp32, r2 = (float)(ratio * ratio). */
+void oracle_sift_match_f32(const float *q, int nq, const float *t, int nt, double ratio, int32_t *best, float *d1,
+                           float *d2, uint8_t *accepted)
+{
+    const float r2 = (float)(ratio * ratio);
+    for (int i = 0; i < nq; ++i) {
+        float b1 = INFINITY, b2 = INFINITY;
+        int bi = -1;
+        for (int j = 0; j < nt; ++j) {
+            float d = 0.0f;
+            for (int c = 0; c < 128; ++c) {
+                const float e = q[(size_t)i * 128 + c] - t[(size_t)j * 128 + c];
+                d = fmaf(e, e, d);
+            }
+            if (d < b1) {
+                b2 = b1;
+                b1 = d;
+                bi = j;
+            } else if (d < b2) {
+                b2 = d;
+            }
+        }
+        best[i] = bi;
+        d1[i] = b1;
+        d2[i] = b2;
+        accepted[i] = (uint8_t)(bi >= 0 && nt >= 2 && b1 < r2 * b2);
+    }
+}

@@ -34,7 +34,7 @@ EXPORTED = ["asift_ctx_create", "asift_ctx_destroy", "asift_ctx_orb_cfg", "asift
             "asift_plan_eval_outputs", "asift_plan_workspace", "asift_plan_set_tuning", "asift_plan_get_tuning",
             "asift_plan_autotune", "asift_plan_destroy", "asift_warp_shape_for", "asift_warp_workspace_size",
             "asift_warp_fwd", "asift_warp_bwd", "asift_ctx_set_match_engine", "asift_ctx_match_engine",
-            "asift_ctx_set_test_hook"]
+            "asift_ctx_set_test_hook", "asift_sift_match_workspace_size", "asift_sift_match"]
 MATCH_AUTO, MATCH_CUDA_CORES, MATCH_TENSOR_CORES = 0, 1, 2
 HOOK_CAND_CAP, HOOK_MATCH_STALL = 1, 2
 INTERP_LANCZOS3, INTERP_NEAREST = 0, 1
@@ -96,6 +96,7 @@ SIFT_KP_DTYPE = np.dtype([("x", np.float32), ("y", np.float32), ("sigma", np.flo
                           ("response", np.float32), ("octave", np.int32), ("layer", np.int32), ("xo", np.float32),
                           ("yo", np.float32), ("so", np.float32), ("pad", np.int32, 2)])
 MATCH_DTYPE = np.dtype([("best", np.int32), ("d1", np.uint16), ("d2", np.uint16)])
+L2_MATCH_DTYPE = np.dtype([("best", np.int32), ("d1", np.float32), ("d2", np.float32)])
 PAIR_DTYPE = np.dtype([("x1", np.float32), ("y1", np.float32), ("x2", np.float32), ("y2", np.float32),
                        ("q", np.int32), ("t", np.int32), ("d1", np.uint16), ("d2", np.uint16)])
 
@@ -141,6 +142,8 @@ def load_library():
         "match_pair_view_counts": (i32, [vp, i32, i32, i32, i32, P(PairCfg), vp, vp, i32, vp, vp]),
         "asift_sift_workspace_size": (sz, [i32, i32, i32]),
         "asift_sift": (i32, [vp, vp, i32, i32, i32, i32, vp, vp, vp, vp, sz, vp]),
+        "asift_sift_match_workspace_size": (sz, [i32, i32]),
+        "asift_sift_match": (i32, [vp, vp, i32, vp, vp, i32, vp, C.c_double, vp, vp, vp, vp, i32, vp, vp, sz, vp]),
         "asift_scale_coefficient_workspace_size": (sz, [i32]),
         "asift_scale_coefficient": (i32, [vp, vp, vp, i32, vp, vp, sz, vp]),
         "asift_eval_workspace_size": (sz, [i32, i32]),
@@ -520,6 +523,30 @@ class Context:
         d = desc[:k].cpu().numpy()
         order = np.lexsort((kps["angle"], kps["x"], kps["y"], -kps["response"]))
         return kps[order], d[order]
+
+    def sift_match(self, dq: torch.Tensor, dt: torch.Tensor, ratio: float = 0.8, n_q: torch.Tensor | None = None,
+                   n_t: torch.Tensor | None = None, kq: torch.Tensor | None = None, kt: torch.Tensor | None = None,
+                   cap: int | None = None):
+        """L2 SIFT matching (asift_sift_match): dq (nq, 128) and dt (nt, 128) fp32 CUDA
+        descriptors, optional device counts n_q / n_t (int32 [1]) and keypoint buffers kq / kt
+        (asift_sift_kp bytes, as sift_raw returns them).  Returns the device per-query results
+        (L2_MATCH_DTYPE bytes), and with keypoints the accepted pairs (PAIR_DTYPE bytes) and
+        their count."""
+        nq, nt = dq.shape[0], dt.shape[0]
+        dev = dq.device
+        ws = self.workspace(("sift_match", nq, nt), self.L.asift_sift_match_workspace_size(nq, nt))
+        out = torch.empty(max(nq, 1) * L2_MATCH_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        pairs = n_pairs = None
+        if kq is not None and kt is not None:
+            cap = nq if cap is None else cap
+            pairs = torch.empty(max(cap, 1) * PAIR_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+            n_pairs = torch.zeros(1, dtype=torch.int32, device=dev)
+        _check("asift_sift_match",
+               self.L.asift_sift_match(self._ctx, _ptr(dq) if nq else None, nq, _ptr(n_q), _ptr(dt) if nt else None,
+                                       nt, _ptr(n_t), float(ratio), _ptr(kq), _ptr(kt), _ptr(out), _ptr(pairs),
+                                       cap or 0, _ptr(n_pairs), _ptr(ws), ws.numel(), _stream()))
+        self.last_sift_match_ws = ws
+        return out, pairs, n_pairs
 
     def scale_coefficient(self, out: torch.Tensor, n_out: torch.Tensor) -> torch.Tensor:
         """Eq. (1) over match_pair's output: a device float64 tensor of one element."""

@@ -24,7 +24,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libasift.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["warp.cu", "warp_nn.cu", "warp_precise.cu", "orb.cu", "match.cu", "match_tc.cu", "dwarp.cu", "eval.cu", "sift.cu", "api.cu"]
+CU_SOURCES = ["warp.cu", "warp_nn.cu", "warp_precise.cu", "orb.cu", "match.cu", "match_tc.cu", "dwarp.cu", "eval.cu", "sift.cu", "sift_match.cu", "api.cu"]
 CPP_SOURCES = ["tables.cpp"]
 
 

@@ -503,11 +503,12 @@ asift_status asift_read_status(void *d_workspace, int clear, int32_t *h_status, 
 
 // ---------------------------------------------------------------- asift_views
 static size_t views_layout(void *base, int H, int W, int nv, size_t n_filter, int32_t **status, DevView **tab,
-                           float **src, float **filt)
+                           DevRotGroup **grp, float **src, float **filt)
 {
     Bump b(base);
     *status = b.take<int32_t>(64);
     *tab = b.take<DevView>(std::max(nv, 1));
+    *grp = b.take<DevRotGroup>(std::max(nv, 1));
     *src = b.take<float>((size_t)src_pitch_of(W) * H);
     *filt = b.take<float>(std::max<size_t>(n_filter, 1));
     return b.off + 256;
@@ -520,8 +521,9 @@ size_t asift_views_workspace_size(int H, int W, int n_views)
     const size_t per_view = (size_t)(W + H + 2) * tilt_filter_pitch(ASIFT_MAX_GAUSS - 1);
     int32_t *s;
     DevView *t;
+    DevRotGroup *r;
     float *f, *g;
-    return views_layout(nullptr, H, W, n_views, per_view * std::max(n_views, 1), &s, &t, &f, &g);
+    return views_layout(nullptr, H, W, n_views, per_view * std::max(n_views, 1), &s, &t, &r, &f, &g);
 }
 
 static asift_status views_impl(asift_ctx *ctx, const uint8_t *d_img, int H, int W, int pitch,
@@ -539,8 +541,9 @@ static asift_status views_impl(asift_ctx *ctx, const uint8_t *d_img, int H, int 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int32_t *status;
     DevView *tab;
+    DevRotGroup *grp;
     float *src, *filt;
-    views_layout(d_workspace, H, W, n_views, tilt_filter_floats(h_views, n_views), &status, &tab, &src, &filt);
+    views_layout(d_workspace, H, W, n_views, tilt_filter_floats(h_views, n_views), &status, &tab, &grp, &src, &filt);
     std::vector<const float *> srcs(n_views, src);
     std::vector<int> pitches(n_views, src_pitch_of(W));
     std::vector<DevView> dv;
@@ -559,8 +562,14 @@ static asift_status views_impl(asift_ctx *ctx, const uint8_t *d_img, int H, int 
             e = launch_warp_lanczos(interp, tab, n_views, n_tiles, lzw, d_view_u8, d_mask, d_view_f32, s);
         return cuda_status(e);
     }
+    std::vector<DevRotGroup> groups;
+    int g_tiles = 0, hk_max = 3;
+    const int seg_w = warp_seg_width_default();
+    build_rot_groups(h_views, dv.data(), n_views, false, seg_w, groups, &g_tiles, &hk_max);
+    if (e == cudaSuccess) e = upload(ctx, grp, groups.data(), sizeof(DevRotGroup) * groups.size(), s);
     if (e == cudaSuccess) e = launch_tilt_filter(tab, n_views, wvm, s);
-    if (e == cudaSuccess) e = launch_warp(tab, n_views, n_tiles, cwm, hpm, d_view_u8, d_mask, d_view_f32, s);
+    if (e == cudaSuccess)
+        e = launch_warp(grp, (int)groups.size(), tab, g_tiles, seg_w, hk_max, d_view_u8, d_mask, d_view_f32, s);
     return cuda_status(e);
 }
 
@@ -847,6 +856,7 @@ struct Pipeline {
     OrbBuffers o{};
     MatchProblem *probs = nullptr;
     ImageConv *conv = nullptr;
+    DevRotGroup *grp = nullptr;              // rotation groups of the Lanczos-3 warp
     std::vector<float *> src;                // fp32 copy of each image
     int32_t *view_count = nullptr, *view_off = nullptr;
     asift_keypoint *kp = nullptr;
@@ -861,6 +871,8 @@ struct Pipeline {
     std::vector<DevView> h_dv;
     std::vector<MatchProblem> h_probs;
     std::vector<ImageConv> h_conv;
+    std::vector<DevRotGroup> h_grp;
+    int grp_tiles = 0, hk_max = 3, seg_w = 0;
     int n_tiles = 0, cw_max = 0, hp_max = 0, max_wv = 0, total_q = 0, total_blk = 0, n_per_view = 0;
     float *tilt_filters = nullptr;           // per view column: Gaussian + tilt filter
     long long cap_rows = 0;
@@ -954,6 +966,7 @@ static bool pipeline_layout(const asift_ctx *ctx, const PairSpec *ps, int P, con
     L.dv = b.take<DevView>(L.nv);
     L.probs = b.take<MatchProblem>(P);
     L.conv = b.take<ImageConv>(2 * P);
+    L.grp = b.take<DevRotGroup>(L.nv);
     build_levels(cfg, L.views.data(), L.nv, nullptr, nullptr, nullptr, nullptr, per_view, L.T, ctx->test_cand_cap);
     orb_layout(b, L.T, L.nv, 2 * P, cfg, L.o);
     L.tab_bytes = (size_t)((char *)(L.o.group_first + 2 * P + 1) - (char *)L.dv);
@@ -963,6 +976,7 @@ static bool pipeline_layout(const asift_ctx *ctx, const PairSpec *ps, int P, con
         c.take<DevView>(L.nv);
         c.take<MatchProblem>(P);
         c.take<ImageConv>(2 * P);
+        c.take<DevRotGroup>(L.nv);
         c.take<DevLevel>(std::max<size_t>((size_t)cfg.n_levels * L.nv, 1));
         c.take<int32_t>(2 * P + 1);
         L.tab_bytes = c.off - tab0;
@@ -1017,7 +1031,8 @@ static bool pipeline_layout(const asift_ctx *ctx, const PairSpec *ps, int P, con
 // Fills the host tables that depend on the image pointers and the outputs,
 // and packs everything that goes to the device into one blob starting at dv.
 static void pipeline_tables(Pipeline &L, const asift_pair_desc *pairs, asift_pair_match *const *outs,
-                            const int *caps, int32_t *const *d_ns, bool per_view, std::vector<unsigned char> &blob)
+                            const int *caps, int32_t *const *d_ns, bool per_view, std::vector<unsigned char> &blob,
+                            int seg_w = 0)
 {
     const int P = L.n_pairs;
     std::vector<const float *> srcs(L.nv);
@@ -1044,9 +1059,12 @@ static void pipeline_tables(Pipeline &L, const asift_pair_desc *pairs, asift_pai
     }
     build_views(L.views.data(), L.nv, srcs.data(), pitches.data(), L.level0_off.data(), per_view, L.tilt_filters,
                 L.h_dv, &L.n_tiles, &L.cw_max, &L.hp_max, &L.max_wv);
+    L.seg_w = seg_w > 0 ? seg_w : warp_seg_width_default();
+    build_rot_groups(L.views.data(), L.h_dv.data(), L.nv, per_view, L.seg_w, L.h_grp, &L.grp_tiles, &L.hk_max);
     blob.assign(L.tab_bytes, 0);
     char *b0 = (char *)L.dv;
     std::memcpy(blob.data(), L.h_dv.data(), sizeof(DevView) * L.nv);
+    std::memcpy(blob.data() + ((char *)L.grp - b0), L.h_grp.data(), sizeof(DevRotGroup) * L.h_grp.size());
     std::memcpy(blob.data() + ((char *)L.o.lv - b0), L.T.lv.data(), sizeof(DevLevel) * L.T.lv.size());
     std::memcpy(blob.data() + ((char *)L.o.group_first - b0), L.first.data(), sizeof(int32_t) * L.first.size());
     std::memcpy(blob.data() + ((char *)L.probs - b0), L.h_probs.data(), sizeof(MatchProblem) * P);
@@ -1069,8 +1087,8 @@ static cudaError_t pipeline_run(asift_ctx *ctx, const Pipeline &L, const asift_p
             } else {
                 e = launch_tilt_filter(L.dv, L.nv, L.max_wv, s);
                 if (e == cudaSuccess)
-                    e = launch_warp(L.dv, L.nv, L.n_tiles, L.cw_max, L.hp_max, L.o.arena_u8, L.o.arena_mask, nullptr,
-                                    s, tune ? tune->warp_grid : 0);
+                    e = launch_warp(L.grp, (int)L.h_grp.size(), L.dv, L.grp_tiles, L.seg_w, L.hk_max, L.o.arena_u8,
+                                    L.o.arena_mask, nullptr, s, tune ? tune->warp_grid : 0);
             }
         } else {
             for (int v = 0; v < L.nv && e == cudaSuccess; ++v) {
@@ -1080,8 +1098,10 @@ static cudaError_t pipeline_run(asift_ctx *ctx, const Pipeline &L, const asift_p
                     continue;
                 }
                 e = launch_tilt_filter(L.dv + v, 1, L.views[v].Wv, s);
+                const DevRotGroup &g = L.h_grp[v];     // per view: group v is view v alone
                 if (e == cudaSuccess)
-                    e = launch_warp(L.dv + v, 1, tiles, L.cw_max, L.hp_max, L.o.arena_u8, L.o.arena_mask, nullptr, s);
+                    e = launch_warp(L.grp + v, 1, L.dv, g.nseg * g.nbands, L.seg_w, L.hk_max, L.o.arena_u8,
+                                    L.o.arena_mask, nullptr, s);
             }
         }
     }
@@ -1213,6 +1233,27 @@ asift_status asift_eval_pairs(asift_ctx *ctx, const asift_pair_match *d_pairs, c
         return ASIFT_ERR_ARG;
     return cuda_status(launch_eval(d_pairs, d_n, cap, h_H_true, th_sq, d_rnd, n_hyp, ransac_th_sq, d_unique, d_inlier,
                                    d_hyp_counts, d_result, d_workspace, static_cast<cudaStream_t>(stream)));
+}
+
+size_t asift_sift_match_workspace_size(int nq, int nt)
+{
+    if (nq < 0 || nt < 0 || nq > (1 << 22) || nt > (1 << 22)) return 0;
+    return sift_match_workspace_bytes(nq, nt);
+}
+
+asift_status asift_sift_match(asift_ctx *ctx, const float *d_q, int nq, const int32_t *d_nq, const float *d_t, int nt,
+                              const int32_t *d_nt, double ratio, const asift_sift_kp *d_kq, const asift_sift_kp *d_kt,
+                              asift_l2_match *d_out, asift_pair_match *d_pairs, int cap, int32_t *d_n_pairs,
+                              void *d_workspace, size_t ws_bytes, void *stream)
+{
+    if (!ctx || nq < 0 || nt < 0 || nq > (1 << 22) || nt > (1 << 22) || (nq && (!d_q || !d_out)) || (nt && !d_t) ||
+        !(ratio > 0.0 && ratio <= 1.0) || cap < 0 || (d_n_pairs && d_kq && d_kt && cap > 0 && !d_pairs) ||
+        !d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255) ||
+        (reinterpret_cast<uintptr_t>(d_q) & 15) || (reinterpret_cast<uintptr_t>(d_t) & 15) ||
+        ws_bytes < sift_match_workspace_bytes(nq, nt))
+        return ASIFT_ERR_ARG;
+    return cuda_status(launch_sift_match(d_q, nq, d_nq, d_t, nt, d_nt, ratio, d_kq, d_kt, d_out, d_pairs, cap,
+                                         d_n_pairs, d_workspace, static_cast<cudaStream_t>(stream)));
 }
 
 size_t asift_sift_workspace_size(int H, int W, int max_kp)

@@ -32,6 +32,25 @@ struct DevView {
     float g[ASIFT_MAX_GAUSS];
 };
 
+// Views of one source image whose rotated canvases are identical (the same
+// cq, sq, Wr and Hr: the same longitude and scale, tilts differing) share one
+// rotation: a tile of the Lanczos-3 warp computes a band of kWarpTH canvas
+// rows over one segment of canvas columns once and applies every member
+// view's Gaussian + tilt filter to it.
+constexpr int kGroupMax = 8;
+struct DevRotGroup {
+    const float *src;       // source image as fp32 (as DevView::src)
+    int32_t src_pitch, W, H, Wr, Hr;
+    long long cq, sq;       // Q31 cos / s, sin / s of the members
+    int32_t n_views;        // members (indices into the launch's view list)
+    int32_t hK;             // largest member K + 3: the strip's halo on either side of a segment
+    int32_t nseg, nbands;   // canvas column segments (seg_w columns) and kWarpTH-row bands
+    int32_t tile_start;     // first linear tile of this group in the launch
+    int16_t lanes_x, stage_pitch;   // rotation step's warp footprint and staging pitch
+    int32_t identity;       // 1: cq = 2^31, sq = 0 (phi = 0, s = 1): the canvas is the source itself
+    int32_t view[kGroupMax];
+};
+
 constexpr int kWarpTW = 64;   // most view columns per warp tile
 constexpr int kWarpTH = 16;   // view rows per warp tile
 constexpr int kWarpThreads = 256;

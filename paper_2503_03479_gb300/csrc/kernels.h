@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "asift.h"
@@ -23,8 +24,13 @@ struct ImageConv;
 cudaError_t launch_convert_images(const ImageConv *d_list, int n, long long max_px, cudaStream_t s);
 int tilt_filter_pitch(int K);
 cudaError_t launch_tilt_filter(const DevView *d_views, int n_views, int max_wv, cudaStream_t s);
-cudaError_t launch_warp(const DevView *d_views, int n_views, int n_tiles, int cw_max, int hp_max, uint8_t *u8,
-                        uint8_t *mask, float *f32, cudaStream_t s, int grid = 0);
+struct DevRotGroup;
+int warp_seg_width_default();
+bool warp_seg_width_ok(int seg_w, int hk_max);
+void build_rot_groups(const asift_view_desc *h, const DevView *dv, int nv, bool per_view, int seg_w,
+                      std::vector<DevRotGroup> &out, int *n_tiles, int *hk_max);
+cudaError_t launch_warp(const DevRotGroup *d_groups, int n_groups, const DevView *d_views, int n_tiles, int seg_w,
+                        int hk_max, uint8_t *u8, uint8_t *mask, float *f32, cudaStream_t s, int grid = 0);
 int warp_nn_strip_width(const asift_view_desc &v, int tw);
 // warp_precise.cu
 int warp_lz_strip_width(const asift_view_desc &v, int tw, int a);
@@ -81,6 +87,11 @@ cudaError_t launch_eval(const asift_pair_match *d_pairs, const int32_t *d_n, int
 size_t sift_workspace_bytes(int W, int H, int max_kp);
 cudaError_t launch_sift(const uint8_t *d_img, int W, int H, int pitch, int max_kp, asift_sift_kp *d_kp, float *d_desc,
                         int32_t *d_n, void *d_ws, cudaStream_t s);
+// sift_match.cu
+size_t sift_match_workspace_bytes(int nq, int nt);
+cudaError_t launch_sift_match(const float *q, int nq, const int32_t *d_nq, const float *t, int nt, const int32_t *d_nt,
+                              double ratio, const asift_sift_kp *kq, const asift_sift_kp *kt, asift_l2_match *out,
+                              asift_pair_match *pairs, int cap, int32_t *d_n, void *ws, cudaStream_t s);
 size_t scale_coeff_workspace_bytes(int cap);
 cudaError_t launch_scale_coeff(const asift_pair_match *d_pairs, const int32_t *d_n, int cap, double *d_f, void *d_ws,
                                cudaStream_t s);

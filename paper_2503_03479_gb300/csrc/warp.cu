@@ -23,6 +23,8 @@
 // warp-wide search over the views' first tile index.
 #include <map>
 #include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -284,97 +286,115 @@ __device__ __forceinline__ void stage_box(float *dst, int P, const float *__rest
     }
 }
 
-__device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restrict__ views, int n_views, int cwp,
-                                               uint8_t *__restrict__ out_u8,
-                                               uint8_t *__restrict__ out_mask, float *__restrict__ out_f32)
+constexpr int kMaxChunks = 24;          // chunks of a tile's canvas strip: (seg_w + 2 hK) / kChunk, seg_w <= 1024
+
+// The first view column x in [lo, hi) whose tilt tap base max(floor(X(x)), 0)
+// is at least c (hi if none): X(x) = tq (2x - Wv + 1) + (Wr - 1) 2^31 grows with x.
+__device__ __forceinline__ int first_col_at(const DevView &V, int c, int lo, int hi)
+{
+    const long long xoff = (long long)(V.Wr - 1) * 2147483648LL;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const long long X = V.tq * (2LL * mid - V.Wv + 1) + xoff;
+        if (max((int)(X >> 32), 0) >= c) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+// One tile: canvas rows [j0, j0 + kWarpTH) of a rotation group over the
+// canvas columns [c0, c1) of segment `seg`, then every member view's columns
+// whose tilt taps start in [c0, c1) (max(floor(X), 0) in [c0, c1)).
+__device__ __forceinline__ void warp_band_tile(int tile, const DevRotGroup *__restrict__ groups, int n_groups,
+                                               const DevView *__restrict__ views, int seg_w, int cwp,
+                                               uint8_t *__restrict__ out_u8, uint8_t *__restrict__ out_mask,
+                                               float *__restrict__ out_f32)
 {
     extern __shared__ float4 smem4[];
     float *smem = reinterpret_cast<float *>(smem4);
     // Cs [kWarpTH][cwp] canvas strip (odd row pitch), then the two staging
-    // buffers [kStage][pitch] of step 1 (one of them holds the tile's filters
-    // for step 2), then the source boxes of the tile's chunks.
+    // buffers [kStage][pitch] of step 1 (the members' filters in step 2),
+    // then the source boxes of the strip's chunks.
     float *Cs = smem;
     float *Sbuf = Cs + kWarpTH * cwp;
     StageBox *Bx = reinterpret_cast<StageBox *>(Sbuf + 2 * kStageBuf);
 
-    const int vi = find_owner(views, n_views, tile, [](const DevView &v) { return v.tile_start; });
-    const DevView &V = views[vi];
-    const int lt = tile - V.tile_start;
-    const int ty = lt / V.ntx, tx = lt - ty * V.ntx;
-    const int xa = tx * V.tw, xb = min(xa + V.tw, V.Wv) - 1;
-    const int j0 = ty * kWarpTH, j1 = min(j0 + kWarpTH, V.Hv) - 1;
+    const int gi = find_owner(groups, n_groups, tile, [](const DevRotGroup &g) { return g.tile_start; });
+    const DevRotGroup &G = groups[gi];
+    const int lt = tile - G.tile_start;
+    const int band = lt / G.nseg, seg = lt - band * G.nseg;
+    const int Wr = G.Wr, W = G.W, H = G.H, hK = G.hK;
+    const int j0 = band * kWarpTH, j1 = min(j0 + kWarpTH, G.Hr) - 1;
     const int nrows = j1 - j0 + 1;
-    const int Wr = V.Wr, K = V.K, W = V.W, H = V.H;
+    const int c0 = seg * seg_w, c1 = min(c0 + seg_w, Wr);
+    const int cx0 = c0 - hK;                // strip position 0 = canvas column cx0 (clamped)
+    const int cw = (c1 - c0) + 2 * hK;
+    const int nch = (cw + kChunk - 1) / kChunk;
     const long long HALF = 2147483648LL;
-    const long long xoff = (long long)(Wr - 1) * HALF;
-    const CanvasGeom G{V.cq, V.sq, (long long)(W - 1) * HALF, (long long)(H - 1) * HALF, Wr, V.Hr};
-
-    const long long Xa = V.tq * (2LL * xa - V.Wv + 1) + xoff;
-    const long long Xb = V.tq * (2LL * xb - V.Wv + 1) + xoff;
-    const int bx0 = (int)(Xa >> 32) - 2, bx1 = (int)(Xb >> 32) + 3;   // unclamped strip of B
-    const int bw = bx1 - bx0 + 1;
-    const int cx0 = bx0 - K;                // strip of C: [cx0, cx0 + cw), covering the Gaussian
-    const int cw = bw + 2 * K;
-
+    const CanvasGeom Gm{G.cq, G.sq, (long long)(W - 1) * HALF, (long long)(H - 1) * HALF, Wr, G.Hr};
     const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     constexpr int kRowStep = kWarpThreads / kChunk;   // a thread walks its column in steps of 4 rows
-    int fbuf = -1;                                    // staging buffer holding the step-2 filters, or -1
 
-    // 1. rotated canvas strip, chunk by chunk: the source box of chunk k + 1
-    //    is copied asynchronously into one staging buffer while chunk k is
-    //    computed from the other, with one barrier per chunk (once chunk k's
-    //    copies have landed, everyone is also done with chunk k - 1's
-    //    buffer).  A warp covers a lanes_x x (32 / lanes_x) block of the
-    //    chunk (the shape and the staging pitch are chosen per view to
-    //    spread its taps over the shared-memory banks); every thread walks
-    //    down one canvas column, where moving kRowStep rows adds
-    //    2 kRowStep (sq, cq) to the Q32 source point.
-    {
-        const float *__restrict__ src = V.src;
-        const int sp = V.src_pitch, P = V.stage_pitch, ax = V.lanes_x;
+    // 1. the rotated canvas on the strip (strip position i holds canvas
+    //    column clamp(cx0 + i, 0, Wr - 1), which realises the clamped borders
+    //    of the Gaussian and of the tilt taps without per-tap clamps)
+    if (G.identity) {
+        // phi = 0, s = 1: every canvas point is a source pixel with zero
+        // fraction, where the normalised weights are the identity, so C is
+        // the source itself, copied exactly
+        const float *__restrict__ src = G.src;
+        for (int el = (int)threadIdx.x; el < nrows * cw; el += kWarpThreads) {
+            const int r = el / cw, i = el - r * cw;
+            Cs[r * cwp + i] = __ldg(src + (size_t)(j0 + r) * G.src_pitch + clampi(cx0 + i, 0, W - 1));
+        }
+        for (int k = (int)threadIdx.x; k < nch; k += kWarpThreads) {
+            StageBox b{};
+            b.interior = true;
+            b.outside = false;
+            Bx[k] = b;
+        }
+        __syncthreads();
+    } else {
+        // chunk by chunk: the source box of chunk k + 1 is copied
+        // asynchronously into one staging buffer while chunk k is computed
+        // from the other, with one barrier per chunk (once chunk k's copies
+        // have landed, everyone is also done with chunk k - 1's buffer).  A
+        // warp covers a lanes_x x (32 / lanes_x) block of the chunk (shape
+        // and staging pitch chosen per rotation to spread its taps over the
+        // shared-memory banks); every thread walks down one canvas column,
+        // where moving kRowStep rows adds 2 kRowStep (sq, cq) to the Q32
+        // source point.
+        const float *__restrict__ src = G.src;
+        const int sp = G.src_pitch, P = G.stage_pitch, ax = G.lanes_x;
         const int cpb = kChunk / ax;
         const int c = (int)(warp % cpb) * ax + (int)(lane % ax);
         const int rg = (int)(warp / cpb) * (32 / ax) + (int)(lane / ax);
         const long long xlim = (long long)(2 * W - 1) * HALF, ylim = (long long)(2 * H - 1) * HALF;
-        const long long dpx = 2LL * kRowStep * V.sq, dpy = 2LL * kRowStep * V.cq;
-        const int nch = (cw + kChunk - 1) / kChunk;
+        const long long dpx = 2LL * kRowStep * G.sq, dpy = 2LL * kRowStep * G.cq;
         // the chunks' source boxes, once per tile: lane group g (four lanes,
         // one corner each) of warp w makes the box of chunk 8 w + g
         for (int base = 0; base < nch; base += kWarpThreads / 4) {
             const int kc = base + (int)(warp * 8u + (lane >> 2)), kk = min(kc, nch - 1);
-            const int c0 = kk * kChunk, cn = min(kChunk, cw - c0);
-            const StageBox b = chunk_box(G, clampi(cx0 + c0, 0, Wr - 1), clampi(cx0 + c0 + cn - 1, 0, Wr - 1), j0,
+            const int q0 = kk * kChunk, cn = min(kChunk, cw - q0);
+            const StageBox b = chunk_box(Gm, clampi(cx0 + q0, 0, Wr - 1), clampi(cx0 + q0 + cn - 1, 0, Wr - 1), j0,
                                          j1, W, H, lane);
             if (kc < nch && (lane & 3u) == 0u) Bx[kc] = b;
         }
         __syncthreads();
-        auto box_of = [&](int k) { return Bx[k]; };
-        // The tile's step-2 filters (column c at Fs + c fp, fp = 4 mod 8 so
-        // that a warp's 8 columns fall on distinct banks) are copied into the
-        // staging buffer that the last staged chunk leaves idle.
-        const int ncols = xb - xa + 1, hp = V.hp, fp = (hp & 7) ? hp : hp + 4;
-        const bool fpre = ncols * fp <= kStageBuf;
-        auto stage_filters = [&](float *dst) {
-            for (int cc = (int)warp; cc < ncols; cc += kWarpThreads / 32)
-                for (int g = (int)lane; g < (hp >> 2); g += 32)
-                    cp_async16(dst + cc * fp + 4 * g, V.filt + (size_t)(xa + cc) * hp + 4 * g);
-        };
         // Chunks whose source lies wholly outside the image are background:
         // they are written as zeros on the way and take no staging buffer, so
         // the copies of the next staged chunk always overlap a computed one.
         auto next_staged = [&](int k, StageBox &b) {
             for (; k < nch; ++k) {
-                b = box_of(k);
+                b = Bx[k];
                 if (!b.outside) break;
-                const int c0 = k * kChunk, cn = min(kChunk, cw - c0);
+                const int q0 = k * kChunk, cn = min(kChunk, cw - q0);
                 if (c < cn)
-                    for (int r = rg; r < nrows; r += kRowStep) Cs[r * cwp + c0 + c] = 0.f;
+                    for (int r = rg; r < nrows; r += kRowStep) Cs[r * cwp + q0 + c] = 0.f;
             }
             return k;
         };
         StageBox bx;
         int k = next_staged(0, bx), buf = 0;
-        fbuf = -1;
         if (k < nch) stage_box(Sbuf, P, src, sp, bx, warp, lane);
         cp_async_commit();
         while (k < nch) {
@@ -382,20 +402,15 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
             __syncthreads();         // and everyone's; everyone is done with the other buffer (chunk k - 1)
             StageBox nb;
             const int kn = next_staged(k + 1, nb);
-            if (kn < nch) {
-                stage_box(Sbuf + (buf ^ 1) * kStageBuf, P, src, sp, nb, warp, lane);
-            } else if (fpre) {
-                stage_filters(Sbuf + (buf ^ 1) * kStageBuf);
-                fbuf = buf ^ 1;
-            }
+            if (kn < nch) stage_box(Sbuf + (buf ^ 1) * kStageBuf, P, src, sp, nb, warp, lane);
             cp_async_commit();
             const float *Ss = Sbuf + buf * kStageBuf;
-            const int c0 = k * kChunk, cn = min(kChunk, cw - c0);
+            const int q0 = k * kChunk, cn = min(kChunk, cw - q0);
             if (c < cn) {
-                const int i = clampi(cx0 + c0 + c, 0, Wr - 1);   // strip position -> canvas column (clamped)
+                const int i = clampi(cx0 + q0 + c, 0, Wr - 1);   // strip position -> canvas column (clamped)
                 long long px, py;
-                G.map(i, j0 + rg, px, py);
-                float *Cp = Cs + c0 + c;
+                Gm.map(i, j0 + rg, px, py);
+                float *Cp = Cs + q0 + c;
                 if (bx.interior) {
                     for (int r = rg; r < nrows; r += kRowStep, px += dpx, py += dpy)
                         Cp[r * cwp] = interp_interior(Ss, P, px, py, bx.sx0, bx.sy0);
@@ -428,79 +443,87 @@ __device__ __forceinline__ void warp_view_tile(int tile, const DevView *__restri
             bx = nb;
             buf ^= 1;
         }
-        if (fpre && fbuf < 0) {      // no staged chunk: the filters go to buffer 0
-            stage_filters(Sbuf);
-            fbuf = 0;
-            cp_async_commit();
-        }
         cp_async_wait<0>();
-        __syncthreads();             // zero-filled columns written after the last staged chunk, filters landed
+        __syncthreads();             // zero-filled chunks written after the last staged one
     }
 
-    // 2. Gaussian along canvas x, tilt resampling, quantisation and the
-    //    footprint mask.  Both filters act along canvas x of one row, so
-    //    per view column x they are one filter h_x over the canvas columns
-    //    x0-2-K .. x0+3+K (computed once per view by tilt_filter_kernel):
-    //    v(x, j) = sum_u h_x[u] C(x0 - 2 - K + u, j).  A warp covers 8 view
-    //    columns x 4 rows and each thread its column's rows rg, rg + 4,
-    //    rg + 8, rg + 12 (one filter load serves four rows).  The mask
-    //    needs canvas columns x0 and x0 + 1 inside the canvas and their
-    //    source points inside the shrunk footprint, tracked in Q32 as in
-    //    step 1.
-    {
-        const int hp = V.hp, nh = 2 * K + 6;
-        const int ncols = xb - xa + 1, fp = (hp & 7) ? hp : hp + 4;
-        const int c = (int)(warp * 8 + (lane & 7u)), rg = (int)(lane >> 3);
-        if (c < ncols) {
-            const int x = xa + c;
-            const long long X = V.tq * (2LL * x - V.Wv + 1) + xoff;
-            const int x0 = (int)(X >> 32);
-            const float *Cb = Cs + (x0 - 2 - K - cx0) + rg * cwp;
-            float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
-            if (fbuf >= 0) {
-                const float *h = Sbuf + fbuf * kStageBuf + c * fp;   // staged during step 1
+    // 2. for every member view: the Gaussian along canvas x, the tilt
+    //    resampling, quantisation and the footprint mask.  Both filters act
+    //    along canvas x of one row, so per view column x they are one filter
+    //    h_x over the canvas columns x0-2-K .. x0+3+K (computed once per view
+    //    by tilt_filter_kernel): v(x, j) = sum_u h_x[u] C(x0 - 2 - K + u, j).
+    //    A warp covers 8 view columns x 4 rows and each thread its column's
+    //    rows rg, rg + 4, rg + 8, rg + 12 (one filter load serves four rows).
+    //    A column whose taps lie in background chunks only is 0 with mask 0
+    //    (every canvas point there maps outside the image).  The mask needs
+    //    canvas columns x0 and x0 + 1 inside the canvas and their source
+    //    points inside the shrunk footprint, tracked in Q32 as in step 1.
+    const int rg = (int)(lane >> 3);
+    const long long xoff = (long long)(Wr - 1) * HALF;
+    const long long mxlo = HALF, mxhi = (long long)(2 * W - 3) * HALF;
+    const long long mylo = HALF, myhi = (long long)(2 * H - 3) * HALF;
+    const long long dpx = 2LL * kRowStep * G.sq, dpy = 2LL * kRowStep * G.cq;
+    for (int m = 0; m < G.n_views; ++m) {
+        const DevView &V = views[G.view[m]];
+        const int xa = first_col_at(V, c0, 0, V.Wv);
+        const int xb = c1 >= Wr ? V.Wv : first_col_at(V, c1, xa, V.Wv);
+        const int ncols = xb - xa;
+        if (ncols <= 0) continue;
+        const int K = V.K, hp = V.hp, nh = 2 * K + 6;
+        const int fp = (hp & 7) ? hp : hp + 4;   // = 4 mod 8: a warp's 8 columns on distinct banks
+        const bool staged = ncols * fp <= 2 * kStageBuf;
+        if (staged) {
+            for (int cc = (int)warp; cc < ncols; cc += kWarpThreads / 32)
+                for (int g = (int)lane; g < (hp >> 2); g += 32)
+                    cp_async16(Sbuf + cc * fp + 4 * g, V.filt + (size_t)(xa + cc) * hp + 4 * g);
+            cp_async_commit();
+            cp_async_wait<0>();
+            __syncthreads();
+        }
+        for (int cb = 0; cb < ncols; cb += kWarpThreads / 4) {
+            const int c = cb + (int)(warp * 8 + (lane & 7u));
+            if (c < ncols) {
+                const int x = xa + c;
+                const long long X = V.tq * (2LL * x - V.Wv + 1) + xoff;
+                const int x0 = (int)(X >> 32);
+                const int p0 = x0 - 2 - K - cx0;   // strip position of the first tap
+                bool bg = true;
+                for (int kc = p0 / kChunk; kc <= (p0 + nh - 1) / kChunk; ++kc) bg &= Bx[kc].outside;
+                float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+                if (!bg) {
+                    const float *Cb = Cs + p0 + rg * cwp;
+                    const float *h = staged ? Sbuf + c * fp : V.filt + (size_t)x * hp;
 #pragma unroll 4
-                for (int u = 0; u < nh; ++u) {
-                    const float hu = h[u];
-                    acc0 = fmaf(hu, Cb[u], acc0);
-                    acc1 = fmaf(hu, Cb[4 * cwp + u], acc1);
-                    acc2 = fmaf(hu, Cb[8 * cwp + u], acc2);
-                    acc3 = fmaf(hu, Cb[12 * cwp + u], acc3);
+                    for (int u = 0; u < nh; ++u) {
+                        const float hu = staged ? h[u] : __ldg(h + u);
+                        acc0 = fmaf(hu, Cb[u], acc0);
+                        acc1 = fmaf(hu, Cb[4 * cwp + u], acc1);
+                        acc2 = fmaf(hu, Cb[8 * cwp + u], acc2);
+                        acc3 = fmaf(hu, Cb[12 * cwp + u], acc3);
+                    }
                 }
-            } else {
-                const float *__restrict__ h = V.filt + (size_t)x * hp;   // too wide to stage: through L1
-#pragma unroll 4
-                for (int u = 0; u < nh; ++u) {
-                    const float hu = __ldg(h + u);
-                    acc0 = fmaf(hu, Cb[u], acc0);
-                    acc1 = fmaf(hu, Cb[4 * cwp + u], acc1);
-                    acc2 = fmaf(hu, Cb[8 * cwp + u], acc2);
-                    acc3 = fmaf(hu, Cb[12 * cwp + u], acc3);
-                }
-            }
-            const float accs[4] = {acc0, acc1, acc2, acc3};
-            const long long mxlo = HALF, mxhi = (long long)(2 * W - 3) * HALF;
-            const long long mylo = HALF, myhi = (long long)(2 * H - 3) * HALF;
-            const long long dpx = 2LL * kRowStep * V.sq, dpy = 2LL * kRowStep * V.cq;
-            const bool cols_ok = x0 >= 0 && x0 + 1 <= Wr - 1;
-            long long pxa, pya, pxb, pyb;
-            G.map(clampi(x0, 0, Wr - 1), j0 + rg, pxa, pya);
-            G.map(clampi(x0 + 1, 0, Wr - 1), j0 + rg, pxb, pyb);
+                const float accs[4] = {acc0, acc1, acc2, acc3};
+                const bool cols_ok = !bg && x0 >= 0 && x0 + 1 <= Wr - 1;
+                long long pxa, pya, pxb, pyb;
+                Gm.map(clampi(x0, 0, Wr - 1), j0 + rg, pxa, pya);
+                Gm.map(clampi(x0 + 1, 0, Wr - 1), j0 + rg, pxb, pyb);
 #pragma unroll
-            for (int q = 0; q < kWarpTH / kRowStep; ++q, pxa += dpx, pya += dpy, pxb += dpx, pyb += dpy) {
-                const int r = rg + q * kRowStep;
-                if (r >= nrows) break;
-                const int j = j0 + r;
-                const float v = accs[q];
-                const bool valid = cols_ok && pxa >= mxlo && pxa <= mxhi && pya >= mylo && pya <= myhi &&
-                                   pxb >= mxlo && pxb <= mxhi && pyb >= mylo && pyb <= myhi;
-                const size_t o = (size_t)V.out_off + (size_t)j * V.Wv + x;
-                if (out_f32) out_f32[o] = v;
-                const int q8 = __float2int_rn(v);
-                out_u8[o] = (uint8_t)min(255, max(0, q8));
-                out_mask[o] = (uint8_t)valid;
+                for (int q = 0; q < kWarpTH / kRowStep; ++q, pxa += dpx, pya += dpy, pxb += dpx, pyb += dpy) {
+                    const int r = rg + q * kRowStep;
+                    if (r >= nrows) break;
+                    const int j = j0 + r;
+                    const float v = accs[q];
+                    const bool valid = cols_ok && pxa >= mxlo && pxa <= mxhi && pya >= mylo && pya <= myhi &&
+                                       pxb >= mxlo && pxb <= mxhi && pyb >= mylo && pyb <= myhi;
+                    const size_t o = (size_t)V.out_off + (size_t)j * V.Wv + x;
+                    if (out_f32) out_f32[o] = v;
+                    const int q8 = __float2int_rn(v);
+                    out_u8[o] = (uint8_t)min(255, max(0, q8));
+                    out_mask[o] = (uint8_t)valid;
+                }
             }
         }
+        __syncthreads();             // the filters' buffer is reused by the next member
     }
 }
 
@@ -539,11 +562,12 @@ __global__ void tilt_filter_kernel(const DevView *__restrict__ views)
 
 // Grid-stride over the tiles: one CTA per tile, or a persistent grid.
 __global__ void __launch_bounds__(kWarpThreads, 3)
-warp_view_kernel(int n_tiles, const DevView *__restrict__ views, int n_views, int cwp,
-                 uint8_t *__restrict__ out_u8, uint8_t *__restrict__ out_mask, float *__restrict__ out_f32)
+warp_band_kernel(int n_tiles, const DevRotGroup *__restrict__ groups, int n_groups, const DevView *__restrict__ views,
+                 int seg_w, int cwp, uint8_t *__restrict__ out_u8, uint8_t *__restrict__ out_mask,
+                 float *__restrict__ out_f32)
 {
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        warp_view_tile(tile, views, n_views, cwp, out_u8, out_mask, out_f32);
+        warp_band_tile(tile, groups, n_groups, views, seg_w, cwp, out_u8, out_mask, out_f32);
         __syncthreads();
     }
 }
@@ -584,11 +608,65 @@ int tilt_filter_pitch(int K) { return (2 * K + 6 + 3) & ~3; }
 
 static int strip_pitch(int cw_max) { return ((cw_max + 3) & ~3) + 1; }
 
-size_t warp_smem_bytes(int cw_max, int hp_max)
+size_t warp_band_smem_bytes(int seg_w, int hk_max)
 {
-    (void)hp_max;
-    const size_t nch = (size_t)(cw_max + kChunk - 1) / kChunk;
-    return sizeof(float) * ((size_t)kWarpTH * strip_pitch(cw_max) + (size_t)2 * kStageBuf) + sizeof(StageBox) * nch;
+    return sizeof(float) * ((size_t)kWarpTH * strip_pitch(seg_w + 2 * hk_max) + (size_t)2 * kStageBuf) +
+           sizeof(StageBox) * kMaxChunks;
+}
+
+// Canvas columns per band tile: a segment keeps the strip (seg_w + 2 hK
+// columns) and the staging buffers at three CTAs per SM.
+int warp_seg_width_default() { return 384; }
+
+bool warp_seg_width_ok(int seg_w, int hk_max)
+{
+    return seg_w >= kChunk && seg_w <= 1024 && (seg_w + 2 * hk_max + kChunk - 1) / kChunk <= kMaxChunks;
+}
+
+// Groups of the views that share a rotated canvas: the same source image and
+// the same (cq, sq, Wr, Hr).  per_view: one group per view (each launched on
+// its own, tile_start 0).  Members keep the order of the view list.
+void build_rot_groups(const asift_view_desc *h, const DevView *dv, int nv, bool per_view, int seg_w,
+                      std::vector<DevRotGroup> &out, int *n_tiles, int *hk_max)
+{
+    out.clear();
+    std::map<std::tuple<const float *, long long, long long, int, int>, int> open;
+    for (int v = 0; v < nv; ++v) {
+        const auto key = std::make_tuple(dv[v].src, h[v].cq, h[v].sq, h[v].Wr, h[v].Hr);
+        auto it = per_view ? open.end() : open.find(key);
+        if (it == open.end() || out[it->second].n_views == kGroupMax) {
+            DevRotGroup g{};
+            g.src = dv[v].src;
+            g.src_pitch = dv[v].src_pitch;
+            g.W = h[v].W;
+            g.H = h[v].H;
+            g.Wr = h[v].Wr;
+            g.Hr = h[v].Hr;
+            g.cq = h[v].cq;
+            g.sq = h[v].sq;
+            g.lanes_x = dv[v].lanes_x;
+            g.stage_pitch = dv[v].stage_pitch;
+            g.identity = (h[v].cq == (1LL << 31) && h[v].sq == 0) ? 1 : 0;
+            out.push_back(g);
+            if (!per_view) open[key] = (int)out.size() - 1;
+            it = per_view ? open.end() : open.find(key);
+        }
+        DevRotGroup &g = per_view ? out.back() : out[it->second];
+        g.view[g.n_views++] = v;
+    }
+    int tiles = 0, hk = 3;
+    for (DevRotGroup &g : out) {
+        int km = 0;
+        for (int m = 0; m < g.n_views; ++m) km = std::max(km, h[g.view[m]].K);
+        g.hK = km + 3;
+        g.nseg = (g.Wr + seg_w - 1) / seg_w;
+        g.nbands = (g.Hr + kWarpTH - 1) / kWarpTH;
+        g.tile_start = per_view ? 0 : tiles;
+        tiles += g.nseg * g.nbands;
+        hk = std::max(hk, g.hK);
+    }
+    *n_tiles = tiles;
+    *hk_max = hk;
 }
 
 // The rotation step's warp footprint (lanes_x canvas columns x 32 / lanes_x
@@ -684,15 +762,17 @@ cudaError_t launch_tilt_filter(const DevView *d_views, int n_views, int max_wv, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_warp(const DevView *d_views, int n_views, int n_tiles, int cw_max, int hp_max,
-                        uint8_t *u8, uint8_t *mask, float *f32, cudaStream_t s, int grid)
+cudaError_t launch_warp(const DevRotGroup *d_groups, int n_groups, const DevView *d_views, int n_tiles, int seg_w,
+                        int hk_max, uint8_t *u8, uint8_t *mask, float *f32, cudaStream_t s, int grid)
 {
-    if (n_tiles <= 0) return cudaSuccess;
-    const size_t smem = warp_smem_bytes(cw_max, hp_max);
-    const cudaError_t e = ensure_dynamic_smem((const void *)warp_view_kernel, smem);
+    if (n_tiles <= 0 || n_groups <= 0) return cudaSuccess;
+    if (!warp_seg_width_ok(seg_w, hk_max)) return cudaErrorInvalidValue;
+    const size_t smem = warp_band_smem_bytes(seg_w, hk_max);
+    const cudaError_t e = ensure_dynamic_smem((const void *)warp_band_kernel, smem);
     if (e != cudaSuccess) return e;
     const int g = (grid > 0 && grid < n_tiles) ? grid : n_tiles;
-    warp_view_kernel<<<g, kWarpThreads, smem, s>>>(n_tiles, d_views, n_views, strip_pitch(cw_max), u8, mask, f32);
+    warp_band_kernel<<<g, kWarpThreads, smem, s>>>(n_tiles, d_groups, n_groups, d_views, seg_w,
+                                                    strip_pitch(seg_w + 2 * hk_max), u8, mask, f32);
     note_launch();
     return cudaGetLastError();
 }

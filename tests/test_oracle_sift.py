@@ -138,3 +138,55 @@ def test_sift_match_equals_brute_force():
     assert np.allclose(r.d1, srt[:, 0], rtol=0, atol=1e-9) and np.allclose(r.d2, srt[:, 1], rtol=0, atol=1e-9)
     assert np.array_equal(r.accepted, srt[:, 0] < 0.64 * srt[:, 1])
     assert r.best[3] == 7 and r.accepted[3]
+
+
+def test_sift_match_f32_exact_case_equals_brute_force():
+    """Descriptors of multiples of 1/64 make every fp32 step exact (differences,
+    squares and sums of at most 128 terms below 2^3 need 15 significant bits),
+    so the fp32 decisions equal exact brute force, ties included: the lowest
+    index is the best, and a tie makes d2 = d1 (no acceptance)."""
+    rng = np.random.default_rng(85)
+    q = (rng.integers(0, 17, (70, 128)) / 64).astype(np.float32)
+    t = (rng.integers(0, 17, (95, 128)) / 64).astype(np.float32)
+    t[40] = q[5]
+    t[41] = q[5]                       # an exact tie at distance 0
+    t[60] = q[6]
+    t[61] = q[6]
+    t[61, 0] += 1 / 64                 # nearest 0, second 1/4096
+    t[62] = q[7]
+    t[62, :4] += 1 / 64                # a clear nearest (4/4096) for the ratio test
+    r = O.sift_match_f32(q, t, 0.8)
+    d = ((q.astype(np.float64)[:, None, :] - t.astype(np.float64)[None]) ** 2).sum(-1)
+    assert np.array_equal(r.best, d.argmin(1))
+    srt = np.sort(d, 1)
+    assert np.array_equal(r.d1.astype(np.float64), srt[:, 0]) and np.array_equal(r.d2.astype(np.float64), srt[:, 1])
+    r2 = np.float32(0.8 * 0.8)
+    want = r.d1 < (r2 * r.d2).astype(np.float32)
+    assert np.array_equal(r.accepted, want)
+    assert r.best[5] == 40 and r.d1[5] == 0 and r.d2[5] == 0 and not r.accepted[5]
+    assert r.best[6] == 60 and r.d2[6] == np.float32(1 / 4096) and r.accepted[6]
+    assert r.best[7] == 62 and r.accepted[7]
+
+
+def test_sift_match_f32_agrees_with_fp64_beyond_its_error_bound():
+    """On unit descriptors the fp32 decisions equal the fp64 matcher's wherever
+    the fp64 margins exceed the fp32 error bound (|d32 - d64| <= (2u + 128u) d
+    with u = 2^-24, about 8e-6 d)."""
+    rng = np.random.default_rng(86)
+    q = rng.random((80, 128))
+    t = rng.random((300, 128))
+    for i in range(40):
+        t[100 + i] = q[i] + rng.normal(0, 0.01 + 0.01 * i, 128)
+    q = (q / np.linalg.norm(q, axis=1, keepdims=True)).astype(np.float32)
+    t = (np.abs(t) / np.linalg.norm(t, axis=1, keepdims=True)).astype(np.float32)
+    a = O.sift_match_f32(q, t, 0.8)
+    b = O.sift_match(q, t, 0.8)
+    bound = 1e-5
+    assert np.all(np.abs(a.d1 - b.d1) <= bound * b.d1 + 1e-12)
+    assert np.all(np.abs(a.d2 - b.d2) <= bound * b.d2 + 1e-12)
+    clear = (b.d2 - b.d1) > 2 * bound * b.d2
+    assert clear.sum() > 70
+    assert np.array_equal(a.best[clear], b.best[clear])
+    decided = np.abs(b.d1 - 0.64 * b.d2) > 2 * bound * b.d2
+    assert np.array_equal(a.accepted[decided], b.accepted[decided])
+    assert a.accepted.sum() > 10
