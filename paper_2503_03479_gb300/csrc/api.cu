@@ -75,6 +75,8 @@ struct LevelTables {
     int det_tiles = 0;
     long long cand_total = 0;
     long long arena_bytes = 0;    // bytes of the levels kept in the workspace arena
+    long long rows_total = 0;     // rows of all levels (mask row hulls)
+    long long rows_level0 = 0;    // of which level 0 (the first entries)
 };
 
 // cap_override > 0 (a failure-path test hook) replaces the configured capacity.
@@ -106,6 +108,8 @@ static void build_levels(const asift_orb_cfg &cfg, const asift_view_desc *views,
     T.det_tiles = 0;
     T.cand_total = 0;
     T.arena_bytes = 0;
+    T.rows_total = 0;
+    T.rows_level0 = 0;
     std::vector<long long> level_off((size_t)L * nv, -1);
     // arena layout: view-major, levels contiguous
     for (int v = 0; v < nv; ++v)
@@ -152,6 +156,9 @@ static void build_levels(const asift_orb_cfg &cfg, const asift_view_desc *views,
             d.cand_cap = cand_capacity(cfg, d.W, d.H, cand_cap_override);
             d.cand_off = (int)T.cand_total;
             T.cand_total += d.cand_cap;
+            d.row_off = (int)T.rows_total;
+            T.rows_total += d.H;
+            if (l == 0) T.rows_level0 += d.H;
             d.det_ntx = (d.W + kDetTW - 1) / kDetTW;
             const int det = d.det_ntx * ((d.H + kDetTH - 1) / kDetTH);
             d.det_tile_start = per_view ? 0 : T.det_tiles;
@@ -616,6 +623,7 @@ struct OrbBuffers {
     SlotKp *slots;
     int32_t *taken, *pool_off;
     int32_t *group_total;
+    int32_t *row_lo, *row_hi;    // mask row hulls of every level (row_off of each entry)
 };
 
 // Workspace region of the ORB stages for nv views in n_groups groups.
@@ -632,6 +640,8 @@ static void orb_layout(Bump &b, const LevelTables &T, int nv, int n_groups, cons
     o.taken = b.take<int32_t>(nl);
     o.pool_off = b.take<int32_t>(nl);
     o.group_total = b.take<int32_t>(n_groups);
+    o.row_lo = b.take<int32_t>(std::max<long long>(T.rows_total, 1));
+    o.row_hi = b.take<int32_t>(std::max<long long>(T.rows_total, 1));
 }
 
 // Runs pyramid -> detect -> select -> pool scan -> orientation + BRIEF.
@@ -646,12 +656,16 @@ static cudaError_t run_orb(asift_ctx *ctx, const LevelTables &T, int nv, int n_g
     const size_t nl = (size_t)L * nv;
     cudaError_t e = cudaMemsetAsync(o.cand_count, 0, sizeof(int32_t) * nl, s);
     if (e != cudaSuccess) return e;
+    // mask row hulls: level 0 scanned, levels >= 1 derived through the pyramid's taps
+    e = launch_mask_rows(o.lv, nv, L, (int)T.rows_level0, o.row_lo, o.row_hi, s);
+    if (e != cudaSuccess) return e;
     if (!per_view) {
         for (int l = 1; l < L && e == cudaSuccess; ++l)
             e = launch_pyramid(o.lv + (size_t)l * nv, nv, T.pyr_tiles[l], s, pyr_grid);
         prof_mark(ctx, 3, s);
         if (e == cudaSuccess)
-            e = launch_detect(o.lv, (int)nl, T.det_tiles, cfg.fast_threshold, o.cand, o.cand_count, s, det_grid);
+            e = launch_detect(o.lv, (int)nl, T.det_tiles, cfg.fast_threshold, o.cand, o.cand_count, o.row_lo, o.row_hi,
+                              s, det_grid);
         prof_mark(ctx, 4, s);
         if (e == cudaSuccess)
             e = launch_select(o.lv, (int)nl, o.cand, o.cand_count, N, o.slots, o.taken, o.status, s);
@@ -666,7 +680,8 @@ static cudaError_t run_orb(asift_ctx *ctx, const LevelTables &T, int nv, int n_g
             }
             for (int l = 0; l < L && e == cudaSuccess; ++l) {
                 const size_t i = (size_t)l * nv + v;
-                e = launch_detect(o.lv + i, 1, det_tiles_of(T.lv[i]), cfg.fast_threshold, o.cand, o.cand_count + i, s);
+                e = launch_detect(o.lv + i, 1, det_tiles_of(T.lv[i]), cfg.fast_threshold, o.cand, o.cand_count + i,
+                                  o.row_lo, o.row_hi, s);
             }
             for (int l = 0; l < L && e == cudaSuccess; ++l) {
                 const size_t i = (size_t)l * nv + v;

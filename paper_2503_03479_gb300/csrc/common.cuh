@@ -81,7 +81,18 @@ struct DevLevel {
     int32_t cand_off, cand_cap;   // candidate buffer slice
     int32_t det_tile_start, det_ntx;   // FAST/Harris/NMS tiles
     int32_t pyr_tile_start, pyr_ntx;   // pyramid tiles (levels >= 1)
+    int32_t row_off;        // first row of this level in the mask row-hull arrays
+    int32_t pad_r;
 };
+
+// Mask row hulls: for every row of every level, the smallest and largest
+// column whose mask is 1 (lo > hi when none).  Every pixel outside a row's
+// hull has mask 0, so FAST, whose 33 x 33 box needs four mask-valid corners,
+// cannot fire at (x, y) unless x - 16 and x + 16 lie in the hulls of rows
+// y - 16 and y + 16.  (The views' masks are row-convex, so the hull is the
+// valid set itself; the corner test stays the arbiter either way.)
+constexpr int32_t kHullEmptyLo = 0x7f7f7f7f;   // byte-fill 0x7f: no column yet
+constexpr int32_t kHullEmptyHi = -1;           // byte-fill 0xff
 
 struct Candidate {          // a corner that survived NMS
     long long r25;

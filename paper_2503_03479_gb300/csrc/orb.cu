@@ -1,9 +1,13 @@
 // orb.cu -- ORB on every simulated view (Sec. III-B; ORB [23]) on sm_103a.
 //
 // Stages, each one launch over all (view, level) entries of a call:
+//   mask_rows_kernel    level 0: each row's hull of mask-valid columns
+//   hull_levels_kernel  levels >= 1: the hulls implied by the previous level's
+//                       through the pyramid's taps (a superset of the valid set)
 //   pyramid_kernel      level l from level l-1: centre-aligned integer bilinear
 //                       (Q11 weights, round half up) + AND of the four mask taps
-//   detect_kernel       FAST-9 + Harris x25 + 3x3 NMS on shared-memory tiles;
+//   detect_kernel       FAST-9 + Harris x25 + 3x3 NMS on shared-memory tiles,
+//                       only where the row hulls allow mask-valid corners;
 //                       survivors appended with a warp-aggregated atomic
 //   select_kernel       per (view, level): exact top-q by (R25 desc, y, x) via
 //                       MSD radix select on a 96-bit key + bitonic sort
@@ -103,6 +107,98 @@ pyramid_kernel(int n_tiles, const DevLevel *__restrict__ lv, int n)
     }
 }
 
+// ---------------------------------------------------------------- mask row hulls
+// Level 0 of every view (the entries 0 .. n - 1): one warp per row finds the
+// first and last column whose mask is nonzero (lo > hi when none).  The row's
+// 16-byte aligned interior is read as uint4 (independent loads, so that a
+// row takes one or two memory latencies), its ragged ends byte by byte.
+__device__ __forceinline__ void hull_word(uint32_t w, int c, int &lo, int &hi)
+{
+    if (w) {
+        lo = min(lo, c + ((__ffs((int)w) - 1) >> 3));
+        hi = max(hi, c + ((31 - __clz((int)w)) >> 3));
+    }
+}
+
+__global__ void __launch_bounds__(256)
+mask_rows_kernel(const DevLevel *__restrict__ lv, int n, int rows, int32_t *__restrict__ row_lo,
+                 int32_t *__restrict__ row_hi)
+{
+    const int lane = threadIdx.x & 31;
+    for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < rows; g += (gridDim.x * blockDim.x) >> 5) {
+        const int e = find_owner(lv, n, g, [](const DevLevel &d) { return d.row_off; });
+        const DevLevel &L = lv[e];
+        const int W = L.W;
+        const uint8_t *__restrict__ m = L.mask + (size_t)(g - L.row_off) * W;
+        const int head = min(W, (int)((16 - ((uintptr_t)m & 15u)) & 15u));   // bytes before the first aligned chunk
+        const int n16 = (W - head) >> 4;                                     // aligned 16-byte chunks
+        const int tail0 = head + 16 * n16;                                   // first byte after them
+        int lo = kHullEmptyLo, hi = kHullEmptyHi;
+        if (lane < head && __ldg(m + lane)) { lo = lane; hi = lane; }      // the ragged ends, bytewise
+        for (int c = tail0 + lane; c < W; c += 32)
+            if (__ldg(m + c)) { lo = min(lo, c); hi = max(hi, c); }
+        const uint4 *__restrict__ m16 = reinterpret_cast<const uint4 *>(m + head);
+        for (int k = lane; k < n16; k += 32) {
+            const uint4 v = __ldg(m16 + k);
+            const int c = head + 16 * k;
+            hull_word(v.x, c, lo, hi);
+            hull_word(v.y, c + 4, lo, hi);
+            hull_word(v.z, c + 8, lo, hi);
+            hull_word(v.w, c + 12, lo, hi);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane == 0) {
+            row_lo[g] = lo;
+            row_hi[g] = hi;
+        }
+    }
+}
+
+// Levels >= 1 of view blockIdx.x, in order: a level-l pixel's mask is the AND
+// of the previous level's at the pyramid's four taps (columns x0(x), x1(x),
+// rows y0(y), y1(y)), so it can be 1 only if x0 >= max(lo(y0), lo(y1)) and
+// x1 <= min(hi(y0), hi(y1)); x0 and x1 grow with x, so those x form an
+// interval, found by two binary searches over the pyramid's own integer tap
+// formulas.  It holds every valid column (exactly them when the previous
+// level's rows are intervals, as the views' masks are).
+__device__ __forceinline__ int pyr_tap0(int o, int nl, int np) { return ((2 * o + 1) * np - nl) / (2 * nl); }
+
+__global__ void __launch_bounds__(256)
+hull_levels_kernel(const DevLevel *__restrict__ lv, int nv, int n_levels, int32_t *__restrict__ row_lo,
+                   int32_t *__restrict__ row_hi)
+{
+    const int v = blockIdx.x;
+    for (int l = 1; l < n_levels; ++l) {
+        const DevLevel &L = lv[(size_t)l * nv + v], &Q = lv[(size_t)(l - 1) * nv + v];
+        const int Wl = L.W, Hl = L.H, Wp = L.Wp, Hp = L.Hp;
+        for (int y = threadIdx.x; y < Hl; y += blockDim.x) {
+            const int y0 = pyr_tap0(y, Hl, Hp), y1 = min(y0 + 1, Hp - 1);
+            const int A = max(row_lo[Q.row_off + y0], row_lo[Q.row_off + y1]);
+            const int B = min(row_hi[Q.row_off + y0], row_hi[Q.row_off + y1]);
+            int lo = 0, hi = Wl;                      // first x with x0(x) >= A
+            while (lo < hi) {
+                const int m = (lo + hi) >> 1;
+                if (pyr_tap0(m, Wl, Wp) >= A) hi = m; else lo = m + 1;
+            }
+            const int a = lo;
+            lo = 0;
+            hi = Wl;                                  // first x with x1(x) > B
+            while (lo < hi) {
+                const int m = (lo + hi) >> 1;
+                if (min(pyr_tap0(m, Wl, Wp) + 1, Wp - 1) > B) hi = m; else lo = m + 1;
+            }
+            const int b = lo - 1;
+            row_lo[L.row_off + y] = a <= b ? a : kHullEmptyLo;
+            row_hi[L.row_off + y] = a <= b ? b : kHullEmptyHi;
+        }
+        __syncthreads();                              // level l done before level l + 1 reads it
+    }
+}
+
 // ---------------------------------------------------------------- staging
 // A row copy of the bytes [g, g + n) to shared memory at s, where s and g are
 // congruent mod 4, moves aligned words: word k starts at byte 4k - (g mod 4)
@@ -156,6 +252,7 @@ struct DetSmem {
     int16_t clist[kRH * kRW];
     __align__(16) uint8_t img[kSH * kSPMax];
     uint8_t isc[kRH][kRW];
+    int16_t ea[kRH], eb[kRH];   // per tile + ring row: columns c whose FAST corners can be mask-valid
     int ncl, ncand;
 };
 
@@ -204,7 +301,8 @@ __device__ __forceinline__ bool fast9_ring(const uint8_t *p, int thr)
 
 template <int P>
 __device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__restrict__ lv, int thr, Candidate *__restrict__ cand,
-              int32_t *__restrict__ cand_count, DetSmem &sm)
+              int32_t *__restrict__ cand_count, const int32_t *__restrict__ row_lo,
+              const int32_t *__restrict__ row_hi, DetSmem &sm)
 {
     auto &isc = sm.isc;
     auto &R = sm.R;
@@ -223,6 +321,27 @@ __device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__r
         return;
     const int tc = threadIdx.x % kDetCols, tr = threadIdx.x / kDetCols;
     constexpr int kThreads = kDetCols * kDetRowsPar;
+
+    // FAST can fire at (x, y) only inside the 16 px border and where the 33 x
+    // 33 box's corners can be mask-valid: x - 16 and x + 16 inside the row
+    // hulls of y - 16 and y + 16.  Per tile + ring row r (y = y0 - 1 + r) the
+    // columns c (x = x0 - 1 + c) that remain; a tile with none is done.
+    bool any = false;
+    if (threadIdx.x < kRH) {
+        const int r = (int)threadIdx.x, y = y0 - 1 + r;
+        int a = 1, b = 0;
+        if (y >= kBorder && y < H - kBorder) {
+            const int lo = max(__ldg(row_lo + L.row_off + y - kBorder), __ldg(row_lo + L.row_off + y + kBorder));
+            const int hi = min(__ldg(row_hi + L.row_off + y - kBorder), __ldg(row_hi + L.row_off + y + kBorder));
+            const int xa = max(kBorder, lo + kBorder), xb = min(W - kBorder - 1, hi - kBorder);
+            a = max(xa - (x0 - 1), 0);
+            b = min(xb - (x0 - 1), kRW - 1);
+        }
+        any = a <= b;
+        sm.ea[r] = (int16_t)(any ? a : 1);
+        sm.eb[r] = (int16_t)(any ? b : 0);
+    }
+    if (!__syncthreads_or(any)) return;
 
     if (threadIdx.x == 0) {
         ncl = 0;
@@ -271,7 +390,6 @@ __device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__r
     // survivors listed (in the Sobel buffer, unused until the gradients);
     // (b) the full test and the mask corners on the list.  Both passes append
     // with one shared atomic per warp (every lane runs every iteration).
-    const int xlo = kBorder, xhi = W - kBorder, ylo = kBorder, yhi = H - kBorder;
     const unsigned lane_id = threadIdx.x & 31u;
     static_assert(kRH * kRW <= kGH * kGW, "the survivor list fits the Sobel buffer");
     int16_t *surv = &gx[0][0];
@@ -279,8 +397,7 @@ __device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__r
     for (int k = 0; k < (kRH * kRW + kThreads - 1) / kThreads; ++k) {
         const int el = (int)threadIdx.x + k * kThreads;
         const int r = el / kRW, c = el - r * kRW;
-        const int x = x0 - 1 + c, y = y0 - 1 + r;
-        const bool pass = el < kRH * kRW && x >= xlo && x < xhi && y >= ylo && y < yhi &&
+        const bool pass = el < kRH * kRW && c >= sm.ea[r] && c <= sm.eb[r] &&
                           fast9_compass<P>(&S[(r - 1 + kHalo) * P + c - 1 + kHalo], thr);
         if (el < kRH * kRW) isc[r][c] = 0;
         const unsigned bal = __ballot_sync(0xffffffffu, pass);
@@ -400,17 +517,17 @@ __device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__r
 // CTAs per SM, what the 39.6 KB of shared memory allows.
 __global__ void __launch_bounds__(kDetCols * kDetRowsPar, 5)
 detect_kernel(int n_tiles, const DevLevel *__restrict__ lv, int n, int thr, Candidate *__restrict__ cand,
-              int32_t *__restrict__ cand_count)
+              int32_t *__restrict__ cand_count, const int32_t *__restrict__ row_lo, const int32_t *__restrict__ row_hi)
 {
     __shared__ DetSmem sm;
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int e = find_owner(lv, n, tile, [](const DevLevel &d) { return d.det_tile_start; });
         static_assert(kSPMin % 4 == 0, "pitch kSPMin + i is = i mod 4");
         switch (lv[e].W & 3) {   // P = W mod 4
-        case 0: detect_tile<kSPMin>(tile, e, lv, thr, cand, cand_count, sm); break;
-        case 1: detect_tile<kSPMin + 1>(tile, e, lv, thr, cand, cand_count, sm); break;
-        case 2: detect_tile<kSPMin + 2>(tile, e, lv, thr, cand, cand_count, sm); break;
-        default: detect_tile<kSPMin + 3>(tile, e, lv, thr, cand, cand_count, sm); break;
+        case 0: detect_tile<kSPMin>(tile, e, lv, thr, cand, cand_count, row_lo, row_hi, sm); break;
+        case 1: detect_tile<kSPMin + 1>(tile, e, lv, thr, cand, cand_count, row_lo, row_hi, sm); break;
+        case 2: detect_tile<kSPMin + 2>(tile, e, lv, thr, cand, cand_count, row_lo, row_hi, sm); break;
+        default: detect_tile<kSPMin + 3>(tile, e, lv, thr, cand, cand_count, row_lo, row_hi, sm); break;
         }
         __syncthreads();
     }
@@ -758,12 +875,26 @@ cudaError_t launch_pyramid(const DevLevel *d_lv, int n, int n_tiles, cudaStream_
     return cudaGetLastError();
 }
 
+cudaError_t launch_mask_rows(const DevLevel *d_lv, int nv, int n_levels, int rows0, int32_t *row_lo, int32_t *row_hi,
+                             cudaStream_t s)
+{
+    if (rows0 <= 0 || nv <= 0) return cudaSuccess;
+    const int blocks = std::max(1, std::min((rows0 + 7) / 8, 65535));   // a warp per row
+    mask_rows_kernel<<<blocks, 256, 0, s>>>(d_lv, nv, rows0, row_lo, row_hi);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || n_levels < 2) return e;
+    hull_levels_kernel<<<nv, 256, 0, s>>>(d_lv, nv, n_levels, row_lo, row_hi);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_detect(const DevLevel *d_lv, int n, int n_tiles, int thr, Candidate *cand, int32_t *count,
-                          cudaStream_t s, int grid)
+                          const int32_t *row_lo, const int32_t *row_hi, cudaStream_t s, int grid)
 {
     if (n_tiles <= 0) return cudaSuccess;
     const int g = (grid > 0 && grid < n_tiles) ? grid : n_tiles;
-    detect_kernel<<<g, kDetCols * kDetRowsPar, 0, s>>>(n_tiles, d_lv, n, thr, cand, count);
+    detect_kernel<<<g, kDetCols * kDetRowsPar, 0, s>>>(n_tiles, d_lv, n, thr, cand, count, row_lo, row_hi);
     note_launch();
     return cudaGetLastError();
 }
