@@ -251,7 +251,7 @@ struct DetSmem {
     int16_t gx[kGH][kGW], gy[kGH][kGW];
     int16_t clist[kRH * kRW];
     __align__(16) uint8_t img[kSH * kSPMax];
-    uint8_t isc[kRH][kRW];
+    uint32_t isc[kRH][(kRW + 31) / 32];   // corner flags of the tile + ring, one bit per column
     int16_t ea[kRH], eb[kRH];   // per tile + ring row: columns c whose FAST corners can be mask-valid
     int ncl, ncand;
 };
@@ -305,6 +305,7 @@ __device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__r
               const int32_t *__restrict__ row_hi, DetSmem &sm)
 {
     auto &isc = sm.isc;
+    constexpr int kIscWords = (kRW + 31) / 32;
     auto &R = sm.R;
     auto &gx = sm.gx;
     auto &gy = sm.gy;
@@ -319,7 +320,6 @@ __device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__r
     // tiles that hold no pixel of the border-limited region, nor a ring pixel of one
     if (x0 + kDetTW + 1 <= kBorder || y0 + kDetTH + 1 <= kBorder || x0 - 1 >= W - kBorder || y0 - 1 >= H - kBorder)
         return;
-    const int tc = threadIdx.x % kDetCols, tr = threadIdx.x / kDetCols;
     constexpr int kThreads = kDetCols * kDetRowsPar;
 
     // FAST can fire at (x, y) only inside the 16 px border and where the 33 x
@@ -347,6 +347,7 @@ __device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__r
         ncl = 0;
         sm.ncand = 0;
     }
+    if (threadIdx.x < kRH * kIscWords) (&isc[0][0])[threadIdx.x] = 0u;
     // staged pixel (r, c) = image (x0 - kHalo + c, y0 - kHalo + r), clamped,
     // at S[r * P + c].  Interior tiles with 3 spare columns of the level on
     // either side copy each row's whole containing words asynchronously
@@ -399,7 +400,6 @@ __device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__r
         const int r = el / kRW, c = el - r * kRW;
         const bool pass = el < kRH * kRW && c >= sm.ea[r] && c <= sm.eb[r] &&
                           fast9_compass<P>(&S[(r - 1 + kHalo) * P + c - 1 + kHalo], thr);
-        if (el < kRH * kRW) isc[r][c] = 0;
         const unsigned bal = __ballot_sync(0xffffffffu, pass);
         if (bal) {
             int base = 0;
@@ -426,7 +426,7 @@ __device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__r
                 flag = M[(y - b) * W + x - b] & M[(y - b) * W + x + b] & M[(y + b) * W + x - b] &
                        M[(y + b) * W + x + b];
             }
-            if (flag) isc[r][c] = flag;
+            if (flag) atomicOr(&isc[r][c >> 5], 1u << (c & 31));
         }
         const unsigned bal = __ballot_sync(0xffffffffu, flag != 0);
         if (bal) {
@@ -472,26 +472,35 @@ __device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__r
     }
     __syncthreads();
 
-    // 3x3 NMS on the tile; survivors appended with one atomic per warp
+    // 3x3 NMS at the corners of the tile proper (the list also holds the
+    // ring's); survivors appended with one atomic per warp
     const unsigned lane = threadIdx.x & 31u;
-    for (int rr = tr; rr < kDetTH; rr += kDetRowsPar) {
-        const int r = rr + 1, c = tc + 1;
-        const int x = x0 + tc, y = y0 + rr;
+    auto is_corner = [&](int r, int c) { return (isc[r][c >> 5] >> (c & 31)) & 1u; };
+#pragma unroll 1
+    for (int q0 = (int)(threadIdx.x & ~31u); q0 < nc; q0 += kThreads) {
+        const int q = q0 + (int)lane;
         bool keep = false;
         long long rv = 0;
-        if (isc[r][c]) {
-            rv = R[r][c];
-            keep = true;
+        int x = 0, y = 0;
+        if (q < nc) {
+            const int p = clist[q];
+            const int r = p / kRW, c = p - r * kRW;
+            if (r >= 1 && r <= kDetTH && c >= 1 && c <= kDetTW) {
+                x = x0 - 1 + c;
+                y = y0 - 1 + r;
+                rv = R[r][c];
+                keep = true;
 #pragma unroll
-            for (int dy = -1; dy <= 1; ++dy)
+                for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
-                for (int dx = -1; dx <= 1; ++dx) {
-                    if ((dx | dy) == 0 || !isc[r + dy][c + dx]) continue;
-                    const long long rn = R[r + dy][c + dx];
-                    // the neighbour precedes p in raster order iff dy < 0 or (dy == 0 and dx < 0)
-                    const bool n_first = dy < 0 || (dy == 0 && dx < 0);
-                    if (!(rv > rn || (rv == rn && !n_first))) keep = false;
-                }
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        if ((dx | dy) == 0 || !is_corner(r + dy, c + dx)) continue;
+                        const long long rn = R[r + dy][c + dx];
+                        // the neighbour precedes p in raster order iff dy < 0 or (dy == 0 and dx < 0)
+                        const bool n_first = dy < 0 || (dy == 0 && dx < 0);
+                        if (!(rv > rn || (rv == rn && !n_first))) keep = false;
+                    }
+            }
         }
         const unsigned ballot = __ballot_sync(0xffffffffu, keep);
         if (ballot) {
