@@ -774,8 +774,27 @@ def run_ours(args):
         ef[2].record(stream)
         torch.cuda.synchronize()
         fms, bms = ef[0].elapsed_time(ef[1]), ef[1].elapsed_time(ef[2])
+        # the parameter gradients alone (what the descent uses), and 20 steps of descent
+        A.warp_backward(ctx, ud, th, lay, vb, image_grad=False)
+        torch.cuda.synchronize()
+        ef[0].record(stream)
+        A.warp_backward(ctx, ud, th, lay, vb, image_grad=False)
+        ef[1].record(stream)
+        torch.cuda.synchronize()
+        pms = ef[0].elapsed_time(ef[1])
+        tgt = A.warp_forward(ctx, ud, th, lay)
+        start = torch.stack([torch.from_numpy(grid_t).cuda(), th[:, 1], th[:, 2] * 0, th[:, 3] * 0], 1)
+        A.refine(ctx, ud, tgt, lay, start, steps=2)
+        torch.cuda.synchronize()
+        ef[0].record(stream)
+        _, dl = A.refine(ctx, ud, tgt, lay, start, steps=20)
+        ef[1].record(stream)
+        torch.cuda.synchronize()
+        rms = ef[0].elapsed_time(ef[1])
+        dl = dl.cpu().numpy()
         diff = {"views": nd, "image": f"{HD}x{HD} fp32", "fwd_ms": fms, "bwd_ms": bms,
-                "views_per_s_fwd_bwd": nd / ((fms + bms) / 1e3)}
+                "bwd_params_only_ms": pms, "views_per_s_fwd_bwd": nd / ((fms + bms) / 1e3),
+                "descent_20_steps_ms": rms, "descent_loss_ratio_median": float(np.median(dl[-1] / dl[0]))}
         del ud
 
     # ---- coarse stage (Sec. III-B): the reference's (t, phi, s) parameter

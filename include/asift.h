@@ -375,10 +375,15 @@ typedef struct {
 } asift_pair_desc;
 
 /* Launch shapes of the batched stages (0 = one CTA per tile / the default).
- * A positive grid makes the stage's kernel persistent over its tile list. */
+ * A positive grid makes the stage's kernel persistent over its tile list.
+ * warp_seg is the tile shape of the view simulation: the canvas columns a
+ * tile rotates once and filters for every view sharing that rotation
+ * (0 = the default 384; 64 .. 1024; wider tiles recompute less of the
+ * Gaussian's halo but hold more shared memory, so fewer fit on an SM). */
 typedef struct {
     int32_t warp_grid, pyramid_grid, detect_grid, match_grid, match_target_items;
     int32_t match_engine;   /* ASIFT_MATCH_*; ASIFT_MATCH_AUTO = the context's engine */
+    int32_t warp_seg;       /* canvas columns per view-simulation tile (0 = 384) */
 } asift_tuning;
 
 typedef struct asift_plan asift_plan;
@@ -418,8 +423,11 @@ ASIFT_API void asift_plan_destroy(asift_plan *plan);
  * asift_warp_bwd takes the output gradient d_vbar (same layout) and writes the
  * image gradient d_ubar (n x H x W, overwritten) and d_pbar[4 i ..] =
  * dL/d(t, phi [per degree], tx, ty) (overwritten); the canvas and its blur are
- * recomputed, nothing is kept from the forward.  A t above t_max sets the
- * status word to ASIFT_ERR_CAPACITY.  Workspace: asift_warp_workspace_size(n).
+ * recomputed, nothing is kept from the forward.  d_ubar may be NULL: then only
+ * the parameter gradients are computed (the image gradient's scatter is
+ * skipped, as photometric descent of the parameters needs).  A t above t_max
+ * sets the status word to ASIFT_ERR_CAPACITY.  Workspace:
+ * asift_warp_workspace_size(n).
  */
 typedef struct {
     int32_t Wr, Hr, Wv, Hv, K, pad;
@@ -434,6 +442,30 @@ ASIFT_API asift_status asift_warp_bwd(asift_ctx *ctx, const float *d_u, int H, i
                                       const asift_warp_shape *h_shapes, double t_max, const float *d_vbar,
                                       const int64_t *h_voff, float *d_ubar, double *d_pbar, void *d_workspace,
                                       size_t ws_bytes, void *stream);
+
+/*
+ * Photometric descent of the view parameters (the refinement of the best
+ * simulated view's tilt and rotation; the paper has no descent, the
+ * configuration asks for one).
+ * asift_warp_loss: per view i (layout of asift_warp_fwd: h_shapes, h_voff),
+ * d_loss[i] = the mean over its pixels of (d_v - d_target)^2 (fp32 squares,
+ * fp64 sums; overwritten) and, when d_vbar is non-NULL, the gradient of the
+ * summed losses, d_vbar = 2 (d_v - d_target) / (Wv Hv) (fp32, same layout).
+ * Workspace: asift_warp_workspace_size(n).
+ * asift_warp_adam: one Adam step on d_params (n x (t, phi, tx, ty), fp64)
+ * with the gradient d_grad (as asift_warp_bwd writes it) and the moment
+ * buffers d_m, d_v (n x 4 doubles, zero before step 0): b1 = 0.9, b2 = 0.999,
+ * eps = 1e-12, step sizes h_lr[4] x decay^step, bias correction with
+ * step + 1; a view whose gradient is not finite takes a zero gradient (its
+ * moments still move it); t is clamped to [t_lo, t_hi].  Errors: ASIFT_ERR_ARG for NULL buffers, n < 1,
+ * step < 0, decay <= 0 or a t range outside [1, 11.4).
+ */
+ASIFT_API asift_status asift_warp_loss(asift_ctx *ctx, int n, const asift_warp_shape *h_shapes, const int64_t *h_voff,
+                                       const float *d_v, const float *d_target, double *d_loss, float *d_vbar,
+                                       void *d_workspace, size_t ws_bytes, void *stream);
+ASIFT_API asift_status asift_warp_adam(asift_ctx *ctx, int n, double *d_params, const double *d_grad, double *d_m,
+                                       double *d_v, int step, const double *h_lr, double decay, double t_lo,
+                                       double t_hi, void *stream);
 
 /* Debug view into match_pair's workspace after a call: device pointers to the
  * pooled keypoints / descriptors / per-query matches of each image and the

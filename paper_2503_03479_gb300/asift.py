@@ -34,7 +34,8 @@ EXPORTED = ["asift_ctx_create", "asift_ctx_destroy", "asift_ctx_orb_cfg", "asift
             "asift_plan_eval_outputs", "asift_plan_workspace", "asift_plan_set_tuning", "asift_plan_get_tuning",
             "asift_plan_autotune", "asift_plan_destroy", "asift_warp_shape_for", "asift_warp_workspace_size",
             "asift_warp_fwd", "asift_warp_bwd", "asift_ctx_set_match_engine", "asift_ctx_match_engine",
-            "asift_ctx_set_test_hook", "asift_sift_match_workspace_size", "asift_sift_match"]
+            "asift_ctx_set_test_hook", "asift_sift_match_workspace_size", "asift_sift_match", "asift_warp_loss",
+            "asift_warp_adam"]
 MATCH_AUTO, MATCH_CUDA_CORES, MATCH_TENSOR_CORES = 0, 1, 2
 HOOK_CAND_CAP, HOOK_MATCH_STALL = 1, 2
 INTERP_LANCZOS3, INTERP_NEAREST = 0, 1
@@ -79,7 +80,8 @@ class PairDesc(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("warp_grid", C.c_int32), ("pyramid_grid", C.c_int32), ("detect_grid", C.c_int32),
-                ("match_grid", C.c_int32), ("match_target_items", C.c_int32), ("match_engine", C.c_int32)]
+                ("match_grid", C.c_int32), ("match_target_items", C.c_int32), ("match_engine", C.c_int32),
+                ("warp_seg", C.c_int32)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -172,6 +174,8 @@ def load_library():
         "asift_warp_workspace_size": (sz, [i32]),
         "asift_warp_fwd": (i32, [vp, vp, i32, i32, i32, vp, vp, C.c_double, vp, vp, vp, sz, vp]),
         "asift_warp_bwd": (i32, [vp, vp, i32, i32, i32, vp, vp, C.c_double, vp, vp, vp, vp, vp, sz, vp]),
+        "asift_warp_loss": (i32, [vp, i32, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
+        "asift_warp_adam": (i32, [vp, i32, vp, vp, vp, vp, i32, vp, C.c_double, C.c_double, C.c_double, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -609,7 +613,8 @@ class TuningCache:
     (Plan.tuning()) per workload key, so that a later plan over the same
     workload skips the search (Plan(..., tuning=cache.get(key)))."""
 
-    FIELDS = ("warp_grid", "pyramid_grid", "detect_grid", "match_grid", "match_target_items", "match_engine")
+    FIELDS = ("warp_grid", "pyramid_grid", "detect_grid", "match_grid", "match_target_items", "match_engine",
+              "warp_seg")
 
     def __init__(self, path: str):
         self.path = path
@@ -833,12 +838,14 @@ def warp_forward(ctx: Context, u: torch.Tensor, params: torch.Tensor, lay: WarpL
     return out
 
 
-def warp_backward(ctx: Context, u: torch.Tensor, params: torch.Tensor, lay: WarpLayout, vbar: torch.Tensor):
+def warp_backward(ctx: Context, u: torch.Tensor, params: torch.Tensor, lay: WarpLayout, vbar: torch.Tensor,
+                  image_grad: bool = True):
+    """(image gradient or None, parameter gradients (n, 4) fp64)."""
     n = u.shape[0]
     u = u.contiguous()
     params = params.contiguous()
     vbar = vbar.contiguous().to(torch.float32)
-    ubar = torch.empty_like(u)
+    ubar = torch.empty_like(u) if image_grad else None
     pbar = torch.empty((n, 4), dtype=torch.float64, device=u.device)
     ws = ctx.workspace("warp_bwd", ctx.L.asift_warp_workspace_size(n))
     _check("asift_warp_bwd", ctx.L.asift_warp_bwd(ctx._ctx, _ptr(u), lay.H, lay.W, n, _ptr(params), lay.shapes,
@@ -866,39 +873,42 @@ class WarpFunction(torch.autograd.Function):
                 pbar if fctx.needs_input_grad[1] else None, None, None)
 
 
+def warp_loss(ctx: Context, v: torch.Tensor, target: torch.Tensor, lay: WarpLayout, with_grad: bool = True):
+    """Per-view mean squared photometric error (fp64 (n,)) and its gradient (flat fp32 or None)."""
+    n = len(lay.voff)
+    loss = torch.empty(n, dtype=torch.float64, device=v.device)
+    vbar = torch.empty_like(v) if with_grad else None
+    ws = ctx.workspace("warp_loss", ctx.L.asift_warp_workspace_size(n))
+    _check("asift_warp_loss", ctx.L.asift_warp_loss(ctx._ctx, n, lay.shapes, lay.voff.ctypes.data_as(C.c_void_p),
+                                                    _ptr(v), _ptr(target), _ptr(loss), _ptr(vbar), _ptr(ws),
+                                                    ws.numel(), _stream()))
+    return loss, vbar
+
+
 def refine(ctx: Context, u: torch.Tensor, target: torch.Tensor, lay: WarpLayout, theta0: torch.Tensor,
            steps: int = 20, lr=(0.1, 2.0, 1.0, 1.0), decay: float = 0.88, t_range=(1.0, None)):
-    """Photometric descent of the view parameters: Adam (step sizes lr for
-    t, phi in degrees, tx, ty, decayed by `decay` per step) on the mean squared
-    difference between warp(u, theta) and the target views (one loss per view,
-    summed).  Returns (theta history [steps+1, n, 4], loss history [steps+1, n])."""
-    theta = theta0.clone().to(torch.float64).requires_grad_(True)
-    lrs = torch.tensor(lr, dtype=torch.float64, device=theta.device)
+    """Photometric descent of the view parameters: Adam (step sizes lr for t,
+    phi in degrees, tx, ty, decayed by `decay` per step) on the mean squared
+    difference between warp(u, theta) and the target views (one loss per
+    view, summed).  Every step runs in the library: the warp, the loss and its
+    gradient (asift_warp_loss), the parameter gradients (asift_warp_bwd
+    without the image gradient) and the update (asift_warp_adam).  Returns
+    (theta history [steps+1, n, 4], loss history [steps+1, n])."""
+    n = theta0.shape[0]
+    theta = theta0.detach().clone().to(torch.float64).contiguous()
     m = torch.zeros_like(theta)
     v = torch.zeros_like(theta)
-    b1, b2, eps = 0.9, 0.999, 1e-12
-    hist, losses = [theta.detach().clone()], []
     tmax = lay.t_max if t_range[1] is None else t_range[1]
-    sizes = [lay.shapes[i].Wv * lay.shapes[i].Hv for i in range(len(lay.voff))]
-    seg = torch.repeat_interleave(torch.arange(len(sizes), device=u.device),
-                                  torch.tensor(sizes, device=u.device))
+    lrs = (C.c_double * 4)(*[float(x) for x in lr])
+    hist, losses = [theta.clone()], []
     for k in range(steps + 1):
-        out = WarpFunction.apply(u, theta, ctx, lay)
-        d2 = (out[: lay.total] - target[: lay.total]) ** 2
-        per_view = torch.zeros(len(sizes), dtype=torch.float64, device=u.device).index_add_(0, seg, d2.double())
-        per_view = per_view / torch.tensor(sizes, dtype=torch.float64, device=u.device)
-        losses.append(per_view.detach().clone())
+        out = warp_forward(ctx, u, theta, lay)
+        loss, vbar = warp_loss(ctx, out, target, lay, with_grad=k < steps)
+        losses.append(loss)
         if k == steps:
             break
-        g, = torch.autograd.grad(per_view.sum(), theta)
-        with torch.no_grad():
-            # a view whose gradient is not finite keeps its parameters this step
-            g = torch.where(torch.isfinite(g).all(1, keepdim=True), g, torch.zeros_like(g))
-            m.mul_(b1).add_(g, alpha=1 - b1)
-            v.mul_(b2).addcmul_(g, g, value=1 - b2)
-            mh = m / (1 - b1 ** (k + 1))
-            vh = v / (1 - b2 ** (k + 1))
-            theta -= (decay ** k) * lrs * mh / (vh.sqrt() + eps)
-            theta[:, 0].clamp_(t_range[0], tmax)
-        hist.append(theta.detach().clone())
+        _, g = warp_backward(ctx, u, theta, lay, vbar, image_grad=False)
+        _check("asift_warp_adam", ctx.L.asift_warp_adam(ctx._ctx, n, _ptr(theta), _ptr(g), _ptr(m), _ptr(v), k, lrs,
+                                                        float(decay), float(t_range[0]), float(tmax), _stream()))
+        hist.append(theta.clone())
     return torch.stack(hist), torch.stack(losses)

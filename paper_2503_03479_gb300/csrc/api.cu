@@ -1324,7 +1324,8 @@ asift_status match_pair_view_counts(asift_ctx *ctx, int H1, int W1, int H2, int 
 static bool tuning_ok(const asift_tuning &t)
 {
     return t.warp_grid >= 0 && t.pyramid_grid >= 0 && t.detect_grid >= 0 && t.match_grid >= 0 &&
-           t.match_target_items >= 0 && t.match_engine >= ASIFT_MATCH_AUTO && t.match_engine <= ASIFT_MATCH_TENSOR_CORES;
+           t.match_target_items >= 0 && t.match_engine >= ASIFT_MATCH_AUTO && t.match_engine <= ASIFT_MATCH_TENSOR_CORES &&
+           (t.warp_seg == 0 || (t.warp_seg >= 64 && t.warp_seg <= 1024));
 }
 
 struct asift_plan {
@@ -1357,9 +1358,32 @@ static void plan_free(asift_plan *p)
     delete p;
 }
 
+// The view simulation's rotation groups for the plan's warp_seg (rebuilt and
+// uploaded when it changed).
+static cudaError_t plan_regroup(asift_plan *p)
+{
+    asift::Pipeline &L = p->L;
+    const int seg = p->tune.warp_seg > 0 ? p->tune.warp_seg : asift::warp_seg_width_default();
+    if (seg == L.seg_w) return cudaSuccess;
+    std::vector<DevRotGroup> g;
+    int tiles = 0, hk = 3;
+    asift::build_rot_groups(L.views.data(), L.h_dv.data(), L.nv, false, seg, g, &tiles, &hk);
+    if (!asift::warp_seg_width_ok(seg, hk)) return cudaErrorInvalidValue;
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(L.grp, g.data(), sizeof(DevRotGroup) * g.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    L.h_grp.swap(g);
+    L.grp_tiles = tiles;
+    L.hk_max = hk;
+    L.seg_w = seg;
+    return cudaSuccess;
+}
+
 // Captures the launch sequence of the plan in a CUDA graph on its stream.
 static cudaError_t plan_capture(asift_plan *p)
 {
+    cudaError_t r0 = plan_regroup(p);
+    if (r0 != cudaSuccess) return r0;
     if (p->exec) { cudaGraphExecDestroy(p->exec); p->exec = nullptr; }
     if (p->graph) { cudaGraphDestroy(p->graph); p->graph = nullptr; }
     if (!p->use_graph) return cudaSuccess;
@@ -1434,7 +1458,12 @@ asift_status asift_plan_create(asift_ctx *ctx, const asift_pair_desc *h_pairs, i
         return ASIFT_ERR_CUDA;
     }
     std::vector<unsigned char> blob;
-    asift::pipeline_tables(p->L, p->pairs.data(), p->outs.data(), p->caps.data(), ns.data(), false, blob);
+    asift::pipeline_tables(p->L, p->pairs.data(), p->outs.data(), p->caps.data(), ns.data(), false, blob,
+                           p->tune.warp_seg);
+    if (!asift::warp_seg_width_ok(p->L.seg_w, p->L.hk_max)) {
+        plan_free(p);
+        return ASIFT_ERR_ARG;
+    }
     cudaError_t e = cudaMemcpyAsync(p->L.dv, blob.data(), blob.size(), cudaMemcpyHostToDevice, p->stream);
     // one plain run validates the sequence and sets the kernels' attributes before capture
     if (e == cudaSuccess) e = asift::pipeline_run(ctx, p->L, pc, false, &p->tune, p->stream);
@@ -1517,9 +1546,16 @@ asift_status asift_plan_set_tuning(asift_plan *plan, const asift_tuning *tuning)
 {
     if (!plan || !tuning) return ASIFT_ERR_ARG;
     if (!tuning_ok(*tuning)) return ASIFT_ERR_ARG;
+    const asift_tuning old = plan->tune;
     plan->tune = *tuning;
     if (cudaStreamSynchronize(plan->stream) != cudaSuccess) return ASIFT_ERR_CUDA;
-    return cuda_status(plan_capture(plan));
+    const cudaError_t e = plan_capture(plan);
+    if (e == cudaErrorInvalidValue) {           // a tile shape the views do not fit
+        plan->tune = old;
+        plan_capture(plan);
+        return ASIFT_ERR_ARG;
+    }
+    return cuda_status(e);
 }
 
 asift_status asift_plan_get_tuning(const asift_plan *plan, asift_tuning *out)
@@ -1560,6 +1596,7 @@ asift_status asift_plan_autotune(asift_plan *plan, int reps, asift_tuning *out)
     };
     asift_tuning &t = plan->tune;
     std::vector<Knob> knobs = {
+        {&t.warp_seg, {0, 256, 512, 768}},     // the view simulation's tile shape (0 = 384)
         {&t.warp_grid, {0, 2 * sms, 3 * sms}},
         {&t.pyramid_grid, {0, 4 * sms, 8 * sms}},
         {&t.detect_grid, {0, 4 * sms, 8 * sms}},
@@ -1572,6 +1609,11 @@ asift_status asift_plan_autotune(asift_plan *plan, int reps, asift_tuning *out)
         for (int c : k.cands) {
             *k.field = c;
             e = plan_capture(plan);
+            if (e == cudaErrorInvalidValue) {      // a tile shape these views do not fit: skipped
+                cudaGetLastError();
+                e = cudaSuccess;
+                continue;
+            }
             float ms = 0.f;
             if (e == cudaSuccess) e = plan_time(plan, reps, &ms);
             if (e != cudaSuccess) break;
@@ -1639,7 +1681,7 @@ static asift_status warp_call(bool backward, asift_ctx *ctx, const float *d_u, i
                               void *d_ws, size_t ws_bytes, void *stream)
 {
     if (!ctx || !d_u || H < 1 || W < 1 || n < 1 || !d_params || !h_shapes || !h_voff || !d_ws ||
-        !(t_max >= 1.0 && t_max < 11.4) || (!backward && !d_v) || (backward && (!d_vbar || !d_ubar || !d_pbar)))
+        !(t_max >= 1.0 && t_max < 11.4) || (!backward && !d_v) || (backward && (!d_vbar || !d_pbar)))
         return ASIFT_ERR_ARG;
     if (ws_bytes < asift_warp_workspace_size(n)) return ASIFT_ERR_ARG;
     Bump b(d_ws);
@@ -1654,7 +1696,7 @@ static asift_status warp_call(bool backward, asift_ctx *ctx, const float *d_u, i
         DiffView &d = h[i];
         d = DiffView{};
         d.u = d_u + (size_t)i * H * W;
-        d.ubar = backward ? d_ubar + (size_t)i * H * W : nullptr;
+        d.ubar = (backward && d_ubar) ? d_ubar + (size_t)i * H * W : nullptr;
         d.vbar = backward ? d_vbar + h_voff[i] : nullptr;
         d.out = backward ? nullptr : d_v + h_voff[i];
         d.param = d_params + 4 * (size_t)i;
@@ -1675,7 +1717,7 @@ static asift_status warp_call(bool backward, asift_ctx *ctx, const float *d_u, i
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = upload(ctx, tab, h.data(), sizeof(DiffView) * n, s);
-    if (e == cudaSuccess && backward) e = cudaMemsetAsync(d_ubar, 0, sizeof(float) * (size_t)n * H * W, s);
+    if (e == cudaSuccess && backward && d_ubar) e = cudaMemsetAsync(d_ubar, 0, sizeof(float) * (size_t)n * H * W, s);
     if (e == cudaSuccess && backward) e = cudaMemsetAsync(d_pbar, 0, sizeof(double) * 4 * (size_t)n, s);
     if (e == cudaSuccess) e = launch_dwarp(backward, tab, n, tiles, cw_max, bw_max, status, s);
     return cuda_status(e);
@@ -1695,6 +1737,47 @@ asift_status asift_warp_bwd(asift_ctx *ctx, const float *d_u, int H, int W, int 
 {
     return warp_call(true, ctx, d_u, H, W, n, d_params, h_shapes, t_max, nullptr, d_vbar, h_voff, d_ubar, d_pbar,
                      d_workspace, ws_bytes, stream);
+}
+
+asift_status asift_warp_loss(asift_ctx *ctx, int n, const asift_warp_shape *h_shapes, const int64_t *h_voff,
+                             const float *d_v, const float *d_target, double *d_loss, float *d_vbar, void *d_workspace,
+                             size_t ws_bytes, void *stream)
+{
+    if (!ctx || n < 1 || !h_shapes || !h_voff || !d_v || !d_target || !d_loss || !d_workspace ||
+        ws_bytes < asift_warp_workspace_size(n))
+        return ASIFT_ERR_ARG;
+    Bump b(d_workspace);
+    b.take<int32_t>(64);
+    WarpSeg *tab = reinterpret_cast<WarpSeg *>(b.take<DiffView>(n));   // the view table's room holds the segments
+    std::vector<WarpSeg> h(n);
+    long long mx = 0;
+    for (int i = 0; i < n; ++i) {
+        if (h_shapes[i].Wv < 1 || h_shapes[i].Hv < 1 || h_voff[i] < 0) return ASIFT_ERR_ARG;
+        h[i].off = h_voff[i];
+        h[i].count = (long long)h_shapes[i].Wv * h_shapes[i].Hv;
+        mx = std::max(mx, h[i].count);
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = upload(ctx, tab, h.data(), sizeof(WarpSeg) * n, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_loss, 0, sizeof(double) * n, s);
+    if (e == cudaSuccess) e = launch_warp_loss(tab, n, mx, d_v, d_target, d_loss, d_vbar, s);
+    return cuda_status(e);
+}
+
+asift_status asift_warp_adam(asift_ctx *ctx, int n, double *d_params, const double *d_grad, double *d_m, double *d_v,
+                             int step, const double *h_lr, double decay, double t_lo, double t_hi, void *stream)
+{
+    if (!ctx || n < 1 || !d_params || !d_grad || !d_m || !d_v || step < 0 || !h_lr || !(decay > 0.0) ||
+        !(t_lo >= 1.0 && t_lo <= t_hi && t_hi < 11.4))
+        return ASIFT_ERR_ARG;
+    AdamArgs a{};
+    for (int k = 0; k < 4; ++k) a.lr[k] = h_lr[k];
+    a.scale = std::pow(decay, (double)step);
+    a.c1 = 1.0 - std::pow(0.9, (double)step + 1);
+    a.c2 = 1.0 - std::pow(0.999, (double)step + 1);
+    a.t_lo = t_lo;
+    a.t_hi = t_hi;
+    return cuda_status(launch_warp_adam(n, d_params, d_grad, d_m, d_v, a, static_cast<cudaStream_t>(stream)));
 }
 
 }  // extern "C"

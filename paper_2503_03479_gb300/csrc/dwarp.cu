@@ -367,6 +367,65 @@ dwarp_bwd_kernel(const DiffView *__restrict__ views, int n_views, int cw_max, in
     }
 }
 
+// ---------------------------------------------------------------- photometric descent
+// Per view i (blockIdx.y): loss_i = mean over its pixels of (v - target)^2
+// (squares in fp32, sums in fp64) and, when vbar is given, the gradient of
+// the summed losses, vbar = 2 (v - target) / count_i.
+__global__ void __launch_bounds__(256)
+warp_loss_kernel(const WarpSeg *__restrict__ segs, const float *__restrict__ v, const float *__restrict__ target,
+                 double *__restrict__ loss, float *__restrict__ vbar)
+{
+    __shared__ double red[8];
+    const WarpSeg S = segs[blockIdx.y];
+    const float inv2 = 2.0f / (float)S.count;
+    double acc = 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < S.count;
+         k += (long long)gridDim.x * blockDim.x) {
+        const float d = v[S.off + k] - target[S.off + k];
+        acc += (double)(d * d);
+        if (vbar) vbar[S.off + k] = inv2 * d;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += red[w];
+        atomicAdd(loss + blockIdx.y, t / (double)S.count);
+    }
+}
+
+// One thread per view: Adam on (t, phi, tx, ty) with step sizes lr scaled by
+// decay^step, b1 = 0.9, b2 = 0.999, eps = 1e-12; a view whose gradient is not
+// finite takes a zero gradient (its moments still move it); t is clamped to
+// [t_lo, t_hi].
+__global__ void __launch_bounds__(128)
+warp_adam_kernel(int n, double *__restrict__ params, const double *__restrict__ grad, double *__restrict__ m,
+                 double *__restrict__ v, const AdamArgs a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    bool finite = true;
+    double g[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        g[k] = grad[4 * i + k];
+        finite &= isfinite(g[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double gk = finite ? g[k] : 0.0;
+        const double mk = 0.9 * m[4 * i + k] + 0.1 * gk;
+        const double vk = 0.999 * v[4 * i + k] + 0.001 * gk * gk;
+        m[4 * i + k] = mk;
+        v[4 * i + k] = vk;
+        double p = params[4 * i + k] - a.scale * a.lr[k] * (mk / a.c1) / (sqrt(vk / a.c2) + 1e-12);
+        if (k == 0) p = fmin(fmax(p, a.t_lo), a.t_hi);
+        params[4 * i + k] = p;
+    }
+}
+
 // ---------------------------------------------------------------- host side
 void dwarp_strip_widths(int Wv, double t_max, int K, int *cw, int *bw)
 {
@@ -396,6 +455,25 @@ cudaError_t launch_dwarp(bool backward, const DiffView *d_views, int n_views, in
         if (e != cudaSuccess) return e;
         dwarp_fwd_kernel<<<n_tiles, kDThreads, smem, s>>>(d_views, n_views, cw_max, bw_max, status);
     }
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_warp_loss(const WarpSeg *d_segs, int n, long long max_count, const float *v, const float *target,
+                             double *loss, float *vbar, cudaStream_t s)
+{
+    if (n <= 0 || max_count <= 0) return cudaSuccess;
+    const int bx = (int)std::min<long long>((max_count + 255) / 256, 64);
+    warp_loss_kernel<<<dim3(bx, n), 256, 0, s>>>(d_segs, v, target, loss, vbar);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_warp_adam(int n, double *params, const double *grad, double *m, double *v, const AdamArgs &a,
+                             cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    warp_adam_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, params, grad, m, v, a);
     note_launch();
     return cudaGetLastError();
 }

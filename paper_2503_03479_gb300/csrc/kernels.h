@@ -123,6 +123,19 @@ void dwarp_strip_widths(int Wv, double t_max, int K, int *cw, int *bw);
 int dwarp_tiles(int Wv, int Hv, int *ntx);
 cudaError_t launch_dwarp(bool backward, const DiffView *d_views, int n_views, int n_tiles, int cw_max, int bw_max,
                          int32_t *status, cudaStream_t s);
+struct WarpSeg {            // one view of a flat view buffer
+    long long off, count;
+};
+struct AdamArgs {           // one Adam step of the view parameters (t, phi, tx, ty)
+    double lr[4];
+    double scale;           // decay^step
+    double c1, c2;          // bias corrections 1 - b1^(step+1), 1 - b2^(step+1)
+    double t_lo, t_hi;
+};
+cudaError_t launch_warp_loss(const WarpSeg *d_segs, int n, long long max_count, const float *v, const float *target,
+                             double *loss, float *vbar, cudaStream_t s);
+cudaError_t launch_warp_adam(int n, double *params, const double *grad, double *m, double *v, const AdamArgs &a,
+                             cudaStream_t s);
 
 // tables.cpp (host; each table generated from its written definition)
 void make_view_desc(int H, int W, double t, double phi_deg, int k, int j, double scale, asift_view_desc *v);

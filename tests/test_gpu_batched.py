@@ -89,7 +89,8 @@ def test_autotuner_picks_valid_shapes_and_keeps_results(A):
     plan = A.Plan(ctx, [p[0] for p in pairs], [p[1] for p in pairs], kmax=KMAX)
     t = plan.autotune(reps=2)
     assert set(t) == {"warp_grid", "pyramid_grid", "detect_grid", "match_grid", "match_target_items",
-                      "match_engine"}
+                      "match_engine", "warp_seg"}
+    assert t["warp_seg"] in (0, 256, 512, 768)
     assert all(v >= 0 for v in t.values())
     # the tuner picks an engine explicitly when the device has tensor cores
     major, _ = torch.cuda.get_device_capability()
@@ -99,6 +100,28 @@ def test_autotuner_picks_valid_shapes_and_keeps_results(A):
     torch.cuda.synchronize()
     for i in range(len(pairs)):
         assert plan.pairs(i).tobytes() == ref[i], i
+    plan.close()
+
+
+def test_every_warp_tile_shape_gives_the_same_pairs(A):
+    """The view simulation's tile shape (canvas columns per tile) is speed
+    only: every shape the autotuner tries, and the widest, give the same
+    accepted pairs, bit for bit."""
+    ctx = A.Context(n_levels=L_, n_features=N_)
+    pairs = _pairs()
+    ref = _reference(A, ctx, pairs)
+    plan = A.Plan(ctx, [p[0] for p in pairs], [p[1] for p in pairs], kmax=KMAX)
+    base = plan.tuning()
+    for seg in (64, 256, 512, 768, 1024):
+        plan.set_tuning(dict(base, warp_seg=seg))
+        assert plan.tuning()["warp_seg"] == seg
+        plan.run()
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        for i in range(len(pairs)):
+            assert plan.pairs(i).tobytes() == ref[i], (seg, i)
+    with pytest.raises(A.AsiftError):
+        plan.set_tuning(dict(base, warp_seg=32))
     plan.close()
 
 

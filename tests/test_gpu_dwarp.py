@@ -10,6 +10,7 @@ parameter gradients within 2e-3 relative (fp32 sums of ~1e5 terms, atomics in
 arbitrary order); GPU gradient vs fp64 central differences (step 1e-3) within
 1e-2 relative.
 """
+import ctypes as C
 import math
 
 import numpy as np
@@ -151,3 +152,61 @@ def test_photometric_descent_refines_tilt_and_rotation(A):
     assert np.median(e1[:, 1] / np.maximum(e0[:, 1], 1e-9)) < 0.2       # rotation
     assert np.median(e1[:, 0] / np.maximum(e0[:, 0], 1e-9)) < 0.5       # tilt
     assert np.median(np.abs(e1[:, 2:]).max(1)) < 1.0                     # translation within a pixel
+
+
+def test_loss_gradient_and_adam_step(A):
+    """asift_warp_loss against numpy (fp32 squares, fp64 mean; the gradient
+    2 d / count bit for bit), asift_warp_adam against the Adam update written
+    out in fp64 (a view with a non-finite gradient takes a zero gradient, t
+    clamped),
+    and the parameter-only backward equal to the full one's parameter part."""
+    ctx = A.Context()
+    rng = np.random.default_rng(12)
+    n, H, W = 5, 96, 96
+    imgs = np.stack([synth.texture(H, W, 950 + i).astype(np.float32) / 255.0 for i in range(n)])
+    th = np.stack([rng.uniform(1.2, 4.0, n), rng.uniform(0, 180, n), rng.uniform(-3, 3, n), rng.uniform(-3, 3, n)], 1)
+    lay = A.warp_layout(H, W, th[:, 0], th[:, 1], 4.5)
+    u = torch.from_numpy(imgs).cuda()
+    tht = torch.from_numpy(th).cuda()
+    v = A.warp_forward(ctx, u, tht, lay)
+    tgt = A.warp_forward(ctx, u, tht + torch.tensor([0.05, 1.0, 0.3, -0.2], dtype=torch.float64, device="cuda"), lay)
+    loss, vbar = A.warp_loss(ctx, v, tgt, lay)
+    vh, th_, lh, gh = v.cpu().numpy(), tgt.cpu().numpy(), loss.cpu().numpy(), vbar.cpu().numpy()
+    for i in range(n):
+        o, cnt = int(lay.voff[i]), lay.shapes[i].Wv * lay.shapes[i].Hv
+        d = vh[o:o + cnt] - th_[o:o + cnt]
+        want = float(np.sum((d * d).astype(np.float64))) / cnt
+        assert abs(lh[i] - want) <= 1e-9 * want + 1e-15, (i, lh[i], want)
+        assert np.array_equal(gh[o:o + cnt], np.float32(2.0 / cnt) * d)
+    # the parameter-only backward gives the full backward's parameter gradients
+    ub, pb = A.warp_backward(ctx, u, tht, lay, vbar)
+    none, pb2 = A.warp_backward(ctx, u, tht, lay, vbar, image_grad=False)
+    assert none is None
+    assert torch.allclose(pb, pb2, rtol=1e-6, atol=1e-9)
+    # one Adam step
+    g = pb2.clone()
+    g[3, 1] = float("nan")                        # view 3 takes a zero gradient
+    m0 = torch.from_numpy(rng.normal(0, 1e-3, (n, 4))).cuda()
+    v0 = torch.from_numpy(rng.uniform(0, 1e-4, (n, 4))).cuda()
+    p = tht.clone()
+    p[0, 0] = 4.49                                # pushed past t_hi by the step below
+    g[0, 0] = -50.0
+    p0, gh, mh, vh0 = p.cpu().numpy(), g.cpu().numpy(), m0.cpu().numpy(), v0.cpu().numpy()
+    m, vv = m0.clone(), v0.clone()
+    lr = (C.c_double * 4)(0.1, 2.0, 1.0, 1.0)
+    step, decay = 3, 0.88
+    assert ctx.L.asift_warp_adam(ctx._ctx, n, C.c_void_p(p.data_ptr()), C.c_void_p(g.data_ptr()),
+                                 C.c_void_p(m.data_ptr()), C.c_void_p(vv.data_ptr()), step, lr, decay, 1.0, 4.5,
+                                 C.c_void_p(torch.cuda.current_stream().cuda_stream)) == A.ASIFT_OK
+    torch.cuda.synchronize()
+    want = p0.copy()
+    for i in range(n):
+        gi = gh[i] if np.isfinite(gh[i]).all() else np.zeros(4)
+        mi = 0.9 * mh[i] + 0.1 * gi
+        vi = 0.999 * vh0[i] + 0.001 * gi * gi
+        upd = decay ** step * np.array([0.1, 2.0, 1.0, 1.0]) * (mi / (1 - 0.9 ** (step + 1))) / \
+            (np.sqrt(vi / (1 - 0.999 ** (step + 1))) + 1e-12)
+        want[i] = p0[i] - upd
+        want[i, 0] = min(max(want[i, 0], 1.0), 4.5)
+    assert np.allclose(p.cpu().numpy(), want, rtol=1e-12, atol=1e-12)
+    assert p[0, 0].item() == 4.5

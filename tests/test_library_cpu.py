@@ -169,7 +169,7 @@ def test_tuning_cache_round_trip(A, tmp_path):
     other = A.TuningCache.key([(768, 1024, 768, 1024)], 5, 8, 1000, "GB300", coarse=True)
     assert key != other and c.get(key) is None
     t = {"warp_grid": 456, "pyramid_grid": 0, "detect_grid": 912, "match_grid": 152, "match_target_items": 4,
-         "match_engine": A.MATCH_TENSOR_CORES}
+         "match_engine": A.MATCH_TENSOR_CORES, "warp_seg": 512}
     c.put(key, t)
     assert A.TuningCache(path).get(key) == t and A.TuningCache(path).get(other) is None
     # the fields of the C struct, nothing else
