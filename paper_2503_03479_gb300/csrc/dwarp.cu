@@ -9,12 +9,14 @@
 // X = t (x' - (Wv-1)/2) + (Wr-1)/2.  Canvas and view sizes are fixed.
 //
 // Backward (one CTA per view tile, no state kept from the forward): the canvas
-// strip C and its blur B are recomputed in shared memory; the tile's part of
-// B-bar (the tilt transposed) and of C-bar (the Gaussian transposed) are
-// accumulated with shared-memory atomics; C-bar then scatters into u-bar (the
-// rotation transposed) with global atomics and drives the parameter
-// derivatives through dL/dp.  Tiles only add partial adjoints, so the sum over
-// tiles is the exact transpose (up to fp32 summation order).
+// strip C, its derivatives dC/dp (one weight evaluation) and its blur B are
+// recomputed in shared memory; the tile's part of B-bar (the tilt transposed)
+// is accumulated with shared-memory atomics, folded onto canvas columns, and
+// C-bar (the Gaussian transposed) gathered from it; C-bar drives the
+// parameter derivatives through the stored dC/dp and, when the image gradient
+// is asked for, scatters into u-bar (the rotation transposed) with global
+// atomics.  Tiles only add partial adjoints, so the sum over tiles is the
+// exact transpose (up to fp32 summation order).
 #include "common.cuh"
 #include "kernels.h"
 
@@ -197,14 +199,21 @@ __device__ __forceinline__ DGeom dgeom(const DiffView &V)
 // Recomputes the canvas strip C (actual columns clo..chi) and its blur B
 // (strip positions bx0.., value of column clamp(i)) of a tile in shared memory.
 __device__ void strips(const DiffView &V, const DTile &T, const DGeom &G, const float *g, float *Cs, float *Bs,
-                       int cw_max, int bw_max)
+                       int cw_max, int bw_max, float *Cx = nullptr, float *Cy = nullptr)
 {
     const int nrows = T.j1 - T.j0 + 1;
     for (int e = threadIdx.x; e < nrows * T.cw; e += blockDim.x) {
         const int r = e / T.cw, c = e - r * T.cw;
         float px, py;
         G.map(T.clo + c, T.j0 + r, px, py);
-        Cs[r * cw_max + c] = canvas_at(V.u, V.W, V.H, px, py, nullptr, nullptr, 0.f, nullptr);
+        if (Cx) {   // with dC/dpx, dC/dpy for the backward (one weight evaluation)
+            float dx, dy;
+            Cs[r * cw_max + c] = canvas_at(V.u, V.W, V.H, px, py, &dx, &dy, 0.f, nullptr);
+            Cx[r * cw_max + c] = dx;
+            Cy[r * cw_max + c] = dy;
+        } else {
+            Cs[r * cw_max + c] = canvas_at(V.u, V.W, V.H, px, py, nullptr, nullptr, 0.f, nullptr);
+        }
     }
     __syncthreads();
     const int last = V.Wr - 1;
@@ -269,7 +278,9 @@ __global__ void __launch_bounds__(kDThreads)
 dwarp_bwd_kernel(const DiffView *__restrict__ views, int n_views, int cw_max, int bw_max, int32_t *status)
 {
     extern __shared__ float sm[];
-    float *Cs = sm, *Bs = Cs + kDTH * cw_max, *Bb = Bs + kDTH * bw_max, *Cb = Bb + kDTH * bw_max;
+    float *Cs = sm, *Cx = Cs + kDTH * cw_max, *Cy = Cx + kDTH * cw_max, *Cb = Cy + kDTH * cw_max;
+    float *Bc = Cb + kDTH * cw_max;                  // B-bar folded onto canvas columns (clo .. chi)
+    float *Bs = Bc + kDTH * cw_max, *Bb = Bs + kDTH * bw_max;
     __shared__ float g[ASIFT_MAX_GAUSS], dg[ASIFT_MAX_GAUSS], red[kDThreads / 32];
     const DTile T = dtile(views, n_views, blockIdx.x);
     const DiffView &V = views[T.v];
@@ -279,14 +290,16 @@ dwarp_bwd_kernel(const DiffView *__restrict__ views, int n_views, int cw_max, in
     }
     const DGeom G = dgeom(V);
     const float sigma = sigma_of(V.param[0]);
-    gauss_taps(sigma, V.K, g, dg);
-    strips(V, T, G, g, Cs, Bs, cw_max, bw_max);
+    const int K = V.K, last = V.Wr - 1;
+    gauss_taps(sigma, K, g, dg);
+    strips(V, T, G, g, Cs, Bs, cw_max, bw_max, Cx, Cy);
     const int nrows = T.j1 - T.j0 + 1, ncols = T.xb - T.xa + 1;
     for (int e = threadIdx.x; e < kDTH * bw_max; e += blockDim.x) Bb[e] = 0.f;
-    for (int e = threadIdx.x; e < kDTH * cw_max; e += blockDim.x) Cb[e] = 0.f;
+    for (int e = threadIdx.x; e < kDTH * cw_max; e += blockDim.x) Bc[e] = 0.f;
     __syncthreads();
 
-    // tilt transposed: B-bar, and dL/dt through X
+    // tilt transposed: B-bar at the strip positions (six shared atomics per
+    // view pixel), and dL/dt through X
     const float cr = (V.Wr - 1) * 0.5f;
     float tb = 0.f;
     for (int e = threadIdx.x; e < nrows * ncols; e += blockDim.x) {
@@ -304,8 +317,7 @@ dwarp_bwd_kernel(const DiffView *__restrict__ views, int n_views, int cw_max, in
 #pragma unroll
         for (int m = 0; m < 6; ++m) {
             // strip position X0+m-2 holds column clamp(X0+m-2): the clamped
-            // taps of the forward accumulate at their strip positions, which
-            // the next step maps onto canvas columns
+            // taps of the forward accumulate at their strip positions
             atomicAdd(Bbrow + X0 + m - 2, w[m] * vb);
             dvdX = fmaf(dw[m], Brow[X0 + m - 2], dvdX);
         }
@@ -313,28 +325,46 @@ dwarp_bwd_kernel(const DiffView *__restrict__ views, int n_views, int cw_max, in
     }
     __syncthreads();
 
-    // Gaussian transposed: C-bar, and dL/dsigma
+    // strip positions folded onto their (clamped) canvas columns, and dL/dsigma
     float sb = 0.f;
     for (int e = threadIdx.x; e < nrows * T.bw; e += blockDim.x) {
         const int r = e / T.bw, c = e - r * T.bw;
         const float b = Bb[r * bw_max + c];
         if (b == 0.f) continue;
-        const int ic = clampi(T.bx0 + c, 0, V.Wr - 1);
+        const int ic = clampi(T.bx0 + c, 0, last);
+        atomicAdd(Bc + r * cw_max + ic - T.clo, b);
         const float *Crow = Cs + r * cw_max - T.clo;
-        float *Cbrow = Cb + r * cw_max - T.clo;
-        atomicAdd(Cbrow + ic, g[0] * b);
         float ds = dg[0] * Crow[ic];
-        for (int k = 1; k <= V.K; ++k) {
-            const int lo = max(ic - k, 0), hi = min(ic + k, V.Wr - 1);
-            atomicAdd(Cbrow + lo, g[k] * b);
-            atomicAdd(Cbrow + hi, g[k] * b);
-            ds = fmaf(dg[k], Crow[lo] + Crow[hi], ds);
-        }
+        for (int k = 1; k <= K; ++k) ds = fmaf(dg[k], Crow[max(ic - k, 0)] + Crow[min(ic + k, last)], ds);
         sb = fmaf(b, ds, sb);
     }
     __syncthreads();
 
-    // rotation transposed: u-bar, and dL/dp -> (phi, tx, ty)
+    // Gaussian transposed as a gather: B(ic) = g0 C(ic) + sum_k g_k (C(max(ic-k, 0))
+    // + C(min(ic+k, last))), so an inner column col takes g_|ic - col| from each
+    // ic within K; the canvas edges 0 and last also take the clamped taps
+    for (int e = threadIdx.x; e < nrows * T.cw; e += blockDim.x) {
+        const int r = e / T.cw, c = e - r * T.cw;
+        const int col = T.clo + c;
+        const float *Bcrow = Bc + r * cw_max - T.clo;
+        float acc = 0.f;
+        if (col > 0 && col < last) {
+            const int lo = max(col - K, T.clo), hi = min(col + K, T.chi);
+            for (int ic = lo; ic <= hi; ++ic) acc = fmaf(g[abs(ic - col)], Bcrow[ic], acc);
+        } else {
+            for (int ic = max(col - K, T.clo); ic <= min(col + K, T.chi); ++ic) {
+                float coef = ic == col ? g[0] : 0.f;
+                for (int k = 1; k <= K; ++k)
+                    coef += g[k] * (float)((max(ic - k, 0) == col) + (min(ic + k, last) == col));
+                acc = fmaf(coef, Bcrow[ic], acc);
+            }
+        }
+        Cb[r * cw_max + c] = acc;
+    }
+    __syncthreads();
+
+    // rotation transposed: dL/dp -> (phi, tx, ty) from the stored dC/dp, and
+    // (when asked for) u-bar by scattering through the rotation's weights
     float pb = 0.f, txb = 0.f, tyb = 0.f;
     const float dg2r = 0.017453292519943295f;
     for (int e = threadIdx.x; e < nrows * T.cw; e += blockDim.x) {
@@ -343,9 +373,12 @@ dwarp_bwd_kernel(const DiffView *__restrict__ views, int n_views, int cw_max, in
         const float cb = Cb[r * cw_max + c];
         if (cb == 0.f) continue;
         const int j = T.j0 + r;
-        float px, py, dcdx, dcdy;
-        G.map(i, j, px, py);
-        canvas_at(V.u, V.W, V.H, px, py, &dcdx, &dcdy, cb, V.ubar);
+        const float dcdx = Cx[r * cw_max + c], dcdy = Cy[r * cw_max + c];
+        if (V.ubar) {
+            float px, py;
+            G.map(i, j, px, py);
+            canvas_at(V.u, V.W, V.H, px, py, nullptr, nullptr, cb, V.ubar);
+        }
         const float dx = (float)i - G.crx, dy = (float)j - G.cry;
         txb = fmaf(cb, dcdx, txb);
         tyb = fmaf(cb, dcdy, tyb);
@@ -445,7 +478,7 @@ cudaError_t launch_dwarp(bool backward, const DiffView *d_views, int n_views, in
                          int32_t *status, cudaStream_t s)
 {
     if (n_tiles <= 0) return cudaSuccess;
-    const size_t smem = sizeof(float) * (size_t)kDTH * (backward ? 2 * (cw_max + bw_max) : (cw_max + bw_max));
+    const size_t smem = sizeof(float) * (size_t)kDTH * (backward ? 5 * cw_max + 2 * bw_max : cw_max + bw_max);
     if (backward) {
         const cudaError_t e = ensure_dynamic_smem((const void *)dwarp_bwd_kernel, smem);
         if (e != cudaSuccess) return e;
