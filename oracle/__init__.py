@@ -140,6 +140,9 @@ def lib():
         L.oracle_gauss_blur.argtypes = [f64p, C.c_int, C.c_int, C.c_double, f64p]
         L.oracle_sift.argtypes = [u8p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
         L.oracle_sift.restype = C.c_int
+        L.oracle_sift_ex.argtypes = [u8p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, f64p, f64p, C.c_int,
+                                     P(C.c_int), C.c_double]
+        L.oracle_sift_ex.restype = C.c_int
         L.oracle_sift_match.argtypes = [f32p, C.c_int, f32p, C.c_int, C.c_double, i32p, f64p, f64p, u8p]
         L.oracle_sift_match_f32.argtypes = [f32p, C.c_int, f32p, C.c_int, C.c_double, i32p, f32p, f32p, u8p]
         L.oracle_sizeof_sift_kp.restype = C.c_int
@@ -583,6 +586,29 @@ def sift(img: np.ndarray, max_kp: int = 5000) -> SiftOut:
     desc = np.zeros((max_kp, 128), np.float32)
     n = lib().oracle_sift(img, W, H, max_kp, kps.ctypes.data, desc.ctypes.data)
     return SiftOut(kps[:n].copy(), desc[:n].copy())
+
+
+@dataclass
+class SiftMarginOut:
+    kps: np.ndarray
+    desc: np.ndarray
+    margin: np.ndarray       # per keypoint: smallest relative margin of its decisions
+    miss: np.ndarray         # (m, 4): candidates rejected by <= M relative: x, y, sigma, angle (-1: any)
+
+
+def sift_margins(img: np.ndarray, max_kp: int = 20000, M: float = 2e-3, max_miss: int = 100000) -> SiftMarginOut:
+    """sift() plus, for parity tests, each keypoint's smallest decision margin
+    and the near-miss candidates (rejected by at most M relative)."""
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    H, W = img.shape
+    kps = np.zeros(max_kp, SIFT_KP_DTYPE)
+    desc = np.zeros((max_kp, 128), np.float32)
+    margin = np.zeros(max_kp, np.float64)
+    miss = np.zeros((max_miss, 4), np.float64)
+    nm = C.c_int(0)
+    n = lib().oracle_sift_ex(img, W, H, max_kp, kps.ctypes.data, desc.ctypes.data, margin, miss.reshape(-1), max_miss,
+                             C.byref(nm), float(M))
+    return SiftMarginOut(kps[:n].copy(), desc[:n].copy(), margin[:n].copy(), miss[:nm.value].copy())
 
 
 @dataclass

@@ -232,12 +232,36 @@ static int solve3(double A[3][3], double b[3], double x[3])
 
 /* Step 3: refinement, contrast and edge tests.  On success fills the
  * octave-relative position (xo, yo), layer and layer offset and |D^|. */
+/* Margin bookkeeping for the parity tests (does not change any decision):
+ * *half receives the smallest distance of an offset component, at any
+ * iteration, to the half-integer where its decision (stay, or move by
+ * lround) would change; *why the failed test (1 not converged or left the
+ * octave, 2 contrast, 3 edge). */
+static int refine_ex(const pyramid *P, int o, int *pk, int *px, int *py, double off[3], double *contrast,
+                     double *dxx_, double *dyy_, double *dxy_, double *half, int *why);
+
 static int refine(const pyramid *P, int o, int *pk, int *px, int *py, double off[3], double *contrast, double *dxx_,
                   double *dyy_, double *dxy_)
+{
+    double half;
+    int why;
+    return refine_ex(P, o, pk, px, py, off, contrast, dxx_, dyy_, dxy_, &half, &why);
+}
+
+static double half_dist(double v)
+{
+    const double a = fabs(v);
+    return fabs(a - (floor(a) + 0.5));
+}
+
+static int refine_ex(const pyramid *P, int o, int *pk, int *px, int *py, double off[3], double *contrast,
+                     double *dxx_, double *dyy_, double *dxy_, double *half, int *why)
 {
     int k = *pk, x = *px, y = *py;
     double g[3], Hm[3][3];
     int ok = 0;
+    *half = INFINITY;
+    *why = 1;
     for (int it = 0; it < SIFT_MAX_INTERP; ++it) {
         const simg *c = &P->D[o][k], *pr = &P->D[o][k - 1], *nx = &P->D[o][k + 1];
         const double v = px_at(c, x, y);
@@ -259,6 +283,7 @@ static int refine(const pyramid *P, int o, int *pk, int *px, int *py, double off
         double A[3][3], b[3] = {-g[0], -g[1], -g[2]};
         memcpy(A, Hm, sizeof(A));
         if (!solve3(A, b, off)) return 0;
+        for (int q = 0; q < 3; ++q) *half = fmin(*half, half_dist(off[q]));
         if (fabs(off[0]) < 0.5 && fabs(off[1]) < 0.5 && fabs(off[2]) < 0.5) {
             *contrast = v + 0.5 * (g[0] * off[0] + g[1] * off[1] + g[2] * off[2]);
             *dxx_ = dxx;
@@ -276,12 +301,15 @@ static int refine(const pyramid *P, int o, int *pk, int *px, int *py, double off
             return 0;
     }
     if (!ok) return 0;
-    if (fabs(*contrast) < SIFT_CONTRAST / SIFT_S) return 0;
-    const double tr = *dxx_ + *dyy_, det = *dxx_ * *dyy_ - *dxy_ * *dxy_;
-    if (det <= 0.0 || tr * tr * SIFT_EDGE_R >= (SIFT_EDGE_R + 1.0) * (SIFT_EDGE_R + 1.0) * det) return 0;
-    *pk = k;
+    *pk = k;          /* the refined position, also when a test below fails */
     *px = x;
     *py = y;
+    *why = 2;
+    if (fabs(*contrast) < SIFT_CONTRAST / SIFT_S) return 0;
+    *why = 3;
+    const double tr = *dxx_ + *dyy_, det = *dxx_ * *dyy_ - *dxy_ * *dxy_;
+    if (det <= 0.0 || tr * tr * SIFT_EDGE_R >= (SIFT_EDGE_R + 1.0) * (SIFT_EDGE_R + 1.0) * det) return 0;
+    *why = 0;
     return 1;
 }
 
@@ -295,7 +323,22 @@ static inline void grad(const simg *G, int x, int y, double *gx, double *gy)
 /* Step 4: the orientation histogram of a keypoint at octave-relative (xo,
  * yo) with octave-relative scale s on Gaussian image G.  Returns the number
  * of peaks written to ang[] (degrees). */
+static int orientations_ex(const simg *G, double xo, double yo, double s, double *ang, double *margin,
+                           double *near_ang, int *n_near, double M);
+
 static int orientations(const simg *G, double xo, double yo, double s, double *ang)
+{
+    double margin;
+    int n_near = 0;
+    return orientations_ex(G, xo, yo, s, ang, &margin, NULL, &n_near, 0.0);
+}
+
+/* As orientations; *margin = the smallest, over the 36 bins, of |min(h - l,
+ * h - r, h - 0.8 max)| / max (a bin is a peak iff that minimum is >= 0 with
+ * the first two > 0), and the bins rejected by less than M (relative) go to
+ * near_ang[] (when not NULL): for the parity tests, no decision changes. */
+static int orientations_ex(const simg *G, double xo, double yo, double s, double *ang, double *margin,
+                           double *near_ang, int *n_near, double M)
 {
     double h[SIFT_ORI_BINS] = {0}, hs[SIFT_ORI_BINS];
     const double sig = SIFT_ORI_SIG * s;
@@ -322,8 +365,14 @@ static int orientations(const simg *G, double xo, double yo, double s, double *a
     double mx = 0.0;
     for (int i = 0; i < SIFT_ORI_BINS; ++i) mx = fmax(mx, hs[i]);
     int n = 0;
+    *margin = INFINITY;
     for (int i = 0; i < SIFT_ORI_BINS; ++i) {
         const double l = hs[(i + SIFT_ORI_BINS - 1) % SIFT_ORI_BINS], r = hs[(i + 1) % SIFT_ORI_BINS];
+        if (mx > 0.0) {
+            const double d = fmin(fmin(hs[i] - l, hs[i] - r), hs[i] - SIFT_ORI_PEAK * mx) / mx;
+            *margin = fmin(*margin, fabs(d));
+            if (near_ang && d < 0.0 && -d <= M) near_ang[(*n_near)++] = i * 360.0 / SIFT_ORI_BINS;
+        }
         if (hs[i] > l && hs[i] > r && hs[i] >= SIFT_ORI_PEAK * mx && mx > 0.0) {
             const double b = i + 0.5 * (l - r) / (l - 2.0 * hs[i] + r);
             double a = b * 360.0 / SIFT_ORI_BINS;
@@ -403,6 +452,7 @@ typedef struct {
     oracle_sift_kp kp;
     double xo, yo, s;
     int o, k;
+    double margin;      /* smallest relative decision margin (parity tests) */
 } kp_full;
 
 static int kpf_cmp(const void *pa, const void *pb) { return kp_cmp(&((const kp_full *)pa)->kp, &((const kp_full *)pb)->kp); }
@@ -410,8 +460,37 @@ static int kpf_cmp(const void *pa, const void *pb) { return kp_cmp(&((const kp_f
 /* SIFT keypoints and descriptors of an 8-bit image (pitch W).  The
  * strongest max_kp keypoints (|D| descending, then y, x, angle) are written
  * to kps[] and desc[] (128 floats each); returns their number. */
+int oracle_sift_ex(const uint8_t *img, int W, int H, int max_kp, oracle_sift_kp *kps, float *desc, double *margin,
+                   double *miss, int max_miss, int *n_miss, double M);
+
 int oracle_sift(const uint8_t *img, int W, int H, int max_kp, oracle_sift_kp *kps, float *desc)
 {
+    return oracle_sift_ex(img, W, H, max_kp, kps, desc, NULL, NULL, 0, NULL, 0.0);
+}
+
+/* A near miss, in original image coordinates: (x, y, sigma, angle or -1). */
+static void add_miss(double *miss, int max_miss, int *n_miss, int o, double xo, double yo, double s, double ang)
+{
+    if (!miss || !n_miss || *n_miss >= max_miss) return;
+    const double scale = ldexp(1.0, o);
+    double *m = miss + 4 * (size_t)(*n_miss)++;
+    m[0] = (xo * scale + 0.5) / 2.0 - 0.5;
+    m[1] = (yo * scale + 0.5) / 2.0 - 0.5;
+    m[2] = s * scale / 2.0;
+    m[3] = ang;
+}
+
+/* oracle_sift with, for the parity tests (no decision changes): margin[i],
+ * the smallest relative margin by which keypoint i passed each of its tests
+ * (the pre-threshold, the 26 extremum comparisons, the refinement's rounding
+ * decisions, contrast, edge ratio and its orientation bins), and miss[] (4
+ * doubles each: x, y, sigma, angle or -1), the candidates rejected by one of
+ * those tests by no more than M relative (a near threshold, a near extremum,
+ * an offset near a half-integer, a near peak bin). */
+int oracle_sift_ex(const uint8_t *img, int W, int H, int max_kp, oracle_sift_kp *kps, float *desc, double *margin,
+                   double *miss, int max_miss, int *n_miss, double M)
+{
+    if (n_miss) *n_miss = 0;
     pyramid *P = (pyramid *)calloc(1, sizeof(pyramid));
     build_pyramid(img, W, H, P);
     int cap = 1024, n = 0;
@@ -422,15 +501,56 @@ int oracle_sift(const uint8_t *img, int W, int H, int max_kp, oracle_sift_kp *kp
             const simg *Dk = &P->D[o][k];
             for (int y = SIFT_BORDER; y < Dk->H - SIFT_BORDER; ++y)
                 for (int x = SIFT_BORDER; x < Dk->W - SIFT_BORDER; ++x) {
-                    if (!(fabs(px_at(Dk, x, y)) > pre)) continue;
-                    if (!is_extremum(P, o, k, x, y)) continue;
+                    const double v = px_at(Dk, x, y);
+                    const double s0 = SIFT_SIGMA0 * pow(2.0, (double)k / SIFT_S);
+                    if (!(fabs(v) > pre)) {
+                        if (fabs(v) > pre * (1.0 - M)) add_miss(miss, max_miss, n_miss, o, x, y, s0, -1.0);
+                        continue;
+                    }
+                    double ext = INFINITY;      /* extremum margin: the closest neighbour, relative to |v| */
+                    if (margin || miss) {
+                        double hi = -INFINITY, lo = INFINITY;
+                        for (int dk = -1; dk <= 1; ++dk)
+                            for (int dy = -1; dy <= 1; ++dy)
+                                for (int dx = -1; dx <= 1; ++dx) {
+                                    if (!dk && !dy && !dx) continue;
+                                    const double w = px_at(&P->D[o][k + dk], x + dx, y + dy);
+                                    hi = fmax(hi, w);
+                                    lo = fmin(lo, w);
+                                }
+                        ext = fmin(fabs(v - hi), fabs(v - lo)) / fabs(v);
+                    }
+                    if (!is_extremum(P, o, k, x, y)) {
+                        if (ext <= M) add_miss(miss, max_miss, n_miss, o, x, y, s0, -1.0);
+                        continue;
+                    }
                     int kk = k, xx = x, yy = y;
-                    double off[3], contrast, dxx, dyy, dxy;
-                    if (!refine(P, o, &kk, &xx, &yy, off, &contrast, &dxx, &dyy, &dxy)) continue;
+                    double off[3], contrast, dxx, dyy, dxy, half;
+                    int why;
+                    const int ok = refine_ex(P, o, &kk, &xx, &yy, off, &contrast, &dxx, &dyy, &dxy, &half, &why);
+                    double con_m = INFINITY, edge_m = INFINITY;
+                    if (why == 0 || why == 2 || why == 3) {
+                        con_m = fabs(fabs(contrast) - SIFT_CONTRAST / SIFT_S) / (SIFT_CONTRAST / SIFT_S);
+                        const double tr = dxx + dyy, det = dxx * dyy - dxy * dxy;
+                        const double lim = (SIFT_EDGE_R + 1.0) * (SIFT_EDGE_R + 1.0) * det;
+                        edge_m = det > 0.0 ? fabs(lim - tr * tr * SIFT_EDGE_R) / lim : 0.0;
+                    }
+                    if (!ok) {
+                        const double m = why == 1 ? half : (why == 2 ? con_m : edge_m);
+                        if (m <= M) {
+                            const double sk = SIFT_SIGMA0 * pow(2.0, (double)kk / SIFT_S);
+                            add_miss(miss, max_miss, n_miss, o, xx, yy, sk, -1.0);
+                        }
+                        continue;
+                    }
                     const double xo = xx + off[0], yo = yy + off[1];
                     const double s = SIFT_SIGMA0 * pow(2.0, (kk + off[2]) / SIFT_S);
-                    double angs[SIFT_ORI_BINS];
-                    const int na = orientations(&P->G[o][kk], xo, yo, s, angs);
+                    double angs[SIFT_ORI_BINS], near[SIFT_ORI_BINS], ori_m;
+                    int n_near = 0;
+                    const int na = orientations_ex(&P->G[o][kk], xo, yo, s, angs, &ori_m, miss ? near : NULL, &n_near, M);
+                    for (int a = 0; a < n_near; ++a) add_miss(miss, max_miss, n_miss, o, xo, yo, s, near[a]);
+                    const double kp_m = fmin(fmin(fmin((fabs(v) - pre) / pre, ext), fmin(2.0 * half, con_m)),
+                                             fmin(edge_m, ori_m));
                     for (int a = 0; a < na; ++a) {
                         if (n == cap) {
                             cap *= 2;
@@ -450,6 +570,7 @@ int oracle_sift(const uint8_t *img, int W, int H, int max_kp, oracle_sift_kp *kp
                         f->s = s;
                         f->o = o;
                         f->k = kk;
+                        f->margin = kp_m;
                     }
                 }
         }
@@ -457,6 +578,7 @@ int oracle_sift(const uint8_t *img, int W, int H, int max_kp, oracle_sift_kp *kp
     const int m = n < max_kp ? n : max_kp;
     for (int i = 0; i < m; ++i) {
         kps[i] = all[i].kp;
+        if (margin) margin[i] = all[i].margin;
         if (desc) descriptor(&P->G[all[i].o][all[i].k], all[i].xo, all[i].yo, all[i].s, all[i].kp.angle,
                              desc + (size_t)128 * i);
     }

@@ -1,12 +1,19 @@
 """GPU SIFT (asift_sift, fp32) against the fp64 SIFT oracle on the same
 images.
 
-Bar: the strong keypoints (the 200 of highest response on each side) agree
-one to one within 0.02 px, 0.5% in scale and 0.5 degrees, with descriptors
-within 0.02 (L2, unit-norm vectors), for at least 95% of them both ways; the
-total counts within 5%.  The GPU's fp32 scale space and the oracle's fp64 one
-can take a marginal decision (an extremum, a contrast or edge test, an 80%
-peak) differently, so weak keypoints are not compared one to one.
+Bars:
+  * one to one on every decided keypoint: every oracle keypoint whose
+    decisions (the pre-threshold, the 26 extremum comparisons, the
+    refinement's rounding, contrast, edge ratio, its orientation bins) all
+    clear their thresholds by more than 2e-3 relative has a GPU keypoint
+    within 0.02 px, 0.5% in scale and 0.5 degrees with a descriptor within
+    0.02 (L2, unit-norm vectors); every GPU keypoint is such a counterpart of
+    an oracle keypoint, or lies at a candidate the oracle rejected by at most
+    2e-3 (a decision the fp32 and fp64 scale spaces may take either way);
+  * the 200 strongest keypoints agree one to one both ways for >= 95%, the
+    total counts within 5%.
+The fp32 rounding of the GPU's scale space is about 1e-5 relative, two
+orders below the 2e-3 margin.
 """
 import math
 
@@ -56,6 +63,42 @@ def test_sift_matches_the_oracle(A, H, W, seed):
     assert _agree(ref.kps, ref.desc, gk, gd) >= 0.95
     assert _agree(gk, gd, ref.kps, ref.desc) >= 0.95
     assert np.abs(np.linalg.norm(gd, axis=1) - 1).max() < 1e-4
+
+
+def _match(k, kb, db, d, pos=0.02, scl=5e-3, ang=0.5):
+    """Index in kb of a counterpart of keypoint k (descriptor d), or -1."""
+    dist = np.hypot(kb["x"] - k["x"], kb["y"] - k["y"])
+    for j in np.flatnonzero(dist < pos):
+        m = kb[j]
+        if (abs(m["sigma"] / k["sigma"] - 1) < scl and abs((m["angle"] - k["angle"] + 180) % 360 - 180) < ang
+                and (d is None or np.linalg.norm(d.astype(np.float64) - db[j]) < 0.02)):
+            return int(j)
+    return -1
+
+
+@pytest.mark.parametrize("H,W,seed", [(160, 200, 81), (240, 320, 5), (97, 131, 7), (300, 400, 12)])
+def test_sift_one_to_one_on_decided_keypoints(A, H, W, seed):
+    ctx = A.Context()
+    img = synth.texture(H, W, seed)
+    gk, gd = ctx.sift(torch.from_numpy(img).cuda(), max_kp=20000)
+    ref = O.sift_margins(img, 20000, M=2e-3)
+    sure = ref.margin > 2e-3
+    assert sure.mean() > 0.8, sure.mean()
+    # every decided oracle keypoint has its GPU counterpart
+    missing = [i for i in np.flatnonzero(sure) if _match(ref.kps[i], gk, gd, ref.desc[i]) < 0]
+    assert not missing, (len(missing), int(sure.sum()))
+    # every GPU keypoint is an oracle keypoint, or sits at a near-miss candidate
+    extra = 0
+    for i in range(len(gk)):
+        if _match(gk[i], ref.kps, ref.desc, gd[i]) >= 0:
+            continue
+        m = ref.miss
+        near = (np.hypot(m[:, 0] - gk[i]["x"], m[:, 1] - gk[i]["y"]) < 1.5) & (np.abs(m[:, 2] / gk[i]["sigma"] - 1) < 0.3)
+        # or an oracle keypoint with a marginal decision (its GPU twin may differ in a test or a bin)
+        k_near = (np.hypot(ref.kps["x"] - gk[i]["x"], ref.kps["y"] - gk[i]["y"]) < 1.5) & ~sure
+        if not (near.any() or k_near.any()):
+            extra += 1
+    assert extra == 0, (extra, len(gk))
 
 
 def test_sift_blob_and_empty_image(A):

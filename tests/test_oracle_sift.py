@@ -190,3 +190,20 @@ def test_sift_match_f32_agrees_with_fp64_beyond_its_error_bound():
     decided = np.abs(b.d1 - 0.64 * b.d2) > 2 * bound * b.d2
     assert np.array_equal(a.accepted[decided], b.accepted[decided])
     assert a.accepted.sum() > 10
+
+
+def test_sift_margins_change_no_decision():
+    """The margin bookkeeping is read-only: the same keypoints and descriptors
+    as sift(); margins are positive; a near-miss list appears; a clean blob is
+    decided by a wide margin."""
+    img = synth.texture(200, 240, 88)
+    a = O.sift(img, 20000)
+    b = O.sift_margins(img, 20000, M=2e-3)
+    assert np.array_equal(a.kps, b.kps) and np.array_equal(a.desc, b.desc)
+    assert (b.margin > 0).all() and len(b.miss) > 0
+    assert ((b.miss[:, 2] > 0) & (b.miss[:, 0] > -1) & (b.miss[:, 0] < 240)).all()
+    yy, xx = np.mgrid[0:120, 0:140].astype(np.float64)
+    blob = np.clip(np.rint(30 + 200 * np.exp(-((xx - 70.2) ** 2 + (yy - 61.4) ** 2) / (2 * 4.0 ** 2))), 0,
+                   255).astype(np.uint8)
+    r = O.sift_margins(blob, 100)
+    assert len(r.kps) >= 1 and r.margin[0] > 1e-2
