@@ -194,8 +194,9 @@ def test_sift_match_f32_agrees_with_fp64_beyond_its_error_bound():
 
 def test_sift_margins_change_no_decision():
     """The margin bookkeeping is read-only: the same keypoints and descriptors
-    as sift(); margins are positive; a near-miss list appears; a clean blob is
-    decided by a wide margin."""
+    as sift(); margins are positive; a near-miss list appears; an isotropic
+    blob's orientation is reported as marginal (its histogram is flat, so
+    several bins sit near the 80% threshold)."""
     img = synth.texture(200, 240, 88)
     a = O.sift(img, 20000)
     b = O.sift_margins(img, 20000, M=2e-3)
@@ -206,4 +207,4 @@ def test_sift_margins_change_no_decision():
     blob = np.clip(np.rint(30 + 200 * np.exp(-((xx - 70.2) ** 2 + (yy - 61.4) ** 2) / (2 * 4.0 ** 2))), 0,
                    255).astype(np.uint8)
     r = O.sift_margins(blob, 100)
-    assert len(r.kps) >= 1 and r.margin[0] > 1e-2
+    assert len(r.kps) > 1 and (r.margin < 1e-2).all()
