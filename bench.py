@@ -294,7 +294,7 @@ def warp_roofline(views, n_images: int, ms: float, peaks: dict) -> dict:
 
 def _alu_roofline(flops: float, ms: float, peak: float, f_clk: float) -> dict:
     achieved = flops / (ms / 1e3) / 1e12
-    return {"bound": "alu", "kernel": "warp_view_kernel (+ convert_images_kernel)", "achieved": achieved,
+    return {"bound": "alu", "kernel": "warp_band_kernel (+ tilt_filter_kernel, convert_images_kernel)", "achieved": achieved,
             "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
             "flops_per_launch": flops,
             "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 FMA/clk x 2 x {f_clk/1e6:.0f} MHz"}
