@@ -1672,6 +1672,7 @@ size_t asift_warp_workspace_size(int n)
     Bump b(nullptr);
     b.take<int32_t>(64);
     b.take<DiffView>(std::max(n, 1));
+    b.take<DiffPrep>(std::max(n, 1));
     return b.off + 256;
 }
 
@@ -1687,6 +1688,7 @@ static asift_status warp_call(bool backward, asift_ctx *ctx, const float *d_u, i
     Bump b(d_ws);
     int32_t *status = b.take<int32_t>(64);
     DiffView *tab = b.take<DiffView>(n);
+    DiffPrep *prep = b.take<DiffPrep>(n);
     std::vector<DiffView> h(n);
     int tiles = 0, cw_max = 1, bw_max = 1;
     for (int i = 0; i < n; ++i) {
@@ -1719,7 +1721,7 @@ static asift_status warp_call(bool backward, asift_ctx *ctx, const float *d_u, i
     cudaError_t e = upload(ctx, tab, h.data(), sizeof(DiffView) * n, s);
     if (e == cudaSuccess && backward && d_ubar) e = cudaMemsetAsync(d_ubar, 0, sizeof(float) * (size_t)n * H * W, s);
     if (e == cudaSuccess && backward) e = cudaMemsetAsync(d_pbar, 0, sizeof(double) * 4 * (size_t)n, s);
-    if (e == cudaSuccess) e = launch_dwarp(backward, tab, n, tiles, cw_max, bw_max, status, s);
+    if (e == cudaSuccess) e = launch_dwarp(backward, tab, prep, n, tiles, cw_max, bw_max, status, s);
     return cuda_status(e);
 }
 

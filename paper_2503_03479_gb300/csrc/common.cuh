@@ -107,7 +107,7 @@ struct SlotKp {             // a selected keypoint before orientation / descript
 };
 
 constexpr int kDetTW = 64, kDetTH = 32;   // FAST tile
-constexpr int kPyrTW = 64, kPyrTH = 16;   // pyramid tile (4 px per thread across x)
+constexpr int kPyrTW = 128, kPyrTH = 32;  // pyramid tile (4 columns x 4 rows per thread)
 
 // ---------------------------------------------------------------- differentiable warp
 // One view of the differentiable path (image i -> view i).
@@ -119,6 +119,16 @@ struct DiffView {
     const double *param;     // t, phi (deg), tx, ty
     double *pbar;            // dL/d(t, phi, tx, ty) (backward)
     int32_t W, H, Wr, Hr, Wv, Hv, K, tile_start, ntx, pad;
+};
+
+// Per-view constants of the differentiable warp, made once per call on the
+// device from the (device-resident) parameters.
+struct DiffPrep {
+    double dsig_dt;                       // dsigma/dt = 0.8 t / sqrt(t^2 - 1) (0 at t <= 1)
+    float c, s;                           // cos, sin of phi
+    float sigma, pad;
+    float g[ASIFT_MAX_GAUSS];             // normalised Gaussian taps g_0..g_K
+    float dg[ASIFT_MAX_GAUSS];            // dg_k / dsigma
 };
 
 // ---------------------------------------------------------------- matching

@@ -14,8 +14,8 @@
 // is accumulated with shared-memory atomics, folded onto canvas columns, and
 // C-bar (the Gaussian transposed) gathered from it; C-bar drives the
 // parameter derivatives through the stored dC/dp and, when the image gradient
-// is asked for, scatters into u-bar (the rotation transposed) with global
-// atomics.  Tiles only add partial adjoints, so the sum over tiles is the
+// is asked for, scatters into u-bar (the rotation transposed) through
+// shared-memory patches flushed with global atomics.  Tiles only add partial adjoints, so the sum over tiles is the
 // exact transpose (up to fp32 summation order).
 #include "common.cuh"
 #include "kernels.h"
@@ -24,50 +24,84 @@ namespace asift {
 
 constexpr int kDTW = 32, kDTH = 8, kDThreads = 256;
 
-// sinc and its derivative; series below |x| < 1e-2 where the closed forms cancel.
-__device__ __forceinline__ void sinc_d(float x, float &sc, float &dsc)
+// sinc(x) and sinc(x/3) with their x-derivatives near x = 0 (|x| < 1e-2),
+// where the closed forms cancel: the series to (pi x)^4.
+__device__ __forceinline__ void sinc_series(float x, float &a, float &da, float &b, float &db)
 {
-    const float ax = fabsf(x);
-    if (ax < 1e-2f) {
-        const float y = 9.8696044010893586f * x * x;   // (pi x)^2
-        sc = 1.f - y * (1.f / 6.f) * (1.f - y * (1.f / 20.f));
-        dsc = -3.2898681336964529f * x * (1.f - y * (1.f / 10.f));   // -(pi^2 x / 3)(1 - (pi x)^2/10)
-        return;
-    }
-    float s, c;
-    sincospif(x, &s, &c);
-    sc = s / (3.14159265358979f * x);
-    dsc = (c - sc) / x;
+    const float y = 9.8696044010893586f * x * x;   // (pi x)^2
+    a = 1.f - y * (1.f / 6.f) * (1.f - y * (1.f / 20.f));
+    da = -3.2898681336964529f * x * (1.f - y * (1.f / 10.f));   // -(pi^2 x / 3)(1 - (pi x)^2/10)
+    const float y3 = y * (1.f / 9.f);                            // (pi x / 3)^2
+    b = 1.f - y3 * (1.f / 6.f) * (1.f - y3 * (1.f / 20.f));
+    db = -0.36554090374405032f * x * (1.f - y3 * (1.f / 10.f));  // -(pi^2 x / 27)(1 - (pi x/3)^2/10)
 }
 
-// Normalised Lanczos-3 weights w_m(f) (m = -2..3) and dw_m/df from L and L'
-// evaluated tap by tap (L' is needed for the backward; the forward uses the
-// same evaluation so both see one function).
-__device__ __forceinline__ void lanczos3_wd(float f, float w[6], float dw[6])
+// Lanczos-3 kernel L(x) = sinc(x) sinc(x/3) (Eq. (4), a = 3) at the six taps
+// x = f - m', m' = -2..3 (index m = m' + 2), and L'(x) when D is true.  One
+// sincospif pair serves all six: sin(pi x) = (-1)^m' sin(pi f), cos likewise,
+// and sin, cos of pi x/3 follow from those of pi f/3 by angle addition with
+// the constants cos, sin of pi m'/3.  With r = 1/x:
+//   sinc(x)   = sin(pi x) r / pi,      d/dx = (cos(pi x) - sinc(x)) r,
+//   sinc(x/3) = 3 sin(pi x/3) r / pi,  d/dx = (cos(pi x/3) - sinc(x/3)) r.
+// Outside |x| < 3 (only x = -3, at f = 0) the kernel and its derivative are 0.
+template <bool D>
+__device__ __forceinline__ void lanczos3_taps(float f, float L[6], float dL[6])
 {
-    float L[6], dL[6], S = 0.f, dS = 0.f;
+    constexpr float kR3 = 0.86602540378443864676f;
+    constexpr float kCos[6] = {-0.5f, 0.5f, 1.f, 0.5f, -0.5f, -1.f};
+    constexpr float kSin[6] = {-kR3, -kR3, 0.f, kR3, kR3, 0.f};
+    float S1, C1, S3, C3;
+    sincospif(f, &S1, &C1);
+    sincospif(f * (1.f / 3.f), &S3, &C3);
 #pragma unroll
     for (int m = 0; m < 6; ++m) {
         const float x = f - (float)(m - 2);
-        if (fabsf(x) < 3.f) {
-            float a, da, b, db;
-            sinc_d(x, a, da);
-            sinc_d(x * (1.f / 3.f), b, db);
-            L[m] = a * b;
-            dL[m] = da * b + a * db * (1.f / 3.f);
-        } else {
-            L[m] = 0.f;
-            dL[m] = 0.f;
+        const float sx = (m & 1) ? -S1 : S1, cx = (m & 1) ? -C1 : C1;
+        const float s3 = fmaf(S3, kCos[m], -C3 * kSin[m]);
+        const float c3 = fmaf(C3, kCos[m], S3 * kSin[m]);
+        const bool small = fabsf(x) < 1e-2f;
+        const float r = __frcp_rn(small ? 1.f : x);
+        float a = sx * r * 0.31830988618379067f, b = s3 * r * 0.95492965855137202f;
+        float da = 0.f, db = 0.f;
+        if (D) {
+            da = (cx - a) * r;
+            db = (c3 - b) * r;
         }
-        S += L[m];
-        dS += dL[m];
+        if (small) {
+            float sa, sda, sb, sdb;
+            sinc_series(x, sa, sda, sb, sdb);
+            a = sa; b = sb; da = sda; db = sdb;
+        }
+        const bool in = fabsf(x) < 3.f;
+        L[m] = in ? a * b : 0.f;
+        if (D) dL[m] = in ? fmaf(da, b, a * db) : 0.f;
     }
+}
+
+// Normalised Lanczos-3 weights w_m(f) (m = -2..3) and dw_m/df, the quotient
+// rule on w_m = L_m / sum_n L_n (the forward and the backward share them).
+__device__ __forceinline__ void lanczos3_wd(float f, float w[6], float dw[6])
+{
+    float L[6], dL[6];
+    lanczos3_taps<true>(f, L, dL);
+    const float S = ((L[0] + L[1]) + (L[2] + L[3])) + (L[4] + L[5]);
+    const float dS = ((dL[0] + dL[1]) + (dL[2] + dL[3])) + (dL[4] + dL[5]);
     const float inv = 1.f / S;
 #pragma unroll
     for (int m = 0; m < 6; ++m) {
         w[m] = L[m] * inv;
         dw[m] = (dL[m] - w[m] * dS) * inv;
     }
+}
+
+// The weights alone.
+__device__ __forceinline__ void lanczos3_w(float f, float w[6])
+{
+    float L[6], dL[6];
+    lanczos3_taps<false>(f, L, dL);
+    const float inv = 1.f / (((L[0] + L[1]) + (L[2] + L[3])) + (L[4] + L[5]));
+#pragma unroll
+    for (int m = 0; m < 6; ++m) w[m] = L[m] * inv;
 }
 
 struct DGeom {
@@ -80,71 +114,182 @@ struct DGeom {
     }
 };
 
-// Canvas value at p, optionally with dC/dpx, dC/dpy, and optionally
-// scattering cb * w_x w_y into ubar.
+// Canvas value at p (taps clamped to the image), optionally with dC/dpx and
+// dC/dpy.
 __device__ __forceinline__ float canvas_at(const float *__restrict__ u, int W, int H, float px, float py,
-                                           float *dcdx, float *dcdy, float cb, float *__restrict__ ubar)
+                                           float *dcdx, float *dcdy)
 {
     const float fx0 = floorf(px), fy0 = floorf(py);
     const int x0 = (int)fx0, y0 = (int)fy0;
     float wx[6], dwx[6], wy[6], dwy[6];
-    lanczos3_wd(px - fx0, wx, dwx);
-    lanczos3_wd(py - fy0, wy, dwy);
+    if (dcdx) {
+        lanczos3_wd(px - fx0, wx, dwx);
+        lanczos3_wd(py - fy0, wy, dwy);
+    } else {
+        lanczos3_w(px - fx0, wx);
+        lanczos3_w(py - fy0, wy);
+    }
     int xs[6];
 #pragma unroll
     for (int m = 0; m < 6; ++m) xs[m] = clampi(x0 + m - 2, 0, W - 1);
     float acc = 0.f, ax = 0.f, ay = 0.f;
 #pragma unroll
     for (int n = 0; n < 6; ++n) {
-        const int yy = clampi(y0 + n - 2, 0, H - 1);
-        const float *row = u + (size_t)yy * W;
+        const float *row = u + (size_t)clampi(y0 + n - 2, 0, H - 1) * W;
         float r = 0.f, dr = 0.f;
 #pragma unroll
         for (int m = 0; m < 6; ++m) {
             const float val = __ldg(row + xs[m]);
             r = fmaf(wx[m], val, r);
-            dr = fmaf(dwx[m], val, dr);
-            if (ubar) atomicAdd(ubar + (size_t)yy * W + xs[m], cb * wx[m] * wy[n]);
+            if (dcdx) dr = fmaf(dwx[m], val, dr);
         }
         acc = fmaf(wy[n], r, acc);
-        ax = fmaf(wy[n], dr, ax);
-        ay = fmaf(dwy[n], r, ay);
+        if (dcdx) {
+            ax = fmaf(wy[n], dr, ax);
+            ay = fmaf(dwy[n], r, ay);
+        }
     }
-    if (dcdx) *dcdx = ax;
-    if (dcdy) *dcdy = ay;
+    if (dcdx) {
+        *dcdx = ax;
+        *dcdy = ay;
+    }
     return acc;
 }
 
-__device__ __forceinline__ float sigma_of(double t) { return t > 1.0 ? (float)(0.8 * sqrt(t * t - 1.0)) : 0.f; }
-
-// Gaussian taps g_0..g_K (and dg/dsigma) into shared memory.
-__device__ void gauss_taps(float sigma, int K, float *g, float *dg)
+// u-bar += cb w_x w_y over the 6 x 6 taps of p (the rotation's sample
+// transposed; clamped taps add at the edge pixels they read).  Where the six
+// columns lie inside the image and the rows' 16-byte groups inside the row
+// (W a multiple of 4), each tap row is two or three float4 reductions over
+// the aligned groups that hold it (zeros on either side), else six scalar ones.
+__device__ __forceinline__ void scatter_ubar(float *__restrict__ ubar, int W, int H, float px, float py, float cb)
 {
-    __shared__ float E, M2;
-    if (threadIdx.x == 0) {
-        float e = 0.f, m2 = 0.f;
-        if (sigma > 0.f) {
-            for (int k = 0; k <= K; ++k) {
-                const float v = expf(-(float)(k * k) / (2.f * sigma * sigma));
-                e += (k == 0) ? v : 2.f * v;
-            }
-            for (int k = 1; k <= K; ++k) m2 += 2.f * expf(-(float)(k * k) / (2.f * sigma * sigma)) * (float)(k * k);
-            m2 /= e;
+    const float fx0 = floorf(px), fy0 = floorf(py);
+    const int x0 = (int)fx0, y0 = (int)fy0;
+    float wx[6], wy[6];
+    lanczos3_w(px - fx0, wx);
+    lanczos3_w(py - fy0, wy);
+    const int xa = x0 - 2, a = xa & ~3, o = xa - a;   // first tap, its group, offset in the group
+    const int ng = o == 3 ? 3 : 2;
+    if ((W & 3) == 0 && xa >= 0 && a + 4 * ng <= W) {
+        // the weights shifted to their lanes in the groups: lane j holds tap j - o
+        float sw[12];
+#pragma unroll
+        for (int j = 0; j < 12; ++j) {
+            float v = 0.f;
+#pragma unroll
+            for (int m = 0; m < 6; ++m) v = (j - m == o) ? wx[m] : v;
+            sw[j] = v;
         }
-        E = e;
-        M2 = m2;
+#pragma unroll
+        for (int n = 0; n < 6; ++n) {
+            const float cn = cb * wy[n];
+            float4 *row = reinterpret_cast<float4 *>(ubar + (size_t)clampi(y0 + n - 2, 0, H - 1) * W + a);
+            atomicAdd(row, make_float4(cn * sw[0], cn * sw[1], cn * sw[2], cn * sw[3]));
+            atomicAdd(row + 1, make_float4(cn * sw[4], cn * sw[5], cn * sw[6], cn * sw[7]));
+            if (ng == 3) atomicAdd(row + 2, make_float4(cn * sw[8], 0.f, 0.f, 0.f));
+        }
+        return;
+    }
+    int xs[6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) xs[m] = clampi(x0 + m - 2, 0, W - 1);
+#pragma unroll
+    for (int n = 0; n < 6; ++n) {
+        float *row = ubar + (size_t)clampi(y0 + n - 2, 0, H - 1) * W;
+        const float cn = cb * wy[n];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) atomicAdd(row + xs[m], cn * wx[m]);
+    }
+}
+
+// A u-bar patch: a block of 32 canvas columns x 8 rows spans at most
+// sqrt(31^2 + 7^2) + 1 < 33 source pixels along either axis, + 5 for the taps
+// and 2 of margin.  The odd row pitch spreads a warp's taps along a steep
+// line of source rows over the banks.
+constexpr int kPatch = 40, kPatchPitch = 41;
+
+// u-bar += cb w_x w_y over the taps of p, into the patch whose pixel (0, 0)
+// is source (bx0, by0) (shared-memory atomics); a tap outside the patch,
+// which its box construction rules out, goes to u-bar directly.
+__device__ __forceinline__ void scatter_patch(float *P, int bx0, int by0, int PW, int PH, float *__restrict__ ubar,
+                                              int W, int H, float px, float py, float cb)
+{
+    const float fx0 = floorf(px), fy0 = floorf(py);
+    const int x0 = (int)fx0, y0 = (int)fy0;
+    const int xl = clampi(x0 - 2, 0, W - 1) - bx0, xh = clampi(x0 + 3, 0, W - 1) - bx0;
+    const int yl = clampi(y0 - 2, 0, H - 1) - by0, yh = clampi(y0 + 3, 0, H - 1) - by0;
+    if (xl < 0 || xh >= PW || yl < 0 || yh >= PH) {
+        scatter_ubar(ubar, W, H, px, py, cb);
+        return;
+    }
+    float wx[6], wy[6];
+    lanczos3_w(px - fx0, wx);
+    lanczos3_w(py - fy0, wy);
+    int xs[6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) xs[m] = clampi(x0 + m - 2, 0, W - 1) - bx0;
+#pragma unroll
+    for (int n = 0; n < 6; ++n) {
+        float *row = P + (clampi(y0 + n - 2, 0, H - 1) - by0) * kPatchPitch;
+        const float cn = cb * wy[n];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) atomicAdd(row + xs[m], cn * wx[m]);
+    }
+}
+
+// One block of 64 threads per view: cos, sin of phi and sigma(t) in fp64,
+// the Gaussian taps g_k = exp(-k^2 / (2 sigma^2)) / E over k = -K..K and
+// dg_k/dsigma = g_k (k^2 - M2) / sigma^3, M2 = sum_k k^2 g_k (the derivative
+// of the normalised taps), so that no tile evaluates them.
+__global__ void __launch_bounds__(64)
+dwarp_prep_kernel(const DiffView *__restrict__ views, DiffPrep *__restrict__ prep)
+{
+    __shared__ float red_e[2], red_m[2];
+    const DiffView &V = views[blockIdx.x];
+    DiffPrep &P = prep[blockIdx.x];
+    const double t = V.param[0];
+    const float sigma = t > 1.0 ? (float)(0.8 * sqrt(t * t - 1.0)) : 0.f;
+    const int K = V.K, k = (int)threadIdx.x;
+    float v = 0.f;
+    if (sigma > 0.f && k <= K) v = expf(-(float)(k * k) / (2.f * sigma * sigma));
+    float e = (k == 0) ? v : 2.f * v, m2 = 2.f * v * (float)(k * k);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        e += __shfl_xor_sync(0xffffffffu, e, o);
+        m2 += __shfl_xor_sync(0xffffffffu, m2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red_e[threadIdx.x >> 5] = e;
+        red_m[threadIdx.x >> 5] = m2;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k <= K; k += blockDim.x) {
+    const float E = red_e[0] + red_e[1], M2 = (red_m[0] + red_m[1]) / E;
+    if (k < ASIFT_MAX_GAUSS) {
         if (sigma > 0.f) {
-            g[k] = expf(-(float)(k * k) / (2.f * sigma * sigma)) / E;
-            dg[k] = g[k] * ((float)(k * k) - M2) / (sigma * sigma * sigma);
+            P.g[k] = k <= K ? v / E : 0.f;
+            P.dg[k] = k <= K ? (v / E) * ((float)(k * k) - M2) / (sigma * sigma * sigma) : 0.f;
         } else {
-            g[k] = (k == 0) ? 1.f : 0.f;
-            dg[k] = 0.f;
+            P.g[k] = (k == 0) ? 1.f : 0.f;
+            P.dg[k] = 0.f;
         }
     }
-    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double r = V.param[1] * (3.14159265358979323846 / 180.0);
+        P.c = (float)cos(r);
+        P.s = (float)sin(r);
+        P.sigma = sigma;
+        P.pad = 0.f;
+        P.dsig_dt = t > 1.0 ? 0.8 * t / sqrt(t * t - 1.0) : 0.0;
+    }
+}
+
+// The view's Gaussian taps into shared memory.
+__device__ __forceinline__ void load_taps(const DiffPrep &P, int K, float *g, float *dg)
+{
+    for (int k = threadIdx.x; k <= K; k += blockDim.x) {
+        g[k] = P.g[k];
+        dg[k] = P.dg[k];
+    }
 }
 
 // A view tile's strips.  B is needed at strip positions bx0..bx1 (the tilt
@@ -181,12 +326,11 @@ __device__ __forceinline__ DTile dtile(const DiffView *views, int n_views, int t
     return T;
 }
 
-__device__ __forceinline__ DGeom dgeom(const DiffView &V)
+__device__ __forceinline__ DGeom dgeom(const DiffView &V, const DiffPrep &P)
 {
-    const double r = V.param[1] * (3.14159265358979323846 / 180.0);
     DGeom G;
-    G.c = (float)cos(r);
-    G.s = (float)sin(r);
+    G.c = P.c;
+    G.s = P.s;
     G.cx = (V.W - 1) * 0.5f;
     G.cy = (V.H - 1) * 0.5f;
     G.tx = (float)V.param[2];
@@ -208,11 +352,11 @@ __device__ void strips(const DiffView &V, const DTile &T, const DGeom &G, const 
         G.map(T.clo + c, T.j0 + r, px, py);
         if (Cx) {   // with dC/dpx, dC/dpy for the backward (one weight evaluation)
             float dx, dy;
-            Cs[r * cw_max + c] = canvas_at(V.u, V.W, V.H, px, py, &dx, &dy, 0.f, nullptr);
+            Cs[r * cw_max + c] = canvas_at(V.u, V.W, V.H, px, py, &dx, &dy);
             Cx[r * cw_max + c] = dx;
             Cy[r * cw_max + c] = dy;
         } else {
-            Cs[r * cw_max + c] = canvas_at(V.u, V.W, V.H, px, py, nullptr, nullptr, 0.f, nullptr);
+            Cs[r * cw_max + c] = canvas_at(V.u, V.W, V.H, px, py, nullptr, nullptr);
         }
     }
     __syncthreads();
@@ -229,7 +373,8 @@ __device__ void strips(const DiffView &V, const DTile &T, const DGeom &G, const 
 }
 
 __global__ void __launch_bounds__(kDThreads)
-dwarp_fwd_kernel(const DiffView *__restrict__ views, int n_views, int cw_max, int bw_max, int32_t *status)
+dwarp_fwd_kernel(const DiffView *__restrict__ views, const DiffPrep *__restrict__ prep, int n_views, int cw_max,
+                 int bw_max, int32_t *status)
 {
     extern __shared__ float sm[];
     float *Cs = sm, *Bs = sm + kDTH * cw_max;
@@ -240,8 +385,9 @@ dwarp_fwd_kernel(const DiffView *__restrict__ views, int n_views, int cw_max, in
         if (threadIdx.x == 0) set_status(status, ASIFT_ERR_CAPACITY);
         return;
     }
-    const DGeom G = dgeom(V);
-    gauss_taps(sigma_of(V.param[0]), V.K, g, dg);
+    const DiffPrep &Pp = prep[T.v];
+    const DGeom G = dgeom(V, Pp);
+    load_taps(Pp, V.K, g, dg);   // visible after the strip's first barrier
     strips(V, T, G, g, Cs, Bs, cw_max, bw_max);
     const int nrows = T.j1 - T.j0 + 1, ncols = T.xb - T.xa + 1;
     const float cr = (V.Wr - 1) * 0.5f;
@@ -251,8 +397,8 @@ dwarp_fwd_kernel(const DiffView *__restrict__ views, int n_views, int cw_max, in
         const float X = T.t * ((float)x - T.crv) + cr;
         const float fX = floorf(X);
         const int X0 = (int)fX;
-        float w[6], dw[6];
-        lanczos3_wd(X - fX, w, dw);
+        float w[6];
+        lanczos3_w(X - fX, w);
         const float *Brow = Bs + r * bw_max - T.bx0;
         float v = 0.f;
 #pragma unroll
@@ -275,7 +421,8 @@ __device__ __forceinline__ float block_sum(float v, float *red)
 }
 
 __global__ void __launch_bounds__(kDThreads)
-dwarp_bwd_kernel(const DiffView *__restrict__ views, int n_views, int cw_max, int bw_max, int32_t *status)
+dwarp_bwd_kernel(const DiffView *__restrict__ views, const DiffPrep *__restrict__ prep, int n_views, int cw_max,
+                 int bw_max, int32_t *status)
 {
     extern __shared__ float sm[];
     float *Cs = sm, *Cx = Cs + kDTH * cw_max, *Cy = Cx + kDTH * cw_max, *Cb = Cy + kDTH * cw_max;
@@ -288,10 +435,10 @@ dwarp_bwd_kernel(const DiffView *__restrict__ views, int n_views, int cw_max, in
         if (threadIdx.x == 0) set_status(status, ASIFT_ERR_CAPACITY);
         return;
     }
-    const DGeom G = dgeom(V);
-    const float sigma = sigma_of(V.param[0]);
+    const DiffPrep &Pp = prep[T.v];
+    const DGeom G = dgeom(V, Pp);
     const int K = V.K, last = V.Wr - 1;
-    gauss_taps(sigma, K, g, dg);
+    load_taps(Pp, K, g, dg);   // visible after the strip's first barrier
     strips(V, T, G, g, Cs, Bs, cw_max, bw_max, Cx, Cy);
     const int nrows = T.j1 - T.j0 + 1, ncols = T.xb - T.xa + 1;
     for (int e = threadIdx.x; e < kDTH * bw_max; e += blockDim.x) Bb[e] = 0.f;
@@ -325,46 +472,51 @@ dwarp_bwd_kernel(const DiffView *__restrict__ views, int n_views, int cw_max, in
     }
     __syncthreads();
 
-    // strip positions folded onto their (clamped) canvas columns, and dL/dsigma
-    float sb = 0.f;
+    // strip positions folded onto their (clamped) canvas columns
     for (int e = threadIdx.x; e < nrows * T.bw; e += blockDim.x) {
         const int r = e / T.bw, c = e - r * T.bw;
         const float b = Bb[r * bw_max + c];
-        if (b == 0.f) continue;
-        const int ic = clampi(T.bx0 + c, 0, last);
-        atomicAdd(Bc + r * cw_max + ic - T.clo, b);
-        const float *Crow = Cs + r * cw_max - T.clo;
-        float ds = dg[0] * Crow[ic];
-        for (int k = 1; k <= K; ++k) ds = fmaf(dg[k], Crow[max(ic - k, 0)] + Crow[min(ic + k, last)], ds);
-        sb = fmaf(b, ds, sb);
+        if (b != 0.f) atomicAdd(Bc + r * cw_max + clampi(T.bx0 + c, 0, last) - T.clo, b);
     }
     __syncthreads();
 
     // Gaussian transposed as a gather: B(ic) = g0 C(ic) + sum_k g_k (C(max(ic-k, 0))
     // + C(min(ic+k, last))), so an inner column col takes g_|ic - col| from each
-    // ic within K; the canvas edges 0 and last also take the clamped taps
+    // ic within K; the canvas edges 0 and last also take the clamped taps.  The
+    // same coefficients with dg/dsigma give dL/dsigma = sum_ic Bbar(ic) dB(ic)/dsigma
+    // = sum_col C(col) sum_ic Bbar(ic) dcoef(ic, col).
+    float sb = 0.f;
     for (int e = threadIdx.x; e < nrows * T.cw; e += blockDim.x) {
         const int r = e / T.cw, c = e - r * T.cw;
         const int col = T.clo + c;
         const float *Bcrow = Bc + r * cw_max - T.clo;
-        float acc = 0.f;
+        float acc = 0.f, dacc = 0.f;
         if (col > 0 && col < last) {
             const int lo = max(col - K, T.clo), hi = min(col + K, T.chi);
-            for (int ic = lo; ic <= hi; ++ic) acc = fmaf(g[abs(ic - col)], Bcrow[ic], acc);
+            for (int ic = lo; ic <= hi; ++ic) {
+                const float b = Bcrow[ic];
+                const int k = abs(ic - col);
+                acc = fmaf(g[k], b, acc);
+                dacc = fmaf(dg[k], b, dacc);
+            }
         } else {
             for (int ic = max(col - K, T.clo); ic <= min(col + K, T.chi); ++ic) {
-                float coef = ic == col ? g[0] : 0.f;
-                for (int k = 1; k <= K; ++k)
-                    coef += g[k] * (float)((max(ic - k, 0) == col) + (min(ic + k, last) == col));
+                float coef = ic == col ? g[0] : 0.f, dcoef = ic == col ? dg[0] : 0.f;
+                for (int k = 1; k <= K; ++k) {
+                    const float n = (float)((max(ic - k, 0) == col) + (min(ic + k, last) == col));
+                    coef = fmaf(g[k], n, coef);
+                    dcoef = fmaf(dg[k], n, dcoef);
+                }
                 acc = fmaf(coef, Bcrow[ic], acc);
+                dacc = fmaf(dcoef, Bcrow[ic], dacc);
             }
         }
         Cb[r * cw_max + c] = acc;
+        sb = fmaf(Cs[r * cw_max + c], dacc, sb);
     }
     __syncthreads();
 
-    // rotation transposed: dL/dp -> (phi, tx, ty) from the stored dC/dp, and
-    // (when asked for) u-bar by scattering through the rotation's weights
+    // rotation transposed: dL/dp -> (phi, tx, ty) from the stored dC/dp
     float pb = 0.f, txb = 0.f, tyb = 0.f;
     const float dg2r = 0.017453292519943295f;
     for (int e = threadIdx.x; e < nrows * T.cw; e += blockDim.x) {
@@ -374,15 +526,66 @@ dwarp_bwd_kernel(const DiffView *__restrict__ views, int n_views, int cw_max, in
         if (cb == 0.f) continue;
         const int j = T.j0 + r;
         const float dcdx = Cx[r * cw_max + c], dcdy = Cy[r * cw_max + c];
-        if (V.ubar) {
-            float px, py;
-            G.map(i, j, px, py);
-            canvas_at(V.u, V.W, V.H, px, py, nullptr, nullptr, cb, V.ubar);
-        }
         const float dx = (float)i - G.crx, dy = (float)j - G.cry;
         txb = fmaf(cb, dcdx, txb);
         tyb = fmaf(cb, dcdy, tyb);
         pb = fmaf(cb, dcdx * (-G.s * dx + G.c * dy) + dcdy * (-G.c * dx - G.s * dy), pb);
+    }
+
+    // and, when asked for, u-bar through the rotation's weights: blocks of
+    // 32 canvas columns x the tile's rows (one point per thread) add into a
+    // shared-memory patch over their taps' source box, which then goes to
+    // u-bar with one global atomic per touched pixel (two patches alternate,
+    // so one barrier separates a block's adds from its flush)
+    if (V.ubar) {
+        __shared__ float patch[2][kPatch * kPatchPitch];
+        const int Wu = V.W, Hu = V.H;
+        const int r = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31u);
+        int buf = 0;
+        for (int q0 = 0; q0 < T.cw; q0 += 32, buf ^= 1) {
+            const int qn = min(32, T.cw - q0);
+            int bx0 = INT_MAX, bx1 = INT_MIN, by0 = INT_MAX, by1 = INT_MIN;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float px, py;
+                G.map(T.clo + q0 + ((k & 1) ? qn - 1 : 0), T.j0 + ((k & 2) ? nrows - 1 : 0), px, py);
+                const int fx = (int)floorf(px), fy = (int)floorf(py);
+                bx0 = min(bx0, fx);
+                bx1 = max(bx1, fx);
+                by0 = min(by0, fy);
+                by1 = max(by1, fy);
+            }
+            // taps floor - 2 .. floor + 3, one pixel more either side for the
+            // rounding of the interior points' positions, clamped like the taps
+            bx0 = clampi(bx0 - 3, 0, Wu - 1);
+            bx1 = clampi(bx1 + 4, 0, Wu - 1);
+            by0 = clampi(by0 - 3, 0, Hu - 1);
+            by1 = clampi(by1 + 4, 0, Hu - 1);
+            const int PW = bx1 - bx0 + 1, PH = by1 - by0 + 1;
+            const bool fits = PW <= kPatch && PH <= kPatch;
+            float *P = patch[buf];
+            if (fits)
+                for (int ly = r; ly < PH; ly += kDThreads / 32)
+                    for (int lx = lane; lx < PW; lx += 32) P[ly * kPatchPitch + lx] = 0.f;
+            __syncthreads();
+            const int c = q0 + lane;
+            if (lane < qn && r < nrows) {
+                const float cb = Cb[r * cw_max + c];
+                if (cb != 0.f) {
+                    float px, py;
+                    G.map(T.clo + c, T.j0 + r, px, py);
+                    if (fits) scatter_patch(P, bx0, by0, PW, PH, V.ubar, Wu, Hu, px, py, cb);
+                    else scatter_ubar(V.ubar, Wu, Hu, px, py, cb);
+                }
+            }
+            __syncthreads();
+            if (fits)
+                for (int ly = r; ly < PH; ly += kDThreads / 32)
+                    for (int lx = lane; lx < PW; lx += 32) {
+                        const float v = P[ly * kPatchPitch + lx];
+                        if (v != 0.f) atomicAdd(V.ubar + (size_t)(by0 + ly) * Wu + bx0 + lx, v);
+                    }
+        }
     }
     const float s_tb = block_sum(tb, red);
     const float s_sb = block_sum(sb, red);
@@ -390,9 +593,7 @@ dwarp_bwd_kernel(const DiffView *__restrict__ views, int n_views, int cw_max, in
     const float s_tx = block_sum(txb, red);
     const float s_ty = block_sum(tyb, red);
     if (threadIdx.x == 0) {
-        const double t = V.param[0];
-        double dt = s_tb;
-        if (t > 1.0) dt += (double)s_sb * 0.8 * t / sqrt(t * t - 1.0);
+        const double dt = (double)s_tb + (double)s_sb * Pp.dsig_dt;
         atomicAdd(V.pbar + 0, dt);
         atomicAdd(V.pbar + 1, (double)s_pb * dg2r);
         atomicAdd(V.pbar + 2, (double)s_tx);
@@ -474,19 +675,21 @@ int dwarp_tiles(int Wv, int Hv, int *ntx)
     return *ntx * ((Hv + kDTH - 1) / kDTH);
 }
 
-cudaError_t launch_dwarp(bool backward, const DiffView *d_views, int n_views, int n_tiles, int cw_max, int bw_max,
-                         int32_t *status, cudaStream_t s)
+cudaError_t launch_dwarp(bool backward, const DiffView *d_views, DiffPrep *d_prep, int n_views, int n_tiles,
+                         int cw_max, int bw_max, int32_t *status, cudaStream_t s)
 {
     if (n_tiles <= 0) return cudaSuccess;
+    dwarp_prep_kernel<<<n_views, 64, 0, s>>>(d_views, d_prep);
+    note_launch();
     const size_t smem = sizeof(float) * (size_t)kDTH * (backward ? 5 * cw_max + 2 * bw_max : cw_max + bw_max);
     if (backward) {
         const cudaError_t e = ensure_dynamic_smem((const void *)dwarp_bwd_kernel, smem);
         if (e != cudaSuccess) return e;
-        dwarp_bwd_kernel<<<n_tiles, kDThreads, smem, s>>>(d_views, n_views, cw_max, bw_max, status);
+        dwarp_bwd_kernel<<<n_tiles, kDThreads, smem, s>>>(d_views, d_prep, n_views, cw_max, bw_max, status);
     } else {
         const cudaError_t e = ensure_dynamic_smem((const void *)dwarp_fwd_kernel, smem);
         if (e != cudaSuccess) return e;
-        dwarp_fwd_kernel<<<n_tiles, kDThreads, smem, s>>>(d_views, n_views, cw_max, bw_max, status);
+        dwarp_fwd_kernel<<<n_tiles, kDThreads, smem, s>>>(d_views, d_prep, n_views, cw_max, bw_max, status);
     }
     note_launch();
     return cudaGetLastError();

@@ -121,8 +121,9 @@ cudaError_t launch_match_tc(const uint8_t *qbase, const uint8_t *qexp, long long
 struct DiffView;
 void dwarp_strip_widths(int Wv, double t_max, int K, int *cw, int *bw);
 int dwarp_tiles(int Wv, int Hv, int *ntx);
-cudaError_t launch_dwarp(bool backward, const DiffView *d_views, int n_views, int n_tiles, int cw_max, int bw_max,
-                         int32_t *status, cudaStream_t s);
+struct DiffPrep;
+cudaError_t launch_dwarp(bool backward, const DiffView *d_views, DiffPrep *d_prep, int n_views, int n_tiles,
+                         int cw_max, int bw_max, int32_t *status, cudaStream_t s);
 struct WarpSeg {            // one view of a flat view buffer
     long long off, count;
 };

@@ -23,88 +23,105 @@
 namespace asift {
 
 // ---------------------------------------------------------------- pyramid
-// Each CTA makes a kPyrTW x kPyrTH tile of level l.  The source columns and
-// weights of the tile's columns and rows are computed once (32-bit integer
-// divisions) and shared; the parent region the tile reads (at most
-// kPyrSW x kPyrSH: 63 steps of at most 1.22 parent pixels plus the second
-// tap) is staged in shared memory, image and mask, with coalesced loads; each
-// output pixel is then four shared-memory reads and integer FMAs per plane.
-constexpr int kPyrSW = 84, kPyrSH = 24;
+// Each CTA makes a kPyrTW x kPyrTH tile of level l: warp w owns rows
+// kPyrRowsW w .. + kPyrRowsW - 1 of it and lane k columns 4k .. 4k + 3, so a
+// thread computes its four columns' source taps once and reuses them on every
+// row; a row's taps are computed by one lane and broadcast.  Parent pixels
+// are read straight from the previous level (just written, so L2-resident);
+// each output pixel is eight byte loads and integer FMAs, and four pixels go
+// out as one word per plane where the row allows.
+constexpr int kPyrRowsW = kPyrTH / 8;
+
+// Centre-aligned source tap of output position o on a level of nl samples
+// whose parent has np: ((2o + 1) np - nl) / (2 nl) as q0 + f / 2048 (f the
+// Q11 fraction, rounded down), q1 = min(q0 + 1, np - 1).  The integer
+// quotients come from a float reciprocal and one correction step, exact
+// because the float quotient is within one of the true one.
+__device__ __forceinline__ int div_floor(int num, int den, float inv, int &rem)
+{
+    int q = __float2int_rz((float)num * inv);
+    int r = num - q * den;
+    if (r < 0) {
+        --q;
+        r += den;
+    } else if (r >= den) {
+        ++q;
+        r -= den;
+    }
+    rem = r;
+    return q;
+}
+
+__device__ __forceinline__ void pyr_tap(int o, int nl, int np, float inv, int &q0, int &q1, int &f)
+{
+    const int den = 2 * nl;
+    int r, r2;
+    q0 = div_floor((2 * o + 1) * np - nl, den, inv, r);
+    f = div_floor(r << 11, den, inv, r2);
+    q1 = min(q0 + 1, np - 1);
+}
 
 __device__ __forceinline__ void pyramid_tile(int tile, const DevLevel *__restrict__ lv, int n)
 {
-    __shared__ int16_t sx0[kPyrTW], sx1[kPyrTW], sfx[kPyrTW];
-    __shared__ int16_t sy0[kPyrTH], sy1[kPyrTH], sfy[kPyrTH];
-    __shared__ uint8_t pimg[kPyrSH][kPyrSW], pmask[kPyrSH][kPyrSW];
     const int e = find_owner(lv, n, tile, [](const DevLevel &d) { return d.pyr_tile_start; });
     const DevLevel &L = lv[e];
     const int lt = tile - L.pyr_tile_start;
     const int ty = lt / L.pyr_ntx, tx = lt - ty * L.pyr_ntx;
     const int Wl = L.W, Hl = L.H, Wp = L.Wp, Hp = L.Hp;
-    const int xb = tx * kPyrTW, yb = ty * kPyrTH;
-    for (int i = threadIdx.x; i < kPyrTW + kPyrTH; i += blockDim.x) {
-        // centre-aligned source position ((2x+1) Wp - Wl) / (2 Wl), Q11 fraction
-        const bool isx = i < kPyrTW;
-        const int o = isx ? xb + i : yb + (i - kPyrTW);
-        const int nl = isx ? Wl : Hl, np = isx ? Wp : Hp;
-        const int num = (2 * o + 1) * np - nl, den = 2 * nl;
-        const int q0 = num / den;
-        const int f = ((num - q0 * den) << 11) / den;
-        const int q1 = min(q0 + 1, np - 1);
-        if (isx) { sx0[i] = (int16_t)q0; sx1[i] = (int16_t)q1; sfx[i] = (int16_t)f; }
-        else { sy0[i - kPyrTW] = (int16_t)q0; sy1[i - kPyrTW] = (int16_t)q1; sfy[i - kPyrTW] = (int16_t)f; }
-    }
-    __syncthreads();
-    // parent region: columns sx0[0] .. sx1[last], rows sy0[0] .. sy1[last]
-    const int nx = min(kPyrTW, Wl - xb), ny = min(kPyrTH, Hl - yb);
-    const int px0 = sx0[0], py0 = sy0[0];
-    const int pw = sx1[nx - 1] - px0 + 1, ph = sy1[ny - 1] - py0 + 1;
-    const bool staged = pw <= kPyrSW && ph <= kPyrSH;   // always, for level ratios up to 1.3
-    if (staged) {
-        const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5;
-        for (int r = wrp; r < ph; r += 8) {
-            const size_t g = (size_t)(py0 + r) * Wp + px0;
-            for (int c = lane; c < pw; c += 32) {
-                pimg[r][c] = L.prev[g + c];
-                pmask[r][c] = L.prev_mask[g + c];
-            }
-        }
-        __syncthreads();
-    }
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const int xb = tx * kPyrTW + 4 * (int)lane;
+    const int yb = ty * kPyrTH + (int)warp * kPyrRowsW;
+    if (yb >= Hl) return;   // warp-uniform; no barrier follows
+    const float invx = __frcp_rn((float)(2 * Wl)), invy = __frcp_rn((float)(2 * Hl));
+    int x0[4], x1[4], fx[4];
 #pragma unroll
-    for (int k = 0; k < (kPyrTW * kPyrTH) / 256; ++k) {
-        const int p = threadIdx.x + k * 256;
-        const int cx = p % kPyrTW, cy = p / kPyrTW;
-        if (cx >= nx || cy >= ny) continue;
-        const int x = xb + cx, y = yb + cy;
-        const int x0 = sx0[cx], x1 = sx1[cx], fx = sfx[cx];
-        const int y0 = sy0[cy], y1 = sy1[cy], fy = sfy[cy];
-        unsigned a, b, c, d, ma, mb, mc, md;
-        if (staged) {
-            const int u0 = x0 - px0, u1 = x1 - px0, v0 = y0 - py0, v1 = y1 - py0;
-            a = pimg[v0][u0]; b = pimg[v0][u1]; c = pimg[v1][u0]; d = pimg[v1][u1];
-            ma = pmask[v0][u0]; mb = pmask[v0][u1]; mc = pmask[v1][u0]; md = pmask[v1][u1];
-        } else {
-            const uint8_t *r0 = L.prev + y0 * Wp, *r1 = L.prev + y1 * Wp;
-            a = r0[x0]; b = r0[x1]; c = r1[x0]; d = r1[x1];
-            const uint8_t *m0 = L.prev_mask + y0 * Wp, *m1 = L.prev_mask + y1 * Wp;
-            ma = m0[x0]; mb = m0[x1]; mc = m1[x0]; md = m1[x1];
+    for (int c = 0; c < 4; ++c) {
+        pyr_tap(min(xb + c, Wl - 1), Wl, Wp, invx, x0[c], x1[c], fx[c]);
+    }
+    int ry0 = 0, ry1 = 0, rfy = 0;
+    if ((int)lane < kPyrRowsW) pyr_tap(min(yb + (int)lane, Hl - 1), Hl, Hp, invy, ry0, ry1, rfy);
+    const int nx = min(4, Wl - xb);   // this lane's columns inside the level (may be <= 0)
+    const uint8_t *__restrict__ prev = L.prev;
+    const uint8_t *__restrict__ prevm = L.prev_mask;
+#pragma unroll
+    for (int r = 0; r < kPyrRowsW; ++r) {
+        const int y = yb + r;
+        const int y0 = __shfl_sync(0xffffffffu, ry0, r), y1 = __shfl_sync(0xffffffffu, ry1, r);
+        const unsigned fy = (unsigned)__shfl_sync(0xffffffffu, rfy, r), gy = 2048u - fy;
+        if (y >= Hl) break;   // warp-uniform
+        const uint8_t *P0 = prev + (size_t)y0 * Wp, *P1 = prev + (size_t)y1 * Wp;
+        const uint8_t *M0 = prevm + (size_t)y0 * Wp, *M1 = prevm + (size_t)y1 * Wp;
+        uint32_t wi = 0, wm = 0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const unsigned a = __ldg(P0 + x0[c]), b = __ldg(P0 + x1[c]);
+            const unsigned cc = __ldg(P1 + x0[c]), d = __ldg(P1 + x1[c]);
+            const unsigned m = __ldg(M0 + x0[c]) & __ldg(M0 + x1[c]) & __ldg(M1 + x0[c]) & __ldg(M1 + x1[c]);
+            const unsigned f = (unsigned)fx[c], g = 2048u - f;
+            const unsigned sum = gy * (g * a + f * b) + fy * (g * cc + f * d);
+            wi |= ((sum + (1u << 21)) >> 22) << (8 * c);
+            wm |= m << (8 * c);
         }
-        const unsigned gx = 2048 - fx, gy = 2048 - fy;
-        const unsigned s = gx * gy * a + (unsigned)fx * gy * b + gx * (unsigned)fy * c + (unsigned)fx * (unsigned)fy * d;
-        L.img_w[y * Wl + x] = (uint8_t)((s + (1u << 21)) >> 22);
-        L.mask_w[y * Wl + x] = (uint8_t)(ma & mb & mc & md);
+        uint8_t *oi = L.img_w + (size_t)y * Wl + xb, *om = L.mask_w + (size_t)y * Wl + xb;
+        if (nx == 4 && ((((uintptr_t)oi) | ((uintptr_t)om)) & 3u) == 0u) {
+            *reinterpret_cast<uint32_t *>(oi) = wi;
+            *reinterpret_cast<uint32_t *>(om) = wm;
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (c < nx) {
+                    oi[c] = (uint8_t)(wi >> (8 * c));
+                    om[c] = (uint8_t)(wm >> (8 * c));
+                }
+        }
     }
 }
 
 // Grid-stride over the tiles: one CTA per tile, or a persistent grid.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 pyramid_kernel(int n_tiles, const DevLevel *__restrict__ lv, int n)
 {
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        pyramid_tile(tile, lv, n);
-        __syncthreads();
-    }
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) pyramid_tile(tile, lv, n);
 }
 
 // ---------------------------------------------------------------- mask row hulls
@@ -235,7 +252,6 @@ constexpr int kHalo = 5;                        // FAST (3) / Harris (4) at the 
 constexpr int kSW = kDetTW + 2 * kHalo;         // staged image
 constexpr int kSH = kDetTH + 2 * kHalo;
 constexpr int kRW = kDetTW + 2, kRH = kDetTH + 2;   // tile + one-pixel ring
-constexpr int kGW = kDetTW + 8, kGH = kDetTH + 8;   // Sobel gradients for the ring's 7x7 windows
 constexpr int kDetCols = 64;                    // threads along x; blockDim = kDetCols * kDetRowsPar
 constexpr int kDetRowsPar = 4;
 // The staged image has a row pitch P in 80..83 congruent to the level's width
@@ -248,7 +264,7 @@ constexpr int kSPMin = kSW + 6, kSPMax = kSPMin + 3;
 
 struct DetSmem {
     long long R[kRH][kRW];
-    int16_t gx[kGH][kGW], gy[kGH][kGW];
+    int16_t surv[kRH * kRW];     // compass survivors
     int16_t clist[kRH * kRW];
     __align__(16) uint8_t img[kSH * kSPMax];
     uint32_t isc[kRH][(kRW + 31) / 32];   // corner flags of the tile + ring, one bit per column
@@ -307,8 +323,6 @@ __device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__r
     auto &isc = sm.isc;
     constexpr int kIscWords = (kRW + 31) / 32;
     auto &R = sm.R;
-    auto &gx = sm.gx;
-    auto &gy = sm.gy;
     int16_t *clist = sm.clist;
     int &ncl = sm.ncl;
 
@@ -392,8 +406,7 @@ __device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__r
     // (b) the full test and the mask corners on the list.  Both passes append
     // with one shared atomic per warp (every lane runs every iteration).
     const unsigned lane_id = threadIdx.x & 31u;
-    static_assert(kRH * kRW <= kGH * kGW, "the survivor list fits the Sobel buffer");
-    int16_t *surv = &gx[0][0];
+    int16_t *surv = sm.surv;
 #pragma unroll 1
     for (int k = 0; k < (kRH * kRW + kThreads - 1) / kThreads; ++k) {
         const int el = (int)threadIdx.x + k * kThreads;
@@ -440,31 +453,44 @@ __device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__r
     const int nc = ncl;
     if (nc == 0) return;
 
-    // Sobel derivatives once per pixel of the ring's windows; gradient (r, c)
-    // is image pixel (x0 - 4 + c, y0 - 4 + r), staged pixel (c + 1, r + 1)
-    for (int el = threadIdx.x; el < kGH * kGW; el += kThreads) {
-        const int r = el / kGW, c = el - r * kGW;
-        const int X = c + 1, Y = r + 1;
-        const uint8_t *q = S + Y * P + X;
-        gx[r][c] = (int16_t)((q[-P + 1] + 2 * q[1] + q[P + 1]) - (q[-P - 1] + 2 * q[-1] + q[P - 1]));
-        gy[r][c] = (int16_t)((q[P - 1] + 2 * q[P] + q[P + 1]) - (q[-P - 1] + 2 * q[-P] + q[-P + 1]));
-    }
-    __syncthreads();
-
-    // Harris x25 at every corner of the tile + ring (7x7 window of the ring
-    // pixel (r, c) = gradient rows r..r+6, columns c..c+6)
+    // Harris x25 at every corner of the tile + ring, one thread per corner,
+    // straight from the staged image: the 7x7 window of Sobel gradients of
+    // ring pixel (r, c) (staged (r + 4, c + 4)) reads the 9 x 9 staged pixels
+    // from (r, c); the thread slides three pixel rows down the window, with
+    // gx = v(x + 1) - v(x - 1) on the column sums v = p0 + 2 p1 + p2 and
+    // gy = d(x - 1) + 2 d(x) + d(x + 1) on the row differences d = p2 - p0.
     for (int q = threadIdx.x; q < nc; q += blockDim.x) {
         const int p = clist[q];
         const int r = p / kRW, c = p - r * kRW;
+        const uint8_t *w = S + r * P + c;
+        int p0[9], p1[9], p2[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            p0[k] = w[k];
+            p1[k] = w[P + k];
+        }
         int a = 0, bb = 0, cc = 0;
 #pragma unroll
         for (int dy = 0; dy < 7; ++dy) {
 #pragma unroll
+            for (int k = 0; k < 9; ++k) p2[k] = w[(dy + 2) * P + k];
+            int v[9], d[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                v[k] = p0[k] + 2 * p1[k] + p2[k];
+                d[k] = p2[k] - p0[k];
+            }
+#pragma unroll
             for (int dx = 0; dx < 7; ++dx) {
-                const int ix = gx[r + dy][c + dx], iy = gy[r + dy][c + dx];
+                const int ix = v[dx + 2] - v[dx], iy = d[dx] + 2 * d[dx + 1] + d[dx + 2];
                 a += ix * ix;
                 bb += iy * iy;
                 cc += ix * iy;
+            }
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                p0[k] = p1[k];
+                p1[k] = p2[k];
             }
         }
         const long long A = a, B = bb, Cc = cc;
