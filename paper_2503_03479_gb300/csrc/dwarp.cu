@@ -209,10 +209,13 @@ __device__ __forceinline__ void scatter_ubar(float *__restrict__ ubar, int W, in
 constexpr int kPatch = 40, kPatchPitch = 41;
 
 // u-bar += cb w_x w_y over the taps of p, into the patch whose pixel (0, 0)
-// is source (bx0, by0) (shared-memory atomics); a tap outside the patch,
-// which its box construction rules out, goes to u-bar directly.
-__device__ __forceinline__ void scatter_patch(float *P, int bx0, int by0, int PW, int PH, float *__restrict__ ubar,
-                                              int W, int H, float px, float py, float cb)
+// is source (bx0, by0), in fixed point: each product is rounded to a multiple
+// of 1/scale and added with a shared-memory integer atomic (exact and in
+// any order, where float adds would need compare-and-swap loops); a tap
+// outside the patch, which its box construction rules out, goes to u-bar
+// directly.
+__device__ __forceinline__ void scatter_patch(int *P, int bx0, int by0, int PW, int PH, float scale,
+                                              float *__restrict__ ubar, int W, int H, float px, float py, float cb)
 {
     const float fx0 = floorf(px), fy0 = floorf(py);
     const int x0 = (int)fx0, y0 = (int)fy0;
@@ -228,13 +231,28 @@ __device__ __forceinline__ void scatter_patch(float *P, int bx0, int by0, int PW
     int xs[6];
 #pragma unroll
     for (int m = 0; m < 6; ++m) xs[m] = clampi(x0 + m - 2, 0, W - 1) - bx0;
+    const float cs = cb * scale;
 #pragma unroll
     for (int n = 0; n < 6; ++n) {
-        float *row = P + (clampi(y0 + n - 2, 0, H - 1) - by0) * kPatchPitch;
-        const float cn = cb * wy[n];
+        int *row = P + (clampi(y0 + n - 2, 0, H - 1) - by0) * kPatchPitch;
+        const float cn = cs * wy[n];
 #pragma unroll
-        for (int m = 0; m < 6; ++m) atomicAdd(row + xs[m], cn * wx[m]);
+        for (int m = 0; m < 6; ++m) atomicAdd(row + xs[m], __float2int_rn(cn * wx[m]));
     }
+}
+
+// The largest value of v over the block, in every thread (red: 8 floats,
+// free on entry).
+__device__ __forceinline__ float block_max_all(float v, float *red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float m = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+    return m;
 }
 
 // One block of 64 threads per view: cos, sin of phi and sigma(t) in fp64,
@@ -517,7 +535,7 @@ dwarp_bwd_kernel(const DiffView *__restrict__ views, const DiffPrep *__restrict_
     __syncthreads();
 
     // rotation transposed: dL/dp -> (phi, tx, ty) from the stored dC/dp
-    float pb = 0.f, txb = 0.f, tyb = 0.f;
+    float pb = 0.f, txb = 0.f, tyb = 0.f, cmax = 0.f;
     const float dg2r = 0.017453292519943295f;
     for (int e = threadIdx.x; e < nrows * T.cw; e += blockDim.x) {
         const int r = e / T.cw, c = e - r * T.cw;
@@ -530,19 +548,29 @@ dwarp_bwd_kernel(const DiffView *__restrict__ views, const DiffPrep *__restrict_
         txb = fmaf(cb, dcdx, txb);
         tyb = fmaf(cb, dcdy, tyb);
         pb = fmaf(cb, dcdx * (-G.s * dx + G.c * dy) + dcdy * (-G.c * dx - G.s * dy), pb);
+        cmax = isfinite(cb) ? fmaxf(cmax, fabsf(cb)) : INFINITY;   // non-finite: the float path
     }
 
     // and, when asked for, u-bar through the rotation's weights: blocks of
     // 32 canvas columns x the tile's rows (one point per thread) add into a
     // shared-memory patch over their taps' source box, which then goes to
     // u-bar with one global atomic per touched pixel (two patches alternate,
-    // so one barrier separates a block's adds from its flush)
+    // so one barrier separates a block's adds from its flush).  The patch
+    // holds fixed point with scale 2^(24 - k), where 2^k bounds the tile's
+    // |C-bar|: a patch pixel sums at most 36 products of at most 1.2 |C-bar|,
+    // below 2^31 / scale, and each product is rounded by at most 2^-25 of the
+    // tile's largest |C-bar|.
     if (V.ubar) {
-        __shared__ float patch[2][kPatch * kPatchPitch];
+        __shared__ int patch[2][kPatch * kPatchPitch];
+        const float cm = block_max_all(cmax, red);
+        int k2;
+        frexpf(cm, &k2);
+        const bool fixed = cm >= 1e-30f && cm < INFINITY;
+        const float scale = fixed ? ldexpf(1.f, 24 - k2) : 0.f, inv = fixed ? ldexpf(1.f, k2 - 24) : 0.f;
         const int Wu = V.W, Hu = V.H;
         const int r = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31u);
         int buf = 0;
-        for (int q0 = 0; q0 < T.cw; q0 += 32, buf ^= 1) {
+        for (int q0 = 0; q0 < T.cw && cm > 0.f; q0 += 32, buf ^= 1) {
             const int qn = min(32, T.cw - q0);
             int bx0 = INT_MAX, bx1 = INT_MIN, by0 = INT_MAX, by1 = INT_MIN;
 #pragma unroll
@@ -562,11 +590,11 @@ dwarp_bwd_kernel(const DiffView *__restrict__ views, const DiffPrep *__restrict_
             by0 = clampi(by0 - 3, 0, Hu - 1);
             by1 = clampi(by1 + 4, 0, Hu - 1);
             const int PW = bx1 - bx0 + 1, PH = by1 - by0 + 1;
-            const bool fits = PW <= kPatch && PH <= kPatch;
-            float *P = patch[buf];
+            const bool fits = fixed && PW <= kPatch && PH <= kPatch;
+            int *P = patch[buf];
             if (fits)
                 for (int ly = r; ly < PH; ly += kDThreads / 32)
-                    for (int lx = lane; lx < PW; lx += 32) P[ly * kPatchPitch + lx] = 0.f;
+                    for (int lx = lane; lx < PW; lx += 32) P[ly * kPatchPitch + lx] = 0;
             __syncthreads();
             const int c = q0 + lane;
             if (lane < qn && r < nrows) {
@@ -574,7 +602,7 @@ dwarp_bwd_kernel(const DiffView *__restrict__ views, const DiffPrep *__restrict_
                 if (cb != 0.f) {
                     float px, py;
                     G.map(T.clo + c, T.j0 + r, px, py);
-                    if (fits) scatter_patch(P, bx0, by0, PW, PH, V.ubar, Wu, Hu, px, py, cb);
+                    if (fits) scatter_patch(P, bx0, by0, PW, PH, scale, V.ubar, Wu, Hu, px, py, cb);
                     else scatter_ubar(V.ubar, Wu, Hu, px, py, cb);
                 }
             }
@@ -582,8 +610,8 @@ dwarp_bwd_kernel(const DiffView *__restrict__ views, const DiffPrep *__restrict_
             if (fits)
                 for (int ly = r; ly < PH; ly += kDThreads / 32)
                     for (int lx = lane; lx < PW; lx += 32) {
-                        const float v = P[ly * kPatchPitch + lx];
-                        if (v != 0.f) atomicAdd(V.ubar + (size_t)(by0 + ly) * Wu + bx0 + lx, v);
+                        const int v = P[ly * kPatchPitch + lx];
+                        if (v != 0) atomicAdd(V.ubar + (size_t)(by0 + ly) * Wu + bx0 + lx, (float)v * inv);
                     }
         }
     }

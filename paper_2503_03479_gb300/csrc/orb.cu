@@ -83,7 +83,7 @@ __device__ __forceinline__ void pyramid_tile(int tile, const DevLevel *__restric
     const int nx = min(4, Wl - xb);   // this lane's columns inside the level (may be <= 0)
     const uint8_t *__restrict__ prev = L.prev;
     const uint8_t *__restrict__ prevm = L.prev_mask;
-#pragma unroll
+#pragma unroll 1
     for (int r = 0; r < kPyrRowsW; ++r) {
         const int y = yb + r;
         const int y0 = __shfl_sync(0xffffffffu, ry0, r), y1 = __shfl_sync(0xffffffffu, ry1, r);
@@ -118,7 +118,7 @@ __device__ __forceinline__ void pyramid_tile(int tile, const DevLevel *__restric
 }
 
 // Grid-stride over the tiles: one CTA per tile, or a persistent grid.
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, 4)
 pyramid_kernel(int n_tiles, const DevLevel *__restrict__ lv, int n)
 {
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) pyramid_tile(tile, lv, n);
@@ -453,48 +453,52 @@ __device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__r
     const int nc = ncl;
     if (nc == 0) return;
 
-    // Harris x25 at every corner of the tile + ring, one thread per corner,
-    // straight from the staged image: the 7x7 window of Sobel gradients of
-    // ring pixel (r, c) (staged (r + 4, c + 4)) reads the 9 x 9 staged pixels
-    // from (r, c); the thread slides three pixel rows down the window, with
-    // gx = v(x + 1) - v(x - 1) on the column sums v = p0 + 2 p1 + p2 and
-    // gy = d(x - 1) + 2 d(x) + d(x + 1) on the row differences d = p2 - p0.
-    for (int q = threadIdx.x; q < nc; q += blockDim.x) {
-        const int p = clist[q];
-        const int r = p / kRW, c = p - r * kRW;
-        const uint8_t *w = S + r * P + c;
-        int p0[9], p1[9], p2[9];
+    // Harris x25 at every corner of the tile + ring, straight from the staged
+    // image, eight lanes per corner: the 7x7 window of Sobel gradients of ring
+    // pixel (r, c) (staged (r + 4, c + 4)) reads the 9 x 9 staged pixels from
+    // (r, c), and lane s < 7 takes window row s from pixel rows s .. s + 2,
+    // with gx = v(x + 1) - v(x - 1) on the column sums v = p0 + 2 p1 + p2 and
+    // gy = d(x - 1) + 2 d(x) + d(x + 1) on the row differences d = p2 - p0;
+    // the group's sums are exact integers in any order.
+    {
+        const int sub = (int)(lane_id & 7u), slot = (int)(threadIdx.x >> 3);
+#pragma unroll 1
+        for (int q0 = 0; q0 < nc; q0 += kThreads / 8) {
+            const int q = q0 + slot;
+            int a = 0, bb = 0, cc = 0, p = 0;
+            if (q < nc) {
+                p = clist[q];
+                if (sub < 7) {
+                    const int r = p / kRW, c = p - r * kRW;
+                    const uint8_t *w = S + (r + sub) * P + c;
+                    int v[9], d[9];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            p0[k] = w[k];
-            p1[k] = w[P + k];
+                    for (int k = 0; k < 9; ++k) {
+                        const int p0 = w[k], p1 = w[P + k], p2 = w[2 * P + k];
+                        v[k] = p0 + 2 * p1 + p2;
+                        d[k] = p2 - p0;
+                    }
+#pragma unroll
+                    for (int dx = 0; dx < 7; ++dx) {
+                        const int ix = v[dx + 2] - v[dx], iy = d[dx] + 2 * d[dx + 1] + d[dx + 2];
+                        a += ix * ix;
+                        bb += iy * iy;
+                        cc += ix * iy;
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) {
+                a += __shfl_xor_sync(0xffffffffu, a, o);
+                bb += __shfl_xor_sync(0xffffffffu, bb, o);
+                cc += __shfl_xor_sync(0xffffffffu, cc, o);
+            }
+            if (q < nc && sub == 0) {
+                const int r = p / kRW, c = p - r * kRW;
+                const long long A = a, B = bb, Cc = cc;
+                R[r][c] = 25 * (A * B - Cc * Cc) - (A + B) * (A + B);
+            }
         }
-        int a = 0, bb = 0, cc = 0;
-#pragma unroll
-        for (int dy = 0; dy < 7; ++dy) {
-#pragma unroll
-            for (int k = 0; k < 9; ++k) p2[k] = w[(dy + 2) * P + k];
-            int v[9], d[9];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                v[k] = p0[k] + 2 * p1[k] + p2[k];
-                d[k] = p2[k] - p0[k];
-            }
-#pragma unroll
-            for (int dx = 0; dx < 7; ++dx) {
-                const int ix = v[dx + 2] - v[dx], iy = d[dx] + 2 * d[dx + 1] + d[dx + 2];
-                a += ix * ix;
-                bb += iy * iy;
-                cc += ix * iy;
-            }
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                p0[k] = p1[k];
-                p1[k] = p2[k];
-            }
-        }
-        const long long A = a, B = bb, Cc = cc;
-        R[r][c] = 25 * (A * B - Cc * Cc) - (A + B) * (A + B);
     }
     __syncthreads();
 
