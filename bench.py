@@ -326,15 +326,17 @@ def match_roofline(sizes, ms: float, tensor: bool, peaks: dict) -> dict:
 def orb_level_bytes(A, views, n_levels: int):
     """Algorithmic bytes of the two HBM-bound ORB stages for one image's views:
     detect reads 1 B per pyramid pixel (every level); the pyramid reads the
-    parent level's image and mask (2 B per parent pixel) and writes the
-    level's image and mask (2 B per pixel) for every level >= 1."""
+    parent level's image (1 B per parent pixel) and writes the level's image
+    (1 B per pixel) for every level >= 1.  A view's footprint mask is 0/1 on
+    an interval of each row at every level, so its pyramid is the row hulls
+    (a few bytes per row), not a second image plane."""
     det = pyr = 0
     for v in views:
         for l in range(n_levels):
             n = A.level_size(v.Wv, l) * A.level_size(v.Hv, l)
             det += n
             if l:
-                pyr += 2 * (A.level_size(v.Wv, l - 1) * A.level_size(v.Hv, l - 1) + n)
+                pyr += A.level_size(v.Wv, l - 1) * A.level_size(v.Hv, l - 1) + n
     return det, pyr
 
 

@@ -624,6 +624,7 @@ struct OrbBuffers {
     int32_t *taken, *pool_off;
     int32_t *group_total;
     int32_t *row_lo, *row_hi;    // mask row hulls of every level (row_off of each entry)
+    int32_t *unit;               // per view: nonzero when its masks are exactly their row hulls
 };
 
 // Workspace region of the ORB stages for nv views in n_groups groups.
@@ -642,6 +643,7 @@ static void orb_layout(Bump &b, const LevelTables &T, int nv, int n_groups, cons
     o.group_total = b.take<int32_t>(n_groups);
     o.row_lo = b.take<int32_t>(std::max<long long>(T.rows_total, 1));
     o.row_hi = b.take<int32_t>(std::max<long long>(T.rows_total, 1));
+    o.unit = b.take<int32_t>(std::max(nv, 1));
 }
 
 // Runs pyramid -> detect -> select -> pool scan -> orientation + BRIEF.
@@ -657,15 +659,15 @@ static cudaError_t run_orb(asift_ctx *ctx, const LevelTables &T, int nv, int n_g
     cudaError_t e = cudaMemsetAsync(o.cand_count, 0, sizeof(int32_t) * nl, s);
     if (e != cudaSuccess) return e;
     // mask row hulls: level 0 scanned, levels >= 1 derived through the pyramid's taps
-    e = launch_mask_rows(o.lv, nv, L, (int)T.rows_level0, o.row_lo, o.row_hi, s);
+    e = launch_mask_rows(o.lv, nv, L, (int)T.rows_level0, o.row_lo, o.row_hi, o.unit, s);
     if (e != cudaSuccess) return e;
     if (!per_view) {
         for (int l = 1; l < L && e == cudaSuccess; ++l)
-            e = launch_pyramid(o.lv + (size_t)l * nv, nv, T.pyr_tiles[l], s, pyr_grid);
+            e = launch_pyramid(o.lv + (size_t)l * nv, nv, T.pyr_tiles[l], o.unit, s, pyr_grid);
         prof_mark(ctx, 3, s);
         if (e == cudaSuccess)
             e = launch_detect(o.lv, (int)nl, T.det_tiles, cfg.fast_threshold, o.cand, o.cand_count, o.row_lo, o.row_hi,
-                              s, det_grid);
+                              o.unit, s, det_grid);
         prof_mark(ctx, 4, s);
         if (e == cudaSuccess)
             e = launch_select(o.lv, (int)nl, o.cand, o.cand_count, N, o.slots, o.taken, o.status, s);
@@ -676,12 +678,12 @@ static cudaError_t run_orb(asift_ctx *ctx, const LevelTables &T, int nv, int n_g
         for (int v = 0; v < nv && e == cudaSuccess; ++v) {
             for (int l = 1; l < L && e == cudaSuccess; ++l) {
                 const size_t i = (size_t)l * nv + v;
-                e = launch_pyramid(o.lv + i, 1, pyr_tiles_of(T.lv[i]), s);
+                e = launch_pyramid(o.lv + i, 1, pyr_tiles_of(T.lv[i]), o.unit, s);
             }
             for (int l = 0; l < L && e == cudaSuccess; ++l) {
                 const size_t i = (size_t)l * nv + v;
                 e = launch_detect(o.lv + i, 1, det_tiles_of(T.lv[i]), cfg.fast_threshold, o.cand, o.cand_count + i,
-                                  o.row_lo, o.row_hi, s);
+                                  o.row_lo, o.row_hi, o.unit, s);
             }
             for (int l = 0; l < L && e == cudaSuccess; ++l) {
                 const size_t i = (size_t)l * nv + v;
@@ -1599,7 +1601,7 @@ asift_status asift_plan_autotune(asift_plan *plan, int reps, asift_tuning *out)
         {&t.warp_seg, {0, 256, 512, 768}},     // the view simulation's tile shape (0 = 384)
         {&t.warp_grid, {0, 2 * sms, 3 * sms}},
         {&t.pyramid_grid, {0, 4 * sms, 8 * sms}},
-        {&t.detect_grid, {0, 4 * sms, 8 * sms}},
+        {&t.detect_grid, {0, 7 * sms, 14 * sms}},
     };
     if (tc_match_available()) knobs.push_back({&t.match_engine, {ASIFT_MATCH_TENSOR_CORES, ASIFT_MATCH_CUDA_CORES}});
     cudaError_t e = cudaSuccess;
@@ -1711,9 +1713,10 @@ static asift_status warp_call(bool backward, asift_ctx *ctx, const float *d_u, i
         d.Hv = S.Hv;
         d.K = S.K;
         d.tile_start = tiles;
-        tiles += dwarp_tiles(S.Wv, S.Hv, &d.ntx);
+        d.tw = dwarp_tile_width(backward);
+        tiles += dwarp_tiles(S.Wv, S.Hv, d.tw, &d.ntx);
         int cw, bw;
-        dwarp_strip_widths(S.Wv, t_max, S.K, &cw, &bw);
+        dwarp_strip_widths(d.tw, t_max, S.K, &cw, &bw);
         cw_max = std::max(cw_max, cw);
         bw_max = std::max(bw_max, bw);
     }

@@ -118,7 +118,7 @@ struct DiffView {
     float *out;              // view (forward)
     const double *param;     // t, phi (deg), tx, ty
     double *pbar;            // dL/d(t, phi, tx, ty) (backward)
-    int32_t W, H, Wr, Hr, Wv, Hv, K, tile_start, ntx, pad;
+    int32_t W, H, Wr, Hr, Wv, Hv, K, tile_start, ntx, tw;   // tw: view columns per tile
 };
 
 // Per-view constants of the differentiable warp, made once per call on the

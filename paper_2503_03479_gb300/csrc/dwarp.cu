@@ -22,7 +22,12 @@
 
 namespace asift {
 
-constexpr int kDTW = 32, kDTH = 8, kDThreads = 256;
+// Tiles of kDTH view rows x tw view columns: the forward takes tw = 64 (its
+// canvas strip, t (tw - 1) + 8 + 2K columns, then recomputes a smaller share
+// of halo per view pixel), the backward tw = 32 (five strips of shared memory
+// per row, so a narrower tile keeps three CTAs per SM).
+constexpr int kDTWFwd = 64, kDTWBwd = 32, kDTH = 8, kDThreads = 256;
+constexpr int kBcPad = ASIFT_MAX_GAUSS;   // zero columns either side of a folded B-bar row (> K)
 
 // sinc(x) and sinc(x/3) with their x-derivatives near x = 0 (|x| < 1e-2),
 // where the closed forms cancel: the series to (pi x)^4.
@@ -328,8 +333,8 @@ __device__ __forceinline__ DTile dtile(const DiffView *views, int n_views, int t
     const DiffView &V = views[T.v];
     const int lt = tile - V.tile_start;
     const int ty = lt / V.ntx, tx = lt - ty * V.ntx;
-    T.xa = tx * kDTW;
-    T.xb = min(T.xa + kDTW, V.Wv) - 1;
+    T.xa = tx * V.tw;
+    T.xb = min(T.xa + V.tw, V.Wv) - 1;
     T.j0 = ty * kDTH;
     T.j1 = min(T.j0 + kDTH, V.Hv) - 1;
     T.t = (float)V.param[0];
@@ -356,6 +361,22 @@ __device__ __forceinline__ DGeom dgeom(const DiffView &V, const DiffPrep &P)
     G.crx = (V.Wr - 1) * 0.5f;
     G.cry = (V.Hr - 1) * 0.5f;
     return G;
+}
+
+// The tilt taps of the tile's view columns (one thread per column): X0 =
+// floor(X) and the Lanczos-3 weights at X - X0 (with their derivatives when
+// dw is given), shared by the tile's rows.
+__device__ __forceinline__ void tilt_columns(const DTile &T, float cr, int *X0s, float (*w)[6], float (*dw)[6])
+{
+    const int ncols = T.xb - T.xa + 1;
+    const int c = (int)threadIdx.x;
+    if (c < ncols) {
+        const float X = T.t * ((float)(T.xa + c) - T.crv) + cr;
+        const float fX = floorf(X);
+        X0s[c] = (int)fX;
+        if (dw) lanczos3_wd(X - fX, w[c], dw[c]);
+        else lanczos3_w(X - fX, w[c]);
+    }
 }
 
 // Recomputes the canvas strip C (actual columns clo..chi) and its blur B
@@ -405,23 +426,21 @@ dwarp_fwd_kernel(const DiffView *__restrict__ views, const DiffPrep *__restrict_
     }
     const DiffPrep &Pp = prep[T.v];
     const DGeom G = dgeom(V, Pp);
-    load_taps(Pp, V.K, g, dg);   // visible after the strip's first barrier
+    __shared__ int tX0[kDTWFwd];
+    __shared__ float tw[kDTWFwd][6];
+    const float cr = (V.Wr - 1) * 0.5f;
+    load_taps(Pp, V.K, g, dg);                  // both visible after the
+    tilt_columns(T, cr, tX0, tw, nullptr);      // strip's first barrier
     strips(V, T, G, g, Cs, Bs, cw_max, bw_max);
     const int nrows = T.j1 - T.j0 + 1, ncols = T.xb - T.xa + 1;
-    const float cr = (V.Wr - 1) * 0.5f;
     for (int e = threadIdx.x; e < nrows * ncols; e += blockDim.x) {
         const int r = e / ncols, c = e - r * ncols;
-        const int x = T.xa + c;
-        const float X = T.t * ((float)x - T.crv) + cr;
-        const float fX = floorf(X);
-        const int X0 = (int)fX;
-        float w[6];
-        lanczos3_w(X - fX, w);
+        const int X0 = tX0[c];
         const float *Brow = Bs + r * bw_max - T.bx0;
         float v = 0.f;
 #pragma unroll
-        for (int m = 0; m < 6; ++m) v = fmaf(w[m], Brow[X0 + m - 2], v);
-        V.out[(size_t)(T.j0 + r) * V.Wv + x] = v;
+        for (int m = 0; m < 6; ++m) v = fmaf(tw[c][m], Brow[X0 + m - 2], v);
+        V.out[(size_t)(T.j0 + r) * V.Wv + T.xa + c] = v;
     }
 }
 
@@ -444,8 +463,10 @@ dwarp_bwd_kernel(const DiffView *__restrict__ views, const DiffPrep *__restrict_
 {
     extern __shared__ float sm[];
     float *Cs = sm, *Cx = Cs + kDTH * cw_max, *Cy = Cx + kDTH * cw_max, *Cb = Cy + kDTH * cw_max;
-    float *Bc = Cb + kDTH * cw_max;                  // B-bar folded onto canvas columns (clo .. chi)
-    float *Bs = Bc + kDTH * cw_max, *Bb = Bs + kDTH * bw_max;
+    // B-bar folded onto canvas columns clo .. chi, with kBcPad zero columns either side
+    const int bcp = cw_max + 2 * kBcPad;
+    float *Bc = Cb + kDTH * cw_max;
+    float *Bs = Bc + kDTH * bcp, *Bb = Bs + kDTH * bw_max;
     __shared__ float g[ASIFT_MAX_GAUSS], dg[ASIFT_MAX_GAUSS], red[kDThreads / 32];
     const DTile T = dtile(views, n_views, blockIdx.x);
     const DiffView &V = views[T.v];
@@ -456,45 +477,64 @@ dwarp_bwd_kernel(const DiffView *__restrict__ views, const DiffPrep *__restrict_
     const DiffPrep &Pp = prep[T.v];
     const DGeom G = dgeom(V, Pp);
     const int K = V.K, last = V.Wr - 1;
-    load_taps(Pp, K, g, dg);   // visible after the strip's first barrier
+    __shared__ int tX0[kDTWBwd];
+    __shared__ float tw[kDTWBwd][6], tdw[kDTWBwd][6], vbs[kDTH][kDTWBwd];
+    const float cr = (V.Wr - 1) * 0.5f;
+    load_taps(Pp, K, g, dg);                    // all visible after the
+    tilt_columns(T, cr, tX0, tw, tdw);          // strip's first barrier
+    {
+        const int ncols = T.xb - T.xa + 1, nrows = T.j1 - T.j0 + 1;
+        for (int e = threadIdx.x; e < nrows * ncols; e += blockDim.x) {
+            const int r = e / ncols, c = e - r * ncols;
+            vbs[r][c] = V.vbar[(size_t)(T.j0 + r) * V.Wv + T.xa + c];
+        }
+    }
     strips(V, T, G, g, Cs, Bs, cw_max, bw_max, Cx, Cy);
     const int nrows = T.j1 - T.j0 + 1, ncols = T.xb - T.xa + 1;
-    for (int e = threadIdx.x; e < kDTH * bw_max; e += blockDim.x) Bb[e] = 0.f;
-    for (int e = threadIdx.x; e < kDTH * cw_max; e += blockDim.x) Bc[e] = 0.f;
-    __syncthreads();
-
-    // tilt transposed: B-bar at the strip positions (six shared atomics per
-    // view pixel), and dL/dt through X
-    const float cr = (V.Wr - 1) * 0.5f;
+    // tilt transposed as a gather: strip position P = bx0 + p takes w_c[P - X0_c + 2]
+    // vbar(c) from the view columns c with X0_c - 2 <= P <= X0_c + 3 (X0 grows
+    // with c, so they are consecutive: at most 6 / t + 1 of them)
+    for (int e = threadIdx.x; e < nrows * T.bw; e += blockDim.x) {
+        const int r = e / T.bw, p = e - r * T.bw, Pp_ = T.bx0 + p;
+        int lo = 0, hi = ncols;   // first column with X0 + 3 >= P
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (tX0[mid] + 3 >= Pp_) hi = mid; else lo = mid + 1;
+        }
+        float acc = 0.f;
+        for (int c = lo; c < ncols && tX0[c] - 2 <= Pp_; ++c) acc = fmaf(tw[c][Pp_ - tX0[c] + 2], vbs[r][c], acc);
+        Bb[r * bw_max + p] = acc;
+    }
+    // dL/dt through X: sum vbar dv/dX (x - (Wv - 1)/2)
     float tb = 0.f;
     for (int e = threadIdx.x; e < nrows * ncols; e += blockDim.x) {
         const int r = e / ncols, c = e - r * ncols;
-        const int x = T.xa + c;
-        const float vb = V.vbar[(size_t)(T.j0 + r) * V.Wv + x];
-        const float X = T.t * ((float)x - T.crv) + cr;
-        const float fX = floorf(X);
-        const int X0 = (int)fX;
-        float w[6], dw[6];
-        lanczos3_wd(X - fX, w, dw);
+        const int X0 = tX0[c];
         const float *Brow = Bs + r * bw_max - T.bx0;
-        float *Bbrow = Bb + r * bw_max - T.bx0;
         float dvdX = 0.f;
 #pragma unroll
-        for (int m = 0; m < 6; ++m) {
-            // strip position X0+m-2 holds column clamp(X0+m-2): the clamped
-            // taps of the forward accumulate at their strip positions
-            atomicAdd(Bbrow + X0 + m - 2, w[m] * vb);
-            dvdX = fmaf(dw[m], Brow[X0 + m - 2], dvdX);
-        }
-        tb = fmaf(vb * dvdX, (float)x - T.crv, tb);
+        for (int m = 0; m < 6; ++m) dvdX = fmaf(tdw[c][m], Brow[X0 + m - 2], dvdX);
+        tb = fmaf(vbs[r][c] * dvdX, (float)(T.xa + c) - T.crv, tb);
     }
     __syncthreads();
 
-    // strip positions folded onto their (clamped) canvas columns
-    for (int e = threadIdx.x; e < nrows * T.bw; e += blockDim.x) {
-        const int r = e / T.bw, c = e - r * T.bw;
-        const float b = Bb[r * bw_max + c];
-        if (b != 0.f) atomicAdd(Bc + r * cw_max + clampi(T.bx0 + c, 0, last) - T.clo, b);
+    // strip positions folded onto their (clamped) canvas columns: an inner
+    // column is one strip position, the canvas edges sum the clamped ones;
+    // the pad columns are zero
+    const int bcw = T.cw + 2 * kBcPad;
+    for (int e = threadIdx.x; e < nrows * bcw; e += blockDim.x) {
+        const int r = e / bcw, c = e - r * bcw - kBcPad, ic = T.clo + c;
+        const float *Bbrow = Bb + r * bw_max;
+        float acc = 0.f;
+        if (c >= 0 && c < T.cw) {
+            if (ic > 0 && ic < last) {
+                const int p = ic - T.bx0;
+                if (p >= 0 && p < T.bw) acc = Bbrow[p];
+            } else {
+                for (int p = 0; p < T.bw; ++p) acc += (clampi(T.bx0 + p, 0, last) == ic) ? Bbrow[p] : 0.f;
+            }
+        }
+        Bc[r * bcp + kBcPad + c] = acc;
     }
     __syncthreads();
 
@@ -507,15 +547,17 @@ dwarp_bwd_kernel(const DiffView *__restrict__ views, const DiffPrep *__restrict_
     for (int e = threadIdx.x; e < nrows * T.cw; e += blockDim.x) {
         const int r = e / T.cw, c = e - r * T.cw;
         const int col = T.clo + c;
-        const float *Bcrow = Bc + r * cw_max - T.clo;
+        const float *Bcrow = Bc + r * bcp + kBcPad - T.clo;
         float acc = 0.f, dacc = 0.f;
         if (col > 0 && col < last) {
-            const int lo = max(col - K, T.clo), hi = min(col + K, T.chi);
-            for (int ic = lo; ic <= hi; ++ic) {
-                const float b = Bcrow[ic];
-                const int k = abs(ic - col);
-                acc = fmaf(g[k], b, acc);
-                dacc = fmaf(dg[k], b, dacc);
+            // symmetric taps in pairs; columns beyond clo .. chi read the zero pads
+            const float *b = Bcrow + col;
+            acc = g[0] * b[0];
+            dacc = dg[0] * b[0];
+            for (int k = 1; k <= K; ++k) {
+                const float pair = b[-k] + b[k];
+                acc = fmaf(g[k], pair, acc);
+                dacc = fmaf(dg[k], pair, dacc);
             }
         } else {
             for (int ic = max(col - K, T.clo); ic <= min(col + K, T.chi); ++ic) {
@@ -689,17 +731,18 @@ warp_adam_kernel(int n, double *__restrict__ params, const double *__restrict__ 
 }
 
 // ---------------------------------------------------------------- host side
-void dwarp_strip_widths(int Wv, double t_max, int K, int *cw, int *bw)
+int dwarp_tile_width(bool backward) { return backward ? kDTWBwd : kDTWFwd; }
+
+void dwarp_strip_widths(int tw, double t_max, int K, int *cw, int *bw)
 {
-    (void)Wv;
-    const int span = (int)std::ceil(t_max * (kDTW - 1)) + 2;
+    const int span = (int)std::ceil(t_max * (tw - 1)) + 2;
     *bw = span + 6;
     *cw = *bw + 2 * K;
 }
 
-int dwarp_tiles(int Wv, int Hv, int *ntx)
+int dwarp_tiles(int Wv, int Hv, int tw, int *ntx)
 {
-    *ntx = (Wv + kDTW - 1) / kDTW;
+    *ntx = (Wv + tw - 1) / tw;
     return *ntx * ((Hv + kDTH - 1) / kDTH);
 }
 
@@ -709,7 +752,8 @@ cudaError_t launch_dwarp(bool backward, const DiffView *d_views, DiffPrep *d_pre
     if (n_tiles <= 0) return cudaSuccess;
     dwarp_prep_kernel<<<n_views, 64, 0, s>>>(d_views, d_prep);
     note_launch();
-    const size_t smem = sizeof(float) * (size_t)kDTH * (backward ? 5 * cw_max + 2 * bw_max : cw_max + bw_max);
+    const size_t smem =
+        sizeof(float) * (size_t)kDTH * (backward ? 5 * cw_max + 2 * kBcPad + 2 * bw_max : cw_max + bw_max);
     if (backward) {
         const cudaError_t e = ensure_dynamic_smem((const void *)dwarp_bwd_kernel, smem);
         if (e != cudaSuccess) return e;

@@ -41,10 +41,11 @@ cudaError_t launch_warp_nn(const DevView *d_views, int n_views, int n_tiles, int
 
 // orb.cu
 cudaError_t launch_mask_rows(const DevLevel *d_lv, int nv, int n_levels, int rows0, int32_t *row_lo, int32_t *row_hi,
-                             cudaStream_t s);
-cudaError_t launch_pyramid(const DevLevel *d_lv, int n, int n_tiles, cudaStream_t s, int grid = 0);
+                             int32_t *unit, cudaStream_t s);
+cudaError_t launch_pyramid(const DevLevel *d_lv, int n, int n_tiles, const int32_t *unit, cudaStream_t s, int grid = 0);
 cudaError_t launch_detect(const DevLevel *d_lv, int n, int n_tiles, int thr, Candidate *cand, int32_t *count,
-                          const int32_t *row_lo, const int32_t *row_hi, cudaStream_t s, int grid = 0);
+                          const int32_t *row_lo, const int32_t *row_hi, const int32_t *unit, cudaStream_t s,
+                          int grid = 0);
 size_t select_smem_bytes();
 cudaError_t launch_select(const DevLevel *d_lv, int n, const Candidate *cand, const int32_t *count, int n_features,
                           SlotKp *slots, int32_t *taken, int32_t *status, cudaStream_t s);
@@ -119,8 +120,9 @@ cudaError_t launch_match_tc(const uint8_t *qbase, const uint8_t *qexp, long long
 
 // dwarp.cu
 struct DiffView;
-void dwarp_strip_widths(int Wv, double t_max, int K, int *cw, int *bw);
-int dwarp_tiles(int Wv, int Hv, int *ntx);
+int dwarp_tile_width(bool backward);
+void dwarp_strip_widths(int tw, double t_max, int K, int *cw, int *bw);
+int dwarp_tiles(int Wv, int Hv, int tw, int *ntx);
 struct DiffPrep;
 cudaError_t launch_dwarp(bool backward, const DiffView *d_views, DiffPrep *d_prep, int n_views, int n_tiles,
                          int cw_max, int bw_max, int32_t *status, cudaStream_t s);

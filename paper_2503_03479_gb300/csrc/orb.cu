@@ -61,7 +61,8 @@ __device__ __forceinline__ void pyr_tap(int o, int nl, int np, float inv, int &q
     q1 = min(q0 + 1, np - 1);
 }
 
-__device__ __forceinline__ void pyramid_tile(int tile, const DevLevel *__restrict__ lv, int n)
+__device__ __forceinline__ void pyramid_tile(int tile, const DevLevel *__restrict__ lv, int n,
+                                             const int32_t *__restrict__ unit)
 {
     const int e = find_owner(lv, n, tile, [](const DevLevel &d) { return d.pyr_tile_start; });
     const DevLevel &L = lv[e];
@@ -83,6 +84,7 @@ __device__ __forceinline__ void pyramid_tile(int tile, const DevLevel *__restric
     const int nx = min(4, Wl - xb);   // this lane's columns inside the level (may be <= 0)
     const uint8_t *__restrict__ prev = L.prev;
     const uint8_t *__restrict__ prevm = L.prev_mask;
+    const bool planes = __ldg(unit + L.view) == 0;   // unit-convex views keep their masks as row hulls only
 #pragma unroll 1
     for (int r = 0; r < kPyrRowsW; ++r) {
         const int y = yb + r;
@@ -96,7 +98,7 @@ __device__ __forceinline__ void pyramid_tile(int tile, const DevLevel *__restric
         for (int c = 0; c < 4; ++c) {
             const unsigned a = __ldg(P0 + x0[c]), b = __ldg(P0 + x1[c]);
             const unsigned cc = __ldg(P1 + x0[c]), d = __ldg(P1 + x1[c]);
-            const unsigned m = __ldg(M0 + x0[c]) & __ldg(M0 + x1[c]) & __ldg(M1 + x0[c]) & __ldg(M1 + x1[c]);
+            const unsigned m = planes ? __ldg(M0 + x0[c]) & __ldg(M0 + x1[c]) & __ldg(M1 + x0[c]) & __ldg(M1 + x1[c]) : 0u;
             const unsigned f = (unsigned)fx[c], g = 2048u - f;
             const unsigned sum = gy * (g * a + f * b) + fy * (g * cc + f * d);
             wi |= ((sum + (1u << 21)) >> 22) << (8 * c);
@@ -105,13 +107,13 @@ __device__ __forceinline__ void pyramid_tile(int tile, const DevLevel *__restric
         uint8_t *oi = L.img_w + (size_t)y * Wl + xb, *om = L.mask_w + (size_t)y * Wl + xb;
         if (nx == 4 && ((((uintptr_t)oi) | ((uintptr_t)om)) & 3u) == 0u) {
             *reinterpret_cast<uint32_t *>(oi) = wi;
-            *reinterpret_cast<uint32_t *>(om) = wm;
+            if (planes) *reinterpret_cast<uint32_t *>(om) = wm;
         } else {
 #pragma unroll
             for (int c = 0; c < 4; ++c)
                 if (c < nx) {
                     oi[c] = (uint8_t)(wi >> (8 * c));
-                    om[c] = (uint8_t)(wm >> (8 * c));
+                    if (planes) om[c] = (uint8_t)(wm >> (8 * c));
                 }
         }
     }
@@ -119,27 +121,37 @@ __device__ __forceinline__ void pyramid_tile(int tile, const DevLevel *__restric
 
 // Grid-stride over the tiles: one CTA per tile, or a persistent grid.
 __global__ void __launch_bounds__(256, 4)
-pyramid_kernel(int n_tiles, const DevLevel *__restrict__ lv, int n)
+pyramid_kernel(int n_tiles, const DevLevel *__restrict__ lv, int n, const int32_t *__restrict__ unit)
 {
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) pyramid_tile(tile, lv, n);
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) pyramid_tile(tile, lv, n, unit);
 }
 
 // ---------------------------------------------------------------- mask row hulls
 // Level 0 of every view (the entries 0 .. n - 1): one warp per row finds the
 // first and last column whose mask is nonzero (lo > hi when none).  The row's
 // 16-byte aligned interior is read as uint4 (independent loads, so that a
-// row takes one or two memory latencies), its ragged ends byte by byte.
-__device__ __forceinline__ void hull_word(uint32_t w, int c, int &lo, int &hi)
+// row takes one or two memory latencies), its ragged ends byte by byte.  The
+// warp also counts the row's nonzero bytes and its bytes equal to 1: a view
+// whose every row has all its nonzero bytes equal to 1 and exactly on
+// [lo, hi] (the views' footprints do) is "unit-convex", unit[view] stays
+// nonzero, and then every level's mask is 1 exactly on its row hulls (the
+// pyramid's AND of four taps keeps rows 0/1 intervals), so the pyramid and the
+// detection can work from the hulls instead of the mask planes.
+__device__ __forceinline__ void hull_word(uint32_t w, int c, int &lo, int &hi, int &nz, int &n1)
 {
     if (w) {
         lo = min(lo, c + ((__ffs((int)w) - 1) >> 3));
         hi = max(hi, c + ((31 - __clz((int)w)) >> 3));
+        // bit 7 of each byte: the byte is nonzero / the byte is 1
+        nz += __popc((((w & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | w) & 0x80808080u);
+        const uint32_t t = w ^ 0x01010101u;
+        n1 += __popc(~((((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t)) & 0x80808080u);
     }
 }
 
 __global__ void __launch_bounds__(256)
 mask_rows_kernel(const DevLevel *__restrict__ lv, int n, int rows, int32_t *__restrict__ row_lo,
-                 int32_t *__restrict__ row_hi)
+                 int32_t *__restrict__ row_hi, int32_t *__restrict__ unit)
 {
     const int lane = threadIdx.x & 31;
     for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < rows; g += (gridDim.x * blockDim.x) >> 5) {
@@ -150,27 +162,35 @@ mask_rows_kernel(const DevLevel *__restrict__ lv, int n, int rows, int32_t *__re
         const int head = min(W, (int)((16 - ((uintptr_t)m & 15u)) & 15u));   // bytes before the first aligned chunk
         const int n16 = (W - head) >> 4;                                     // aligned 16-byte chunks
         const int tail0 = head + 16 * n16;                                   // first byte after them
-        int lo = kHullEmptyLo, hi = kHullEmptyHi;
-        if (lane < head && __ldg(m + lane)) { lo = lane; hi = lane; }      // the ragged ends, bytewise
-        for (int c = tail0 + lane; c < W; c += 32)
-            if (__ldg(m + c)) { lo = min(lo, c); hi = max(hi, c); }
+        int lo = kHullEmptyLo, hi = kHullEmptyHi, nz = 0, n1 = 0;
+        if (lane < head) {                                                    // the ragged ends, bytewise
+            const int v = __ldg(m + lane);
+            if (v) { lo = lane; hi = lane; ++nz; n1 += v == 1; }
+        }
+        for (int c = tail0 + lane; c < W; c += 32) {
+            const int v = __ldg(m + c);
+            if (v) { lo = min(lo, c); hi = max(hi, c); ++nz; n1 += v == 1; }
+        }
         const uint4 *__restrict__ m16 = reinterpret_cast<const uint4 *>(m + head);
         for (int k = lane; k < n16; k += 32) {
             const uint4 v = __ldg(m16 + k);
             const int c = head + 16 * k;
-            hull_word(v.x, c, lo, hi);
-            hull_word(v.y, c + 4, lo, hi);
-            hull_word(v.z, c + 8, lo, hi);
-            hull_word(v.w, c + 12, lo, hi);
+            hull_word(v.x, c, lo, hi, nz, n1);
+            hull_word(v.y, c + 4, lo, hi, nz, n1);
+            hull_word(v.z, c + 8, lo, hi, nz, n1);
+            hull_word(v.w, c + 12, lo, hi, nz, n1);
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
             lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
             hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            nz += __shfl_xor_sync(0xffffffffu, nz, o);
+            n1 += __shfl_xor_sync(0xffffffffu, n1, o);
         }
         if (lane == 0) {
             row_lo[g] = lo;
             row_hi[g] = hi;
+            if (nz != n1 || (nz != 0 && nz != hi - lo + 1)) atomicAnd(unit + L.view, 0);
         }
     }
 }
@@ -318,7 +338,7 @@ __device__ __forceinline__ bool fast9_ring(const uint8_t *p, int thr)
 template <int P>
 __device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__restrict__ lv, int thr, Candidate *__restrict__ cand,
               int32_t *__restrict__ cand_count, const int32_t *__restrict__ row_lo,
-              const int32_t *__restrict__ row_hi, DetSmem &sm)
+              const int32_t *__restrict__ row_hi, const int32_t *__restrict__ unit, DetSmem &sm)
 {
     auto &isc = sm.isc;
     constexpr int kIscWords = (kRW + 31) / 32;
@@ -423,6 +443,7 @@ __device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__r
     }
     __syncthreads();
     const int nca = sm.ncand;
+    const bool unit_view = __ldg(unit + L.view) != 0;
 #pragma unroll 1
     for (int q0 = (int)(threadIdx.x & ~31u); q0 < nca; q0 += kThreads) {
         const int q = q0 + (int)lane_id;
@@ -433,11 +454,15 @@ __device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__r
             r = el / kRW;
             c = el - r * kRW;
             if (fast9_ring<P>(&S[(r - 1 + kHalo) * P + c - 1 + kHalo], thr)) {
-                const int x = x0 - 1 + c, y = y0 - 1 + r;
-                const uint8_t *M = L.mask;
-                const int b = kBorder;
-                flag = M[(y - b) * W + x - b] & M[(y - b) * W + x + b] & M[(y + b) * W + x - b] &
-                       M[(y + b) * W + x + b];
+                if (unit_view) {
+                    flag = 1;   // the row hulls are the mask: eligible = the box's corners mask-valid
+                } else {
+                    const int x = x0 - 1 + c, y = y0 - 1 + r;
+                    const uint8_t *M = L.mask;
+                    const int b = kBorder;
+                    flag = M[(y - b) * W + x - b] & M[(y - b) * W + x + b] & M[(y + b) * W + x - b] &
+                           M[(y + b) * W + x + b];
+                }
             }
             if (flag) atomicOr(&isc[r][c >> 5], 1u << (c & 31));
         }
@@ -552,21 +577,23 @@ __device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__r
     }
 }
 
-// Grid-stride over the tiles: one CTA per tile, or a persistent grid.  Five
-// CTAs per SM, what the 39.6 KB of shared memory allows.
-__global__ void __launch_bounds__(kDetCols * kDetRowsPar, 5)
+// Grid-stride over the tiles: one CTA per tile, or a persistent grid.  Seven
+// CTAs per SM, what the 31 KB of shared memory allows (a tile's life is
+// mostly the latency of its loads and barriers, so residency pays).
+__global__ void __launch_bounds__(kDetCols * kDetRowsPar, 7)
 detect_kernel(int n_tiles, const DevLevel *__restrict__ lv, int n, int thr, Candidate *__restrict__ cand,
-              int32_t *__restrict__ cand_count, const int32_t *__restrict__ row_lo, const int32_t *__restrict__ row_hi)
+              int32_t *__restrict__ cand_count, const int32_t *__restrict__ row_lo, const int32_t *__restrict__ row_hi,
+              const int32_t *__restrict__ unit)
 {
     __shared__ DetSmem sm;
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int e = find_owner(lv, n, tile, [](const DevLevel &d) { return d.det_tile_start; });
         static_assert(kSPMin % 4 == 0, "pitch kSPMin + i is = i mod 4");
         switch (lv[e].W & 3) {   // P = W mod 4
-        case 0: detect_tile<kSPMin>(tile, e, lv, thr, cand, cand_count, row_lo, row_hi, sm); break;
-        case 1: detect_tile<kSPMin + 1>(tile, e, lv, thr, cand, cand_count, row_lo, row_hi, sm); break;
-        case 2: detect_tile<kSPMin + 2>(tile, e, lv, thr, cand, cand_count, row_lo, row_hi, sm); break;
-        default: detect_tile<kSPMin + 3>(tile, e, lv, thr, cand, cand_count, row_lo, row_hi, sm); break;
+        case 0: detect_tile<kSPMin>(tile, e, lv, thr, cand, cand_count, row_lo, row_hi, unit, sm); break;
+        case 1: detect_tile<kSPMin + 1>(tile, e, lv, thr, cand, cand_count, row_lo, row_hi, unit, sm); break;
+        case 2: detect_tile<kSPMin + 2>(tile, e, lv, thr, cand, cand_count, row_lo, row_hi, unit, sm); break;
+        default: detect_tile<kSPMin + 3>(tile, e, lv, thr, cand, cand_count, row_lo, row_hi, unit, sm); break;
         }
         __syncthreads();
     }
@@ -905,21 +932,23 @@ orient_brief_kernel(const DevLevel *__restrict__ lv, int n_views, int n_levels, 
 }
 
 // ---------------------------------------------------------------- host side
-cudaError_t launch_pyramid(const DevLevel *d_lv, int n, int n_tiles, cudaStream_t s, int grid)
+cudaError_t launch_pyramid(const DevLevel *d_lv, int n, int n_tiles, const int32_t *unit, cudaStream_t s, int grid)
 {
     if (n_tiles <= 0) return cudaSuccess;
     const int g = (grid > 0 && grid < n_tiles) ? grid : n_tiles;
-    pyramid_kernel<<<g, 256, 0, s>>>(n_tiles, d_lv, n);
+    pyramid_kernel<<<g, 256, 0, s>>>(n_tiles, d_lv, n, unit);
     note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_mask_rows(const DevLevel *d_lv, int nv, int n_levels, int rows0, int32_t *row_lo, int32_t *row_hi,
-                             cudaStream_t s)
+                             int32_t *unit, cudaStream_t s)
 {
     if (rows0 <= 0 || nv <= 0) return cudaSuccess;
+    cudaError_t e0 = cudaMemsetAsync(unit, 0xFF, sizeof(int32_t) * (size_t)nv, s);   // every view unit-convex until a row says not
+    if (e0 != cudaSuccess) return e0;
     const int blocks = std::max(1, std::min((rows0 + 7) / 8, 65535));   // a warp per row
-    mask_rows_kernel<<<blocks, 256, 0, s>>>(d_lv, nv, rows0, row_lo, row_hi);
+    mask_rows_kernel<<<blocks, 256, 0, s>>>(d_lv, nv, rows0, row_lo, row_hi, unit);
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || n_levels < 2) return e;
@@ -929,11 +958,11 @@ cudaError_t launch_mask_rows(const DevLevel *d_lv, int nv, int n_levels, int row
 }
 
 cudaError_t launch_detect(const DevLevel *d_lv, int n, int n_tiles, int thr, Candidate *cand, int32_t *count,
-                          const int32_t *row_lo, const int32_t *row_hi, cudaStream_t s, int grid)
+                          const int32_t *row_lo, const int32_t *row_hi, const int32_t *unit, cudaStream_t s, int grid)
 {
     if (n_tiles <= 0) return cudaSuccess;
     const int g = (grid > 0 && grid < n_tiles) ? grid : n_tiles;
-    detect_kernel<<<g, kDetCols * kDetRowsPar, 0, s>>>(n_tiles, d_lv, n, thr, cand, count, row_lo, row_hi);
+    detect_kernel<<<g, kDetCols * kDetRowsPar, 0, s>>>(n_tiles, d_lv, n, thr, cand, count, row_lo, row_hi, unit);
     note_launch();
     return cudaGetLastError();
 }

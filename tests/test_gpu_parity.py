@@ -141,6 +141,30 @@ def test_orb_parity_small_pair(A):
         assert len(kp) > 2000
 
 
+def test_orb_parity_general_masks(A):
+    """Masks that are not the views' own: a footprint with holes (rows not
+    intervals), one scaled to 255, one with mixed nonzero values, beside
+    untouched footprints.  Views whose masks are 0/1 intervals per row take
+    the row-hull path; the others the mask planes; all bit-exact."""
+    ctx = A.Context(n_levels=5, n_features=400)
+    img = synth.texture(300, 360, 17)
+    vo = _views_gpu(A, ctx, img, A.view_table(300, 360, 3), with_f32=False)
+    rng = np.random.default_rng(5)
+    for i in range(len(vo.views)):
+        m = vo.view(i, "mask")
+        H, W = m.shape
+        if i % 4 == 1:      # holes: several rows split into two or more runs
+            for _ in range(6):
+                y, x = int(rng.integers(0, H - 20)), int(rng.integers(0, W - 20))
+                m[y:y + 20, x:x + int(rng.integers(3, 20))] = 0
+        elif i % 4 == 2:    # a footprint of 255s
+            m.mul_(255)
+        elif i % 4 == 3:    # nonzero values 1 and 3 mixed
+            sel = torch.from_numpy(rng.random((H, W)) < 0.3).to(m.device)
+            m[sel & (m > 0)] = 3
+    _check_orb(A, ctx, vo, 5, 400)
+
+
 def test_orb_parity_ragged_many_levels(A):
     ctx = A.Context(n_levels=6, n_features=300)
     img = synth.texture(211, 263, 91)
