@@ -91,18 +91,24 @@ __device__ __forceinline__ void pyramid_tile(int tile, const DevLevel *__restric
         const int y0 = __shfl_sync(0xffffffffu, ry0, r), y1 = __shfl_sync(0xffffffffu, ry1, r);
         const unsigned fy = (unsigned)__shfl_sync(0xffffffffu, rfy, r), gy = 2048u - fy;
         if (y >= Hl) break;   // warp-uniform
+        if (nx <= 0) continue;
         const uint8_t *P0 = prev + (size_t)y0 * Wp, *P1 = prev + (size_t)y1 * Wp;
-        const uint8_t *M0 = prevm + (size_t)y0 * Wp, *M1 = prevm + (size_t)y1 * Wp;
         uint32_t wi = 0, wm = 0;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const unsigned a = __ldg(P0 + x0[c]), b = __ldg(P0 + x1[c]);
             const unsigned cc = __ldg(P1 + x0[c]), d = __ldg(P1 + x1[c]);
-            const unsigned m = planes ? __ldg(M0 + x0[c]) & __ldg(M0 + x1[c]) & __ldg(M1 + x0[c]) & __ldg(M1 + x1[c]) : 0u;
             const unsigned f = (unsigned)fx[c], g = 2048u - f;
             const unsigned sum = gy * (g * a + f * b) + fy * (g * cc + f * d);
             wi |= ((sum + (1u << 21)) >> 22) << (8 * c);
-            wm |= m << (8 * c);
+        }
+        if (planes) {
+            const uint8_t *M0 = prevm + (size_t)y0 * Wp, *M1 = prevm + (size_t)y1 * Wp;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const unsigned m = __ldg(M0 + x0[c]) & __ldg(M0 + x1[c]) & __ldg(M1 + x0[c]) & __ldg(M1 + x1[c]);
+                wm |= m << (8 * c);
+            }
         }
         uint8_t *oi = L.img_w + (size_t)y * Wl + xb, *om = L.mask_w + (size_t)y * Wl + xb;
         if (nx == 4 && ((((uintptr_t)oi) | ((uintptr_t)om)) & 3u) == 0u) {
@@ -197,12 +203,22 @@ mask_rows_kernel(const DevLevel *__restrict__ lv, int n, int rows, int32_t *__re
 
 // Levels >= 1 of view blockIdx.x, in order: a level-l pixel's mask is the AND
 // of the previous level's at the pyramid's four taps (columns x0(x), x1(x),
-// rows y0(y), y1(y)), so it can be 1 only if x0 >= max(lo(y0), lo(y1)) and
-// x1 <= min(hi(y0), hi(y1)); x0 and x1 grow with x, so those x form an
-// interval, found by two binary searches over the pyramid's own integer tap
-// formulas.  It holds every valid column (exactly them when the previous
-// level's rows are intervals, as the views' masks are).
+// rows y0(y), y1(y)), so it can be 1 only if x0 >= max(lo(y0), lo(y1)) = A
+// and x1 <= min(hi(y0), hi(y1)) = B; x0 and x1 grow with x, so those x form
+// an interval.  With x0(x) = floor(((2x + 1) Wp - Wl) / (2 Wl)) (the numerator
+// is >= 0), x0(x) >= A  <=>  x >= ceil((2 Wl A + Wl - Wp) / (2 Wp)), and
+// x1(x) = min(x0(x) + 1, Wp - 1) > B  <=>  x0(x) >= B when B < Wp - 1 (never
+// otherwise), so both ends are one integer division each.  The interval holds
+// every valid column (exactly them when the previous level's rows are
+// intervals, as the views' masks are).
 __device__ __forceinline__ int pyr_tap0(int o, int nl, int np) { return ((2 * o + 1) * np - nl) / (2 * nl); }
+
+// First x >= 0 with x0(x) >= A (A >= 0), not clamped above.
+__device__ __forceinline__ int first_x_at(long long A, int Wl, int Wp)
+{
+    const long long n = 2LL * Wl * A + Wl - Wp, d = 2LL * Wp;
+    return n <= 0 ? 0 : (int)((n + d - 1) / d);
+}
 
 __global__ void __launch_bounds__(256)
 hull_levels_kernel(const DevLevel *__restrict__ lv, int nv, int n_levels, int32_t *__restrict__ row_lo,
@@ -216,19 +232,11 @@ hull_levels_kernel(const DevLevel *__restrict__ lv, int nv, int n_levels, int32_
             const int y0 = pyr_tap0(y, Hl, Hp), y1 = min(y0 + 1, Hp - 1);
             const int A = max(row_lo[Q.row_off + y0], row_lo[Q.row_off + y1]);
             const int B = min(row_hi[Q.row_off + y0], row_hi[Q.row_off + y1]);
-            int lo = 0, hi = Wl;                      // first x with x0(x) >= A
-            while (lo < hi) {
-                const int m = (lo + hi) >> 1;
-                if (pyr_tap0(m, Wl, Wp) >= A) hi = m; else lo = m + 1;
+            int a = 1, b = 0;
+            if (A <= B) {   // else a parent row is empty: so is this one
+                a = min(first_x_at(A, Wl, Wp), Wl);
+                b = B >= Wp - 1 ? Wl - 1 : min(first_x_at(B, Wl, Wp), Wl) - 1;
             }
-            const int a = lo;
-            lo = 0;
-            hi = Wl;                                  // first x with x1(x) > B
-            while (lo < hi) {
-                const int m = (lo + hi) >> 1;
-                if (min(pyr_tap0(m, Wl, Wp) + 1, Wp - 1) > B) hi = m; else lo = m + 1;
-            }
-            const int b = lo - 1;
             row_lo[L.row_off + y] = a <= b ? a : kHullEmptyLo;
             row_hi[L.row_off + y] = a <= b ? b : kHullEmptyHi;
         }
