@@ -376,6 +376,7 @@ typedef struct {
 
 /* Launch shapes of the batched stages (0 = one CTA per tile / the default).
  * A positive grid makes the stage's kernel persistent over its tile list.
+ * The detection runs over the list of tiles that can hold corners.
  * warp_seg is the tile shape of the view simulation: the canvas columns a
  * tile rotates once and filters for every view sharing that rotation
  * (0 = the default 384; 64 .. 1024; wider tiles recompute less of the

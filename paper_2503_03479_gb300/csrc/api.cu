@@ -625,6 +625,8 @@ struct OrbBuffers {
     int32_t *group_total;
     int32_t *row_lo, *row_hi;    // mask row hulls of every level (row_off of each entry)
     int32_t *unit;               // per view: nonzero when its masks are exactly their row hulls
+    DetItem *det_list;           // the detection tiles worth processing, and their count
+    int32_t *det_count;
 };
 
 // Workspace region of the ORB stages for nv views in n_groups groups.
@@ -644,6 +646,8 @@ static void orb_layout(Bump &b, const LevelTables &T, int nv, int n_groups, cons
     o.row_lo = b.take<int32_t>(std::max<long long>(T.rows_total, 1));
     o.row_hi = b.take<int32_t>(std::max<long long>(T.rows_total, 1));
     o.unit = b.take<int32_t>(std::max(nv, 1));
+    o.det_list = b.take<DetItem>(std::max<long long>(T.det_tiles, 1));
+    o.det_count = b.take<int32_t>(1);
 }
 
 // Runs pyramid -> detect -> select -> pool scan -> orientation + BRIEF.
@@ -667,7 +671,7 @@ static cudaError_t run_orb(asift_ctx *ctx, const LevelTables &T, int nv, int n_g
         prof_mark(ctx, 3, s);
         if (e == cudaSuccess)
             e = launch_detect(o.lv, (int)nl, T.det_tiles, cfg.fast_threshold, o.cand, o.cand_count, o.row_lo, o.row_hi,
-                              o.unit, s, det_grid);
+                              o.unit, o.det_list, o.det_count, s, det_grid);
         prof_mark(ctx, 4, s);
         if (e == cudaSuccess)
             e = launch_select(o.lv, (int)nl, o.cand, o.cand_count, N, o.slots, o.taken, o.status, s);
@@ -683,7 +687,7 @@ static cudaError_t run_orb(asift_ctx *ctx, const LevelTables &T, int nv, int n_g
             for (int l = 0; l < L && e == cudaSuccess; ++l) {
                 const size_t i = (size_t)l * nv + v;
                 e = launch_detect(o.lv + i, 1, det_tiles_of(T.lv[i]), cfg.fast_threshold, o.cand, o.cand_count + i,
-                                  o.row_lo, o.row_hi, o.unit, s);
+                                  o.row_lo, o.row_hi, o.unit, o.det_list, o.det_count, s);
             }
             for (int l = 0; l < L && e == cudaSuccess; ++l) {
                 const size_t i = (size_t)l * nv + v;

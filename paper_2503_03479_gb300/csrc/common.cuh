@@ -121,6 +121,11 @@ struct DiffView {
     int32_t W, H, Wr, Hr, Wv, Hv, K, tile_start, ntx, tw;   // tw: view columns per tile
 };
 
+// A tile of the ORB detection: its level entry and its index in the launch.
+struct DetItem {
+    int32_t e, tile;
+};
+
 // Per-view constants of the differentiable warp, made once per call on the
 // device from the (device-resident) parameters.
 struct DiffPrep {

@@ -40,12 +40,13 @@ cudaError_t launch_warp_nn(const DevView *d_views, int n_views, int n_tiles, int
                            float *f32, cudaStream_t s, int grid = 0);
 
 // orb.cu
+struct DetItem;
 cudaError_t launch_mask_rows(const DevLevel *d_lv, int nv, int n_levels, int rows0, int32_t *row_lo, int32_t *row_hi,
                              int32_t *unit, cudaStream_t s);
 cudaError_t launch_pyramid(const DevLevel *d_lv, int n, int n_tiles, const int32_t *unit, cudaStream_t s, int grid = 0);
 cudaError_t launch_detect(const DevLevel *d_lv, int n, int n_tiles, int thr, Candidate *cand, int32_t *count,
-                          const int32_t *row_lo, const int32_t *row_hi, const int32_t *unit, cudaStream_t s,
-                          int grid = 0);
+                          const int32_t *row_lo, const int32_t *row_hi, const int32_t *unit, DetItem *list,
+                          int32_t *list_count, cudaStream_t s, int grid = 0);
 size_t select_smem_bytes();
 cudaError_t launch_select(const DevLevel *d_lv, int n, const Candidate *cand, const int32_t *count, int n_features,
                           SlotKp *slots, int32_t *taken, int32_t *status, cudaStream_t s);

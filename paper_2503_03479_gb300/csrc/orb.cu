@@ -290,15 +290,58 @@ constexpr int kDetRowsPar = 4;
 // compile-time constants.
 constexpr int kSPMin = kSW + 6, kSPMax = kSPMin + 3;
 
+constexpr int kStageBytes = (kSH * kSPMax + 15) & ~15;
 struct DetSmem {
     long long R[kRH][kRW];
     int16_t surv[kRH * kRW];     // compass survivors
     int16_t clist[kRH * kRW];
-    __align__(16) uint8_t img[kSH * kSPMax];
+    __align__(16) uint8_t img[kStageBytes];   // the tile's stage
     uint32_t isc[kRH][(kRW + 31) / 32];   // corner flags of the tile + ring, one bit per column
     int16_t ea[kRH], eb[kRH];   // per tile + ring row: columns c whose FAST corners can be mask-valid
     int ncl, ncand;
 };
+
+// The tile's geometry and stage layout, shared by its preparation and its
+// processing.
+struct DetGeom {
+    int x0, y0, W, H, s0;
+    bool interior, wide;
+    const uint8_t *g0;
+};
+
+__device__ __forceinline__ DetGeom det_geom(const DevLevel &L, int tile)
+{
+    DetGeom G;
+    const int lt = tile - L.det_tile_start;
+    const int ty = lt / L.det_ntx, tx = lt - ty * L.det_ntx;
+    G.W = L.W;
+    G.H = L.H;
+    G.x0 = tx * kDetTW;
+    G.y0 = ty * kDetTH;
+    G.interior = G.x0 - kHalo >= 0 && G.y0 - kHalo >= 0 && G.x0 + kDetTW + kHalo <= G.W && G.y0 + kDetTH + kHalo <= G.H;
+    G.wide = G.interior && G.x0 - kHalo >= 3 && G.x0 + kDetTW + kHalo + 3 <= G.W;
+    G.g0 = G.interior ? L.img + (size_t)(G.y0 - kHalo) * G.W + (G.x0 - kHalo) : L.img;
+    G.s0 = G.interior ? (int)((uintptr_t)G.g0 & 3u) : 0;
+    return G;
+}
+
+// Columns c of ring row r (y = y0 - 1 + r, x = x0 - 1 + c) where FAST corners
+// can be mask-valid: inside the 16 px border, with x - 16 and x + 16 inside
+// the row hulls of y - 16 and y + 16 (a > b when none).
+__device__ __forceinline__ void det_row_cols(const DevLevel &L, int x0, int y0, int r, const int32_t *__restrict__ row_lo,
+                                             const int32_t *__restrict__ row_hi, int &a, int &b)
+{
+    const int y = y0 - 1 + r, W = L.W, H = L.H;
+    a = 1;
+    b = 0;
+    if (y >= kBorder && y < H - kBorder) {
+        const int lo = max(__ldg(row_lo + L.row_off + y - kBorder), __ldg(row_lo + L.row_off + y + kBorder));
+        const int hi = min(__ldg(row_hi + L.row_off + y - kBorder), __ldg(row_hi + L.row_off + y + kBorder));
+        const int xa = max(kBorder, lo + kBorder), xb = min(W - kBorder - 1, hi - kBorder);
+        a = max(xa - (x0 - 1), 0);
+        b = min(xb - (x0 - 1), kRW - 1);
+    }
+}
 
 // 1 iff 9 cyclically consecutive bits of the 16-bit mask m are set.
 __device__ __forceinline__ bool has_run9(unsigned m)
@@ -343,69 +386,32 @@ __device__ __forceinline__ bool fast9_ring(const uint8_t *p, int thr)
     return has_run9(bm) || has_run9(dm);
 }
 
-template <int P>
-__device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__restrict__ lv, int thr, Candidate *__restrict__ cand,
-              int32_t *__restrict__ cand_count, const int32_t *__restrict__ row_lo,
-              const int32_t *__restrict__ row_hi, const int32_t *__restrict__ unit, DetSmem &sm)
+// Preparation of a listed tile: its columns per ring row, and its stage:
+// staged pixel (r, c) = image (x0 - kHalo + c, y0 - kHalo + r), clamped, at
+// S[r * P + c].  Interior tiles with 3 spare columns of the level on either
+// side copy each row's whole containing words asynchronously (every word
+// inside the level row; one commit group); other interior tiles copy words
+// with byte-exact edges; the rest copy bytes with clamping.
+__device__ __forceinline__ void det_prepare(const DetItem it, const DevLevel *__restrict__ lv,
+                                            const int32_t *__restrict__ row_lo, const int32_t *__restrict__ row_hi,
+                                            DetSmem &sm)
 {
-    auto &isc = sm.isc;
-    constexpr int kIscWords = (kRW + 31) / 32;
-    auto &R = sm.R;
-    int16_t *clist = sm.clist;
-    int &ncl = sm.ncl;
-
-    const DevLevel &L = lv[e];
-    const int lt = tile - L.det_tile_start;
-    const int ty = lt / L.det_ntx, tx = lt - ty * L.det_ntx;
-    const int W = L.W, H = L.H;
-    const int x0 = tx * kDetTW, y0 = ty * kDetTH;
-    // tiles that hold no pixel of the border-limited region, nor a ring pixel of one
-    if (x0 + kDetTW + 1 <= kBorder || y0 + kDetTH + 1 <= kBorder || x0 - 1 >= W - kBorder || y0 - 1 >= H - kBorder)
-        return;
     constexpr int kThreads = kDetCols * kDetRowsPar;
-
-    // FAST can fire at (x, y) only inside the 16 px border and where the 33 x
-    // 33 box's corners can be mask-valid: x - 16 and x + 16 inside the row
-    // hulls of y - 16 and y + 16.  Per tile + ring row r (y = y0 - 1 + r) the
-    // columns c (x = x0 - 1 + c) that remain; a tile with none is done.
-    bool any = false;
+    const DevLevel &L = lv[it.e];
+    const DetGeom G = det_geom(L, it.tile);
+    const int P = kSPMin + (G.W & 3);
     if (threadIdx.x < kRH) {
-        const int r = (int)threadIdx.x, y = y0 - 1 + r;
-        int a = 1, b = 0;
-        if (y >= kBorder && y < H - kBorder) {
-            const int lo = max(__ldg(row_lo + L.row_off + y - kBorder), __ldg(row_lo + L.row_off + y + kBorder));
-            const int hi = min(__ldg(row_hi + L.row_off + y - kBorder), __ldg(row_hi + L.row_off + y + kBorder));
-            const int xa = max(kBorder, lo + kBorder), xb = min(W - kBorder - 1, hi - kBorder);
-            a = max(xa - (x0 - 1), 0);
-            b = min(xb - (x0 - 1), kRW - 1);
-        }
-        any = a <= b;
-        sm.ea[r] = (int16_t)(any ? a : 1);
-        sm.eb[r] = (int16_t)(any ? b : 0);
+        int a, b;
+        det_row_cols(L, G.x0, G.y0, (int)threadIdx.x, row_lo, row_hi, a, b);
+        sm.ea[threadIdx.x] = (int16_t)(a <= b ? a : 1);
+        sm.eb[threadIdx.x] = (int16_t)(a <= b ? b : 0);
     }
-    if (!__syncthreads_or(any)) return;
-
-    if (threadIdx.x == 0) {
-        ncl = 0;
-        sm.ncand = 0;
-    }
-    if (threadIdx.x < kRH * kIscWords) (&isc[0][0])[threadIdx.x] = 0u;
-    // staged pixel (r, c) = image (x0 - kHalo + c, y0 - kHalo + r), clamped,
-    // at S[r * P + c].  Interior tiles with 3 spare columns of the level on
-    // either side copy each row's whole containing words asynchronously
-    // (every word inside the level row); other interior tiles copy words
-    // with byte-exact edges; the rest copy bytes with clamping.
-    const uint8_t *__restrict__ I = L.img;
-    const bool interior = x0 - kHalo >= 0 && y0 - kHalo >= 0 && x0 + kDetTW + kHalo <= W && y0 + kDetTH + kHalo <= H;
-    const bool wide = interior && x0 - kHalo >= 3 && x0 + kDetTW + kHalo + 3 <= W;
-    const uint8_t *g0 = interior ? I + (size_t)(y0 - kHalo) * W + (x0 - kHalo) : I;
-    const int s0 = interior ? (int)((uintptr_t)g0 & 3u) : 0;
-    uint8_t *S = sm.img + s0;
-    if (wide) {
+    uint8_t *S = sm.img + G.s0;
+    if (G.wide) {
         constexpr int kNW = (kSW + 6) / 4;   // words of a row copy
         for (int el = threadIdx.x; el < kSH * kNW; el += kThreads) {
             const int r = el / kNW, k = el - r * kNW;
-            const uint8_t *g = g0 + (size_t)r * W;
+            const uint8_t *g = G.g0 + (size_t)r * G.W;
             const int mis = (int)((uintptr_t)g & 3u);
             if (4 * k < mis + kSW)
                 asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
@@ -413,20 +419,41 @@ __device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__r
                              "l"(g - mis + 4 * k)
                              : "memory");
         }
-        asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
-    } else if (interior) {
+    } else if (G.interior) {
         constexpr int kNW = (kSW + 6) / 4;   // words of a row copy
         for (int el = threadIdx.x; el < kSH * kNW; el += kThreads) {
             const int r = el / kNW, k = el - r * kNW;
-            store_word(S + r * P, kSW, k, load_word(g0 + (size_t)r * W, kSW, k));
+            store_word(S + r * P, kSW, k, load_word(G.g0 + (size_t)r * G.W, kSW, k));
         }
     } else {
+        const uint8_t *__restrict__ I = L.img;
+        const int W = G.W, H = G.H;
         for (int el = threadIdx.x; el < kSH * kSW; el += kThreads) {
             const int r = el / kSW, c = el - r * kSW;
-            S[r * P + c] = I[clampi(y0 - kHalo + r, 0, H - 1) * W + clampi(x0 - kHalo + c, 0, W - 1)];
+            S[r * P + c] = I[clampi(G.y0 - kHalo + r, 0, H - 1) * W + clampi(G.x0 - kHalo + c, 0, W - 1)];
         }
     }
-    __syncthreads();
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// A prepared tile (its stage and row columns visible, counters zeroed):
+// FAST, Harris, NMS and the candidates.
+template <int P>
+__device__ __forceinline__ void det_process(const DetItem it, const DevLevel *__restrict__ lv, int thr,
+                                            Candidate *__restrict__ cand, int32_t *__restrict__ cand_count,
+                                            const int32_t *__restrict__ unit, DetSmem &sm)
+{
+    auto &isc = sm.isc;
+    auto &R = sm.R;
+    int16_t *clist = sm.clist;
+    int &ncl = sm.ncl;
+    const int e = it.e;
+    const DevLevel &L = lv[e];
+    const DetGeom G = det_geom(L, it.tile);
+    const int x0 = G.x0, y0 = G.y0, W = G.W;
+    const int16_t *ea = sm.ea, *eb = sm.eb;
+    const uint8_t *S = sm.img + G.s0;
+    constexpr int kThreads = kDetCols * kDetRowsPar;
 
     // corner flags on the tile + ring in two passes, so that the full ring test
     // runs with every lane busy: (a) border and compass test for every pixel,
@@ -439,7 +466,7 @@ __device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__r
     for (int k = 0; k < (kRH * kRW + kThreads - 1) / kThreads; ++k) {
         const int el = (int)threadIdx.x + k * kThreads;
         const int r = el / kRW, c = el - r * kRW;
-        const bool pass = el < kRH * kRW && c >= sm.ea[r] && c <= sm.eb[r] &&
+        const bool pass = el < kRH * kRW && c >= ea[r] && c <= eb[r] &&
                           fast9_compass<P>(&S[(r - 1 + kHalo) * P + c - 1 + kHalo], thr);
         const unsigned bal = __ballot_sync(0xffffffffu, pass);
         if (bal) {
@@ -585,26 +612,71 @@ __device__ __forceinline__ void detect_tile(int tile, int e, const DevLevel *__r
     }
 }
 
-// Grid-stride over the tiles: one CTA per tile, or a persistent grid.  Seven
-// CTAs per SM, what the 31 KB of shared memory allows (a tile's life is
-// mostly the latency of its loads and barriers, so residency pays).
+// The tiles worth detecting on: one block per level entry, a thread per
+// tile.  A tile is listed when one of its ring rows has columns where FAST
+// corners can be mask-valid (det_row_cols); the others hold no candidate.
+__global__ void __launch_bounds__(256)
+det_list_kernel(const DevLevel *__restrict__ lv, const int32_t *__restrict__ row_lo, const int32_t *__restrict__ row_hi,
+                DetItem *__restrict__ list, int32_t *__restrict__ count)
+{
+    const int e = blockIdx.x;
+    const DevLevel &L = lv[e];
+    const int nt = L.det_ntx * ((L.H + kDetTH - 1) / kDetTH);
+    const unsigned lane = threadIdx.x & 31u;
+    for (int b0 = 0; b0 < nt; b0 += blockDim.x) {
+        const int lt = b0 + (int)threadIdx.x;
+        bool any = false;
+        if (lt < nt) {
+            const int ty = lt / L.det_ntx, tx = lt - ty * L.det_ntx;
+            const int x0 = tx * kDetTW, y0 = ty * kDetTH;
+            for (int r = 0; r < kRH && !any; ++r) {
+                int a, b;
+                det_row_cols(L, x0, y0, r, row_lo, row_hi, a, b);
+                any = a <= b;
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, any);
+        if (bal) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(count, __popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (any) list[base + __popc(bal & ((1u << lane) - 1u))] = DetItem{e, L.det_tile_start + lt};
+        }
+    }
+}
+
+// One CTA per listed tile (a positive grid makes it persistent over the list;
+// the launch is sized to every tile of the call, and the CTAs past the list's
+// count leave at once).  Seven CTAs per SM, what the 31 KB of shared memory
+// allows.  Staging the next tile while processing one, in a persistent grid,
+// was slower: tiles differ widely in work, and a fixed stride or a claimed
+// counter balances them worse than the hardware's block scheduler.
 __global__ void __launch_bounds__(kDetCols * kDetRowsPar, 7)
-detect_kernel(int n_tiles, const DevLevel *__restrict__ lv, int n, int thr, Candidate *__restrict__ cand,
-              int32_t *__restrict__ cand_count, const int32_t *__restrict__ row_lo, const int32_t *__restrict__ row_hi,
-              const int32_t *__restrict__ unit)
+detect_kernel(const DevLevel *__restrict__ lv, const DetItem *__restrict__ list, const int32_t *__restrict__ count,
+              int thr, Candidate *__restrict__ cand, int32_t *__restrict__ cand_count,
+              const int32_t *__restrict__ row_lo, const int32_t *__restrict__ row_hi, const int32_t *__restrict__ unit)
 {
     __shared__ DetSmem sm;
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int e = find_owner(lv, n, tile, [](const DevLevel &d) { return d.det_tile_start; });
-        static_assert(kSPMin % 4 == 0, "pitch kSPMin + i is = i mod 4");
-        switch (lv[e].W & 3) {   // P = W mod 4
-        case 0: detect_tile<kSPMin>(tile, e, lv, thr, cand, cand_count, row_lo, row_hi, unit, sm); break;
-        case 1: detect_tile<kSPMin + 1>(tile, e, lv, thr, cand, cand_count, row_lo, row_hi, unit, sm); break;
-        case 2: detect_tile<kSPMin + 2>(tile, e, lv, thr, cand, cand_count, row_lo, row_hi, unit, sm); break;
-        default: detect_tile<kSPMin + 3>(tile, e, lv, thr, cand, cand_count, row_lo, row_hi, unit, sm); break;
+    const int n = __ldg(count);
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        const DetItem cur = list[k];
+        det_prepare(cur, lv, row_lo, row_hi, sm);
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        if (threadIdx.x == 0) {
+            sm.ncl = 0;
+            sm.ncand = 0;
+        }
+        if (threadIdx.x < kRH * ((kRW + 31) / 32)) (&sm.isc[0][0])[threadIdx.x] = 0u;
+        __syncthreads();
+        switch (lv[cur.e].W & 3) {
+        case 0: det_process<kSPMin>(cur, lv, thr, cand, cand_count, unit, sm); break;
+        case 1: det_process<kSPMin + 1>(cur, lv, thr, cand, cand_count, unit, sm); break;
+        case 2: det_process<kSPMin + 2>(cur, lv, thr, cand, cand_count, unit, sm); break;
+        default: det_process<kSPMin + 3>(cur, lv, thr, cand, cand_count, unit, sm); break;
         }
         __syncthreads();
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 // ---------------------------------------------------------------- selection
@@ -966,11 +1038,18 @@ cudaError_t launch_mask_rows(const DevLevel *d_lv, int nv, int n_levels, int row
 }
 
 cudaError_t launch_detect(const DevLevel *d_lv, int n, int n_tiles, int thr, Candidate *cand, int32_t *count,
-                          const int32_t *row_lo, const int32_t *row_hi, const int32_t *unit, cudaStream_t s, int grid)
+                          const int32_t *row_lo, const int32_t *row_hi, const int32_t *unit, DetItem *list,
+                          int32_t *list_count, cudaStream_t s, int grid)
 {
-    if (n_tiles <= 0) return cudaSuccess;
-    const int g = (grid > 0 && grid < n_tiles) ? grid : n_tiles;
-    detect_kernel<<<g, kDetCols * kDetRowsPar, 0, s>>>(n_tiles, d_lv, n, thr, cand, count, row_lo, row_hi, unit);
+    if (n_tiles <= 0 || n <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(list_count, 0, sizeof(int32_t), s);   // the list is rebuilt per launch
+    if (e != cudaSuccess) return e;
+    det_list_kernel<<<n, 256, 0, s>>>(d_lv, row_lo, row_hi, list, list_count);
+    note_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int g = grid > 0 ? std::min(grid, n_tiles) : n_tiles;
+    detect_kernel<<<g, kDetCols * kDetRowsPar, 0, s>>>(d_lv, list, list_count, thr, cand, count, row_lo, row_hi, unit);
     note_launch();
     return cudaGetLastError();
 }
