@@ -888,16 +888,20 @@ orient_brief_kernel(const DevLevel *__restrict__ lv, int n_views, int n_levels, 
     const long long slot = (long long)v_begin * n_features + (long long)blockIdx.x * kObWarps + w;
     if (slot >= (long long)v_end * n_features) return;
     const int v = (int)(slot / n_features), rnk = (int)(slot - (long long)v * n_features);
-    // find the level whose slot range holds rnk
-    int e = -1, r = 0;
-    for (int l = 0; l < n_levels; ++l) {
-        const int ei = l * n_views + v;
-        const DevLevel &L = lv[ei];
-        if (rnk >= L.qoff && rnk < L.qoff + taken[ei]) { e = ei; r = rnk - L.qoff; break; }
-    }
-    if (e < 0) return;
-    const DevLevel &L = lv[e];
     const SlotKp s = slots[slot];
+    // the level whose slot range holds rnk: lane l checks level l (one round
+    // of loads instead of a dependent chain over the levels); ranges are disjoint
+    bool hit = false;
+    if ((int)lane < n_levels) {
+        const int ei = (int)lane * n_views + v;
+        const int q = lv[ei].qoff;
+        hit = rnk >= q && rnk < q + taken[ei];
+    }
+    const unsigned lv_hit = __ballot_sync(0xffffffffu, hit);
+    if (lv_hit == 0u) return;
+    const int e = (__ffs((int)lv_hit) - 1) * n_views + v;
+    const DevLevel &L = lv[e];
+    const int r = rnk - L.qoff;
     const int x = s.yx & 0xffff, y = s.yx >> 16;
     const int W = L.W, H = L.H;
 
