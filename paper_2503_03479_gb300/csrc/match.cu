@@ -264,10 +264,12 @@ pair_write_kernel(const MatchProblem *__restrict__ many, int n_probs, const Matc
     const MatchProblem &P = prob(many, single, p);
     const int lb = blockIdx.x - P.blk_off;
     const int nq = count_of(P.d_nq, P.nq_cap);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {   // this block's offset: the earlier blocks' counts, summed by warp 0
         int b = 0;
-        for (int k = P.blk_off; k < (int)blockIdx.x; ++k) b += block_count[k];
-        base = b;
+        for (int k = P.blk_off + (int)threadIdx.x; k < (int)blockIdx.x; k += 32) b += block_count[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+        if (threadIdx.x == 0) base = b;
     }
     const int i = lb * kPairBlock + threadIdx.x;
     const bool a = i < nq && P.accept[i];
