@@ -6,9 +6,11 @@
 //                       through the pyramid's taps (a superset of the valid set)
 //   pyramid_kernel      level l from level l-1: centre-aligned integer bilinear
 //                       (Q11 weights, round half up) + AND of the four mask taps
-//   detect_kernel       FAST-9 + Harris x25 + 3x3 NMS on shared-memory tiles,
-//                       only where the row hulls allow mask-valid corners;
-//                       survivors appended with a warp-aggregated atomic
+//                       (a view whose masks are its row hulls needs no plane)
+//   det_list_kernel     the detection tiles whose rows the hulls leave open
+//   detect_kernel       FAST-9 + Harris x25 + 3x3 NMS on shared-memory tiles of
+//                       that list; survivors appended with a warp-aggregated
+//                       atomic
 //   select_kernel       per (view, level): exact top-q by (R25 desc, y, x) via
 //                       MSD radix select on a 96-bit key + bitonic sort
 //   pool_scan_kernel    canonical pool offsets (view, level, rank)
