@@ -463,19 +463,35 @@ __device__ __forceinline__ void det_process(const DetItem it, const DevLevel *__
     // (b) the full test and the mask corners on the list.  Both passes append
     // with one shared atomic per warp (every lane runs every iteration).
     const unsigned lane_id = threadIdx.x & 31u;
+    // (a) as a bitmask per thread (bit k: pixel threadIdx.x + k * kThreads),
+    // appended once at the end with a warp scan and one atomic per warp
     int16_t *surv = sm.surv;
+    constexpr int kPass = (kRH * kRW + kThreads - 1) / kThreads;
+    static_assert(kPass <= 32, "a thread's compass results fit one word");
+    unsigned bits = 0u;
 #pragma unroll 1
-    for (int k = 0; k < (kRH * kRW + kThreads - 1) / kThreads; ++k) {
+    for (int k = 0; k < kPass; ++k) {
         const int el = (int)threadIdx.x + k * kThreads;
         const int r = el / kRW, c = el - r * kRW;
         const bool pass = el < kRH * kRW && c >= ea[r] && c <= eb[r] &&
                           fast9_compass<P>(&S[(r - 1 + kHalo) * P + c - 1 + kHalo], thr);
-        const unsigned bal = __ballot_sync(0xffffffffu, pass);
-        if (bal) {
-            int base = 0;
-            if (lane_id == 0) base = atomicAdd(&sm.ncand, __popc(bal));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (pass) surv[base + __popc(bal & ((1u << lane_id) - 1u))] = (int16_t)el;
+        bits |= (unsigned)pass << k;
+    }
+    {
+        const int cnt = __popc(bits);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((int)lane_id >= o) incl += v;
+        }
+        int base = 0;
+        if (lane_id == 31u && incl > 0) base = atomicAdd(&sm.ncand, incl);
+        base = __shfl_sync(0xffffffffu, base, 31) + incl - cnt;
+        while (bits) {
+            const int k = __ffs((int)bits) - 1;
+            bits &= bits - 1u;
+            surv[base++] = (int16_t)((int)threadIdx.x + k * kThreads);
         }
     }
     __syncthreads();
