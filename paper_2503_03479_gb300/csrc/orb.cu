@@ -364,11 +364,13 @@ template <int P>
 __device__ __forceinline__ bool fast9_compass(const uint8_t *p, int thr)
 {
     const int ctr = p[0];
-    const int hi = ctr + thr, lo = ctr - thr;
     const int n0 = p[-3 * P], n4 = p[3], n8 = p[3 * P], n12 = p[-3];
-    const int nb = (n0 > hi) + (n4 > hi) + (n8 > hi) + (n12 > hi);
-    const int nd = (n0 < lo) + (n4 < lo) + (n8 < lo) + (n12 < lo);
-    return nb >= 2 || nd >= 2;
+    // at least two of the four brighter than ctr + thr <=> the second largest
+    // is; at least two darker than ctr - thr <=> the second smallest is.  Of
+    // four values, with A = min(max pair maxima), B = max(pair minima), the
+    // second largest is max(A, B) and the second smallest min(A, B).
+    const int A = min(max(n0, n4), max(n8, n12)), B = max(min(n0, n4), min(n8, n12));
+    return max(A, B) > ctr + thr || min(A, B) < ctr - thr;
 }
 
 template <int P>
@@ -469,13 +471,18 @@ __device__ __forceinline__ void det_process(const DetItem it, const DevLevel *__
     constexpr int kPass = (kRH * kRW + kThreads - 1) / kThreads;
     static_assert(kPass <= 32, "a thread's compass results fit one word");
     unsigned bits = 0u;
+    int r = (int)threadIdx.x / kRW, c = (int)threadIdx.x - r * kRW;   // pixel el = r kRW + c, stepped by kThreads
 #pragma unroll 1
     for (int k = 0; k < kPass; ++k) {
-        const int el = (int)threadIdx.x + k * kThreads;
-        const int r = el / kRW, c = el - r * kRW;
-        const bool pass = el < kRH * kRW && c >= ea[r] && c <= eb[r] &&
+        const bool pass = r < kRH && c >= ea[r] && c <= eb[r] &&
                           fast9_compass<P>(&S[(r - 1 + kHalo) * P + c - 1 + kHalo], thr);
         bits |= (unsigned)pass << k;
+        c += kThreads % kRW;
+        r += kThreads / kRW;
+        if (c >= kRW) {
+            c -= kRW;
+            ++r;
+        }
     }
     {
         const int cnt = __popc(bits);
