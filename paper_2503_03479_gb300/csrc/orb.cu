@@ -299,7 +299,7 @@ struct DetSmem {
     int16_t clist[kRH * kRW];
     __align__(16) uint8_t img[kStageBytes];   // the tile's stage
     uint32_t isc[kRH][(kRW + 31) / 32];   // corner flags of the tile + ring, one bit per column
-    int16_t ea[kRH], eb[kRH];   // per tile + ring row: columns c whose FAST corners can be mask-valid
+    uint32_t eab[kRH];   // per tile + ring row: columns a .. b whose FAST corners can be mask-valid, a | b << 16
     int ncl, ncand;
 };
 
@@ -407,8 +407,7 @@ __device__ __forceinline__ void det_prepare(const DetItem it, const DevLevel *__
     if (threadIdx.x < kRH) {
         int a, b;
         det_row_cols(L, G.x0, G.y0, (int)threadIdx.x, row_lo, row_hi, a, b);
-        sm.ea[threadIdx.x] = (int16_t)(a <= b ? a : 1);
-        sm.eb[threadIdx.x] = (int16_t)(a <= b ? b : 0);
+        sm.eab[threadIdx.x] = a <= b ? (uint32_t)a | (uint32_t)b << 16 : 1u;   // none: a = 1 > b = 0
     }
     uint8_t *S = sm.img + G.s0;
     if (G.wide) {
@@ -455,7 +454,7 @@ __device__ __forceinline__ void det_process(const DetItem it, const DevLevel *__
     const DevLevel &L = lv[e];
     const DetGeom G = det_geom(L, it.tile);
     const int x0 = G.x0, y0 = G.y0, W = G.W;
-    const int16_t *ea = sm.ea, *eb = sm.eb;
+    const uint32_t *eab = sm.eab;
     const uint8_t *S = sm.img + G.s0;
     constexpr int kThreads = kDetCols * kDetRowsPar;
 
@@ -474,7 +473,8 @@ __device__ __forceinline__ void det_process(const DetItem it, const DevLevel *__
     int r = (int)threadIdx.x / kRW, c = (int)threadIdx.x - r * kRW;   // pixel el = r kRW + c, stepped by kThreads
 #pragma unroll 1
     for (int k = 0; k < kPass; ++k) {
-        const bool pass = r < kRH && c >= ea[r] && c <= eb[r] &&
+        const uint32_t ab = r < kRH ? eab[r] : 1u;
+        const bool pass = c >= (int)(ab & 0xffffu) && c <= (int)(ab >> 16) &&
                           fast9_compass<P>(&S[(r - 1 + kHalo) * P + c - 1 + kHalo], thr);
         bits |= (unsigned)pass << k;
         c += kThreads % kRW;
