@@ -462,6 +462,8 @@ __device__ __forceinline__ void warp_band_tile(int tile, const DevRotGroup *__re
     const long long xoff = (long long)(Wr - 1) * HALF;
     const long long mxlo = HALF, mxhi = (long long)(2 * W - 3) * HALF;
     const long long mylo = HALF, myhi = (long long)(2 * H - 3) * HALF;
+    const unsigned long long mxr = (unsigned long long)(mxhi - mxlo), myr = (unsigned long long)(myhi - mylo);
+    const bool fp_any = mxhi >= mxlo && myhi >= mylo;   // the shrunk footprint is empty below 2 x 2 pixels
     const long long dpx = 2LL * kRowStep * G.sq, dpy = 2LL * kRowStep * G.cq;
     for (int m = 0; m < G.n_views; ++m) {
         const DevView &V = views[G.view[m]];
@@ -503,18 +505,24 @@ __device__ __forceinline__ void warp_band_tile(int tile, const DevRotGroup *__re
                     }
                 }
                 const float accs[4] = {acc0, acc1, acc2, acc3};
-                const bool cols_ok = !bg && x0 >= 0 && x0 + 1 <= Wr - 1;
+                const bool cols_ok = fp_any && !bg && x0 >= 0 && x0 + 1 <= Wr - 1;
+                // the source points relative to the footprint's low corner: each
+                // coordinate is inside [lo, hi] iff its offset, as unsigned, is <= hi - lo
                 long long pxa, pya, pxb, pyb;
                 Gm.map(clampi(x0, 0, Wr - 1), j0 + rg, pxa, pya);
                 Gm.map(clampi(x0 + 1, 0, Wr - 1), j0 + rg, pxb, pyb);
+                pxa -= mxlo;
+                pxb -= mxlo;
+                pya -= mylo;
+                pyb -= mylo;
 #pragma unroll
                 for (int q = 0; q < kWarpTH / kRowStep; ++q, pxa += dpx, pya += dpy, pxb += dpx, pyb += dpy) {
                     const int r = rg + q * kRowStep;
                     if (r >= nrows) break;
                     const int j = j0 + r;
                     const float v = accs[q];
-                    const bool valid = cols_ok && pxa >= mxlo && pxa <= mxhi && pya >= mylo && pya <= myhi &&
-                                       pxb >= mxlo && pxb <= mxhi && pyb >= mylo && pyb <= myhi;
+                    const bool valid = cols_ok && (unsigned long long)pxa <= mxr && (unsigned long long)pya <= myr &&
+                                       (unsigned long long)pxb <= mxr && (unsigned long long)pyb <= myr;
                     const size_t o = (size_t)V.out_off + (size_t)j * V.Wv + x;
                     if (out_f32) out_f32[o] = v;
                     const int q8 = __float2int_rn(v);
