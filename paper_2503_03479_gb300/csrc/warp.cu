@@ -334,6 +334,15 @@ __device__ __forceinline__ void warp_band_tile(int tile, const DevRotGroup *__re
     const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     constexpr int kRowStep = kWarpThreads / kChunk;   // a thread walks its column in steps of 4 rows
 
+    // each member's view columns [xa, xb) for step 2, found once per tile by
+    // two threads per member (visible after step 1's last barrier)
+    __shared__ int mcols[2 * kGroupMax];
+    if ((int)threadIdx.x < 2 * G.n_views) {
+        const DevView &V = views[G.view[threadIdx.x >> 1]];
+        mcols[threadIdx.x] = (threadIdx.x & 1u) == 0u ? first_col_at(V, c0, 0, V.Wv)
+                                                      : (c1 >= Wr ? V.Wv : first_col_at(V, c1, 0, V.Wv));
+    }
+
     // 1. the rotated canvas on the strip (strip position i holds canvas
     //    column clamp(cx0 + i, 0, Wr - 1), which realises the clamped borders
     //    of the Gaussian and of the tilt taps without per-tap clamps)
@@ -467,8 +476,7 @@ __device__ __forceinline__ void warp_band_tile(int tile, const DevRotGroup *__re
     const long long dpx = 2LL * kRowStep * G.sq, dpy = 2LL * kRowStep * G.cq;
     for (int m = 0; m < G.n_views; ++m) {
         const DevView &V = views[G.view[m]];
-        const int xa = first_col_at(V, c0, 0, V.Wv);
-        const int xb = c1 >= Wr ? V.Wv : first_col_at(V, c1, xa, V.Wv);
+        const int xa = mcols[2 * m], xb = mcols[2 * m + 1];
         const int ncols = xb - xa;
         if (ncols <= 0) continue;
         const int K = V.K, hp = V.hp, nh = 2 * K + 6;
