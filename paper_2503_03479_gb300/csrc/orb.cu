@@ -966,15 +966,22 @@ orient_brief_kernel(const DevLevel *__restrict__ lv, int n_views, int n_levels, 
             if (c4 + k < kSm) h[rr * kSm + c4 + k] = (uint16_t)a;
         }
     }
-    // centroid moments on the raw patch (disc of radius 15)
+    // centroid moments on the raw patch (disc of radius 15): lane dx + 15
+    // sums its column over the disc's rows |dy| <= hh (exact integer sums)
     int m10 = 0, m01 = 0;
-    for (int i = lane; i < kSm * kSm; i += 32) {
-        const int dy = i / kSm - 15, dx = i % kSm - 15;
-        if (dx * dx + dy * dy <= kPatchR2) {
-            const int val = p[(dy + 18) * kPP + dx + 18];
-            m10 += dx * val;
-            m01 += dy * val;
+    if ((int)lane < kSm) {
+        const int dx = (int)lane - 15;
+        int hh = 15;
+        while (hh * hh > kPatchR2 - dx * dx) --hh;
+        const uint8_t *col = p + 18 * kPP + dx + 18;   // dy = 0
+        int sv = 0, sy = 0;
+        for (int dy = -hh; dy <= hh; ++dy) {
+            const int val = col[dy * kPP];
+            sv += val;
+            sy += dy * val;
         }
+        m10 = dx * sv;
+        m01 = sy;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
