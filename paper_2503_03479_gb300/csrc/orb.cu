@@ -87,6 +87,7 @@ __device__ __forceinline__ void pyramid_tile(int tile, const DevLevel *__restric
     const uint8_t *__restrict__ prev = L.prev;
     const uint8_t *__restrict__ prevm = L.prev_mask;
     const bool planes = __ldg(unit + L.view) == 0;   // unit-convex views keep their masks as row hulls only
+    const bool pairs = x1[0] == x0[0] + 1 && x1[1] == x0[1] + 1 && x1[2] == x0[2] + 1 && x1[3] == x0[3] + 1;
 #pragma unroll 1
     for (int r = 0; r < kPyrRowsW; ++r) {
         const int y = yb + r;
@@ -96,13 +97,24 @@ __device__ __forceinline__ void pyramid_tile(int tile, const DevLevel *__restric
         if (nx <= 0) continue;
         const uint8_t *P0 = prev + (size_t)y0 * Wp, *P1 = prev + (size_t)y1 * Wp;
         uint32_t wi = 0, wm = 0;
+        if (pairs) {   // x1 = x0 + 1 in all four columns: one address per tap pair
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const unsigned a = __ldg(P0 + x0[c]), b = __ldg(P0 + x1[c]);
-            const unsigned cc = __ldg(P1 + x0[c]), d = __ldg(P1 + x1[c]);
-            const unsigned f = (unsigned)fx[c], g = 2048u - f;
-            const unsigned sum = gy * (g * a + f * b) + fy * (g * cc + f * d);
-            wi |= ((sum + (1u << 21)) >> 22) << (8 * c);
+            for (int c = 0; c < 4; ++c) {
+                const uint8_t *q0 = P0 + x0[c], *q1 = P1 + x0[c];
+                const unsigned a = __ldg(q0), b = __ldg(q0 + 1), cc = __ldg(q1), d = __ldg(q1 + 1);
+                const unsigned f = (unsigned)fx[c], g = 2048u - f;
+                const unsigned sum = gy * (g * a + f * b) + fy * (g * cc + f * d);
+                wi |= ((sum + (1u << 21)) >> 22) << (8 * c);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const unsigned a = __ldg(P0 + x0[c]), b = __ldg(P0 + x1[c]);
+                const unsigned cc = __ldg(P1 + x0[c]), d = __ldg(P1 + x1[c]);
+                const unsigned f = (unsigned)fx[c], g = 2048u - f;
+                const unsigned sum = gy * (g * a + f * b) + fy * (g * cc + f * d);
+                wi |= ((sum + (1u << 21)) >> 22) << (8 * c);
+            }
         }
         if (planes) {
             const uint8_t *M0 = prevm + (size_t)y0 * Wp, *M1 = prevm + (size_t)y1 * Wp;
