@@ -904,7 +904,11 @@ constexpr int kSm = 31;             // smoothed patch
 // the smoothing taps [18 34 49 54 49 34 18] packed for dp4a: taps 0-3, taps 4-6 (and 0)
 constexpr unsigned kTapsLo = 18u | 34u << 8 | 49u << 16 | 54u << 24, kTapsHi = 49u | 34u << 8 | 18u << 16;
 
-__constant__ int c_smooth[7] = {18, 34, 49, 54, 49, 34, 18};
+// the same taps as byte pairs for dp2a over two 16-bit intermediate values:
+// (c0, c1), (c2, c3), (c4, c5), and shifted by one row (0, c0), (c1, c2), (c3, c4), (c5, c6)
+constexpr unsigned kV01 = 18u | 34u << 8, kV23 = 49u | 54u << 8, kV45 = 49u | 34u << 8, kV6 = 18u;
+constexpr unsigned kW0 = 0u | 18u << 8, kW12 = 34u | 49u << 8, kW34 = 54u | 49u << 8, kW56 = 34u | 18u << 8;
+constexpr int kHP = kPatch + 1;     // column pitch of the transposed intermediate (u16; even)
 
 __global__ void __launch_bounds__(kObWarps * 32)
 orient_brief_kernel(const DevLevel *__restrict__ lv, int n_views, int n_levels, int n_features, int v_begin, int v_end,
@@ -914,7 +918,7 @@ orient_brief_kernel(const DevLevel *__restrict__ lv, int n_views, int n_levels, 
                     uint4 *__restrict__ desc_out)
 {
     __shared__ __align__(16) uint8_t P[kObWarps][kPatch * kPP];
-    __shared__ uint16_t Hs[kObWarps][kPatch * kSm];
+    __shared__ __align__(16) uint16_t Hs[kObWarps][kSm * kHP];   // horizontal sums, column-major (column c, row r at c kHP + r)
     __shared__ uint8_t S[kObWarps][kSm * kSm];
     __shared__ long long eb[kBins][2];
     for (int i = threadIdx.x; i < kBins * 2; i += blockDim.x) eb[i >> 1][i & 1] = bins[i];
@@ -975,7 +979,7 @@ orient_brief_kernel(const DevLevel *__restrict__ lv, int n_views, int n_levels, 
         for (int k = 0; k < 4; ++k) {
             const unsigned sel = 0x3210u + 0x1111u * (unsigned)k;
             const unsigned a = __dp4a(__byte_perm(w1, w2, sel), kTapsHi, __dp4a(__byte_perm(w0, w1, sel), kTapsLo, 0u));
-            if (c4 + k < kSm) h[rr * kSm + c4 + k] = (uint16_t)a;
+            if (c4 + k < kSm) h[(c4 + k) * kHP + rr] = (uint16_t)a;
         }
     }
     // centroid moments on the raw patch (disc of radius 15): lane dx + 15
@@ -1002,20 +1006,24 @@ orient_brief_kernel(const DevLevel *__restrict__ lv, int n_views, int n_levels, 
     }
     __syncwarp();
     // vertical pass, rounded half up: lane item = (column, 4 consecutive
-    // rows), the 10 intermediate values loaded once
+    // rows r0 .. r0 + 3), its 10 intermediate values as 5 row pairs of the
+    // column-major buffer; each output is dp2a's over the pairs with the taps
+    // as byte pairs (exact integer sums; the pad row 37 only reaches row 31,
+    // which is not kept)
     uint8_t *sm = S[w];
+    __syncwarp();
     for (int i = lane; i < kSm * 8; i += 32) {
         const int g = i / kSm, cc = i - g * kSm, r0 = 4 * g;
-        unsigned hv[10];
+        const uint32_t *pc = reinterpret_cast<const uint32_t *>(h + cc * kHP + r0);
+        const uint32_t P0 = pc[0], P1 = pc[1], P2 = pc[2], P3 = pc[3], P4 = pc[4];
+        const unsigned o0 = __dp2a_lo(P2, kV45, __dp2a_lo(P1, kV23, __dp2a_lo(P0, kV01, kV6 * (P3 & 0xffffu))));
+        const unsigned o1 = __dp2a_lo(P3, kW56, __dp2a_lo(P2, kW34, __dp2a_lo(P1, kW12, __dp2a_lo(P0, kW0, 0u))));
+        const unsigned o2 = __dp2a_lo(P3, kV45, __dp2a_lo(P2, kV23, __dp2a_lo(P1, kV01, kV6 * (P4 & 0xffffu))));
+        const unsigned o3 = __dp2a_lo(P4, kW56, __dp2a_lo(P3, kW34, __dp2a_lo(P2, kW12, __dp2a_lo(P1, kW0, 0u))));
+        const unsigned o[4] = {o0, o1, o2, o3};
 #pragma unroll
-        for (int t = 0; t < 10; ++t) hv[t] = (r0 + t < kPatch) ? h[(r0 + t) * kSm + cc] : 0u;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            unsigned a = 0;
-#pragma unroll
-            for (int t = 0; t < 7; ++t) a += (unsigned)c_smooth[t] * hv[q + t];
-            if (r0 + q < kSm) sm[(r0 + q) * kSm + cc] = (uint8_t)((a + 32768u) >> 16);
-        }
+        for (int q = 0; q < 4; ++q)
+            if (r0 + q < kSm) sm[(r0 + q) * kSm + cc] = (uint8_t)((o[q] + 32768u) >> 16);
     }
     // orientation sector: on or left of e_b, strictly right of e_{b+1}
     int bin = 0;
