@@ -408,13 +408,12 @@ __device__ __forceinline__ bool fast9_ring(const uint8_t *p, int thr)
 // side copy each row's whole containing words asynchronously (every word
 // inside the level row; one commit group); other interior tiles copy words
 // with byte-exact edges; the rest copy bytes with clamping.
-__device__ __forceinline__ void det_prepare(const DetItem it, const DevLevel *__restrict__ lv,
+__device__ __forceinline__ void det_prepare(const DetItem it, const DetGeom &G, const DevLevel *__restrict__ lv,
                                             const int32_t *__restrict__ row_lo, const int32_t *__restrict__ row_hi,
                                             DetSmem &sm)
 {
     constexpr int kThreads = kDetCols * kDetRowsPar;
     const DevLevel &L = lv[it.e];
-    const DetGeom G = det_geom(L, it.tile);
     const int P = kSPMin + (G.W & 3);
     if (threadIdx.x < kRH) {
         int a, b;
@@ -454,7 +453,7 @@ __device__ __forceinline__ void det_prepare(const DetItem it, const DevLevel *__
 // A prepared tile (its stage and row columns visible, counters zeroed):
 // FAST, Harris, NMS and the candidates.
 template <int P>
-__device__ __forceinline__ void det_process(const DetItem it, const DevLevel *__restrict__ lv, int thr,
+__device__ __forceinline__ void det_process(const DetItem it, const DetGeom &G, const DevLevel *__restrict__ lv, int thr,
                                             Candidate *__restrict__ cand, int32_t *__restrict__ cand_count,
                                             const int32_t *__restrict__ unit, DetSmem &sm)
 {
@@ -464,7 +463,6 @@ __device__ __forceinline__ void det_process(const DetItem it, const DevLevel *__
     int &ncl = sm.ncl;
     const int e = it.e;
     const DevLevel &L = lv[e];
-    const DetGeom G = det_geom(L, it.tile);
     const int x0 = G.x0, y0 = G.y0, W = G.W;
     const uint32_t *eab = sm.eab;
     const uint8_t *S = sm.img + G.s0;
@@ -472,9 +470,9 @@ __device__ __forceinline__ void det_process(const DetItem it, const DevLevel *__
 
     // corner flags on the tile + ring in two passes, so that the full ring test
     // runs with every lane busy: (a) border and compass test for every pixel,
-    // survivors listed (in the Sobel buffer, unused until the gradients);
-    // (b) the full test and the mask corners on the list.  Both passes append
-    // with one shared atomic per warp (every lane runs every iteration).
+    // survivors listed; (b) the full test and the mask corners on the list,
+    // appended with one shared atomic per warp (every lane runs every
+    // iteration).
     const unsigned lane_id = threadIdx.x & 31u;
     // (a) as a bitmask per thread (bit k: pixel threadIdx.x + k * kThreads),
     // appended once at the end with a warp scan and one atomic per warp
@@ -697,7 +695,8 @@ detect_kernel(const DevLevel *__restrict__ lv, const DetItem *__restrict__ list,
     const int n = __ldg(count);
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
         const DetItem cur = list[k];
-        det_prepare(cur, lv, row_lo, row_hi, sm);
+        const DetGeom G = det_geom(lv[cur.e], cur.tile);
+        det_prepare(cur, G, lv, row_lo, row_hi, sm);
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         if (threadIdx.x == 0) {
             sm.ncl = 0;
@@ -705,11 +704,11 @@ detect_kernel(const DevLevel *__restrict__ lv, const DetItem *__restrict__ list,
         }
         if (threadIdx.x < kRH * ((kRW + 31) / 32)) (&sm.isc[0][0])[threadIdx.x] = 0u;
         __syncthreads();
-        switch (lv[cur.e].W & 3) {
-        case 0: det_process<kSPMin>(cur, lv, thr, cand, cand_count, unit, sm); break;
-        case 1: det_process<kSPMin + 1>(cur, lv, thr, cand, cand_count, unit, sm); break;
-        case 2: det_process<kSPMin + 2>(cur, lv, thr, cand, cand_count, unit, sm); break;
-        default: det_process<kSPMin + 3>(cur, lv, thr, cand, cand_count, unit, sm); break;
+        switch (G.W & 3) {
+        case 0: det_process<kSPMin>(cur, G, lv, thr, cand, cand_count, unit, sm); break;
+        case 1: det_process<kSPMin + 1>(cur, G, lv, thr, cand, cand_count, unit, sm); break;
+        case 2: det_process<kSPMin + 2>(cur, G, lv, thr, cand, cand_count, unit, sm); break;
+        default: det_process<kSPMin + 3>(cur, G, lv, thr, cand, cand_count, unit, sm); break;
         }
         __syncthreads();
     }
@@ -738,6 +737,7 @@ select_kernel(const DevLevel *__restrict__ lv, const Candidate *__restrict__ can
     __shared__ unsigned long long pre_hi, msk_hi;
     __shared__ unsigned pre_lo, msk_lo;
     __shared__ int need, done, nsel;
+    __shared__ int wsum[8];
 
     const int e = blockIdx.x;
     const DevLevel &L = lv[e];
@@ -772,21 +772,36 @@ select_kernel(const DevLevel *__restrict__ lv, const Candidate *__restrict__ can
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            int cum = 0, b = 0;
-            for (b = 0; b < 256; ++b) {
-                if (cum + (int)hist[b] >= need) break;
-                cum += (int)hist[b];
+        // the digit: the first bin b whose inclusive count reaches `need`,
+        // from a block scan of the 256 bins (thread b holds bin b)
+        {
+            const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+            const int v = threadIdx.x < 256 ? (int)hist[threadIdx.x] : 0;
+            int incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if ((int)lane >= o) incl += t;
             }
-            need -= cum;
-            if (d < 8) {
-                pre_hi |= (unsigned long long)b << (56 - 8 * d);
-                msk_hi |= 255ULL << (56 - 8 * d);
-            } else {
-                pre_lo |= (unsigned)b << (24 - 8 * (d - 8));
-                msk_lo |= 255u << (24 - 8 * (d - 8));
+            if (lane == 31u && wid < 8u) wsum[wid] = incl;
+            const int nd = need;   // read before the barrier: the winner below rewrites it
+            __syncthreads();
+            if (threadIdx.x < 256) {
+                for (unsigned w = 0; w < wid; ++w) incl += wsum[w];
+                const int excl = incl - v;
+                if (excl < nd && incl >= nd) {   // exactly one bin
+                    const unsigned b = threadIdx.x;
+                    need = nd - excl;
+                    if (d < 8) {
+                        pre_hi |= (unsigned long long)b << (56 - 8 * d);
+                        msk_hi |= 255ULL << (56 - 8 * d);
+                    } else {
+                        pre_lo |= b << (24 - 8 * (d - 8));
+                        msk_lo |= 255u << (24 - 8 * (d - 8));
+                    }
+                    if (v == nd - excl) done = 1;   // the whole bucket is selected
+                }
             }
-            if ((int)hist[b] == need) done = 1;   // the whole bucket is selected
         }
         __syncthreads();
     }
