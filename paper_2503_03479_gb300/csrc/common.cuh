@@ -121,9 +121,10 @@ struct DiffView {
     int32_t W, H, Wr, Hr, Wv, Hv, K, tile_start, ntx, tw;   // tw: view columns per tile
 };
 
-// A tile of the ORB detection: its level entry and its index in the launch.
+// A tile of the ORB detection: its level entry and its origin on the level.
 struct DetItem {
-    int32_t e, tile;
+    int32_t e;
+    uint16_t x0, y0;
 };
 
 // Per-view constants of the differentiable warp, made once per call on the

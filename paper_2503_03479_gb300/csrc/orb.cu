@@ -323,15 +323,13 @@ struct DetGeom {
     const uint8_t *g0;
 };
 
-__device__ __forceinline__ DetGeom det_geom(const DevLevel &L, int tile)
+__device__ __forceinline__ DetGeom det_geom(const DevLevel &L, const DetItem it)
 {
     DetGeom G;
-    const int lt = tile - L.det_tile_start;
-    const int ty = lt / L.det_ntx, tx = lt - ty * L.det_ntx;
     G.W = L.W;
     G.H = L.H;
-    G.x0 = tx * kDetTW;
-    G.y0 = ty * kDetTH;
+    G.x0 = it.x0;
+    G.y0 = it.y0;
     G.interior = G.x0 - kHalo >= 0 && G.y0 - kHalo >= 0 && G.x0 + kDetTW + kHalo <= G.W && G.y0 + kDetTH + kHalo <= G.H;
     G.wide = G.interior && G.x0 - kHalo >= 3 && G.x0 + kDetTW + kHalo + 3 <= G.W;
     G.g0 = G.interior ? L.img + (size_t)(G.y0 - kHalo) * G.W + (G.x0 - kHalo) : L.img;
@@ -371,18 +369,36 @@ __device__ __forceinline__ bool has_run9(unsigned m)
 // FAST-9 at the staged pixel p (row pitch P): the Bresenham circle of radius
 // 3 from (0,-3) clockwise, with compile-time offsets.  A 9-arc holds at least
 // 2 of the 4 compass points, so pixels with fewer bright and fewer dark
-// compass points cannot pass (fast9_compass); fast9_ring is the full test.
-template <int P>
-__device__ __forceinline__ bool fast9_compass(const uint8_t *p, int thr)
+// compass points cannot pass (compass2); fast9_ring is the full test.
+__device__ __forceinline__ uint32_t vmax2(uint32_t a, uint32_t b)
 {
-    const int ctr = p[0];
-    const int n0 = p[-3 * P], n4 = p[3], n8 = p[3 * P], n12 = p[-3];
-    // at least two of the four brighter than ctr + thr <=> the second largest
-    // is; at least two darker than ctr - thr <=> the second smallest is.  Of
-    // four values, with A = min(max pair maxima), B = max(pair minima), the
-    // second largest is max(A, B) and the second smallest min(A, B).
-    const int A = min(max(n0, n4), max(n8, n12)), B = max(min(n0, n4), min(n8, n12));
-    return max(A, B) > ctr + thr || min(A, B) < ctr - thr;
+    uint32_t d;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+__device__ __forceinline__ uint32_t vmin2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+// The compass test of two pixels at once, one per 16-bit lane (values 0..255):
+// centres c, compass points n, e, s, w.  At least two of the four points are
+// brighter than c + thr iff the second largest is, and at least two darker
+// than c - thr iff the second smallest is; of four values, with A the smaller
+// of the two pair maxima and B the larger of the two pair minima, the second
+// largest is max(A, B) and the second smallest min(A, B).  With kp = 511 - thr
+// in each lane (0 <= thr <= 255), hi + kp - c and c + kp - lo lie in [1, 766]
+// in every lane, so the 32-bit sums carry and borrow nothing between the
+// lanes, and reach 512 (bit 9 of the lane) exactly when hi > c + thr, resp.
+// lo < c - thr.  Returns bits 9 and 25: the pixels passing.
+__device__ __forceinline__ uint32_t compass2(uint32_t c, uint32_t n, uint32_t e, uint32_t s, uint32_t w, uint32_t kp)
+{
+    const uint32_t A = vmin2(vmax2(n, e), vmax2(s, w)), B = vmax2(vmin2(n, e), vmin2(s, w));
+    const uint32_t hi = vmax2(A, B), lo = vmin2(A, B);
+    return ((hi + kp - c) | (c + kp - lo)) & 0x02000200u;
 }
 
 template <int P>
@@ -474,25 +490,46 @@ __device__ __forceinline__ void det_process(const DetItem it, const DetGeom &G, 
     // appended with one shared atomic per warp (every lane runs every
     // iteration).
     const unsigned lane_id = threadIdx.x & 31u;
-    // (a) as a bitmask per thread (bit k: pixel threadIdx.x + k * kThreads),
-    // appended once at the end with a warp scan and one atomic per warp
+    // (a) four pixels of a ring row per thread and pass: the aligned stage
+    // word holding them, its two neighbours in the row and the words three
+    // rows up and down give the pixels and their compass points as 16-bit
+    // lane pairs (even and odd pixels).  Bit 4k + i of the thread's mask is
+    // pixel i of its group in pass k; the survivors are appended once at the
+    // end with a warp scan and one atomic per warp.
     int16_t *surv = sm.surv;
-    constexpr int kPass = (kRH * kRW + kThreads - 1) / kThreads;
-    static_assert(kPass <= 32, "a thread's compass results fit one word");
+    constexpr int kGW = (kRW + 6) / 4;   // groups per ring row: the row's columns after up to 3 of lead-in
+    constexpr int kGPass = (kRH * kGW + kThreads - 1) / kThreads;
+    static_assert(4 * kGPass <= 32, "a thread's compass results fit one word");
+    constexpr int kNm = (4 - (3 * P) % 4) % 4;   // offset of the window three rows up in its aligned word
+    constexpr int kSm = (3 * P) % 4;             // and of the window three rows down
+    const uint8_t *img = sm.img;                 // ring pixel (r, c) at byte s0 + (r + 4) P + c + 4
+    auto word = [&](int off) { return *reinterpret_cast<const uint32_t *>(img + off); };
+    const uint32_t kp = (uint32_t)(511 - thr) * 0x00010001u;
     unsigned bits = 0u;
-    int r = (int)threadIdx.x / kRW, c = (int)threadIdx.x - r * kRW;   // pixel el = r kRW + c, stepped by kThreads
 #pragma unroll 1
-    for (int k = 0; k < kPass; ++k) {
-        const uint32_t ab = r < kRH ? eab[r] : 1u;
-        const bool pass = c >= (int)(ab & 0xffffu) && c <= (int)(ab >> 16) &&
-                          fast9_compass<P>(&S[(r - 1 + kHalo) * P + c - 1 + kHalo], thr);
-        bits |= (unsigned)pass << k;
-        c += kThreads % kRW;
-        r += kThreads / kRW;
-        if (c >= kRW) {
-            c -= kRW;
-            ++r;
-        }
+    for (int k = 0; k < kGPass; ++k) {
+        const int el = (int)threadIdx.x + k * kThreads;
+        const int r = el / kGW, g = el - r * kGW;
+        if (r >= kRH) break;
+        const uint32_t ab = eab[r];
+        const int q = G.s0 + (r + 4) * P + 4;    // ring column 0
+        const int cb = 4 * g - (q & 3);          // ring column of the group's pixel 0
+        const int lo = (int)(ab & 0xffffu) - cb, hi = (int)(ab >> 16) - cb;
+        const uint32_t m = (0xFu << min(max(lo, 0), 4)) & (0xFu >> min(max(3 - hi, 0), 4));
+        if (m == 0u) continue;
+        const int wa = (q & ~3) + 4 * g;
+        const uint32_t w1 = word(wa);
+        const uint32_t ww = __funnelshift_r(word(wa - 4), w1, 8), we = __funnelshift_r(w1, word(wa + 4), 24);
+        const uint32_t wn = kNm ? __funnelshift_r(word(wa - 3 * P - kNm), word(wa - 3 * P - kNm + 4), 8 * kNm)
+                                : word(wa - 3 * P);
+        const uint32_t ws = kSm ? __funnelshift_r(word(wa + 3 * P - kSm), word(wa + 3 * P - kSm + 4), 8 * kSm)
+                                : word(wa + 3 * P);
+        constexpr uint32_t kEven = 0x00ff00ffu;
+        const uint32_t pe = compass2(w1 & kEven, wn & kEven, we & kEven, ws & kEven, ww & kEven, kp);
+        const uint32_t po = compass2(__byte_perm(w1, 0u, 0x4341), __byte_perm(wn, 0u, 0x4341), __byte_perm(we, 0u, 0x4341),
+                                     __byte_perm(ws, 0u, 0x4341), __byte_perm(ww, 0u, 0x4341), kp);
+        const uint32_t t = pe | (po << 1);       // bits 9, 10, 25, 26: pixels 0, 1, 2, 3
+        bits |= (((t >> 9) | (t >> 23)) & m) << (4 * k);
     }
     {
         const int cnt = __popc(bits);
@@ -506,9 +543,12 @@ __device__ __forceinline__ void det_process(const DetItem it, const DetGeom &G, 
         if (lane_id == 31u && incl > 0) base = atomicAdd(&sm.ncand, incl);
         base = __shfl_sync(0xffffffffu, base, 31) + incl - cnt;
         while (bits) {
-            const int k = __ffs((int)bits) - 1;
+            const int b = __ffs((int)bits) - 1;
             bits &= bits - 1u;
-            surv[base++] = (int16_t)((int)threadIdx.x + k * kThreads);
+            const int el = (int)threadIdx.x + (b >> 2) * kThreads;
+            const int r = el / kGW, g = el - r * kGW;
+            const int q = G.s0 + (r + 4) * P + 4;
+            surv[base++] = (int16_t)(r * kRW + 4 * g + (b & 3) - (q & 3));
         }
     }
     __syncthreads();
@@ -661,9 +701,11 @@ det_list_kernel(const DevLevel *__restrict__ lv, const int32_t *__restrict__ row
     for (int b0 = 0; b0 < nt; b0 += blockDim.x) {
         const int lt = b0 + (int)threadIdx.x;
         bool any = false;
+        int x0 = 0, y0 = 0;
         if (lt < nt) {
             const int ty = lt / L.det_ntx, tx = lt - ty * L.det_ntx;
-            const int x0 = tx * kDetTW, y0 = ty * kDetTH;
+            x0 = tx * kDetTW;
+            y0 = ty * kDetTH;
             for (int r = 0; r < kRH && !any; ++r) {
                 int a, b;
                 det_row_cols(L, x0, y0, r, row_lo, row_hi, a, b);
@@ -675,7 +717,7 @@ det_list_kernel(const DevLevel *__restrict__ lv, const int32_t *__restrict__ row
             int base = 0;
             if (lane == 0) base = atomicAdd(count, __popc(bal));
             base = __shfl_sync(0xffffffffu, base, 0);
-            if (any) list[base + __popc(bal & ((1u << lane) - 1u))] = DetItem{e, L.det_tile_start + lt};
+            if (any) list[base + __popc(bal & ((1u << lane) - 1u))] = DetItem{e, (uint16_t)x0, (uint16_t)y0};
         }
     }
 }
@@ -695,7 +737,7 @@ detect_kernel(const DevLevel *__restrict__ lv, const DetItem *__restrict__ list,
     const int n = __ldg(count);
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
         const DetItem cur = list[k];
-        const DetGeom G = det_geom(lv[cur.e], cur.tile);
+        const DetGeom G = det_geom(lv[cur.e], cur);
         det_prepare(cur, G, lv, row_lo, row_hi, sm);
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         if (threadIdx.x == 0) {
