@@ -431,20 +431,18 @@ hamming_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constan
                 const uint32_t taddr =
                     tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((acc * kTcQB + qb) * kTcBN);
                 const int valid = min(kTcBN, it.t1 - tb);
-#pragma unroll 1
-                for (int c = 0; c < kTcBN / 32; c += 2) {
-                    __syncwarp();                        // tcgen05.ld is warp-collective
-                    uint32_t r[2][32];
-                    tmem_ld32(taddr + (uint32_t)(c * 32), r[0]);
-                    tmem_ld32(taddr + (uint32_t)(c * 32 + 32), r[1]);
-                    tmem_wait_ld();
-                    if (valid == kTcBN) {
-                        epi_chunk<true>(r[0], 32, tb + c * 32, b1, b2, thr, best);
-                        epi_chunk<true>(r[1], 32, tb + c * 32 + 32, b1, b2, thr, best);
-                    } else {
-                        epi_chunk<false>(r[0], valid - c * 32, tb + c * 32, b1, b2, thr, best);
-                        epi_chunk<false>(r[1], valid - c * 32 - 32, tb + c * 32 + 32, b1, b2, thr, best);
-                    }
+                __syncwarp();                            // tcgen05.ld is warp-collective
+                uint32_t r[kTcBN / 32][32];              // the whole tile row: one wait per tile
+#pragma unroll
+                for (int c = 0; c < kTcBN / 32; ++c) tmem_ld32(taddr + (uint32_t)(c * 32), r[c]);
+                tmem_wait_ld();
+                if (valid == kTcBN) {
+#pragma unroll
+                    for (int c = 0; c < kTcBN / 32; ++c) epi_chunk<true>(r[c], 32, tb + c * 32, b1, b2, thr, best);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < kTcBN / 32; ++c)
+                        epi_chunk<false>(r[c], valid - c * 32, tb + c * 32, b1, b2, thr, best);
                 }
                 tc_fence_before();
                 __syncwarp();
