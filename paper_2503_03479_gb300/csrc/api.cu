@@ -663,7 +663,9 @@ static cudaError_t run_orb(asift_ctx *ctx, const LevelTables &T, int nv, int n_g
     cudaError_t e = cudaMemsetAsync(o.cand_count, 0, sizeof(int32_t) * nl, s);
     if (e != cudaSuccess) return e;
     // mask row hulls: level 0 scanned, levels >= 1 derived through the pyramid's taps
-    e = launch_mask_rows(o.lv, nv, L, (int)T.rows_level0, o.row_lo, o.row_hi, o.unit, s);
+    int max_h1 = 0;   // the tallest level >= 1 (one thread per row of each)
+    for (size_t i = (size_t)nv; i < T.lv.size(); ++i) max_h1 = std::max(max_h1, T.lv[i].H);
+    e = launch_mask_rows(o.lv, nv, L, (int)T.rows_level0, max_h1, o.row_lo, o.row_hi, o.unit, s);
     if (e != cudaSuccess) return e;
     if (!per_view) {
         for (int l = 1; l < L && e == cudaSuccess; ++l)

@@ -41,8 +41,8 @@ cudaError_t launch_warp_nn(const DevView *d_views, int n_views, int n_tiles, int
 
 // orb.cu
 struct DetItem;
-cudaError_t launch_mask_rows(const DevLevel *d_lv, int nv, int n_levels, int rows0, int32_t *row_lo, int32_t *row_hi,
-                             int32_t *unit, cudaStream_t s);
+cudaError_t launch_mask_rows(const DevLevel *d_lv, int nv, int n_levels, int rows0, int max_h1, int32_t *row_lo,
+                             int32_t *row_hi, int32_t *unit, cudaStream_t s);
 cudaError_t launch_pyramid(const DevLevel *d_lv, int n, int n_tiles, const int32_t *unit, cudaStream_t s, int grid = 0);
 cudaError_t launch_detect(const DevLevel *d_lv, int n, int n_tiles, int thr, Candidate *cand, int32_t *count,
                           const int32_t *row_lo, const int32_t *row_hi, const int32_t *unit, DetItem *list,

@@ -215,47 +215,60 @@ mask_rows_kernel(const DevLevel *__restrict__ lv, int n, int rows, int32_t *__re
     }
 }
 
-// Levels >= 1 of view blockIdx.x, in order: a level-l pixel's mask is the AND
-// of the previous level's at the pyramid's four taps (columns x0(x), x1(x),
-// rows y0(y), y1(y)), so it can be 1 only if x0 >= max(lo(y0), lo(y1)) = A
-// and x1 <= min(hi(y0), hi(y1)) = B; x0 and x1 grow with x, so those x form
-// an interval.  With x0(x) = floor(((2x + 1) Wp - Wl) / (2 Wl)) (the numerator
-// is >= 0), x0(x) >= A  <=>  x >= ceil((2 Wl A + Wl - Wp) / (2 Wp)), and
+// Levels >= 1: a level-l pixel's mask is the AND of the previous level's at
+// the pyramid's four taps (columns x0(x), x1(x), rows y0(y), y1(y)), so it can
+// be 1 only if x0 >= max(lo(y0), lo(y1)) = A and x1 <= min(hi(y0), hi(y1)) = B;
+// x0 and x1 grow with x, so those x form an interval [F(A), G(B)].  With
+// x0(x) = floor(((2x + 1) Wp - Wl) / (2 Wl)) (the numerator is >= 0),
+// x0(x) >= A  <=>  x >= ceil((2 Wl A + Wl - Wp) / (2 Wp)), and
 // x1(x) = min(x0(x) + 1, Wp - 1) > B  <=>  x0(x) >= B when B < Wp - 1 (never
-// otherwise), so both ends are one integer division each.  The interval holds
-// every valid column (exactly them when the previous level's rows are
-// intervals, as the views' masks are).
+// otherwise).  The interval holds every valid column (exactly them when the
+// previous level's rows are intervals, as the views' masks are).
+//   F and G do not decrease, so F(max(a, b)) = max(F(a), F(b)) and G(min) =
+// min(G): level l's hull of row y is F_l(...F_1(max lo_0)) and G_l(...G_1(min
+// hi_0)) over the level-0 rows reached from y through l steps of the row taps,
+// a contiguous range (consecutive y0 differ by 1 or 2).  An empty parent row
+// (A > B gives F(A) > G(B)) leaves every row built on it empty, whether it is
+// stored as kHullEmpty* or as its own empty interval, so one thread per row
+// computes every level at once, with no pass per level.
 __device__ __forceinline__ int pyr_tap0(int o, int nl, int np) { return ((2 * o + 1) * np - nl) / (2 * nl); }
 
-// First x >= 0 with x0(x) >= A (A >= 0), not clamped above.
-__device__ __forceinline__ int first_x_at(long long A, int Wl, int Wp)
+// min(first x >= 0 with x0(x) >= A, Wl) for A >= 0: Wl when A >= Wp (x0 < Wp).
+__device__ __forceinline__ int first_x_at(int A, int Wl, int Wp)
 {
+    if (A >= Wp) return Wl;
     const long long n = 2LL * Wl * A + Wl - Wp, d = 2LL * Wp;
-    return n <= 0 ? 0 : (int)((n + d - 1) / d);
+    return n <= 0 ? 0 : (int)min((n + d - 1) / d, (long long)Wl);
 }
 
+// blockIdx.x: level entry nv + k (levels >= 1); a thread per row.
 __global__ void __launch_bounds__(256)
-hull_levels_kernel(const DevLevel *__restrict__ lv, int nv, int n_levels, int32_t *__restrict__ row_lo,
-                   int32_t *__restrict__ row_hi)
+hull_levels_kernel(const DevLevel *__restrict__ lv, int nv, int32_t *__restrict__ row_lo, int32_t *__restrict__ row_hi)
 {
-    const int v = blockIdx.x;
-    for (int l = 1; l < n_levels; ++l) {
-        const DevLevel &L = lv[(size_t)l * nv + v], &Q = lv[(size_t)(l - 1) * nv + v];
-        const int Wl = L.W, Hl = L.H, Wp = L.Wp, Hp = L.Hp;
-        for (int y = threadIdx.x; y < Hl; y += blockDim.x) {
-            const int y0 = pyr_tap0(y, Hl, Hp), y1 = min(y0 + 1, Hp - 1);
-            const int A = max(row_lo[Q.row_off + y0], row_lo[Q.row_off + y1]);
-            const int B = min(row_hi[Q.row_off + y0], row_hi[Q.row_off + y1]);
-            int a = 1, b = 0;
-            if (A <= B) {   // else a parent row is empty: so is this one
-                a = min(first_x_at(A, Wl, Wp), Wl);
-                b = B >= Wp - 1 ? Wl - 1 : min(first_x_at(B, Wl, Wp), Wl) - 1;
-            }
-            row_lo[L.row_off + y] = a <= b ? a : kHullEmptyLo;
-            row_hi[L.row_off + y] = a <= b ? b : kHullEmptyHi;
-        }
-        __syncthreads();                              // level l done before level l + 1 reads it
+    const DevLevel &L = lv[nv + blockIdx.x];
+    const int y = blockIdx.y * blockDim.x + threadIdx.x;
+    if (y >= L.H) return;
+    const int v = L.view, l = L.level;
+    int ra = y, rb = y;                                  // the rows reached, level by level down to 0
+    for (int k = l; k >= 1; --k) {
+        const DevLevel &Q = lv[(size_t)k * nv + v];
+        ra = pyr_tap0(ra, Q.H, Q.Hp);
+        rb = min(pyr_tap0(rb, Q.H, Q.Hp) + 1, Q.Hp - 1);
     }
+    const int off0 = lv[v].row_off;
+    int A = 0, B = 0x7fffffff;
+    for (int r = ra; r <= rb; ++r) {
+        A = max(A, __ldg(row_lo + off0 + r));
+        B = min(B, __ldg(row_hi + off0 + r));
+    }
+    for (int k = 1; k <= l; ++k) {
+        const DevLevel &Q = lv[(size_t)k * nv + v];
+        const int Wl = Q.W, Wp = Q.Wp;
+        A = first_x_at(A, Wl, Wp);
+        B = B < 0 ? -1 : (B >= Wp - 1 ? Wl - 1 : first_x_at(B, Wl, Wp) - 1);
+    }
+    row_lo[L.row_off + y] = A <= B ? A : kHullEmptyLo;
+    row_hi[L.row_off + y] = A <= B ? B : kHullEmptyHi;
 }
 
 // ---------------------------------------------------------------- staging
@@ -1134,8 +1147,8 @@ cudaError_t launch_pyramid(const DevLevel *d_lv, int n, int n_tiles, const int32
     return cudaGetLastError();
 }
 
-cudaError_t launch_mask_rows(const DevLevel *d_lv, int nv, int n_levels, int rows0, int32_t *row_lo, int32_t *row_hi,
-                             int32_t *unit, cudaStream_t s)
+cudaError_t launch_mask_rows(const DevLevel *d_lv, int nv, int n_levels, int rows0, int max_h1, int32_t *row_lo,
+                             int32_t *row_hi, int32_t *unit, cudaStream_t s)
 {
     if (rows0 <= 0 || nv <= 0) return cudaSuccess;
     cudaError_t e0 = cudaMemsetAsync(unit, 0xFF, sizeof(int32_t) * (size_t)nv, s);   // every view unit-convex until a row says not
@@ -1144,8 +1157,9 @@ cudaError_t launch_mask_rows(const DevLevel *d_lv, int nv, int n_levels, int row
     mask_rows_kernel<<<blocks, 256, 0, s>>>(d_lv, nv, rows0, row_lo, row_hi, unit);
     note_launch();
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || n_levels < 2) return e;
-    hull_levels_kernel<<<nv, 256, 0, s>>>(d_lv, nv, n_levels, row_lo, row_hi);
+    if (e != cudaSuccess || n_levels < 2 || max_h1 <= 0) return e;
+    const dim3 g((unsigned)((n_levels - 1) * nv), (unsigned)((max_h1 + 255) / 256));
+    hull_levels_kernel<<<g, 256, 0, s>>>(d_lv, nv, row_lo, row_hi);
     note_launch();
     return cudaGetLastError();
 }
