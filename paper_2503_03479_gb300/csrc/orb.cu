@@ -319,8 +319,10 @@ constexpr int kSPMin = kSW + 6, kSPMax = kSPMin + 3;
 
 constexpr int kStageBytes = (kSH * kSPMax + 15) & ~15;
 struct DetSmem {
-    long long R[kRH][kRW];
-    int16_t surv[kRH * kRW];     // compass survivors
+    union {                      // the survivors are read before any response is written
+        long long R[kRH][kRW];
+        int16_t surv[kRH * kRW]; // compass survivors
+    };
     int16_t clist[kRH * kRW];
     __align__(16) uint8_t img[kStageBytes];   // the tile's stage
     uint32_t isc[kRH][(kRW + 31) / 32];   // corner flags of the tile + ring, one bit per column
@@ -737,11 +739,11 @@ det_list_kernel(const DevLevel *__restrict__ lv, const int32_t *__restrict__ row
 
 // One CTA per listed tile (a positive grid makes it persistent over the list;
 // the launch is sized to every tile of the call, and the CTAs past the list's
-// count leave at once).  Seven CTAs per SM, what the 31 KB of shared memory
-// allows.  Staging the next tile while processing one, in a persistent grid,
+// count leave at once).  Eight CTAs per SM, what 32 registers and the 26 KB of
+// shared memory (the survivors share the responses' space) allow.  Staging the next tile while processing one, in a persistent grid,
 // was slower: tiles differ widely in work, and a fixed stride or a claimed
 // counter balances them worse than the hardware's block scheduler.
-__global__ void __launch_bounds__(kDetCols * kDetRowsPar, 7)
+__global__ void __launch_bounds__(kDetCols * kDetRowsPar, 8)
 detect_kernel(const DevLevel *__restrict__ lv, const DetItem *__restrict__ list, const int32_t *__restrict__ count,
               int thr, Candidate *__restrict__ cand, int32_t *__restrict__ cand_count,
               const int32_t *__restrict__ row_lo, const int32_t *__restrict__ row_hi, const int32_t *__restrict__ unit)
