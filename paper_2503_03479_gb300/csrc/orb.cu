@@ -982,16 +982,35 @@ constexpr unsigned kV01 = 18u | 34u << 8, kV23 = 49u | 54u << 8, kV45 = 49u | 34
 constexpr unsigned kW0 = 0u | 18u << 8, kW12 = 34u | 49u << 8, kW34 = 54u | 49u << 8, kW56 = 34u | 18u << 8;
 constexpr int kHP = kPatch + 1;     // column pitch of the transposed intermediate (u16; even)
 
-__global__ void __launch_bounds__(kObWarps * 32)
+// the disc's half height at column offset |dx| <= 15: the largest hh with
+// hh^2 + dx^2 <= 15^2, four bits per |dx|
+constexpr int disc_half(int dx)
+{
+    int hh = 15;
+    while (hh * hh > kPatchR2 - dx * dx) --hh;
+    return hh;
+}
+constexpr unsigned long long disc_table()
+{
+    unsigned long long t = 0;
+    for (int d = 0; d <= 15; ++d) t |= (unsigned long long)disc_half(d) << (4 * d);
+    return t;
+}
+constexpr unsigned long long kDiscHalf = disc_table();
+static_assert(disc_half(0) == 15 && disc_half(9) == 12 && disc_half(15) == 0, "disc half heights");
+
+__global__ void __launch_bounds__(kObWarps * 32, 7)
 orient_brief_kernel(const DevLevel *__restrict__ lv, int n_views, int n_levels, int n_features, int v_begin, int v_end,
                     const SlotKp *__restrict__ slots, const int32_t *__restrict__ taken,
                     const int32_t *__restrict__ pool_off, const int *__restrict__ pattern /* [30][256] packed int8x4 */,
                     const long long *__restrict__ bins /* [30][2] Q30 */, asift_keypoint *__restrict__ kp_out,
                     uint4 *__restrict__ desc_out)
 {
+    // the smoothed patch S takes the raw patch's place once the horizontal
+    // pass and the moments are done with it
     __shared__ __align__(16) uint8_t P[kObWarps][kPatch * kPP];
     __shared__ __align__(16) uint16_t Hs[kObWarps][kSm * kHP];   // horizontal sums, column-major (column c, row r at c kHP + r)
-    __shared__ uint8_t S[kObWarps][kSm * kSm];
+    static_assert(kSm * kSm <= kPatch * kPP, "the smoothed patch fits the raw patch's space");
     __shared__ long long eb[kBins][2];
     for (int i = threadIdx.x; i < kBins * 2; i += blockDim.x) eb[i >> 1][i & 1] = bins[i];
     __syncthreads();
@@ -1059,8 +1078,7 @@ orient_brief_kernel(const DevLevel *__restrict__ lv, int n_views, int n_levels, 
     int m10 = 0, m01 = 0;
     if ((int)lane < kSm) {
         const int dx = (int)lane - 15;
-        int hh = 15;
-        while (hh * hh > kPatchR2 - dx * dx) --hh;
+        const int hh = (int)((kDiscHalf >> (4 * abs(dx))) & 15ull);
         const uint8_t *col = p + 18 * kPP + dx + 18;   // dy = 0
         int sv = 0, sy = 0;
         for (int dy = -hh; dy <= hh; ++dy) {
@@ -1082,7 +1100,7 @@ orient_brief_kernel(const DevLevel *__restrict__ lv, int n_views, int n_levels, 
     // column-major buffer; each output is dp2a's over the pairs with the taps
     // as byte pairs (exact integer sums; the pad row 37 only reaches row 31,
     // which is not kept)
-    uint8_t *sm = S[w];
+    uint8_t *sm = P[w];
     __syncwarp();
     for (int i = lane; i < kSm * 8; i += 32) {
         const int g = i / kSm, cc = i - g * kSm, r0 = 4 * g;
