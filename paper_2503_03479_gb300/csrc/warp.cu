@@ -7,7 +7,7 @@
 // floor(X(x'_last)) + 3] are the columns the tilt taps read.  The CTA:
 //   1. computes the rotated canvas C on that strip in chunks of kChunk
 //      columns; for each chunk the source pixels its 6x6 Lanczos-3 taps can
-//      reach (the bounding box of the rotated chunk, at most 72 x 72, rounded
+//      reach (the bounding box of the rotated chunk, at most 41 x 44, rounded
 //      out to 16-byte groups) are staged in shared memory with asynchronous
 //      copies, double-buffered, so every tap is a shared-memory load
 //      (Eq. (3)-(4); geometry in exact Q32 fixed point);
@@ -31,9 +31,9 @@
 
 namespace asift {
 
-constexpr int kChunk = 64;              // canvas columns per staged chunk
-constexpr int kStage = 72;              // staged source box (rows), >= 64|c| + 16|s| + 6
-constexpr int kPitchMin = 76, kPitchMax = 80;   // row pitch of the staged box (76 or 80), chosen per view
+constexpr int kChunk = 32;              // canvas columns per staged chunk
+constexpr int kStage = 41;              // staged source box (rows), >= 32|c| + 16|s| + 6
+constexpr int kPitchMin = 44, kPitchMax = 48;   // row pitch of the staged box (44 or 48), chosen per view
 constexpr int kStageBuf = kStage * kPitchMax;   // floats per staging buffer (two, double-buffered)
 
 // The hardware reciprocal (rcp.approx: relative error within one ulp).
@@ -243,9 +243,10 @@ __device__ __forceinline__ StageBox chunk_box(const CanvasGeom &G, int i_lo, int
     // multiple of 4 floats, columns >= W of the last group zero)
     b.sx0 = clampi(sx0 - 2, 0, W - 1) & ~3;
     b.sy0 = clampi(sy0 - 2, 0, H - 1);
-    // a chunk spans at most 63 columns and 15 rows of the canvas, so the box
-    // spans at most sqrt(63^2 + 15^2) + 1 + 5 < 72 = kStage source pixels,
-    // 72 + 3 + 3 -> at most 76 = kPitchMin columns once rounded out
+    // a chunk spans at most 31 columns and 15 rows of the canvas, so its
+    // corners' integer parts differ by at most sqrt(31^2 + 15^2) + 1 < 36 and
+    // the box spans at most 35 + 6 = 41 = kStage rows and 35 + 9 = 44 =
+    // kPitchMin columns once rounded out to 16-byte groups
     b.bwid = ((clampi(sx1 + 3, 0, W - 1) - b.sx0 + 1) + 3) & ~3;
     b.bhgt = clampi(sy1 + 3, 0, H - 1) - b.sy0 + 1;
     return b;
@@ -286,7 +287,7 @@ __device__ __forceinline__ void stage_box(float *dst, int P, const float *__rest
     }
 }
 
-constexpr int kMaxChunks = 24;          // chunks of a tile's canvas strip: (seg_w + 2 hK) / kChunk, seg_w <= 1024
+constexpr int kMaxChunks = 40;          // chunks of a tile's canvas strip: (seg_w + 2 hK) / kChunk, seg_w <= 1024
 
 // The first view column x in [lo, hi) whose tilt tap base max(floor(X(x)), 0)
 // is at least c (hi if none): X(x) = tq (2x - Wv + 1) + (Wr - 1) 2^31 grows with x.
@@ -332,7 +333,9 @@ __device__ __forceinline__ void warp_band_tile(int tile, const DevRotGroup *__re
     const long long HALF = 2147483648LL;
     const CanvasGeom Gm{G.cq, G.sq, (long long)(W - 1) * HALF, (long long)(H - 1) * HALF, Wr, G.Hr};
     const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    constexpr int kRowStep = kWarpThreads / kChunk;   // a thread walks its column in steps of 4 rows
+    constexpr int kRowStep = kWarpThreads / kChunk;   // step 1: a thread walks its column in steps of kRowStep rows
+    constexpr int kFiltStep = 4;                      // step 2: a thread's rows rg, rg + 4, rg + 8, rg + 12
+    static_assert(kWarpTH == 4 * kFiltStep, "step 2 keeps four rows per thread");
 
     // each member's view columns [xa, xb) for step 2, found once per tile by
     // two threads per member (visible after step 1's last barrier)
@@ -473,7 +476,7 @@ __device__ __forceinline__ void warp_band_tile(int tile, const DevRotGroup *__re
     const long long mylo = HALF, myhi = (long long)(2 * H - 3) * HALF;
     const unsigned long long mxr = (unsigned long long)(mxhi - mxlo), myr = (unsigned long long)(myhi - mylo);
     const bool fp_any = mxhi >= mxlo && myhi >= mylo;   // the shrunk footprint is empty below 2 x 2 pixels
-    const long long dpx = 2LL * kRowStep * G.sq, dpy = 2LL * kRowStep * G.cq;
+    const long long dpx = 2LL * kFiltStep * G.sq, dpy = 2LL * kFiltStep * G.cq;
     for (int m = 0; m < G.n_views; ++m) {
         const DevView &V = views[G.view[m]];
         const int xa = mcols[2 * m], xb = mcols[2 * m + 1];
@@ -524,8 +527,8 @@ __device__ __forceinline__ void warp_band_tile(int tile, const DevRotGroup *__re
                 pya -= mylo;
                 pyb -= mylo;
 #pragma unroll
-                for (int q = 0; q < kWarpTH / kRowStep; ++q, pxa += dpx, pya += dpy, pxb += dpx, pyb += dpy) {
-                    const int r = rg + q * kRowStep;
+                for (int q = 0; q < kWarpTH / kFiltStep; ++q, pxa += dpx, pya += dpy, pxb += dpx, pyb += dpy) {
+                    const int r = rg + q * kFiltStep;
                     if (r >= nrows) break;
                     const int j = j0 + r;
                     const float v = accs[q];
@@ -577,7 +580,7 @@ __global__ void tilt_filter_kernel(const DevView *__restrict__ views)
 }
 
 // Grid-stride over the tiles: one CTA per tile, or a persistent grid.
-__global__ void __launch_bounds__(kWarpThreads, 3)
+__global__ void __launch_bounds__(kWarpThreads, 4)
 warp_band_kernel(int n_tiles, const DevRotGroup *__restrict__ groups, int n_groups, const DevView *__restrict__ views,
                  int seg_w, int cwp, uint8_t *__restrict__ out_u8, uint8_t *__restrict__ out_mask,
                  float *__restrict__ out_f32)
@@ -631,7 +634,7 @@ size_t warp_band_smem_bytes(int seg_w, int hk_max)
 }
 
 // Canvas columns per band tile: a segment keeps the strip (seg_w + 2 hK
-// columns) and the staging buffers at three CTAs per SM.
+// columns) and the staging buffers at four CTAs per SM.
 int warp_seg_width_default() { return 384; }
 
 bool warp_seg_width_ok(int seg_w, int hk_max)
