@@ -379,12 +379,12 @@ typedef struct {
  * The detection runs over the list of tiles that can hold corners.
  * warp_seg is the tile shape of the view simulation: the canvas columns a
  * tile rotates once and filters for every view sharing that rotation
- * (0 = the default 384; 64 .. 1024; wider tiles recompute less of the
+ * (0 = the default 576; 64 .. 1024; wider tiles recompute less of the
  * Gaussian's halo but hold more shared memory, so fewer fit on an SM). */
 typedef struct {
     int32_t warp_grid, pyramid_grid, detect_grid, match_grid, match_target_items;
     int32_t match_engine;   /* ASIFT_MATCH_*; ASIFT_MATCH_AUTO = the context's engine */
-    int32_t warp_seg;       /* canvas columns per view-simulation tile (0 = 384) */
+    int32_t warp_seg;       /* canvas columns per view-simulation tile (0 = 576) */
 } asift_tuning;
 
 typedef struct asift_plan asift_plan;

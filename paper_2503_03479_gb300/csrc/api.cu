@@ -1604,10 +1604,10 @@ asift_status asift_plan_autotune(asift_plan *plan, int reps, asift_tuning *out)
     };
     asift_tuning &t = plan->tune;
     std::vector<Knob> knobs = {
-        {&t.warp_seg, {0, 256, 512, 768}},     // the view simulation's tile shape (0 = 384)
-        {&t.warp_grid, {0, 2 * sms, 3 * sms}},
+        {&t.warp_seg, {0, 384, 512, 768}},     // the view simulation's tile shape (0 = 576)
+        {&t.warp_grid, {0, 3 * sms, 4 * sms}},
         {&t.pyramid_grid, {0, 4 * sms, 8 * sms}},
-        {&t.detect_grid, {0, 7 * sms, 14 * sms}},
+        {&t.detect_grid, {0, 8 * sms, 16 * sms}},
     };
     if (tc_match_available()) knobs.push_back({&t.match_engine, {ASIFT_MATCH_TENSOR_CORES, ASIFT_MATCH_CUDA_CORES}});
     cudaError_t e = cudaSuccess;

@@ -635,7 +635,7 @@ size_t warp_band_smem_bytes(int seg_w, int hk_max)
 
 // Canvas columns per band tile: a segment keeps the strip (seg_w + 2 hK
 // columns) and the staging buffers at four CTAs per SM.
-int warp_seg_width_default() { return 384; }
+int warp_seg_width_default() { return 576; }
 
 bool warp_seg_width_ok(int seg_w, int hk_max)
 {

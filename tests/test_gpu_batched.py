@@ -90,7 +90,7 @@ def test_autotuner_picks_valid_shapes_and_keeps_results(A):
     t = plan.autotune(reps=2)
     assert set(t) == {"warp_grid", "pyramid_grid", "detect_grid", "match_grid", "match_target_items",
                       "match_engine", "warp_seg"}
-    assert t["warp_seg"] in (0, 256, 512, 768)
+    assert t["warp_seg"] in (0, 384, 512, 768)
     assert all(v >= 0 for v in t.values())
     # the tuner picks an engine explicitly when the device has tensor cores
     major, _ = torch.cuda.get_device_capability()
@@ -112,7 +112,7 @@ def test_every_warp_tile_shape_gives_the_same_pairs(A):
     ref = _reference(A, ctx, pairs)
     plan = A.Plan(ctx, [p[0] for p in pairs], [p[1] for p in pairs], kmax=KMAX)
     base = plan.tuning()
-    for seg in (64, 256, 512, 768, 1024):
+    for seg in (64, 256, 384, 576, 768, 1024):
         plan.set_tuning(dict(base, warp_seg=seg))
         assert plan.tuning()["warp_seg"] == seg
         plan.run()
