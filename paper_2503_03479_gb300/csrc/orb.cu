@@ -2,8 +2,9 @@
 //
 // Stages, each one launch over all (view, level) entries of a call:
 //   mask_rows_kernel    level 0: each row's hull of mask-valid columns
-//   hull_levels_kernel  levels >= 1: the hulls implied by the previous level's
-//                       through the pyramid's taps (a superset of the valid set)
+//   hull_levels_kernel  levels >= 1: the hulls implied through the pyramid's
+//                       taps (a superset of the valid set), every level at
+//                       once from level 0's
 //   pyramid_kernel      level l from level l-1: centre-aligned integer bilinear
 //                       (Q11 weights, round half up) + AND of the four mask taps
 //                       (a view whose masks are its row hulls needs no plane)
@@ -739,9 +740,10 @@ det_list_kernel(const DevLevel *__restrict__ lv, const int32_t *__restrict__ row
 
 // One CTA per listed tile (a positive grid makes it persistent over the list;
 // the launch is sized to every tile of the call, and the CTAs past the list's
-// count leave at once).  Eight CTAs per SM, what 32 registers and the 26 KB of
-// shared memory (the survivors share the responses' space) allow.  Staging the next tile while processing one, in a persistent grid,
-// was slower: tiles differ widely in work, and a fixed stride or a claimed
+// count leave at once).  Eight CTAs per SM, what 32 registers and the 26 KB
+// of shared memory (the survivors share the responses' space) allow.
+// Staging the next tile while processing one, in a persistent grid, was
+// slower: tiles differ widely in work, and a fixed stride or a claimed
 // counter balances them worse than the hardware's block scheduler.
 __global__ void __launch_bounds__(kDetCols * kDetRowsPar, 8)
 detect_kernel(const DevLevel *__restrict__ lv, const DetItem *__restrict__ list, const int32_t *__restrict__ count,
