@@ -95,6 +95,34 @@ static int level_quota(const asift_orb_cfg &cfg, const int *Ws, const int *Hs, i
     return (int)(l == 0 ? q + (cfg.n_features - used) : q);
 }
 
+// The back-projection of level l of view a: level pixel (x, y) -> view pixel
+// x0 = (x + 1/2) Wv / Wl - 1/2, y0 likewise with Hv / Hl; canvas offset
+// dx = t (x0 - (Wv - 1)/2), dy = y0 - (Hr - 1)/2; source point
+// (cos dx + sin dy) / s + (W - 1)/2, (-sin dx + cos dy) / s + (H - 1)/2, with
+// exact trig at multiples of 90 degrees as in the view table.  Composed into
+// one affine map in fp64.
+static void backprojection_map(const asift_view_desc &a, int l, double bp[6])
+{
+    double c = std::cos(a.phi_deg * (3.14159265358979323846 / 180.0));
+    double sn = std::sin(a.phi_deg * (3.14159265358979323846 / 180.0));
+    if (std::fmod(a.phi_deg, 90.0) == 0.0) {
+        const long q = ((long)(a.phi_deg / 90.0) % 4 + 4) % 4;
+        c = (q == 0) ? 1.0 : (q == 2 ? -1.0 : 0.0);
+        sn = (q == 1) ? 1.0 : (q == 3 ? -1.0 : 0.0);
+    }
+    const double cs = c / a.s, ss = sn / a.s;
+    const double rx = (double)a.Wv / (double)level_size(a.Wv, l), ry = (double)a.Hv / (double)level_size(a.Hv, l);
+    // dx = ax x + bx, dy = ay y + by
+    const double ax = a.t * rx, bx = a.t * (0.5 * rx - 0.5 - (a.Wv - 1) * 0.5);
+    const double ay = ry, by = 0.5 * ry - 0.5 - (a.Hr - 1) * 0.5;
+    bp[0] = cs * ax;
+    bp[1] = ss * ay;
+    bp[2] = cs * bx + ss * by + (a.W - 1) * 0.5;
+    bp[3] = -ss * ax;
+    bp[4] = cs * ay;
+    bp[5] = -ss * bx + cs * by + (a.H - 1) * 0.5;
+}
+
 // Level tables of n views.  Level 0 of view v is (l0_img[v], l0_mask[v]) when
 // given, otherwise it lives in the arena like the other levels.  per_view:
 // every tile_start is 0 (each entry is launched on its own).
@@ -156,6 +184,7 @@ static void build_levels(const asift_orb_cfg &cfg, const asift_view_desc *views,
             d.cand_cap = cand_capacity(cfg, d.W, d.H, cand_cap_override);
             d.cand_off = (int)T.cand_total;
             T.cand_total += d.cand_cap;
+            backprojection_map(views[v], l, d.bp);
             d.row_off = (int)T.rows_total;
             T.rows_total += d.H;
             if (l == 0) T.rows_level0 += d.H;
@@ -218,20 +247,6 @@ static void build_views(const asift_view_desc *h, int nv, const float *const *sr
         }
         d.tile_start = per_view ? 0 : tiles;
         tiles += d.ntx * ((a.Hv + kWarpTH - 1) / kWarpTH);
-        d.t = a.t;
-        // cos phi / s and sin phi / s for the back-projection, exact trig at
-        // multiples of 90 degrees as in the view table
-        {
-            double c = std::cos(a.phi_deg * (3.14159265358979323846 / 180.0));
-            double sn = std::sin(a.phi_deg * (3.14159265358979323846 / 180.0));
-            if (std::fmod(a.phi_deg, 90.0) == 0.0) {
-                const long q = ((long)(a.phi_deg / 90.0) % 4 + 4) % 4;
-                c = (q == 0) ? 1.0 : (q == 2 ? -1.0 : 0.0);
-                sn = (q == 1) ? 1.0 : (q == 3 ? -1.0 : 0.0);
-            }
-            d.cosd = c / a.s;
-            d.sind = sn / a.s;
-        }
         for (int k = 0; k < ASIFT_MAX_GAUSS; ++k) d.g[k] = (k <= a.K) ? a.g[k] : 0.f;
         d.hp = tilt_filter_pitch(a.K);
         d.filt = H ? H + hoff : nullptr;
@@ -1145,7 +1160,8 @@ static cudaError_t pipeline_run(asift_ctx *ctx, const Pipeline &L, const asift_p
         }
     }
     prof_mark(ctx, 7, s);
-    if (e == cudaSuccess) e = launch_pairs(L.probs, P, L.h_probs[0], L.total_blk, L.block_count, L.dv, L.status, s);
+    if (e == cudaSuccess)
+        e = launch_pairs(L.probs, P, L.h_probs[0], L.total_blk, L.block_count, L.o.lv, L.nv, L.status, s);
     prof_mark(ctx, 8, s);
     return e;
 }

@@ -28,7 +28,6 @@ struct DevView {
     float *filt;            // per view column x: the Gaussian + tilt filter over canvas columns x0-2-K .. x0+3+K
     long long cq, sq, tq;   // Q31 cos, sin, tilt
     long long out_off;      // byte offset of the view in the u8 / mask arenas
-    double cosd, sind, t;   // fp64 geometry for back-projection
     float g[ASIFT_MAX_GAUSS];
 };
 
@@ -83,6 +82,11 @@ struct DevLevel {
     int32_t pyr_tile_start, pyr_ntx;   // pyramid tiles (levels >= 1)
     int32_t row_off;        // first row of this level in the mask row-hull arrays
     int32_t pad_r;
+    // back-projection of a level pixel (x, y) to the source image (Eq. (2)
+    // inverted through the level's scale, the tilt and the rotation), one
+    // fp64 affine map composed on the host: x_s = bp[0] x + bp[1] y + bp[2],
+    // y_s = bp[3] x + bp[4] y + bp[5]
+    double bp[6];
 };
 
 // Mask row hulls: for every row of every level, the smallest and largest

@@ -80,7 +80,7 @@ cudaError_t launch_hamming_noalloc(const uint8_t *q, int nq, const int32_t *d_nq
                                    const int32_t *d_nt, int num, int den, asift_match *out, uint8_t *accept,
                                    int32_t *n_acc, cudaStream_t s);
 cudaError_t launch_pairs(const MatchProblem *d_probs, int n_probs, const MatchProblem &single, int total_blk,
-                         int32_t *block_count, const DevView *views, int32_t *status, cudaStream_t s);
+                         int32_t *block_count, const DevLevel *lv, int nv, int32_t *status, cudaStream_t s);
 // eval.cu
 size_t eval_workspace_bytes(int cap, int n_hyp);
 cudaError_t launch_eval(const asift_pair_match *d_pairs, const int32_t *d_n, int cap, const double *h_H_true,

@@ -238,24 +238,18 @@ pair_count_kernel(const MatchProblem *__restrict__ many, int n_probs, const Matc
     if (threadIdx.x == 0) block_count[blockIdx.x] = s;
 }
 
-// Keypoint of view V at level l, position (x, y) -> source image pixel.
-__device__ void backproject(const DevView &V, int l, int x, int y, float *sx, float *sy)
+// Keypoint at (x, y) of level entry L -> source image pixel (the level's
+// back-projection map, composed on the host in fp64).
+__device__ __forceinline__ void backproject(const DevLevel &L, int x, int y, float *sx, float *sy)
 {
-    long long p5 = 1, p6 = 1;
-    for (int i = 0; i < l; ++i) { p5 *= 5; p6 *= 6; }
-    const int Wl = (int)((2LL * V.Wv * p5 + p6) / (2 * p6));
-    const int Hl = (int)((2LL * V.Hv * p5 + p6) / (2 * p6));
-    const double x0 = (x + 0.5) * (double)V.Wv / (double)Wl - 0.5;
-    const double y0 = (y + 0.5) * (double)V.Hv / (double)Hl - 0.5;
-    const double X = V.t * (x0 - (V.Wv - 1) * 0.5) + (V.Wr - 1) * 0.5;
-    const double dx = X - (V.Wr - 1) * 0.5, dy = y0 - (V.Hr - 1) * 0.5;
-    *sx = (float)(V.cosd * dx + V.sind * dy + (V.W - 1) * 0.5);
-    *sy = (float)(-V.sind * dx + V.cosd * dy + (V.H - 1) * 0.5);
+    const double X = (double)x, Y = (double)y;
+    *sx = (float)fma(L.bp[0], X, fma(L.bp[1], Y, L.bp[2]));
+    *sy = (float)fma(L.bp[3], X, fma(L.bp[4], Y, L.bp[5]));
 }
 
 __global__ void __launch_bounds__(kPairBlock)
 pair_write_kernel(const MatchProblem *__restrict__ many, int n_probs, const MatchProblem single,
-                  const int32_t *__restrict__ block_count, const DevView *__restrict__ views,
+                  const int32_t *__restrict__ block_count, const DevLevel *__restrict__ lv, int nv,
                   int32_t *__restrict__ status)
 {
     __shared__ int wsum[kPairBlock / 32];
@@ -294,8 +288,8 @@ pair_write_kernel(const MatchProblem *__restrict__ many, int n_probs, const Matc
         if (o < P.cap && mm.best >= 0 && mm.best < count_of(P.d_nt, P.nt_cap)) {
             const asift_keypoint k1 = P.kp1[i], k2 = P.kp2[mm.best];
             asift_pair_match pm;
-            backproject(views[k1.view], k1.level, k1.x, k1.y, &pm.x1, &pm.y1);
-            backproject(views[k2.view], k2.level, k2.x, k2.y, &pm.x2, &pm.y2);
+            backproject(lv[(size_t)k1.level * nv + k1.view], k1.x, k1.y, &pm.x1, &pm.y1);
+            backproject(lv[(size_t)k2.level * nv + k2.view], k2.x, k2.y, &pm.x2, &pm.y2);
             pm.q = i;
             pm.t = mm.best;
             pm.d1 = mm.d1;
@@ -388,11 +382,11 @@ cudaError_t launch_hamming(const uint8_t *q, int nq, const int32_t *d_nq, const 
 }
 
 cudaError_t launch_pairs(const MatchProblem *d_probs, int n_probs, const MatchProblem &single, int total_blk,
-                         int32_t *block_count, const DevView *views, int32_t *status, cudaStream_t s)
+                         int32_t *block_count, const DevLevel *lv, int nv, int32_t *status, cudaStream_t s)
 {
     if (total_blk <= 0) return cudaSuccess;
     pair_count_kernel<<<total_blk, kPairBlock, 0, s>>>(d_probs, n_probs, single, block_count);
-    pair_write_kernel<<<total_blk, kPairBlock, 0, s>>>(d_probs, n_probs, single, block_count, views, status);
+    pair_write_kernel<<<total_blk, kPairBlock, 0, s>>>(d_probs, n_probs, single, block_count, lv, nv, status);
     note_launch(2);
     return cudaGetLastError();
 }
