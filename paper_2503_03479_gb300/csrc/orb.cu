@@ -417,21 +417,25 @@ __device__ __forceinline__ uint32_t compass2(uint32_t c, uint32_t n, uint32_t e,
     return ((hi + kp - c) | (c + kp - lo)) & 0x02000200u;
 }
 
+// The full FAST-9 test at a compass survivor: ring point k of the circle in
+// lane 0 and point k + 8 in lane 1 of a 16-bit pair, both tests per pair
+// with the compass test's offset kp (bit 9 of each lane), gathered into the
+// 16-bit masks of brighter and darker points.
 template <int P>
-__device__ __forceinline__ bool fast9_ring(const uint8_t *p, int thr)
+__device__ __forceinline__ bool fast9_ring(const uint8_t *p, uint32_t kp)
 {
-    const int ctr = p[0];
-    const int hi = ctr + thr, lo = ctr - thr;
-    const int v[16] = {p[-3 * P], p[-3 * P + 1], p[-2 * P + 2], p[-P + 3], p[3], p[P + 3], p[2 * P + 2],
-                       p[3 * P + 1], p[3 * P], p[3 * P - 1], p[2 * P - 2], p[P - 3], p[-3], p[-P - 3],
-                       p[-2 * P - 2], p[-3 * P - 1]};
-    unsigned bm = 0, dm = 0;
+    const uint32_t c2 = (uint32_t)p[0] * 0x00010001u;
+    const uint32_t v[16] = {p[-3 * P], p[-3 * P + 1], p[-2 * P + 2], p[-P + 3], p[3], p[P + 3], p[2 * P + 2],
+                            p[3 * P + 1], p[3 * P], p[3 * P - 1], p[2 * P - 2], p[P - 3], p[-3], p[-P - 3],
+                            p[-2 * P - 2], p[-3 * P - 1]};
+    uint32_t yb = 0u, yd = 0u;   // bits k and 16 + k: points k and k + 8
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        bm |= (unsigned)(v[k] > hi) << k;
-        dm |= (unsigned)(v[k] < lo) << k;
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t pr = v[k] | v[k + 8] << 16;
+        yb |= ((pr + kp - c2) >> (9 - k)) & (0x00010001u << k);
+        yd |= ((c2 + kp - pr) >> (9 - k)) & (0x00010001u << k);
     }
-    return has_run9(bm) || has_run9(dm);
+    return has_run9(__byte_perm(yb, 0u, 0x4420)) || has_run9(__byte_perm(yd, 0u, 0x4420));
 }
 
 // Preparation of a listed tile: its columns per ring row, and its stage:
@@ -579,7 +583,7 @@ __device__ __forceinline__ void det_process(const DetItem it, const DetGeom &G, 
             const int el = surv[q];
             r = el / kRW;
             c = el - r * kRW;
-            if (fast9_ring<P>(&S[(r - 1 + kHalo) * P + c - 1 + kHalo], thr)) {
+            if (fast9_ring<P>(&S[(r - 1 + kHalo) * P + c - 1 + kHalo], kp)) {
                 if (unit_view) {
                     flag = 1;   // the row hulls are the mask: eligible = the box's corners mask-valid
                 } else {
@@ -1046,6 +1050,7 @@ orient_brief_kernel(const DevLevel *__restrict__ lv, int n_views, int n_levels, 
         // from the two aligned words of the image row around it (both inside
         // the row for keypoints at least 22 px from its ends)
         const int q = (int)lane / 10, j = (int)lane - 10 * q;
+#pragma unroll 4   // four rows' loads in flight
         for (int rr = q; rr < kPatch; rr += 3) {
             if (lane >= 30) break;
             const uint8_t *g = L.img + (size_t)(y - 18 + rr) * W + (x - 18);
