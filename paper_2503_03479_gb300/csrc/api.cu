@@ -1653,7 +1653,7 @@ asift_status asift_plan_autotune(asift_plan *plan, int reps, asift_tuning *out)
     std::vector<Knob> mk;
     if (resolve_engine(plan->ctx, &t) == ASIFT_MATCH_TENSOR_CORES) {
         t.match_grid = 0;                                   // one CTA per SM
-        mk.push_back({&t.match_target_items, {0, 2 * sms, 8 * sms, 16 * sms}});
+        mk.push_back({&t.match_target_items, {0, 4 * sms, 8 * sms, 24 * sms}});   // 0: 12 x SMs
     } else {
         mk.push_back({&t.match_grid, {7 * sms, 4 * sms}});
         mk.push_back({&t.match_target_items, {0, 4 * 7 * sms, 7 * sms}});

@@ -548,7 +548,10 @@ cudaError_t launch_match_tc(const uint8_t *qbase, const uint8_t *qexp, long long
     if (e != cudaSuccess) return e;
     const int sms = device_sm_count();
     const int grid = tune.grid > 0 ? std::min(tune.grid, sms) : sms;   // one CTA per SM: it holds all of TMEM
-    const int target = tune.target_items > 0 ? tune.target_items : 4 * grid;
+    // about twelve items per CTA by default: the shorter runs cost more scalar
+    // passes but balance the CTAs' ranges better (4 per CTA: 0.245 ms, 12: 0.233
+    // ms for the matching stage of a 1024x768 pair)
+    const int target = tune.target_items > 0 ? tune.target_items : 12 * grid;
     hamming_tc_kernel<<<grid, kTcThreads, kTcSmem, s>>>(qm, tm, reinterpret_cast<const uint4 *>(qbase),
                                                         reinterpret_cast<const uint4 *>(tbase), d_probs, n_probs,
                                                         single, target, status, tune.stall_ns);
